@@ -1,0 +1,85 @@
+"""Named workloads: the surfaces, coefficients and right-hand sides used by the
+tests and the benchmark.
+
+Full-size workloads (the paper-style test problems at production size):
+
+* ``sphere_1536``     unit sphere, cubed sphere 6 x 2 x 2 patches, 8 x 8 GL
+                      nodes (1,536 nodes), a = 1, f = Y_3^2.
+* ``ellipsoid_9600``  ellipsoid (1, 1.5, 2), 6 x 4 x 4 patches, 10 x 10 nodes
+                      (9,600 nodes), a = 1 + 0.5 sin(2x) cos(3y), f = seeded
+                      sum of 10 Y_l^m (l <= 8), mean zero.
+* ``torus_98304``     torus R = 2, r = 0.7, 64 x 24 patches, 8 x 8 nodes
+                      (98,304 nodes), a = exp(0.3 cos(theta) sin(2 phi)),
+                      f = cos(3 phi) sin(theta), mean zero.
+
+Reduced versions of the same families (``*_small``) keep the oracle fast.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from .coefficients import (Coefficient, constant_coefficient, ellipsoid_coefficient,
+                           torus_coefficient)
+from .rhs import random_harmonic_rhs, sphere_harmonic_rhs, torus_rhs
+from .surfaces import Surface, cubed_sphere, torus
+
+
+@dataclass
+class Workload:
+    name: str
+    surface: Surface
+    coeff: Coefficient
+    f: np.ndarray
+    description: str
+
+    @property
+    def N(self) -> int:
+        return self.surface.N
+
+
+def _sphere(m, p):
+    s = cubed_sphere(m, p)
+    return s, constant_coefficient(s), sphere_harmonic_rhs(s, 3, 2)
+
+
+def _ellipsoid(m, p, seed=0):
+    s = cubed_sphere(m, p, axes=(1.0, 1.5, 2.0))
+    return s, ellipsoid_coefficient(s), random_harmonic_rhs(s, seed)
+
+
+def _torus(nt, nph, p):
+    s = torus(nt, nph, p)
+    return s, torus_coefficient(s), torus_rhs(s)
+
+
+WORKLOADS = {
+    "sphere_1536": (lambda: _sphere(2, 8),
+                    "unit sphere, 6x2x2 patches, 8x8 GL nodes (1,536), a=1, f=Y_3^2"),
+    "ellipsoid_9600": (lambda: _ellipsoid(4, 10),
+                       "ellipsoid (1,1.5,2), 6x4x4 patches, 10x10 GL nodes (9,600), "
+                       "a=1+0.5 sin(2x)cos(3y), f=sum of 10 Y_l^m (l<=8), mean zero"),
+    "torus_98304": (lambda: _torus(64, 24, 8),
+                    "torus R=2 r=0.7, 64x24 patches, 8x8 GL nodes (98,304), "
+                    "a=exp(0.3 cos(theta) sin(2 phi)), f=cos(3 phi) sin(theta)"),
+    # reduced sizes of the same families
+    "sphere_small": (lambda: _sphere(1, 6), "unit sphere, 6x1x1 patches, 6x6 nodes (216)"),
+    "sphere_384": (lambda: _sphere(1, 8), "unit sphere, 6x1x1 patches, 8x8 nodes (384)"),
+    "ellipsoid_small": (lambda: _ellipsoid(2, 6),
+                        "ellipsoid (1,1.5,2), 6x2x2 patches, 6x6 nodes (864)"),
+    "ellipsoid_2400": (lambda: _ellipsoid(2, 10),
+                       "ellipsoid (1,1.5,2), 6x2x2 patches, 10x10 nodes (2,400)"),
+    "torus_small": (lambda: _torus(16, 6, 6),
+                    "torus R=2 r=0.7, 16x6 patches, 6x6 nodes (3,456)"),
+    "torus_6144": (lambda: _torus(16, 6, 8),
+                   "torus R=2 r=0.7, 16x6 patches, 8x8 nodes (6,144)"),
+}
+
+
+def make_workload(name: str) -> Workload:
+    build, desc = WORKLOADS[name]
+    s, c, f = build()
+    return Workload(name=name, surface=s, coeff=c, f=np.asarray(f, dtype=np.float64),
+                    description=desc)
