@@ -1,0 +1,211 @@
+/*
+ * parametrix.h -- C ABI of the GB300 (sm_103a) parametrix surface-PDE library.
+ *
+ * The library discretises and solves  div_G(a grad_G u) = f  on a closed
+ * surface G with the parametrix integral-equation method of Goodwill and
+ * O'Neil ("A parametrix method for elliptic surface PDEs"):
+ *   - parametrix K(x, x') = log|x - x'| / (2 pi a(x'))           (Sec. 4.2, eq. diff_param)
+ *   - remainder  R(x, x') = (a(x)/a(x')) [ q^2/pi - H(x) q/pi ]
+ *                           + grad_G a(x) . r / (2 pi a(x') |r|^2),
+ *     r = x - x', q = n(x).r/|r|^2                  (Thm. parametrix, eq. explicit_remainder, c = 0)
+ *   - second-kind equation  sigma + R[sigma] = f,  u = K[sigma]  (Thm. second_kind, eq. IE)
+ *   - Nystrom discretisation with smooth, singular (polar) and nearly
+ *     singular (adaptive) quadrature                              (Sec. 6.1)
+ *
+ * Surface discretisation (the input of pm_surface_create): npatch
+ * quadrilateral patches, each the image of [-1,1]^2, with p x p nodes at the
+ * tensor product of the ascending p-point Gauss-Legendre nodes.  Node
+ * numbering is patch-major: global index  P*p*p + i*p + j  for node (u_i, v_j)
+ * of patch P (i along u, j along v).  N = npatch*p*p.  All array arguments
+ * are row-major, node-major (e.g. nodes[3*k + c]).
+ *
+ * Conventions for every call:
+ *   - Every function returns a pm_status; nothing aborts, traps or prints.
+ *     pm_last_error() returns a message for the calling thread's last error.
+ *   - The caller owns all arrays it passes.  Inputs are copied during the
+ *     call; the library never keeps a caller pointer.
+ *   - Host pointers must be valid for the sizes stated; device pointers
+ *     (on_device = 1) must be device memory on the context's device.
+ *   - A NULL stream means the CUDA legacy default stream.  Calls with host
+ *     buffers synchronise the stream before returning; calls with device
+ *     buffers are asynchronous on the stream.
+ *   - Handles are not thread-safe: one thread at a time per surface.
+ */
+#ifndef PARAMETRIX_H
+#define PARAMETRIX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pm_ctx pm_ctx;          /* one CUDA device                        */
+typedef struct pm_surface pm_surface;  /* geometry + near field + coefficient    */
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,       /* bad size, NULL, non-finite or inconsistent input */
+    PM_ERR_OOM = 2,               /* device or host allocation failed               */
+    PM_ERR_CUDA = 3,              /* a CUDA runtime call failed                     */
+    PM_ERR_NOT_CONVERGED = 4,     /* pm_solve: tolerance not reached in maxit       */
+    PM_ERR_BREAKDOWN = 5,         /* pm_solve: Krylov breakdown                     */
+    PM_ERR_RHS_NOT_MEAN_ZERO = 6, /* pm_solve: f has a non-zero mean (Thm. LBsolvable) */
+    PM_ERR_TIMEOUT = 7,           /* a bounded device wait ran out                  */
+    PM_ERR_INTERNAL = 8,          /* a device-side check failed (recorded, not trapped) */
+    PM_ERR_NO_COEFF = 9           /* the surface has no coefficient yet             */
+} pm_status;
+
+typedef enum {
+    PM_PREC_FP64 = 0,     /* float64 smooth sums and float64 near-field values      */
+    PM_PREC_FP32 = 1,     /* float32 smooth sums with compensated (TwoSum) tile
+                             accumulation, float32 near-field values               */
+    PM_PREC_FP32_TC = 2   /* reserved for the tensor-core FMM far field            */
+} pm_precision;
+
+/* Quadrature and solver options (pm_default_opts fills the defaults). */
+typedef struct {
+    double near_factor;     /* target is near a patch if |x - c_P| < near_factor * rho_P
+                               (c_P, rho_P: centroid and radius of the 4 corner images);
+                               Sec. 6.1.2 uses 1.5                                     */
+    double theta_tol;       /* self rule: absolute tolerance of the adaptive theta panels
+                               on int L(theta)^2 (Sec. 6.1.1 criterion); 1e-14          */
+    double theta_max_width; /* self rule: largest theta panel (radians); pi/16          */
+    double near_eta;        /* near rule: split a sub-square while the target is within
+                               2*near_eta*(its corner radius) of its centre; 1.0       */
+    int near_max_depth;     /* near rule: deepest subdivision level; 12                 */
+    int near_max_leaves;    /* near rule: leaf budget per (target, patch), <= 512; 512 */
+    int gmres_restart;      /* pm_solve: Krylov subspace size per cycle; 50             */
+    int max_refine;         /* pm_solve: iterative-refinement steps; 8                  */
+    double inner_tol;       /* pm_solve: relative tolerance of each inner float32 GMRES; 1e-6 */
+    double mean_tol;        /* pm_solve: |sum w f| / (sqrt(sum w) ||f||_w) above which f
+                               is rejected as not mean zero; 1e-8                       */
+} pm_opts;
+
+void pm_default_opts(pm_opts* opts);
+
+/* Create a context on CUDA device `device`.  *out is NULL on failure. */
+pm_status pm_ctx_create(int device, pm_ctx** out);
+void pm_ctx_destroy(pm_ctx* ctx);
+
+/*
+ * Create a surface and build its near field (Sec. 6.1).
+ *   nodes     [N*3]  positions y(u_i, v_j)
+ *   normals   [N*3]  outward unit normals
+ *   tangents  [N*6]  (dy/du, dy/dv) with respect to the [-1,1]^2 patch coordinates
+ *   curvature [N]    mean curvature H = (1/2) div_G n (outward n: H = 1/R on a sphere)
+ *   weights   [N]    smooth-rule weights w = omega_i omega_j |y_u x y_v| (Gauss weights
+ *                    omega); checked against the tangents to 1e-8 relative
+ *   opts      NULL for the defaults
+ * The near field is built once here, in float64, as coefficient-independent
+ * quadrature weights (self: polar rule of eq. radial_int; near: adaptive
+ * subdivision of Sec. 6.1.2).  Requires 2 <= p <= 11 and npatch >= 1.
+ * PM_ERR_INVALID_ARG for bad sizes, NULL arrays or non-finite/inconsistent values.
+ */
+pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p,
+                            const double* nodes, const double* normals,
+                            const double* tangents, const double* curvature,
+                            const double* weights, const pm_opts* opts,
+                            pm_surface** out);
+void pm_surface_destroy(pm_surface* s);
+
+/* Number of nodes N and near-field blocks (target, near patch) of a surface. */
+pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);
+
+/*
+ * Set the coefficient a (> 0) of div_G(a grad_G u) = f (Sec. 4.2).
+ *   a      [N]    host array, every value finite and > 0
+ *   grad_a [N*3]  host array of the surface gradient grad_G a at the nodes, or
+ *                 NULL to compute it by spectral differentiation of the patch
+ *                 interpolant of a (eq. gradg)
+ * Combines the stored quadrature weights into the near-field corrections of
+ * R and K; no quadrature is recomputed.
+ */
+pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const double* grad_a);
+
+/*
+ * Apply the discretised remainder operator: out = R~ sigma (Sec. 6.1, eq. IEsum).
+ * R~ sigma_i = sum_{j != i} w_j R(x_i, x_j) sigma_j + sum_{near k} C_ik sigma_k.
+ * The identity and the rank-one term of the solve are NOT included.
+ *   sigma, out  [nrhs*N] float64, right-hand side r at offset r*N
+ *   on_device   1: device pointers (asynchronous on stream); 0: host pointers
+ * PM_ERR_NO_COEFF before pm_surface_set_coeff.
+ */
+pm_status pm_apply_R(pm_surface* s, const double* sigma, double* out, int nrhs,
+                     pm_precision prec, int on_device, void* stream);
+
+/* out = K~ sigma, the discretised parametrix operator including 1/a(x')
+ * (eq. representation); same conventions as pm_apply_R. */
+pm_status pm_apply_K(pm_surface* s, const double* sigma, double* out, int nrhs,
+                     pm_precision prec, int on_device, void* stream);
+
+/* Parts of an apply, for testing and profiling; same conventions. */
+enum {
+    PM_PART_SMOOTH_R = 0,   /* sum_{j != i} w_j R(x_i, x_j) sigma_j only        */
+    PM_PART_SMOOTH_K = 1,   /* sum_{j != i} w_j K(x_i, x_j) sigma_j only        */
+    PM_PART_NEAR_R = 2,     /* sum_{near k} C^R_ik sigma_k only                 */
+    PM_PART_NEAR_K = 3      /* sum_{near k} C^K_ik sigma_k only                 */
+};
+pm_status pm_apply_part(pm_surface* s, int part, const double* sigma, double* out,
+                        int nrhs, pm_precision prec, int on_device, void* stream);
+
+/*
+ * Copy the near field to host arrays: row_ptr [N+1], blk_patch [nblocks]
+ * (block b of row i covers patch blk_patch[b]; the target's own patch is the
+ * first block of its row), corr_R / corr_K [nblocks*p*p] float64 corrections
+ * C_ik = W_ik / a_k - w_k F(x_i, x_k) (k != i), C_ii = W_ii / a_i.
+ * Any output pointer may be NULL.  corr_* need pm_surface_set_coeff first.
+ */
+pm_status pm_surface_get_near(const pm_surface* s, int* row_ptr, int* blk_patch,
+                              double* corr_R, double* corr_K);
+
+/* Flags of pm_solve. */
+#define PM_SOLVE_PROJECT_RHS 1u    /* subtract the mean of f instead of rejecting it */
+#define PM_SOLVE_DEVICE_PTRS 2u    /* f, u, sigma_out are device pointers            */
+
+typedef struct {
+    int iterations;          /* total inner GMRES iterations                         */
+    int refinements;         /* outer refinement steps (true-residual evaluations)   */
+    double residual;         /* final true relative residual ||f - A sigma|| / ||f|| */
+    double removed_mean;     /* mean subtracted from f (PM_SOLVE_PROJECT_RHS)         */
+    double seconds;          /* wall time of the call                                */
+} pm_solve_info;
+
+/*
+ * Solve div_G(a grad_G u) = f for the mean-zero u (Thm. LBsolvable, Thm. second_kind):
+ * (I + R~ + 1 w^T) sigma = f by float64 GMRES with float32 (prec = PM_PREC_FP32) or
+ * float64 (PM_PREC_FP64) operator applies, iterative refinement on float64 true
+ * residuals until ||f - A sigma||/||f|| <= tol, then u = K~ sigma (float64) minus
+ * its weighted mean.
+ *   f, u       [nrhs*N]  (host, or device with PM_SOLVE_DEVICE_PTRS)
+ *   sigma_out  [nrhs*N] or NULL
+ *   info       [nrhs] or NULL
+ * PM_ERR_RHS_NOT_MEAN_ZERO if f is not mean zero and PM_SOLVE_PROJECT_RHS is not set;
+ * PM_ERR_NOT_CONVERGED if tol is not met within maxit inner iterations.
+ */
+pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double tol,
+                   int maxit, pm_precision prec, unsigned flags, double* sigma_out,
+                   pm_solve_info* info, void* stream);
+
+/*
+ * Per-phase kernel timing.  While enabled, the library records a pair of CUDA
+ * events on the launching stream around every launch of each phase; reading
+ * synchronises on those events and returns the summed milliseconds and the
+ * launch count since the last reset (reset = 1 clears them).
+ */
+enum {
+    PM_PHASE_PREP = 0,        /* source strengths s = w sigma / a          */
+    PM_PHASE_DIRECT_R = 1,    /* smooth remainder sum                      */
+    PM_PHASE_DIRECT_K = 2,    /* smooth parametrix sum                     */
+    PM_PHASE_NEAR = 3,        /* near-field correction + split reduction   */
+    PM_PHASE_SOLVE_VEC = 4,   /* GMRES vector kernels                      */
+    PM_PHASE_COUNT = 5
+};
+pm_status pm_profile_enable(pm_surface* s, int enable);
+pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, int reset);
+
+const char* pm_status_str(pm_status st);
+const char* pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARAMETRIX_H */

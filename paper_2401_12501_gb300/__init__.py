@@ -1,0 +1,174 @@
+"""GB300-native parametrix solver for div_G(a grad_G u) = f on closed surfaces.
+
+The compute path is the CUDA library ``libparametrix.so`` (C ABI in
+``include/parametrix.h``); this package only marshals arguments.  Host arrays
+are numpy float64; device arrays are contiguous float64 torch CUDA tensors.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PM_PART_NEAR_K, PM_PART_NEAR_R, PM_PART_SMOOTH_K,  # noqa: F401
+                   PM_PART_SMOOTH_R, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
+                   PM_SOLVE_DEVICE_PTRS, PM_SOLVE_PROJECT_RHS, PmError, PmSolveInfo,
+                   check, default_opts, ptr)
+
+PRECISIONS = {"fp64": PM_PREC_FP64, "fp32": PM_PREC_FP32, "fp32_tc": PM_PREC_FP32_TC}
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _is_device(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Context:
+    """pm_ctx: one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        check(_lib.lib().pm_ctx_create(int(device), C.byref(h)), "pm_ctx_create")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            _lib.lib().pm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surface:
+    """pm_surface: discretised closed surface, near field and coefficient."""
+
+    def __init__(self, ctx: Context, npatch: int, p: int, nodes, normals, tangents,
+                 curvature, weights, opts=None):
+        N = npatch * p * p
+        self.ctx, self.npatch, self.p, self.N = ctx, npatch, p, N
+        arrs = [_f64(nodes, 3 * N), _f64(normals, 3 * N), _f64(tangents, 6 * N),
+                _f64(curvature, N), _f64(weights, N)]
+        h = C.c_void_p()
+        o = C.byref(opts) if opts is not None else None
+        check(_lib.lib().pm_surface_create(ctx.handle, npatch, p, *[ptr(a) for a in arrs],
+                                           o, C.byref(h)), "pm_surface_create")
+        self.handle = h
+
+    @classmethod
+    def from_fixture(cls, ctx, surf, opts=None):
+        return cls(ctx, surf.npatch, surf.p, surf.nodes, surf.normals, surf.tangents,
+                   surf.curvature, surf.weights, opts)
+
+    def close(self):
+        if self.handle:
+            _lib.lib().pm_surface_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, nb = C.c_int(), C.c_int()
+        check(_lib.lib().pm_surface_info(self.handle, C.byref(n), C.byref(nb)), "pm_surface_info")
+        return n.value, nb.value
+
+    def set_coeff(self, a, grad_a=None):
+        a = _f64(a, self.N)
+        g = None if grad_a is None else _f64(grad_a, 3 * self.N)
+        check(_lib.lib().pm_surface_set_coeff(self.handle, ptr(a), ptr(g)),
+              "pm_surface_set_coeff")
+
+    def _apply(self, fn, args, sigma, prec, stream, out=None):
+        prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        dev = _is_device(sigma)
+        if dev:
+            import torch
+            if sigma.dtype != torch.float64 or not sigma.is_contiguous():
+                raise ValueError("device sigma must be a contiguous float64 tensor")
+            nrhs = sigma.numel() // self.N
+            if out is None:
+                out = torch.empty_like(sigma)
+            st = C.c_void_p(stream if stream is not None else
+                            torch.cuda.current_stream(sigma.device).cuda_stream)
+        else:
+            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+            nrhs = sigma.size // self.N
+            out = np.empty_like(sigma) if out is None else out
+            st = C.c_void_p(stream)
+        if nrhs * self.N != (sigma.numel() if dev else sigma.size):
+            raise ValueError("sigma size is not a multiple of N")
+        check(fn(self.handle, *args, ptr(sigma), ptr(out), nrhs, prec, 1 if dev else 0, st),
+              fn.__name__)
+        return out
+
+    def apply_R(self, sigma, prec="fp32", stream=None, out=None):
+        return self._apply(_lib.lib().pm_apply_R, (), sigma, prec, stream, out)
+
+    def apply_K(self, sigma, prec="fp32", stream=None, out=None):
+        return self._apply(_lib.lib().pm_apply_K, (), sigma, prec, stream, out)
+
+    def apply_part(self, part, sigma, prec="fp32", stream=None, out=None):
+        return self._apply(_lib.lib().pm_apply_part, (int(part),), sigma, prec, stream, out)
+
+    def get_near(self, corrections=True):
+        """(row_ptr [N+1], blk_patch [nblk], corr_R, corr_K [nblk, p*p]) as numpy arrays."""
+        N, nb = self.info()
+        pp = self.p * self.p
+        rp = np.empty(N + 1, dtype=np.int32)
+        bp = np.empty(nb, dtype=np.int32)
+        cr = np.empty((nb, pp)) if corrections else None
+        ck = np.empty((nb, pp)) if corrections else None
+        check(_lib.lib().pm_surface_get_near(self.handle, ptr(rp), ptr(bp), ptr(cr), ptr(ck)),
+              "pm_surface_get_near")
+        return rp, bp, cr, ck
+
+    def profile(self, enable=True):
+        check(_lib.lib().pm_profile_enable(self.handle, 1 if enable else 0), "pm_profile_enable")
+
+    def profile_read(self, phase, reset=False):
+        """(milliseconds, launches) of one phase since the last reset."""
+        ms, n = C.c_double(), C.c_int()
+        check(_lib.lib().pm_profile_read(self.handle, int(phase), C.byref(ms), C.byref(n),
+                                         1 if reset else 0), "pm_profile_read")
+        return ms.value, n.value
+
+    def solve(self, f, tol=1e-10, maxit=2000, prec="fp32", project_rhs=False,
+              return_sigma=False, stream=None):
+        """u (mean zero) with div(a grad u) = f; returns (u, info[, sigma])."""
+        prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        dev = _is_device(f)
+        flags = (PM_SOLVE_PROJECT_RHS if project_rhs else 0) | (PM_SOLVE_DEVICE_PTRS if dev else 0)
+        if dev:
+            import torch
+            nrhs = f.numel() // self.N
+            u = torch.empty_like(f)
+            sig = torch.empty_like(f) if return_sigma else None
+            st = C.c_void_p(stream if stream is not None else
+                            torch.cuda.current_stream(f.device).cuda_stream)
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            nrhs = f.size // self.N
+            u = np.empty_like(f)
+            sig = np.empty_like(f) if return_sigma else None
+            st = C.c_void_p(stream)
+        infos = (PmSolveInfo * nrhs)()
+        check(_lib.lib().pm_solve(self.handle, ptr(f), ptr(u), nrhs, float(tol), int(maxit),
+                                  prec, flags, ptr(sig), infos, st), "pm_solve")
+        out = (u, list(infos))
+        return out + (sig,) if return_sigma else out

@@ -1,0 +1,124 @@
+"""ctypes binding of libparametrix.so (argument marshalling only).
+
+Every function here converts Python arguments to the C ABI declared in
+include/parametrix.h and raises on a non-zero status.  All computation runs
+in the CUDA library; if the library has not been built this module raises
+at import time instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libparametrix.so")
+
+PM_OK = 0
+PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC = 0, 1, 2
+PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
+PM_SOLVE_PROJECT_RHS = 1
+PM_SOLVE_DEVICE_PTRS = 2
+
+STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA",
+                4: "PM_ERR_NOT_CONVERGED", 5: "PM_ERR_BREAKDOWN",
+                6: "PM_ERR_RHS_NOT_MEAN_ZERO", 7: "PM_ERR_TIMEOUT", 8: "PM_ERR_INTERNAL",
+                9: "PM_ERR_NO_COEFF"}
+
+# every symbol include/parametrix.h declares
+EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_create",
+           "pm_surface_destroy", "pm_surface_info", "pm_surface_set_coeff", "pm_apply_R",
+           "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
+           "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read"]
+PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC = range(5)
+
+
+class PmOpts(C.Structure):
+    _fields_ = [("near_factor", C.c_double), ("theta_tol", C.c_double),
+                ("theta_max_width", C.c_double), ("near_eta", C.c_double),
+                ("near_max_depth", C.c_int), ("near_max_leaves", C.c_int),
+                ("gmres_restart", C.c_int), ("max_refine", C.c_int),
+                ("inner_tol", C.c_double), ("mean_tol", C.c_double)]
+
+
+class PmSolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
+                ("residual", C.c_double), ("removed_mean", C.c_double),
+                ("seconds", C.c_double)]
+
+
+class PmError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.pm_default_opts.argtypes = [C.POINTER(PmOpts)]
+    lib.pm_default_opts.restype = None
+    lib.pm_ctx_create.argtypes = [C.c_int, C.POINTER(P)]
+    lib.pm_ctx_destroy.argtypes = [P]
+    lib.pm_ctx_destroy.restype = None
+    lib.pm_surface_create.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P,
+                                      C.POINTER(PmOpts), C.POINTER(P)]
+    lib.pm_surface_destroy.argtypes = [P]
+    lib.pm_surface_destroy.restype = None
+    lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.pm_surface_set_coeff.argtypes = [P, P, P]
+    for name in ("pm_apply_R", "pm_apply_K"):
+        getattr(lib, name).argtypes = [P, P, P, C.c_int, C.c_int, C.c_int, P]
+    lib.pm_apply_part.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int, C.c_int, P]
+    lib.pm_surface_get_near.argtypes = [P, P, P, P, P]
+    lib.pm_solve.argtypes = [P, P, P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint,
+                             P, C.POINTER(PmSolveInfo), P]
+    lib.pm_profile_enable.argtypes = [P, C.c_int]
+    lib.pm_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
+    lib.pm_status_str.argtypes = [C.c_int]
+    lib.pm_status_str.restype = C.c_char_p
+    lib.pm_last_error.argtypes = []
+    lib.pm_last_error.restype = C.c_char_p
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def check(status: int, where: str):
+    if status != PM_OK:
+        msg = lib().pm_last_error().decode(errors="replace")
+        raise PmError(status, where, msg)
+
+
+def ptr(a) -> C.c_void_p:
+    """Address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return C.c_void_p(None)
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def default_opts() -> PmOpts:
+    o = PmOpts()
+    lib().pm_default_opts(C.byref(o))
+    return o

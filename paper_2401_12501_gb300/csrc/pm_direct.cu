@@ -1,0 +1,324 @@
+// Smooth-rule N-body sums of the remainder and the parametrix (Sec. 6.1.3).
+//
+// For every target i (its own node included among the sources, excluded from
+// the sum) with source strengths s_j = w_j sigma_j / a_j:
+//
+//   R part:  y_i = sum_{j != i} s_j [ (a_i/pi) q^2 - (a_i H_i/pi) q + g_i.r/(2 pi r^2) ],
+//            q = n_i.r / r^2,  r = x_i - x_j        (Thm. parametrix, eq. explicit_remainder)
+//   K part:  u_i = sum_{j != i} s_j log|r| / (2 pi) = (ln 2 / (4 pi)) sum s_j log2(r^2)
+//                                                    (eq. diff_param)
+//
+// The R term is evaluated in the factorised form
+//   s * inv * ( (n'.r)(n'.r) inv + m.r ),   inv = 1/r^2,
+//   n' = sqrt(a_i/pi) n_i,  m = -(a_i H_i/pi) n_i + g_i/(2 pi),
+// i.e. 16 float32 instructions and one MUFU reciprocal per pair.  The j == i
+// pair needs no branch: r^2 is formed as r.r + eps2 with eps2 far below any
+// inter-node distance, so the self pair has n'.r = m.r = 0 and contributes 0.
+//
+// float32 path: each thread keeps two targets in registers; sources (x,y,z,s)
+// are staged through shared memory in tiles of 256 and broadcast to the warp.
+// Each tile's partial sum is added to a (hi, lo) pair with TwoSum, so the
+// rounding error grows with the tile length, not with N.  Sources are split
+// over gridDim.y; each split writes hi + lo as a float64 partial that the
+// near-field kernel adds (pm_nearfield.cu).
+#include "pm_internal.cuh"
+
+#include <cmath>
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTPT = 2;                 // targets per thread
+constexpr int kTile = 256;              // sources per shared-memory tile
+constexpr int kTargetsPerBlock = kThreads * kTPT;
+static_assert(kTile == kTargetsPerBlock, "tile and target block must match (diagonal test)");
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Knuth's TwoSum: hi + lo += v with the rounding error of the addition kept.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    float s = hi + v;
+    float bp = s - hi;
+    float err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+__global__ void k_prep32(const double* __restrict__ sigma, const double* __restrict__ wa,
+                         float4* __restrict__ src, float* __restrict__ sig32, int N, int pp,
+                         int ppad) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double sg = sigma[j];
+    src[j].w = (float)(wa[j] * sg);
+    int P = j / pp;
+    sig32[(size_t)P * ppad + (j - P * pp)] = (float)sg;
+}
+
+__global__ void k_prep64(const double* __restrict__ sigma, const double* __restrict__ wa,
+                         pm_d4* __restrict__ src, int N) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    src[j].w = wa[j] * sigma[j];
+}
+
+__global__ void k_pack(const double* __restrict__ x, const double* __restrict__ n,
+                       const double* __restrict__ H, const double* __restrict__ a,
+                       const double* __restrict__ g, const double* __restrict__ w,
+                       float4* __restrict__ tgt, float4* __restrict__ src32,
+                       pm_d4* __restrict__ src64, double* __restrict__ wa, int N, int Npad,
+                       double far) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    if (i >= N) {
+        // padding sources: zero strength, far from every target (finite kernels)
+        src32[i] = make_float4((float)far, (float)far, (float)far, 0.f);
+        src64[i] = pm_d4{far, far, far, 0.0};
+        return;
+    }
+    const double xi = x[3 * i], yi = x[3 * i + 1], zi = x[3 * i + 2];
+    const double nx = n[3 * i], ny = n[3 * i + 1], nz = n[3 * i + 2];
+    const double ai = a[i];
+    const double c1 = sqrt(ai / M_PI);
+    const double cH = -ai * H[i] / M_PI;
+    const double c2 = 0.5 / M_PI;
+    tgt[i] = make_float4((float)xi, (float)yi, (float)zi, 0.f);
+    tgt[N + i] = make_float4((float)(c1 * nx), (float)(c1 * ny), (float)(c1 * nz), 0.f);
+    tgt[2 * N + i] = make_float4((float)(cH * nx + c2 * g[3 * i]), (float)(cH * ny + c2 * g[3 * i + 1]),
+                                 (float)(cH * nz + c2 * g[3 * i + 2]), 0.f);
+    src32[i] = make_float4((float)xi, (float)yi, (float)zi, 0.f);
+    src64[i] = pm_d4{xi, yi, zi, 0.0};
+    wa[i] = w[i] / ai;
+}
+
+// ------------------------------------------------------------------ float32 remainder sum
+__global__ void __launch_bounds__(kThreads)
+k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
+             int chunk, float eps2, double* __restrict__ partial) {
+    __shared__ float4 sh[kTile];
+    const int tid = threadIdx.x;
+    const int tbase = blockIdx.x * kTargetsPerBlock;
+    float tx[kTPT], ty[kTPT], tz[kTPT], nx[kTPT], ny[kTPT], nz[kTPT], mx[kTPT], my[kTPT],
+        mz[kTPT], hi[kTPT], lo[kTPT];
+#pragma unroll
+    for (int t = 0; t < kTPT; ++t) {
+        const int i = tbase + t * kThreads + tid;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
+        if (i < N) {
+            a = tgt[i];
+            b = tgt[N + i];
+            c = tgt[2 * N + i];
+        }
+        tx[t] = a.x; ty[t] = a.y; tz[t] = a.z;
+        nx[t] = b.x; ny[t] = b.y; nz[t] = b.z;
+        mx[t] = c.x; my[t] = c.y; mz[t] = c.z;
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(s0 + chunk, Npad);
+    for (int base = s0; base < s1; base += kTile) {
+        __syncthreads();
+        sh[tid] = src[base + tid];
+        sh[tid + kThreads] = src[base + kThreads + tid];
+        __syncthreads();
+        float part[kTPT];
+#pragma unroll
+        for (int t = 0; t < kTPT; ++t) part[t] = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < kTile; ++j) {
+            const float4 s = sh[j];
+#pragma unroll
+            for (int t = 0; t < kTPT; ++t) {
+                const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                const float inv = rcp_approx(r2);
+                const float nr = fmaf(nx[t], dx, fmaf(ny[t], dy, nz[t] * dz));
+                const float mr = fmaf(mx[t], dx, fmaf(my[t], dy, mz[t] * dz));
+                const float inner = fmaf(nr, nr * inv, mr);
+                part[t] = fmaf(s.w * inv, inner, part[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kTPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kTPT; ++t) {
+        const int i = tbase + t * kThreads + tid;
+        if (i < N) partial[(size_t)blockIdx.y * N + i] = (double)hi[t] + (double)lo[t];
+    }
+}
+
+// ------------------------------------------------------------------ float32 parametrix sum
+__global__ void __launch_bounds__(kThreads)
+k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
+             int chunk, double* __restrict__ partial) {
+    __shared__ float4 sh[kTile];
+    const int tid = threadIdx.x;
+    const int tbase = blockIdx.x * kTargetsPerBlock;
+    float tx[kTPT], ty[kTPT], tz[kTPT], hi[kTPT], lo[kTPT];
+#pragma unroll
+    for (int t = 0; t < kTPT; ++t) {
+        const int i = tbase + t * kThreads + tid;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N) a = tgt[i];
+        tx[t] = a.x; ty[t] = a.y; tz[t] = a.z;
+        hi[t] = 0.f; lo[t] = 0.f;
+    }
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(s0 + chunk, Npad);
+    for (int base = s0; base < s1; base += kTile) {
+        __syncthreads();
+        sh[tid] = src[base + tid];
+        sh[tid + kThreads] = src[base + kThreads + tid];
+        __syncthreads();
+        float part[kTPT];
+#pragma unroll
+        for (int t = 0; t < kTPT; ++t) part[t] = 0.f;
+        if (base != tbase) {
+#pragma unroll 8
+            for (int j = 0; j < kTile; ++j) {
+                const float4 s = sh[j];
+#pragma unroll
+                for (int t = 0; t < kTPT; ++t) {
+                    const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    part[t] = fmaf(s.w, lg2_approx(r2), part[t]);
+                }
+            }
+        } else {
+            // the tile that holds this block's own targets: skip j == i
+#pragma unroll 4
+            for (int j = 0; j < kTile; ++j) {
+                const float4 s = sh[j];
+#pragma unroll
+                for (int t = 0; t < kTPT; ++t) {
+                    const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float l = (j == t * kThreads + tid) ? 0.f : lg2_approx(r2);
+                    part[t] = fmaf(s.w, l, part[t]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kTPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
+    }
+    const double scale = M_LN2 / (4.0 * M_PI);
+#pragma unroll
+    for (int t = 0; t < kTPT; ++t) {
+        const int i = tbase + t * kThreads + tid;
+        if (i < N) partial[(size_t)blockIdx.y * N + i] = scale * ((double)hi[t] + (double)lo[t]);
+    }
+}
+
+// ------------------------------------------------------------------ float64 sums
+constexpr int kTile64 = 128;
+
+__global__ void __launch_bounds__(kThreads)
+k_direct_64(const pm_d4* __restrict__ src, const double* __restrict__ x,
+            const double* __restrict__ n, const double* __restrict__ H,
+            const double* __restrict__ a, const double* __restrict__ g, int N, int Npad,
+            int chunk, int kernel_K, double* __restrict__ partial) {
+    __shared__ pm_d4 sh[kTile64];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kThreads + tid;
+    double tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0, mx = 0, my = 0, mz = 0;
+    if (i < N) {
+        tx = x[3 * i]; ty = x[3 * i + 1]; tz = x[3 * i + 2];
+        const double c1 = sqrt(a[i] / M_PI), cH = -a[i] * H[i] / M_PI, c2 = 0.5 / M_PI;
+        nx = c1 * n[3 * i]; ny = c1 * n[3 * i + 1]; nz = c1 * n[3 * i + 2];
+        mx = cH * n[3 * i] + c2 * g[3 * i];
+        my = cH * n[3 * i + 1] + c2 * g[3 * i + 1];
+        mz = cH * n[3 * i + 2] + c2 * g[3 * i + 2];
+    }
+    double acc = 0.0;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(s0 + chunk, Npad);
+    for (int base = s0; base < s1; base += kTile64) {
+        __syncthreads();
+        sh[tid] = src[base + tid];
+        __syncthreads();
+        for (int jj = 0; jj < kTile64; ++jj) {
+            const int j = base + jj;
+            const pm_d4 s = sh[jj];
+            const double dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            double term;
+            if (kernel_K) {
+                term = s.w * log(r2);
+            } else {
+                const double inv = 1.0 / r2;
+                const double nr = nx * dx + ny * dy + nz * dz;
+                const double mr = mx * dx + my * dy + mz * dz;
+                term = s.w * inv * (nr * nr * inv + mr);
+            }
+            acc += (j == i || j >= N) ? 0.0 : term;
+        }
+    }
+    if (i < N) partial[(size_t)blockIdx.y * N + i] = kernel_K ? acc / (4.0 * M_PI) : acc;
+}
+
+}  // namespace
+
+int pm_direct_splits(const pm_surface* s, pm_precision prec) {
+    const int per_block = (prec == PM_PREC_FP64) ? kThreads : kTargetsPerBlock;
+    const int tile = (prec == PM_PREC_FP64) ? kTile64 : kTile;
+    const int tblocks = pm_ceil_div(s->N, per_block);
+    const int want = 4 * s->ctx->num_sms;
+    int ns = pm_ceil_div(want, tblocks);
+    ns = std::max(1, std::min(ns, std::min(s->max_split, s->Npad / tile)));
+    return ns;
+}
+
+pm_status pm_pack_targets(pm_surface* s, cudaStream_t st) {
+    const int N = s->N;
+    const double far = 1e3 * (1.0 + s->scale) + 1e3 * s->h_far;
+    k_pack<<<pm_ceil_div(s->Npad, 256), 256, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->w,
+                                                       s->tgt32, s->src32, s->src64, s->wa, N,
+                                                       s->Npad, far);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_prep_sources(pm_surface* s, const double* sigma, pm_precision prec,
+                          cudaStream_t st) {
+    const int N = s->N;
+    if (prec == PM_PREC_FP64)
+        k_prep64<<<pm_ceil_div(N, 256), 256, 0, st>>>(sigma, s->wa, s->src64, N);
+    else
+        k_prep32<<<pm_ceil_div(N, 256), 256, 0, st>>>(sigma, s->wa, s->src32, s->sig32, N,
+                                                       s->pp, s->ppad);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nsplit,
+                        cudaStream_t st) {
+    const int N = s->N;
+    if (prec == PM_PREC_FP64) {
+        const int chunk = pm_ceil_div(pm_ceil_div(s->Npad, nsplit), kTile64) * kTile64;
+        dim3 grid(pm_ceil_div(N, kThreads), nsplit);
+        k_direct_64<<<grid, kThreads, 0, st>>>(s->src64, s->x, s->n, s->H, s->a, s->g, N,
+                                               s->Npad, chunk, which_K, s->partial);
+    } else {
+        const int chunk = pm_ceil_div(pm_ceil_div(s->Npad, nsplit), kTile) * kTile;
+        dim3 grid(pm_ceil_div(N, kTargetsPerBlock), nsplit);
+        if (which_K)
+            k_direct_K32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
+                                                    s->partial);
+        else
+            k_direct_R32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
+                                                    s->eps2, s->partial);
+    }
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}

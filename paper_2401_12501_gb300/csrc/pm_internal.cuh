@@ -1,0 +1,210 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/parametrix.h"
+
+// ----------------------------------------------------------------------------- errors
+void pm_set_error(const char* fmt, ...);
+
+#define PM_CUDA_TRY(expr)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            pm_set_error("%s:%d: %s: %s", __FILE__, __LINE__, #expr,               \
+                         cudaGetErrorString(e_));                                  \
+            return e_ == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;     \
+        }                                                                          \
+    } while (0)
+
+#define PM_TRY(expr)                                                               \
+    do {                                                                           \
+        pm_status s_ = (expr);                                                     \
+        if (s_ != PM_OK) return s_;                                                \
+    } while (0)
+
+// Device-side error word: kernels record a failed check here (no trap).
+enum : int {
+    PM_DEV_OK = 0,
+    PM_DEV_LEAF_OVERFLOW = 1,   // near rule exceeded its leaf budget
+    PM_DEV_BAD_INDEX = 2,       // an index check failed
+    PM_DEV_NONFINITE = 3,       // a non-finite quadrature value
+};
+
+// (x, y, z, s) in float64, 32-byte aligned for one 256-bit access
+struct alignas(32) pm_d4 {
+    double x, y, z, w;
+};
+
+// ----------------------------------------------------------------------------- constants
+constexpr int PM_MAX_P = 16;
+constexpr int PM_MAX_P_API = 11;     // quadrature kernels give one basis entry per thread (p*p <= 128)
+constexpr int PM_GL16 = 16;          // points per quadrature panel
+constexpr int PM_RADIAL_PANELS = 4;  // self rule: [0,L/8],[L/8,L/4],[L/4,L/2],[L/2,L]
+
+// Host-computed tables for the quadrature kernels (constant memory).
+struct QuadTables {
+    double t[PM_MAX_P];            // p-point Gauss-Legendre nodes (ascending)
+    double wt[PM_MAX_P];           // p-point Gauss-Legendre weights
+    double bary[PM_MAX_P];         // barycentric weights of the nodes
+    double Dm[PM_MAX_P * PM_MAX_P];// Dm[i*p + a] = l_a'(t_i) (spectral differentiation)
+    double Lm[PM_MAX_P];           // l_a(-1)
+    double Lp[PM_MAX_P];           // l_a(+1)
+    double g16t[PM_GL16];          // 16-point Gauss-Legendre nodes on [-1,1]
+    double g16w[PM_GL16];          // and weights
+    double logE[PM_GL16];          // product-log correction of the first radial panel
+    int p;
+};
+
+// ----------------------------------------------------------------------------- handles
+struct pm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaDeviceProp prop{};
+};
+
+struct pm_surface {
+    pm_ctx* ctx = nullptr;
+    pm_opts opts{};
+    int npatch = 0, p = 0, pp = 0, ppad = 0, N = 0, Npad = 0;
+    double scale = 1.0;           // bounding-box diagonal (for the self-pair guard)
+    double h_far = 0.0;           // largest |coordinate| (placement of padding sources)
+    float eps2 = 0.f;             // r^2 guard of the float32 R sum
+
+    // float64 geometry (device)
+    double* x = nullptr;          // [N*3]
+    double* n = nullptr;          // [N*3]
+    double* H = nullptr;          // [N]
+    double* w = nullptr;          // [N]
+    double* J = nullptr;          // [N] |y_u x y_v|
+    double* npatch_n = nullptr;   // [N*3] normal of the interpolated patch at each node
+    double* centroid = nullptr;   // [npatch*3]
+    double* radius = nullptr;     // [npatch]
+    std::vector<double> h_x, h_w, h_tg; // host copies used for the spectral gradient
+
+    // near field (CSR over (target, patch) blocks)
+    int nblk = 0;
+    int* row_ptr = nullptr;       // [N+1]
+    int* blk_patch = nullptr;     // [nblk]
+    int* blk_row = nullptr;       // [nblk]
+    double* W_lb = nullptr;       // [nblk*pp] int (q^2 - H q)/pi l_k J~
+    double* W_g = nullptr;        // [3*nblk*pp] int r/(2 pi r^2) l_k J~ (component-major)
+    double* W_k = nullptr;        // [nblk*pp] int log|r|/(2 pi) l_k J~
+    int* dev_err = nullptr;       // device error word
+
+    // self-rule plan: theta nodes per local node
+    int* th_off = nullptr;        // [pp+1]
+    double* th_ang = nullptr;     // [nth]
+    double* th_w = nullptr;       // [nth]
+    double* th_L = nullptr;       // [nth]
+    int nth_total = 0;
+
+    // coefficient-dependent data
+    bool has_coeff = false;
+    double* a = nullptr;          // [N]
+    double* g = nullptr;          // [N*3]
+    double* wa = nullptr;         // [N] w/a
+    float4* src32 = nullptr;      // [Npad] (x, y, z, s)
+    float4* tgt32 = nullptr;      // [3*N] (x,y,z,0), (sqrt(a/pi) n, 0), (m, 0)
+    pm_d4* src64 = nullptr;     // [Npad] (x, y, z, s)
+    double* cR64 = nullptr;       // [nblk*pp]
+    double* cK64 = nullptr;       // [nblk*pp]
+    float* cR32 = nullptr;        // [nblk*ppad]
+    float* cK32 = nullptr;        // [nblk*ppad]
+
+    // per-phase timing (events recorded around launches while enabled)
+    bool profiling = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
+    double prof_ms[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
+    int prof_n[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
+
+    // scratch
+    double* partial = nullptr;    // [max_split*N]
+    int max_split = 0;
+    float* sig32 = nullptr;       // [npatch*ppad]
+    double* dbuf_in = nullptr;    // [N] host-pointer staging
+    double* dbuf_out = nullptr;   // [N]
+    size_t dbuf_n = 0;
+};
+
+// ----------------------------------------------------------------------------- modules
+// quadrature setup (host)
+void pm_build_tables(int p, QuadTables* T);
+void pm_theta_plan(const QuadTables& T, double tol, double max_width,
+                   std::vector<int>& off, std::vector<double>& ang,
+                   std::vector<double>& wts, std::vector<double>& len);
+
+// near field (pm_nearfield.cu)
+pm_status pm_near_build(pm_surface* s, const QuadTables& T);
+pm_status pm_near_combine_coeff(pm_surface* s, cudaStream_t st);
+pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double* out,
+                        int add_partials, int nsplit, pm_precision prec, cudaStream_t st);
+void pm_patch_gradient(const pm_surface* s, const QuadTables& T, const double* a,
+                       double* grad);
+
+// smooth sums (pm_direct.cu)
+int pm_direct_splits(const pm_surface* s, pm_precision prec);
+pm_status pm_prep_sources(pm_surface* s, const double* sigma, pm_precision prec,
+                          cudaStream_t st);
+pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nsplit,
+                        cudaStream_t st);
+pm_status pm_pack_targets(pm_surface* s, cudaStream_t st);
+
+// solve (pm_solve.cu)
+pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,
+                        pm_precision prec, unsigned flags, double* sigma_out,
+                        pm_solve_info* info, cudaStream_t st);
+
+// apply helpers (pm_api.cu)
+pm_status pm_apply_dev(pm_surface* s, int part_mask_K, int smooth, int near,
+                       const double* sigma, double* out, pm_precision prec,
+                       cudaStream_t st);
+pm_status pm_ensure_scratch(pm_surface* s, size_t n);
+
+// Records an event pair around the launches in its scope when profiling is on.
+struct PhaseTimer {
+    pm_surface* s;
+    int phase;
+    cudaStream_t st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PhaseTimer(pm_surface* s_, int phase_, cudaStream_t st_) : s(s_), phase(phase_), st(st_) {
+        if (s->profiling && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess)
+            cudaEventRecord(e0, st);
+    }
+    ~PhaseTimer() {
+        if (e1) {
+            cudaEventRecord(e1, st);
+            s->prof_events.push_back({phase, {e0, e1}});
+        } else if (e0) {
+            cudaEventDestroy(e0);
+        }
+    }
+};
+
+template <typename T>
+static inline pm_status pm_dmalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        pm_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                     cudaGetErrorString(e));
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
+    }
+    return PM_OK;
+}
+
+template <typename T>
+static inline void pm_dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+static inline int pm_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -1,0 +1,647 @@
+// Near field of the Nystrom discretisation (Sec. 6.1.1, 6.1.2): structure,
+// float64 quadrature weights, coefficient combination and the correction SpMV.
+//
+// For a target i and a near patch P (the target's own patch or any patch
+// whose centroid is closer than near_factor * radius, Sec. 6.1.2) the library
+// stores three coefficient-independent weight sets, for k in P:
+//
+//   W_lb[ik]  = int_P (q^2 - H_i q)/pi          l_k(u,v) J~(u,v) du dv,  q = n.r/|r|^2
+//   W_g[c,ik] = int_P r_c / (2 pi |r|^2)        l_k(u,v) J~(u,v) du dv   (c = x, y, z)
+//   W_k[ik]   = int_P log|r| / (2 pi)           l_k(u,v) J~(u,v) du dv
+//
+// with r = x_i - y~(u,v), y~ and J~ the tensor interpolants of the patch's
+// node positions and |y_u x y_v|, and l_k the tensor Lagrange basis.  Since
+// a(x') enters R and K only as 1/a(x') and a(x_i), grad a(x_i) only as
+// factors, the remainder weight of Thm. parametrix is
+//   W^R_ik = a_i W_lb[ik] + grad_a_i . W_g[:, ik]   (multiplying sigma_k / a_k),
+// so pm_surface_set_coeff only recombines.
+//
+// Self patch (eq. radial_int): polar coordinates about the target's reference
+// point; theta panels from the host plan (adaptive on int L^2, capped width);
+// four radial Gauss panels [0,L/8], [L/8,L/4], [L/4,L/2], [L/2,L], the first
+// with product-log weights for the log|r| kernel.  The normal in q is that of
+// the interpolated patch at the target, and x - y~ is formed from node
+// offsets so it keeps its precision as y~ -> x.
+// Near patches: quadtree subdivision of [-1,1]^2, splitting a square while the
+// target lies within 2*eta*(corner radius) of its centre image, 16 x 16 Gauss
+// rule on each leaf (a geometric a-priori criterion standing in for the
+// adaptive error test of Sec. 6.1.2).
+#include "pm_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace {
+
+__constant__ QuadTables cT;
+
+constexpr int kQThreads = 128;
+constexpr int kMaxLeaves = 512;
+constexpr int kMaxLevel = 1024;   // squares per BFS level
+
+// Lagrange basis l_a(u) = lambda_a prod_{b != a} (u - t_b), by prefix/suffix
+// products (no division; exact at the nodes).
+__device__ __forceinline__ void lagrange(double u, int p, double* out) {
+    double d[PM_MAX_P];
+    for (int b = 0; b < p; ++b) d[b] = u - cT.t[b];
+    double pre = 1.0;
+    for (int a = 0; a < p; ++a) {
+        out[a] = pre;
+        pre *= d[a];
+    }
+    double suf = 1.0;
+    for (int a = p - 1; a >= 0; --a) {
+        out[a] *= suf * cT.bary[a];
+        suf *= d[a];
+    }
+}
+
+// y~(u, v) for one patch from its node positions X (global layout).
+__device__ void interp_pos(const double* X, int p, double u, double v, double* y) {
+    double lu[PM_MAX_P], lv[PM_MAX_P];
+    lagrange(u, p, lu);
+    lagrange(v, p, lv);
+    double y0 = 0, y1 = 0, y2 = 0;
+    for (int a = 0; a < p; ++a) {
+        double z0 = 0, z1 = 0, z2 = 0;
+        for (int b = 0; b < p; ++b) {
+            const double* xp = X + 3 * (a * p + b);
+            z0 += xp[0] * lv[b];
+            z1 += xp[1] * lv[b];
+            z2 += xp[2] * lv[b];
+        }
+        y0 += lu[a] * z0;
+        y1 += lu[a] * z1;
+        y2 += lu[a] * z2;
+    }
+    y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
+// ------------------------------------------------------------------ patch data
+__global__ void k_patch_geom(const double* __restrict__ x, int npatch, int p,
+                             double* __restrict__ centroid, double* __restrict__ radius) {
+    int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= npatch) return;
+    const double* X = x + (size_t)3 * P * p * p;
+    const double cu[4] = {1, -1, -1, 1}, cv[4] = {1, 1, -1, -1};
+    double c[4][3];
+    for (int k = 0; k < 4; ++k) interp_pos(X, p, cu[k], cv[k], c[k]);
+    double m[3];
+    for (int d = 0; d < 3; ++d) m[d] = 0.25 * (c[0][d] + c[1][d] + c[2][d] + c[3][d]);
+    double r = 0;
+    for (int k = 0; k < 4; ++k) {
+        double dx = c[k][0] - m[0], dy = c[k][1] - m[1], dz = c[k][2] - m[2];
+        r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    for (int d = 0; d < 3; ++d) centroid[3 * P + d] = m[d];
+    radius[P] = r;
+}
+
+// Unit normal of the interpolated patch at each node (spectral derivatives).
+__global__ void k_node_normals(const double* __restrict__ x, int N, int p,
+                               double* __restrict__ nn) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int pp = p * p, P = k / pp, loc = k - P * pp, i0 = loc / p, j0 = loc % p;
+    const double* X = x + (size_t)3 * P * pp;
+    double yu[3] = {0, 0, 0}, yv[3] = {0, 0, 0};
+    for (int m = 0; m < p; ++m) {
+        const double du = cT.Dm[i0 * p + m], dv = cT.Dm[j0 * p + m];
+        for (int c = 0; c < 3; ++c) {
+            yu[c] += du * X[3 * (m * p + j0) + c];
+            yv[c] += dv * X[3 * (i0 * p + m) + c];
+        }
+    }
+    double c0 = yu[1] * yv[2] - yu[2] * yv[1];
+    double c1 = yu[2] * yv[0] - yu[0] * yv[2];
+    double c2 = yu[0] * yv[1] - yu[1] * yv[0];
+    double inv = 1.0 / sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    nn[3 * k] = c0 * inv;
+    nn[3 * k + 1] = c1 * inv;
+    nn[3 * k + 2] = c2 * inv;
+}
+
+__device__ __forceinline__ bool is_near(const double* xi, const double* cen, double rad,
+                                        double factor) {
+    double dx = xi[0] - cen[0], dy = xi[1] - cen[1], dz = xi[2] - cen[2];
+    return sqrt(dx * dx + dy * dy + dz * dz) < factor * rad;
+}
+
+__global__ void k_near_count(const double* __restrict__ x, const double* __restrict__ centroid,
+                             const double* __restrict__ radius, int N, int npatch, int pp,
+                             double factor, int* __restrict__ count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int own = i / pp;
+    int c = 1;
+    for (int P = 0; P < npatch; ++P)
+        if (P != own && is_near(x + 3 * i, centroid + 3 * P, radius[P], factor)) ++c;
+    count[i] = c;
+}
+
+__global__ void k_near_fill(const double* __restrict__ x, const double* __restrict__ centroid,
+                            const double* __restrict__ radius, int N, int npatch, int pp,
+                            double factor, const int* __restrict__ row_ptr,
+                            int* __restrict__ blk_patch, int* __restrict__ blk_row) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int own = i / pp;
+    int b = row_ptr[i];
+    const int end = row_ptr[i + 1];
+    blk_patch[b] = own;
+    blk_row[b] = i;
+    ++b;
+    for (int P = 0; P < npatch && b < end; ++P)
+        if (P != own && is_near(x + 3 * i, centroid + 3 * P, radius[P], factor)) {
+            blk_patch[b] = P;
+            blk_row[b] = i;
+            ++b;
+        }
+}
+
+// ------------------------------------------------------------------ self quadrature
+// One block per target; shared memory (doubles): D [3*pp], Jn [pp],
+// lu [128*p], lv [128*p], f [5*128].
+__global__ void __launch_bounds__(kQThreads)
+k_self_quad(int N, int p, const double* __restrict__ x, const double* __restrict__ J,
+            const double* __restrict__ nn, const double* __restrict__ H,
+            const int* __restrict__ th_off, const double* __restrict__ th_ang,
+            const double* __restrict__ th_w, const double* __restrict__ th_L,
+            const int* __restrict__ row_ptr, int nblk, double* __restrict__ W_lb,
+            double* __restrict__ W_g, double* __restrict__ W_k) {
+    extern __shared__ double sm[];
+    const int pp = p * p;
+    double* sD = sm;                       // [3][pp]
+    double* sJ = sD + 3 * pp;              // [pp]
+    double* sLu = sJ + pp;                 // [128][p]
+    double* sLv = sLu + kQThreads * p;     // [128][p]
+    double* sF = sLv + kQThreads * p;      // [5][128]
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int P = i / pp, loc = i - P * pp;
+    const double u0 = cT.t[loc / p], v0 = cT.t[loc % p];
+    const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
+    for (int k = tid; k < pp; k += kQThreads) {
+        const size_t gk = (size_t)P * pp + k;
+        sD[k] = x[3 * gk] - xi0;
+        sD[pp + k] = x[3 * gk + 1] - xi1;
+        sD[2 * pp + k] = x[3 * gk + 2] - xi2;
+        sJ[k] = J[gk];
+    }
+    const double n0 = nn[3 * i], n1 = nn[3 * i + 1], n2 = nn[3 * i + 2];
+    const double Hi = H[i];
+    const int t0 = th_off[loc], t1 = th_off[loc + 1];
+    const int npts = (t1 - t0) * (PM_RADIAL_PANELS * PM_GL16);
+    const double lo_f[4] = {0.0, 0.125, 0.25, 0.5};
+    const double hi_f[4] = {0.125, 0.25, 0.5, 1.0};
+    double acc_lb = 0, acc_g0 = 0, acc_g1 = 0, acc_g2 = 0, acc_k = 0;
+    const int a_own = tid / p, b_own = tid - (tid / p) * p;
+    __syncthreads();
+    for (int base = 0; base < npts; base += kQThreads) {
+        const int q = base + tid;
+        double* lu = sLu + tid * p;
+        double* lv = sLv + tid * p;
+        double f_lb = 0, f_g0 = 0, f_g1 = 0, f_g2 = 0, f_k = 0;
+        if (q < npts) {
+            const int kth = t0 + q / (PM_RADIAL_PANELS * PM_GL16);
+            const int rj = q % (PM_RADIAL_PANELS * PM_GL16);
+            const int panel = rj / PM_GL16, node = rj % PM_GL16;
+            const double L = th_L[kth];
+            const double h = (hi_f[panel] - lo_f[panel]) * L;
+            const double r = lo_f[panel] * L + 0.5 * h * (cT.g16t[node] + 1.0);
+            const double wr = 0.5 * h * cT.g16w[node];
+            double sn, cs;
+            sincos(th_ang[kth], &sn, &cs);
+            const double u = u0 + r * cs, v = v0 + r * sn;
+            lagrange(u, p, lu);
+            lagrange(v, p, lv);
+            double d0 = 0, d1 = 0, d2 = 0, jj = 0;
+            for (int a = 0; a < p; ++a) {
+                double z0 = 0, z1 = 0, z2 = 0, zj = 0;
+                for (int b = 0; b < p; ++b) {
+                    const double l = lv[b];
+                    const int k = a * p + b;
+                    z0 += sD[k] * l;
+                    z1 += sD[pp + k] * l;
+                    z2 += sD[2 * pp + k] * l;
+                    zj += sJ[k] * l;
+                }
+                d0 += lu[a] * z0;
+                d1 += lu[a] * z1;
+                d2 += lu[a] * z2;
+                jj += lu[a] * zj;
+            }
+            // r_vec = x_i - y~ = -(sum of offsets)
+            const double rx = -d0, ry = -d1, rz = -d2;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double inv = 1.0 / r2;
+            const double qq = (n0 * rx + n1 * ry + n2 * rz) * inv;
+            const double base_w = th_w[kth] * wr * r * jj;
+            f_lb = base_w * (qq * qq - Hi * qq) * (1.0 / M_PI);
+            const double gfac = base_w * inv * (0.5 / M_PI);
+            f_g0 = gfac * rx;
+            f_g1 = gfac * ry;
+            f_g2 = gfac * rz;
+            double lg = 0.5 * log(r2);
+            if (panel == 0) lg += cT.logE[node];
+            f_k = base_w * lg * (0.5 / M_PI);
+        } else {
+            for (int a = 0; a < p; ++a) { lu[a] = 0.0; lv[a] = 0.0; }
+        }
+        sF[tid] = f_lb;
+        sF[kQThreads + tid] = f_g0;
+        sF[2 * kQThreads + tid] = f_g1;
+        sF[3 * kQThreads + tid] = f_g2;
+        sF[4 * kQThreads + tid] = f_k;
+        __syncthreads();
+        if (tid < pp) {
+            const int lim = min(kQThreads, npts - base);
+            for (int qq = 0; qq < lim; ++qq) {
+                const double c = sLu[qq * p + a_own] * sLv[qq * p + b_own];
+                acc_lb += sF[qq] * c;
+                acc_g0 += sF[kQThreads + qq] * c;
+                acc_g1 += sF[2 * kQThreads + qq] * c;
+                acc_g2 += sF[3 * kQThreads + qq] * c;
+                acc_k += sF[4 * kQThreads + qq] * c;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < pp) {
+        const size_t b0 = (size_t)row_ptr[i];   // own patch is the row's first block
+        W_lb[b0 * pp + tid] = acc_lb;
+        W_g[(0 * (size_t)nblk + b0) * pp + tid] = acc_g0;
+        W_g[(1 * (size_t)nblk + b0) * pp + tid] = acc_g1;
+        W_g[(2 * (size_t)nblk + b0) * pp + tid] = acc_g2;
+        W_k[b0 * pp + tid] = acc_k;
+    }
+}
+
+// ------------------------------------------------------------------ near quadrature
+// One block per (target, non-self near patch).  Square codes: level (4 bits),
+// iu (12 bits), iv (12 bits); square = [-1 + 2 iu/2^l, -1 + 2 (iu+1)/2^l] x (same for v).
+__device__ __forceinline__ int sq_code(int lev, int iu, int iv) { return (lev << 24) | (iu << 12) | iv; }
+__device__ __forceinline__ void sq_box(int code, double& u0, double& u1, double& v0, double& v1) {
+    const int lev = code >> 24, iu = (code >> 12) & 0xfff, iv = code & 0xfff;
+    const double h = 2.0 / (double)(1 << lev);
+    u0 = -1.0 + iu * h;
+    u1 = u0 + h;
+    v0 = -1.0 + iv * h;
+    v1 = v0 + h;
+}
+
+__global__ void __launch_bounds__(kQThreads)
+k_near_quad(int p, int nblk, const double* __restrict__ x, const double* __restrict__ J,
+            const double* __restrict__ n, const double* __restrict__ H,
+            const int* __restrict__ blk_row, const int* __restrict__ blk_patch,
+            const int* __restrict__ row_ptr, double eta, int max_depth, int max_leaves,
+            double* __restrict__ W_lb, double* __restrict__ W_g, double* __restrict__ W_k,
+            int* __restrict__ err) {
+    const int b = blockIdx.x;
+    const int i = blk_row[b];
+    if (b == row_ptr[i]) return;   // the self block is done by k_self_quad
+    const int P = blk_patch[b];
+    const int pp = p * p;
+    const int tid = threadIdx.x;
+    __shared__ double sD[3 * PM_MAX_P * PM_MAX_P];
+    __shared__ double sJ[PM_MAX_P * PM_MAX_P];
+    __shared__ double sLu[PM_GL16 * PM_MAX_P], sLv[PM_GL16 * PM_MAX_P];
+    __shared__ double sZ[4 * PM_MAX_P * PM_GL16];     // [4][a][r]
+    __shared__ double sF[5 * PM_GL16 * PM_GL16];      // [5][q*16 + r]
+    __shared__ int sCur[kMaxLevel], sNext[kMaxLevel], sLeaf[kMaxLeaves], sSorted[kMaxLeaves];
+    __shared__ int nCur, nNext, nLeaf, overflow;
+    const double* X = x + (size_t)3 * P * pp;
+    const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
+    for (int k = tid; k < pp; k += kQThreads) {
+        const size_t gk = (size_t)P * pp + k;
+        sD[k] = x[3 * gk] - xi0;
+        sD[pp + k] = x[3 * gk + 1] - xi1;
+        sD[2 * pp + k] = x[3 * gk + 2] - xi2;
+        sJ[k] = J[gk];
+    }
+    if (tid == 0) {
+        sCur[0] = sq_code(0, 0, 0);
+        nCur = 1;
+        nLeaf = 0;
+        overflow = 0;
+    }
+    __syncthreads();
+    const int leaf_cap = min(max_leaves, kMaxLeaves);
+    // breadth-first subdivision
+    for (int lev = 0; lev <= max_depth; ++lev) {
+        if (tid == 0) nNext = 0;
+        __syncthreads();
+        for (int s = tid; s < nCur; s += kQThreads) {
+            const int code = sCur[s];
+            double u0, u1, v0, v1;
+            sq_box(code, u0, u1, v0, v1);
+            const double us[5] = {u0, u1, u1, u0, 0.5 * (u0 + u1)};
+            const double vs[5] = {v0, v0, v1, v1, 0.5 * (v0 + v1)};
+            double y[5][3];
+            for (int k = 0; k < 5; ++k) interp_pos(X, p, us[k], vs[k], y[k]);
+            double size = 0;
+            for (int k = 0; k < 4; ++k) {
+                const double dx = y[k][0] - y[4][0], dy = y[k][1] - y[4][1], dz = y[k][2] - y[4][2];
+                size = fmax(size, sqrt(dx * dx + dy * dy + dz * dz));
+            }
+            const double dx = xi0 - y[4][0], dy = xi1 - y[4][1], dz = xi2 - y[4][2];
+            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            const bool split = (lev < max_depth) && (dist < 2.0 * eta * size);
+            if (split) {
+                const int slot = atomicAdd(&nNext, 4);
+                if (slot + 4 <= kMaxLevel) {
+                    const int l1 = lev + 1, iu = (code >> 12) & 0xfff, iv = code & 0xfff;
+                    sNext[slot] = sq_code(l1, 2 * iu, 2 * iv);
+                    sNext[slot + 1] = sq_code(l1, 2 * iu + 1, 2 * iv);
+                    sNext[slot + 2] = sq_code(l1, 2 * iu, 2 * iv + 1);
+                    sNext[slot + 3] = sq_code(l1, 2 * iu + 1, 2 * iv + 1);
+                } else {
+                    overflow = 1;
+                }
+            } else {
+                const int slot = atomicAdd(&nLeaf, 1);
+                if (slot < leaf_cap) sLeaf[slot] = code; else overflow = 1;
+            }
+        }
+        __syncthreads();
+        const int nn_ = min(nNext, kMaxLevel);
+        for (int s = tid; s < nn_; s += kQThreads) sCur[s] = sNext[s];
+        __syncthreads();
+        if (tid == 0) nCur = nn_;
+        __syncthreads();
+        if (nCur == 0) break;
+    }
+    const int nleaves = min(nLeaf, leaf_cap);
+    if (overflow && tid == 0) atomicExch(err, PM_DEV_LEAF_OVERFLOW);
+    // deterministic leaf order: rank sort by code
+    for (int s = tid; s < nleaves; s += kQThreads) {
+        const int c = sLeaf[s];
+        int rank = 0;
+        for (int t = 0; t < nleaves; ++t) rank += (sLeaf[t] < c);
+        sSorted[rank] = c;
+    }
+    __syncthreads();
+    const int a_own = tid / p, b_own = tid - (tid / p) * p;
+    double acc[5] = {0, 0, 0, 0, 0};
+    const double n0 = n[3 * i], n1 = n[3 * i + 1], n2 = n[3 * i + 2];
+    const double Hi = H[i];
+    for (int L = 0; L < nleaves; ++L) {
+        double u0, u1, v0, v1;
+        sq_box(sSorted[L], u0, u1, v0, v1);
+        const double hu = 0.5 * (u1 - u0), hv = 0.5 * (v1 - v0);
+        if (tid < PM_GL16) lagrange(u0 + hu * (cT.g16t[tid] + 1.0), p, sLu + tid * p);
+        else if (tid < 2 * PM_GL16)
+            lagrange(v0 + hv * (cT.g16t[tid - PM_GL16] + 1.0), p, sLv + (tid - PM_GL16) * p);
+        __syncthreads();
+        // Z[c][a][r] = sum_b D_c[a][b] l_b(v_r)  (c = 3: J)
+        for (int e = tid; e < 4 * p * PM_GL16; e += kQThreads) {
+            const int c = e / (p * PM_GL16), rem = e - c * p * PM_GL16;
+            const int a = rem / PM_GL16, r = rem - a * PM_GL16;
+            const double* src = (c < 3) ? (sD + c * pp) : sJ;
+            double z = 0;
+            for (int bb = 0; bb < p; ++bb) z += src[a * p + bb] * sLv[r * p + bb];
+            sZ[(c * p + a) * PM_GL16 + r] = z;
+        }
+        __syncthreads();
+        for (int e = tid; e < PM_GL16 * PM_GL16; e += kQThreads) {
+            const int qn = e / PM_GL16, r = e - qn * PM_GL16;
+            double d0 = 0, d1 = 0, d2 = 0, jj = 0;
+            for (int a = 0; a < p; ++a) {
+                const double l = sLu[qn * p + a];
+                d0 += l * sZ[(0 * p + a) * PM_GL16 + r];
+                d1 += l * sZ[(1 * p + a) * PM_GL16 + r];
+                d2 += l * sZ[(2 * p + a) * PM_GL16 + r];
+                jj += l * sZ[(3 * p + a) * PM_GL16 + r];
+            }
+            const double rx = -d0, ry = -d1, rz = -d2;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            const double inv = 1.0 / r2;
+            const double qq = (n0 * rx + n1 * ry + n2 * rz) * inv;
+            const double wgt = hu * cT.g16w[qn] * hv * cT.g16w[r] * jj;
+            sF[e] = wgt * (qq * qq - Hi * qq) * (1.0 / M_PI);
+            const double gfac = wgt * inv * (0.5 / M_PI);
+            sF[256 + e] = gfac * rx;
+            sF[512 + e] = gfac * ry;
+            sF[768 + e] = gfac * rz;
+            sF[1024 + e] = wgt * 0.25 / M_PI * log(r2);
+        }
+        __syncthreads();
+        // T[k][a][r] = sum_q F[k][q][r] l_a(u_q)  (reuse sZ region is too small; use a loop)
+        if (tid < pp) {
+            for (int r = 0; r < PM_GL16; ++r) {
+                double t5[5] = {0, 0, 0, 0, 0};
+                for (int qn = 0; qn < PM_GL16; ++qn) {
+                    const double l = sLu[qn * p + a_own];
+                    const int e = qn * PM_GL16 + r;
+                    t5[0] += sF[e] * l;
+                    t5[1] += sF[256 + e] * l;
+                    t5[2] += sF[512 + e] * l;
+                    t5[3] += sF[768 + e] * l;
+                    t5[4] += sF[1024 + e] * l;
+                }
+                const double lb = sLv[r * p + b_own];
+                for (int k = 0; k < 5; ++k) acc[k] += t5[k] * lb;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < pp) {
+        const size_t o = (size_t)b * pp + tid;
+        W_lb[o] = acc[0];
+        W_g[0 * (size_t)nblk * pp + o] = acc[1];
+        W_g[1 * (size_t)nblk * pp + o] = acc[2];
+        W_g[2 * (size_t)nblk * pp + o] = acc[3];
+        W_k[o] = acc[4];
+    }
+}
+
+// ------------------------------------------------------------------ coefficient combination
+__global__ void k_combine(int nblk, int pp, int ppad, const int* __restrict__ blk_row,
+                          const int* __restrict__ blk_patch, const double* __restrict__ x,
+                          const double* __restrict__ n, const double* __restrict__ H,
+                          const double* __restrict__ w, const double* __restrict__ a,
+                          const double* __restrict__ g, const double* __restrict__ W_lb,
+                          const double* __restrict__ W_g, const double* __restrict__ W_k,
+                          double* __restrict__ cR64, double* __restrict__ cK64,
+                          float* __restrict__ cR32, float* __restrict__ cK32) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)nblk * ppad) return;
+    const int b = (int)(e / ppad), k = (int)(e - (size_t)b * ppad);
+    if (k >= pp) {
+        cR32[e] = 0.f;
+        cK32[e] = 0.f;
+        return;
+    }
+    const int i = blk_row[b], P = blk_patch[b];
+    const int j = P * pp + k;
+    const size_t o = (size_t)b * pp + k;
+    const size_t nv = (size_t)nblk * pp;
+    const double ai = a[i];
+    const double WR = ai * W_lb[o] + g[3 * i] * W_g[o] + g[3 * i + 1] * W_g[nv + o] +
+                      g[3 * i + 2] * W_g[2 * nv + o];
+    double cr, ck;
+    if (j == i) {
+        cr = WR / ai;
+        ck = W_k[o] / ai;
+    } else {
+        const double aj = a[j];
+        const double rx = x[3 * i] - x[3 * j], ry = x[3 * i + 1] - x[3 * j + 1],
+                     rz = x[3 * i + 2] - x[3 * j + 2];
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double q = (n[3 * i] * rx + n[3 * i + 1] * ry + n[3 * i + 2] * rz) / r2;
+        const double Rij = (ai / aj) * (q * q - H[i] * q) / M_PI +
+                           (g[3 * i] * rx + g[3 * i + 1] * ry + g[3 * i + 2] * rz) /
+                               (2.0 * M_PI * aj * r2);
+        const double Kij = log(r2) / (4.0 * M_PI * aj);
+        cr = WR / aj - w[j] * Rij;
+        ck = W_k[o] / aj - w[j] * Kij;
+    }
+    cR64[o] = cr;
+    cK64[o] = ck;
+    cR32[e] = (float)cr;
+    cK32[e] = (float)ck;
+}
+
+// ------------------------------------------------------------------ correction SpMV
+// One warp per target row: out_i = sum_s partial[s][i] + sum_b C[b, :] . sigma[patch_b]
+__global__ void k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
+                               const int* __restrict__ blk_patch, const float* __restrict__ vals,
+                               const float* __restrict__ sig32, const double* __restrict__ partial,
+                               int nsplit, int use_near, double* __restrict__ out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= N) return;
+    const int i = warp;
+    double acc = (lane < nsplit) ? partial[(size_t)lane * N + i] : 0.0;
+    if (use_near) {
+        float accf = 0.f;
+        const int q4 = ppad >> 2;
+        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+            const float4* v4 = reinterpret_cast<const float4*>(vals + (size_t)b * ppad);
+            const float4* s4 = reinterpret_cast<const float4*>(sig32 + (size_t)blk_patch[b] * ppad);
+            for (int k = lane; k < q4; k += 32) {
+                const float4 v = __ldg(v4 + k), s = __ldg(s4 + k);
+                accf = fmaf(v.x, s.x, fmaf(v.y, s.y, fmaf(v.z, s.z, fmaf(v.w, s.w, accf))));
+            }
+        }
+        acc += (double)accf;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = acc;
+}
+
+__global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
+                               const int* __restrict__ blk_patch, const double* __restrict__ vals,
+                               const double* __restrict__ sigma, const double* __restrict__ partial,
+                               int nsplit, int use_near, double* __restrict__ out) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= N) return;
+    const int i = warp;
+    double acc = (lane < nsplit) ? partial[(size_t)lane * N + i] : 0.0;
+    if (use_near) {
+        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+            const double* v = vals + (size_t)b * pp;
+            const double* sg = sigma + (size_t)blk_patch[b] * pp;
+            for (int k = lane; k < pp; k += 32) acc += v[k] * sg[k];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[i] = acc;
+}
+
+}  // namespace
+
+pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
+    const int N = s->N, npatch = s->npatch, p = s->p, pp = s->pp;
+    PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
+    PM_TRY(pm_dmalloc(&s->centroid, 3 * (size_t)npatch));
+    PM_TRY(pm_dmalloc(&s->radius, npatch));
+    PM_TRY(pm_dmalloc(&s->npatch_n, 3 * (size_t)N));
+    PM_TRY(pm_dmalloc(&s->row_ptr, (size_t)N + 1));
+    PM_TRY(pm_dmalloc(&s->dev_err, 1));
+    PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
+    k_patch_geom<<<pm_ceil_div(npatch, 128), 128>>>(s->x, npatch, p, s->centroid, s->radius);
+    k_node_normals<<<pm_ceil_div(N, 128), 128>>>(s->x, N, p, s->npatch_n);
+    int* count = nullptr;
+    PM_TRY(pm_dmalloc(&count, N));
+    k_near_count<<<pm_ceil_div(N, 128), 128>>>(s->x, s->centroid, s->radius, N, npatch, pp,
+                                                s->opts.near_factor, count);
+    PM_CUDA_TRY(cudaGetLastError());
+    std::vector<int> hc(N), hr(N + 1);
+    cudaError_t e = cudaMemcpy(hc.data(), count, sizeof(int) * N, cudaMemcpyDeviceToHost);
+    cudaFree(count);
+    if (e != cudaSuccess) {
+        pm_set_error("near count copy: %s", cudaGetErrorString(e));
+        return PM_ERR_CUDA;
+    }
+    hr[0] = 0;
+    for (int i = 0; i < N; ++i) {
+        if (hc[i] < 1 || hc[i] > npatch) {
+            pm_set_error("near list count %d out of range at row %d", hc[i], i);
+            return PM_ERR_INTERNAL;
+        }
+        hr[i + 1] = hr[i] + hc[i];
+    }
+    s->nblk = hr[N];
+    PM_CUDA_TRY(cudaMemcpy(s->row_ptr, hr.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice));
+    PM_TRY(pm_dmalloc(&s->blk_patch, s->nblk));
+    PM_TRY(pm_dmalloc(&s->blk_row, s->nblk));
+    k_near_fill<<<pm_ceil_div(N, 128), 128>>>(s->x, s->centroid, s->radius, N, npatch, pp,
+                                               s->opts.near_factor, s->row_ptr, s->blk_patch,
+                                               s->blk_row);
+    PM_CUDA_TRY(cudaGetLastError());
+    const size_t nv = (size_t)s->nblk * pp;
+    PM_TRY(pm_dmalloc(&s->W_lb, nv));
+    PM_TRY(pm_dmalloc(&s->W_g, 3 * nv));
+    PM_TRY(pm_dmalloc(&s->W_k, nv));
+    const size_t smem = sizeof(double) * (4 * (size_t)pp + 2 * (size_t)kQThreads * p + 5 * kQThreads);
+    if (smem > 48 * 1024)
+        PM_CUDA_TRY(cudaFuncSetAttribute(k_self_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    k_self_quad<<<N, kQThreads, smem>>>(N, p, s->x, s->J, s->npatch_n, s->H, s->th_off,
+                                        s->th_ang, s->th_w, s->th_L, s->row_ptr, s->nblk,
+                                        s->W_lb, s->W_g, s->W_k);
+    PM_CUDA_TRY(cudaGetLastError());
+    k_near_quad<<<s->nblk, kQThreads>>>(p, s->nblk, s->x, s->J, s->n, s->H, s->blk_row,
+                                        s->blk_patch, s->row_ptr, s->opts.near_eta,
+                                        std::min(s->opts.near_max_depth, 12),
+                                        s->opts.near_max_leaves, s->W_lb, s->W_g, s->W_k,
+                                        s->dev_err);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    int herr = 0;
+    PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != PM_DEV_OK) {
+        pm_set_error("near-field quadrature: device check %d failed (leaf budget exceeded)", herr);
+        return PM_ERR_INTERNAL;
+    }
+    return PM_OK;
+}
+
+pm_status pm_near_combine_coeff(pm_surface* s, cudaStream_t st) {
+    const size_t ne = (size_t)s->nblk * s->ppad;
+    k_combine<<<pm_ceil_div((long long)ne, 256), 256, 0, st>>>(
+        s->nblk, s->pp, s->ppad, s->blk_row, s->blk_patch, s->x, s->n, s->H, s->w, s->a, s->g,
+        s->W_lb, s->W_g, s->W_k, s->cR64, s->cK64, s->cR32, s->cK32);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double* out,
+                        int use_near, int nsplit, pm_precision prec, cudaStream_t st) {
+    const int N = s->N;
+    const int threads = 256;
+    const int blocks = pm_ceil_div((long long)N * 32, threads);
+    if (prec == PM_PREC_FP64)
+        k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
+                                                   which_K ? s->cK64 : s->cR64, sigma,
+                                                   s->partial, nsplit, use_near, out);
+    else
+        k_near_apply32<<<blocks, threads, 0, st>>>(N, s->ppad, s->row_ptr, s->blk_patch,
+                                                   which_K ? s->cK32 : s->cR32, s->sig32,
+                                                   s->partial, nsplit, use_near, out);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}

@@ -1,0 +1,177 @@
+"""GPU parity of the operator applies against the float64 oracle (through the C ABI).
+
+Tolerances: float64 applies agree with the oracle to 1e-10 relative (the two
+sides use different quadrature rules, each converged to ~1e-13); float32
+applies to 2e-6 relative L2 (per-pair float32 rounding, compensated
+accumulation), inside the 1e-5 bound stated for float32 applies.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import oracle_processes
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def oracle(name, rows=None):
+    from oracle.operator import Discretization, NearField
+    key = (name, None if rows is None else tuple(rows))
+    if key not in _ORACLE:
+        wl = make_workload(name)
+        d = Discretization.from_workload(wl)
+        nf = NearField(d, rows=rows, processes=oracle_processes())
+        _ORACLE[key] = (wl, d, nf)
+    return _ORACLE[key]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_12501_gb300 as pm
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+_SURF = {}
+
+
+def gpu_surface(ctx, name):
+    import paper_2401_12501_gb300 as pm
+    if name not in _SURF:
+        wl = make_workload(name)
+        s = pm.Surface.from_fixture(ctx, wl.surface)
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        _SURF[name] = (wl, s)
+    return _SURF[name]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["sphere_384", "ellipsoid_small"])
+def test_near_structure_and_corrections(ctx, name):
+    wl, d, nf = oracle(name)
+    _, s = gpu_surface(ctx, name)
+    rp, bp, cR, cK = s.get_near()
+    pp = d.p * d.p
+    assert rp[0] == 0 and rp[-1] == len(bp)
+    for i in range(d.N):
+        gpu_patches = list(bp[rp[i]:rp[i + 1]])
+        ora = nf.corr[i]
+        assert gpu_patches[0] == i // pp                      # own patch first
+        assert sorted(gpu_patches) == sorted(P for P, _, _ in ora)
+        sR = max(np.abs(c[1]).max() for c in ora)
+        sK = max(np.abs(c[2]).max() for c in ora)
+        for P, CR, CK in ora:
+            b = rp[i] + gpu_patches.index(P)
+            assert np.abs(cR[b] - CR).max() <= 1e-10 * sR, (i, P)
+            assert np.abs(cK[b] - CK).max() <= 1e-10 * sK, (i, P)
+
+
+@pytest.mark.parametrize("name", ["sphere_384", "ellipsoid_small"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
+def test_full_apply_parity(ctx, name, prec, tol):
+    from oracle.operator import apply_K, apply_R
+    wl, d, nf = oracle(name)
+    _, s = gpu_surface(ctx, name)
+    rng = np.random.default_rng(1)
+    sigma = rng.standard_normal(d.N) + 1.0
+    assert rel(s.apply_R(sigma, prec), apply_R(d, nf, sigma)) < tol
+    assert rel(s.apply_K(sigma, prec), apply_K(d, nf, sigma)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_smooth_parts(ctx, prec, tol):
+    import paper_2401_12501_gb300 as pm
+    wl, d, _ = oracle("ellipsoid_small")
+    _, s = gpu_surface(ctx, "ellipsoid_small")
+    sigma = np.random.default_rng(2).standard_normal(d.N)
+    assert rel(s.apply_part(pm.PM_PART_SMOOTH_R, sigma, prec), d.smooth_apply("R", sigma)) < tol
+    assert rel(s.apply_part(pm.PM_PART_SMOOTH_K, sigma, prec), d.smooth_apply("K", sigma)) < tol
+
+
+@pytest.mark.parametrize("name", ["sphere_1536", "ellipsoid_9600", "torus_98304"])
+def test_sampled_rows_full_size(ctx, name):
+    """Full-size workloads: sampled rows computed one by one by the oracle."""
+    from oracle.operator import apply_K, apply_R
+    wl = make_workload(name)
+    N, pp = wl.N, wl.surface.p ** 2
+    rng = np.random.default_rng(3)
+    rows = sorted(set([0, pp - 1, N - 1] + list(rng.integers(0, N, 21))))
+    _, d, nf = oracle(name, rows)
+    _, s = gpu_surface(ctx, name)
+    sigma = rng.standard_normal(N) + 1.0
+    oR = apply_R(d, nf, sigma, rows)
+    oK = apply_K(d, nf, sigma, rows)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+        yR = s.apply_R(sigma, prec)[rows]
+        yK = s.apply_K(sigma, prec)[rows]
+        assert np.abs(yR - oR).max() <= tol * np.abs(oR).max(), (prec, yR, oR)
+        assert np.abs(yK - oK).max() <= tol * np.abs(oK).max(), (prec, yK, oK)
+
+
+def test_sphere_remainder_closed_form(ctx):
+    """Unit sphere, a = 1: R~ sigma = -(1/4 pi) sum_j w_j sigma_j at every node."""
+    wl, s = gpu_surface(ctx, "sphere_1536")
+    sigma = np.random.default_rng(4).standard_normal(wl.N) + 0.5
+    want = -np.dot(wl.surface.weights, sigma) / (4 * np.pi)
+    assert np.abs(s.apply_R(sigma, "fp64") - want).max() < 1e-7 * abs(want)
+    assert np.abs(s.apply_R(sigma, "fp32") - want).max() < 1e-5 * abs(want)
+
+
+def test_multi_rhs_and_device_pointers(ctx):
+    import torch
+    wl, s = gpu_surface(ctx, "ellipsoid_small")
+    sig = np.random.default_rng(5).standard_normal((3, wl.N))
+    for prec in ("fp32", "fp64"):
+        host = s.apply_R(sig, prec)
+        dev = s.apply_R(torch.from_numpy(sig).cuda(), prec).cpu().numpy()
+        single = np.stack([s.apply_R(sig[r], prec) for r in range(3)])
+        assert np.array_equal(host, dev)          # deterministic kernels
+        assert np.array_equal(host, single)
+
+
+def test_invalid_inputs(ctx):
+    import paper_2401_12501_gb300 as pm
+    wl = make_workload("sphere_small")
+    sf = wl.surface
+    bad_w = sf.weights.copy()
+    bad_w[5] *= 1.01
+    with pytest.raises(pm.PmError) as e:
+        pm.Surface(ctx, sf.npatch, sf.p, sf.nodes, sf.normals, sf.tangents, sf.curvature, bad_w)
+    assert e.value.status == 1
+    nodes = sf.nodes.copy()
+    nodes[3, 1] = np.nan
+    with pytest.raises(pm.PmError) as e:
+        pm.Surface(ctx, sf.npatch, sf.p, nodes, sf.normals, sf.tangents, sf.curvature, sf.weights)
+    assert e.value.status == 1
+    s = pm.Surface.from_fixture(ctx, sf)
+    with pytest.raises(pm.PmError) as e:
+        s.apply_R(np.ones(sf.N))
+    assert e.value.status == 9                    # PM_ERR_NO_COEFF
+    with pytest.raises(pm.PmError) as e:
+        s.set_coeff(-np.ones(sf.N))
+    assert e.value.status == 1
+    s.close()
+
+
+def test_spectral_gradient_matches_closed_form(ctx):
+    """grad_a = NULL: the library differentiates the interpolant of a (eq. gradg)."""
+    import paper_2401_12501_gb300 as pm
+    wl = make_workload("ellipsoid_9600")
+    s = pm.Surface.from_fixture(ctx, wl.surface)
+    s.set_coeff(wl.coeff.a)          # spectral gradient
+    s2 = gpu_surface(ctx, "ellipsoid_9600")[1]
+    sigma = np.random.default_rng(6).standard_normal(wl.N)
+    a = s.apply_R(sigma, "fp64")
+    b = s2.apply_R(sigma, "fp64")
+    assert rel(a, b) < 1e-5
+    s.close()

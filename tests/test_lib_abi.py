@@ -1,0 +1,53 @@
+"""The C-ABI library loads and exports every symbol include/parametrix.h declares
+(no compute calls: this runs without a GPU)."""
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "parametrix.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(pm_[a-z_A-Z]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_12501_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2401_12501_gb300 import _lib
+    declared = declared_symbols()
+    assert len(declared) >= 14
+    assert set(declared) == set(_lib.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\sT\s(pm_\w+)", out))
+    for name in declared:
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_status_strings_and_defaults(lib):
+    import ctypes as C
+    from paper_2401_12501_gb300 import _lib
+    for st in range(10):
+        assert lib.pm_status_str(st)
+    o = _lib.default_opts()
+    assert o.near_factor == 1.5 and o.near_max_leaves <= 512
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    import ctypes as C
+    assert lib.pm_ctx_create(0, None) == 1           # PM_ERR_INVALID_ARG
+    assert lib.pm_surface_info(None, None, None) == 1
+    assert lib.pm_profile_enable(None, 1) == 1
