@@ -250,6 +250,7 @@ extern "C" void pm_ctx_destroy(pm_ctx* c) { delete c; }
 static void free_surface(pm_surface* s) {
     if (!s) return;
     if (s->ctx) cudaSetDevice(s->ctx->device);
+    pm_solve_free(s);
     pm_dfree(s->x); pm_dfree(s->n); pm_dfree(s->H); pm_dfree(s->w); pm_dfree(s->J);
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);

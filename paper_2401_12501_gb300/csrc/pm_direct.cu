@@ -56,7 +56,8 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 
 __global__ void k_prep32(const double* __restrict__ sigma, const double* __restrict__ wa,
                          float4* __restrict__ src, float* __restrict__ sig32, int N, int pp,
-                         int ppad) {
+                         int ppad, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     double sg = sigma[j];
@@ -66,7 +67,8 @@ __global__ void k_prep32(const double* __restrict__ sigma, const double* __restr
 }
 
 __global__ void k_prep64(const double* __restrict__ sigma, const double* __restrict__ wa,
-                         pm_d4* __restrict__ src, int N) {
+                         pm_d4* __restrict__ src, int N, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     src[j].w = wa[j] * sigma[j];
@@ -104,7 +106,8 @@ __global__ void k_pack(const double* __restrict__ x, const double* __restrict__ 
 // ------------------------------------------------------------------ float32 remainder sum
 __global__ void __launch_bounds__(kThreads)
 k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
-             int chunk, float eps2, double* __restrict__ partial) {
+             int chunk, float eps2, double* __restrict__ partial, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ float4 sh[kTile];
     const int tid = threadIdx.x;
     const int tbase = blockIdx.x * kTargetsPerBlock;
@@ -161,7 +164,8 @@ k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
 // ------------------------------------------------------------------ float32 parametrix sum
 __global__ void __launch_bounds__(kThreads)
 k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
-             int chunk, double* __restrict__ partial) {
+             int chunk, double* __restrict__ partial, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ float4 sh[kTile];
     const int tid = threadIdx.x;
     const int tbase = blockIdx.x * kTargetsPerBlock;
@@ -227,7 +231,8 @@ __global__ void __launch_bounds__(kThreads)
 k_direct_64(const pm_d4* __restrict__ src, const double* __restrict__ x,
             const double* __restrict__ n, const double* __restrict__ H,
             const double* __restrict__ a, const double* __restrict__ g, int N, int Npad,
-            int chunk, int kernel_K, double* __restrict__ partial) {
+            int chunk, int kernel_K, double* __restrict__ partial, const int* __restrict__ skip) {
+    if (skip && *skip) return;
     __shared__ pm_d4 sh[kTile64];
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kThreads + tid;
@@ -293,10 +298,10 @@ pm_status pm_prep_sources(pm_surface* s, const double* sigma, pm_precision prec,
                           cudaStream_t st) {
     const int N = s->N;
     if (prec == PM_PREC_FP64)
-        k_prep64<<<pm_ceil_div(N, 256), 256, 0, st>>>(sigma, s->wa, s->src64, N);
+        k_prep64<<<pm_ceil_div(N, 256), 256, 0, st>>>(sigma, s->wa, s->src64, N, s->skip_flag);
     else
         k_prep32<<<pm_ceil_div(N, 256), 256, 0, st>>>(sigma, s->wa, s->src32, s->sig32, N,
-                                                       s->pp, s->ppad);
+                                                       s->pp, s->ppad, s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
@@ -308,16 +313,17 @@ pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nspli
         const int chunk = pm_ceil_div(pm_ceil_div(s->Npad, nsplit), kTile64) * kTile64;
         dim3 grid(pm_ceil_div(N, kThreads), nsplit);
         k_direct_64<<<grid, kThreads, 0, st>>>(s->src64, s->x, s->n, s->H, s->a, s->g, N,
-                                               s->Npad, chunk, which_K, s->partial);
+                                               s->Npad, chunk, which_K, s->partial,
+                                               s->skip_flag);
     } else {
         const int chunk = pm_ceil_div(pm_ceil_div(s->Npad, nsplit), kTile) * kTile;
         dim3 grid(pm_ceil_div(N, kTargetsPerBlock), nsplit);
         if (which_K)
             k_direct_K32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
-                                                    s->partial);
+                                                    s->partial, s->skip_flag);
         else
             k_direct_R32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
-                                                    s->eps2, s->partial);
+                                                    s->eps2, s->partial, s->skip_flag);
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;

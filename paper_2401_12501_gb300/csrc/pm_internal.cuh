@@ -68,6 +68,8 @@ struct pm_ctx {
     cudaDeviceProp prop{};
 };
 
+struct PmSolveWork;
+
 struct pm_surface {
     pm_ctx* ctx = nullptr;
     pm_opts opts{};
@@ -123,6 +125,11 @@ struct pm_surface {
     double prof_ms[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
     int prof_n[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
 
+    // solve workspace (pm_solve.cu) and the device flag that lets the apply
+    // kernels of a finished Krylov cycle return at once
+    PmSolveWork* solve_work = nullptr;
+    const int* skip_flag = nullptr;
+
     // scratch
     double* partial = nullptr;    // [max_split*N]
     int max_split = 0;
@@ -159,6 +166,8 @@ pm_status pm_pack_targets(pm_surface* s, cudaStream_t st);
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,
                         pm_precision prec, unsigned flags, double* sigma_out,
                         pm_solve_info* info, cudaStream_t st);
+
+void pm_solve_free(pm_surface* s);
 
 // apply helpers (pm_api.cu)
 pm_status pm_apply_dev(pm_surface* s, int part_mask_K, int smooth, int near,

@@ -508,7 +508,9 @@ __global__ void k_combine(int nblk, int pp, int ppad, const int* __restrict__ bl
 __global__ void k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
                                const int* __restrict__ blk_patch, const float* __restrict__ vals,
                                const float* __restrict__ sig32, const double* __restrict__ partial,
-                               int nsplit, int use_near, double* __restrict__ out) {
+                               int nsplit, int use_near, double* __restrict__ out,
+                               const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
@@ -534,7 +536,9 @@ __global__ void k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
                                const int* __restrict__ blk_patch, const double* __restrict__ vals,
                                const double* __restrict__ sigma, const double* __restrict__ partial,
-                               int nsplit, int use_near, double* __restrict__ out) {
+                               int nsplit, int use_near, double* __restrict__ out,
+                               const int* __restrict__ skip) {
+    if (skip && *skip) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
@@ -637,11 +641,13 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
     if (prec == PM_PREC_FP64)
         k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK64 : s->cR64, sigma,
-                                                   s->partial, nsplit, use_near, out);
+                                                   s->partial, nsplit, use_near, out,
+                                                   s->skip_flag);
     else
         k_near_apply32<<<blocks, threads, 0, st>>>(N, s->ppad, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK32 : s->cR32, s->sig32,
-                                                   s->partial, nsplit, use_near, out);
+                                                   s->partial, nsplit, use_near, out,
+                                                   s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }

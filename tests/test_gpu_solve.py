@@ -1,0 +1,132 @@
+"""GPU solve (device GMRES + iterative refinement + representation) against the oracle.
+
+* Unit sphere, a = 1, f = Y_3^2 (1,536 nodes): u = -f/12 to discretisation
+  accuracy, and the oracle's dense solve to 1e-8 relative L2, in both the
+  float64 and the refined float32 operator precision.
+* Variable coefficient (ellipsoid, 864 nodes): oracle dense solve to 1e-8.
+* Full-size ellipsoid (9,600 nodes): the GPU sigma satisfies the ORACLE's
+  discrete equation at sampled rows (residual computed by the oracle row by
+  row), and u equals the oracle's K~ sigma at those rows minus the mean.
+* Mean handling (Thm. LBsolvable): a non-mean-zero f is rejected unless the
+  projection flag is set; u is mean zero.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import oracle_processes
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+_CACHE = {}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_12501_gb300 as pm
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+def setup(ctx, name):
+    import paper_2401_12501_gb300 as pm
+    if name not in _CACHE:
+        wl = make_workload(name)
+        s = pm.Surface.from_fixture(ctx, wl.surface)
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        _CACHE[name] = (wl, s)
+    return _CACHE[name]
+
+
+_OR = {}
+
+
+def oracle_solution(name):
+    from oracle.operator import Discretization, NearField
+    from oracle.solve import solve
+    if name not in _OR:
+        wl = make_workload(name)
+        d = Discretization.from_workload(wl)
+        nf = NearField(d, processes=oracle_processes())
+        u, sig, _ = solve(d, nf, wl.f, return_sigma=True)
+        _OR[name] = (d, nf, u, sig)
+    return _OR[name]
+
+
+def rel_l2(a, b, w):
+    return float(np.sqrt(np.dot(w, (a - b) ** 2) / np.dot(w, b * b)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sphere_eigenfunction_solve(ctx, prec):
+    wl, s = setup(ctx, "sphere_1536")
+    u, info = s.solve(wl.f, tol=1e-11, prec=prec)
+    w = wl.surface.weights
+    assert info[0].residual <= 1e-11
+    assert rel_l2(u, -wl.f / 12, w) < 1e-5            # discretisation error
+    d, nf, uo, so = oracle_solution("sphere_1536")
+    assert rel_l2(u, uo, w) < 1e-8
+    assert abs(np.dot(w, u)) < 1e-12 * np.sqrt(np.dot(w, u * u))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_variable_coefficient_solve_matches_oracle(ctx, prec):
+    wl, s = setup(ctx, "ellipsoid_small")
+    u, info, sig = s.solve(wl.f, tol=1e-11, prec=prec, return_sigma=True)
+    d, nf, uo, so = oracle_solution("ellipsoid_small")
+    w = wl.surface.weights
+    assert rel_l2(u, uo, w) < 1e-8
+    assert rel_l2(sig, so, w) < 1e-8
+    if prec == "fp32":
+        assert info[0].refinements >= 2                 # float64 residual refinement used
+
+
+def test_full_size_solution_satisfies_oracle_equation(ctx):
+    from oracle.operator import Discretization, NearField, apply_K, apply_R
+    wl, s = setup(ctx, "ellipsoid_9600")
+    u, info, sig = s.solve(wl.f, tol=1e-10, prec="fp32", return_sigma=True)
+    assert info[0].residual <= 1e-10
+    d = Discretization.from_workload(wl)
+    rng = np.random.default_rng(7)
+    rows = sorted(set([0, 99, wl.N - 1] + [int(i) for i in rng.integers(0, wl.N, 13)]))
+    nf = NearField(d, rows=rows, processes=oracle_processes())
+    w = wl.surface.weights
+    A_sig = sig[rows] + apply_R(d, nf, sig, rows) + np.dot(w, sig)
+    assert np.abs(A_sig - wl.f[rows]).max() < 1e-8 * np.abs(wl.f).max()
+    # u = K~ sigma - mean: compare the mean-free parts at the sampled rows
+    Ks = apply_K(d, nf, sig, rows)
+    full_K = s.apply_K(sig, "fp64")
+    mean = np.dot(w, full_K) / w.sum()
+    assert np.abs(full_K[rows] - Ks).max() < 1e-10 * np.abs(Ks).max()
+    assert np.abs(u[rows] - (Ks - mean)).max() < 1e-9 * np.abs(u).max()
+
+
+def test_mean_handling(ctx):
+    import paper_2401_12501_gb300 as pm
+    wl, s = setup(ctx, "ellipsoid_small")
+    f = wl.f + 0.3
+    with pytest.raises(pm.PmError) as e:
+        s.solve(f, tol=1e-10)
+    assert e.value.status == 6                           # PM_ERR_RHS_NOT_MEAN_ZERO
+    u, info = s.solve(f, tol=1e-10, project_rhs=True)
+    assert abs(info[0].removed_mean - 0.3) < 1e-12
+    u0, _ = s.solve(wl.f, tol=1e-10)
+    w = wl.surface.weights
+    assert rel_l2(u, u0, w) < 1e-9
+
+
+def test_device_pointers_and_batch(ctx):
+    import torch
+    wl, s = setup(ctx, "ellipsoid_small")
+    f2 = np.stack([wl.f, -2.0 * wl.f])
+    u_h, infos = s.solve(f2, tol=1e-10)
+    u_d, _ = s.solve(torch.from_numpy(f2).cuda(), tol=1e-10)
+    assert np.allclose(u_h, u_d.cpu().numpy(), rtol=0, atol=1e-12 * np.abs(u_h).max())
+    w = wl.surface.weights
+    assert rel_l2(u_h[1], -2.0 * u_h[0], w) < 1e-9
+    assert len(infos) == 2 and all(i.residual <= 1e-10 for i in infos)
