@@ -78,6 +78,9 @@ typedef struct {
     double inner_tol;       /* pm_solve: relative tolerance of each inner float32 GMRES; 1e-6 */
     double mean_tol;        /* pm_solve: |sum w f| / (sqrt(sum w) ||f||_w) above which f
                                is rejected as not mean zero; 1e-8                       */
+    int direct_tpt;         /* float32 smooth sums: targets per thread (1, 2 or 4); 0 = auto */
+    int direct_blocks_per_sm; /* float32 smooth sums: source splits chosen so the grid holds
+                               about this many blocks per SM (1..16); 0 = auto          */
 } pm_opts;
 
 void pm_default_opts(pm_opts* opts);
@@ -106,6 +109,13 @@ pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p,
                             const double* weights, const pm_opts* opts,
                             pm_surface** out);
 void pm_surface_destroy(pm_surface* s);
+
+/*
+ * Change the float32 smooth-sum launch shape of an existing surface (the
+ * autotuner's knobs; no quadrature is recomputed).  direct_tpt in {0,1,2,4},
+ * direct_blocks_per_sm in 0..16 (0 = automatic choice).
+ */
+pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_blocks_per_sm);
 
 /* Number of nodes N and near-field blocks (target, near patch) of a surface. */
 pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);

@@ -83,6 +83,10 @@ class Surface:
         except Exception:
             pass
 
+    def tune(self, direct_tpt=0, direct_blocks_per_sm=0):
+        check(_lib.lib().pm_surface_tune(self.handle, int(direct_tpt), int(direct_blocks_per_sm)),
+              "pm_surface_tune")
+
     def info(self):
         n, nb = C.c_int(), C.c_int()
         check(_lib.lib().pm_surface_info(self.handle, C.byref(n), C.byref(nb)), "pm_surface_info")

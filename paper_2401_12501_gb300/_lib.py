@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR
 EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_create",
            "pm_surface_destroy", "pm_surface_info", "pm_surface_set_coeff", "pm_apply_R",
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
-           "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read"]
+           "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
+           "pm_surface_tune"]
 PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC = range(5)
 
 
@@ -40,7 +41,8 @@ class PmOpts(C.Structure):
                 ("theta_max_width", C.c_double), ("near_eta", C.c_double),
                 ("near_max_depth", C.c_int), ("near_max_leaves", C.c_int),
                 ("gmres_restart", C.c_int), ("max_refine", C.c_int),
-                ("inner_tol", C.c_double), ("mean_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("mean_tol", C.c_double),
+                ("direct_tpt", C.c_int), ("direct_blocks_per_sm", C.c_int)]
 
 
 class PmSolveInfo(C.Structure):
@@ -70,6 +72,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                       C.POINTER(PmOpts), C.POINTER(P)]
     lib.pm_surface_destroy.argtypes = [P]
     lib.pm_surface_destroy.restype = None
+    lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.pm_surface_set_coeff.argtypes = [P, P, P]
     for name in ("pm_apply_R", "pm_apply_K"):

@@ -58,6 +58,8 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->max_refine = 8;
     o->inner_tol = 1e-6;
     o->mean_tol = 1e-8;
+    o->direct_tpt = 0;
+    o->direct_blocks_per_sm = 0;
 }
 
 // ----------------------------------------------------------------------------- tables
@@ -394,6 +396,17 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
 #undef PM_STEP
 #undef PM_CSTEP
     *out = s;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_blocks_per_sm) {
+    if (!s || !(direct_tpt == 0 || direct_tpt == 1 || direct_tpt == 2 || direct_tpt == 4) ||
+        direct_blocks_per_sm < 0 || direct_blocks_per_sm > 16) {
+        pm_set_error("pm_surface_tune: NULL surface or knob out of range");
+        return PM_ERR_INVALID_ARG;
+    }
+    s->opts.direct_tpt = direct_tpt;
+    s->opts.direct_blocks_per_sm = direct_blocks_per_sm;
     return PM_OK;
 }
 

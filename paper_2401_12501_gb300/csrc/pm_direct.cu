@@ -23,6 +23,7 @@
 // near-field kernel adds (pm_nearfield.cu).
 #include "pm_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace {
@@ -31,7 +32,6 @@ constexpr int kThreads = 128;
 constexpr int kTPT = 2;                 // targets per thread
 constexpr int kTile = 256;              // sources per shared-memory tile
 constexpr int kTargetsPerBlock = kThreads * kTPT;
-static_assert(kTile == kTargetsPerBlock, "tile and target block must match (diagonal test)");
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
@@ -104,17 +104,24 @@ __global__ void k_pack(const double* __restrict__ x, const double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ float32 remainder sum
+// Block = 128 threads x TPT targets; blockIdx.y selects a source chunk of any
+// length (the chunks split N evenly, so every block has the same work).  The
+// chunk is staged through shared memory in stages of kStage sources; every
+// kTile sources the tile partial is folded into (hi, lo) with TwoSum.
+constexpr int kStage = 1024;
+
+template <int TPT>
 __global__ void __launch_bounds__(kThreads)
-k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
-             int chunk, float eps2, double* __restrict__ partial, const int* __restrict__ skip) {
+k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int chunk,
+             float eps2, float2* __restrict__ partial, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    __shared__ float4 sh[kTile];
+    __shared__ float4 sh[kStage];
     const int tid = threadIdx.x;
-    const int tbase = blockIdx.x * kTargetsPerBlock;
-    float tx[kTPT], ty[kTPT], tz[kTPT], nx[kTPT], ny[kTPT], nz[kTPT], mx[kTPT], my[kTPT],
-        mz[kTPT], hi[kTPT], lo[kTPT];
+    const int tbase = blockIdx.x * kThreads * TPT;
+    float tx[TPT], ty[TPT], tz[TPT], nx[TPT], ny[TPT], nz[TPT], mx[TPT], my[TPT], mz[TPT],
+        hi[TPT], lo[TPT];
 #pragma unroll
-    for (int t = 0; t < kTPT; ++t) {
+    for (int t = 0; t < TPT; ++t) {
         const int i = tbase + t * kThreads + tid;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a, c = a;
         if (i < N) {
@@ -128,50 +135,55 @@ k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
         hi[t] = 0.f; lo[t] = 0.f;
     }
     const int s0 = blockIdx.y * chunk;
-    const int s1 = min(s0 + chunk, Npad);
-    for (int base = s0; base < s1; base += kTile) {
+    const int s1 = min(s0 + chunk, N);
+    for (int base = s0; base < s1; base += kStage) {
+        const int len = min(kStage, s1 - base);
         __syncthreads();
-        sh[tid] = src[base + tid];
-        sh[tid + kThreads] = src[base + kThreads + tid];
+        for (int j = tid; j < len; j += kThreads) sh[j] = src[base + j];
         __syncthreads();
-        float part[kTPT];
+        for (int j0 = 0; j0 < len; j0 += kTile) {
+            const int j1 = min(j0 + kTile, len);
+            float part[TPT];
 #pragma unroll
-        for (int t = 0; t < kTPT; ++t) part[t] = 0.f;
-#pragma unroll 8
-        for (int j = 0; j < kTile; ++j) {
-            const float4 s = sh[j];
+            for (int t = 0; t < TPT; ++t) part[t] = 0.f;
+#pragma unroll 4
+            for (int j = j0; j < j1; ++j) {
+                const float4 s = sh[j];
 #pragma unroll
-            for (int t = 0; t < kTPT; ++t) {
-                const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                const float inv = rcp_approx(r2);
-                const float nr = fmaf(nx[t], dx, fmaf(ny[t], dy, nz[t] * dz));
-                const float mr = fmaf(mx[t], dx, fmaf(my[t], dy, mz[t] * dz));
-                const float inner = fmaf(nr, nr * inv, mr);
-                part[t] = fmaf(s.w * inv, inner, part[t]);
+                for (int t = 0; t < TPT; ++t) {
+                    const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                    const float inv = rcp_approx(r2);
+                    const float nr = fmaf(nx[t], dx, fmaf(ny[t], dy, nz[t] * dz));
+                    const float mr = fmaf(mx[t], dx, fmaf(my[t], dy, mz[t] * dz));
+                    const float inner = fmaf(nr, nr * inv, mr);
+                    part[t] = fmaf(s.w * inv, inner, part[t]);
+                }
             }
-        }
 #pragma unroll
-        for (int t = 0; t < kTPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
+            for (int t = 0; t < TPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
+        }
     }
 #pragma unroll
-    for (int t = 0; t < kTPT; ++t) {
+    for (int t = 0; t < TPT; ++t) {
         const int i = tbase + t * kThreads + tid;
-        if (i < N) partial[(size_t)blockIdx.y * N + i] = (double)hi[t] + (double)lo[t];
+        if (i < N) partial[(size_t)blockIdx.y * N + i] = make_float2(hi[t], lo[t]);
     }
 }
 
 // ------------------------------------------------------------------ float32 parametrix sum
+template <int TPT>
 __global__ void __launch_bounds__(kThreads)
-k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int Npad,
-             int chunk, double* __restrict__ partial, const int* __restrict__ skip) {
+k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int chunk,
+             float2* __restrict__ partial, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    __shared__ float4 sh[kTile];
+    __shared__ float4 sh[kStage];
     const int tid = threadIdx.x;
-    const int tbase = blockIdx.x * kTargetsPerBlock;
-    float tx[kTPT], ty[kTPT], tz[kTPT], hi[kTPT], lo[kTPT];
+    const int tbase = blockIdx.x * kThreads * TPT;
+    const int tend = tbase + kThreads * TPT;
+    float tx[TPT], ty[TPT], tz[TPT], hi[TPT], lo[TPT];
 #pragma unroll
-    for (int t = 0; t < kTPT; ++t) {
+    for (int t = 0; t < TPT; ++t) {
         const int i = tbase + t * kThreads + tid;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         if (i < N) a = tgt[i];
@@ -179,48 +191,51 @@ k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
         hi[t] = 0.f; lo[t] = 0.f;
     }
     const int s0 = blockIdx.y * chunk;
-    const int s1 = min(s0 + chunk, Npad);
-    for (int base = s0; base < s1; base += kTile) {
+    const int s1 = min(s0 + chunk, N);
+    for (int base = s0; base < s1; base += kStage) {
+        const int len = min(kStage, s1 - base);
         __syncthreads();
-        sh[tid] = src[base + tid];
-        sh[tid + kThreads] = src[base + kThreads + tid];
+        for (int j = tid; j < len; j += kThreads) sh[j] = src[base + j];
         __syncthreads();
-        float part[kTPT];
+        for (int j0 = 0; j0 < len; j0 += kTile) {
+            const int j1 = min(j0 + kTile, len);
+            float part[TPT];
 #pragma unroll
-        for (int t = 0; t < kTPT; ++t) part[t] = 0.f;
-        if (base != tbase) {
-#pragma unroll 8
-            for (int j = 0; j < kTile; ++j) {
-                const float4 s = sh[j];
-#pragma unroll
-                for (int t = 0; t < kTPT; ++t) {
-                    const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    part[t] = fmaf(s.w, lg2_approx(r2), part[t]);
-                }
-            }
-        } else {
-            // the tile that holds this block's own targets: skip j == i
+            for (int t = 0; t < TPT; ++t) part[t] = 0.f;
+            // does this tile hold one of the block's own targets (j == i)?
+            if (base + j1 <= tbase || base + j0 >= tend) {
 #pragma unroll 4
-            for (int j = 0; j < kTile; ++j) {
-                const float4 s = sh[j];
+                for (int j = j0; j < j1; ++j) {
+                    const float4 s = sh[j];
 #pragma unroll
-                for (int t = 0; t < kTPT; ++t) {
-                    const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float l = (j == t * kThreads + tid) ? 0.f : lg2_approx(r2);
-                    part[t] = fmaf(s.w, l, part[t]);
+                    for (int t = 0; t < TPT; ++t) {
+                        const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        part[t] = fmaf(s.w, lg2_approx(r2), part[t]);
+                    }
+                }
+            } else {
+                for (int j = j0; j < j1; ++j) {
+                    const float4 s = sh[j];
+#pragma unroll
+                    for (int t = 0; t < TPT; ++t) {
+                        const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float l = (base + j == tbase + t * kThreads + tid) ? 0.f : lg2_approx(r2);
+                        part[t] = fmaf(s.w, l, part[t]);
+                    }
                 }
             }
+#pragma unroll
+            for (int t = 0; t < TPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
         }
-#pragma unroll
-        for (int t = 0; t < kTPT; ++t) two_sum_acc(hi[t], lo[t], part[t]);
     }
-    const double scale = M_LN2 / (4.0 * M_PI);
+    const float scale = (float)(M_LN2 / (4.0 * M_PI));
 #pragma unroll
-    for (int t = 0; t < kTPT; ++t) {
+    for (int t = 0; t < TPT; ++t) {
         const int i = tbase + t * kThreads + tid;
-        if (i < N) partial[(size_t)blockIdx.y * N + i] = scale * ((double)hi[t] + (double)lo[t]);
+        // scaling (hi, lo) by a float keeps the pair's relative accuracy
+        if (i < N) partial[(size_t)blockIdx.y * N + i] = make_float2(hi[t] * scale, lo[t] * scale);
     }
 }
 
@@ -274,13 +289,19 @@ k_direct_64(const pm_d4* __restrict__ src, const double* __restrict__ x,
 
 }  // namespace
 
+static int direct_tpt(const pm_surface* s) {
+    const int t = s->opts.direct_tpt;
+    return (t == 1 || t == 2 || t == 4) ? t : 2;
+}
+
 int pm_direct_splits(const pm_surface* s, pm_precision prec) {
-    const int per_block = (prec == PM_PREC_FP64) ? kThreads : kTargetsPerBlock;
-    const int tile = (prec == PM_PREC_FP64) ? kTile64 : kTile;
+    const int per_block = (prec == PM_PREC_FP64) ? kThreads : kThreads * direct_tpt(s);
     const int tblocks = pm_ceil_div(s->N, per_block);
-    const int want = 4 * s->ctx->num_sms;
-    int ns = pm_ceil_div(want, tblocks);
-    ns = std::max(1, std::min(ns, std::min(s->max_split, s->Npad / tile)));
+    int bps = s->opts.direct_blocks_per_sm;
+    if (bps < 1 || bps > 16) bps = 8;
+    const int want = bps * s->ctx->num_sms;
+    int ns = (want + tblocks / 2) / tblocks;            // nearest split count
+    ns = std::max(1, std::min(ns, std::min(s->max_split, std::max(1, s->N / 64))));
     return ns;
 }
 
@@ -316,14 +337,19 @@ pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nspli
                                                s->Npad, chunk, which_K, s->partial,
                                                s->skip_flag);
     } else {
-        const int chunk = pm_ceil_div(pm_ceil_div(s->Npad, nsplit), kTile) * kTile;
-        dim3 grid(pm_ceil_div(N, kTargetsPerBlock), nsplit);
-        if (which_K)
-            k_direct_K32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
-                                                    s->partial, s->skip_flag);
-        else
-            k_direct_R32<<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, s->Npad, chunk,
-                                                    s->eps2, s->partial, s->skip_flag);
+        const int tpt = direct_tpt(s);
+        const int chunk = pm_ceil_div(N, nsplit);
+        dim3 grid(pm_ceil_div(N, kThreads * tpt), nsplit);
+        float2* part = reinterpret_cast<float2*>(s->partial);
+#define PM_LAUNCH(T)                                                                        \
+        if (which_K)                                                                        \
+            k_direct_K32<T><<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, chunk, part,  \
+                                                       s->skip_flag);                       \
+        else                                                                                \
+            k_direct_R32<T><<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, chunk,        \
+                                                       s->eps2, part, s->skip_flag);
+        if (tpt == 1) { PM_LAUNCH(1) } else if (tpt == 4) { PM_LAUNCH(4) } else { PM_LAUNCH(2) }
+#undef PM_LAUNCH
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;

@@ -504,33 +504,74 @@ __global__ void k_combine(int nblk, int pp, int ppad, const int* __restrict__ bl
 }
 
 // ------------------------------------------------------------------ correction SpMV
-// One warp per target row: out_i = sum_s partial[s][i] + sum_b C[b, :] . sigma[patch_b]
-__global__ void k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
-                               const int* __restrict__ blk_patch, const float* __restrict__ vals,
-                               const float* __restrict__ sig32, const double* __restrict__ partial,
-                               int nsplit, int use_near, double* __restrict__ out,
-                               const int* __restrict__ skip) {
+// One warp per target row: out_i = sum_s partial[s][i] + sum_b C[b, :] . sigma[patch_b].
+// float32 path: the row's blocks are contiguous, so the warp walks the flat
+// list of float4 values (four loads in flight per lane); the split partials
+// (hi, lo) and the lane sums are combined with TwoSum in float32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+__global__ void __launch_bounds__(256)
+k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
+               const int* __restrict__ blk_patch, const float* __restrict__ vals,
+               const float* __restrict__ sig32, const float2* __restrict__ partial,
+               int nsplit, int use_near, double* __restrict__ out,
+               const int* __restrict__ skip) {
     if (skip && *skip) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
     const int i = warp;
-    double acc = (lane < nsplit) ? partial[(size_t)lane * N + i] : 0.0;
-    if (use_near) {
-        float accf = 0.f;
-        const int q4 = ppad >> 2;
-        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
-            const float4* v4 = reinterpret_cast<const float4*>(vals + (size_t)b * ppad);
-            const float4* s4 = reinterpret_cast<const float4*>(sig32 + (size_t)blk_patch[b] * ppad);
-            for (int k = lane; k < q4; k += 32) {
-                const float4 v = __ldg(v4 + k), s = __ldg(s4 + k);
-                accf = fmaf(v.x, s.x, fmaf(v.y, s.y, fmaf(v.z, s.z, fmaf(v.w, s.w, accf))));
-            }
-        }
-        acc += (double)accf;
+    float hi = 0.f, lo = 0.f;
+    for (int sp = lane; sp < nsplit; sp += 32) {
+        const float2 v = partial[(size_t)sp * N + i];
+        float s, e;
+        two_sum(hi, v.x, s, e);
+        hi = s;
+        lo += e + v.y;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) out[i] = acc;
+    if (use_near) {
+        const int q4 = ppad >> 2;
+        const int rb = row_ptr[i];
+        const int total = (row_ptr[i + 1] - rb) * q4;
+        const float4* v4 = reinterpret_cast<const float4*>(vals) + (size_t)rb * q4;
+        const float4* s4 = reinterpret_cast<const float4*>(sig32);
+        float acc = 0.f;
+        for (int e0 = 0; e0 < total; e0 += 128) {
+            float4 v[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * 32 + lane;
+                if (e < total) {
+                    const int b = e / q4;
+                    v[u] = __ldg(v4 + e);
+                    x[u] = __ldg(s4 + (size_t)blk_patch[rb + b] * q4 + (e - b * q4));
+                } else {
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[u] = v[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                acc = fmaf(v[u].x, x[u].x, fmaf(v[u].y, x[u].y, fmaf(v[u].z, x[u].z, fmaf(v[u].w, x[u].w, acc))));
+        }
+        float s, e;
+        two_sum(hi, acc, s, e);
+        hi = s;
+        lo += e;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo += e + l2;
+    }
+    if (lane == 0) out[i] = (double)hi + (double)lo;
 }
 
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
@@ -646,8 +687,8 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
     else
         k_near_apply32<<<blocks, threads, 0, st>>>(N, s->ppad, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK32 : s->cR32, s->sig32,
-                                                   s->partial, nsplit, use_near, out,
-                                                   s->skip_flag);
+                                                   reinterpret_cast<const float2*>(s->partial),
+                                                   nsplit, use_near, out, s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
