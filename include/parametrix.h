@@ -207,7 +207,8 @@ enum {
     PM_PHASE_DIRECT_K = 2,    /* smooth parametrix sum                     */
     PM_PHASE_NEAR = 3,        /* near-field correction + split reduction   */
     PM_PHASE_SOLVE_VEC = 4,   /* GMRES vector kernels                      */
-    PM_PHASE_COUNT = 5
+    PM_PHASE_DIRECT64 = 5,    /* float64 smooth sums (R or K)              */
+    PM_PHASE_COUNT = 6
 };
 pm_status pm_profile_enable(pm_surface* s, int enable);
 pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, int reset);

@@ -33,7 +33,8 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
            "pm_surface_tune"]
-PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC = range(5)
+(PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
+ PM_PHASE_DIRECT64) = range(6)
 
 
 class PmOpts(C.Structure):

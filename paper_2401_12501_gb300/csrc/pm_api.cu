@@ -502,7 +502,8 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
     }
     if (smooth) {
         nsplit = pm_direct_splits(s, prec);
-        PhaseTimer t(s, kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R, st);
+        PhaseTimer t(s, prec == PM_PREC_FP64 ? PM_PHASE_DIRECT64
+                                             : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
         PM_TRY(pm_direct_sum(s, kernel_K, prec, nsplit, st));
     }
     PhaseTimer t(s, PM_PHASE_NEAR, st);

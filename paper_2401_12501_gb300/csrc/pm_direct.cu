@@ -298,7 +298,7 @@ int pm_direct_splits(const pm_surface* s, pm_precision prec) {
     const int per_block = (prec == PM_PREC_FP64) ? kThreads : kThreads * direct_tpt(s);
     const int tblocks = pm_ceil_div(s->N, per_block);
     int bps = s->opts.direct_blocks_per_sm;
-    if (bps < 1 || bps > 16) bps = 8;
+    if (bps < 1 || bps > 16) bps = 12;
     const int want = bps * s->ctx->num_sms;
     int ns = (want + tblocks / 2) / tblocks;            // nearest split count
     ns = std::max(1, std::min(ns, std::min(s->max_split, std::max(1, s->N / 64))));

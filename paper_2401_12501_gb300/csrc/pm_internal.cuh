@@ -122,8 +122,8 @@ struct pm_surface {
     // per-phase timing (events recorded around launches while enabled)
     bool profiling = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
-    double prof_ms[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
-    int prof_n[PM_PHASE_COUNT] = {0, 0, 0, 0, 0};
+    double prof_ms[PM_PHASE_COUNT] = {};
+    int prof_n[PM_PHASE_COUNT] = {};
 
     // solve workspace (pm_solve.cu) and the device flag that lets the apply
     // kernels of a finished Krylov cycle return at once
