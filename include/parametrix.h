@@ -58,7 +58,10 @@ typedef enum {
     PM_PREC_FP64 = 0,     /* float64 smooth sums and float64 near-field values      */
     PM_PREC_FP32 = 1,     /* float32 smooth sums with compensated (TwoSum) tile
                              accumulation, float32 near-field values               */
-    PM_PREC_FP32_TC = 2   /* reserved for the tensor-core FMM far field            */
+    PM_PREC_FP32_TC = 2,  /* reserved for the tensor-core FMM far field            */
+    PM_PREC_FF = 3        /* float-float (FP32-pair, ~48-bit) smooth sums on the FP32
+                             pipe, float64 near-field values: float64-class accuracy
+                             (~1e-13 relative) at a fraction of GB300's float64 cost */
 } pm_precision;
 
 /* Quadrature and solver options (pm_default_opts fills the defaults). */
@@ -78,6 +81,8 @@ typedef struct {
     double inner_tol;       /* pm_solve: relative tolerance of each inner float32 GMRES; 1e-6 */
     double mean_tol;        /* pm_solve: |sum w f| / (sqrt(sum w) ||f||_w) above which f
                                is rejected as not mean zero; 1e-8                       */
+    int residual_prec;      /* pm_solve: precision of true residuals and of u = K~ sigma
+                               (PM_PREC_FF or PM_PREC_FP64); default PM_PREC_FF         */
     int direct_tpt;         /* float32 smooth sums: targets per thread (1, 2 or 4); 0 = auto */
     int direct_blocks_per_sm; /* float32 smooth sums: source splits chosen so the grid holds
                                about this many blocks per SM (1..16); 0 = auto          */
@@ -181,10 +186,10 @@ typedef struct {
 
 /*
  * Solve div_G(a grad_G u) = f for the mean-zero u (Thm. LBsolvable, Thm. second_kind):
- * (I + R~ + 1 w^T) sigma = f by float64 GMRES with float32 (prec = PM_PREC_FP32) or
- * float64 (PM_PREC_FP64) operator applies, iterative refinement on float64 true
- * residuals until ||f - A sigma||/||f|| <= tol, then u = K~ sigma (float64) minus
- * its weighted mean.
+ * (I + R~ + 1 w^T) sigma = f by GMRES with a float64 Krylov basis and operator
+ * applies in `prec` (PM_PREC_FP32, PM_PREC_FF or PM_PREC_FP64), iterative
+ * refinement on true residuals in opts.residual_prec until ||f - A sigma||/||f||
+ * <= tol, then u = K~ sigma (in opts.residual_prec) minus its weighted mean.
  *   f, u       [nrhs*N]  (host, or device with PM_SOLVE_DEVICE_PTRS)
  *   sigma_out  [nrhs*N] or NULL
  *   info       [nrhs] or NULL
@@ -212,6 +217,13 @@ enum {
 };
 pm_status pm_profile_enable(pm_surface* s, int enable);
 pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, int reset);
+
+/*
+ * Diagnostic: the library's float-float natural logarithm (Tang's table
+ * method) of x = xh + xl for n host values, written to out (host, float64).
+ */
+pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int n,
+                            double* out);
 
 const char* pm_status_str(pm_status st);
 const char* pm_last_error(void);

@@ -13,11 +13,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PM_PART_NEAR_K, PM_PART_NEAR_R, PM_PART_SMOOTH_K,  # noqa: F401
-                   PM_PART_SMOOTH_R, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
+                   PM_PART_SMOOTH_R, PM_PREC_FF, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
                    PM_SOLVE_DEVICE_PTRS, PM_SOLVE_PROJECT_RHS, PmError, PmSolveInfo,
                    check, default_opts, ptr)
 
-PRECISIONS = {"fp64": PM_PREC_FP64, "fp32": PM_PREC_FP32, "fp32_tc": PM_PREC_FP32_TC}
+PRECISIONS = {"fp64": PM_PREC_FP64, "fp32": PM_PREC_FP32, "fp32_tc": PM_PREC_FP32_TC,
+              "ff": PM_PREC_FF}
 
 
 def _f64(a, n):
@@ -82,6 +83,15 @@ class Surface:
             self.close()
         except Exception:
             pass
+
+    def selftest_fflog(self, xh, xl):
+        """The library's float-float logarithm of xh + xl (float32 arrays)."""
+        xh = np.ascontiguousarray(xh, dtype=np.float32)
+        xl = np.ascontiguousarray(xl, dtype=np.float32)
+        out = np.empty(xh.size)
+        check(_lib.lib().pm_selftest_fflog(self.handle, ptr(xh), ptr(xl), xh.size, ptr(out)),
+              "pm_selftest_fflog")
+        return out
 
     def tune(self, direct_tpt=0, direct_blocks_per_sm=0):
         check(_lib.lib().pm_surface_tune(self.handle, int(direct_tpt), int(direct_blocks_per_sm)),

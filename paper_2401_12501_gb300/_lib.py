@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libparametrix.so")
 
 PM_OK = 0
-PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC = 0, 1, 2
+PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF = 0, 1, 2, 3
 PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
 PM_SOLVE_PROJECT_RHS = 1
 PM_SOLVE_DEVICE_PTRS = 2
@@ -32,7 +32,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_destroy", "pm_surface_info", "pm_surface_set_coeff", "pm_apply_R",
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
-           "pm_surface_tune"]
+           "pm_surface_tune", "pm_selftest_fflog"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -43,7 +43,8 @@ class PmOpts(C.Structure):
                 ("near_max_depth", C.c_int), ("near_max_leaves", C.c_int),
                 ("gmres_restart", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("mean_tol", C.c_double),
-                ("direct_tpt", C.c_int), ("direct_blocks_per_sm", C.c_int)]
+                ("residual_prec", C.c_int), ("direct_tpt", C.c_int),
+                ("direct_blocks_per_sm", C.c_int)]
 
 
 class PmSolveInfo(C.Structure):
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.argtypes = [P]
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
+    lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.pm_surface_set_coeff.argtypes = [P, P, P]
     for name in ("pm_apply_R", "pm_apply_K"):

@@ -58,6 +58,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->max_refine = 8;
     o->inner_tol = 1e-6;
     o->mean_tol = 1e-8;
+    o->residual_prec = PM_PREC_FF;
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
 }
@@ -261,6 +262,7 @@ static void free_surface(pm_surface* s) {
     pm_dfree(s->a); pm_dfree(s->g); pm_dfree(s->wa); pm_dfree(s->src32); pm_dfree(s->tgt32);
     pm_dfree(s->src64); pm_dfree(s->cR64); pm_dfree(s->cK64); pm_dfree(s->cR32);
     pm_dfree(s->cK32); pm_dfree(s->partial); pm_dfree(s->sig32);
+    pm_dfree(s->src_ff); pm_dfree(s->tgt_ff); pm_dfree(s->log_tab);
     pm_dfree(s->dbuf_in); pm_dfree(s->dbuf_out);
     for (auto& ev : s->prof_events) {
         cudaEventDestroy(ev.second.first);
@@ -451,6 +453,7 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
         PM_CUDA_TRY(cudaMemcpy(s->g, gh.data(), 3 * sizeof(double) * N, cudaMemcpyHostToDevice));
     }
     PM_TRY(pm_pack_targets(s, st));
+    PM_TRY(pm_pack_ff(s, st));
     PM_TRY(pm_near_combine_coeff(s, st));
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     s->has_coeff = true;
@@ -498,13 +501,23 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
     int nsplit = 0;
     if (smooth || near) {
         PhaseTimer t(s, PM_PHASE_PREP, st);
-        PM_TRY(pm_prep_sources(s, sigma, prec, st));
+        if (prec == PM_PREC_FF) {
+            PM_TRY(pm_prep_ff(s, sigma, st));
+        } else {
+            PM_TRY(pm_prep_sources(s, sigma, prec, st));
+        }
     }
     if (smooth) {
-        nsplit = pm_direct_splits(s, prec);
-        PhaseTimer t(s, prec == PM_PREC_FP64 ? PM_PHASE_DIRECT64
-                                             : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
-        PM_TRY(pm_direct_sum(s, kernel_K, prec, nsplit, st));
+        PhaseTimer t(s, prec == PM_PREC_FP64 || prec == PM_PREC_FF
+                            ? PM_PHASE_DIRECT64
+                            : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
+        if (prec == PM_PREC_FF) {
+            nsplit = pm_ff_splits(s);
+            PM_TRY(pm_direct_ff(s, kernel_K, nsplit, st));
+        } else {
+            nsplit = pm_direct_splits(s, prec);
+            PM_TRY(pm_direct_sum(s, kernel_K, prec, nsplit, st));
+        }
     }
     PhaseTimer t(s, PM_PHASE_NEAR, st);
     return pm_near_apply(s, kernel_K, sigma, out, near, nsplit, prec, st);
@@ -517,7 +530,7 @@ static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
         pm_set_error("apply: NULL argument or nrhs < 1");
         return PM_ERR_INVALID_ARG;
     }
-    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32) {
+    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF) {
         pm_set_error("apply: precision %d is not available for this operator", (int)prec);
         return PM_ERR_INVALID_ARG;
     }
@@ -623,7 +636,7 @@ extern "C" pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrh
         pm_set_error("pm_solve: NULL argument, nrhs < 1, tol <= 0 or maxit < 1");
         return PM_ERR_INVALID_ARG;
     }
-    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32) {
+    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF) {
         pm_set_error("pm_solve: precision %d is not available", (int)prec);
         return PM_ERR_INVALID_ARG;
     }

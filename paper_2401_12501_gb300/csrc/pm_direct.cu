@@ -29,9 +29,7 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kTPT = 2;                 // targets per thread
-constexpr int kTile = 256;              // sources per shared-memory tile
-constexpr int kTargetsPerBlock = kThreads * kTPT;
+constexpr int kTile = 256;              // sources per compensation tile
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;

@@ -114,6 +114,9 @@ struct pm_surface {
     float4* src32 = nullptr;      // [Npad] (x, y, z, s)
     float4* tgt32 = nullptr;      // [3*N] (x,y,z,0), (sqrt(a/pi) n, 0), (m, 0)
     pm_d4* src64 = nullptr;     // [Npad] (x, y, z, s)
+    float4* src_ff = nullptr;     // [2N] float-float sources
+    float4* tgt_ff = nullptr;     // [6N] float-float targets
+    float4* log_tab = nullptr;    // [128] table of the float-float logarithm
     double* cR64 = nullptr;       // [nblk*pp]
     double* cK64 = nullptr;       // [nblk*pp]
     float* cR32 = nullptr;        // [nblk*ppad]
@@ -161,6 +164,13 @@ pm_status pm_prep_sources(pm_surface* s, const double* sigma, pm_precision prec,
 pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nsplit,
                         cudaStream_t st);
 pm_status pm_pack_targets(pm_surface* s, cudaStream_t st);
+
+// float-float sums (pm_ffsum.cu)
+pm_status pm_ff_setup(pm_surface* s);
+pm_status pm_pack_ff(pm_surface* s, cudaStream_t st);
+pm_status pm_prep_ff(pm_surface* s, const double* sigma, cudaStream_t st);
+int pm_ff_splits(const pm_surface* s);
+pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st);
 
 // solve (pm_solve.cu)
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,

@@ -577,14 +577,22 @@ k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
                                const int* __restrict__ blk_patch, const double* __restrict__ vals,
                                const double* __restrict__ sigma, const double* __restrict__ partial,
-                               int nsplit, int use_near, double* __restrict__ out,
+                               int nsplit, int partial_ff, int use_near, double* __restrict__ out,
                                const int* __restrict__ skip) {
     if (skip && *skip) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
     const int i = warp;
-    double acc = (lane < nsplit) ? partial[(size_t)lane * N + i] : 0.0;
+    double acc = 0.0;
+    if (lane < nsplit) {
+        if (partial_ff) {
+            const float2 v = reinterpret_cast<const float2*>(partial)[(size_t)lane * N + i];
+            acc = (double)v.x + (double)v.y;
+        } else {
+            acc = partial[(size_t)lane * N + i];
+        }
+    }
     if (use_near) {
         for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
             const double* v = vals + (size_t)b * pp;
@@ -679,10 +687,11 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
     const int N = s->N;
     const int threads = 256;
     const int blocks = pm_ceil_div((long long)N * 32, threads);
-    if (prec == PM_PREC_FP64)
+    if (prec == PM_PREC_FP64 || prec == PM_PREC_FF)
         k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK64 : s->cR64, sigma,
-                                                   s->partial, nsplit, use_near, out,
+                                                   s->partial, nsplit, prec == PM_PREC_FF ? 1 : 0,
+                                                   use_near, out,
                                                    s->skip_flag);
     else
         k_near_apply32<<<blocks, threads, 0, st>>>(N, s->ppad, s->row_ptr, s->blk_patch,

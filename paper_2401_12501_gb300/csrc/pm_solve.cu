@@ -108,15 +108,6 @@ __global__ void k_add_cols(double* __restrict__ h, const double* __restrict__ h2
     if (j < n) h[j] += h2[j];
 }
 
-// out = b - (v + y + wdot)  (residual)
-__global__ void k_residual(const double* __restrict__ b, const double* __restrict__ v,
-                           const double* __restrict__ y, const double* __restrict__ wdot,
-                           double* __restrict__ out, int N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    out[i] = b[i] - (v[i] + y[i] + *wdot);
-}
-
 __global__ void k_scale_copy(const double* __restrict__ src, const double* __restrict__ s,
                              int invert, double* __restrict__ dst, int N,
                              const int* __restrict__ done) {
@@ -288,6 +279,10 @@ struct Solver {
     cudaStream_t st;
     int grid_n;
 
+    pm_precision residual_prec() const {
+        return s->opts.residual_prec == PM_PREC_FP64 ? PM_PREC_FP64 : PM_PREC_FF;
+    }
+
     // dst[0..ncols) = columns(A) . b (deterministic two-pass reduction)
     pm_status dots(const double* A, long long lda, int ncols, const double* b, double* dst,
                    const int* done) {
@@ -336,7 +331,21 @@ struct Solver {
             k_scale_copy<<<grid_n, 256, 0, st>>>(W.r, W.scal + 3, 1, W.V, W.N, W.done);
             const int steps = std::min(m, max_iter - total);
             s->skip_flag = W.done;
+            // launch the cycle in chunks; between chunks read the done flag so a
+            // converged cycle stops launching (kernels after convergence no-op)
+            const int chunk = (steps <= 8) ? steps : 4;
             for (int k = 0; k < steps; ++k) {
+                if (k > 0 && k % chunk == 0) {
+                    cudaError_t ce = cudaMemcpyAsync(W.pinned_i + 2, W.done, sizeof(int),
+                                                     cudaMemcpyDeviceToHost, st);
+                    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+                    if (ce != cudaSuccess) {
+                        s->skip_flag = nullptr;
+                        pm_set_error("gmres: %s", cudaGetErrorString(ce));
+                        return PM_ERR_CUDA;
+                    }
+                    if (W.pinned_i[2]) break;
+                }
                 double* vk = W.V + (size_t)k * ldv;
                 double* vk1 = W.V + (size_t)(k + 1) * ldv;
                 double* hk = W.H + (size_t)k * (m + 2);
@@ -374,9 +383,9 @@ struct Solver {
         return PM_OK;
     }
 
-    // res = f - A sigma in float64
+    // res = f - A sigma in the residual precision (float-float or float64)
     pm_status true_residual(const double* f, const double* sig, double* res) {
-        PM_TRY(apply_A(sig, W.w, PM_PREC_FP64, nullptr));
+        PM_TRY(apply_A(sig, W.w, residual_prec(), nullptr));
         k_residual_from<<<grid_n, 256, 0, st>>>(f, W.w, res, W.N);
         PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
@@ -428,20 +437,27 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     double relres = 0.0;
     pm_status result = PM_OK;
     if (fnorm > 0.0) {
-        if (prec == PM_PREC_FP64) {
-            // one float64 GMRES to the target, confirmed by the true residual
-            PM_TRY(S.gmres(W.f, W.sig, PM_PREC_FP64, tol * fnorm, maxit, &iters));
+        if (prec == PM_PREC_FP64 || prec == PM_PREC_FF) {
+            // one GMRES with accurate applies to the target, confirmed by the true residual
+            PM_TRY(S.gmres(W.f, W.sig, prec, tol * fnorm, maxit, &iters));
             PM_TRY(S.true_residual(W.f, W.sig, W.res));
             double rn = 0;
             PM_TRY(S.norm2(W.res, &rn));
             relres = rn / fnorm;
             refinements = 1;
         } else {
-            // iterative refinement: float64 residual, float32-operator GMRES correction
+            // iterative refinement: accurate residual, float32-operator GMRES correction
             for (;;) {
-                PM_TRY(S.true_residual(W.f, W.sig, W.res));
                 double rn = 0;
-                PM_TRY(S.norm2(W.res, &rn));
+                if (refinements == 0) {
+                    // sigma = 0: the residual is f itself
+                    PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * N,
+                                                cudaMemcpyDeviceToDevice, st));
+                    rn = fnorm;
+                } else {
+                    PM_TRY(S.true_residual(W.f, W.sig, W.res));
+                    PM_TRY(S.norm2(W.res, &rn));
+                }
                 relres = rn / fnorm;
                 if (relres <= tol || refinements >= s->opts.max_refine || iters >= maxit) break;
                 int it = 0;
@@ -458,8 +474,8 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
             result = PM_ERR_NOT_CONVERGED;
         }
     }
-    // u = K~ sigma (float64), then subtract its weighted mean (eq. representation)
-    PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig, W.u, PM_PREC_FP64, st));
+    // u = K~ sigma (accurate), then subtract its weighted mean (eq. representation)
+    PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig, W.u, S.residual_prec(), st));
     PM_TRY(S.dots(s->w, 0, 1, W.u, W.scal + 6, nullptr));
     k_add_shift<<<S.grid_n, 256, 0, st>>>(W.u, W.scal + 6, -1.0 / sw, N);
     PM_CUDA_TRY(cudaGetLastError());

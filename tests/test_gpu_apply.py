@@ -175,3 +175,48 @@ def test_spectral_gradient_matches_closed_form(ctx):
     b = s2.apply_R(sigma, "fp64")
     assert rel(a, b) < 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_small", "sphere_384"])
+def test_float_float_apply_parity(ctx, name):
+    """Float-float smooth sums + float64 near field match the float64 oracle like the
+    float64 path does (the remaining difference is the two sides' quadrature rules),
+    and agree with the float64 path itself to 1e-13."""
+    from oracle.operator import apply_K, apply_R
+    wl, d, nf = oracle(name)
+    _, s = gpu_surface(ctx, name)
+    sigma = np.random.default_rng(8).standard_normal(d.N) + 1.0
+    assert rel(s.apply_R(sigma, "ff"), apply_R(d, nf, sigma)) < 1e-11
+    assert rel(s.apply_K(sigma, "ff"), apply_K(d, nf, sigma)) < 1e-11
+    assert rel(s.apply_R(sigma, "ff"), s.apply_R(sigma, "fp64")) < 1e-13
+    assert rel(s.apply_K(sigma, "ff"), s.apply_K(sigma, "fp64")) < 1e-13
+
+
+def test_float_float_full_size_rows(ctx):
+    from oracle.operator import apply_K, apply_R
+    name = "ellipsoid_9600"
+    wl = make_workload(name)
+    rng = np.random.default_rng(9)
+    rows = sorted(set([0, wl.N - 1] + [int(i) for i in rng.integers(0, wl.N, 10)]))
+    _, d, nf = oracle(name, rows)
+    _, s = gpu_surface(ctx, name)
+    sigma = rng.standard_normal(wl.N) + 1.0
+    oR = apply_R(d, nf, sigma, rows)
+    oK = apply_K(d, nf, sigma, rows)
+    assert np.abs(s.apply_R(sigma, "ff")[rows] - oR).max() < 1e-10 * np.abs(oR).max()
+    assert np.abs(s.apply_K(sigma, "ff")[rows] - oK).max() < 1e-10 * np.abs(oK).max()
+
+
+def test_float_float_logarithm(ctx):
+    """Tang's table-driven float-float log against the float64 logarithm."""
+    _, s = gpu_surface(ctx, "sphere_384")
+    rng = np.random.default_rng(10)
+    x = np.concatenate([10.0 ** rng.uniform(-12, 6, 20000), 1.0 + rng.uniform(-1e-3, 1e-3, 2000),
+                        [1.0, 2.0, 0.5, 1.0 + 2.0 ** -23, 1.9999999]])
+    xh = x.astype(np.float32)
+    xl = (x - xh.astype(np.float64)).astype(np.float32)
+    xx = xh.astype(np.float64) + xl.astype(np.float64)
+    got = s.selftest_fflog(xh, xl)
+    ref = np.log(xx)
+    err = np.abs(got - ref) / np.maximum(1.0, np.abs(ref))
+    assert err.max() < 3e-14, err.max()

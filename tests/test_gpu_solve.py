@@ -130,3 +130,19 @@ def test_device_pointers_and_batch(ctx):
     w = wl.surface.weights
     assert rel_l2(u_h[1], -2.0 * u_h[0], w) < 1e-9
     assert len(infos) == 2 and all(i.residual <= 1e-10 for i in infos)
+
+
+def test_float64_residual_option_matches(ctx):
+    """opts.residual_prec = PM_PREC_FP64 gives the same solution as the float-float default."""
+    import paper_2401_12501_gb300 as pm
+    wl = make_workload("ellipsoid_small")
+    o = pm.default_opts()
+    o.residual_prec = pm.PM_PREC_FP64
+    s64 = pm.Surface.from_fixture(ctx, wl.surface, o)
+    s64.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+    _, sff = setup(ctx, "ellipsoid_small")
+    u64, i64 = s64.solve(wl.f, tol=1e-11, prec="fp32")
+    uff, iff = sff.solve(wl.f, tol=1e-11, prec="fp32")
+    w = wl.surface.weights
+    assert rel_l2(u64, uff, w) < 1e-10
+    s64.close()
