@@ -204,7 +204,10 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  * Per-phase kernel timing.  While enabled, the library records a pair of CUDA
  * events on the launching stream around every launch of each phase; reading
  * synchronises on those events and returns the summed milliseconds and the
- * launch count since the last reset (reset = 1 clears them).
+ * launch count since the last reset (reset = 1 clears them).  With
+ * phase = PM_PHASE_COUNT, *ms is 0 and *launches is the number of kernels the
+ * library launched for this surface since the last reset (counted whether or
+ * not timing is enabled).
  */
 enum {
     PM_PHASE_PREP = 0,        /* source strengths s = w sigma / a          */

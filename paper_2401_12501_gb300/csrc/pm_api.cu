@@ -520,6 +520,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
         }
     }
     PhaseTimer t(s, PM_PHASE_NEAR, st);
+    s->launch_total += (smooth || near) + smooth + 1;
     return pm_near_apply(s, kernel_K, sigma, out, near, nsplit, prec, st);
 }
 
@@ -604,9 +605,15 @@ extern "C" pm_status pm_profile_enable(pm_surface* s, int enable) {
 
 extern "C" pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches,
                                      int reset) {
-    if (!s || phase < 0 || phase >= PM_PHASE_COUNT) {
+    if (!s || phase < 0 || phase > PM_PHASE_COUNT) {
         pm_set_error("pm_profile_read: NULL surface or bad phase");
         return PM_ERR_INVALID_ARG;
+    }
+    if (phase == PM_PHASE_COUNT) {
+        if (ms) *ms = 0.0;
+        if (launches) *launches = (int)std::min<long long>(s->launch_total, 2147483647LL);
+        if (reset) s->launch_total = 0;
+        return PM_OK;
     }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     for (auto& ev : s->prof_events) {
@@ -621,11 +628,13 @@ extern "C" pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* 
     s->prof_events.clear();
     if (ms) *ms = s->prof_ms[phase];
     if (launches) *launches = s->prof_n[phase];
-    if (reset)
+    if (reset) {
         for (int k = 0; k < PM_PHASE_COUNT; ++k) {
             s->prof_ms[k] = 0;
             s->prof_n[k] = 0;
         }
+        s->launch_total = 0;
+    }
     return PM_OK;
 }
 

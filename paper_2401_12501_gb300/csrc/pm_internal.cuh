@@ -127,6 +127,7 @@ struct pm_surface {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
     double prof_ms[PM_PHASE_COUNT] = {};
     int prof_n[PM_PHASE_COUNT] = {};
+    long long launch_total = 0;   // kernels launched for this surface since the last reset
 
     // solve workspace (pm_solve.cu) and the device flag that lets the apply
     // kernels of a finished Krylov cycle return at once

@@ -287,7 +287,9 @@ struct Solver {
     pm_status dots(const double* A, long long lda, int ncols, const double* b, double* dst,
                    const int* done) {
         k_multidot<<<W.nred, kRedThreads, 0, st>>>(A, lda, ncols, b, W.N, W.part, done);
+        s->launch_total++;
         k_reduce_cols<<<pm_ceil_div(ncols, 64), 64, 0, st>>>(W.part, W.nred, ncols, dst, done);
+        s->launch_total++;
         PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
     }
@@ -297,6 +299,7 @@ struct Solver {
         PM_TRY(pm_apply_dev(s, 0, 1, 1, v, W.tmp, prec, st));
         PM_TRY(dots(s->w, 0, 1, v, W.scal + 0, done));
         k_apply_A_finish<<<grid_n, 256, 0, st>>>(v, W.tmp, W.scal + 0, out, W.N, done);
+        s->launch_total++;
         PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
     }
@@ -328,7 +331,9 @@ struct Solver {
         while (total < max_iter) {
             PM_TRY(dots(W.r, 0, 1, W.r, W.scal + 1, nullptr));
             k_cycle_start<<<1, 1, 0, st>>>(W.scal + 1, W.g, m, W.scal, tol_abs, W.done, W.iters);
+            s->launch_total++;
             k_scale_copy<<<grid_n, 256, 0, st>>>(W.r, W.scal + 3, 1, W.V, W.N, W.done);
+            s->launch_total++;
             const int steps = std::min(m, max_iter - total);
             s->skip_flag = W.done;
             // launch the cycle in chunks; between chunks read the done flag so a
@@ -354,18 +359,25 @@ struct Solver {
                 // classical Gram-Schmidt, applied twice
                 dots(W.V, ldv, k + 1, W.w, hk, W.done);
                 k_sub_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, k + 1, hk, W.w, W.N, W.done);
+                s->launch_total++;
                 dots(W.V, ldv, k + 1, W.w, W.hcol, W.done);
                 k_sub_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, k + 1, W.hcol, W.w, W.N, W.done);
+                s->launch_total++;
                 k_add_cols<<<pm_ceil_div(k + 1, 64), 64, 0, st>>>(hk, W.hcol, k + 1, W.done);
+                s->launch_total++;
                 dots(W.w, 0, 1, W.w, W.scal + 1, W.done);
                 k_arnoldi_rotate<<<1, 1, 0, st>>>(W.H, m + 2, k, W.cs, W.sn, W.g, W.scal + 1,
                                                   W.scal, tol_abs, W.done, W.iters);
+                s->launch_total++;
                 k_scale_copy<<<grid_n, 256, 0, st>>>(W.w, W.scal + 2, 0, vk1, W.N, W.done);
+                s->launch_total++;
             }
             s->skip_flag = nullptr;
             PM_CUDA_TRY(cudaGetLastError());
             k_backsolve<<<1, 1, 0, st>>>(W.H, m + 2, W.g, W.iters, W.y);
+            s->launch_total++;
             k_add_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, W.iters, W.y, W.delta, W.N);
+            s->launch_total++;
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + 1, W.done, sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -376,8 +388,10 @@ struct Solver {
             // cycle exhausted: restart from the residual of the operator in use
             PM_TRY(apply_A(W.delta, W.w, prec, nullptr));
             k_residual_from<<<grid_n, 256, 0, st>>>(b, W.w, W.r, W.N);
+            s->launch_total++;
         }
         k_axpy<<<grid_n, 256, 0, st>>>(x, W.delta, 1.0, W.N);
+        s->launch_total++;
         PM_CUDA_TRY(cudaGetLastError());
         *iters_used = total;
         return PM_OK;
@@ -387,6 +401,7 @@ struct Solver {
     pm_status true_residual(const double* f, const double* sig, double* res) {
         PM_TRY(apply_A(sig, W.w, residual_prec(), nullptr));
         k_residual_from<<<grid_n, 256, 0, st>>>(f, W.w, res, W.N);
+        s->launch_total++;
         PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
     }
@@ -412,6 +427,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     double sw = 0.0;
     for (double v : s->h_w) sw += v;
     k_mul<<<S.grid_n, 256, 0, st>>>(s->w, W.f, W.tmp, N);
+    s->launch_total++;
     PM_TRY(S.dots(W.tmp, 0, 1, W.f, W.scal + 5, nullptr));      // sum w f^2
     PM_TRY(S.dots(s->w, 0, 1, W.f, W.scal + 4, nullptr));       // sum w f
     PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -429,6 +445,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     if (flags & PM_SOLVE_PROJECT_RHS) {
         removed = wf / sw;
         k_add_shift<<<S.grid_n, 256, 0, st>>>(W.f, W.scal + 4, -1.0 / sw, N);
+        s->launch_total++;
     }
     double fnorm = 0.0;
     PM_TRY(S.norm2(W.f, &fnorm));
@@ -478,6 +495,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig, W.u, S.residual_prec(), st));
     PM_TRY(S.dots(s->w, 0, 1, W.u, W.scal + 6, nullptr));
     k_add_shift<<<S.grid_n, 256, 0, st>>>(W.u, W.scal + 6, -1.0 / sw, N);
+    s->launch_total++;
     PM_CUDA_TRY(cudaGetLastError());
     PM_CUDA_TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * N, d2h, st));
     if (sigma_out)
