@@ -31,6 +31,11 @@ if ROOT not in sys.path:
 METRIC = "R-apply Gpairs/s; solves/s at 1e-8 rel err vs plain GPU solve; p50/p99 latency"
 UNIT = "Gpairs/s"
 FLOPS_PER_PAIR_R = 26      # variable-a remainder pair (algorithmic count)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# of the current kernel versions on this workload (profiles/k_direct_*_ellipsoid_9600.md);
+# set to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
+                 ("k_direct_ff_R", "ellipsoid_9600"): 1236992}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -259,7 +264,8 @@ def run_gpu(args, rank, world, local_rank):
            "achieved": round(FLOPS_PER_PAIR_R * pairs / (fp32_k * 1e-3) / 1e12, 3),
            "peak": round(peak, 2), "unit": "TFLOP/s",
            "frac": round(FLOPS_PER_PAIR_R * pairs / (fp32_k * 1e-3) / 1e12 / peak, 4),
-           "traffic": None, "kernel_ms": round(fp32_k, 5),
+           "traffic": TRAFFIC_BYTES.get(("k_direct_R32", args.workload)),
+           "kernel_ms": round(fp32_k, 5),
            "flops_per_pair": FLOPS_PER_PAIR_R,
            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts)",
            "step_time_share": round(fp32_ms / (total_ms / 1.0), 4)}
@@ -268,7 +274,8 @@ def run_gpu(args, rank, world, local_rank):
            "achieved": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12, 3) if ff_k else None,
            "peak": round(peak, 2), "unit": "TFLOP/s",
            "frac": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12 / peak, 4) if ff_k else None,
-           "traffic": None, "kernel_ms_per_apply": round(ff_k, 5),
+           "traffic": TRAFFIC_BYTES.get(("k_direct_ff_R", args.workload)),
+           "kernel_ms_per_apply": round(ff_k, 5),
            "note": "algorithmic flops of the float64-class sum; each flop costs ~8 float32 "
                    "instructions in float-float arithmetic",
            "step_time_share": round(ff_ms / total_ms, 4)}
