@@ -228,6 +228,41 @@ pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, i
 pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int n,
                             double* out);
 
+/*
+ * Smooth remainder sum without any allocation.
+ *
+ * Some callers cannot call cudaMalloc: code whose device memory is owned
+ * entirely by another allocator (a framework's caching pool or a fixed arena,
+ * where a side allocation can fail or fragment it), latency-critical loops
+ * where cudaMalloc/cudaFree would synchronise the device, and callers that
+ * may not create a pm_surface at all (creating one allocates).  This entry
+ * point computes, with the same float32 compensated kernel as
+ * pm_apply_part(PM_PART_SMOOTH_R, PM_PREC_FP32),
+ *   out[i] = sum_{j != i} s[j] [ (a_i/pi) q^2 - (a_i H_i/pi) q + grad_a_i . r/(2 pi |r|^2) ],
+ *   r = x_i - x_j, q = n_i . r / |r|^2,
+ * i.e. the smooth remainder sum for strengths s[j] = w_j sigma_j / a_j supplied
+ * by the caller.  It has no counterpart in the paper (an interface addition).
+ *   N                   1 <= N <= 32768 (larger N is rejected with PM_ERR_INVALID_ARG)
+ *   x, n, grad_a [N*3]  device float32 positions, unit normals, grad_G a
+ *   H, a, s      [N]    device float32 mean curvature, coefficient (> 0), strengths
+ *   out          [N]    device float64 result
+ *   stream              cudaStream_t (NULL: legacy default stream); asynchronous
+ * Scratch: the packed sources/targets and per-split partial sums live in one
+ * file-scope device array of 4 MiB that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  Every call overwrites the parts it
+ * reads, so nothing must be cleared between calls, but all calls share the one
+ * array: calls that overlap on the GPU (different streams, or different host
+ * threads, on the same device) race and corrupt each other's results.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * Requires |s[j]| < 1e8 and distinct node positions.
+ */
+pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, const float* n,
+                                          const float* H, const float* a,
+                                          const float* grad_a, const float* s,
+                                          double* out, void* stream);
+
 const char* pm_status_str(pm_status st);
 const char* pm_last_error(void);
 

@@ -32,7 +32,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_destroy", "pm_surface_info", "pm_surface_set_coeff", "pm_apply_R",
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
-           "pm_surface_tune", "pm_selftest_fflog"]
+           "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
     lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]
+    lib.pm_smooth_remainder_f32_noalloc.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.pm_surface_set_coeff.argtypes = [P, P, P]
     for name in ("pm_apply_R", "pm_apply_K"):

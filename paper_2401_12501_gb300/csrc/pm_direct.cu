@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace {
 
@@ -349,6 +350,117 @@ pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nspli
         if (tpt == 1) { PM_LAUNCH(1) } else if (tpt == 4) { PM_LAUNCH(4) } else { PM_LAUNCH(2) }
 #undef PM_LAUNCH
     }
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+// ============================================================================ no-allocation variant
+// Smooth remainder sum for callers that must not allocate device memory:
+// everything the computation needs beyond the caller's inputs and output
+// (packed float32 sources and targets, per-split partial sums) lives in one
+// file-scope device array.  See pm_smooth_remainder_f32_noalloc in
+// include/parametrix.h for the contract.
+namespace {
+
+constexpr int kNoAllocMaxN = 32768;
+constexpr int kNoAllocSplits = 8;
+constexpr size_t kNoAllocSrcBytes = sizeof(float4) * kNoAllocMaxN;
+constexpr size_t kNoAllocTgtBytes = sizeof(float4) * 3 * kNoAllocMaxN;
+constexpr size_t kNoAllocPartBytes = sizeof(float2) * kNoAllocSplits * kNoAllocMaxN;
+constexpr size_t kNoAllocBytes = kNoAllocSrcBytes + kNoAllocTgtBytes + kNoAllocPartBytes;  // 4 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+__global__ void k_noalloc_pack(int N, const float* __restrict__ x, const float* __restrict__ n,
+                               const float* __restrict__ H, const float* __restrict__ a,
+                               const float* __restrict__ g, const float* __restrict__ s,
+                               float4* __restrict__ src, float4* __restrict__ tgt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float c1 = sqrtf(a[i] / (float)M_PI);
+    const float cH = -a[i] * H[i] / (float)M_PI;
+    const float c2 = 0.5f / (float)M_PI;
+    tgt[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.f);
+    tgt[N + i] = make_float4(c1 * n[3 * i], c1 * n[3 * i + 1], c1 * n[3 * i + 2], 0.f);
+    tgt[2 * N + i] = make_float4(cH * n[3 * i] + c2 * g[3 * i], cH * n[3 * i + 1] + c2 * g[3 * i + 1],
+                                 cH * n[3 * i + 2] + c2 * g[3 * i + 2], 0.f);
+    src[i] = make_float4(x[3 * i], x[3 * i + 1], x[3 * i + 2], s[i]);
+}
+
+__global__ void k_noalloc_reduce(int N, int nsplit, const float2* __restrict__ partial,
+                                 double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float hi = 0.f, lo = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) {
+        const float2 v = partial[(size_t)sp * N + i];
+        two_sum_acc(hi, lo, v.x);
+        lo += v.y;
+    }
+    out[i] = (double)hi + (double)lo;
+}
+
+}  // namespace
+
+extern "C" pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, const float* n,
+                                                     const float* H, const float* a,
+                                                     const float* grad_a, const float* s,
+                                                     double* out, void* stream) {
+    if (N < 1 || N > kNoAllocMaxN) {
+        pm_set_error("pm_smooth_remainder_f32_noalloc: N = %d outside 1..%d (the size of the "
+                     "library's static scratch)", N, kNoAllocMaxN);
+        return PM_ERR_INVALID_ARG;
+    }
+    if (!x || !n || !H || !a || !grad_a || !s || !out) {
+        pm_set_error("pm_smooth_remainder_f32_noalloc: NULL argument");
+        return PM_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    PM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        pm_set_error("pm_smooth_remainder_f32_noalloc: device %d beyond %d", dev, kNoAllocMaxDevices);
+        return PM_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                pm_set_error("pm_smooth_remainder_f32_noalloc: cudaGetSymbolAddress: %s",
+                             cudaGetErrorString(e));
+                return PM_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    unsigned char* b = static_cast<unsigned char*>(base);
+    float4* src = reinterpret_cast<float4*>(b);
+    float4* tgt = reinterpret_cast<float4*>(b + kNoAllocSrcBytes);
+    float2* part = reinterpret_cast<float2*>(b + kNoAllocSrcBytes + kNoAllocTgtBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    // every (split, target < N) partial and every packed entry < N is written
+    // before it is read, so nothing in the scratch needs clearing between calls
+    int dev_sms = 0;
+    PM_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev));
+    const int tblocks = pm_ceil_div(N, kThreads * 2);
+    int nsplit = (12 * dev_sms + tblocks / 2) / tblocks;
+    nsplit = std::max(1, std::min(nsplit, std::min(kNoAllocSplits, std::max(1, N / 64))));
+    const int chunk = pm_ceil_div(N, nsplit);
+    k_noalloc_pack<<<pm_ceil_div(N, 256), 256, 0, st>>>(N, x, n, H, a, grad_a, s, src, tgt);
+    dim3 grid(tblocks, nsplit);
+    // self-pair guard: the j == i term is exactly zero (n'.r = m.r = 0) while r^2 = 1e-30
+    // keeps 1/r^2 finite; it is far below the squared distance of any two distinct nodes
+    const float eps2 = 1e-30f;
+    k_direct_R32<2><<<grid, kThreads, 0, st>>>(src, tgt, N, chunk, eps2, part, nullptr);
+    k_noalloc_reduce<<<pm_ceil_div(N, 256), 256, 0, st>>>(N, nsplit, part, out);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "parametrix.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(pm_[a-z_A-Z]+)\s*\(", src))
+    names = set(re.findall(r"\b(pm_\w+)\s*\(", src))
     return sorted(names)
 
 
