@@ -59,9 +59,12 @@ typedef enum {
     PM_PREC_FP32 = 1,     /* float32 smooth sums with compensated (TwoSum) tile
                              accumulation, float32 near-field values               */
     PM_PREC_FP32_TC = 2,  /* reserved for the tensor-core FMM far field            */
-    PM_PREC_FF = 3        /* float-float (FP32-pair, ~48-bit) smooth sums on the FP32
+    PM_PREC_FF = 3,       /* float-float (FP32-pair, ~48-bit) smooth sums on the FP32
                              pipe, float64 near-field values: float64-class accuracy
                              (~1e-13 relative) at a fraction of GB300's float64 cost */
+    PM_PREC_FMM = 4       /* float32 Chebyshev kernel-interpolation FMM for the smooth
+                             sums (far field by 6x6x6-point box expansions, adjacent
+                             leaves exact), float32 near-field values; large surfaces */
 } pm_precision;
 
 /* Quadrature and solver options (pm_default_opts fills the defaults). */
@@ -83,6 +86,7 @@ typedef struct {
                                is rejected as not mean zero; 1e-8                       */
     int residual_prec;      /* pm_solve: precision of true residuals and of u = K~ sigma
                                (PM_PREC_FF or PM_PREC_FP64); default PM_PREC_FF         */
+    int fmm_depth;          /* PM_PREC_FMM: octree depth (2..8); 0 = chosen by a cost model */
     int direct_tpt;         /* float32 smooth sums: targets per thread (1, 2 or 4); 0 = auto */
     int direct_blocks_per_sm; /* float32 smooth sums: source splits chosen so the grid holds
                                about this many blocks per SM (1..16); 0 = auto          */
@@ -121,6 +125,13 @@ void pm_surface_destroy(pm_surface* s);
  * direct_blocks_per_sm in 0..16 (0 = automatic choice).
  */
 pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_blocks_per_sm);
+
+/*
+ * FMM tree statistics (builds the tree on first use): stats[0] = adjacent-leaf
+ * source/target pairs evaluated exactly, stats[1] = far-field box pairs
+ * (V lists), stats[2] = depth, stats[3] = number of boxes.
+ */
+pm_status pm_surface_fmm_stats(pm_surface* s, double stats[4]);
 
 /* Number of nodes N and near-field blocks (target, near patch) of a surface. */
 pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);

@@ -13,12 +13,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PM_PART_NEAR_K, PM_PART_NEAR_R, PM_PART_SMOOTH_K,  # noqa: F401
-                   PM_PART_SMOOTH_R, PM_PREC_FF, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
+                   PM_PART_SMOOTH_R, PM_PREC_FF, PM_PREC_FMM, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
                    PM_SOLVE_DEVICE_PTRS, PM_SOLVE_PROJECT_RHS, PmError, PmSolveInfo,
                    check, default_opts, ptr)
 
 PRECISIONS = {"fp64": PM_PREC_FP64, "fp32": PM_PREC_FP32, "fp32_tc": PM_PREC_FP32_TC,
-              "ff": PM_PREC_FF}
+              "ff": PM_PREC_FF, "fmm": PM_PREC_FMM}
 
 
 def _f64(a, n):
@@ -92,6 +92,12 @@ class Surface:
         check(_lib.lib().pm_selftest_fflog(self.handle, ptr(xh), ptr(xl), xh.size, ptr(out)),
               "pm_selftest_fflog")
         return out
+
+    def fmm_stats(self):
+        """(near pairs, far box pairs, depth, boxes) of the FMM tree (built on first use)."""
+        st = np.zeros(4)
+        check(_lib.lib().pm_surface_fmm_stats(self.handle, ptr(st)), "pm_surface_fmm_stats")
+        return {"p2p_pairs": st[0], "m2l_box_pairs": st[1], "depth": int(st[2]), "boxes": int(st[3])}
 
     def tune(self, direct_tpt=0, direct_blocks_per_sm=0):
         check(_lib.lib().pm_surface_tune(self.handle, int(direct_tpt), int(direct_blocks_per_sm)),

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libparametrix.so")
 
 PM_OK = 0
-PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF = 0, 1, 2, 3
+PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF, PM_PREC_FMM = 0, 1, 2, 3, 4
 PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
 PM_SOLVE_PROJECT_RHS = 1
 PM_SOLVE_DEVICE_PTRS = 2
@@ -32,7 +32,8 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_destroy", "pm_surface_info", "pm_surface_set_coeff", "pm_apply_R",
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
-           "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc"]
+           "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
+           "pm_surface_fmm_stats"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -43,7 +44,7 @@ class PmOpts(C.Structure):
                 ("near_max_depth", C.c_int), ("near_max_leaves", C.c_int),
                 ("gmres_restart", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("mean_tol", C.c_double),
-                ("residual_prec", C.c_int), ("direct_tpt", C.c_int),
+                ("residual_prec", C.c_int), ("fmm_depth", C.c_int), ("direct_tpt", C.c_int),
                 ("direct_blocks_per_sm", C.c_int)]
 
 
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.argtypes = [P]
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
+    lib.pm_surface_fmm_stats.argtypes = [P, P]
     lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]
     lib.pm_smooth_remainder_f32_noalloc.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]

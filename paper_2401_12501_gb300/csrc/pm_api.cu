@@ -59,6 +59,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->inner_tol = 1e-6;
     o->mean_tol = 1e-8;
     o->residual_prec = PM_PREC_FF;
+    o->fmm_depth = 0;
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
 }
@@ -254,6 +255,7 @@ static void free_surface(pm_surface* s) {
     if (!s) return;
     if (s->ctx) cudaSetDevice(s->ctx->device);
     pm_solve_free(s);
+    pm_fmm_free(s);
     pm_dfree(s->x); pm_dfree(s->n); pm_dfree(s->H); pm_dfree(s->w); pm_dfree(s->J);
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);
@@ -412,6 +414,14 @@ extern "C" pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_b
     return PM_OK;
 }
 
+extern "C" pm_status pm_surface_fmm_stats(pm_surface* s, double stats[4]) {
+    if (!s || !stats) { pm_set_error("pm_surface_fmm_stats: NULL argument"); return PM_ERR_INVALID_ARG; }
+    PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    PM_TRY(pm_fmm_build(s));
+    for (int k = 0; k < 4; ++k) stats[k] = s->fmm_stats[k];
+    return PM_OK;
+}
+
 extern "C" pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks) {
     if (!s) { pm_set_error("pm_surface_info: NULL surface"); return PM_ERR_INVALID_ARG; }
     if (N) *N = s->N;
@@ -504,7 +514,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
         if (prec == PM_PREC_FF) {
             PM_TRY(pm_prep_ff(s, sigma, st));
         } else {
-            PM_TRY(pm_prep_sources(s, sigma, prec, st));
+            PM_TRY(pm_prep_sources(s, sigma, prec == PM_PREC_FMM ? PM_PREC_FP32 : prec, st));
         }
     }
     if (smooth) {
@@ -514,14 +524,18 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
         if (prec == PM_PREC_FF) {
             nsplit = pm_ff_splits(s);
             PM_TRY(pm_direct_ff(s, kernel_K, nsplit, st));
+        } else if (prec == PM_PREC_FMM) {
+            nsplit = 1;
+            PM_TRY(pm_fmm_apply(s, kernel_K, st));
         } else {
             nsplit = pm_direct_splits(s, prec);
             PM_TRY(pm_direct_sum(s, kernel_K, prec, nsplit, st));
         }
     }
     PhaseTimer t(s, PM_PHASE_NEAR, st);
-    s->launch_total += (smooth || near) + smooth + 1;
-    return pm_near_apply(s, kernel_K, sigma, out, near, nsplit, prec, st);
+    s->launch_total += (smooth || near) + (smooth && prec != PM_PREC_FMM) + 1;
+    return pm_near_apply(s, kernel_K, sigma, out, near, nsplit,
+                         prec == PM_PREC_FMM ? PM_PREC_FP32 : prec, st);
 }
 
 static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
@@ -531,7 +545,8 @@ static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
         pm_set_error("apply: NULL argument or nrhs < 1");
         return PM_ERR_INVALID_ARG;
     }
-    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF) {
+    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF &&
+        prec != PM_PREC_FMM) {
         pm_set_error("apply: precision %d is not available for this operator", (int)prec);
         return PM_ERR_INVALID_ARG;
     }
@@ -645,7 +660,8 @@ extern "C" pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrh
         pm_set_error("pm_solve: NULL argument, nrhs < 1, tol <= 0 or maxit < 1");
         return PM_ERR_INVALID_ARG;
     }
-    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF) {
+    if (prec != PM_PREC_FP64 && prec != PM_PREC_FP32 && prec != PM_PREC_FF &&
+        prec != PM_PREC_FMM) {
         pm_set_error("pm_solve: precision %d is not available", (int)prec);
         return PM_ERR_INVALID_ARG;
     }

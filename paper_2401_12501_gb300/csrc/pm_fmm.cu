@@ -1,0 +1,720 @@
+// Chebyshev kernel-interpolation FMM for the smooth remainder and parametrix
+// sums on large surfaces (the fast far-field apply of Sec. 6.2, in the
+// interpolation form rather than the paper's IFMM).
+//
+// The smooth remainder sum factors into nine translation-invariant kernels of
+// r = x - y with target-only coefficients:
+//   y_i = sum_{a,b} n'_a n'_b phi_ab(x_i) + sum_a m_a psi_a(x_i),
+//   phi_ab(x) = sum_j s_j r_a r_b / |r|^4,   psi_a(x) = sum_j s_j r_a / |r|^2,
+// with n' = sqrt(a_i/pi) n_i and m = -(a_i H_i/pi) n_i + grad a_i /(2 pi)
+// (eq. explicit_remainder, c = 0); the parametrix sum is the single kernel
+// log|r| / (2 pi) (eq. diff_param).
+//
+// Tree: a uniform-depth octree over the occupied boxes (all leaves on one
+// level, so only U lists at the leaves and V lists per level are needed); the
+// depth is chosen on the host by a cost model (pair counts of the direct near
+// field against node-pair counts of the far field).  Each box carries an
+// n x n x n tensor grid of Chebyshev points (first kind); expansions are the
+// values at those points:
+//   P2M  M_B[m] = sum_{j in B} s_j S_m(y_j)             (S_m: tensor Lagrange basis)
+//   M2M  M_P[m] = sum_children sum_k S^P_m(y^C_k) M_C[k]
+//   M2L  L_T[c][l] += sum_{S in V(T)} sum_m kernel_c(x^T_l - y^S_m) M_S[m]
+//        (evaluated directly between the two boxes' Chebyshev points)
+//   L2L  L_C[c][k] += sum_l S^P_l(x^C_k) L_P[c][l]
+//   L2P  phi_c(x_i) = sum_l S_l(x_i) L_B[c][l], then the target combination
+//   P2P  leaf targets against the sources of the 27 adjacent leaves, exact kernel.
+// Everything is float32 except the host-side tree; the near-field correction
+// (CSR) is added by the regular correction kernel.
+#include "pm_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <type_traits>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+constexpr int kFmmN = 6;                       // Chebyshev points per dimension
+constexpr int kFmmN3 = kFmmN * kFmmN * kFmmN;  // 216
+constexpr int kThreads = 256;
+constexpr int kMaxLeafPts = 4096;
+
+struct FmmConst {
+    float cheb[kFmmN];          // Chebyshev points of the first kind on [-1, 1]
+    float bary[kFmmN];          // barycentric weights
+    float T[2][kFmmN][kFmmN];   // T[o][m][k] = l_m((t_k + (2o - 1)) / 2): child point k in parent coords
+};
+__constant__ FmmConst cF;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
+// 1-D Lagrange basis at the Chebyshev points (product form, exact at the points)
+__device__ __forceinline__ void cheb_basis(float u, float* out) {
+    float d[kFmmN];
+#pragma unroll
+    for (int b = 0; b < kFmmN; ++b) d[b] = u - cF.cheb[b];
+    float pre = 1.f;
+#pragma unroll
+    for (int a = 0; a < kFmmN; ++a) {
+        out[a] = pre;
+        pre *= d[a];
+    }
+    float suf = 1.f;
+#pragma unroll
+    for (int a = kFmmN - 1; a >= 0; --a) {
+        out[a] *= suf * cF.bary[a];
+        suf *= d[a];
+    }
+}
+
+struct DevTree {
+    int N, nlev, depth, nbox_total;
+    float3 origin;
+    float L0;
+    const int* perm;          // sorted position -> original node
+    const int* lev_off;       // [depth+2] first box index of each level
+    const int3* box_ijk;      // [nbox] integer coordinates at its level
+    const int* box_first;     // [nbox+1 per leaf] point ranges (leaves only; index by leaf id)
+    const int* parent;        // [nbox]
+    const int* child_off;     // [nbox+1] CSR of children
+    const int* child;         // children box ids
+    const int* v_off;         // [nbox+1] CSR of V lists
+    const int* v_list;
+    const int* u_off;         // [nleaf+1] CSR of U lists (leaf ids)
+    const int* u_list;
+};
+
+__device__ __forceinline__ float3 box_center(const DevTree& t, int lev, int3 ijk) {
+    const float h = t.L0 / (float)(1 << lev);
+    return make_float3(t.origin.x + (ijk.x + 0.5f) * h, t.origin.y + (ijk.y + 0.5f) * h,
+                       t.origin.z + (ijk.z + 0.5f) * h);
+}
+
+// gather sorted sources: (x, y, z, s) in leaf order
+__global__ void k_fmm_gather(const float4* __restrict__ src, const int* __restrict__ perm, int N,
+                             float4* __restrict__ sorted, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) sorted[i] = src[perm[i]];
+}
+
+// P2M: one block per leaf, thread per Chebyshev point
+__global__ void __launch_bounds__(kThreads)
+k_fmm_p2m(DevTree t, const float4* __restrict__ pts, float* __restrict__ M,
+          const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int leaf = blockIdx.x;
+    const int box = t.lev_off[t.depth] + leaf;
+    const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
+    const float h = t.L0 / (float)(1 << t.depth);
+    const float3 c = box_center(t, t.depth, t.box_ijk[box]);
+    const float sc = 2.f / h;
+    __shared__ float sL[64][3 * kFmmN];
+    __shared__ float sS[64];
+    const int m = threadIdx.x;
+    const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
+    float acc = 0.f;
+    for (int base = p0; base < p1; base += 64) {
+        const int cnt = min(64, p1 - base);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const float4 q = pts[base + threadIdx.x];
+            float l[kFmmN];
+            cheb_basis((q.x - c.x) * sc, l);
+            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][a] = l[a];
+            cheb_basis((q.y - c.y) * sc, l);
+            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][kFmmN + a] = l[a];
+            cheb_basis((q.z - c.z) * sc, l);
+            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][2 * kFmmN + a] = l[a];
+            sS[threadIdx.x] = q.w;
+        }
+        __syncthreads();
+        if (m < kFmmN3)
+            for (int j = 0; j < cnt; ++j)
+                acc = fmaf(sS[j] * sL[j][m1], sL[j][kFmmN + m2] * sL[j][2 * kFmmN + m3], acc);
+    }
+    if (m < kFmmN3) M[(size_t)box * kFmmN3 + m] = acc;
+}
+
+// M2M for the boxes of one level: M_P = sum_children T(child) M_child
+__global__ void __launch_bounds__(kThreads)
+k_fmm_m2m(DevTree t, int lev, float* __restrict__ M, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int box = t.lev_off[lev] + blockIdx.x;
+    const int m = threadIdx.x;
+    __shared__ float sM[kFmmN3];
+    const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
+    const int3 pijk = t.box_ijk[box];
+    float acc = 0.f;
+    for (int e = t.child_off[box]; e < t.child_off[box + 1]; ++e) {
+        const int ch = t.child[e];
+        const int3 cijk = t.box_ijk[ch];
+        const int ox = cijk.x - 2 * pijk.x, oy = cijk.y - 2 * pijk.y, oz = cijk.z - 2 * pijk.z;
+        __syncthreads();
+        if (m < kFmmN3) sM[m] = M[(size_t)ch * kFmmN3 + m];
+        __syncthreads();
+        if (m < kFmmN3)
+            for (int k = 0; k < kFmmN3; ++k) {
+                const int k1 = k / (kFmmN * kFmmN), k2 = (k / kFmmN) % kFmmN, k3 = k % kFmmN;
+                acc = fmaf(cF.T[ox][m1][k1] * cF.T[oy][m2][k2], cF.T[oz][m3][k3] * sM[k], acc);
+            }
+    }
+    if (m < kFmmN3) M[(size_t)box * kFmmN3 + m] = acc;
+}
+
+// M2L: one block per target box (any level >= 2), thread per target Chebyshev point;
+// direct evaluation between the target box's points and each V-list box's points.
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_fmm_m2l(DevTree t, int box0, const float* __restrict__ M, float* __restrict__ Lc,
+          const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int box = box0 + blockIdx.x;
+    int lev = 0;
+    while (lev + 1 <= t.depth && t.lev_off[lev + 1] <= box) ++lev;
+    const float h = t.L0 / (float)(1 << lev);
+    const float3 c = box_center(t, lev, t.box_ijk[box]);
+    const int l = threadIdx.x;
+    const int l1 = l / (kFmmN * kFmmN), l2 = (l / kFmmN) % kFmmN, l3 = l % kFmmN;
+    const float tx = c.x + 0.5f * h * cF.cheb[l1 % kFmmN];
+    const float ty = c.y + 0.5f * h * cF.cheb[l2 % kFmmN];
+    const float tz = c.z + 0.5f * h * cF.cheb[l3 % kFmmN];
+    __shared__ float4 sP[kFmmN3];
+    constexpr int C = KERNEL_K ? 1 : 9;
+    float acc[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = 0.f;
+    for (int e = t.v_off[box]; e < t.v_off[box + 1]; ++e) {
+        const int sb = t.v_list[e];
+        const float3 sc = box_center(t, lev, t.box_ijk[sb]);
+        __syncthreads();
+        if (l < kFmmN3) {
+            const int k1 = l / (kFmmN * kFmmN), k2 = (l / kFmmN) % kFmmN, k3 = l % kFmmN;
+            sP[l] = make_float4(sc.x + 0.5f * h * cF.cheb[k1], sc.y + 0.5f * h * cF.cheb[k2],
+                                sc.z + 0.5f * h * cF.cheb[k3], M[(size_t)sb * kFmmN3 + l]);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < kFmmN3; ++k) {
+            const float4 s = sP[k];
+            const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (KERNEL_K) {
+                acc[0] = fmaf(s.w, lg2_approx(r2), acc[0]);
+            } else {
+                const float inv = rcp_approx(r2);
+                const float ax = dx * inv, ay = dy * inv, az = dz * inv;
+                const float sx = s.w * ax, sy = s.w * ay, sz = s.w * az;
+                acc[0] = fmaf(sx, dx * inv, acc[0]);   // xx: r_x r_x / r^4
+                acc[1] = fmaf(sx, ay, acc[1]);         // xy
+                acc[2] = fmaf(sx, az, acc[2]);         // xz
+                acc[3] = fmaf(sy, ay, acc[3]);         // yy
+                acc[4] = fmaf(sy, az, acc[4]);         // yz
+                acc[5] = fmaf(sz, az, acc[5]);         // zz
+                acc[6] += sx;                          // x: r_x / r^2
+                acc[7] += sy;
+                acc[8] += sz;
+            }
+        }
+    }
+    if (l < kFmmN3)
+#pragma unroll
+        for (int q = 0; q < C; ++q) Lc[((size_t)box * C + q) * kFmmN3 + l] = acc[q];
+}
+
+// L2L for the boxes of one level (children receive their parent's local expansion)
+template <int C>
+__global__ void __launch_bounds__(kThreads)
+k_fmm_l2l(DevTree t, int lev, float* __restrict__ Lc, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int box = t.lev_off[lev] + blockIdx.x;
+    const int par = t.parent[box];
+    const int k = threadIdx.x;
+    const int3 cijk = t.box_ijk[box], pijk = t.box_ijk[par];
+    const int ox = cijk.x - 2 * pijk.x, oy = cijk.y - 2 * pijk.y, oz = cijk.z - 2 * pijk.z;
+    __shared__ float sL[kFmmN3];
+    const int k1 = k / (kFmmN * kFmmN), k2 = (k / kFmmN) % kFmmN, k3 = k % kFmmN;
+    for (int q = 0; q < C; ++q) {
+        __syncthreads();
+        if (k < kFmmN3) sL[k] = Lc[((size_t)par * C + q) * kFmmN3 + k];
+        __syncthreads();
+        if (k < kFmmN3) {
+            float acc = 0.f;
+            for (int m = 0; m < kFmmN3; ++m) {
+                const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
+                acc = fmaf(cF.T[ox][m1][k1] * cF.T[oy][m2][k2], cF.T[oz][m3][k3] * sL[m], acc);
+            }
+            Lc[((size_t)box * C + q) * kFmmN3 + k] += acc;
+        }
+    }
+}
+
+// L2P + P2P for one leaf: far field from the local expansion, near field by
+// the exact kernel over the U-list leaves; writes (hi, lo) for each target.
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_fmm_leaf(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ tgt,
+           const float* __restrict__ Lc, float eps2, float2* __restrict__ out,
+           const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int leaf = blockIdx.x;
+    const int box = t.lev_off[t.depth] + leaf;
+    const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
+    const float h = t.L0 / (float)(1 << t.depth);
+    const float3 c = box_center(t, t.depth, t.box_ijk[box]);
+    const float sc = 2.f / h;
+    constexpr int C = KERNEL_K ? 1 : 9;
+    __shared__ float sLoc[C * kFmmN3];
+    __shared__ float4 sP[kThreads];
+    for (int e = threadIdx.x; e < C * kFmmN3; e += kThreads)
+        sLoc[e] = Lc[(size_t)box * C * kFmmN3 + e];
+    for (int base = p0; base < p1; base += kThreads) {
+        const int i = base + threadIdx.x;
+        const bool active = i < p1;
+        float4 X = make_float4(0.f, 0.f, 0.f, 0.f), NN = X, MM = X;
+        int orig = 0;
+        if (active) {
+            orig = t.perm[i];
+            X = tgt[orig];
+            NN = tgt[t.N + orig];
+            MM = tgt[2 * t.N + orig];
+        }
+        __syncthreads();
+        // far field: phi_c(x) = sum_l S_l(x) L[c][l]
+        float far = 0.f;
+        if (active) {
+            float bx[kFmmN], by[kFmmN], bz[kFmmN];
+            cheb_basis((X.x - c.x) * sc, bx);
+            cheb_basis((X.y - c.y) * sc, by);
+            cheb_basis((X.z - c.z) * sc, bz);
+            float phi[C];
+#pragma unroll
+            for (int q = 0; q < C; ++q) phi[q] = 0.f;
+            for (int l1 = 0; l1 < kFmmN; ++l1)
+                for (int l2 = 0; l2 < kFmmN; ++l2) {
+                    const float w12 = bx[l1] * by[l2];
+#pragma unroll
+                    for (int l3 = 0; l3 < kFmmN; ++l3) {
+                        const float w = w12 * bz[l3];
+                        const int l = (l1 * kFmmN + l2) * kFmmN + l3;
+#pragma unroll
+                        for (int q = 0; q < C; ++q) phi[q] = fmaf(w, sLoc[q * kFmmN3 + l], phi[q]);
+                    }
+                }
+            if (KERNEL_K) {
+                far = phi[0] * (float)(M_LN2 / (4.0 * M_PI));
+            } else {
+                far = NN.x * NN.x * phi[0] + NN.y * NN.y * phi[3] + NN.z * NN.z * phi[5] +
+                      2.f * (NN.x * NN.y * phi[1] + NN.x * NN.z * phi[2] + NN.y * NN.z * phi[4]) +
+                      MM.x * phi[6] + MM.y * phi[7] + MM.z * phi[8];
+            }
+        }
+        // near field: exact kernel over the U list (the leaf itself included)
+        float hi = 0.f, lo = 0.f;
+        for (int e = t.u_off[leaf]; e < t.u_off[leaf + 1]; ++e) {
+            const int ul = t.u_list[e];
+            const int q0 = t.box_first[ul], q1 = t.box_first[ul + 1];
+            for (int qb = q0; qb < q1; qb += kThreads) {
+                const int cnt = min(kThreads, q1 - qb);
+                __syncthreads();
+                if (threadIdx.x < cnt) sP[threadIdx.x] = pts[qb + threadIdx.x];
+                __syncthreads();
+                float part = 0.f;
+                if (active) {
+                    for (int j = 0; j < cnt; ++j) {
+                        const float4 s = sP[j];
+                        const float dx = X.x - s.x, dy = X.y - s.y, dz = X.z - s.z;
+                        if (KERNEL_K) {
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float lg = (qb + j == i) ? 0.f : lg2_approx(r2);
+                            part = fmaf(s.w, lg, part);
+                        } else {
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                            const float inv = rcp_approx(r2);
+                            const float nr = fmaf(NN.x, dx, fmaf(NN.y, dy, NN.z * dz));
+                            const float mr = fmaf(MM.x, dx, fmaf(MM.y, dy, MM.z * dz));
+                            part = fmaf(s.w * inv, fmaf(nr, nr * inv, mr), part);
+                        }
+                    }
+                }
+                two_sum_acc(hi, lo, KERNEL_K ? part * (float)(M_LN2 / (4.0 * M_PI)) : part);
+            }
+        }
+        if (active) {
+            two_sum_acc(hi, lo, far);
+            out[orig] = make_float2(hi, lo);
+        }
+    }
+}
+
+}  // namespace
+
+// ============================================================================ host tree
+struct PmFmmTree {
+    int depth = 0, nbox = 0, nleaf = 0;
+    float3 origin{};
+    float L0 = 0.f;
+    std::vector<int> lev_off;
+    // device arrays
+    int *perm = nullptr, *lev_off_d = nullptr, *box_first = nullptr, *parent = nullptr;
+    int *child_off = nullptr, *child = nullptr, *v_off = nullptr, *v_list = nullptr;
+    int *u_off = nullptr, *u_list = nullptr;
+    int3* box_ijk = nullptr;
+    float4* sorted = nullptr;
+    float* M = nullptr;
+    float* Lc = nullptr;     // [nbox][9][216]
+    long long p2p_pairs = 0, m2l_pairs = 0;
+    ~PmFmmTree() {
+        pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
+        pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
+        pm_dfree(u_off); pm_dfree(u_list); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
+        pm_dfree(Lc);
+    }
+};
+
+void pm_fmm_free(pm_surface* s) {
+    delete s->fmm;
+    s->fmm = nullptr;
+}
+
+namespace {
+
+struct Key {
+    int x, y, z;
+    bool operator==(const Key& o) const { return x == o.x && y == o.y && z == o.z; }
+};
+struct KeyHash {
+    size_t operator()(const Key& k) const {
+        return ((size_t)(unsigned)k.x * 73856093u) ^ ((size_t)(unsigned)k.y * 19349663u) ^
+               ((size_t)(unsigned)k.z * 83492791u);
+    }
+};
+
+long long morton(int x, int y, int z) {
+    long long m = 0;
+    for (int b = 0; b < 20; ++b) {
+        m |= (long long)((x >> b) & 1) << (3 * b + 2);
+        m |= (long long)((y >> b) & 1) << (3 * b + 1);
+        m |= (long long)((z >> b) & 1) << (3 * b);
+    }
+    return m;
+}
+
+// Occupied boxes and interaction counts of a uniform tree of the given depth.
+struct LevelBoxes {
+    std::vector<Key> keys;
+    std::unordered_map<Key, int, KeyHash> index;
+};
+
+void build_levels(const std::vector<double>& x, int N, double ox, double oy, double oz,
+                  double L0, int depth, std::vector<LevelBoxes>& lv) {
+    lv.assign(depth + 1, LevelBoxes());
+    const int nb = 1 << depth;
+    std::vector<long long> codes;
+    for (int i = 0; i < N; ++i) {
+        int ix = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i] - ox) / L0 * nb)));
+        int iy = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 1] - oy) / L0 * nb)));
+        int iz = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 2] - oz) / L0 * nb)));
+        codes.push_back(morton(ix, iy, iz));
+        for (int l = depth; l >= 0; --l) {
+            Key k{ix >> (depth - l), iy >> (depth - l), iz >> (depth - l)};
+            auto& L = lv[l];
+            if (L.index.find(k) == L.index.end()) {
+                L.index[k] = (int)L.keys.size();
+                L.keys.push_back(k);
+            }
+        }
+    }
+    // order the boxes of each level by Morton code
+    for (int l = 0; l <= depth; ++l) {
+        auto& L = lv[l];
+        std::sort(L.keys.begin(), L.keys.end(), [](const Key& a, const Key& b) {
+            return morton(a.x, a.y, a.z) < morton(b.x, b.y, b.z);
+        });
+        L.index.clear();
+        for (int b = 0; b < (int)L.keys.size(); ++b) L.index[L.keys[b]] = b;
+    }
+}
+
+}  // namespace
+
+pm_status pm_fmm_build(pm_surface* s) {
+    if (s->fmm) return PM_OK;
+    const int N = s->N;
+    const std::vector<double>& x = s->h_x;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], x[3 * i + c]);
+            hi[c] = std::max(hi[c], x[3 * i + c]);
+        }
+    double L0 = 0;
+    for (int c = 0; c < 3; ++c) L0 = std::max(L0, hi[c] - lo[c]);
+    L0 *= 1.0001;
+    const double ox = 0.5 * (lo[0] + hi[0]) - 0.5 * L0, oy = 0.5 * (lo[1] + hi[1]) - 0.5 * L0,
+                 oz = 0.5 * (lo[2] + hi[2]) - 0.5 * L0;
+    // choose the depth by a cost model: P2P pairs * 19 + M2L node pairs * 22 instructions
+    int best_depth = 2;
+    double best_cost = 1e300;
+    std::vector<LevelBoxes> best_lv;
+    const int forced = s->opts.fmm_depth;
+    for (int depth = 2; depth <= 8; ++depth) {
+        if (forced >= 2 && depth != forced) continue;
+        std::vector<LevelBoxes> lv;
+        build_levels(x, N, ox, oy, oz, L0, depth, lv);
+        // leaf occupancies
+        const int nb = 1 << depth;
+        std::vector<int> occ(lv[depth].keys.size(), 0);
+        for (int i = 0; i < N; ++i) {
+            int ix = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i] - ox) / L0 * nb)));
+            int iy = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 1] - oy) / L0 * nb)));
+            int iz = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 2] - oz) / L0 * nb)));
+            occ[lv[depth].index[Key{ix, iy, iz}]]++;
+        }
+        int maxocc = *std::max_element(occ.begin(), occ.end());
+        double p2p = 0, m2l = 0;
+        for (size_t b = 0; b < lv[depth].keys.size(); ++b) {
+            const Key k = lv[depth].keys[b];
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        auto it = lv[depth].index.find(Key{k.x + dx, k.y + dy, k.z + dz});
+                        if (it != lv[depth].index.end()) p2p += (double)occ[b] * occ[it->second];
+                    }
+        }
+        for (int l = 2; l <= depth; ++l)
+            for (const Key& k : lv[l].keys) {
+                const Key p{k.x >> 1, k.y >> 1, k.z >> 1};
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dz = -1; dz <= 1; ++dz) {
+                            if (lv[l - 1].index.find(Key{p.x + dx, p.y + dy, p.z + dz}) ==
+                                lv[l - 1].index.end())
+                                continue;
+                            for (int c = 0; c < 8; ++c) {
+                                Key q{2 * (p.x + dx) + (c >> 2), 2 * (p.y + dy) + ((c >> 1) & 1),
+                                      2 * (p.z + dz) + (c & 1)};
+                                if (std::max({std::abs(q.x - k.x), std::abs(q.y - k.y),
+                                              std::abs(q.z - k.z)}) <= 1)
+                                    continue;
+                                if (lv[l].index.count(q)) m2l += 1;
+                            }
+                        }
+            }
+        const double cost = p2p * 19.0 + m2l * kFmmN3 * (double)kFmmN3 * 22.0;
+        if (maxocc <= kMaxLeafPts && cost < best_cost) {
+            best_cost = cost;
+            best_depth = depth;
+            best_lv = lv;
+            s->fmm_stats[0] = p2p;
+            s->fmm_stats[1] = m2l;
+        }
+        if (forced < 2 && cost > 4 * best_cost) break;
+    }
+    if (best_lv.empty()) {
+        pm_set_error("pm_fmm_build: no tree depth keeps leaves below %d points", kMaxLeafPts);
+        return PM_ERR_INVALID_ARG;
+    }
+    const int depth = best_depth;
+    std::vector<LevelBoxes>& lv = best_lv;
+    PmFmmTree* T = new PmFmmTree();
+    s->fmm = T;
+    T->depth = depth;
+    T->L0 = (float)L0;
+    T->origin = make_float3((float)ox, (float)oy, (float)oz);
+    T->lev_off.assign(depth + 2, 0);
+    for (int l = 0; l <= depth; ++l) T->lev_off[l + 1] = T->lev_off[l] + (int)lv[l].keys.size();
+    T->nbox = T->lev_off[depth + 1];
+    T->nleaf = (int)lv[depth].keys.size();
+    std::vector<int3> ijk(T->nbox);
+    std::vector<int> parent(T->nbox, -1), child_off(T->nbox + 1, 0), child;
+    std::vector<std::vector<int>> kids(T->nbox);
+    for (int l = 0; l <= depth; ++l)
+        for (size_t b = 0; b < lv[l].keys.size(); ++b) {
+            const Key k = lv[l].keys[b];
+            const int id = T->lev_off[l] + (int)b;
+            ijk[id] = make_int3(k.x, k.y, k.z);
+            if (l > 0) {
+                const int pid = T->lev_off[l - 1] + lv[l - 1].index[Key{k.x >> 1, k.y >> 1, k.z >> 1}];
+                parent[id] = pid;
+                kids[pid].push_back(id);
+            }
+        }
+    for (int b = 0; b < T->nbox; ++b) {
+        child_off[b + 1] = child_off[b] + (int)kids[b].size();
+        child.insert(child.end(), kids[b].begin(), kids[b].end());
+    }
+    // V lists (levels >= 2)
+    std::vector<int> v_off(T->nbox + 1, 0), v_list;
+    for (int l = 0; l <= depth; ++l)
+        for (size_t b = 0; b < lv[l].keys.size(); ++b) {
+            const int id = T->lev_off[l] + (int)b;
+            if (l >= 2) {
+                const Key k = lv[l].keys[b];
+                const Key p{k.x >> 1, k.y >> 1, k.z >> 1};
+                std::vector<int> vl;
+                for (int dx = -1; dx <= 1; ++dx)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dz = -1; dz <= 1; ++dz) {
+                            if (!lv[l - 1].index.count(Key{p.x + dx, p.y + dy, p.z + dz})) continue;
+                            for (int c = 0; c < 8; ++c) {
+                                Key q{2 * (p.x + dx) + (c >> 2), 2 * (p.y + dy) + ((c >> 1) & 1),
+                                      2 * (p.z + dz) + (c & 1)};
+                                if (std::max({std::abs(q.x - k.x), std::abs(q.y - k.y),
+                                              std::abs(q.z - k.z)}) <= 1)
+                                    continue;
+                                auto it = lv[l].index.find(q);
+                                if (it != lv[l].index.end()) vl.push_back(T->lev_off[l] + it->second);
+                            }
+                        }
+                std::sort(vl.begin(), vl.end());
+                v_list.insert(v_list.end(), vl.begin(), vl.end());
+            }
+            v_off[id + 1] = (int)v_list.size();
+        }
+    // points sorted by leaf (Morton order of leaves), U lists
+    const int nb = 1 << depth;
+    std::vector<int> leaf_of(N);
+    std::vector<int> cnt(T->nleaf, 0);
+    for (int i = 0; i < N; ++i) {
+        int ix = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i] - ox) / L0 * nb)));
+        int iy = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 1] - oy) / L0 * nb)));
+        int iz = std::min(nb - 1, std::max(0, (int)std::floor((x[3 * i + 2] - oz) / L0 * nb)));
+        leaf_of[i] = lv[depth].index[Key{ix, iy, iz}];
+        cnt[leaf_of[i]]++;
+    }
+    std::vector<int> first(T->nleaf + 1, 0);
+    for (int b = 0; b < T->nleaf; ++b) first[b + 1] = first[b] + cnt[b];
+    std::vector<int> fill(first.begin(), first.end() - 1), perm(N);
+    for (int i = 0; i < N; ++i) perm[fill[leaf_of[i]]++] = i;
+    std::vector<int> u_off(T->nleaf + 1, 0), u_list;
+    for (int b = 0; b < T->nleaf; ++b) {
+        const Key k = lv[depth].keys[b];
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    auto it = lv[depth].index.find(Key{k.x + dx, k.y + dy, k.z + dz});
+                    if (it != lv[depth].index.end()) u_list.push_back(it->second);
+                }
+        u_off[b + 1] = (int)u_list.size();
+    }
+    T->p2p_pairs = (long long)s->fmm_stats[0];
+    T->m2l_pairs = (long long)s->fmm_stats[1];
+    s->fmm_stats[2] = depth;
+    s->fmm_stats[3] = T->nbox;
+    // device copies
+    auto up = [&](auto** d, const auto& h) -> pm_status {
+        using E = typename std::remove_reference<decltype(h[0])>::type;
+        PM_TRY(pm_dmalloc(d, std::max<size_t>(1, h.size())));
+        if (!h.empty())
+            PM_CUDA_TRY(cudaMemcpy(*d, h.data(), sizeof(E) * h.size(), cudaMemcpyHostToDevice));
+        return PM_OK;
+    };
+    PM_TRY(up(&T->perm, perm));
+    PM_TRY(up(&T->lev_off_d, T->lev_off));
+    PM_TRY(up(&T->box_first, first));
+    PM_TRY(up(&T->parent, parent));
+    PM_TRY(up(&T->child_off, child_off));
+    PM_TRY(up(&T->child, child));
+    PM_TRY(up(&T->v_off, v_off));
+    PM_TRY(up(&T->v_list, v_list));
+    PM_TRY(up(&T->u_off, u_off));
+    PM_TRY(up(&T->u_list, u_list));
+    PM_TRY(up(&T->box_ijk, ijk));
+    PM_TRY(pm_dmalloc(&T->sorted, N));
+    PM_TRY(pm_dmalloc(&T->M, (size_t)T->nbox * kFmmN3));
+    PM_TRY(pm_dmalloc(&T->Lc, (size_t)T->nbox * 9 * kFmmN3));
+    // interpolation constants
+    FmmConst F;
+    std::memset(&F, 0, sizeof(F));
+    double cheb[kFmmN], bary[kFmmN];
+    for (int k = 0; k < kFmmN; ++k) cheb[k] = std::cos(M_PI * (2 * k + 1) / (2.0 * kFmmN));
+    for (int a = 0; a < kFmmN; ++a) {
+        double prod = 1.0;
+        for (int b = 0; b < kFmmN; ++b)
+            if (b != a) prod *= cheb[a] - cheb[b];
+        bary[a] = 1.0 / prod;
+        F.cheb[a] = (float)cheb[a];
+        F.bary[a] = (float)bary[a];
+    }
+    for (int o = 0; o < 2; ++o)
+        for (int m = 0; m < kFmmN; ++m)
+            for (int k = 0; k < kFmmN; ++k) {
+                const double u = 0.5 * (cheb[k] + (2 * o - 1));
+                double v = bary[m];
+                for (int b = 0; b < kFmmN; ++b)
+                    if (b != m) v *= u - cheb[b];
+                F.T[o][m][k] = (float)v;
+            }
+    PM_CUDA_TRY(cudaMemcpyToSymbol(cF, &F, sizeof(F)));
+    return PM_OK;
+}
+
+pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
+    PM_TRY(pm_fmm_build(s));
+    PmFmmTree* T = s->fmm;
+    DevTree t;
+    t.N = s->N;
+    t.depth = T->depth;
+    t.nlev = T->depth + 1;
+    t.nbox_total = T->nbox;
+    t.origin = T->origin;
+    t.L0 = T->L0;
+    t.perm = T->perm;
+    t.lev_off = T->lev_off_d;
+    t.box_ijk = T->box_ijk;
+    t.box_first = T->box_first;
+    t.parent = T->parent;
+    t.child_off = T->child_off;
+    t.child = T->child;
+    t.v_off = T->v_off;
+    t.v_list = T->v_list;
+    t.u_off = T->u_off;
+    t.u_list = T->u_list;
+    const int* skip = s->skip_flag;
+    const int depth = T->depth;
+    k_fmm_gather<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->src32, T->perm, s->N, T->sorted, skip);
+    k_fmm_p2m<<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, T->M, skip);
+    for (int l = depth - 1; l >= 2; --l) {
+        const int nb = T->lev_off[l + 1] - T->lev_off[l];
+        k_fmm_m2m<<<nb, kThreads, 0, st>>>(t, l, T->M, skip);
+    }
+    const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
+    if (which_K)
+        k_fmm_m2l<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
+    else
+        k_fmm_m2l<false><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
+    for (int l = 3; l <= depth; ++l) {
+        const int nb = T->lev_off[l + 1] - T->lev_off[l];
+        if (which_K)
+            k_fmm_l2l<1><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
+        else
+            k_fmm_l2l<9><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
+    }
+    float2* out = reinterpret_cast<float2*>(s->partial);
+    if (which_K)
+        k_fmm_leaf<true><<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, s->tgt32, T->Lc, s->eps2, out, skip);
+    else
+        k_fmm_leaf<false><<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, s->tgt32, T->Lc, s->eps2, out, skip);
+    s->launch_total += 4 + 2 * std::max(0, depth - 2);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}

@@ -69,6 +69,7 @@ struct pm_ctx {
 };
 
 struct PmSolveWork;
+struct PmFmmTree;
 
 struct pm_surface {
     pm_ctx* ctx = nullptr;
@@ -132,6 +133,8 @@ struct pm_surface {
     // solve workspace (pm_solve.cu) and the device flag that lets the apply
     // kernels of a finished Krylov cycle return at once
     PmSolveWork* solve_work = nullptr;
+    PmFmmTree* fmm = nullptr;
+    double fmm_stats[4] = {0, 0, 0, 0};
     const int* skip_flag = nullptr;
 
     // scratch
@@ -172,6 +175,11 @@ pm_status pm_pack_ff(pm_surface* s, cudaStream_t st);
 pm_status pm_prep_ff(pm_surface* s, const double* sigma, cudaStream_t st);
 int pm_ff_splits(const pm_surface* s);
 pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st);
+
+// Chebyshev FMM (pm_fmm.cu)
+pm_status pm_fmm_build(pm_surface* s);
+pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st);
+void pm_fmm_free(pm_surface* s);
 
 // solve (pm_solve.cu)
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,

@@ -1,0 +1,84 @@
+"""Chebyshev FMM far field (PM_PREC_FMM) against the direct sums and the oracle.
+
+The FMM replaces the far part of the smooth sums by 6x6x6-point Chebyshev
+interpolation between boxes; its error against the exact sum is bounded by
+the per-config tolerance for float32-class applies (at most 1e-5 relative).
+"""
+
+import numpy as np
+import pytest
+
+from conftest import oracle_processes
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_FMM = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_12501_gb300 as pm
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+_S = {}
+
+
+def surf(ctx, name):
+    import paper_2401_12501_gb300 as pm
+    if name not in _S:
+        wl = make_workload(name)
+        s = pm.Surface.from_fixture(ctx, wl.surface)
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        _S[name] = (wl, s)
+    return _S[name]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["torus_98304", "ellipsoid_9600"])
+def test_fmm_matches_direct_sum(ctx, name):
+    import paper_2401_12501_gb300 as pm
+    wl, s = surf(ctx, name)
+    st = s.fmm_stats()
+    assert st["depth"] >= 2 and st["boxes"] > 8
+    rng = np.random.default_rng(12)
+    sigma = rng.standard_normal(wl.N) + 1.0
+    for part in (pm.PM_PART_SMOOTH_R, pm.PM_PART_SMOOTH_K):
+        exact = s.apply_part(part, sigma, "ff")
+        fmm = s.apply_part(part, sigma, "fmm")
+        assert rel(fmm, exact) < TOL_FMM, (part, rel(fmm, exact), st)
+
+
+def test_fmm_full_apply_against_oracle_rows(ctx):
+    from oracle.operator import Discretization, NearField, apply_K, apply_R
+    wl, s = surf(ctx, "torus_98304")
+    rng = np.random.default_rng(13)
+    rows = sorted(set([0, wl.N - 1] + [int(i) for i in rng.integers(0, wl.N, 14)]))
+    d = Discretization.from_workload(wl)
+    nf = NearField(d, rows=rows, processes=oracle_processes())
+    sigma = rng.standard_normal(wl.N) + 1.0
+    oR = apply_R(d, nf, sigma, rows)
+    oK = apply_K(d, nf, sigma, rows)
+    yR = s.apply_R(sigma, "fmm")[rows]
+    yK = s.apply_K(sigma, "fmm")[rows]
+    assert np.abs(yR - oR).max() <= TOL_FMM * np.abs(oR).max()
+    assert np.abs(yK - oK).max() <= TOL_FMM * np.abs(oK).max()
+
+
+def test_fmm_operator_in_refined_solve(ctx):
+    """GMRES with FMM applies + float-float refinement reaches the same solution."""
+    wl, s = surf(ctx, "ellipsoid_9600")
+    u_fmm, i_fmm = s.solve(wl.f, tol=1e-10, prec="fmm")
+    u_32, _ = s.solve(wl.f, tol=1e-10, prec="fp32")
+    w = wl.surface.weights
+    assert i_fmm[0].residual <= 1e-10
+    assert np.sqrt(np.dot(w, (u_fmm - u_32) ** 2) / np.dot(w, u_32 ** 2)) < 1e-8
