@@ -63,7 +63,7 @@ typedef enum {
                              pipe, float64 near-field values: float64-class accuracy
                              (~1e-13 relative) at a fraction of GB300's float64 cost */
     PM_PREC_FMM = 4       /* float32 Chebyshev kernel-interpolation FMM for the smooth
-                             sums (far field by 6x6x6-point box expansions, adjacent
+                             sums (far field by 8x8x8-point box expansions, adjacent
                              leaves exact), float32 near-field values; large surfaces */
 } pm_precision;
 

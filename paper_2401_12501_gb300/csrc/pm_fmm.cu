@@ -37,9 +37,9 @@
 
 namespace {
 
-constexpr int kFmmN = 6;                       // Chebyshev points per dimension
-constexpr int kFmmN3 = kFmmN * kFmmN * kFmmN;  // 216
-constexpr int kThreads = 256;
+constexpr int kFmmN = 8;                       // Chebyshev points per dimension
+constexpr int kFmmN3 = kFmmN * kFmmN * kFmmN;  // 512
+constexpr int kThreads = 512;                  // one thread per expansion point
 constexpr int kMaxLeafPts = 4096;
 
 struct FmmConst {
@@ -471,7 +471,8 @@ pm_status pm_fmm_build(pm_surface* s) {
     L0 *= 1.0001;
     const double ox = 0.5 * (lo[0] + hi[0]) - 0.5 * L0, oy = 0.5 * (lo[1] + hi[1]) - 0.5 * L0,
                  oz = 0.5 * (lo[2] + hi[2]) - 0.5 * L0;
-    // choose the depth by a cost model: P2P pairs * 19 + M2L node pairs * 22 instructions
+    // choose the depth by a cost model calibrated on GB300 with these kernels:
+    // about 4 ns per adjacent-leaf pair (P2P) and 1 ns per far-field Chebyshev node pair
     int best_depth = 2;
     double best_cost = 1e300;
     std::vector<LevelBoxes> best_lv;
@@ -519,7 +520,7 @@ pm_status pm_fmm_build(pm_surface* s) {
                             }
                         }
             }
-        const double cost = p2p * 19.0 + m2l * kFmmN3 * (double)kFmmN3 * 22.0;
+        const double cost = p2p * 4.0 + m2l * kFmmN3 * (double)kFmmN3 * 1.0;
         if (maxocc <= kMaxLeafPts && cost < best_cost) {
             best_cost = cost;
             best_depth = depth;
