@@ -87,6 +87,8 @@ typedef struct {
     int residual_prec;      /* pm_solve: precision of true residuals and of u = K~ sigma
                                (PM_PREC_FF or PM_PREC_FP64); default PM_PREC_FF         */
     int fmm_depth;          /* PM_PREC_FMM: octree depth (2..8); 0 = chosen by a cost model */
+    int batch_rhs;          /* nrhs > 1: 1 = batched kernels and lockstep GMRES over all
+                               right-hand sides (default), 0 = one right-hand side at a time */
     int direct_tpt;         /* float32 smooth sums: targets per thread (1, 2 or 4); 0 = auto */
     int direct_blocks_per_sm; /* float32 smooth sums: source splits chosen so the grid holds
                                about this many blocks per SM (1..16); 0 = auto          */
@@ -204,6 +206,9 @@ typedef struct {
  *   f, u       [nrhs*N]  (host, or device with PM_SOLVE_DEVICE_PTRS)
  *   sigma_out  [nrhs*N] or NULL
  *   info       [nrhs] or NULL
+ * With nrhs > 1 (and opts.batch_rhs) all right-hand sides are solved together:
+ * batched multi-RHS smooth sums and lockstep GMRES; info[r].iterations then
+ * counts the lockstep Arnoldi steps of the whole batch.
  * PM_ERR_RHS_NOT_MEAN_ZERO if f is not mean zero and PM_SOLVE_PROJECT_RHS is not set;
  * PM_ERR_NOT_CONVERGED if tol is not met within maxit inner iterations.
  */

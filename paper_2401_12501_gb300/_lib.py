@@ -44,7 +44,8 @@ class PmOpts(C.Structure):
                 ("near_max_depth", C.c_int), ("near_max_leaves", C.c_int),
                 ("gmres_restart", C.c_int), ("max_refine", C.c_int),
                 ("inner_tol", C.c_double), ("mean_tol", C.c_double),
-                ("residual_prec", C.c_int), ("fmm_depth", C.c_int), ("direct_tpt", C.c_int),
+                ("residual_prec", C.c_int), ("fmm_depth", C.c_int), ("batch_rhs", C.c_int),
+                ("direct_tpt", C.c_int),
                 ("direct_blocks_per_sm", C.c_int)]
 
 

@@ -60,6 +60,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->mean_tol = 1e-8;
     o->residual_prec = PM_PREC_FF;
     o->fmm_depth = 0;
+    o->batch_rhs = 1;
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
 }
@@ -256,6 +257,8 @@ static void free_surface(pm_surface* s) {
     if (s->ctx) cudaSetDevice(s->ctx->device);
     pm_solve_free(s);
     pm_fmm_free(s);
+    pm_batch_free(s);
+    pm_batch_solve_free(s);
     pm_dfree(s->x); pm_dfree(s->n); pm_dfree(s->H); pm_dfree(s->w); pm_dfree(s->J);
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);
@@ -554,10 +557,27 @@ static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = s->N;
+    const bool batched = nrhs > 1 && smooth && near && s->opts.batch_rhs &&
+                         (prec == PM_PREC_FP32 || prec == PM_PREC_FF);
     if (on_device) {
-        for (int r = 0; r < nrhs; ++r)
-            PM_TRY(pm_apply_dev(s, kernel_K, smooth, near, sigma + r * N, out + r * N, prec, st));
+        if (batched) {
+            PM_TRY(pm_apply_batch(s, kernel_K, sigma, (long long)N, out, (long long)N, nrhs, prec, st));
+        } else {
+            for (int r = 0; r < nrhs; ++r)
+                PM_TRY(pm_apply_dev(s, kernel_K, smooth, near, sigma + r * N, out + r * N, prec, st));
+        }
         PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+    if (batched) {
+        PM_TRY(pm_ensure_scratch(s, N * (size_t)nrhs));
+        PM_CUDA_TRY(cudaMemcpyAsync(s->dbuf_in, sigma, N * nrhs * sizeof(double),
+                                    cudaMemcpyHostToDevice, st));
+        PM_TRY(pm_apply_batch(s, kernel_K, s->dbuf_in, (long long)N, s->dbuf_out, (long long)N,
+                              nrhs, prec, st));
+        PM_CUDA_TRY(cudaMemcpyAsync(out, s->dbuf_out, N * nrhs * sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        PM_CUDA_TRY(cudaStreamSynchronize(st));
         return PM_OK;
     }
     PM_TRY(pm_ensure_scratch(s, N));
@@ -668,6 +688,9 @@ extern "C" pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrh
     if (!s->has_coeff) { pm_set_error("pm_solve: call pm_surface_set_coeff first"); return PM_ERR_NO_COEFF; }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     const size_t N = s->N;
+    if (nrhs > 1 && s->opts.batch_rhs)
+        return pm_solve_batch(s, f, u, nrhs, tol, maxit, prec, flags, sigma_out, info,
+                              (cudaStream_t)stream);
     pm_status worst = PM_OK;
     for (int r = 0; r < nrhs; ++r) {
         pm_status st = pm_solve_impl(s, f + r * N, u + r * N, tol, maxit, prec, flags,

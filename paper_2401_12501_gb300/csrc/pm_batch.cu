@@ -1,0 +1,1004 @@
+// Batched (multi right-hand side) applies and solves on one surface.
+//
+// Many right-hand sides on the same surface and coefficient share every
+// pair's geometry: for the remainder, r, |r|^2, 1/|r|^2, n'.r and m.r are
+// target/source properties, so the pair factor g = (1/|r|^2)((n'.r)^2/|r|^2 + m.r)
+// is formed once and each right-hand side adds s_r * g (one FMA per RHS).
+// The same holds for the parametrix (one lg2 per pair) and for the float-float
+// accurate sums (one float-float product per RHS).
+//
+// The batched solve runs independent GMRES iterations for all right-hand
+// sides in lockstep (one batched apply per Arnoldi step, per-RHS Krylov bases
+// and Givens rotations, per-RHS convergence flags); iterative refinement uses
+// batched float-float residuals; u = K~ sigma uses the batched float-float
+// parametrix sum.
+#include "pm_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kRB = 8;          // right-hand sides per block (float32)
+constexpr int kRBff = 4;        // right-hand sides per block (float-float)
+constexpr int kTile = 256;
+constexpr int kStage = 512;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (v - bp);
+    hi = s;
+}
+
+// s[r][j] = w_j sigma_r[j] / a_j (float32), sig32[r][patch][k] = sigma_r
+__global__ void k_prep32_multi(const double* __restrict__ sigma, long long ld_sigma,
+                               const double* __restrict__ wa, float* __restrict__ s, int N,
+                               int pp, int ppad, int npatch, float* __restrict__ sig32,
+                               const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (j >= N) return;
+    const double v = sigma[r * ld_sigma + j];
+    s[(size_t)r * N + j] = (float)(wa[j] * v);
+    const int P = j / pp;
+    sig32[((size_t)r * npatch + P) * ppad + (j - P * pp)] = (float)v;
+}
+
+// float32 smooth sums for a group of kRB right-hand sides (blockIdx.z)
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, int nrhs,
+                 const float4* __restrict__ tgt, int N, int chunk, float eps2,
+                 float2* __restrict__ partial, int nsplit, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ float4 sP[kStage];
+    __shared__ float sS[kRB][kStage];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kThreads + tid;
+    const int r0 = blockIdx.z * kRB;
+    const int nr = min(kRB, nrhs - r0);
+    const int tbase = blockIdx.x * kThreads, tend = tbase + kThreads;
+    float tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0, mx = 0, my = 0, mz = 0;
+    if (i < N) {
+        const float4 a = tgt[i];
+        tx = a.x; ty = a.y; tz = a.z;
+        if (!KERNEL_K) {
+            const float4 b = tgt[N + i], c = tgt[2 * N + i];
+            nx = b.x; ny = b.y; nz = b.z;
+            mx = c.x; my = c.y; mz = c.z;
+        }
+    }
+    float hi[kRB], lo[kRB];
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) hi[q] = lo[q] = 0.f;
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(s0 + chunk, N);
+    for (int base = s0; base < s1; base += kStage) {
+        const int len = min(kStage, s1 - base);
+        __syncthreads();
+        for (int j = tid; j < len; j += kThreads) {
+            sP[j] = pos[base + j];
+#pragma unroll
+            for (int q = 0; q < kRB; ++q)
+                sS[q][j] = (q < nr) ? s[(size_t)(r0 + q) * N + base + j] : 0.f;
+        }
+        __syncthreads();
+        for (int j0 = 0; j0 < len; j0 += kTile) {
+            const int j1 = min(j0 + kTile, len);
+            const bool own = KERNEL_K && !(base + j1 <= tbase || base + j0 >= tend);
+            float part[kRB];
+#pragma unroll
+            for (int q = 0; q < kRB; ++q) part[q] = 0.f;
+#pragma unroll 2
+            for (int j = j0; j < j1; ++j) {
+                const float4 p = sP[j];
+                const float dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
+                float gfac;
+                if (KERNEL_K) {
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    gfac = (own && base + j == i) ? 0.f : lg2_approx(r2);
+                } else {
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                    const float inv = rcp_approx(r2);
+                    const float nr2 = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+                    const float mr = fmaf(mx, dx, fmaf(my, dy, mz * dz));
+                    gfac = inv * fmaf(nr2, nr2 * inv, mr);
+                }
+#pragma unroll
+                for (int q = 0; q < kRB; ++q) part[q] = fmaf(sS[q][j], gfac, part[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kRB; ++q) two_sum_acc(hi[q], lo[q], part[q]);
+        }
+    }
+    if (i < N) {
+        const float sc = KERNEL_K ? (float)(M_LN2 / (4.0 * M_PI)) : 1.f;
+#pragma unroll
+        for (int q = 0; q < kRB; ++q)
+            if (q < nr)
+                partial[((size_t)(r0 + q) * nsplit + blockIdx.y) * N + i] =
+                    make_float2(hi[q] * sc, lo[q] * sc);
+    }
+}
+
+// out_r[i] = sum_s partial[r][s][i] + sum_b C[b,:] . sigma_r[patch_b]   (warp per (row, rhs))
+__global__ void __launch_bounds__(256)
+k_near_multi32(int N, int ppad, int npatch, const int* __restrict__ row_ptr,
+               const int* __restrict__ blk_patch, const float* __restrict__ vals,
+               const float* __restrict__ sig32, const float2* __restrict__ partial, int nsplit,
+               double* __restrict__ out, long long ld_out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.y;
+    if (warp >= N) return;
+    const int i = warp;
+    float hi = 0.f, lo = 0.f;
+    for (int sp = lane; sp < nsplit; sp += 32) {
+        const float2 v = partial[((size_t)r * nsplit + sp) * N + i];
+        two_sum_acc(hi, lo, v.x);
+        lo += v.y;
+    }
+    const int q4 = ppad >> 2;
+    const int rb = row_ptr[i];
+    const int total = (row_ptr[i + 1] - rb) * q4;
+    const float4* v4 = reinterpret_cast<const float4*>(vals) + (size_t)rb * q4;
+    const float4* s4 = reinterpret_cast<const float4*>(sig32 + (size_t)r * npatch * ppad);
+    float acc = 0.f;
+    for (int e = lane; e < total; e += 32) {
+        const int b = e / q4;
+        const float4 v = __ldg(v4 + e);
+        const float4 x = __ldg(s4 + (size_t)blk_patch[rb + b] * q4 + (e - b * q4));
+        acc = fmaf(v.x, x.x, fmaf(v.y, x.y, fmaf(v.z, x.z, fmaf(v.w, x.w, acc))));
+    }
+    two_sum_acc(hi, lo, acc);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        two_sum_acc(hi, lo, h2);
+        lo += l2;
+    }
+    if (lane == 0) out[r * ld_out + i] = (double)hi + (double)lo;
+}
+
+// ------------------------------------------------------------------ float-float batched sums
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    e = b - (s - a);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e += a.l + b.l;
+    ff r;
+    fast_two_sum(s, e, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    ff r;
+    fast_two_sum(p, e, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ ff ff_sqr(ff a) {
+    const float p = a.h * a.h;
+    float e = fmaf(a.h, a.h, -p);
+    e = fmaf(2.f * a.h, a.l, e);
+    ff r;
+    fast_two_sum(p, e, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ ff ff_rcp(ff a) {
+    const float y = rcp_approx(a.h);
+    const float p = a.h * y;
+    const float ep = fmaf(a.h, y, -p);
+    const float res = ((1.f - p) - ep) - a.l * y;
+    ff r;
+    fast_two_sum(y, y * res, r.h, r.l);
+    return r;
+}
+// float-float natural logarithm, same table method as the single-RHS kernels
+__device__ __forceinline__ ff ff_log(ff x, const float4* __restrict__ tab) {
+    int e;
+    const float mh = frexpf(x.h, &e);
+    const float sc = ldexpf(1.f, -e + 1);
+    ff m{mh * 2.f, x.l * sc};
+    e -= 1;
+    const int k = (int)((m.h - 1.f) * 128.f);
+    const float4 T = tab[min(max(k, 0), 127)];
+    const ff p = ff_mul(m, ff{T.x, T.y});
+    float th, tl;
+    fast_two_sum(p.h - 1.f, p.l, th, tl);
+    const ff t{th, tl};
+    const ff t2 = ff_sqr(t);
+    const float tf = t.h;
+    const float poly = fmaf(fmaf(fmaf(-1.f / 6.f, tf, 0.2f), tf, -0.25f), tf, 1.f / 3.f);
+    const float cubic = tf * tf * tf * poly;
+    const float L2H = 0.693147182464599609375f;
+    const float L2L = -1.904654323148236e-09f;
+    const float ef = (float)e;
+    const float lp = L2H * ef;
+    float le = fmaf(L2H, ef, -lp);
+    le = fmaf(L2L, ef, le);
+    ff r;
+    fast_two_sum(lp, le, r.h, r.l);
+    r = ff_add(r, ff{T.z, T.w});
+    r = ff_add(r, t);
+    r = ff_add(r, ff{-0.5f * t2.h, -0.5f * t2.l});
+    r = ff_add(r, ff{cubic, 0.f});
+    return r;
+}
+
+// float-float strengths: sff[r][j] = (hi, lo) of w_j sigma_r[j] / a_j
+__global__ void k_prep_ff_multi(const double* __restrict__ sigma, long long ld_sigma,
+                                const double* __restrict__ wa, float2* __restrict__ sff, int N,
+                                const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (j >= N) return;
+    const double v = wa[j] * sigma[r * ld_sigma + j];
+    const float h = (float)v;
+    sff[(size_t)r * N + j] = make_float2(h, (float)(v - (double)h));
+}
+
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ sff, int nrhs,
+                  const float4* __restrict__ tg, const float4* __restrict__ log_tab, int N,
+                  int chunk, float2* __restrict__ partial, int nsplit,
+                  const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    constexpr int kSt = 256;
+    __shared__ float4 sh[2 * kSt];
+    __shared__ float2 sS[kRBff][kSt];
+    __shared__ float4 stab[128];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * kThreads + tid;
+    const int r0 = blockIdx.z * kRBff;
+    const int nr = min(kRBff, nrhs - r0);
+    const int tbase = blockIdx.x * kThreads, tend = tbase + kThreads;
+    if (KERNEL_K)
+        for (int k = tid; k < 128; k += kThreads) stab[k] = log_tab[k];
+    ff X[3], NP[3], MM[3];
+    {
+        float4 v[6];
+        for (int q = 0; q < 6; ++q) v[q] = (i < N) ? tg[6 * (size_t)i + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        X[0] = ff{v[0].x, v[1].x}; X[1] = ff{v[0].y, v[1].y}; X[2] = ff{v[0].z, v[1].z};
+        NP[0] = ff{v[2].x, v[3].x}; NP[1] = ff{v[2].y, v[3].y}; NP[2] = ff{v[2].z, v[3].z};
+        MM[0] = ff{v[4].x, v[5].x}; MM[1] = ff{v[4].y, v[5].y}; MM[2] = ff{v[4].z, v[5].z};
+    }
+    ff acc[kRBff];
+#pragma unroll
+    for (int q = 0; q < kRBff; ++q) acc[q] = ff{0.f, 0.f};
+    const int s0 = blockIdx.y * chunk;
+    const int s1 = min(s0 + chunk, N);
+    for (int base = s0; base < s1; base += kSt) {
+        const int len = min(kSt, s1 - base);
+        __syncthreads();
+        for (int j = tid; j < 2 * len; j += kThreads) sh[j] = src_ff[2 * (size_t)base + j];
+        for (int j = tid; j < len; j += kThreads)
+#pragma unroll
+            for (int q = 0; q < kRBff; ++q)
+                sS[q][j] = (q < nr) ? sff[(size_t)(r0 + q) * N + base + j] : make_float2(0.f, 0.f);
+        __syncthreads();
+        const bool own = !(base + len <= tbase || base >= tend);
+        for (int j = 0; j < len; ++j) {
+            if (own && base + j == i) continue;
+            const float4 A = sh[2 * j], B = sh[2 * j + 1];
+            const ff dx = ff_sub(X[0], ff{A.x, B.x});
+            const ff dy = ff_sub(X[1], ff{A.y, B.y});
+            const ff dz = ff_sub(X[2], ff{A.z, B.z});
+            const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+            ff gfac;
+            if (KERNEL_K) {
+                gfac = ff_log(r2, stab);
+            } else {
+                const ff inv = ff_rcp(r2);
+                const ff nr2 = ff_add(ff_add(ff_mul(NP[0], dx), ff_mul(NP[1], dy)), ff_mul(NP[2], dz));
+                const ff mr = ff_add(ff_add(ff_mul(MM[0], dx), ff_mul(MM[1], dy)), ff_mul(MM[2], dz));
+                gfac = ff_mul(inv, ff_add(ff_mul(nr2, ff_mul(nr2, inv)), mr));
+            }
+#pragma unroll
+            for (int q = 0; q < kRBff; ++q) {
+                const float2 sv = sS[q][j];
+                acc[q] = ff_add(acc[q], ff_mul(ff{sv.x, sv.y}, gfac));
+            }
+        }
+    }
+    if (i < N) {
+#pragma unroll
+        for (int q = 0; q < kRBff; ++q) {
+            if (q >= nr) continue;
+            ff v = acc[q];
+            if (KERNEL_K) v = ff_mul(v, ff{(float)(1.0 / (4.0 * M_PI)),
+                                           (float)(1.0 / (4.0 * M_PI) - (double)(float)(1.0 / (4.0 * M_PI)))});
+            partial[((size_t)(r0 + q) * nsplit + blockIdx.y) * N + i] = make_float2(v.h, v.l);
+        }
+    }
+}
+
+// float64 near field + float-float split partials, warp per (row, rhs)
+__global__ void __launch_bounds__(256)
+k_near_multi64(int N, int pp, const int* __restrict__ row_ptr, const int* __restrict__ blk_patch,
+               const double* __restrict__ vals, const double* __restrict__ sigma,
+               long long ld_sigma, const float2* __restrict__ partial, int nsplit,
+               double* __restrict__ out, long long ld_out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.y;
+    if (warp >= N) return;
+    const int i = warp;
+    double acc = 0.0;
+    for (int sp = lane; sp < nsplit; sp += 32) {
+        const float2 v = partial[((size_t)r * nsplit + sp) * N + i];
+        acc += (double)v.x + (double)v.y;
+    }
+    const double* sg = sigma + r * ld_sigma;
+    for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        const double* v = vals + (size_t)b * pp;
+        const double* x = sg + (size_t)blk_patch[b] * pp;
+        for (int k = lane; k < pp; k += 32) acc += v[k] * x[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[r * ld_out + i] = acc;
+}
+
+}  // namespace
+
+// ============================================================================ batched apply
+struct PmBatchWork {
+    int cap = 0;               // right-hand sides the buffers hold
+    float* s32 = nullptr;      // [cap][N]
+    float* sig32 = nullptr;    // [cap][npatch][ppad]
+    float2* sff = nullptr;     // [cap][N]
+    float2* part = nullptr;    // [cap][nsplit_max][N]
+    int nsplit_max = 0;
+};
+
+void pm_batch_free(pm_surface* s) {
+    if (!s->batch) return;
+    pm_dfree(s->batch->s32);
+    pm_dfree(s->batch->sig32);
+    pm_dfree(s->batch->sff);
+    pm_dfree(s->batch->part);
+    delete s->batch;
+    s->batch = nullptr;
+}
+
+static pm_status batch_ensure(pm_surface* s, int nrhs) {
+    const int nsplit_max = 8;
+    if (s->batch && s->batch->cap >= nrhs) return PM_OK;
+    pm_batch_free(s);
+    s->batch = new PmBatchWork();
+    PmBatchWork& B = *s->batch;
+    B.cap = nrhs;
+    B.nsplit_max = nsplit_max;
+    PM_TRY(pm_dmalloc(&B.s32, (size_t)nrhs * s->N));
+    PM_TRY(pm_dmalloc(&B.sig32, (size_t)nrhs * s->npatch * s->ppad));
+    PM_CUDA_TRY(cudaMemset(B.sig32, 0, sizeof(float) * (size_t)nrhs * s->npatch * s->ppad));
+    PM_TRY(pm_dmalloc(&B.sff, (size_t)nrhs * s->N));
+    PM_TRY(pm_dmalloc(&B.part, (size_t)nrhs * nsplit_max * s->N));
+    return PM_OK;
+}
+
+static int batch_splits(const pm_surface* s, int nrhs, int rb) {
+    const int tblocks = pm_ceil_div(s->N, kThreads) * pm_ceil_div(nrhs, rb);
+    const int want = 8 * s->ctx->num_sms;
+    int ns = (want + tblocks / 2) / tblocks;
+    return std::max(1, std::min(ns, std::min(8, std::max(1, s->N / 256))));
+}
+
+// out[r*ld_out + i] = (R~ or K~) sigma_r, r < nrhs; sigma_r at sigma + r*ld_sigma.
+pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long long ld_sigma,
+                         double* out, long long ld_out, int nrhs, pm_precision prec,
+                         cudaStream_t st) {
+    PM_TRY(batch_ensure(s, nrhs));
+    PmBatchWork& B = *s->batch;
+    const int N = s->N;
+    const int* skip = s->skip_flag;
+    dim3 gp(pm_ceil_div(N, 256), nrhs);
+    if (prec == PM_PREC_FF) {
+        const int ns = batch_splits(s, nrhs, kRBff);
+        {
+            PhaseTimer t(s, PM_PHASE_PREP, st);
+            k_prep_ff_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.sff, N, skip);
+        }
+        {
+            PhaseTimer t(s, PM_PHASE_DIRECT64, st);
+            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, kRBff));
+            const int chunk = pm_ceil_div(N, ns);
+            if (kernel_K)
+                k_direct_multi_ff<true><<<g, kThreads, 0, st>>>(s->src_ff, B.sff, nrhs, s->tgt_ff,
+                                                               s->log_tab, N, chunk, B.part, ns, skip);
+            else
+                k_direct_multi_ff<false><<<g, kThreads, 0, st>>>(s->src_ff, B.sff, nrhs, s->tgt_ff,
+                                                                s->log_tab, N, chunk, B.part, ns, skip);
+        }
+        PhaseTimer t(s, PM_PHASE_NEAR, st);
+        dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
+        k_near_multi64<<<gn, 256, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
+                                           kernel_K ? s->cK64 : s->cR64, sigma, ld_sigma, B.part,
+                                           ns, out, ld_out, skip);
+    } else {
+        const int ns = batch_splits(s, nrhs, kRB);
+        {
+            PhaseTimer t(s, PM_PHASE_PREP, st);
+            k_prep32_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.s32, N, s->pp, s->ppad,
+                                               s->npatch, B.sig32, skip);
+        }
+        {
+            PhaseTimer t(s, kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R, st);
+            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, kRB));
+            const int chunk = pm_ceil_div(N, ns);
+            if (kernel_K)
+                k_direct_multi32<true><<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N,
+                                                              chunk, s->eps2, B.part, ns, skip);
+            else
+                k_direct_multi32<false><<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N,
+                                                               chunk, s->eps2, B.part, ns, skip);
+        }
+        PhaseTimer t(s, PM_PHASE_NEAR, st);
+        dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
+        k_near_multi32<<<gn, 256, 0, st>>>(N, s->ppad, s->npatch, s->row_ptr, s->blk_patch,
+                                           kernel_K ? s->cK32 : s->cR32, B.sig32, B.part, ns, out,
+                                           ld_out, skip);
+    }
+    s->launch_total += 3;
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+// ============================================================================ batched solve
+namespace {
+
+constexpr int kRed = 256;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// partial[r][blk][j] = sum over the block's rows of A_r,j[i] * b_r[i]
+__global__ void __launch_bounds__(kRed)
+k_bdots(const double* __restrict__ A, long long col_stride, long long rhs_stride_A, int ncols,
+        const double* __restrict__ b, long long rhs_stride_b, int N,
+        double* __restrict__ partial, const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    __shared__ double sh[32];
+    const double* Ar = A + r * rhs_stride_A;
+    const double* br = b + r * rhs_stride_b;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = 0; j < ncols; ++j) {
+        const double* a = Ar + j * col_stride;
+        double acc = 0.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) acc += a[i] * br[i];
+        acc = warp_sum_d(acc);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) sh[wid] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+            t = warp_sum_d(t);
+            if (threadIdx.x == 0) partial[((size_t)r * gridDim.x + blockIdx.x) * ncols + j] = t;
+        }
+    }
+}
+
+__global__ void k_breduce(const double* __restrict__ partial, int nblk, int ncols,
+                          double* __restrict__ out, long long ld_out, const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncols) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[((size_t)r * nblk + b) * ncols + j];
+    out[r * ld_out + j] = s;
+}
+
+// w_r -= sum_j A_r,j c_r[j]
+__global__ void k_bsub(const double* __restrict__ A, long long col_stride, long long rhs_stride_A,
+                       int ncols, const double* __restrict__ c, long long ldc,
+                       double* __restrict__ w, int N, const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double* Ar = A + r * rhs_stride_A;
+    const double* cr = c + r * ldc;
+    double acc = w[(size_t)r * N + i];
+    for (int j = 0; j < ncols; ++j) acc -= Ar[j * col_stride + i] * cr[j];
+    w[(size_t)r * N + i] = acc;
+}
+
+__global__ void k_badd_cols(double* __restrict__ h, long long ldh, const double* __restrict__ h2,
+                            long long ldh2, int n, const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) h[r * ldh + j] += h2[r * ldh2 + j];
+}
+
+// out_r = v_r + y_r + wdot_r  (A v with the rank-one term)
+__global__ void k_bfinishA(const double* __restrict__ v, long long ldv, const double* __restrict__ y,
+                           const double* __restrict__ wdot, long long ldw,
+                           double* __restrict__ out, int N, const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    out[(size_t)r * N + i] = v[r * ldv + i] + y[(size_t)r * N + i] + wdot[r * ldw];
+}
+
+__global__ void k_bscale_copy(const double* __restrict__ src, long long lds,
+                              const double* __restrict__ sc, long long ldsc, int invert,
+                              double* __restrict__ dst, long long ldd, int N,
+                              const int* __restrict__ done) {
+    const int r = blockIdx.y;
+    if (done && done[r]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double s = sc[r * ldsc];
+    const double f = invert ? (s != 0.0 ? 1.0 / s : 0.0) : s;
+    dst[r * ldd + i] = src[r * lds + i] * f;
+}
+
+// scal layout per rhs: [0] w.v  [1] norm^2  [2] 1/|w|  [3] beta  [4] tol_abs
+__global__ void k_bcycle_start(int nrhs, const double* __restrict__ nrm2, long long ldn,
+                               double* __restrict__ g, int m, double* __restrict__ scal,
+                               int* __restrict__ done, int* __restrict__ iters,
+                               int* __restrict__ all_done) {
+    __shared__ int any_active;
+    if (threadIdx.x == 0) any_active = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+        const double beta = sqrt(nrm2[r * ldn]);
+        double* gr = g + (size_t)r * (m + 1);
+        for (int k = 0; k <= m; ++k) gr[k] = 0.0;
+        gr[0] = beta;
+        scal[r * 8 + 3] = beta;
+        iters[r] = 0;
+        const int d = (beta <= scal[r * 8 + 4] || beta == 0.0) ? 1 : 0;
+        done[r] = d;
+        if (!d) atomicOr(&any_active, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *all_done = any_active ? 0 : 1;
+}
+
+__global__ void k_brotate(int nrhs, double* __restrict__ H, int ldh, int m, int k,
+                          double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                          double* __restrict__ scal, int* __restrict__ done,
+                          int* __restrict__ iters, int* __restrict__ all_done) {
+    __shared__ int any_active;
+    if (threadIdx.x == 0) any_active = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+        if (done[r]) continue;
+        double* h = H + ((size_t)r * m + k) * ldh;
+        double* csr = cs + (size_t)r * m;
+        double* snr = sn + (size_t)r * m;
+        double* gr = g + (size_t)r * (m + 1);
+        const double hn = sqrt(scal[r * 8 + 1]);
+        h[k + 1] = hn;
+        scal[r * 8 + 2] = (hn > 0.0) ? 1.0 / hn : 0.0;
+        for (int j = 0; j < k; ++j) {
+            const double t = csr[j] * h[j] + snr[j] * h[j + 1];
+            h[j + 1] = -snr[j] * h[j] + csr[j] * h[j + 1];
+            h[j] = t;
+        }
+        const double a = h[k], b = h[k + 1];
+        const double den = hypot(a, b);
+        const double c = (den > 0.0) ? a / den : 1.0, s_ = (den > 0.0) ? b / den : 0.0;
+        csr[k] = c;
+        snr[k] = s_;
+        h[k] = den;
+        h[k + 1] = 0.0;
+        gr[k + 1] = -s_ * gr[k];
+        gr[k] = c * gr[k];
+        iters[r] = k + 1;
+        const int d = (fabs(gr[k + 1]) <= scal[r * 8 + 4] || hn <= 1e-300 || !(hn == hn)) ? 1 : 0;
+        done[r] = d;
+        if (!d) atomicOr(&any_active, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *all_done = any_active ? 0 : 1;
+}
+
+__global__ void k_bbacksolve(int nrhs, const double* __restrict__ H, int ldh, int m,
+                             const double* __restrict__ g, const int* __restrict__ iters,
+                             double* __restrict__ y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    const int n = iters[r];
+    const double* Hr = H + (size_t)r * m * ldh;
+    const double* gr = g + (size_t)r * (m + 1);
+    double* yr = y + (size_t)r * m;
+    for (int i = n - 1; i >= 0; --i) {
+        double t = gr[i];
+        for (int j = i + 1; j < n; ++j) t -= Hr[(size_t)j * ldh + i] * yr[j];
+        const double d = Hr[(size_t)i * ldh + i];
+        yr[i] = (d != 0.0) ? t / d : 0.0;
+    }
+}
+
+__global__ void k_badd_combo(const double* __restrict__ V, long long col_stride,
+                             long long rhs_stride, const int* __restrict__ iters,
+                             const double* __restrict__ y, int m, double* __restrict__ x, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = iters[r];
+    const double* Vr = V + r * rhs_stride;
+    double acc = x[(size_t)r * N + i];
+    for (int j = 0; j < n; ++j) acc += Vr[j * col_stride + i] * y[(size_t)r * m + j];
+    x[(size_t)r * N + i] = acc;
+}
+
+__global__ void k_bresidual(const double* __restrict__ b, const double* __restrict__ Ax,
+                            double* __restrict__ out, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[(size_t)r * N + i] = b[(size_t)r * N + i] - Ax[(size_t)r * N + i];
+}
+
+__global__ void k_baxpy(double* __restrict__ y, const double* __restrict__ x, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[(size_t)r * N + i] += x[(size_t)r * N + i];
+}
+
+__global__ void k_bshift(double* __restrict__ y, const double* __restrict__ shift, long long lds,
+                         double sgn, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[(size_t)r * N + i] += sgn * shift[r * lds];
+}
+
+__global__ void k_bmul(const double* __restrict__ w, const double* __restrict__ f,
+                       double* __restrict__ out, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[(size_t)r * N + i] = w[i] * f[(size_t)r * N + i];
+}
+
+}  // namespace
+
+struct PmBatchSolveWork {
+    int nrhs = 0, m = 0, N = 0, nred = 0;
+    double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
+    double *part = nullptr, *scal = nullptr, *hcol = nullptr, *dots = nullptr;
+    double *w = nullptr, *tmp = nullptr, *r = nullptr, *res = nullptr, *delta = nullptr;
+    double *sig = nullptr, *f = nullptr, *u = nullptr;
+    int *done = nullptr, *iters = nullptr, *all_done = nullptr;
+    double* pinned = nullptr;
+    int* pinned_i = nullptr;
+};
+
+void pm_batch_solve_free(pm_surface* s) {
+    if (!s->bsolve) return;
+    PmBatchSolveWork& W = *s->bsolve;
+    pm_dfree(W.V); pm_dfree(W.H); pm_dfree(W.cs); pm_dfree(W.sn); pm_dfree(W.g); pm_dfree(W.y);
+    pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.dots); pm_dfree(W.w);
+    pm_dfree(W.tmp); pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig);
+    pm_dfree(W.f); pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.all_done);
+    if (W.pinned) cudaFreeHost(W.pinned);
+    if (W.pinned_i) cudaFreeHost(W.pinned_i);
+    delete s->bsolve;
+    s->bsolve = nullptr;
+}
+
+static pm_status bsolve_work(pm_surface* s, int nrhs, PmBatchSolveWork** out) {
+    const int m = std::max(2, std::min(s->opts.gmres_restart, 400));
+    if (s->bsolve && s->bsolve->nrhs >= nrhs && s->bsolve->m == m) {
+        *out = s->bsolve;
+        return PM_OK;
+    }
+    pm_batch_solve_free(s);
+    s->bsolve = new PmBatchSolveWork();
+    PmBatchSolveWork& W = *s->bsolve;
+    const int N = s->N;
+    W.nrhs = nrhs;
+    W.m = m;
+    W.N = N;
+    W.nred = std::max(1, std::min(pm_ceil_div(N, 2048), 64));
+    const size_t RN = (size_t)nrhs * N;
+    PM_TRY(pm_dmalloc(&W.V, (size_t)nrhs * (m + 1) * N));
+    PM_TRY(pm_dmalloc(&W.H, (size_t)nrhs * m * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.cs, (size_t)nrhs * m));
+    PM_TRY(pm_dmalloc(&W.sn, (size_t)nrhs * m));
+    PM_TRY(pm_dmalloc(&W.g, (size_t)nrhs * (m + 1)));
+    PM_TRY(pm_dmalloc(&W.y, (size_t)nrhs * m));
+    PM_TRY(pm_dmalloc(&W.part, (size_t)nrhs * W.nred * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.scal, (size_t)nrhs * 8));
+    PM_TRY(pm_dmalloc(&W.hcol, (size_t)nrhs * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.dots, (size_t)nrhs * 8));
+    PM_TRY(pm_dmalloc(&W.w, RN));
+    PM_TRY(pm_dmalloc(&W.tmp, RN));
+    PM_TRY(pm_dmalloc(&W.r, RN));
+    PM_TRY(pm_dmalloc(&W.res, RN));
+    PM_TRY(pm_dmalloc(&W.delta, RN));
+    PM_TRY(pm_dmalloc(&W.sig, RN));
+    PM_TRY(pm_dmalloc(&W.f, RN));
+    PM_TRY(pm_dmalloc(&W.u, RN));
+    PM_TRY(pm_dmalloc(&W.done, nrhs));
+    PM_TRY(pm_dmalloc(&W.iters, nrhs));
+    PM_TRY(pm_dmalloc(&W.all_done, 1));
+    PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, sizeof(double) * 8 * (size_t)nrhs));
+    PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_i, sizeof(int) * (2 * (size_t)nrhs + 4)));
+    *out = &W;
+    return PM_OK;
+}
+
+namespace {
+
+struct BSolver {
+    pm_surface* s;
+    PmBatchSolveWork& W;
+    int nrhs;
+    cudaStream_t st;
+    int grid_n;
+
+    pm_precision residual_prec() const {
+        return s->opts.residual_prec == PM_PREC_FP64 ? PM_PREC_FP64 : PM_PREC_FF;
+    }
+
+    // dst[r*lddst + j] = A_r,j . b_r for j < ncols
+    void dots(const double* A, long long col_stride, long long rhs_stride_A, int ncols,
+              const double* b, long long rhs_stride_b, double* dst, long long lddst,
+              const int* done) {
+        k_bdots<<<dim3(W.nred, nrhs), kRed, 0, st>>>(A, col_stride, rhs_stride_A, ncols, b,
+                                                      rhs_stride_b, W.N, W.part, done);
+        k_breduce<<<dim3(pm_ceil_div(ncols, 64), nrhs), 64, 0, st>>>(W.part, W.nred, ncols, dst,
+                                                                       lddst, done);
+        s->launch_total += 2;
+    }
+
+    // out_r = A v_r (I + R~ + 1 w^T) for all r
+    pm_status apply_A(const double* v, long long ldv, double* out, pm_precision prec,
+                      const int* done) {
+        if (prec == PM_PREC_FP64) {
+            for (int r = 0; r < nrhs; ++r)
+                PM_TRY(pm_apply_dev(s, 0, 1, 1, v + r * ldv, W.tmp + (size_t)r * W.N, prec, st));
+        } else {
+            PM_TRY(pm_apply_batch(s, 0, v, ldv, W.tmp, W.N, nrhs, prec, st));
+        }
+        dots(s->w, 0, 0, 1, v, ldv, W.dots + 0, 8, done);
+        k_bfinishA<<<dim3(grid_n, nrhs), 256, 0, st>>>(v, ldv, W.tmp, W.dots + 0, 8, out, W.N, done);
+        s->launch_total += 1;
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+
+    pm_status norms(const double* v, double* host) {   // host[r] = ||v_r||_2
+        dots(v, 0, W.N, 1, v, W.N, W.dots + 1, 8, nullptr);
+        PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.dots, sizeof(double) * 8 * nrhs,
+                                    cudaMemcpyDeviceToHost, st));
+        PM_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int r = 0; r < nrhs; ++r) host[r] = std::sqrt(W.pinned[8 * r + 1]);
+        return PM_OK;
+    }
+
+    // lockstep restarted GMRES on A d_r = b_r from d = 0 (operator in prec); x += d.
+    pm_status gmres(const double* b, double* x, pm_precision prec, const std::vector<double>& tol_abs,
+                    int max_iter, int* iters_used) {
+        const int m = W.m, N = W.N;
+        const long long ldV = (long long)(m + 1) * N;
+        const int ldh = m + 2;
+        PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * nrhs * N, cudaMemcpyDeviceToDevice, st));
+        PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * nrhs * N, st));
+        for (int r = 0; r < nrhs; ++r) W.pinned[8 * r + 4] = tol_abs[r];
+        // tolerance into scal[r][4]
+        for (int r = 0; r < nrhs; ++r)
+            PM_CUDA_TRY(cudaMemcpyAsync(W.scal + 8 * r + 4, W.pinned + 8 * r + 4, sizeof(double),
+                                        cudaMemcpyHostToDevice, st));
+        int total = 0;
+        while (total < max_iter) {
+            dots(W.r, 0, N, 1, W.r, N, W.scal + 1, 8, nullptr);
+            k_bcycle_start<<<1, 256, 0, st>>>(nrhs, W.scal + 1, 8, W.g, m, W.scal, W.done, W.iters,
+                                              W.all_done);
+            k_bscale_copy<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.r, N, W.scal + 3, 8, 1, W.V, ldV, N,
+                                                              W.done);
+            s->launch_total += 2;
+            const int steps = std::min(m, max_iter - total);
+            s->skip_flag = W.all_done;
+            const int chunk = (steps <= 8) ? steps : 4;
+            for (int k = 0; k < steps; ++k) {
+                if (k > 0 && k % chunk == 0) {
+                    PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.all_done, sizeof(int),
+                                                cudaMemcpyDeviceToHost, st));
+                    PM_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (W.pinned_i[0]) break;
+                }
+                double* vk = W.V + (size_t)k * N;         // column k of rhs 0; rhs stride ldV
+                double* vk1 = W.V + (size_t)(k + 1) * N;
+                double* hk = W.H + (size_t)k * ldh;         // rhs stride m*ldh
+                pm_status stt = apply_A(vk, ldV, W.w, prec, W.done);
+                if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
+                dots(W.V, N, ldV, k + 1, W.w, N, hk, (long long)m * ldh, W.done);
+                k_bsub<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.V, N, ldV, k + 1, hk, (long long)m * ldh,
+                                                           W.w, N, W.done);
+                dots(W.V, N, ldV, k + 1, W.w, N, W.hcol, m + 2, W.done);
+                k_bsub<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.V, N, ldV, k + 1, W.hcol, m + 2, W.w, N,
+                                                           W.done);
+                k_badd_cols<<<dim3(pm_ceil_div(k + 1, 64), nrhs), 64, 0, st>>>(
+                    hk, (long long)m * ldh, W.hcol, m + 2, k + 1, W.done);
+                dots(W.w, 0, N, 1, W.w, N, W.scal + 1, 8, W.done);
+                k_brotate<<<1, 256, 0, st>>>(nrhs, W.H, ldh, m, k, W.cs, W.sn, W.g, W.scal, W.done,
+                                             W.iters, W.all_done);
+                k_bscale_copy<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.w, N, W.scal + 2, 8, 0, vk1, ldV,
+                                                                  N, W.done);
+                s->launch_total += 5;
+            }
+            s->skip_flag = nullptr;
+            k_bbacksolve<<<pm_ceil_div(nrhs, 64), 64, 0, st>>>(nrhs, W.H, ldh, m, W.g, W.iters, W.y);
+            k_badd_combo<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.V, N, ldV, W.iters, W.y, m, W.delta, N);
+            s->launch_total += 2;
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int) * nrhs,
+                                        cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + nrhs, W.done, sizeof(int) * nrhs,
+                                        cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaStreamSynchronize(st));
+            int it = 0, all = 1;
+            for (int r = 0; r < nrhs; ++r) {
+                it = std::max(it, W.pinned_i[r]);
+                all &= W.pinned_i[nrhs + r];
+            }
+            total += it;
+            if (all || it == 0) break;
+            PM_TRY(apply_A(W.delta, N, W.w, prec, nullptr));
+            k_bresidual<<<dim3(grid_n, nrhs), 256, 0, st>>>(b, W.w, W.r, N);
+            s->launch_total += 1;
+        }
+        k_baxpy<<<dim3(grid_n, nrhs), 256, 0, st>>>(x, W.delta, N);
+        s->launch_total += 1;
+        PM_CUDA_TRY(cudaGetLastError());
+        *iters_used = total;
+        return PM_OK;
+    }
+
+    pm_status true_residual(const double* f, const double* sig, double* res) {
+        PM_TRY(apply_A(sig, W.N, W.w, residual_prec(), nullptr));
+        k_bresidual<<<dim3(grid_n, nrhs), 256, 0, st>>>(f, W.w, res, W.N);
+        s->launch_total += 1;
+        return PM_OK;
+    }
+};
+
+}  // namespace
+
+// Batched solve of nrhs right-hand sides (same surface and coefficient), in lockstep.
+pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, double tol,
+                         int maxit, pm_precision prec, unsigned flags, double* sigma_out,
+                         pm_solve_info* info, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    PmBatchSolveWork* Wp = nullptr;
+    PM_TRY(bsolve_work(s, nrhs, &Wp));
+    PmBatchSolveWork& W = *Wp;
+    const int N = s->N;
+    BSolver S{s, W, nrhs, st, pm_ceil_div(N, 256)};
+    const bool dev = (flags & PM_SOLVE_DEVICE_PTRS) != 0;
+    PM_CUDA_TRY(cudaMemcpyAsync(W.f, f, sizeof(double) * (size_t)nrhs * N,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    double sw = 0.0;
+    for (double v : s->h_w) sw += v;
+    // weighted means and norms of every f_r (Thm. LBsolvable)
+    k_bmul<<<dim3(S.grid_n, nrhs), 256, 0, st>>>(s->w, W.f, W.tmp, N);
+    S.dots(W.tmp, 0, N, 1, W.f, N, W.dots + 5, 8, nullptr);      // sum w f^2
+    S.dots(s->w, 0, 0, 1, W.f, N, W.dots + 4, 8, nullptr);       // sum w f
+    PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.dots, sizeof(double) * 8 * nrhs,
+                                cudaMemcpyDeviceToHost, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> removed(nrhs, 0.0), fnorm(nrhs, 0.0);
+    for (int r = 0; r < nrhs; ++r) {
+        const double wf = W.pinned[8 * r + 4], wff = W.pinned[8 * r + 5];
+        if (wff > 0.0 && std::fabs(wf) > s->opts.mean_tol * std::sqrt(sw * wff) &&
+            !(flags & PM_SOLVE_PROJECT_RHS)) {
+            pm_set_error("pm_solve: right-hand side %d has weighted mean %.3e; pass "
+                         "PM_SOLVE_PROJECT_RHS to subtract it", r, wf / sw);
+            return PM_ERR_RHS_NOT_MEAN_ZERO;
+        }
+        if (flags & PM_SOLVE_PROJECT_RHS) removed[r] = wf / sw;
+    }
+    if (flags & PM_SOLVE_PROJECT_RHS) {
+        k_bshift<<<dim3(S.grid_n, nrhs), 256, 0, st>>>(W.f, W.dots + 4, 8, -1.0 / sw, N);
+        s->launch_total += 1;
+    }
+    PM_TRY(S.norms(W.f, fnorm.data()));
+    PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * (size_t)nrhs * N, st));
+    int iters = 0, refinements = 0;
+    std::vector<double> relres(nrhs, 0.0);
+    const bool accurate_inner = (prec == PM_PREC_FP64 || prec == PM_PREC_FF);
+    std::vector<double> tabs(nrhs);
+    for (;;) {
+        std::vector<double> rn(nrhs);
+        if (refinements == 0) {
+            PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * (size_t)nrhs * N,
+                                        cudaMemcpyDeviceToDevice, st));
+            rn = fnorm;
+        } else {
+            PM_TRY(S.true_residual(W.f, W.sig, W.res));
+            PM_TRY(S.norms(W.res, rn.data()));
+        }
+        bool all_ok = true;
+        for (int r = 0; r < nrhs; ++r) {
+            relres[r] = fnorm[r] > 0 ? rn[r] / fnorm[r] : 0.0;
+            all_ok &= relres[r] <= tol;
+        }
+        if (all_ok || refinements >= (accurate_inner ? 2 : s->opts.max_refine) || iters >= maxit)
+            break;
+        for (int r = 0; r < nrhs; ++r) {
+            const double inner = accurate_inner ? 0.5 * tol * fnorm[r] / std::max(rn[r], 1e-300)
+                                                : std::max(s->opts.inner_tol,
+                                                           0.5 * tol * fnorm[r] / std::max(rn[r], 1e-300));
+            tabs[r] = (relres[r] <= tol) ? 1e300 : inner * rn[r];
+        }
+        int it = 0;
+        PM_TRY(S.gmres(W.res, W.sig, prec, tabs, maxit - iters, &it));
+        iters += it;
+        ++refinements;
+        if (it == 0) break;
+    }
+    pm_status result = PM_OK;
+    for (int r = 0; r < nrhs; ++r)
+        if (!(relres[r] <= tol)) {
+            pm_set_error("pm_solve: right-hand side %d: relative residual %.3e above %.3e", r,
+                         relres[r], tol);
+            result = PM_ERR_NOT_CONVERGED;
+        }
+    // u = K~ sigma (accurate), minus its weighted mean
+    if (S.residual_prec() == PM_PREC_FP64) {
+        for (int r = 0; r < nrhs; ++r)
+            PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig + (size_t)r * N, W.u + (size_t)r * N, PM_PREC_FP64, st));
+    } else {
+        PM_TRY(pm_apply_batch(s, 1, W.sig, N, W.u, N, nrhs, PM_PREC_FF, st));
+    }
+    S.dots(s->w, 0, 0, 1, W.u, N, W.dots + 6, 8, nullptr);
+    k_bshift<<<dim3(S.grid_n, nrhs), 256, 0, st>>>(W.u, W.dots + 6, 8, -1.0 / sw, N);
+    s->launch_total += 1;
+    const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    PM_CUDA_TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * (size_t)nrhs * N, d2h, st));
+    if (sigma_out)
+        PM_CUDA_TRY(cudaMemcpyAsync(sigma_out, W.sig, sizeof(double) * (size_t)nrhs * N, d2h, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int r = 0; r < nrhs; ++r) {
+            info[r].iterations = iters;
+            info[r].refinements = refinements;
+            info[r].residual = relres[r];
+            info[r].removed_mean = removed[r];
+            info[r].seconds = secs;
+        }
+    return result;
+}

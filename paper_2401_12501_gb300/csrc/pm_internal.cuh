@@ -70,6 +70,8 @@ struct pm_ctx {
 
 struct PmSolveWork;
 struct PmFmmTree;
+struct PmBatchWork;
+struct PmBatchSolveWork;
 
 struct pm_surface {
     pm_ctx* ctx = nullptr;
@@ -134,6 +136,8 @@ struct pm_surface {
     // kernels of a finished Krylov cycle return at once
     PmSolveWork* solve_work = nullptr;
     PmFmmTree* fmm = nullptr;
+    PmBatchWork* batch = nullptr;
+    PmBatchSolveWork* bsolve = nullptr;
     double fmm_stats[4] = {0, 0, 0, 0};
     const int* skip_flag = nullptr;
 
@@ -180,6 +184,16 @@ pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st);
 pm_status pm_fmm_build(pm_surface* s);
 pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st);
 void pm_fmm_free(pm_surface* s);
+
+// batched applies and solves (pm_batch.cu)
+pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long long ld_sigma,
+                         double* out, long long ld_out, int nrhs, pm_precision prec,
+                         cudaStream_t st);
+pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, double tol,
+                         int maxit, pm_precision prec, unsigned flags, double* sigma_out,
+                         pm_solve_info* info, cudaStream_t st);
+void pm_batch_free(pm_surface* s);
+void pm_batch_solve_free(pm_surface* s);
 
 // solve (pm_solve.cu)
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,

@@ -12,6 +12,7 @@ from .surfaces import (  # noqa: F401
     Surface,
     cubed_sphere,
     torus,
+    star_surface,
     gauss_legendre,
 )
 from .coefficients import (  # noqa: F401
@@ -31,5 +32,6 @@ from .rhs import (  # noqa: F401
 from .configs import (  # noqa: F401
     Workload,
     make_workload,
+    star_batch,
     WORKLOADS,
 )

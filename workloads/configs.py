@@ -22,9 +22,9 @@ from dataclasses import dataclass
 import numpy as np
 
 from .coefficients import (Coefficient, constant_coefficient, ellipsoid_coefficient,
-                           torus_coefficient)
+                           smooth_random_coefficient, torus_coefficient)
 from .rhs import random_harmonic_rhs, sphere_harmonic_rhs, torus_rhs
-from .surfaces import Surface, cubed_sphere, torus
+from .surfaces import Surface, cubed_sphere, star_surface, torus
 
 
 @dataclass
@@ -48,6 +48,17 @@ def _sphere(m, p):
 def _ellipsoid(m, p, seed=0):
     s = cubed_sphere(m, p, axes=(1.0, 1.5, 2.0))
     return s, ellipsoid_coefficient(s), random_harmonic_rhs(s, seed)
+
+
+def star_batch(m: int = 8, p: int = 8, n_rhs: int = 64, n_coeff: int = 8):
+    """Batched workload: the star-shaped surface with n_coeff smooth random
+    coefficient fields a = 1 + 0.4 tanh(g) (seeds 0..n_coeff-1) and n_rhs
+    right-hand sides, each a mean-zero N(0,1) combination of all real Y_l^m with
+    1 <= l <= 12 (seeds 0..n_rhs-1)."""
+    s = star_surface(m, p)
+    coeffs = [smooth_random_coefficient(s, seed) for seed in range(n_coeff)]
+    fs = np.stack([random_harmonic_rhs(s, seed, n_terms=168, lmax=12) for seed in range(n_rhs)])
+    return s, coeffs, fs
 
 
 def _torus(nt, nph, p):
@@ -75,6 +86,15 @@ WORKLOADS = {
                     "torus R=2 r=0.7, 16x6 patches, 6x6 nodes (3,456)"),
     "torus_6144": (lambda: _torus(16, 6, 8),
                    "torus R=2 r=0.7, 16x6 patches, 8x8 nodes (6,144)"),
+    "star_24576": (lambda: (lambda s: (s, smooth_random_coefficient(s, 0),
+                                       random_harmonic_rhs(s, 0, n_terms=168, lmax=12)))(
+                       star_surface(8, 8)),
+                   "star rho=1+0.3 sin(3 theta) cos(2 phi), 6x8x8 patches, 8x8 nodes (24,576), "
+                   "a=1+0.4 tanh(g) seed 0, f=mean-zero N(0,1) combination of Y_l^m, l<=12"),
+    "star_small": (lambda: (lambda s: (s, smooth_random_coefficient(s, 0),
+                                       random_harmonic_rhs(s, 0, n_terms=168, lmax=12)))(
+                       star_surface(2, 6)),
+                   "star, 6x2x2 patches, 6x6 nodes (864)"),
 }
 
 

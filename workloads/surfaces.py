@@ -197,3 +197,69 @@ def torus(n_theta: int, n_phi: int, p: int, R: float = 2.0, r: float = 0.7) -> S
         curvature=H.reshape(N), weights=w.reshape(N), gauss_curvature=kg.reshape(N),
         params={"theta": th.reshape(N), "phi": ph.reshape(N), "R": R, "r": r},
         area=4 * np.pi ** 2 * R * r, volume=2 * np.pi ** 2 * R * r * r, genus=1)
+
+
+def star_surface(m: int, p: int, amp: float = 0.3) -> Surface:
+    """Star-shaped surface x = rho(theta, phi) e_r over the cubed-sphere directions.
+
+    rho = 1 + amp sin(3 theta) cos(2 phi), theta the polar angle and phi the
+    azimuth of the direction.  Taken literally, rho is Lipschitz but not
+    differentiable at the two poles (sin 3 theta ~ 3 theta there); the poles sit
+    at patch corners of the cubed sphere, so no node lies on them.  Positions,
+    tangents (chain rule through the cubed-sphere map), the normal and the mean
+    curvature come from closed-form first and second derivatives in (theta, phi).
+    """
+    ys, dys_du, dys_dv, face, xi, eta = _cubed_sphere_directions(m, p)
+    P = ys.shape[0]
+    d = ys.reshape(-1, 3)
+    du = dys_du.reshape(-1, 3)
+    dv = dys_dv.reshape(-1, 3)
+    th = np.arccos(np.clip(d[:, 2], -1.0, 1.0))
+    ph = np.arctan2(d[:, 1], d[:, 0])
+    st, ct, sp, cp = np.sin(th), np.cos(th), np.sin(ph), np.cos(ph)
+    rho = 1 + amp * np.sin(3 * th) * np.cos(2 * ph)
+    r_t = 3 * amp * np.cos(3 * th) * np.cos(2 * ph)
+    r_p = -2 * amp * np.sin(3 * th) * np.sin(2 * ph)
+    r_tt = -9 * amp * np.sin(3 * th) * np.cos(2 * ph)
+    r_tp = -6 * amp * np.cos(3 * th) * np.sin(2 * ph)
+    r_pp = -4 * amp * np.sin(3 * th) * np.cos(2 * ph)
+    er = np.stack([st * cp, st * sp, ct], -1)
+    et = np.stack([ct * cp, ct * sp, -st], -1)
+    ep = np.stack([-sp, cp, np.zeros_like(ph)], -1)
+    # parametrisation in (theta, phi)
+    X = rho[:, None] * er
+    X_t = r_t[:, None] * er + rho[:, None] * et
+    X_p = r_p[:, None] * er + (rho * st)[:, None] * ep
+    # second derivatives (d er/dt = et, d er/dp = st ep, d et/dt = -er, d et/dp = ct ep,
+    # d ep/dp = -(st er + ct et))
+    X_tt = r_tt[:, None] * er + 2 * r_t[:, None] * et - rho[:, None] * er
+    X_tp = (r_tp[:, None] * er + r_t[:, None] * st[:, None] * ep + r_p[:, None] * et
+            + (rho * ct)[:, None] * ep)
+    X_pp = (r_pp[:, None] * er + 2 * (r_p * st)[:, None] * ep
+            - (rho * st)[:, None] * (st[:, None] * er + ct[:, None] * et))
+    nrm = np.cross(X_t, X_p)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    out = np.sum(nrm * er, 1) < 0
+    nrm[out] *= -1.0
+    E, F, G = np.sum(X_t * X_t, 1), np.sum(X_t * X_p, 1), np.sum(X_p * X_p, 1)
+    e, f, g = np.sum(X_tt * nrm, 1), np.sum(X_tp * nrm, 1), np.sum(X_pp * nrm, 1)
+    H = -(e * G - 2 * f * F + g * E) / (2 * (E * G - F * F))
+    KG = (e * g - f * f) / (E * G - F * F)
+    # tangents with respect to the patch coordinates: chain rule through theta(d), phi(d)
+    th_u = -du[:, 2] / st
+    th_v = -dv[:, 2] / st
+    rxy2 = d[:, 0] ** 2 + d[:, 1] ** 2
+    ph_u = (d[:, 0] * du[:, 1] - d[:, 1] * du[:, 0]) / rxy2
+    ph_v = (d[:, 0] * dv[:, 1] - d[:, 1] * dv[:, 0]) / rxy2
+    yu = X_t * th_u[:, None] + X_p * ph_u[:, None]
+    yv = X_t * th_v[:, None] + X_p * ph_v[:, None]
+    # orient normals like y_u x y_v (outward on the cubed sphere)
+    _, wt = gauss_legendre(p)
+    jac = np.linalg.norm(np.cross(yu, yv), axis=1)
+    w = (wt[:, None] * wt[None, :]).ravel()
+    w = np.tile(w, P) * jac
+    N = P * p * p
+    return Surface(kind="star", npatch=P, p=p, nodes=X, normals=nrm,
+                   tangents=np.concatenate([yu, yv], -1), curvature=H, weights=w,
+                   gauss_curvature=KG, params={"theta": th, "phi": ph, "amp": amp},
+                   area=None, volume=None, genus=0)
