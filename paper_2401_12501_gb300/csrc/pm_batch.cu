@@ -22,8 +22,8 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kRB = 8;          // right-hand sides per block (float32)
-constexpr int kRBff = 4;        // right-hand sides per block (float-float)
+constexpr int kRB = 16;         // right-hand sides per block (float32)
+constexpr int kRBff = 16;       // right-hand sides per block (float-float)
 constexpr int kTile = 256;
 constexpr int kStage = 512;
 
@@ -67,7 +67,7 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
                  float2* __restrict__ partial, int nsplit, const int* __restrict__ skip) {
     if (skip && *skip) return;
     __shared__ float4 sP[kStage];
-    __shared__ float sS[kRB][kStage];
+    __shared__ float4 sS[kStage][kRB / 4];      // strengths of kRB right-hand sides per source
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kThreads + tid;
     const int r0 = blockIdx.z * kRB;
@@ -93,9 +93,12 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
         __syncthreads();
         for (int j = tid; j < len; j += kThreads) {
             sP[j] = pos[base + j];
+            float v[kRB];
 #pragma unroll
-            for (int q = 0; q < kRB; ++q)
-                sS[q][j] = (q < nr) ? s[(size_t)(r0 + q) * N + base + j] : 0.f;
+            for (int q = 0; q < kRB; ++q) v[q] = (q < nr) ? s[(size_t)(r0 + q) * N + base + j] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kRB / 4; ++q)
+                sS[j][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncthreads();
         for (int j0 = 0; j0 < len; j0 += kTile) {
@@ -120,7 +123,13 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
                     gfac = inv * fmaf(nr2, nr2 * inv, mr);
                 }
 #pragma unroll
-                for (int q = 0; q < kRB; ++q) part[q] = fmaf(sS[q][j], gfac, part[q]);
+                for (int q = 0; q < kRB / 4; ++q) {
+                    const float4 sv = sS[j][q];
+                    part[4 * q] = fmaf(sv.x, gfac, part[4 * q]);
+                    part[4 * q + 1] = fmaf(sv.y, gfac, part[4 * q + 1]);
+                    part[4 * q + 2] = fmaf(sv.z, gfac, part[4 * q + 2]);
+                    part[4 * q + 3] = fmaf(sv.w, gfac, part[4 * q + 3]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < kRB; ++q) two_sum_acc(hi[q], lo[q], part[q]);
@@ -328,8 +337,17 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
             }
 #pragma unroll
             for (int q = 0; q < kRBff; ++q) {
+                // s * g in float-float (product and its error), then a lazy
+                // float-float accumulation: TwoSum on the high parts, all error
+                // terms summed in the low part (renormalised at the end)
                 const float2 sv = sS[q][j];
-                acc[q] = ff_add(acc[q], ff_mul(ff{sv.x, sv.y}, gfac));
+                const float p = sv.x * gfac.h;
+                float e = fmaf(sv.x, gfac.h, -p);
+                e = fmaf(sv.x, gfac.l, fmaf(sv.y, gfac.h, e));
+                const float t = acc[q].h + p;
+                const float bp = t - acc[q].h;
+                acc[q].l += ((acc[q].h - (t - bp)) + (p - bp)) + e;
+                acc[q].h = t;
             }
         }
     }
@@ -337,7 +355,8 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
 #pragma unroll
         for (int q = 0; q < kRBff; ++q) {
             if (q >= nr) continue;
-            ff v = acc[q];
+            ff v;
+            fast_two_sum(acc[q].h, acc[q].l, v.h, v.l);
             if (KERNEL_K) v = ff_mul(v, ff{(float)(1.0 / (4.0 * M_PI)),
                                            (float)(1.0 / (4.0 * M_PI) - (double)(float)(1.0 / (4.0 * M_PI)))});
             partial[((size_t)(r0 + q) * nsplit + blockIdx.y) * N + i] = make_float2(v.h, v.l);
