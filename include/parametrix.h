@@ -34,6 +34,8 @@
 #ifndef PARAMETRIX_H
 #define PARAMETRIX_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -243,6 +245,39 @@ pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, i
  */
 pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int n,
                             double* out);
+
+/*
+ * Serving: continuous batching of solve requests over many operators.
+ *
+ * An operator is a pm_surface whose coefficient is set.  pm_server_create starts
+ * n_workers threads, each with its own CUDA stream.  A worker takes the operator
+ * whose oldest waiting request arrived first among the operators no other worker
+ * is serving, admits up to max_batch of that operator's waiting requests (in
+ * arrival order) while their device footprint fits the budget, and solves them
+ * together (batched applies, lockstep GMRES, float-float refinement; see
+ * pm_solve).  Requests arriving meanwhile join later batches, so work on
+ * different operators overlaps on the device.  Footprint per request:
+ * (gmres_restart + 11) * N * 8 bytes.  Operators handed to a server must not be
+ * used by the caller until every request on them has been waited for.
+ *   hbm_budget_bytes  device bytes the server may reserve for admitted requests
+ *   max_batch         right-hand sides per batch (1 = one request at a time)
+ * pm_server_submit copies f (host, [N]) and returns a ticket; PM_ERR_OOM if one
+ * request alone exceeds the budget.  pm_server_wait blocks until the ticket is
+ * done (timeout_ms < 0: no limit; PM_ERR_TIMEOUT otherwise), copies u (host,
+ * [N]) and the solve info, reports the submit-to-finish latency, and releases
+ * the ticket; it returns the solve's status.
+ */
+typedef struct pm_server pm_server;
+pm_status pm_server_create(pm_ctx* ctx, size_t hbm_budget_bytes, int max_batch, int n_workers,
+                           pm_server** out);
+void pm_server_destroy(pm_server* sv);
+pm_status pm_server_submit(pm_server* sv, pm_surface* op, const double* f, double tol,
+                           pm_precision prec, unsigned long long* ticket);
+pm_status pm_server_poll(pm_server* sv, unsigned long long ticket, int* done);
+pm_status pm_server_wait(pm_server* sv, unsigned long long ticket, double* u,
+                         pm_solve_info* info, double* latency_s, int timeout_ms);
+pm_status pm_server_stats(pm_server* sv, long long* batches, long long* solved,
+                          long long* max_batch, size_t* bytes_in_use);
 
 /*
  * Smooth remainder sum without any allocation.

@@ -192,3 +192,58 @@ class Surface:
                                   prec, flags, ptr(sig), infos, st), "pm_solve")
         out = (u, list(infos))
         return out + (sig,) if return_sigma else out
+
+
+class Server:
+    """pm_server: continuous batching of solve requests over many operators."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_batch: int = 64, n_workers: int = 4):
+        h = C.c_void_p()
+        check(_lib.lib().pm_server_create(ctx.handle, int(hbm_budget_bytes), int(max_batch),
+                                          int(n_workers), C.byref(h)), "pm_server_create")
+        self.handle = h
+        self._sizes = {}
+
+    def submit(self, op: Surface, f, tol=1e-8, prec="fp32"):
+        f = _f64(f, op.N)
+        t = C.c_ulonglong()
+        prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        check(_lib.lib().pm_server_submit(self.handle, op.handle, ptr(f), float(tol), prec,
+                                          C.byref(t)), "pm_server_submit")
+        self._sizes[t.value] = op.N
+        return t.value
+
+    def poll(self, ticket):
+        d = C.c_int()
+        check(_lib.lib().pm_server_poll(self.handle, C.c_ulonglong(ticket), C.byref(d)),
+              "pm_server_poll")
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(u, info, latency_seconds) of a finished request."""
+        u = np.empty(self._sizes.pop(ticket))
+        info = PmSolveInfo()
+        lat = C.c_double()
+        check(_lib.lib().pm_server_wait(self.handle, C.c_ulonglong(ticket), ptr(u),
+                                        C.byref(info), C.byref(lat), int(timeout_ms)),
+              "pm_server_wait")
+        return u, info, lat.value
+
+    def stats(self):
+        b, s, m = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        used = C.c_size_t()
+        check(_lib.lib().pm_server_stats(self.handle, C.byref(b), C.byref(s), C.byref(m),
+                                         C.byref(used)), "pm_server_stats")
+        return {"batches": b.value, "solved": s.value, "max_batch": m.value,
+                "bytes_in_use": used.value}
+
+    def close(self):
+        if self.handle:
+            _lib.lib().pm_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

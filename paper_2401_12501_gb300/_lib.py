@@ -33,7 +33,8 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_apply_K", "pm_apply_part", "pm_surface_get_near", "pm_solve",
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
            "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
-           "pm_surface_fmm_stats"]
+           "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
+           "pm_server_poll", "pm_server_wait", "pm_server_stats"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -78,6 +79,15 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
     lib.pm_surface_fmm_stats.argtypes = [P, P]
+    lib.pm_server_create.argtypes = [P, C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]
+    lib.pm_server_destroy.argtypes = [P]
+    lib.pm_server_destroy.restype = None
+    lib.pm_server_submit.argtypes = [P, P, P, C.c_double, C.c_int, C.POINTER(C.c_ulonglong)]
+    lib.pm_server_poll.argtypes = [P, C.c_ulonglong, C.POINTER(C.c_int)]
+    lib.pm_server_wait.argtypes = [P, C.c_ulonglong, P, C.POINTER(PmSolveInfo),
+                                   C.POINTER(C.c_double), C.c_int]
+    lib.pm_server_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]
     lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]
     lib.pm_smooth_remainder_f32_noalloc.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
