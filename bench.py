@@ -316,6 +316,182 @@ def run_gpu(args, rank, world, local_rank):
     return line
 
 
+# ----------------------------------------------------------------------------- other configs
+def run_batched(args, dev):
+    """24,576-node star, 64 right-hand sides: batched lockstep solve vs one at a time."""
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import star_batch
+    s_surf, coeffs, F = star_batch(n_rhs=64, n_coeff=1)
+    ctx = pm.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    s = pm.Surface.from_fixture(ctx, s_surf)
+    t_build = time.perf_counter() - t0
+    s.set_coeff(coeffs[0].a, coeffs[0].grad_a)
+    Fd = torch.from_numpy(F).to(dev)
+    s.solve(Fd[0], tol=args.tol, prec="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_plain = 8
+    for r in range(n_plain):
+        s.solve(Fd[r], tol=args.tol, prec="fp32")
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / n_plain
+    s.solve(Fd, tol=args.tol, prec="fp32")
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        U, info = s.solve(Fd, tol=args.tol, prec="fp32")
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / reps
+    s.close()
+    return {"workload": "star_24576 x 64 rhs (a = 1 + 0.4 tanh(g), seed 0)", "N": s_surf.N,
+            "near_build_s": round(t_build, 3), "tol": args.tol,
+            "plain_solves_per_s": round(1.0 / t_plain, 2),
+            "batched_solves_per_s": round(64 / t_batch, 2),
+            "speedup_vs_plain": round(t_plain * 64 / t_batch, 2),
+            "max_residual": max(i.residual for i in info),
+            "lockstep_arnoldi_steps": info[0].iterations}
+
+
+def run_fmm(args, dev):
+    """98,304-node torus: float32 apply with the Chebyshev FMM vs the direct sum."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import make_workload
+    wl = make_workload("torus_98304")
+    ctx = pm.Context(dev.index or 0)
+    t0 = time.perf_counter()
+    s = pm.Surface.from_fixture(ctx, wl.surface)
+    t_build = time.perf_counter() - t0
+    s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+    st = s.fmm_stats()
+    sig = torch.from_numpy(np.random.default_rng(3).standard_normal(wl.N)).to(dev)
+    out = {}
+    for prec in ("fp32", "fmm", "ff"):
+        y = torch.empty_like(sig)
+        s.apply_R(sig, prec, out=y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            s.apply_R(sig, prec, out=y)
+        torch.cuda.synchronize()
+        out[prec] = ((time.perf_counter() - t0) / reps, y.cpu().numpy())
+    ex = out["ff"][1]
+    res = {"workload": "torus_98304", "N": wl.N, "near_build_s": round(t_build, 3),
+           "fmm_tree": st, "apply_R_ms": {k: round(v[0] * 1e3, 3) for k, v in out.items()},
+           "rel_err_vs_float_float": {k: float(np.linalg.norm(v[1] - ex) / np.linalg.norm(ex))
+                                      for k, v in out.items() if k != "ff"},
+           "direct_gpairs_per_s": round(wl.N ** 2 / out["fp32"][0] / 1e9, 1)}
+    s.close()
+    return res
+
+
+def _snap_surface(family, n_target, rng):
+    from workloads import cubed_sphere, star_surface, torus
+    p = int(rng.choice([8, 10]))
+    if family == "torus":
+        best = None
+        for nph in range(3, 80):
+            nth = max(3, int(round(nph * 8 / 3)))
+            n = nth * nph * p * p
+            if best is None or abs(np.log(n / n_target)) < abs(np.log(best[2] / n_target)):
+                best = (nth, nph, n)
+        return ("torus", p, best[0], best[1]), lambda: torus(best[0], best[1], p)
+    m = max(1, int(round(np.sqrt(n_target / (6 * p * p)))))
+    if family == "sphere":
+        return ("sphere", p, m), lambda: cubed_sphere(m, p)
+    if family == "ellipsoid":
+        return ("ellipsoid", p, m), lambda: cubed_sphere(m, p, axes=(1.0, 1.5, 2.0))
+    return ("star", p, m), lambda: star_surface(m, p)
+
+
+import numpy as np  # noqa: E402  (used by the serving helpers)
+
+
+def run_served(args, dev):
+    """Poisson arrivals of solve requests over a pool of operators; batched server
+    vs a one-request-at-a-time server on the same arrival trace."""
+    import threading as th
+    import paper_2401_12501_gb300 as pm
+    from workloads import random_harmonic_rhs, smooth_random_coefficient
+    rng = np.random.default_rng(0)
+    n_req, rate = args.serve_requests, args.serve_rate
+    fams = ["sphere", "ellipsoid", "torus", "star"]
+    lo, hi = np.log(1500.0), np.log(float(args.serve_nmax))
+    keys, draws = {}, []
+    for _ in range(n_req):
+        fam = fams[int(rng.integers(0, 4))]
+        key, mk = _snap_surface(fam, float(np.exp(rng.uniform(lo, hi))), rng)
+        cseed = int(rng.integers(0, 4))
+        keys.setdefault((key, cseed), mk)
+        draws.append(((key, cseed), int(rng.integers(0, 1 << 30))))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    ctx = pm.Context(dev.index or 0)
+    ops, builds, rhs = {}, [], {}
+    for k, mk in keys.items():
+        surf = mk()
+        co = smooth_random_coefficient(surf, k[1])
+        t0 = time.perf_counter()
+        op = pm.Surface.from_fixture(ctx, surf)
+        op.set_coeff(co.a, co.grad_a)
+        builds.append(time.perf_counter() - t0)
+        ops[k] = (surf, op)
+    for i, (k, fseed) in enumerate(draws):
+        surf = ops[k][0]
+        rhs[i] = random_harmonic_rhs(surf, fseed % 1000, n_terms=20, lmax=12)
+
+    def serve(max_batch, n_workers):
+        sv = pm.Server(ctx, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30),
+                       max_batch=max_batch, n_workers=n_workers)
+        tickets = [None] * n_req
+        t_start = time.perf_counter()
+
+        def client():
+            for i in range(n_req):
+                dt = arrivals[i] - (time.perf_counter() - t_start)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = sv.submit(ops[draws[i][0]][1], rhs[i], tol=args.serve_tol)
+
+        c = th.Thread(target=client)
+        c.start()
+        lat, res = [], []
+        for i in range(n_req):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            u, info, l = sv.wait(tickets[i])
+            lat.append(l)
+            res.append(info.residual)
+        c.join()
+        wall = time.perf_counter() - t_start
+        st = sv.stats()
+        sv.close()
+        lat = np.array(lat)
+        return {"p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+                "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+                "solves_per_s": round(n_req / wall, 2), "wall_s": round(wall, 3),
+                "batches": st["batches"], "max_batch": st["max_batch"],
+                "max_residual": float(max(res))}
+
+    served = serve(max_batch=64, n_workers=4)
+    plain = serve(max_batch=1, n_workers=1)
+    for _, op in ops.values():
+        op.close()
+    sizes = sorted(s.N for s, _ in ops.values())
+    return {"requests": n_req, "arrival_rate_per_s": rate, "seed": 0,
+            "operators": len(ops), "node_range": [sizes[0], sizes[-1]],
+            "n_max_drawn": args.serve_nmax, "tol": args.serve_tol,
+            "near_build_s_total": round(sum(builds), 3),
+            "near_build_s_max": round(max(builds), 3),
+            "continuous_batching": served, "one_at_a_time": plain,
+            "solves_per_s_ratio": round(served["solves_per_s"] / plain["solves_per_s"], 2)}
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -327,6 +503,13 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, FMM and served measurements")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-nmax", type=int, default=30000)
+    ap.add_argument("--serve-tol", type=float, default=1e-8)
+    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     args = ap.parse_args()
 
     if args.oracle_leg:
@@ -364,6 +547,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     line = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and not args.no_extra:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        for key, fn in (("batched_star_24576", run_batched), ("fmm_torus_98304", run_fmm),
+                        ("served", run_served)):
+            try:
+                line[key] = fn(args, dev)
+            except Exception as e:  # report, do not hide
+                line[key] = {"error": str(e)[:400]}
     if rank == 0:
         if not args.no_cpu_baseline:
             try:
