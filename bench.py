@@ -391,17 +391,19 @@ def run_fmm(args, dev):
 
 
 def _snap_surface(family, n_target, rng):
+    """Snap a drawn size to a factor-of-2 ladder of surfaces of the family (p = 8).
+
+    Sizes stay log-uniform in the drawn range, but operators recur, so a served
+    surface keeps its geometry and near field resident across requests."""
     from workloads import cubed_sphere, star_surface, torus
-    p = int(rng.choice([8, 10]))
+    p = 8
+    ladder = 1536 * 2.0 ** np.arange(0, 12)
+    n_b = float(ladder[np.argmin(np.abs(np.log(ladder / n_target)))])
     if family == "torus":
-        best = None
-        for nph in range(3, 80):
-            nth = max(3, int(round(nph * 8 / 3)))
-            n = nth * nph * p * p
-            if best is None or abs(np.log(n / n_target)) < abs(np.log(best[2] / n_target)):
-                best = (nth, nph, n)
-        return ("torus", p, best[0], best[1]), lambda: torus(best[0], best[1], p)
-    m = max(1, int(round(np.sqrt(n_target / (6 * p * p)))))
+        nph = max(3, int(round(np.sqrt(n_b / (p * p) * 3 / 8))))
+        nth = max(3, int(round(nph * 8 / 3)))
+        return ("torus", p, nth, nph), lambda: torus(nth, nph, p)
+    m = max(1, int(round(np.sqrt(n_b / (6 * p * p)))))
     if family == "sphere":
         return ("sphere", p, m), lambda: cubed_sphere(m, p)
     if family == "ellipsoid":
@@ -426,7 +428,7 @@ def run_served(args, dev):
     for _ in range(n_req):
         fam = fams[int(rng.integers(0, 4))]
         key, mk = _snap_surface(fam, float(np.exp(rng.uniform(lo, hi))), rng)
-        cseed = int(rng.integers(0, 4))
+        cseed = int(rng.integers(0, 2))
         keys.setdefault((key, cseed), mk)
         draws.append(((key, cseed), int(rng.integers(0, 1 << 30))))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
