@@ -509,10 +509,13 @@ pm_status pm_ensure_scratch(pm_surface* s, size_t n) {
 }
 
 // One right-hand side, device pointers.  kernel_K selects K instead of R.
+// prepped != 0: the float32 source strengths (src32.w, sig32) for sigma were
+// already written by the caller's kernel (fused Arnoldi step), skip the prep.
 pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const double* sigma,
-                       double* out, pm_precision prec, cudaStream_t st) {
+                       double* out, pm_precision prec, cudaStream_t st, int prepped) {
     int nsplit = 0;
-    if (smooth || near) {
+    prepped = prepped && (prec == PM_PREC_FP32 || prec == PM_PREC_FMM);
+    if ((smooth || near) && !prepped) {
         PhaseTimer t(s, PM_PHASE_PREP, st);
         if (prec == PM_PREC_FF) {
             PM_TRY(pm_prep_ff(s, sigma, st));
@@ -536,7 +539,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
         }
     }
     PhaseTimer t(s, PM_PHASE_NEAR, st);
-    s->launch_total += (smooth || near) + (smooth && prec != PM_PREC_FMM) + 1;
+    s->launch_total += ((smooth || near) && !prepped) + (smooth && prec != PM_PREC_FMM) + 1;
     return pm_near_apply(s, kernel_K, sigma, out, near, nsplit,
                          prec == PM_PREC_FMM ? PM_PREC_FP32 : prec, st);
 }

@@ -131,6 +131,32 @@ __device__ __forceinline__ ff ff_log(ff x, const float4* __restrict__ tab) {
     return r;
 }
 
+// Unnormalised variants: the low word may exceed half an ulp of the high word;
+// values are renormalised (fast_two_sum) before they feed further products.
+__device__ __forceinline__ ff ff_mul_lazy(ff a, ff b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_sqr_lazy(ff a) {
+    const float p = a.h * a.h;
+    float e = fmaf(a.h, a.h, -p);
+    e = fmaf(2.f * a.h, a.l, e);
+    return ff{p, e};
+}
+__device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return ff{s, e + (a.l + b.l)};
+}
+__device__ __forceinline__ ff ff_norm(ff a) {
+    ff r;
+    fast_two_sum(a.h, a.l, r.h, r.l);
+    return r;
+}
+
 __device__ __forceinline__ ff ff_from_double(double v) {
     const float h = (float)v;
     return ff{h, (float)(v - (double)h)};
@@ -207,22 +233,32 @@ k_direct_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
             const ff dx = ff_sub(X[0], ff{A.x, B.x});
             const ff dy = ff_sub(X[1], ff{A.y, B.y});
             const ff dz = ff_sub(X[2], ff{A.z, B.z});
-            const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+            const ff r2 = ff_norm(ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)),
+                                              ff_sqr_lazy(dz)));
             const ff s{A.w, B.w};
             ff term;
             if (KERNEL_K) {
-                term = ff_mul(s, ff_log(r2, stab));
+                term = ff_mul_lazy(s, ff_log(r2, stab));
             } else {
                 const ff inv = ff_rcp(r2);
-                const ff nr = ff_add(ff_add(ff_mul(NP[0], dx), ff_mul(NP[1], dy)), ff_mul(NP[2], dz));
-                const ff mr = ff_add(ff_add(ff_mul(MM[0], dx), ff_mul(MM[1], dy)), ff_mul(MM[2], dz));
-                const ff inner = ff_add(ff_mul(nr, ff_mul(nr, inv)), mr);
-                term = ff_mul(ff_mul(s, inv), inner);
+                const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
+                                                              ff_mul_lazy(NP[1], dy)),
+                                                  ff_mul_lazy(NP[2], dz)));
+                const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
+                                          ff_mul_lazy(MM[2], dz));
+                const ff q = ff_mul(nr, inv);
+                const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, q), mr));
+                term = ff_mul_lazy(ff_mul(s, inv), inner);
             }
-            acc = ff_add(acc, term);
+            // lazy accumulation: TwoSum on the high words, error terms in the low word
+            const float t = acc.h + term.h;
+            const float bp = t - acc.h;
+            acc.l += ((acc.h - (t - bp)) + (term.h - bp)) + term.l;
+            acc.h = t;
         }
     }
     if (i < N) {
+        acc = ff_norm(acc);
         if (KERNEL_K) acc = ff_mul(acc, ff_from_double(1.0 / (4.0 * M_PI)));
         partial[(size_t)blockIdx.y * N + i] = make_float2(acc.h, acc.l);
     }

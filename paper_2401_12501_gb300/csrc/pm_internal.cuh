@@ -205,7 +205,7 @@ void pm_solve_free(pm_surface* s);
 // apply helpers (pm_api.cu)
 pm_status pm_apply_dev(pm_surface* s, int part_mask_K, int smooth, int near,
                        const double* sigma, double* out, pm_precision prec,
-                       cudaStream_t st);
+                       cudaStream_t st, int prepped = 0);
 pm_status pm_ensure_scratch(pm_surface* s, size_t n);
 
 // Records an event pair around the launches in its scope when profiling is on.

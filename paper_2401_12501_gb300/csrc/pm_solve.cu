@@ -11,9 +11,19 @@
 // the Hessenberg Givens rotations and the least-squares update stay float64.
 //
 // No host round-trip per Arnoldi step: every kernel of a cycle takes a device
-// "done" flag that the rotation kernel sets once the residual estimate meets
-// the tolerance (or the Arnoldi vector vanishes); later kernels of the cycle
-// return immediately.  The host synchronises once per cycle.
+// "done" flag that the rotation sets once the residual estimate meets the
+// tolerance (or the Arnoldi vector vanishes); later kernels of the cycle
+// return immediately.  The host reads the flag every few steps.
+//
+// One Arnoldi step is the operator apply (float32 sums + near field) and four
+// fused kernels over blocks of 256 rows: (1) finish A v and form this block's
+// partial dots V_j . w; (2) reduce them, subtract, partial dots again (the
+// second Gram-Schmidt pass); (3) reduce, subtract, partial |w|^2; (4) reduce,
+// Givens update, v_{k+1} = w/|w| together with the float32 source strengths
+// of the next apply and the partial of sum_j w_j v_j for its rank-one term.
+// Every block reduces the previous kernel's per-block partials itself, in a
+// fixed order, so all blocks hold bit-identical sums and the result does not
+// depend on scheduling.
 #include "pm_internal.cuh"
 
 #include <chrono>
@@ -71,18 +81,6 @@ __global__ void k_reduce_cols(const double* __restrict__ partial, int nblk, int 
     out[j] = s;
 }
 
-// w -= sum_j A_j * c[j]
-__global__ void k_sub_combo(const double* __restrict__ A, long long lda, int ncols,
-                            const double* __restrict__ c, double* __restrict__ w, int N,
-                            const int* __restrict__ done) {
-    if (done && *done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double acc = w[i];
-    for (int j = 0; j < ncols; ++j) acc -= A[j * lda + i] * c[j];
-    w[i] = acc;
-}
-
 // out = v + y + scal[0] (the rank-one term sum_j w_j v_j)
 __global__ void k_apply_A_finish(const double* __restrict__ v, const double* __restrict__ y,
                                  const double* __restrict__ wdot, double* __restrict__ out, int N,
@@ -98,24 +96,6 @@ __global__ void k_residual_from(const double* __restrict__ b, const double* __re
                                 double* __restrict__ r, int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) r[i] = b[i] - Ax[i];
-}
-
-// h[j] += h2[j], j < n
-__global__ void k_add_cols(double* __restrict__ h, const double* __restrict__ h2, int n,
-                           const int* __restrict__ done) {
-    if (done && *done) return;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) h[j] += h2[j];
-}
-
-__global__ void k_scale_copy(const double* __restrict__ src, const double* __restrict__ s,
-                             int invert, double* __restrict__ dst, int N,
-                             const int* __restrict__ done) {
-    if (done && *done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const double f = invert ? 1.0 / *s : *s;
-    dst[i] = src[i] * f;
 }
 
 __global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b,
@@ -135,32 +115,14 @@ __global__ void k_add_shift(double* __restrict__ y, const double* __restrict__ s
     if (i < N) y[i] += sgn * *shift;
 }
 
-// Start of a cycle: beta = sqrt(nrm2), g = (beta, 0, ...), v0 = r / beta.
-__global__ void k_cycle_start(const double* __restrict__ nrm2, double* __restrict__ g, int m,
-                              double* __restrict__ scal, double tol_abs, int* __restrict__ done,
-                              int* __restrict__ iters) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double beta = sqrt(*nrm2);
-    for (int k = 0; k <= m; ++k) g[k] = 0.0;
-    g[0] = beta;
-    scal[3] = beta;
-    *iters = 0;
-    *done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
-}
-
-// Arnoldi step k finished its orthogonalisation: column h[0..k] and the
-// squared norm of the new vector are in place.  Apply the previous Givens
-// rotations, form the new one, update g, test convergence.
-__global__ void k_arnoldi_rotate(double* __restrict__ H, int ldh, int k, double* __restrict__ cs,
-                                 double* __restrict__ sn, double* __restrict__ g,
-                                 const double* __restrict__ nrm2, double* __restrict__ scal,
-                                 double tol_abs, int* __restrict__ done, int* __restrict__ iters) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (*done) return;
+// Arnoldi step k finished its orthogonalisation: column h[0..k] is in place and
+// hn = |w| is the norm of the new vector.  Apply the previous Givens rotations,
+// form the new one, update g, test convergence.  One thread.
+__device__ void givens_update(double* __restrict__ H, int ldh, int k, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double hn,
+                              double tol_abs, int* __restrict__ done, int* __restrict__ iters) {
     double* h = H + (size_t)k * ldh;    // column k, entries 0..k+1
-    const double hn = sqrt(*nrm2);
     h[k + 1] = hn;
-    scal[2] = (hn > 0.0) ? 1.0 / hn : 0.0;
     for (int j = 0; j < k; ++j) {
         const double t = cs[j] * h[j] + sn[j] * h[j + 1];
         h[j + 1] = -sn[j] * h[j] + cs[j] * h[j + 1];
@@ -178,6 +140,176 @@ __global__ void k_arnoldi_rotate(double* __restrict__ H, int ldh, int k, double*
     *iters = k + 1;
     // breakdown (hn tiny) means the Krylov space is invariant: the LS solution is exact
     if (fabs(g[k + 1]) <= tol_abs || hn <= 1e-300 || !(hn == hn)) *done = 1;
+}
+
+// ---------------------------------------------------------------- fused Arnoldi step
+constexpr int kArnThreads = 256;    // rows per block
+constexpr int kArnMaxCols = 408;    // >= restart + 1
+
+// The flag read once per block, so that every thread of a block takes the same path.
+__device__ __forceinline__ bool block_done(const int* __restrict__ done) {
+    __shared__ int sd;
+    if (threadIdx.x == 0) sd = done ? *reinterpret_cast<const volatile int*>(done) : 0;
+    __syncthreads();
+    return sd != 0;
+}
+
+// out_sh[j] = sum over blocks b of part[b * ld + j], j < n: a warp per column,
+// lanes over blocks, fixed order (identical in every block).
+__device__ void reduce_cols_sh(const double* __restrict__ part, int nblk, int ld, int n,
+                               double* out_sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = wid; j < n; j += nw) {
+        double t = 0.0;
+        for (int b = lane; b < nblk; b += 32) t += part[(size_t)b * ld + j];
+        t = warp_sum(t);
+        if (lane == 0) out_sh[j] = t;
+    }
+    __syncthreads();
+}
+
+// part_row[j] = sum over the block's rows r0 + t of V_j[r0 + t] w_sh[t], j < ncols
+__device__ void col_dots_sh(const double* __restrict__ V, long long ldv, int ncols,
+                            const double* w_sh, int r0, int nr, double* __restrict__ part_row) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = wid; j < ncols; j += nw) {
+        const double* a = V + (size_t)j * ldv + r0;
+        double t = 0.0;
+        for (int q = lane; q < nr; q += 32) t += a[q] * w_sh[q];
+        t = warp_sum(t);
+        if (lane == 0) part_row[j] = t;
+    }
+}
+
+// v_i = r_i * inv, with the float32 strengths of the next apply (src32 != NULL)
+// and this block's partial of sum_i wq_i v_i.
+__device__ void scale_prep_wdot(const double* __restrict__ r, double inv, double* __restrict__ v,
+                                const double* __restrict__ wq, const double* __restrict__ wa,
+                                float4* __restrict__ src32, float* __restrict__ sig32, int pp,
+                                int ppad, double* __restrict__ pw_row, int N, double* red) {
+    const int i = blockIdx.x * kArnThreads + threadIdx.x;
+    double t = 0.0;
+    if (i < N) {
+        const double vi = r[i] * inv;
+        v[i] = vi;
+        if (src32) {
+            src32[i].w = (float)(wa[i] * vi);
+            const int P = i / pp;
+            sig32[(size_t)P * ppad + (i - P * pp)] = (float)vi;
+        }
+        t = wq[i] * vi;
+    }
+    t = block_sum(t, red);
+    if (threadIdx.x == 0) pw_row[0] = t;
+}
+
+// This block's partial of r . r.
+__global__ void __launch_bounds__(kArnThreads)
+k_sq_partial(const double* __restrict__ r, int N, double* __restrict__ pout, int ld) {
+    __shared__ double red[32];
+    const int i = blockIdx.x * kArnThreads + threadIdx.x;
+    const double v = (i < N) ? r[i] : 0.0;
+    const double t = block_sum(v * v, red);
+    if (threadIdx.x == 0) pout[(size_t)blockIdx.x * ld] = t;
+}
+
+// Cycle start: beta = |r|, g = (beta, 0, ...), v0 = r / beta (+ prep, wq . v0 partials).
+__global__ void __launch_bounds__(kArnThreads)
+k_arn_start(const double* __restrict__ pin, int nblk, int ld, double* __restrict__ g, int m,
+            double* __restrict__ scal, double tol_abs, int* __restrict__ done,
+            int* __restrict__ iters, const double* __restrict__ r, double* __restrict__ v0,
+            const double* __restrict__ wq, const double* __restrict__ wa,
+            float4* __restrict__ src32, float* __restrict__ sig32, int pp, int ppad,
+            double* __restrict__ pw, int N) {
+    __shared__ double red[32];
+    reduce_cols_sh(pin, nblk, ld, 1, red);
+    const double beta = sqrt(red[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k <= m; ++k) g[k] = 0.0;
+        g[0] = beta;
+        scal[3] = beta;
+        *iters = 0;
+        *done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    scale_prep_wdot(r, beta > 0.0 ? 1.0 / beta : 0.0, v0, wq, wa, src32, sig32, pp, ppad,
+                    pw + (size_t)blockIdx.x * ld, N, red);
+}
+
+// (1) w = v + y + sum_j wq_j v_j (A v with the rank-one term); partial dots V_j . w, j < ncols.
+__global__ void __launch_bounds__(kArnThreads)
+k_arn_first(const double* __restrict__ v, const double* __restrict__ y,
+            const double* __restrict__ pw, int nblk, int ld, const double* __restrict__ V,
+            long long ldv, int ncols, double* __restrict__ w, double* __restrict__ pout, int N,
+            const int* __restrict__ done) {
+    __shared__ double red[32];
+    __shared__ double w_sh[kArnThreads];
+    if (block_done(done)) return;
+    reduce_cols_sh(pw, nblk, ld, 1, red);
+    const int r0 = blockIdx.x * kArnThreads, i = r0 + threadIdx.x;
+    double wi = 0.0;
+    if (i < N) {
+        wi = v[i] + y[i] + red[0];
+        w[i] = wi;
+    }
+    w_sh[threadIdx.x] = wi;
+    __syncthreads();
+    col_dots_sh(V, ldv, ncols, w_sh, r0, min(kArnThreads, N - r0), pout + (size_t)blockIdx.x * ld);
+}
+
+// (2)/(3) h = sum of the partial dots; block 0 stores the Hessenberg column
+// (accumulate: adds the second pass); w -= V h; then this block's partial dots
+// V_j . w (last == 0) or w . w (last == 1).
+__global__ void __launch_bounds__(kArnThreads)
+k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __restrict__ V,
+           long long ldv, int ncols, double* __restrict__ hk, int accumulate,
+           double* __restrict__ w, double* __restrict__ pout, int last, int N,
+           const int* __restrict__ done) {
+    __shared__ double h_sh[kArnMaxCols];
+    __shared__ double w_sh[kArnThreads];
+    __shared__ double red[32];
+    if (block_done(done)) return;
+    reduce_cols_sh(pin, nblk, ld, ncols, h_sh);
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < ncols; j += blockDim.x)
+            hk[j] = accumulate ? hk[j] + h_sh[j] : h_sh[j];
+    const int r0 = blockIdx.x * kArnThreads, i = r0 + threadIdx.x;
+    double wi = 0.0;
+    if (i < N) {
+        wi = w[i];
+        for (int j = 0; j < ncols; ++j) wi -= V[(size_t)j * ldv + i] * h_sh[j];
+        w[i] = wi;
+    }
+    if (!last) {
+        w_sh[threadIdx.x] = wi;
+        __syncthreads();
+        col_dots_sh(V, ldv, ncols, w_sh, r0, min(kArnThreads, N - r0),
+                    pout + (size_t)blockIdx.x * ld);
+    } else {
+        const double t = block_sum(wi * wi, red);
+        if (threadIdx.x == 0) pout[(size_t)blockIdx.x * ld] = t;
+    }
+}
+
+// (4) |w| from the partials; block 0 applies the Givens update (may set done);
+// v_{k+1} = w / |w| with the next apply's prep and wq . v_{k+1} partials.
+__global__ void __launch_bounds__(kArnThreads)
+k_arn_normalize(const double* __restrict__ pin, int nblk, int ld, double* __restrict__ H,
+                int ldh, int k, double* __restrict__ cs, double* __restrict__ sn,
+                double* __restrict__ g, double tol_abs, int* __restrict__ done,
+                int* __restrict__ iters, const double* __restrict__ w,
+                double* __restrict__ vnext, const double* __restrict__ wq,
+                const double* __restrict__ wa, float4* __restrict__ src32,
+                float* __restrict__ sig32, int pp, int ppad, double* __restrict__ pw, int N) {
+    __shared__ double red[32];
+    __shared__ double nrm[1];
+    if (block_done(done)) return;
+    reduce_cols_sh(pin, nblk, ld, 1, nrm);
+    const double hn = sqrt(nrm[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        givens_update(H, ldh, k, cs, sn, g, hn, tol_abs, done, iters);
+    scale_prep_wdot(w, hn > 0.0 ? 1.0 / hn : 0.0, vnext, wq, wa, src32, sig32, pp, ppad,
+                    pw + (size_t)blockIdx.x * ld, N, red);
 }
 
 // y = H(0:n,0:n)^{-1} g(0:n) by back substitution, n = *iters
@@ -206,9 +338,10 @@ __global__ void k_add_combo(const double* __restrict__ V, long long ldv,
 }
 
 struct Work {
-    int N = 0, m = 0, nred = 0;
+    int N = 0, m = 0, nred = 0, narn = 0;
     double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *part = nullptr, *scal = nullptr, *hcol = nullptr;
+    double *pa = nullptr, *pb = nullptr;      // per-block partials of the fused Arnoldi kernels
     double *w = nullptr, *tmp = nullptr, *r = nullptr, *res = nullptr, *delta = nullptr;
     double *sig = nullptr, *f = nullptr, *u = nullptr;
     int *done = nullptr, *iters = nullptr;
@@ -226,7 +359,7 @@ void pm_solve_free(pm_surface* s) {
     pm_dfree(W.V); pm_dfree(W.H); pm_dfree(W.cs); pm_dfree(W.sn); pm_dfree(W.g); pm_dfree(W.y);
     pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.w); pm_dfree(W.tmp);
     pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig); pm_dfree(W.f);
-    pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters);
+    pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.pa); pm_dfree(W.pb);
     if (W.pinned) cudaFreeHost(W.pinned);
     if (W.pinned_i) cudaFreeHost(W.pinned_i);
     delete s->solve_work;
@@ -255,6 +388,9 @@ pm_status get_work(pm_surface* s, Work** out) {
     PM_TRY(pm_dmalloc(&W.g, m + 1));
     PM_TRY(pm_dmalloc(&W.y, m));
     PM_TRY(pm_dmalloc(&W.part, (size_t)W.nred * (m + 2)));
+    W.narn = pm_ceil_div(N, kArnThreads);
+    PM_TRY(pm_dmalloc(&W.pa, (size_t)W.narn * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.pb, (size_t)W.narn * (m + 2)));
     PM_TRY(pm_dmalloc(&W.scal, 8));
     PM_TRY(pm_dmalloc(&W.hcol, m + 2));
     PM_TRY(pm_dmalloc(&W.w, N));
@@ -328,12 +464,17 @@ struct Solver {
         int total = 0;
         PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * W.N, cudaMemcpyDeviceToDevice, st));
         PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * W.N, st));
+        // the float32 strengths of each basis vector are written by the kernel
+        // that forms it (FP32 / FMM operators)
+        const bool fuse_prep = prec == PM_PREC_FP32 || prec == PM_PREC_FMM;
+        float4* src32 = fuse_prep ? s->src32 : nullptr;
+        const int nb = W.narn, ld = m + 2;
         while (total < max_iter) {
-            PM_TRY(dots(W.r, 0, 1, W.r, W.scal + 1, nullptr));
-            k_cycle_start<<<1, 1, 0, st>>>(W.scal + 1, W.g, m, W.scal, tol_abs, W.done, W.iters);
-            s->launch_total++;
-            k_scale_copy<<<grid_n, 256, 0, st>>>(W.r, W.scal + 3, 1, W.V, W.N, W.done);
-            s->launch_total++;
+            k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
+            k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, tol_abs, W.done,
+                                                    W.iters, W.r, W.V, s->w, s->wa, src32,
+                                                    s->sig32, s->pp, s->ppad, W.pb, W.N);
+            s->launch_total += 2;
             const int steps = std::min(m, max_iter - total);
             s->skip_flag = W.done;
             // launch the cycle in chunks; between chunks read the done flag so a
@@ -354,23 +495,20 @@ struct Solver {
                 double* vk = W.V + (size_t)k * ldv;
                 double* vk1 = W.V + (size_t)(k + 1) * ldv;
                 double* hk = W.H + (size_t)k * (m + 2);
-                pm_status stt = apply_A(vk, W.w, prec, W.done);
+                // W.tmp = R~ v_k (sources already prepared when fuse_prep)
+                pm_status stt = pm_apply_dev(s, 0, 1, 1, vk, W.tmp, prec, st, fuse_prep ? 1 : 0);
                 if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
-                // classical Gram-Schmidt, applied twice
-                dots(W.V, ldv, k + 1, W.w, hk, W.done);
-                k_sub_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, k + 1, hk, W.w, W.N, W.done);
-                s->launch_total++;
-                dots(W.V, ldv, k + 1, W.w, W.hcol, W.done);
-                k_sub_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, k + 1, W.hcol, W.w, W.N, W.done);
-                s->launch_total++;
-                k_add_cols<<<pm_ceil_div(k + 1, 64), 64, 0, st>>>(hk, W.hcol, k + 1, W.done);
-                s->launch_total++;
-                dots(W.w, 0, 1, W.w, W.scal + 1, W.done);
-                k_arnoldi_rotate<<<1, 1, 0, st>>>(W.H, m + 2, k, W.cs, W.sn, W.g, W.scal + 1,
-                                                  W.scal, tol_abs, W.done, W.iters);
-                s->launch_total++;
-                k_scale_copy<<<grid_n, 256, 0, st>>>(W.w, W.scal + 2, 0, vk1, W.N, W.done);
-                s->launch_total++;
+                // partials ping-pong between W.pb and W.pa
+                k_arn_first<<<nb, kArnThreads, 0, st>>>(vk, W.tmp, W.pb, nb, ld, W.V, ldv, k + 1,
+                                                        W.w, W.pa, W.N, W.done);
+                k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, k + 1, hk, 0, W.w,
+                                                       W.pb, 0, W.N, W.done);
+                k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, k + 1, hk, 1, W.w,
+                                                       W.pa, 1, W.N, W.done);
+                k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
+                    W.pa, nb, ld, W.H, m + 2, k, W.cs, W.sn, W.g, tol_abs, W.done, W.iters, W.w,
+                    vk1, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, W.N);
+                s->launch_total += 4;
             }
             s->skip_flag = nullptr;
             PM_CUDA_TRY(cudaGetLastError());

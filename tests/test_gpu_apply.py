@@ -131,12 +131,14 @@ def test_multi_rhs_and_device_pointers(ctx):
     import torch
     wl, s = gpu_surface(ctx, "ellipsoid_small")
     sig = np.random.default_rng(5).standard_normal((3, wl.N))
-    for prec in ("fp32", "fp64"):
+    # several right-hand sides go through the batched kernels, which sum in a
+    # different order from the one-at-a-time path: equal to working precision
+    for prec, tol in (("fp32", 2e-6), ("fp64", 1e-13), ("ff", 5e-13)):
         host = s.apply_R(sig, prec)
         dev = s.apply_R(torch.from_numpy(sig).cuda(), prec).cpu().numpy()
         single = np.stack([s.apply_R(sig[r], prec) for r in range(3)])
         assert np.array_equal(host, dev)          # deterministic kernels
-        assert np.array_equal(host, single)
+        assert np.abs(host - single).max() <= tol * np.abs(single).max(), prec
 
 
 def test_invalid_inputs(ctx):
