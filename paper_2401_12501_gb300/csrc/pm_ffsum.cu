@@ -52,17 +52,6 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     e = b - (s - a);
 }
 
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    e += a.l + b.l;
-    ff r;
-    fast_two_sum(s, e, r.h, r.l);
-    return r;
-}
-
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
-
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     const float p = a.h * b.h;
     float e = fmaf(a.h, b.h, -p);
@@ -73,66 +62,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     return r;
 }
 
-__device__ __forceinline__ ff ff_mulf(ff a, float b) {
-    const float p = a.h * b;
-    float e = fmaf(a.h, b, -p);
-    e = fmaf(a.l, b, e);
-    ff r;
-    fast_two_sum(p, e, r.h, r.l);
-    return r;
-}
-
-__device__ __forceinline__ ff ff_sqr(ff a) {
-    const float p = a.h * a.h;
-    float e = fmaf(a.h, a.h, -p);
-    e = fmaf(2.f * a.h, a.l, e);
-    ff r;
-    fast_two_sum(p, e, r.h, r.l);
-    return r;
-}
-
-// 1/a: y = rcp(a.h), one Newton step y + y (1 - a y) with the residual in float-float
-__device__ __forceinline__ ff ff_rcp(ff a) {
-    const float y = rcp_approx(a.h);
-    const float p = a.h * y;
-    const float ep = fmaf(a.h, y, -p);          // a.h y = p + ep exactly
-    const float res = ((1.f - p) - ep) - a.l * y;
-    ff r;
-    fast_two_sum(y, y * res, r.h, r.l);
-    return r;
-}
-
-// ln(x) for x = hi + lo > 0 (Tang's table method, see the file header).
-// tab: [k] = (1/c_k hi, 1/c_k lo, ln c_k hi, ln c_k lo)
-__device__ __forceinline__ ff ff_log(ff x, const float4* __restrict__ tab) {
-    int e;
-    const float mh = frexpf(x.h, &e);            // x.h = mh 2^e, mh in [0.5, 1)
-    const float sc = ldexpf(1.f, -e + 1);        // exact power of two
-    ff m{mh * 2.f, x.l * sc};                    // m in [1, 2)
-    e -= 1;
-    const int k = (int)((m.h - 1.f) * (float)kLogTable);   // top 7 fraction bits
-    const float4 T = tab[min(max(k, 0), kLogTable - 1)];
-    const ff p = ff_mul(m, ff{T.x, T.y});        // m / c_k = 1 + t
-    float th, tl;
-    fast_two_sum(p.h - 1.f, p.l, th, tl);        // p.h - 1 is exact (Sterbenz)
-    const ff t{th, tl};
-    const ff t2 = ff_sqr(t);
-    const float tf = t.h;
-    const float poly = fmaf(fmaf(fmaf(-1.f / 6.f, tf, 0.2f), tf, -0.25f), tf, 1.f / 3.f);
-    const float cubic = tf * tf * tf * poly;
-    // e ln 2 in float-float: ln 2 = L2H + L2L
-    const float L2H = 0.693147182464599609375f;      // float(ln 2)
-    const float L2L = -1.904654323148236e-09f;       // ln 2 - L2H
-    ff r = ff_mulf(ff{L2H, L2L}, (float)e);
-    r = ff_add(r, ff{T.z, T.w});
-    r = ff_add(r, t);
-    r = ff_add(r, ff{-0.5f * t2.h, -0.5f * t2.l});
-    r = ff_add(r, ff{cubic, 0.f});
-    return r;
-}
-
-// Unnormalised variants: the low word may exceed half an ulp of the high word;
-// values are renormalised (fast_two_sum) before they feed further products.
+// Unnormalised variants: the low word may exceed half an ulp of the high word.
+// Products of such pairs keep float-float accuracy only while the low word
+// stays within a few ulps of the high word, so every sum that can cancel
+// (differences, dot products, the bracket of the remainder term) is
+// renormalised before it is multiplied; sums of positive terms (r^2) and the
+// reciprocal and logarithm, whose low words stay small, are not.
 __device__ __forceinline__ ff ff_mul_lazy(ff a, ff b) {
     const float p = a.h * b.h;
     float e = fmaf(a.h, b.h, -p);
@@ -154,6 +89,55 @@ __device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
 __device__ __forceinline__ ff ff_norm(ff a) {
     ff r;
     fast_two_sum(a.h, a.l, r.h, r.l);
+    return r;
+}
+
+// a - b, normalised: where the high words cancel the low word would otherwise
+// be as large as the high word, and products with it would lose the l^2 term
+__device__ __forceinline__ ff ff_sub(ff a, ff b) {
+    float s, e;
+    two_sum(a.h, -b.h, s, e);
+    return ff_norm(ff{s, e + (a.l - b.l)});
+}
+
+// 1/a: y = rcp(a.h) and one Newton step y + y (1 - a y), the residual 1 - a y
+// formed with the exact product a.h y = p + ep; returned unnormalised as (y, y res)
+__device__ __forceinline__ ff ff_rcp_lazy(ff a) {
+    const float y = rcp_approx(a.h);
+    const float p = a.h * y;
+    const float ep = fmaf(a.h, y, -p);
+    const float res = ((1.f - p) - ep) - a.l * y;
+    return ff{y, y * res};
+}
+
+// ln(x) for x = hi + lo > 0 (Tang's table method, see the file header):
+// tab[k] = (1/c_k hi, 1/c_k lo, ln c_k hi, ln c_k lo).  The parts e ln 2,
+// ln c_k, t and -t^2/2 + t^3 (...) are summed with error-free high words and
+// plain low words; the result is left unnormalised.
+__device__ __forceinline__ ff ff_log_lazy(ff x, const float4* __restrict__ tab) {
+    int e;
+    const float mh = frexpf(x.h, &e);
+    const float sc = ldexpf(1.f, -e + 1);
+    ff m{mh * 2.f, x.l * sc};
+    e -= 1;
+    const int k = (int)((m.h - 1.f) * (float)kLogTable);
+    const float4 T = tab[min(max(k, 0), kLogTable - 1)];
+    const ff p = ff_mul(m, ff{T.x, T.y});
+    float th, tl;
+    fast_two_sum(p.h - 1.f, p.l, th, tl);
+    const ff t{th, tl};
+    const ff t2 = ff_sqr_lazy(t);
+    const float tf = t.h;
+    const float poly = fmaf(fmaf(fmaf(-1.f / 6.f, tf, 0.2f), tf, -0.25f), tf, 1.f / 3.f);
+    const float cubic = tf * tf * tf * poly;
+    const float L2H = 0.693147182464599609375f;
+    const float L2L = -1.904654323148236e-09f;
+    const float ef = (float)e;
+    const float eh = L2H * ef;
+    const ff el{eh, fmaf(L2H, ef, -eh) + L2L * ef};    // e ln 2; the FMA recovers L2H e exactly
+    ff r = ff_add_lazy(el, ff{T.z, T.w});
+    r = ff_add_lazy(r, t);
+    r = ff_add_lazy(r, ff{-0.5f * t2.h, fmaf(-0.5f, t2.l, cubic)});
     return r;
 }
 
@@ -233,22 +217,21 @@ k_direct_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
             const ff dx = ff_sub(X[0], ff{A.x, B.x});
             const ff dy = ff_sub(X[1], ff{A.y, B.y});
             const ff dz = ff_sub(X[2], ff{A.z, B.z});
-            const ff r2 = ff_norm(ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)),
-                                              ff_sqr_lazy(dz)));
+            const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
             const ff s{A.w, B.w};
             ff term;
             if (KERNEL_K) {
-                term = ff_mul_lazy(s, ff_log(r2, stab));
+                term = ff_mul_lazy(s, ff_log_lazy(r2, stab));
             } else {
-                const ff inv = ff_rcp(r2);
+                const ff inv = ff_rcp_lazy(r2);
                 const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
                                                               ff_mul_lazy(NP[1], dy)),
                                                   ff_mul_lazy(NP[2], dz)));
                 const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
                                           ff_mul_lazy(MM[2], dz));
-                const ff q = ff_mul(nr, inv);
+                const ff q = ff_mul_lazy(nr, inv);
                 const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, q), mr));
-                term = ff_mul_lazy(ff_mul(s, inv), inner);
+                term = ff_mul_lazy(ff_mul_lazy(s, inv), inner);
             }
             // lazy accumulation: TwoSum on the high words, error terms in the low word
             const float t = acc.h + term.h;
@@ -271,7 +254,7 @@ __global__ void k_fflog_test(const float* __restrict__ xh, const float* __restri
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const ff r = ff_log(ff{xh[i], xl[i]}, stab);
+    const ff r = ff_norm(ff_log_lazy(ff{xh[i], xl[i]}, stab));
     out[i] = (double)r.h + (double)r.l;
 }
 
