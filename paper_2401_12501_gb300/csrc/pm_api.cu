@@ -414,6 +414,7 @@ extern "C" pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_b
     }
     s->opts.direct_tpt = direct_tpt;
     s->opts.direct_blocks_per_sm = direct_blocks_per_sm;
+    s->graph_epoch++;
     return PM_OK;
 }
 
@@ -470,6 +471,7 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
     PM_TRY(pm_near_combine_coeff(s, st));
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     s->has_coeff = true;
+    s->graph_epoch++;
     return PM_OK;
 }
 

@@ -213,14 +213,21 @@ k_sq_partial(const double* __restrict__ r, int N, double* __restrict__ pout, int
     if (threadIdx.x == 0) pout[(size_t)blockIdx.x * ld] = t;
 }
 
+// Step index of the fused kernels: the device counter (graph-driven cycles,
+// where one captured step serves every k) or the launch argument.
+__device__ __forceinline__ int step_index(int k_arg, const int* __restrict__ k_dev) {
+    return k_dev ? *k_dev : k_arg;
+}
+
 // Cycle start: beta = |r|, g = (beta, 0, ...), v0 = r / beta (+ prep, wq . v0 partials).
+// par = (tol_abs, steps).  use_cond: also sets the graph's loop condition.
 __global__ void __launch_bounds__(kArnThreads)
 k_arn_start(const double* __restrict__ pin, int nblk, int ld, double* __restrict__ g, int m,
-            double* __restrict__ scal, double tol_abs, int* __restrict__ done,
+            double* __restrict__ scal, const double* __restrict__ par, int* __restrict__ done,
             int* __restrict__ iters, const double* __restrict__ r, double* __restrict__ v0,
             const double* __restrict__ wq, const double* __restrict__ wa,
             float4* __restrict__ src32, float* __restrict__ sig32, int pp, int ppad,
-            double* __restrict__ pw, int N) {
+            double* __restrict__ pw, int N, int use_cond, cudaGraphConditionalHandle cond) {
     __shared__ double red[32];
     reduce_cols_sh(pin, nblk, ld, 1, red);
     const double beta = sqrt(red[0]);
@@ -229,22 +236,26 @@ k_arn_start(const double* __restrict__ pin, int nblk, int ld, double* __restrict
         g[0] = beta;
         scal[3] = beta;
         *iters = 0;
-        *done = (beta <= tol_abs || beta == 0.0) ? 1 : 0;
+        const int d = (beta <= par[0] || beta == 0.0) ? 1 : 0;
+        *done = d;
+        if (use_cond) cudaGraphSetConditional(cond, (!d && par[1] >= 1.0) ? 1u : 0u);
     }
     __syncthreads();
     scale_prep_wdot(r, beta > 0.0 ? 1.0 / beta : 0.0, v0, wq, wa, src32, sig32, pp, ppad,
                     pw + (size_t)blockIdx.x * ld, N, red);
 }
 
-// (1) w = v + y + sum_j wq_j v_j (A v with the rank-one term); partial dots V_j . w, j < ncols.
+// (1) w = v_k + y + sum_j wq_j v_k,j (A v_k with the rank-one term); partial dots V_j . w, j <= k.
 __global__ void __launch_bounds__(kArnThreads)
-k_arn_first(const double* __restrict__ v, const double* __restrict__ y,
-            const double* __restrict__ pw, int nblk, int ld, const double* __restrict__ V,
-            long long ldv, int ncols, double* __restrict__ w, double* __restrict__ pout, int N,
+k_arn_first(const double* __restrict__ y, const double* __restrict__ pw, int nblk, int ld,
+            const double* __restrict__ V, long long ldv, int k_arg, const int* __restrict__ k_dev,
+            double* __restrict__ w, double* __restrict__ pout, int N,
             const int* __restrict__ done) {
     __shared__ double red[32];
     __shared__ double w_sh[kArnThreads];
     if (block_done(done)) return;
+    const int k = step_index(k_arg, k_dev);
+    const double* v = V + (size_t)k * ldv;
     reduce_cols_sh(pw, nblk, ld, 1, red);
     const int r0 = blockIdx.x * kArnThreads, i = r0 + threadIdx.x;
     double wi = 0.0;
@@ -254,21 +265,24 @@ k_arn_first(const double* __restrict__ v, const double* __restrict__ y,
     }
     w_sh[threadIdx.x] = wi;
     __syncthreads();
-    col_dots_sh(V, ldv, ncols, w_sh, r0, min(kArnThreads, N - r0), pout + (size_t)blockIdx.x * ld);
+    col_dots_sh(V, ldv, k + 1, w_sh, r0, min(kArnThreads, N - r0), pout + (size_t)blockIdx.x * ld);
 }
 
-// (2)/(3) h = sum of the partial dots; block 0 stores the Hessenberg column
+// (2)/(3) h = sum of the partial dots; block 0 stores the Hessenberg column k
 // (accumulate: adds the second pass); w -= V h; then this block's partial dots
 // V_j . w (last == 0) or w . w (last == 1).
 __global__ void __launch_bounds__(kArnThreads)
 k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __restrict__ V,
-           long long ldv, int ncols, double* __restrict__ hk, int accumulate,
-           double* __restrict__ w, double* __restrict__ pout, int last, int N,
-           const int* __restrict__ done) {
+           long long ldv, double* __restrict__ H, int ldh, int k_arg,
+           const int* __restrict__ k_dev, int accumulate, double* __restrict__ w,
+           double* __restrict__ pout, int last, int N, const int* __restrict__ done) {
     __shared__ double h_sh[kArnMaxCols];
     __shared__ double w_sh[kArnThreads];
     __shared__ double red[32];
     if (block_done(done)) return;
+    const int k = step_index(k_arg, k_dev);
+    const int ncols = k + 1;
+    double* hk = H + (size_t)k * ldh;
     reduce_cols_sh(pin, nblk, ld, ncols, h_sh);
     if (blockIdx.x == 0)
         for (int j = threadIdx.x; j < ncols; j += blockDim.x)
@@ -291,25 +305,51 @@ k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __res
     }
 }
 
-// (4) |w| from the partials; block 0 applies the Givens update (may set done);
-// v_{k+1} = w / |w| with the next apply's prep and wq . v_{k+1} partials.
+// (4) |w| from the partials; v_{k+1} = w / |w| with the next apply's prep and
+// wq . v_{k+1} partials.  givens: block 0 also applies the Givens update (may
+// set done); otherwise k_arn_advance does it after this kernel.
 __global__ void __launch_bounds__(kArnThreads)
 k_arn_normalize(const double* __restrict__ pin, int nblk, int ld, double* __restrict__ H,
-                int ldh, int k, double* __restrict__ cs, double* __restrict__ sn,
-                double* __restrict__ g, double tol_abs, int* __restrict__ done,
-                int* __restrict__ iters, const double* __restrict__ w,
-                double* __restrict__ vnext, const double* __restrict__ wq,
-                const double* __restrict__ wa, float4* __restrict__ src32,
-                float* __restrict__ sig32, int pp, int ppad, double* __restrict__ pw, int N) {
+                int ldh, int k_arg, const int* __restrict__ k_dev, int givens,
+                double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                const double* __restrict__ par, int* __restrict__ done, int* __restrict__ iters,
+                const double* __restrict__ w, double* __restrict__ V, long long ldv,
+                const double* __restrict__ wq, const double* __restrict__ wa,
+                float4* __restrict__ src32, float* __restrict__ sig32, int pp, int ppad,
+                double* __restrict__ pw, int N) {
     __shared__ double red[32];
     __shared__ double nrm[1];
     if (block_done(done)) return;
+    const int k = step_index(k_arg, k_dev);
     reduce_cols_sh(pin, nblk, ld, 1, nrm);
     const double hn = sqrt(nrm[0]);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        givens_update(H, ldh, k, cs, sn, g, hn, tol_abs, done, iters);
-    scale_prep_wdot(w, hn > 0.0 ? 1.0 / hn : 0.0, vnext, wq, wa, src32, sig32, pp, ppad,
-                    pw + (size_t)blockIdx.x * ld, N, red);
+    if (givens && blockIdx.x == 0 && threadIdx.x == 0)
+        givens_update(H, ldh, k, cs, sn, g, hn, par[0], done, iters);
+    scale_prep_wdot(w, hn > 0.0 ? 1.0 / hn : 0.0, V + (size_t)(k + 1) * ldv, wq, wa, src32,
+                    sig32, pp, ppad, pw + (size_t)blockIdx.x * ld, N, red);
+}
+
+// Graph-driven cycles: the Givens update of step k = *iters (one warp; the same
+// fixed-order reduction of |w|^2 as k_arn_normalize), then the loop condition:
+// continue while not converged and fewer than par[1] steps were taken.  The
+// condition is written on every path, so the loop always ends: at the latest
+// after par[1] <= restart steps, since *iters grows by one per step.
+__global__ void k_arn_advance(const double* __restrict__ pin, int nblk, int ld,
+                              double* __restrict__ H, int ldh, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g,
+                              const double* __restrict__ par, int* __restrict__ done,
+                              int* __restrict__ iters, cudaGraphConditionalHandle cond) {
+    __shared__ double nrm[1];
+    const bool was_done = block_done(done);
+    if (!was_done) reduce_cols_sh(pin, nblk, ld, 1, nrm);
+    if (threadIdx.x != 0) return;
+    if (was_done) {
+        cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int k = *iters;
+    givens_update(H, ldh, k, cs, sn, g, sqrt(nrm[0]), par[0], done, iters);
+    cudaGraphSetConditional(cond, (!*done && (double)(k + 1) < par[1]) ? 1u : 0u);
 }
 
 // y = H(0:n,0:n)^{-1} g(0:n) by back substitution, n = *iters
@@ -345,8 +385,20 @@ struct Work {
     double *w = nullptr, *tmp = nullptr, *r = nullptr, *res = nullptr, *delta = nullptr;
     double *sig = nullptr, *f = nullptr, *u = nullptr;
     int *done = nullptr, *iters = nullptr;
-    double* pinned = nullptr;   // host-pinned scalars read back per cycle
+    double* par = nullptr;          // device (tol_abs, steps) of the current cycle
+    double* pinned = nullptr;       // host-pinned scalars read back per cycle
+    double* pinned_par = nullptr;   // host-pinned staging of par
     int* pinned_i = nullptr;
+    // one GMRES cycle as a CUDA graph: prologue, a device-driven while loop over
+    // Arnoldi steps, epilogue (FP32 / FMM operators, profiling off)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+    pm_precision graph_prec = PM_PREC_FP64;
+    long long graph_epoch = -1;
+    long long failed_epoch = -1;
+    pm_precision failed_prec = PM_PREC_FP64;
+    int body_launches = 0;          // kernels per loop iteration
 };
 
 }  // namespace
@@ -360,6 +412,12 @@ void pm_solve_free(pm_surface* s) {
     pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.w); pm_dfree(W.tmp);
     pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig); pm_dfree(W.f);
     pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.pa); pm_dfree(W.pb);
+    pm_dfree(W.par);
+    if (W.exec) cudaGraphExecDestroy(W.exec);
+    if (W.graph) cudaGraphDestroy(W.graph);
+    if (W.cap_stream) cudaStreamDestroy(W.cap_stream);
+    if (W.body_stream) cudaStreamDestroy(W.body_stream);
+    if (W.pinned_par) cudaFreeHost(W.pinned_par);
     if (W.pinned) cudaFreeHost(W.pinned);
     if (W.pinned_i) cudaFreeHost(W.pinned_i);
     delete s->solve_work;
@@ -403,7 +461,9 @@ pm_status get_work(pm_surface* s, Work** out) {
     PM_TRY(pm_dmalloc(&W.u, N));
     PM_TRY(pm_dmalloc(&W.done, 1));
     PM_TRY(pm_dmalloc(&W.iters, 1));
+    PM_TRY(pm_dmalloc(&W.par, 2));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, 8 * sizeof(double)));
+    PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_par, 2 * sizeof(double)));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_i, 4 * sizeof(int)));
     *out = &W;
     return PM_OK;
@@ -455,6 +515,122 @@ struct Solver {
         return PM_OK;
     }
 
+    void drop_graph() {
+        if (W.exec) cudaGraphExecDestroy(W.exec);
+        if (W.graph) cudaGraphDestroy(W.graph);
+        W.exec = nullptr;
+        W.graph = nullptr;
+    }
+
+    // Capture one GMRES cycle: [|r|^2 partials, start] -> while (cond) { apply,
+    // first, pass, pass, normalize, advance } -> [back substitution, x update].
+    // Every kernel reads the step index and the cycle parameters from device
+    // memory, so one instantiated graph serves every cycle of every solve.
+    pm_status capture_graph(pm_precision prec) {
+        const int m = W.m, nb = W.narn, ld = m + 2, N = W.N;
+        const long long ldv = N;
+        float4* src32 = s->src32;
+        if (!W.cap_stream)
+            PM_CUDA_TRY(cudaStreamCreateWithFlags(&W.cap_stream, cudaStreamNonBlocking));
+        if (!W.body_stream)
+            PM_CUDA_TRY(cudaStreamCreateWithFlags(&W.body_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = W.cap_stream, bs = W.body_stream;
+        PM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        cudaStreamCaptureStatus cst;
+        cudaError_t ce = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+        cudaGraphConditionalHandle cond = 0;
+        if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
+        if (ce == cudaSuccess) {
+            k_sq_partial<<<nb, kArnThreads, 0, cs>>>(W.r, N, W.pa, ld);
+            k_arn_start<<<nb, kArnThreads, 0, cs>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
+                                                    W.iters, W.r, W.V, s->w, s->wa, src32, s->sig32,
+                                                    s->pp, s->ppad, W.pb, N, 1, cond);
+            ce = cudaGetLastError();
+        }
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        if (ce == cudaSuccess)
+            ce = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode = nullptr;
+        if (ce == cudaSuccess) ce = cudaGraphAddNode(&cnode, g, deps, nullptr, ndeps, &cp);
+        if (ce == cudaSuccess)
+            ce = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies);
+        if (ce == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            ce = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                const long long before = s->launch_total;
+                s->skip_flag = W.done;
+                const pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V, W.tmp, prec, bs, 1);
+                s->skip_flag = nullptr;
+                W.body_launches = (int)(s->launch_total - before) + 5;
+                s->launch_total = before;
+                k_arn_first<<<nb, kArnThreads, 0, bs>>>(W.tmp, W.pb, nb, ld, W.V, ldv, 0, W.iters,
+                                                        W.w, W.pa, N, W.done);
+                k_arn_pass<<<nb, kArnThreads, 0, bs>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, 0,
+                                                       W.iters, 0, W.w, W.pb, 0, N, W.done);
+                k_arn_pass<<<nb, kArnThreads, 0, bs>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, 0,
+                                                       W.iters, 1, W.w, W.pa, 1, N, W.done);
+                k_arn_normalize<<<nb, kArnThreads, 0, bs>>>(
+                    W.pa, nb, ld, W.H, m + 2, 0, W.iters, 0, W.cs, W.sn, W.g, W.par, W.done,
+                    W.iters, W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, N);
+                k_arn_advance<<<1, 32, 0, bs>>>(W.pa, nb, ld, W.H, m + 2, W.cs, W.sn, W.g, W.par,
+                                                W.done, W.iters, cond);
+                ce = cudaGetLastError();
+                cudaGraph_t body_out = nullptr;
+                const cudaError_t ce2 = cudaStreamEndCapture(bs, &body_out);
+                if (ce == cudaSuccess) ce = ce2;
+                if (ce == cudaSuccess && stt != PM_OK) ce = cudaErrorUnknown;
+            }
+        }
+        if (ce == cudaSuccess) {
+            k_backsolve<<<1, 1, 0, cs>>>(W.H, m + 2, W.g, W.iters, W.y);
+            k_add_combo<<<pm_ceil_div(N, 256), 256, 0, cs>>>(W.V, ldv, W.iters, W.y, W.delta, N);
+            ce = cudaGetLastError();
+        }
+        cudaGraph_t out = nullptr;
+        const cudaError_t ce3 = cudaStreamEndCapture(cs, &out);
+        if (ce == cudaSuccess) ce = ce3;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&W.exec, out, 0);
+        if (ce != cudaSuccess) {
+            if (out) cudaGraphDestroy(out);
+            W.exec = nullptr;
+            cudaGetLastError();
+            pm_set_error("gmres graph capture: %s", cudaGetErrorString(ce));
+            return PM_ERR_CUDA;
+        }
+        W.graph = out;
+        return PM_OK;
+    }
+
+    // The cycle graph for this operator precision, (re)built when the surface's
+    // buffers or launch shapes changed.  A capture that fails is not retried for
+    // the same state; the cycle then runs as host-issued launches.
+    bool ensure_graph(pm_precision prec) {
+        if (W.exec && W.graph_prec == prec && W.graph_epoch == s->graph_epoch) return true;
+        if (W.failed_epoch == s->graph_epoch && W.failed_prec == prec) return false;
+        drop_graph();
+        // one un-captured apply creates whatever the apply allocates lazily
+        if (pm_apply_dev(s, 0, 1, 1, W.V, W.tmp, prec, st, 0) != PM_OK ||
+            cudaStreamSynchronize(st) != cudaSuccess || capture_graph(prec) != PM_OK) {
+            drop_graph();
+            W.failed_epoch = s->graph_epoch;
+            W.failed_prec = prec;
+            return false;
+        }
+        W.graph_prec = prec;
+        W.graph_epoch = s->graph_epoch;
+        return true;
+    }
+
     // Restarted GMRES(m) for A d = b from d = 0 with the operator in `prec`,
     // stopping when the residual estimate is below tol_abs; x += d.
     pm_status gmres(const double* b, double* x, pm_precision prec, double tol_abs, int max_iter,
@@ -462,65 +638,73 @@ struct Solver {
         const int m = W.m;
         const long long ldv = W.N;
         int total = 0;
-        PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * W.N, cudaMemcpyDeviceToDevice, st));
-        PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * W.N, st));
         // the float32 strengths of each basis vector are written by the kernel
         // that forms it (FP32 / FMM operators)
         const bool fuse_prep = prec == PM_PREC_FP32 || prec == PM_PREC_FMM;
+        const bool graph = fuse_prep && !s->profiling && ensure_graph(prec);
+        PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * W.N, cudaMemcpyDeviceToDevice, st));
+        PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * W.N, st));
         float4* src32 = fuse_prep ? s->src32 : nullptr;
         const int nb = W.narn, ld = m + 2;
         while (total < max_iter) {
-            k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
-            k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, tol_abs, W.done,
-                                                    W.iters, W.r, W.V, s->w, s->wa, src32,
-                                                    s->sig32, s->pp, s->ppad, W.pb, W.N);
-            s->launch_total += 2;
             const int steps = std::min(m, max_iter - total);
-            s->skip_flag = W.done;
-            // launch the cycle in chunks; between chunks read the done flag so a
-            // converged cycle stops launching (kernels after convergence no-op)
-            const int chunk = (steps <= 8) ? steps : 4;
-            for (int k = 0; k < steps; ++k) {
-                if (k > 0 && k % chunk == 0) {
-                    cudaError_t ce = cudaMemcpyAsync(W.pinned_i + 2, W.done, sizeof(int),
-                                                     cudaMemcpyDeviceToHost, st);
-                    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-                    if (ce != cudaSuccess) {
-                        s->skip_flag = nullptr;
-                        pm_set_error("gmres: %s", cudaGetErrorString(ce));
-                        return PM_ERR_CUDA;
+            W.pinned_par[0] = tol_abs;
+            W.pinned_par[1] = (double)steps;
+            PM_CUDA_TRY(cudaMemcpyAsync(W.par, W.pinned_par, 2 * sizeof(double),
+                                        cudaMemcpyHostToDevice, st));
+            if (graph) {
+                PM_CUDA_TRY(cudaGraphLaunch(W.exec, st));
+            } else {
+                k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
+                k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
+                                                        W.iters, W.r, W.V, s->w, s->wa, src32,
+                                                        s->sig32, s->pp, s->ppad, W.pb, W.N, 0, 0);
+                s->launch_total += 2;
+                s->skip_flag = W.done;
+                // launch the cycle in chunks; between chunks read the done flag so a
+                // converged cycle stops launching (kernels after convergence no-op)
+                const int chunk = (steps <= 8) ? steps : 4;
+                for (int k = 0; k < steps; ++k) {
+                    if (k > 0 && k % chunk == 0) {
+                        cudaError_t ce = cudaMemcpyAsync(W.pinned_i + 2, W.done, sizeof(int),
+                                                         cudaMemcpyDeviceToHost, st);
+                        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+                        if (ce != cudaSuccess) {
+                            s->skip_flag = nullptr;
+                            pm_set_error("gmres: %s", cudaGetErrorString(ce));
+                            return PM_ERR_CUDA;
+                        }
+                        if (W.pinned_i[2]) break;
                     }
-                    if (W.pinned_i[2]) break;
+                    // W.tmp = R~ v_k (sources already prepared when fuse_prep)
+                    pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V + (size_t)k * ldv, W.tmp, prec,
+                                                 st, fuse_prep ? 1 : 0);
+                    if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
+                    // partials ping-pong between W.pb and W.pa
+                    k_arn_first<<<nb, kArnThreads, 0, st>>>(W.tmp, W.pb, nb, ld, W.V, ldv, k,
+                                                            nullptr, W.w, W.pa, W.N, W.done);
+                    k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, k,
+                                                           nullptr, 0, W.w, W.pb, 0, W.N, W.done);
+                    k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, k,
+                                                           nullptr, 1, W.w, W.pa, 1, W.N, W.done);
+                    k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
+                        W.pa, nb, ld, W.H, m + 2, k, nullptr, 1, W.cs, W.sn, W.g, W.par, W.done,
+                        W.iters, W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad,
+                        W.pb, W.N);
+                    s->launch_total += 4;
                 }
-                double* vk = W.V + (size_t)k * ldv;
-                double* vk1 = W.V + (size_t)(k + 1) * ldv;
-                double* hk = W.H + (size_t)k * (m + 2);
-                // W.tmp = R~ v_k (sources already prepared when fuse_prep)
-                pm_status stt = pm_apply_dev(s, 0, 1, 1, vk, W.tmp, prec, st, fuse_prep ? 1 : 0);
-                if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
-                // partials ping-pong between W.pb and W.pa
-                k_arn_first<<<nb, kArnThreads, 0, st>>>(vk, W.tmp, W.pb, nb, ld, W.V, ldv, k + 1,
-                                                        W.w, W.pa, W.N, W.done);
-                k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, k + 1, hk, 0, W.w,
-                                                       W.pb, 0, W.N, W.done);
-                k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, k + 1, hk, 1, W.w,
-                                                       W.pa, 1, W.N, W.done);
-                k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
-                    W.pa, nb, ld, W.H, m + 2, k, W.cs, W.sn, W.g, tol_abs, W.done, W.iters, W.w,
-                    vk1, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, W.N);
-                s->launch_total += 4;
+                s->skip_flag = nullptr;
+                PM_CUDA_TRY(cudaGetLastError());
+                k_backsolve<<<1, 1, 0, st>>>(W.H, m + 2, W.g, W.iters, W.y);
+                k_add_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, W.iters, W.y, W.delta, W.N);
+                s->launch_total += 2;
             }
-            s->skip_flag = nullptr;
-            PM_CUDA_TRY(cudaGetLastError());
-            k_backsolve<<<1, 1, 0, st>>>(W.H, m + 2, W.g, W.iters, W.y);
-            s->launch_total++;
-            k_add_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, W.iters, W.y, W.delta, W.N);
-            s->launch_total++;
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + 1, W.done, sizeof(int), cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaStreamSynchronize(st));
             const int it = W.pinned_i[0];
             const int converged = W.pinned_i[1];
+            if (graph) s->launch_total += 4 + (long long)it * W.body_launches;
             total += it;
             if (converged || it == 0) break;
             // cycle exhausted: restart from the residual of the operator in use
