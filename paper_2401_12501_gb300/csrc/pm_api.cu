@@ -267,7 +267,7 @@ static void free_surface(pm_surface* s) {
     pm_dfree(s->a); pm_dfree(s->g); pm_dfree(s->wa); pm_dfree(s->src32); pm_dfree(s->tgt32);
     pm_dfree(s->src64); pm_dfree(s->cR64); pm_dfree(s->cK64); pm_dfree(s->cR32);
     pm_dfree(s->cK32); pm_dfree(s->partial); pm_dfree(s->sig32);
-    pm_dfree(s->src_ff); pm_dfree(s->tgt_ff); pm_dfree(s->log_tab);
+    pm_dfree(s->src_ff); pm_dfree(s->tgt_ff); pm_dfree(s->src_kg); pm_dfree(s->log_tab);
     pm_dfree(s->dbuf_in); pm_dfree(s->dbuf_out);
     for (auto& ev : s->prof_events) {
         cudaEventDestroy(ev.second.first);

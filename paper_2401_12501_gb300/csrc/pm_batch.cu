@@ -12,6 +12,7 @@
 // and Givens rotations, per-RHS convergence flags); iterative refinement uses
 // batched float-float residuals; u = K~ sigma uses the batched float-float
 // parametrix sum.
+#include "pm_ff.cuh"
 #include "pm_internal.cuh"
 
 #include <algorithm>
@@ -186,84 +187,16 @@ k_near_multi32(int N, int ppad, int npatch, const int* __restrict__ row_ptr,
 }
 
 // ------------------------------------------------------------------ float-float batched sums
-struct ff {
-    float h, l;
-};
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    e = b - (s - a);
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    e += a.l + b.l;
-    ff r;
-    fast_two_sum(s, e, r.h, r.l);
-    return r;
-}
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.h, -b.l}); }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    ff r;
-    fast_two_sum(p, e, r.h, r.l);
-    return r;
-}
-__device__ __forceinline__ ff ff_sqr(ff a) {
-    const float p = a.h * a.h;
-    float e = fmaf(a.h, a.h, -p);
-    e = fmaf(2.f * a.h, a.l, e);
-    ff r;
-    fast_two_sum(p, e, r.h, r.l);
-    return r;
-}
-__device__ __forceinline__ ff ff_rcp(ff a) {
-    const float y = rcp_approx(a.h);
-    const float p = a.h * y;
-    const float ep = fmaf(a.h, y, -p);
-    const float res = ((1.f - p) - ep) - a.l * y;
-    ff r;
-    fast_two_sum(y, y * res, r.h, r.l);
-    return r;
-}
-// float-float natural logarithm, same table method as the single-RHS kernels
-__device__ __forceinline__ ff ff_log(ff x, const float4* __restrict__ tab) {
-    int e;
-    const float mh = frexpf(x.h, &e);
-    const float sc = ldexpf(1.f, -e + 1);
-    ff m{mh * 2.f, x.l * sc};
-    e -= 1;
-    const int k = (int)((m.h - 1.f) * 128.f);
-    const float4 T = tab[min(max(k, 0), 127)];
-    const ff p = ff_mul(m, ff{T.x, T.y});
-    float th, tl;
-    fast_two_sum(p.h - 1.f, p.l, th, tl);
-    const ff t{th, tl};
-    const ff t2 = ff_sqr(t);
-    const float tf = t.h;
-    const float poly = fmaf(fmaf(fmaf(-1.f / 6.f, tf, 0.2f), tf, -0.25f), tf, 1.f / 3.f);
-    const float cubic = tf * tf * tf * poly;
-    const float L2H = 0.693147182464599609375f;
-    const float L2L = -1.904654323148236e-09f;
-    const float ef = (float)e;
-    const float lp = L2H * ef;
-    float le = fmaf(L2H, ef, -lp);
-    le = fmaf(L2L, ef, le);
-    ff r;
-    fast_two_sum(lp, le, r.h, r.l);
-    r = ff_add(r, ff{T.z, T.w});
-    r = ff_add(r, t);
-    r = ff_add(r, ff{-0.5f * t2.h, -0.5f * t2.l});
-    r = ff_add(r, ff{cubic, 0.f});
-    return r;
-}
+// (arithmetic and the coordinate split in pm_ff.cuh)
+using pmff::ff;
+using pmff::ff_add_lazy;
+using pmff::ff_log_lazy;
+using pmff::ff_mul;
+using pmff::ff_mul_lazy;
+using pmff::ff_norm;
+using pmff::ff_rcp_lazy;
+using pmff::ff_sqr_lazy;
+using pmff::fast_two_sum;
 
 // float-float strengths: sff[r][j] = (hi, lo) of w_j sigma_r[j] / a_j
 __global__ void k_prep_ff_multi(const double* __restrict__ sigma, long long ld_sigma,
@@ -278,6 +211,9 @@ __global__ void k_prep_ff_multi(const double* __restrict__ sigma, long long ld_s
     sff[(size_t)r * N + j] = make_float2(h, (float)(v - (double)h));
 }
 
+// src_ff: source coordinates (their .w strengths are not read; sff holds the
+// strengths of every right-hand side) -- plain float-float pairs for the
+// remainder, the grid split for the parametrix (pm_ffsum.cu)
 template <bool KERNEL_K>
 __global__ void __launch_bounds__(kThreads)
 k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ sff, int nrhs,
@@ -297,7 +233,12 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
     if (KERNEL_K)
         for (int k = tid; k < 128; k += kThreads) stab[k] = log_tab[k];
     ff X[3], NP[3], MM[3];
-    {
+    if (KERNEL_K) {
+        // src_ff = grid-split coordinates (pm_ffsum.cu); the target's own entry gives X
+        const float4 a = (i < N) ? src_ff[2 * (size_t)i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = (i < N) ? src_ff[2 * (size_t)i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        X[0] = ff{a.x, b.x}; X[1] = ff{a.y, b.y}; X[2] = ff{a.z, b.z};
+    } else {
         float4 v[6];
         for (int q = 0; q < 6; ++q) v[q] = (i < N) ? tg[6 * (size_t)i + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         X[0] = ff{v[0].x, v[1].x}; X[1] = ff{v[0].y, v[1].y}; X[2] = ff{v[0].z, v[1].z};
@@ -322,18 +263,22 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
         for (int j = 0; j < len; ++j) {
             if (own && base + j == i) continue;
             const float4 A = sh[2 * j], B = sh[2 * j + 1];
-            const ff dx = ff_sub(X[0], ff{A.x, B.x});
-            const ff dy = ff_sub(X[1], ff{A.y, B.y});
-            const ff dz = ff_sub(X[2], ff{A.z, B.z});
-            const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+            const ff dx = KERNEL_K ? pmff::ff_grid_sub(X[0], A.x, B.x) : pmff::ff_sub(X[0], ff{A.x, B.x});
+            const ff dy = KERNEL_K ? pmff::ff_grid_sub(X[1], A.y, B.y) : pmff::ff_sub(X[1], ff{A.y, B.y});
+            const ff dz = KERNEL_K ? pmff::ff_grid_sub(X[2], A.z, B.z) : pmff::ff_sub(X[2], ff{A.z, B.z});
+            const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
             ff gfac;
             if (KERNEL_K) {
-                gfac = ff_log(r2, stab);
+                gfac = ff_norm(ff_log_lazy(r2, stab));
             } else {
-                const ff inv = ff_rcp(r2);
-                const ff nr2 = ff_add(ff_add(ff_mul(NP[0], dx), ff_mul(NP[1], dy)), ff_mul(NP[2], dz));
-                const ff mr = ff_add(ff_add(ff_mul(MM[0], dx), ff_mul(MM[1], dy)), ff_mul(MM[2], dz));
-                gfac = ff_mul(inv, ff_add(ff_mul(nr2, ff_mul(nr2, inv)), mr));
+                const ff inv = ff_rcp_lazy(r2);
+                const ff nr2 = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
+                                                               ff_mul_lazy(NP[1], dy)),
+                                                   ff_mul_lazy(NP[2], dz)));
+                const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
+                                          ff_mul_lazy(MM[2], dz));
+                const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr2, ff_mul_lazy(nr2, inv)), mr));
+                gfac = ff_mul(inv, inner);
             }
 #pragma unroll
             for (int q = 0; q < kRBff; ++q) {
@@ -456,7 +401,7 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
             dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, kRBff));
             const int chunk = pm_ceil_div(N, ns);
             if (kernel_K)
-                k_direct_multi_ff<true><<<g, kThreads, 0, st>>>(s->src_ff, B.sff, nrhs, s->tgt_ff,
+                k_direct_multi_ff<true><<<g, kThreads, 0, st>>>(s->src_kg, B.sff, nrhs, s->tgt_ff,
                                                                s->log_tab, N, chunk, B.part, ns, skip);
             else
                 k_direct_multi_ff<false><<<g, kThreads, 0, st>>>(s->src_ff, B.sff, nrhs, s->tgt_ff,

@@ -2,24 +2,17 @@
 //
 // GB300 executes float64 at a small fraction of its float32 rate, so the
 // accurate remainder and parametrix sums used for true residuals and for the
-// representation u = K~ sigma are evaluated in float-float arithmetic: every
-// quantity is an unevaluated sum hi + lo of two floats (about 48 significant
-// bits).  The primitives are the error-free transformations TwoSum (Knuth)
-// and TwoProduct via FMA, composed into the usual double-word add, multiply
-// and reciprocal (one Newton step from the hardware reciprocal).
-//
-// The natural logarithm of a float-float number follows Tang's table-driven
-// method ("Table-driven implementation of the logarithm function in IEEE
-// floating-point arithmetic", ACM TOMS 16, 1990): x = 2^e m, m in [1, 2);
-// m = c_k (1 + t) with c_k = 1 + (k + 1/2)/128 taken from the top seven
-// mantissa bits, so |t| <= 2^-8; ln x = e ln 2 + ln c_k + ln(1 + t), with
-// ln(1 + t) = t - t^2/2 + t^3 (1/3 - t/4 + t^2/5 - t^3/6) (truncation below
-// 2^-56).  The table of ln c_k and 1/c_k is computed on the host in float64.
+// representation u = K~ sigma are evaluated in float-float arithmetic (every
+// quantity an unevaluated sum hi + lo of two floats, about 48 significant
+// bits; the arithmetic, the logarithm and the coordinate split are in
+// pm_ff.cuh).  The table of ln c_k and 1/c_k for the logarithm is computed on
+// the host in float64.
 //
 // Kernels mirror the float32 ones (pm_direct.cu): 128 threads, one target
 // per thread, sources staged in shared memory, source chunks over gridDim.y,
 // (hi, lo) partials combined by the float64 near-field kernel.  The self
 // pair is excluded explicitly in the tile that holds the block's targets.
+#include "pm_ff.cuh"
 #include "pm_internal.cuh"
 
 #include <algorithm>
@@ -27,140 +20,31 @@
 
 namespace {
 
+using namespace pmff;
+
 constexpr int kThreads = 128;
 constexpr int kStage = 512;        // sources per shared-memory stage (2 float4 each)
-constexpr int kLogTable = 128;
-
-struct ff {
-    float h, l;
-};
-
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    e = b - (s - a);
-}
-
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    ff r;
-    fast_two_sum(p, e, r.h, r.l);
-    return r;
-}
-
-// Unnormalised variants: the low word may exceed half an ulp of the high word.
-// Products of such pairs keep float-float accuracy only while the low word
-// stays within a few ulps of the high word, so every sum that can cancel
-// (differences, dot products, the bracket of the remainder term) is
-// renormalised before it is multiplied; sums of positive terms (r^2) and the
-// reciprocal and logarithm, whose low words stay small, are not.
-__device__ __forceinline__ ff ff_mul_lazy(ff a, ff b) {
-    const float p = a.h * b.h;
-    float e = fmaf(a.h, b.h, -p);
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return ff{p, e};
-}
-__device__ __forceinline__ ff ff_sqr_lazy(ff a) {
-    const float p = a.h * a.h;
-    float e = fmaf(a.h, a.h, -p);
-    e = fmaf(2.f * a.h, a.l, e);
-    return ff{p, e};
-}
-__device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    return ff{s, e + (a.l + b.l)};
-}
-__device__ __forceinline__ ff ff_norm(ff a) {
-    ff r;
-    fast_two_sum(a.h, a.l, r.h, r.l);
-    return r;
-}
-
-// a - b, normalised: where the high words cancel the low word would otherwise
-// be as large as the high word, and products with it would lose the l^2 term
-__device__ __forceinline__ ff ff_sub(ff a, ff b) {
-    float s, e;
-    two_sum(a.h, -b.h, s, e);
-    return ff_norm(ff{s, e + (a.l - b.l)});
-}
-
-// 1/a: y = rcp(a.h) and one Newton step y + y (1 - a y), the residual 1 - a y
-// formed with the exact product a.h y = p + ep; returned unnormalised as (y, y res)
-__device__ __forceinline__ ff ff_rcp_lazy(ff a) {
-    const float y = rcp_approx(a.h);
-    const float p = a.h * y;
-    const float ep = fmaf(a.h, y, -p);
-    const float res = ((1.f - p) - ep) - a.l * y;
-    return ff{y, y * res};
-}
-
-// ln(x) for x = hi + lo > 0 (Tang's table method, see the file header):
-// tab[k] = (1/c_k hi, 1/c_k lo, ln c_k hi, ln c_k lo).  The parts e ln 2,
-// ln c_k, t and -t^2/2 + t^3 (...) are summed with error-free high words and
-// plain low words; the result is left unnormalised.
-__device__ __forceinline__ ff ff_log_lazy(ff x, const float4* __restrict__ tab) {
-    int e;
-    const float mh = frexpf(x.h, &e);
-    const float sc = ldexpf(1.f, -e + 1);
-    ff m{mh * 2.f, x.l * sc};
-    e -= 1;
-    const int k = (int)((m.h - 1.f) * (float)kLogTable);
-    const float4 T = tab[min(max(k, 0), kLogTable - 1)];
-    const ff p = ff_mul(m, ff{T.x, T.y});
-    float th, tl;
-    fast_two_sum(p.h - 1.f, p.l, th, tl);
-    const ff t{th, tl};
-    const ff t2 = ff_sqr_lazy(t);
-    const float tf = t.h;
-    const float poly = fmaf(fmaf(fmaf(-1.f / 6.f, tf, 0.2f), tf, -0.25f), tf, 1.f / 3.f);
-    const float cubic = tf * tf * tf * poly;
-    const float L2H = 0.693147182464599609375f;
-    const float L2L = -1.904654323148236e-09f;
-    const float ef = (float)e;
-    const float eh = L2H * ef;
-    const ff el{eh, fmaf(L2H, ef, -eh) + L2L * ef};    // e ln 2; the FMA recovers L2H e exactly
-    ff r = ff_add_lazy(el, ff{T.z, T.w});
-    r = ff_add_lazy(r, t);
-    r = ff_add_lazy(r, ff{-0.5f * t2.h, fmaf(-0.5f, t2.l, cubic)});
-    return r;
-}
-
-__device__ __forceinline__ ff ff_from_double(double v) {
-    const float h = (float)v;
-    return ff{h, (float)(v - (double)h)};
-}
 
 // -------------------------------------------------------------------- packing
 // sources: src_ff[2j] = (xh, yh, zh, s_h), src_ff[2j+1] = (xl, yl, zl, s_l)
 // targets: tg_ff[6i + 0..5] = x (hi, lo), n' (hi, lo), m (hi, lo), each (.x, .y, .z)
+// parametrix sums: src_kg[2j], src_kg[2j+1] as src_ff with the coordinates
+// split on the grid (pm_ff.cuh); targets read their coordinates from it too.
+// The remainder sums keep plain float-float coordinates: its n' . r of nearby
+// points cancels to O(r^2), where the grid split's absolute error would show.
 __global__ void k_pack_ff(const double* __restrict__ x, const double* __restrict__ n,
                           const double* __restrict__ H, const double* __restrict__ a,
-                          const double* __restrict__ g, float4* __restrict__ src,
-                          float4* __restrict__ tg, int N) {
+                          const double* __restrict__ g, double grid, float4* __restrict__ src,
+                          float4* __restrict__ tg, float4* __restrict__ src_kg, int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    ff c[3][3];
+    ff c[3][3], xg[3];
     const double c1 = sqrt(a[i] / M_PI), cH = -a[i] * H[i] / M_PI, c2 = 0.5 / M_PI;
     for (int d = 0; d < 3; ++d) {
         c[0][d] = ff_from_double(x[3 * i + d]);
         c[1][d] = ff_from_double(c1 * n[3 * i + d]);
         c[2][d] = ff_from_double(cH * n[3 * i + d] + c2 * g[3 * i + d]);
+        xg[d] = ff_grid_split(x[3 * i + d], grid);
     }
     for (int q = 0; q < 3; ++q) {
         tg[6 * (size_t)i + 2 * q] = make_float4(c[q][0].h, c[q][1].h, c[q][2].h, 0.f);
@@ -168,16 +52,21 @@ __global__ void k_pack_ff(const double* __restrict__ x, const double* __restrict
     }
     src[2 * (size_t)i] = make_float4(c[0][0].h, c[0][1].h, c[0][2].h, 0.f);
     src[2 * (size_t)i + 1] = make_float4(c[0][0].l, c[0][1].l, c[0][2].l, 0.f);
+    src_kg[2 * (size_t)i] = make_float4(xg[0].h, xg[1].h, xg[2].h, 0.f);
+    src_kg[2 * (size_t)i + 1] = make_float4(xg[0].l, xg[1].l, xg[2].l, 0.f);
 }
 
 __global__ void k_prep_ff(const double* __restrict__ sigma, const double* __restrict__ wa,
-                          float4* __restrict__ src, int N, const int* __restrict__ skip) {
+                          float4* __restrict__ src, float4* __restrict__ src_kg, int N,
+                          const int* __restrict__ skip) {
     if (skip && *skip) return;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const ff s = ff_from_double(wa[j] * sigma[j]);
     src[2 * (size_t)j].w = s.h;
     src[2 * (size_t)j + 1].w = s.l;
+    src_kg[2 * (size_t)j].w = s.h;
+    src_kg[2 * (size_t)j + 1].w = s.l;
 }
 
 // -------------------------------------------------------------------- sums
@@ -195,7 +84,12 @@ k_direct_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
     if (KERNEL_K)
         for (int k = tid; k < kLogTable; k += kThreads) stab[k] = log_tab[k];
     ff X[3], NP[3], MM[3];
-    {
+    if (KERNEL_K) {
+        // src = grid-split coordinates; the target's own entry gives X
+        const float4 a = (i < N) ? src[2 * (size_t)i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = (i < N) ? src[2 * (size_t)i + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        X[0] = ff{a.x, b.x}; X[1] = ff{a.y, b.y}; X[2] = ff{a.z, b.z};
+    } else {
         float4 v[6];
         for (int q = 0; q < 6; ++q) v[q] = (i < N) ? tg[6 * (size_t)i + q] : make_float4(0.f, 0.f, 0.f, 0.f);
         X[0] = ff{v[0].x, v[1].x}; X[1] = ff{v[0].y, v[1].y}; X[2] = ff{v[0].z, v[1].z};
@@ -214,9 +108,9 @@ k_direct_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
         for (int j = 0; j < len; ++j) {
             const float4 A = sh[2 * j], B = sh[2 * j + 1];
             if (own && base + j == i) continue;
-            const ff dx = ff_sub(X[0], ff{A.x, B.x});
-            const ff dy = ff_sub(X[1], ff{A.y, B.y});
-            const ff dz = ff_sub(X[2], ff{A.z, B.z});
+            const ff dx = KERNEL_K ? ff_grid_sub(X[0], A.x, B.x) : ff_sub(X[0], ff{A.x, B.x});
+            const ff dy = KERNEL_K ? ff_grid_sub(X[1], A.y, B.y) : ff_sub(X[1], ff{A.y, B.y});
+            const ff dz = KERNEL_K ? ff_grid_sub(X[2], A.z, B.z) : ff_sub(X[2], ff{A.z, B.z});
             const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
             const ff s{A.w, B.w};
             ff term;
@@ -275,20 +169,31 @@ pm_status pm_ff_setup(pm_surface* s) {
     if (!s->src_ff) {
         PM_TRY(pm_dmalloc(&s->src_ff, 2 * (size_t)s->N));
         PM_TRY(pm_dmalloc(&s->tgt_ff, 6 * (size_t)s->N));
+        PM_TRY(pm_dmalloc(&s->src_kg, 2 * (size_t)s->N));
     }
     return PM_OK;
 }
 
+// Grid of the coordinate split: 2^(E - 22) with 2^E >= max |x| (pm_ff.cuh), so a
+// high word has at most 23 significant bits and two of them differ exactly.
+double pm_ff_grid(const pm_surface* s) {
+    int E = 0;
+    const double f = std::frexp(std::max(s->h_far, 1e-300), &E);
+    if (f == 0.5) E -= 1;                     // max |x| a power of two: 2^E = max |x|
+    return std::ldexp(1.0, E - 22);
+}
+
 pm_status pm_pack_ff(pm_surface* s, cudaStream_t st) {
     PM_TRY(pm_ff_setup(s));
-    k_pack_ff<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->src_ff,
-                                                       s->tgt_ff, s->N);
+    k_pack_ff<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->x, s->n, s->H, s->a, s->g,
+                                                       pm_ff_grid(s), s->src_ff, s->tgt_ff, s->src_kg,
+                                                       s->N);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
 
 pm_status pm_prep_ff(pm_surface* s, const double* sigma, cudaStream_t st) {
-    k_prep_ff<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(sigma, s->wa, s->src_ff, s->N,
+    k_prep_ff<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(sigma, s->wa, s->src_ff, s->src_kg, s->N,
                                                        s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -307,7 +212,7 @@ pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st) 
     dim3 grid(pm_ceil_div(N, kThreads), nsplit);
     float2* part = reinterpret_cast<float2*>(s->partial);
     if (which_K)
-        k_direct_ff<true><<<grid, kThreads, 0, st>>>(s->src_ff, s->tgt_ff, s->log_tab, N, chunk,
+        k_direct_ff<true><<<grid, kThreads, 0, st>>>(s->src_kg, s->tgt_ff, s->log_tab, N, chunk,
                                                      part, s->skip_flag);
     else
         k_direct_ff<false><<<grid, kThreads, 0, st>>>(s->src_ff, s->tgt_ff, s->log_tab, N, chunk,

@@ -119,6 +119,7 @@ struct pm_surface {
     pm_d4* src64 = nullptr;     // [Npad] (x, y, z, s)
     float4* src_ff = nullptr;     // [2N] float-float sources
     float4* tgt_ff = nullptr;     // [6N] float-float targets
+    float4* src_kg = nullptr;     // [2N] grid-split coordinates + strengths (parametrix sums)
     float4* log_tab = nullptr;    // [128] table of the float-float logarithm
     double* cR64 = nullptr;       // [nblk*pp]
     double* cK64 = nullptr;       // [nblk*pp]
