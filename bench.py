@@ -36,7 +36,7 @@ FLOPS_PER_PAIR_R = 26      # variable-a remainder pair (algorithmic count)
 # of the current kernel versions on this workload (profiles/k_direct_*_ellipsoid_9600.md);
 # set to None whenever the kernel changes until it is captured again.
 TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
-                 ("k_direct_ff_R", "ellipsoid_9600"): None}
+                 ("k_direct_ff_R", "ellipsoid_9600"): 1236224}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -150,6 +150,22 @@ def run_oracle_subprocess(workload: str, seconds: float):
 PHASES = ["prep", "direct_R32", "direct_K32", "near", "vec", "direct_ff_or_64"]
 
 
+def _nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def _nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def _phase_totals(surf, reset=True):
     out = {}
     for k, nm in enumerate(PHASES):
@@ -231,12 +247,14 @@ def run_gpu(args, rank, world, local_rank):
            for _ in range(args.steps)]
     surf.profile(True)
     surf.profile_read(0, reset=True)
+    _nvtx_push("solve_profiled_pass")           # ncu --nvtx-include selects these launches
     for k in range(args.steps):
         flush.fill_(float(k))
         pev[k][0].record(stream)
         step()
         pev[k][1].record(stream)
     torch.cuda.synchronize()
+    _nvtx_pop()
     surf.profile(False)
     ph = _phase_totals(surf)
     prof_total_ms = sum(a.elapsed_time(b) for a, b in pev)
