@@ -94,6 +94,11 @@ typedef struct {
     int direct_tpt;         /* float32 smooth sums: targets per thread (1, 2 or 4); 0 = auto */
     int direct_blocks_per_sm; /* float32 smooth sums: source splits chosen so the grid holds
                                about this many blocks per SM (1..16); 0 = auto          */
+    int direct_symmetric;   /* float-float smooth sums: 1 = evaluate each
+                               unordered node pair once (tile pairs; row and column sums
+                               from the shared pair geometry) where the (N/128) x N
+                               partial slices fit in 96 MB, else one-sided sums (default);
+                               0 = one-sided sums always                                */
 } pm_opts;
 
 void pm_default_opts(pm_opts* opts);

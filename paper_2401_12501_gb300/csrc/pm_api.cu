@@ -63,6 +63,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->batch_rhs = 1;
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
+    o->direct_symmetric = 1;
 }
 
 // ----------------------------------------------------------------------------- tables
@@ -390,7 +391,7 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     PM_STEP(pm_near_build(s, T));
 
     // scratch for the smooth sums
-    s->max_split = 32;
+    s->max_split = std::max(32, pm_sym_tiles(s));     // one slice per tile for the symmetric sums
     PM_STEP(pm_dmalloc(&s->partial, (size_t)s->max_split * N));
     PM_STEP(pm_dmalloc(&s->sig32, (size_t)npatch * s->ppad));
     PM_CSTEP(cudaMemset(s->sig32, 0, sizeof(float) * (size_t)npatch * s->ppad));
@@ -529,7 +530,11 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
         PhaseTimer t(s, prec == PM_PREC_FP64 || prec == PM_PREC_FF
                             ? PM_PHASE_DIRECT64
                             : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
-        if (prec == PM_PREC_FF) {
+        const int nt = pm_sym_tiles(s);
+        if (prec == PM_PREC_FF && nt > 0) {
+            nsplit = nt;
+            PM_TRY(pm_sym_ff(s, kernel_K, st));
+        } else if (prec == PM_PREC_FF) {
             nsplit = pm_ff_splits(s);
             PM_TRY(pm_direct_ff(s, kernel_K, nsplit, st));
         } else if (prec == PM_PREC_FMM) {

@@ -585,12 +585,12 @@ __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
     if (warp >= N) return;
     const int i = warp;
     double acc = 0.0;
-    if (lane < nsplit) {
+    for (int sp = lane; sp < nsplit; sp += 32) {
         if (partial_ff) {
-            const float2 v = reinterpret_cast<const float2*>(partial)[(size_t)lane * N + i];
-            acc = (double)v.x + (double)v.y;
+            const float2 v = reinterpret_cast<const float2*>(partial)[(size_t)sp * N + i];
+            acc += (double)v.x + (double)v.y;
         } else {
-            acc = partial[(size_t)lane * N + i];
+            acc += partial[(size_t)sp * N + i];
         }
     }
     if (use_near) {
