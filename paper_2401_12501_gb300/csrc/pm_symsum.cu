@@ -71,6 +71,80 @@ __device__ __forceinline__ void tile_pair(int p, int nt, int& a, int& b) {
 // has visited all 32 targets of the warp and sits on lane (its source mod 32).
 // Rotation costs two shuffles per step instead of a per-source warp reduction.
 template <bool KERNEL_K>
+struct SymCtx {
+    const float4 *sA, *sB, *sNh, *sNl, *sMh, *sMl, *stab;
+    const ff *X, *NP, *MM;
+    ff si;
+};
+
+// The pair loop of one block; DIAG: tile against itself, rows only, the self
+// pair evaluated at a unit offset with zero strength (exactly zero).
+template <bool KERNEL_K, bool DIAG>
+__device__ __forceinline__ void sym_loop(const SymCtx<KERNEL_K>& C, int lane, int tid, ff& acc,
+                                         ff* colv) {
+    const int src_lane_next = (lane + 1) & 31;
+    const ff X0 = C.X[0], X1 = C.X[1], X2 = C.X[2];
+#pragma unroll
+    for (int c = 0; c < kW; ++c) {
+        ff cacc{0.f, 0.f};                         // column sum of the source evaluated next
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+            const int q = c * 32 + ((lane + k) & 31);
+            const float4 A = C.sA[q], B = C.sB[q];
+            const ff dx = KERNEL_K ? ff_grid_sub(X0, A.x, B.x) : ff_sub(X0, ff{A.x, B.x});
+            const ff dy = KERNEL_K ? ff_grid_sub(X1, A.y, B.y) : ff_sub(X1, ff{A.y, B.y});
+            const ff dz = KERNEL_K ? ff_grid_sub(X2, A.z, B.z) : ff_sub(X2, ff{A.z, B.z});
+            ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
+            ff sj{A.w, B.w};
+            if (DIAG && q == tid) {
+                r2 = ff{1.f, 0.f};
+                sj = ff{0.f, 0.f};
+            }
+            ff row, col{0.f, 0.f};
+            if (KERNEL_K) {
+                const ff L = ff_norm(ff_log_lazy(r2, C.stab));
+                row = ff_mul_lazy(sj, L);
+                if (!DIAG) col = ff_mul_lazy(C.si, L);
+            } else {
+                const ff inv = ff_rcp_lazy(r2);
+                const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(C.NP[0], dx),
+                                                              ff_mul_lazy(C.NP[1], dy)),
+                                                  ff_mul_lazy(C.NP[2], dz)));
+                const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(C.MM[0], dx),
+                                                      ff_mul_lazy(C.MM[1], dy)),
+                                          ff_mul_lazy(C.MM[2], dz));
+                const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, ff_mul_lazy(nr, inv)), mr));
+                row = ff_mul_lazy(ff_mul_lazy(sj, inv), inner);
+                if (!DIAG) {
+                    const float4 nh = C.sNh[q], nl = C.sNl[q], mh = C.sMh[q], ml = C.sMl[q];
+                    const ff nrj = ff_norm(ff_add_lazy(
+                        ff_add_lazy(ff_mul_lazy(ff{nh.x, nl.x}, dx), ff_mul_lazy(ff{nh.y, nl.y}, dy)),
+                        ff_mul_lazy(ff{nh.z, nl.z}, dz)));
+                    const ff mrj = ff_add_lazy(
+                        ff_add_lazy(ff_mul_lazy(ff{mh.x, ml.x}, dx), ff_mul_lazy(ff{mh.y, ml.y}, dy)),
+                        ff_mul_lazy(ff{mh.z, ml.z}, dz));
+                    // reversed pair: r -> -r, so (n'_j . r)^2 is unchanged and m_j . r flips
+                    const ff innerj = ff_norm(ff_add_lazy(ff_mul_lazy(nrj, ff_mul_lazy(nrj, inv)),
+                                                          ff{-mrj.h, -mrj.l}));
+                    col = ff_mul_lazy(ff_mul_lazy(C.si, inv), innerj);
+                }
+            }
+            // row: TwoSum on the high words, error terms in the low word
+            const float t = acc.h + row.h;
+            const float bp = t - acc.h;
+            acc.l += ((acc.h - (t - bp)) + (row.h - bp)) + row.l;
+            acc.h = t;
+            if (!DIAG) {
+                cacc = ff_add_lazy(cacc, col);
+                cacc = ff{__shfl_sync(0xffffffffu, cacc.h, src_lane_next),
+                          __shfl_sync(0xffffffffu, cacc.l, src_lane_next)};
+            }
+        }
+        colv[c] = cacc;                            // column c * 32 + lane of this warp's targets
+    }
+}
+
+template <bool KERNEL_K>
 __global__ void __launch_bounds__(kT)
 k_sym_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
          const float4* __restrict__ log_tab, int N, int nt, float far_h, float far_l,
@@ -123,65 +197,13 @@ k_sym_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
     }
     __syncthreads();
     const bool diag = (a == b);
-    const int src_lane_next = (lane + 1) & 31;
     ff acc{0.f, 0.f};
     ff colv[kW];
-#pragma unroll
-    for (int c = 0; c < kW; ++c) {
-        ff cacc{0.f, 0.f};                         // column sum of the source evaluated next
-        for (int k = 0; k < 32; ++k) {
-            const int q = c * 32 + ((lane + k) & 31);
-            const bool self = diag && q == tid;
-            const float4 A = sA[q], B = sB[q];
-            const ff dx = KERNEL_K ? ff_grid_sub(X[0], A.x, B.x) : ff_sub(X[0], ff{A.x, B.x});
-            const ff dy = KERNEL_K ? ff_grid_sub(X[1], A.y, B.y) : ff_sub(X[1], ff{A.y, B.y});
-            const ff dz = KERNEL_K ? ff_grid_sub(X[2], A.z, B.z) : ff_sub(X[2], ff{A.z, B.z});
-            // the self pair (diagonal blocks only) is evaluated at a unit offset and dropped
-            const ff r2 = self ? ff{1.f, 0.f}
-                               : ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)),
-                                             ff_sqr_lazy(dz));
-            const ff sj{self ? 0.f : A.w, self ? 0.f : B.w};
-            ff row, col{0.f, 0.f};
-            if (KERNEL_K) {
-                const ff L = ff_norm(ff_log_lazy(r2, stab));
-                row = ff_mul_lazy(sj, L);
-                if (!diag) col = ff_mul_lazy(si, L);
-            } else {
-                const ff inv = ff_rcp_lazy(r2);
-                const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
-                                                              ff_mul_lazy(NP[1], dy)),
-                                                  ff_mul_lazy(NP[2], dz)));
-                const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
-                                          ff_mul_lazy(MM[2], dz));
-                const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, ff_mul_lazy(nr, inv)), mr));
-                row = ff_mul_lazy(ff_mul_lazy(sj, inv), inner);
-                if (!diag) {
-                    const float4 nh = sNh[q], nl = sNl[q], mh = sMh[q], ml = sMl[q];
-                    const ff nrj = ff_norm(ff_add_lazy(
-                        ff_add_lazy(ff_mul_lazy(ff{nh.x, nl.x}, dx), ff_mul_lazy(ff{nh.y, nl.y}, dy)),
-                        ff_mul_lazy(ff{nh.z, nl.z}, dz)));
-                    const ff mrj = ff_add_lazy(
-                        ff_add_lazy(ff_mul_lazy(ff{mh.x, ml.x}, dx), ff_mul_lazy(ff{mh.y, ml.y}, dy)),
-                        ff_mul_lazy(ff{mh.z, ml.z}, dz));
-                    // reversed pair: r -> -r, so (n'_j . r)^2 is unchanged and m_j . r flips
-                    const ff innerj = ff_norm(ff_add_lazy(ff_mul_lazy(nrj, ff_mul_lazy(nrj, inv)),
-                                                          ff{-mrj.h, -mrj.l}));
-                    col = ff_mul_lazy(ff_mul_lazy(si, inv), innerj);
-                }
-            }
-            // row: TwoSum on the high words, error terms in the low word
-            const float t = acc.h + row.h;
-            const float bp = t - acc.h;
-            acc.l += ((acc.h - (t - bp)) + (row.h - bp)) + row.l;
-            acc.h = t;
-            if (!diag) {
-                cacc = ff_add_lazy(cacc, col);
-                cacc = ff{__shfl_sync(0xffffffffu, cacc.h, src_lane_next),
-                          __shfl_sync(0xffffffffu, cacc.l, src_lane_next)};
-            }
-        }
-        colv[c] = cacc;                            // column c * 32 + lane of this warp's targets
-    }
+    const SymCtx<KERNEL_K> C{sA, sB, sNh, sNl, sMh, sMl, stab, X, NP, MM, si};
+    if (diag)
+        sym_loop<KERNEL_K, true>(C, lane, tid, acc, colv);
+    else
+        sym_loop<KERNEL_K, false>(C, lane, tid, acc, colv);
     const float scale_h = KERNEL_K ? (float)(1.0 / (4.0 * M_PI)) : 1.f;
     const float scale_l = KERNEL_K ? (float)(1.0 / (4.0 * M_PI) - (double)(float)(1.0 / (4.0 * M_PI))) : 0.f;
     if (i < N) {
