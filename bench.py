@@ -36,7 +36,9 @@ FLOPS_PER_PAIR_R = 26      # variable-a remainder pair (algorithmic count)
 # of the current kernel versions on this workload (profiles/k_direct_*_ellipsoid_9600.md);
 # set to None whenever the kernel changes until it is captured again.
 TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
-                 ("k_direct_ff_R", "ellipsoid_9600"): 1236224}
+                 ("k_direct_ff_R", "ellipsoid_9600"): 1236224,
+                 ("k_sym_ff_R", "ellipsoid_9600"): 1299712}
+SYM_PARTIAL_CAP = 96 * 1024 * 1024      # the library's cap on symmetric-sum partial slices
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -312,14 +314,21 @@ def run_gpu(args, rank, world, local_rank):
            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts)",
            "step_time_share": round(fp32_ms / prof_total_ms, 4)}
     ff_k = ff_ms / max(1, rf + 1) / args.steps if ff_n else 0.0
-    rff = {"bound": "alu", "kernel": "k_direct_ff (float-float remainder/parametrix sums)",
+    nt = -(-N // 128)
+    sym = N >= 256 and nt * N * 8 <= SYM_PARTIAL_CAP
+    ff_name = "k_sym_ff" if sym else "k_direct_ff"
+    rff = {"bound": "alu",
+           "kernel": ff_name + (" (symmetric tile-pair float-float remainder/parametrix sums)" if sym
+                                else " (float-float remainder/parametrix sums)"),
            "achieved": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12, 3) if ff_k else None,
            "peak": round(peak, 2), "unit": "TFLOP/s",
            "frac": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12 / peak, 4) if ff_k else None,
-           "traffic": TRAFFIC_BYTES.get(("k_direct_ff_R", args.workload)),
+           "traffic": TRAFFIC_BYTES.get((ff_name + "_R", args.workload)),
            "kernel_ms_per_apply": round(ff_k, 5),
-           "note": "algorithmic flops of the float64-class sum; each flop costs ~8 float32 "
-                   "instructions in float-float arithmetic",
+           "note": "algorithmic flops of the float64-class sum (26 per ordered pair) over the "
+                   "average of the step's float-float launches; float-float arithmetic costs "
+                   "~10 float32 instructions per algorithmic flop (274 per unordered pair for "
+                   "the remainder, 130 for the parametrix, each unordered pair evaluated once)",
            "step_time_share": round(ff_ms / prof_total_ms, 4)}
     dominant, other = (rff, r32) if ff_ms > fp32_ms else (r32, rff)
     line = {
