@@ -429,9 +429,11 @@ def run_fmm(args, dev):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         reps = 3
+        _nvtx_push("fmm_torus_" + prec)
         for _ in range(reps):
             s.apply_R(sig, prec, out=y)
         torch.cuda.synchronize()
+        _nvtx_pop()
         out[prec] = ((time.perf_counter() - t0) / reps, y.cpu().numpy())
     ex = out["ff"][1]
     res = {"workload": "torus_98304", "N": wl.N, "near_build_s": round(t_build, 3),
@@ -565,6 +567,8 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default="batched,fmm,served",
+                    help="comma-separated extra measurements to run (batched, fmm, served)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -612,8 +616,11 @@ def main():
     if rank == 0 and not args.no_extra:
         import torch
         dev = torch.device("cuda", local_rank)
-        for key, fn in (("batched_star_24576", run_batched), ("fmm_torus_98304", run_fmm),
-                        ("served", run_served)):
+        want = set(args.extras.split(","))
+        for name, key, fn in (("batched", "batched_star_24576", run_batched),
+                              ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served)):
+            if name not in want:
+                continue
             try:
                 line[key] = fn(args, dev)
             except Exception as e:  # report, do not hide

@@ -99,6 +99,10 @@ typedef struct {
                                from the shared pair geometry) where the (N/128) x N
                                partial slices fit in 96 MB, else one-sided sums (default);
                                0 = one-sided sums always                                */
+    int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as per-offset operator GEMMs on
+                               the tensor cores (float32 emulated on bfloat16, float32
+                               accumulation; operators ~3.3 GB per context, built once)
+                               (default); 0 = M2L evaluated directly on the float32 pipe */
 } pm_opts;
 
 void pm_default_opts(pm_opts* opts);

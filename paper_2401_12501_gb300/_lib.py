@@ -47,7 +47,8 @@ class PmOpts(C.Structure):
                 ("inner_tol", C.c_double), ("mean_tol", C.c_double),
                 ("residual_prec", C.c_int), ("fmm_depth", C.c_int), ("batch_rhs", C.c_int),
                 ("direct_tpt", C.c_int),
-                ("direct_blocks_per_sm", C.c_int), ("direct_symmetric", C.c_int)]
+                ("direct_blocks_per_sm", C.c_int), ("direct_symmetric", C.c_int),
+                ("fmm_tensor_m2l", C.c_int)]
 
 
 class PmSolveInfo(C.Structure):

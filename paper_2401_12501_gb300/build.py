@@ -57,7 +57,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
     if jobs or force or _newer(LIB, objs):
-        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs])
+        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lcublas"])
     return LIB
 
 

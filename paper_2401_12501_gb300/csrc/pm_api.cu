@@ -64,6 +64,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
     o->direct_symmetric = 1;
+    o->fmm_tensor_m2l = 1;
 }
 
 // ----------------------------------------------------------------------------- tables
@@ -250,7 +251,13 @@ extern "C" pm_status pm_ctx_create(int device, pm_ctx** out) {
     return PM_OK;
 }
 
-extern "C" void pm_ctx_destroy(pm_ctx* c) { delete c; }
+extern "C" void pm_ctx_destroy(pm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    pm_dfree(c->fmm_opR);
+    pm_dfree(c->fmm_opK);
+    delete c;
+}
 
 // ----------------------------------------------------------------------------- surfaces
 static void free_surface(pm_surface* s) {
@@ -538,7 +545,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
             nsplit = pm_ff_splits(s);
             PM_TRY(pm_direct_ff(s, kernel_K, nsplit, st));
         } else if (prec == PM_PREC_FMM) {
-            nsplit = 1;
+            nsplit = pm_fmm_splits();
             PM_TRY(pm_fmm_apply(s, kernel_K, st));
         } else {
             nsplit = pm_direct_splits(s, prec);

@@ -22,10 +22,14 @@
 //        (evaluated directly between the two boxes' Chebyshev points)
 //   L2L  L_C[c][k] += sum_l S^P_l(x^C_k) L_P[c][l]
 //   L2P  phi_c(x_i) = sum_l S_l(x_i) L_B[c][l], then the target combination
-//   P2P  leaf targets against the sources of the 27 adjacent leaves, exact kernel.
+//   P2P  leaf targets against the sources of the 27 adjacent leaves, exact kernel,
+//        one block per (leaf, neighbour); every term goes to its own partial slice
+//        (27 neighbours + the far field), which the near-field kernel adds.
 // Everything is float32 except the host-side tree; the near-field correction
 // (CSR) is added by the regular correction kernel.
 #include "pm_internal.cuh"
+
+#include <cublas_v2.h>
 
 #include <algorithm>
 #include <cmath>
@@ -267,27 +271,32 @@ k_fmm_l2l(DevTree t, int lev, float* __restrict__ Lc, const int* __restrict__ sk
     }
 }
 
-// L2P + P2P for one leaf: far field from the local expansion, near field by
-// the exact kernel over the U-list leaves; writes (hi, lo) for each target.
+// P2P for one (leaf, U-list neighbour) pair, blockIdx = (leaf, e): the exact
+// kernel between the leaf's targets and the sources of the e-th leaf of its U
+// list (the leaf itself included), written as (hi, lo) to partial slice e of
+// each target (zeros when the leaf has fewer than e + 1 neighbours).  Splitting
+// the near field by neighbour gives ~27 blocks per leaf of similar work.
+constexpr int kP2PThreads = 256;
+constexpr int kUMax = 27;                      // U list: the 3 x 3 x 3 leaves around a leaf
+
 template <bool KERNEL_K>
-__global__ void __launch_bounds__(kThreads)
-k_fmm_leaf(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ tgt,
-           const float* __restrict__ Lc, float eps2, float2* __restrict__ out,
-           const int* __restrict__ skip) {
+__global__ void __launch_bounds__(kP2PThreads)
+k_fmm_p2p(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ tgt, float eps2,
+          float2* __restrict__ out, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int leaf = blockIdx.x;
-    const int box = t.lev_off[t.depth] + leaf;
+    const int leaf = blockIdx.x, e = blockIdx.y;
     const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
-    const float h = t.L0 / (float)(1 << t.depth);
-    const float3 c = box_center(t, t.depth, t.box_ijk[box]);
-    const float sc = 2.f / h;
-    constexpr int C = KERNEL_K ? 1 : 9;
-    __shared__ float sLoc[C * kFmmN3];
-    __shared__ float4 sP[kThreads];
-    for (int e = threadIdx.x; e < C * kFmmN3; e += kThreads)
-        sLoc[e] = Lc[(size_t)box * C * kFmmN3 + e];
-    for (int base = p0; base < p1; base += kThreads) {
-        const int i = base + threadIdx.x;
+    const int ne = t.u_off[leaf + 1] - t.u_off[leaf];
+    float2* slice = out + (size_t)e * t.N;
+    if (e >= ne) {
+        for (int i = p0 + threadIdx.x; i < p1; i += kP2PThreads) slice[t.perm[i]] = make_float2(0.f, 0.f);
+        return;
+    }
+    const int ul = t.u_list[t.u_off[leaf] + e];
+    const int q0 = t.box_first[ul], q1 = t.box_first[ul + 1];
+    __shared__ float4 sP[kP2PThreads];
+    for (int tb = p0; tb < p1; tb += kP2PThreads) {
+        const int i = tb + threadIdx.x;
         const bool active = i < p1;
         float4 X = make_float4(0.f, 0.f, 0.f, 0.f), NN = X, MM = X;
         int orig = 0;
@@ -297,70 +306,184 @@ k_fmm_leaf(DevTree t, const float4* __restrict__ pts, const float4* __restrict__
             NN = tgt[t.N + orig];
             MM = tgt[2 * t.N + orig];
         }
-        __syncthreads();
-        // far field: phi_c(x) = sum_l S_l(x) L[c][l]
-        float far = 0.f;
-        if (active) {
-            float bx[kFmmN], by[kFmmN], bz[kFmmN];
-            cheb_basis((X.x - c.x) * sc, bx);
-            cheb_basis((X.y - c.y) * sc, by);
-            cheb_basis((X.z - c.z) * sc, bz);
-            float phi[C];
-#pragma unroll
-            for (int q = 0; q < C; ++q) phi[q] = 0.f;
-            for (int l1 = 0; l1 < kFmmN; ++l1)
-                for (int l2 = 0; l2 < kFmmN; ++l2) {
-                    const float w12 = bx[l1] * by[l2];
-#pragma unroll
-                    for (int l3 = 0; l3 < kFmmN; ++l3) {
-                        const float w = w12 * bz[l3];
-                        const int l = (l1 * kFmmN + l2) * kFmmN + l3;
-#pragma unroll
-                        for (int q = 0; q < C; ++q) phi[q] = fmaf(w, sLoc[q * kFmmN3 + l], phi[q]);
-                    }
-                }
-            if (KERNEL_K) {
-                far = phi[0] * (float)(M_LN2 / (4.0 * M_PI));
-            } else {
-                far = NN.x * NN.x * phi[0] + NN.y * NN.y * phi[3] + NN.z * NN.z * phi[5] +
-                      2.f * (NN.x * NN.y * phi[1] + NN.x * NN.z * phi[2] + NN.y * NN.z * phi[4]) +
-                      MM.x * phi[6] + MM.y * phi[7] + MM.z * phi[8];
-            }
-        }
-        // near field: exact kernel over the U list (the leaf itself included)
         float hi = 0.f, lo = 0.f;
-        for (int e = t.u_off[leaf]; e < t.u_off[leaf + 1]; ++e) {
-            const int ul = t.u_list[e];
-            const int q0 = t.box_first[ul], q1 = t.box_first[ul + 1];
-            for (int qb = q0; qb < q1; qb += kThreads) {
-                const int cnt = min(kThreads, q1 - qb);
-                __syncthreads();
-                if (threadIdx.x < cnt) sP[threadIdx.x] = pts[qb + threadIdx.x];
-                __syncthreads();
-                float part = 0.f;
-                if (active) {
-                    for (int j = 0; j < cnt; ++j) {
-                        const float4 s = sP[j];
-                        const float dx = X.x - s.x, dy = X.y - s.y, dz = X.z - s.z;
-                        if (KERNEL_K) {
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const float lg = (qb + j == i) ? 0.f : lg2_approx(r2);
-                            part = fmaf(s.w, lg, part);
-                        } else {
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                            const float inv = rcp_approx(r2);
-                            const float nr = fmaf(NN.x, dx, fmaf(NN.y, dy, NN.z * dz));
-                            const float mr = fmaf(MM.x, dx, fmaf(MM.y, dy, MM.z * dz));
-                            part = fmaf(s.w * inv, fmaf(nr, nr * inv, mr), part);
-                        }
+        for (int qb = q0; qb < q1; qb += kP2PThreads) {
+            const int cnt = min(kP2PThreads, q1 - qb);
+            __syncthreads();
+            if (threadIdx.x < cnt) sP[threadIdx.x] = pts[qb + threadIdx.x];
+            __syncthreads();
+            float part = 0.f;
+            if (active) {
+                for (int j = 0; j < cnt; ++j) {
+                    const float4 s = sP[j];
+                    const float dx = X.x - s.x, dy = X.y - s.y, dz = X.z - s.z;
+                    if (KERNEL_K) {
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float lg = (qb + j == i) ? 0.f : lg2_approx(r2);
+                        part = fmaf(s.w, lg, part);
+                    } else {
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                        const float inv = rcp_approx(r2);
+                        const float nr = fmaf(NN.x, dx, fmaf(NN.y, dy, NN.z * dz));
+                        const float mr = fmaf(MM.x, dx, fmaf(MM.y, dy, MM.z * dz));
+                        part = fmaf(s.w, fmaf(nr, nr * inv, mr) * inv, part);
                     }
                 }
-                two_sum_acc(hi, lo, KERNEL_K ? part * (float)(M_LN2 / (4.0 * M_PI)) : part);
             }
+            two_sum_acc(hi, lo, KERNEL_K ? part * (float)(M_LN2 / (4.0 * M_PI)) : part);
         }
-        if (active) {
-            two_sum_acc(hi, lo, far);
-            out[orig] = make_float2(hi, lo);
+        if (active) slice[orig] = make_float2(hi, lo);
+    }
+}
+
+// L2P for one leaf: phi_c(x) = sum_l S_l(x) L[c][l] and the target combination,
+// written to partial slice kUMax of each target.
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_fmm_l2p(DevTree t, const float4* __restrict__ tgt, const float* __restrict__ Lc,
+          float2* __restrict__ out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int leaf = blockIdx.x;
+    const int box = t.lev_off[t.depth] + leaf;
+    const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
+    const float h = t.L0 / (float)(1 << t.depth);
+    const float3 c = box_center(t, t.depth, t.box_ijk[box]);
+    const float sc = 2.f / h;
+    constexpr int C = KERNEL_K ? 1 : 9;
+    __shared__ float sLoc[C * kFmmN3];
+    for (int q = threadIdx.x; q < C * kFmmN3; q += kThreads) sLoc[q] = Lc[(size_t)box * C * kFmmN3 + q];
+    __syncthreads();
+    float2* slice = out + (size_t)kUMax * t.N;
+    for (int i = p0 + threadIdx.x; i < p1; i += kThreads) {
+        const int orig = t.perm[i];
+        const float4 X = tgt[orig], NN = tgt[t.N + orig], MM = tgt[2 * t.N + orig];
+        float bx[kFmmN], by[kFmmN], bz[kFmmN];
+        cheb_basis((X.x - c.x) * sc, bx);
+        cheb_basis((X.y - c.y) * sc, by);
+        cheb_basis((X.z - c.z) * sc, bz);
+        float phi[C];
+#pragma unroll
+        for (int q = 0; q < C; ++q) phi[q] = 0.f;
+        for (int l1 = 0; l1 < kFmmN; ++l1)
+            for (int l2 = 0; l2 < kFmmN; ++l2) {
+                const float w12 = bx[l1] * by[l2];
+#pragma unroll
+                for (int l3 = 0; l3 < kFmmN; ++l3) {
+                    const float w = w12 * bz[l3];
+                    const int l = (l1 * kFmmN + l2) * kFmmN + l3;
+#pragma unroll
+                    for (int q = 0; q < C; ++q) phi[q] = fmaf(w, sLoc[q * kFmmN3 + l], phi[q]);
+                }
+            }
+        float far;
+        if (KERNEL_K) {
+            far = phi[0] * (float)(M_LN2 / (4.0 * M_PI));
+        } else {
+            far = NN.x * NN.x * phi[0] + NN.y * NN.y * phi[3] + NN.z * NN.z * phi[5] +
+                  2.f * (NN.x * NN.y * phi[1] + NN.x * NN.z * phi[2] + NN.y * NN.z * phi[4]) +
+                  MM.x * phi[6] + MM.y * phi[7] + MM.z * phi[8];
+        }
+        slice[orig] = make_float2(far, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------- M2L as GEMMs
+// The M2L operator between two boxes of one level depends only on their offset
+// d = ijk_T - ijk_S (a V-list offset: max |d_i| in {2, 3}, 316 of them) and on
+// the box size h, through  r = h (d + (t_l - t_m) / 2)  between target point l
+// and source point m.  The kernels are homogeneous: r_a r_b / r^4 and r_a / r^2
+// scale as h^-2 and h^-1, lg2 r^2 = lg2 u^2 + 2 lg2 h.  So one unit-box operator
+// per offset serves every level: rows c * 512 + l (kernel c, target point l),
+// columns m, column-major.  For each offset the columns of all box pairs with
+// that offset are gathered into B, one strided-batched GEMM forms C = A_d B_d
+// for all offsets, and each target box sums its V-list columns of C, scaled for
+// its level, in V-list order.
+constexpr int kNOff = 316;
+
+__global__ void k_fmm_build_op(int which_K, const int3* __restrict__ offs, float* __restrict__ A) {
+    const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
+    const int o = blockIdx.y;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * kFmmN3) return;
+    const int row = (int)(e % rows), m = (int)(e / rows);
+    const int c = row / kFmmN3, l = row % kFmmN3;
+    const int l1 = l / (kFmmN * kFmmN), l2 = (l / kFmmN) % kFmmN, l3 = l % kFmmN;
+    const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
+    const int3 d = offs[o];
+    auto cheb = [](int k) { return cos(M_PI * (2 * k + 1) / (2.0 * kFmmN)); };
+    const double ux = d.x + 0.5 * (cheb(l1) - cheb(m1));
+    const double uy = d.y + 0.5 * (cheb(l2) - cheb(m2));
+    const double uz = d.z + 0.5 * (cheb(l3) - cheb(m3));
+    const double r2 = ux * ux + uy * uy + uz * uz;
+    double v;
+    if (which_K) {
+        v = log2(r2);
+    } else {
+        const double u[3] = {ux, uy, uz};
+        const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+        v = (c < 6) ? u[pa[c]] * u[pb[c]] / (r2 * r2) : u[c - 6] / r2;
+    }
+    A[(size_t)o * rows * kFmmN3 + e] = (float)v;
+}
+
+// B[:, vcol[e]] = M of the e-th V-list source (one block per V-list entry)
+__global__ void __launch_bounds__(kThreads)
+k_fmm_m2l_gather(const int* __restrict__ v_list, const int* __restrict__ vcol, int e0,
+                 const float* __restrict__ M, float* __restrict__ B, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int e = e0 + blockIdx.x;
+    const int m = threadIdx.x;
+    if (m < kFmmN3) B[(size_t)vcol[e] * kFmmN3 + m] = M[(size_t)v_list[e] * kFmmN3 + m];
+}
+
+// sum of a box's multipole values (the log kernel's level term), fixed order
+__global__ void __launch_bounds__(kThreads)
+k_fmm_msum(int box0, const float* __restrict__ M, float* __restrict__ msum,
+           const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int box = box0 + blockIdx.x;
+    __shared__ float sh[kThreads / 32];
+    float v = (threadIdx.x < kFmmN3) ? M[(size_t)box * kFmmN3 + threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
+        msum[box] = t;
+    }
+}
+
+// L_T[c][l] = sum over V(T), in V-list order, of scale_c(h) C[c * 512 + l, vcol[e]]
+// (+ 2 lg2(h) msum_S for the log kernel); one block per target box of level >= 2.
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kThreads)
+k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* __restrict__ vcol,
+                  const float* __restrict__ msum, float* __restrict__ Lc,
+                  const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int box = box0 + blockIdx.x;
+    int lev = 0;
+    while (lev + 1 <= t.depth && t.lev_off[lev + 1] <= box) ++lev;
+    const float h = t.L0 / (float)(1 << lev);
+    constexpr int C = KERNEL_K ? 1 : 9;
+    constexpr int rows = C * kFmmN3;
+    const int l = threadIdx.x;
+    if (l >= kFmmN3) return;
+    const int e0 = t.v_off[box], e1 = t.v_off[box + 1];
+    if (KERNEL_K) {
+        const float lh = 2.f * log2f(h);
+        float acc = 0.f;
+        for (int e = e0; e < e1; ++e)
+            acc += Cm[(size_t)vcol[e] * rows + l] + lh * msum[t.v_list[e]];
+        Lc[(size_t)box * kFmmN3 + l] = acc;
+    } else {
+        const float s2 = 1.f / (h * h), s1 = 1.f / h;
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            float acc = 0.f;
+            for (int e = e0; e < e1; ++e) acc += Cm[(size_t)vcol[e] * rows + q * kFmmN3 + l];
+            Lc[((size_t)box * C + q) * kFmmN3 + l] = acc * (q < 6 ? s2 : s1);
         }
     }
 }
@@ -380,9 +503,18 @@ struct PmFmmTree {
     int3* box_ijk = nullptr;
     float4* sorted = nullptr;
     float* M = nullptr;
-    float* Lc = nullptr;     // [nbox][9][216]
+    float* Lc = nullptr;     // [nbox][9][512]
     long long p2p_pairs = 0, m2l_pairs = 0;
+    // M2L as GEMMs: V-list entry -> column (offset * nmax + rank within the offset)
+    int nmax = 0, nv = 0;
+    int* vcol = nullptr;
+    float *Bm = nullptr, *Cm = nullptr, *msum = nullptr;
+    cublasHandle_t blas = nullptr;
+    void* blas_ws = nullptr;
     ~PmFmmTree() {
+        if (blas) cublasDestroy(blas);
+        pm_dfree(vcol); pm_dfree(Bm); pm_dfree(Cm); pm_dfree(msum);
+        if (blas_ws) cudaFree(blas_ws);
         pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
         pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
         pm_dfree(u_off); pm_dfree(u_list); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
@@ -407,6 +539,22 @@ struct KeyHash {
                ((size_t)(unsigned)k.z * 83492791u);
     }
 };
+
+// index of a V-list offset d (max |d_i| in {2, 3}) in 0..315, or -1
+int off_index(int dx, int dy, int dz) {
+    if (std::max({std::abs(dx), std::abs(dy), std::abs(dz)}) < 2 || std::abs(dx) > 3 ||
+        std::abs(dy) > 3 || std::abs(dz) > 3)
+        return -1;
+    int k = 0;
+    for (int x = -3; x <= 3; ++x)
+        for (int y = -3; y <= 3; ++y)
+            for (int z = -3; z <= 3; ++z) {
+                if (std::max({std::abs(x), std::abs(y), std::abs(z)}) < 2) continue;
+                if (x == dx && y == dy && z == dz) return k;
+                ++k;
+            }
+    return -1;
+}
 
 long long morton(int x, int y, int z) {
     long long m = 0;
@@ -640,6 +788,26 @@ pm_status pm_fmm_build(pm_surface* s) {
     PM_TRY(up(&T->u_off, u_off));
     PM_TRY(up(&T->u_list, u_list));
     PM_TRY(up(&T->box_ijk, ijk));
+    // M2L columns: group the V-list entries by offset
+    {
+        std::vector<int> cnt_o(kNOff, 0), rank(v_list.size());
+        for (int b = 0; b < T->nbox; ++b)
+            for (int e = v_off[b]; e < v_off[b + 1]; ++e) {
+                const int3 dt = ijk[b], ds = ijk[v_list[e]];
+                const int o = off_index(dt.x - ds.x, dt.y - ds.y, dt.z - ds.z);
+                if (o < 0) {
+                    pm_set_error("pm_fmm_build: V-list offset outside the interaction range");
+                    return PM_ERR_INTERNAL;
+                }
+                rank[e] = (o << 20) | cnt_o[o]++;      // (offset, rank) packed, rank < 2^20
+            }
+        T->nmax = std::max(1, *std::max_element(cnt_o.begin(), cnt_o.end()));
+        std::vector<int> vcol(v_list.size());
+        for (size_t e = 0; e < v_list.size(); ++e)
+            vcol[e] = (rank[e] >> 20) * T->nmax + (rank[e] & ((1 << 20) - 1));
+        T->nv = (int)v_list.size();
+        PM_TRY(up(&T->vcol, vcol));
+    }
     PM_TRY(pm_dmalloc(&T->sorted, N));
     PM_TRY(pm_dmalloc(&T->M, (size_t)T->nbox * kFmmN3));
     PM_TRY(pm_dmalloc(&T->Lc, (size_t)T->nbox * 9 * kFmmN3));
@@ -668,6 +836,82 @@ pm_status pm_fmm_build(pm_surface* s) {
     PM_CUDA_TRY(cudaMemcpyToSymbol(cF, &F, sizeof(F)));
     return PM_OK;
 }
+
+namespace {
+
+// Unit-box M2L operators of the context (one set per kernel family), built once.
+pm_status ensure_m2l_ops(pm_surface* s, int which_K, float** out) {
+    pm_ctx* c = s->ctx;
+    std::lock_guard<std::mutex> lk(c->fmm_mu);
+    float*& A = which_K ? c->fmm_opK : c->fmm_opR;
+    if (!A) {
+        const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
+        std::vector<int3> offs;
+        for (int x = -3; x <= 3; ++x)
+            for (int y = -3; y <= 3; ++y)
+                for (int z = -3; z <= 3; ++z)
+                    if (std::max({std::abs(x), std::abs(y), std::abs(z)}) >= 2)
+                        offs.push_back(make_int3(x, y, z));
+        float* tmp = nullptr;
+        int3* doffs = nullptr;
+        PM_TRY(pm_dmalloc(&tmp, (size_t)kNOff * rows * kFmmN3));
+        PM_TRY(pm_dmalloc(&doffs, offs.size()));
+        cudaStream_t bs = nullptr;
+        cudaError_t ce = cudaMemcpy(doffs, offs.data(), sizeof(int3) * offs.size(),
+                                    cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        if (ce == cudaSuccess) {
+            const dim3 g(pm_ceil_div((long long)rows * kFmmN3, 256), kNOff);
+            k_fmm_build_op<<<g, 256, 0, bs>>>(which_K, doffs, tmp);
+            ce = cudaGetLastError();
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs);
+        }
+        if (bs) cudaStreamDestroy(bs);
+        pm_dfree(doffs);
+        if (ce != cudaSuccess) {
+            pm_dfree(tmp);
+            pm_set_error("FMM M2L operators: %s", cudaGetErrorString(ce));
+            return PM_ERR_CUDA;
+        }
+        A = tmp;
+    }
+    *out = A;
+    return PM_OK;
+}
+
+// cuBLAS handle (float32 emulated on bfloat16 tensor cores, always), its
+// workspace (set explicitly so that the GEMM can be captured in a graph) and the
+// gathered multipole and result matrices of the tree.
+pm_status ensure_m2l_gemm(PmFmmTree* T) {
+    if (!T->blas) {
+        if (cublasCreate(&T->blas) != CUBLAS_STATUS_SUCCESS) {
+            T->blas = nullptr;
+            pm_set_error("FMM: cublasCreate failed");
+            return PM_ERR_CUDA;
+        }
+        const size_t ws = 64u << 20;
+        PM_CUDA_TRY(cudaMalloc(&T->blas_ws, ws));
+        if (cublasSetWorkspace(T->blas, T->blas_ws, ws) != CUBLAS_STATUS_SUCCESS ||
+            cublasSetEmulationStrategy(T->blas, CUBLAS_EMULATION_STRATEGY_EAGER) !=
+                CUBLAS_STATUS_SUCCESS) {
+            pm_set_error("FMM: cuBLAS workspace / emulation setup failed");
+            return PM_ERR_CUDA;
+        }
+    }
+    if (!T->Bm) {
+        const size_t cols = (size_t)kNOff * T->nmax;
+        PM_TRY(pm_dmalloc(&T->Bm, cols * kFmmN3));
+        PM_CUDA_TRY(cudaMemset(T->Bm, 0, sizeof(float) * cols * kFmmN3));   // padding columns
+        PM_TRY(pm_dmalloc(&T->Cm, cols * 9 * kFmmN3));
+        PM_TRY(pm_dmalloc(&T->msum, (size_t)T->nbox));
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+// Partial slices the FMM writes per target (U-list neighbours + far field).
+int pm_fmm_splits() { return kUMax + 1; }
 
 pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     PM_TRY(pm_fmm_build(s));
@@ -699,10 +943,38 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
         k_fmm_m2m<<<nb, kThreads, 0, st>>>(t, l, T->M, skip);
     }
     const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
-    if (which_K)
+    if (s->opts.fmm_tensor_m2l) {
+        float* A = nullptr;
+        PM_TRY(ensure_m2l_ops(s, which_K, &A));
+        PM_TRY(ensure_m2l_gemm(T));
+        const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
+        if (which_K && nm2l > 0) k_fmm_msum<<<nm2l, kThreads, 0, st>>>(b2, T->M, T->msum, skip);
+        if (T->nv > 0)
+            k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, 0, T->M, T->Bm, skip);
+        PM_CUDA_TRY(cudaGetLastError());
+        const float one = 1.f, zero = 0.f;
+        if (cublasSetStream(T->blas, st) != CUBLAS_STATUS_SUCCESS ||
+            cublasGemmStridedBatchedEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, T->nmax, kFmmN3,
+                                       &one, A, CUDA_R_32F, rows, (long long)rows * kFmmN3,
+                                       T->Bm, CUDA_R_32F, kFmmN3, (long long)kFmmN3 * T->nmax,
+                                       &zero, T->Cm, CUDA_R_32F, rows, (long long)rows * T->nmax,
+                                       kNOff, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                                       CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+            pm_set_error("FMM: M2L GEMM (float32 emulated on bfloat16) failed");
+            return PM_ERR_CUDA;
+        }
+        if (which_K)
+            k_fmm_m2l_scatter<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->Cm, T->vcol, T->msum,
+                                                               T->Lc, skip);
+        else
+            k_fmm_m2l_scatter<false><<<nm2l, kThreads, 0, st>>>(t, b2, T->Cm, T->vcol, T->msum,
+                                                                T->Lc, skip);
+        s->launch_total += 2 + (which_K ? 1 : 0);
+    } else if (which_K) {
         k_fmm_m2l<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
-    else
+    } else {
         k_fmm_m2l<false><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
+    }
     for (int l = 3; l <= depth; ++l) {
         const int nb = T->lev_off[l + 1] - T->lev_off[l];
         if (which_K)
@@ -711,11 +983,15 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
             k_fmm_l2l<9><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
     }
     float2* out = reinterpret_cast<float2*>(s->partial);
-    if (which_K)
-        k_fmm_leaf<true><<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, s->tgt32, T->Lc, s->eps2, out, skip);
-    else
-        k_fmm_leaf<false><<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, s->tgt32, T->Lc, s->eps2, out, skip);
-    s->launch_total += 4 + 2 * std::max(0, depth - 2);
+    const dim3 g2(T->nleaf, kUMax);
+    if (which_K) {
+        k_fmm_p2p<true><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
+        k_fmm_l2p<true><<<T->nleaf, kThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
+    } else {
+        k_fmm_p2p<false><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
+        k_fmm_l2p<false><<<T->nleaf, kThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
+    }
+    s->launch_total += 5 + 2 * std::max(0, depth - 2);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/parametrix.h"
@@ -66,6 +67,11 @@ struct pm_ctx {
     int device = 0;
     int num_sms = 0;
     cudaDeviceProp prop{};
+    // FMM M2L operators for unit boxes, one per V-list offset, shared by all
+    // surfaces of the context; built on first use (pm_fmm.cu)
+    std::mutex fmm_mu;
+    float* fmm_opR = nullptr;     // [316][9*512][512] column-major per offset
+    float* fmm_opK = nullptr;     // [316][512][512]
 };
 
 struct PmSolveWork;
@@ -184,6 +190,7 @@ pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st);
 
 // Chebyshev FMM (pm_fmm.cu)
 pm_status pm_fmm_build(pm_surface* s);
+int pm_fmm_splits();
 pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st);
 void pm_fmm_free(pm_surface* s);
 
