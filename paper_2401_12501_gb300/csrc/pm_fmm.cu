@@ -277,6 +277,7 @@ k_fmm_l2l(DevTree t, int lev, float* __restrict__ Lc, const int* __restrict__ sk
 // each target (zeros when the leaf has fewer than e + 1 neighbours).  Splitting
 // the near field by neighbour gives ~27 blocks per leaf of similar work.
 constexpr int kP2PThreads = 256;
+constexpr int kP2PStage = 512;                 // sources staged in shared memory per pass
 constexpr int kUMax = 27;                      // U list: the 3 x 3 x 3 leaves around a leaf
 
 template <bool KERNEL_K>
@@ -294,7 +295,7 @@ k_fmm_p2p(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ 
     }
     const int ul = t.u_list[t.u_off[leaf] + e];
     const int q0 = t.box_first[ul], q1 = t.box_first[ul + 1];
-    __shared__ float4 sP[kP2PThreads];
+    __shared__ float4 sP[kP2PStage];
     for (int tb = p0; tb < p1; tb += kP2PThreads) {
         const int i = tb + threadIdx.x;
         const bool active = i < p1;
@@ -307,10 +308,10 @@ k_fmm_p2p(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ 
             MM = tgt[2 * t.N + orig];
         }
         float hi = 0.f, lo = 0.f;
-        for (int qb = q0; qb < q1; qb += kP2PThreads) {
-            const int cnt = min(kP2PThreads, q1 - qb);
+        for (int qb = q0; qb < q1; qb += kP2PStage) {
+            const int cnt = min(kP2PStage, q1 - qb);
             __syncthreads();
-            if (threadIdx.x < cnt) sP[threadIdx.x] = pts[qb + threadIdx.x];
+            for (int j = threadIdx.x; j < cnt; j += kP2PThreads) sP[j] = pts[qb + j];
             __syncthreads();
             float part = 0.f;
             if (active) {
@@ -891,8 +892,12 @@ pm_status ensure_m2l_gemm(PmFmmTree* T) {
         }
         const size_t ws = 64u << 20;
         PM_CUDA_TRY(cudaMalloc(&T->blas_ws, ws));
+        // operators and multipoles are finite by construction (finite strengths), so the
+        // emulation's scan for infinities and NaNs in A and B is skipped
         if (cublasSetWorkspace(T->blas, T->blas_ws, ws) != CUBLAS_STATUS_SUCCESS ||
             cublasSetEmulationStrategy(T->blas, CUBLAS_EMULATION_STRATEGY_EAGER) !=
+                CUBLAS_STATUS_SUCCESS ||
+            cublasSetEmulationSpecialValuesSupport(T->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE) !=
                 CUBLAS_STATUS_SUCCESS) {
             pm_set_error("FMM: cuBLAS workspace / emulation setup failed");
             return PM_ERR_CUDA;
