@@ -38,7 +38,7 @@ FLOPS_PER_PAIR_R = 26      # variable-a remainder pair (algorithmic count)
 TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
                  ("k_direct_ff_R", "ellipsoid_9600"): 1236224,
                  ("k_sym_ff_R", "ellipsoid_9600"): 1299712}
-SYM_PARTIAL_CAP = 96 * 1024 * 1024      # the library's cap on symmetric-sum partial slices
+SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
@@ -436,7 +436,28 @@ def run_fmm(args, dev):
         _nvtx_pop()
         out[prec] = ((time.perf_counter() - t0) / reps, y.cpu().numpy())
     ex = out["ff"][1]
+    # whole solves (tol 1e-8): GMRES with FMM applies vs with direct float32 applies,
+    # float-float refinement and representation in both
+    solves = {}
+    for prec in ("fmm", "fp32"):
+        s.solve(wl.f, tol=1e-8, prec=prec)                  # warm (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, info = s.solve(wl.f, tol=1e-8, prec=prec)
+        solves[prec] = (time.perf_counter() - t0, u, info[0])
+    w = wl.surface.weights
+    du = solves["fmm"][1] - solves["fp32"][1]
+    m2l_pairs = st["m2l_box_pairs"]
     res = {"workload": "torus_98304", "N": wl.N, "near_build_s": round(t_build, 3),
+           "m2l": "per-offset operator GEMMs on the tensor cores (float32 emulated on bfloat16, "
+                  "float32 accumulation)",
+           "m2l_gemm_flops_per_apply": 2.0 * 9 * 512 * 512 * m2l_pairs,
+           "m2l_operator_bytes_per_apply": 316 * 9 * 512 * 512 * 4,
+           "solve_tol_1e-8": {p: {"ms": round(v[0] * 1e3, 2), "iterations": v[2].iterations,
+                                  "refinements": v[2].refinements,
+                                  "residual": v[2].residual} for p, v in solves.items()},
+           "solve_u_rel_diff_fmm_vs_fp32": float(np.sqrt(np.dot(w, du * du) /
+                                                         np.dot(w, solves["fp32"][1] ** 2))),
            "fmm_tree": st, "apply_R_ms": {k: round(v[0] * 1e3, 3) for k, v in out.items()},
            "rel_err_vs_float_float": {k: float(np.linalg.norm(v[1] - ex) / np.linalg.norm(ex))
                                       for k, v in out.items() if k != "ff"},

@@ -97,7 +97,7 @@ typedef struct {
     int direct_symmetric;   /* float-float smooth sums: 1 = evaluate each
                                unordered node pair once (tile pairs; row and column sums
                                from the shared pair geometry) where the (N/128) x N
-                               partial slices fit in 96 MB, else one-sided sums (default);
+                               partial slices fit in 1 GiB, else one-sided sums (default);
                                0 = one-sided sums always                                */
     int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as per-offset operator GEMMs on
                                the tensor cores (float32 emulated on bfloat16, float32

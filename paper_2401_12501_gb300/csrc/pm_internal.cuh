@@ -212,7 +212,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
 void pm_solve_free(pm_surface* s);
 
 // symmetric tile-pair float-float sums (pm_symsum.cu); partial slices capped at this size
-constexpr double kSymPartialCap = 96.0 * 1024.0 * 1024.0;
+constexpr double kSymPartialCap = 1024.0 * 1024.0 * 1024.0;
 int pm_sym_tiles(const pm_surface* s);
 pm_status pm_sym_ff(pm_surface* s, int which_K, cudaStream_t st);
 double pm_ff_grid(const pm_surface* s);
