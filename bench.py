@@ -313,7 +313,7 @@ def run_gpu(args, rank, world, local_rank):
            "flops_per_pair": FLOPS_PER_PAIR_R,
            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts)",
            "step_time_share": round(fp32_ms / prof_total_ms, 4)}
-    ff_k = ff_ms / max(1, rf + 1) / args.steps if ff_n else 0.0
+    ff_k = ff_ms / ff_n if ff_n else 0.0
     nt = -(-N // 128)
     sym = N >= 256 and nt * N * 8 <= SYM_PARTIAL_CAP
     ff_name = "k_sym_ff" if sym else "k_direct_ff"

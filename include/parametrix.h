@@ -99,6 +99,10 @@ typedef struct {
                                from the shared pair geometry) where the (N/128) x N
                                partial slices fit in 1 GiB, else one-sided sums (default);
                                0 = one-sided sums always                                */
+    int residual_update;    /* pm_solve with float32/FMM applies: after a correction d, take
+                               r - A32 d as the next residual when 1e-5 |d| (the float32
+                               operator's error bound on d) is below 0.1 tol |f|, instead of
+                               recomputing f - A sigma in residual_prec; 1 (default) or 0 */
     int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as per-offset operator GEMMs on
                                the tensor cores (float32 emulated on bfloat16, float32
                                accumulation; operators ~3.3 GB per context, built once)
@@ -206,6 +210,7 @@ typedef struct {
     double residual;         /* final true relative residual ||f - A sigma|| / ||f|| */
     double removed_mean;     /* mean subtracted from f (PM_SOLVE_PROJECT_RHS)         */
     double seconds;          /* wall time of the call                                */
+    int residual_updates;    /* residuals taken as r - A32 d (opts.residual_update)   */
 } pm_solve_info;
 
 /*

@@ -48,13 +48,13 @@ class PmOpts(C.Structure):
                 ("residual_prec", C.c_int), ("fmm_depth", C.c_int), ("batch_rhs", C.c_int),
                 ("direct_tpt", C.c_int),
                 ("direct_blocks_per_sm", C.c_int), ("direct_symmetric", C.c_int),
-                ("fmm_tensor_m2l", C.c_int)]
+                ("residual_update", C.c_int), ("fmm_tensor_m2l", C.c_int)]
 
 
 class PmSolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
                 ("residual", C.c_double), ("removed_mean", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("residual_updates", C.c_int)]
 
 
 class PmError(RuntimeError):

@@ -64,6 +64,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     o->direct_tpt = 0;
     o->direct_blocks_per_sm = 0;
     o->direct_symmetric = 1;
+    o->residual_update = 1;
     o->fmm_tensor_m2l = 1;
 }
 

@@ -963,6 +963,7 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
             info[r].residual = relres[r];
             info[r].removed_mean = removed[r];
             info[r].seconds = secs;
+            info[r].residual_updates = 0;
         }
     return result;
 }

@@ -172,3 +172,32 @@ def test_graph_cycle_matches_host_issued(ctx, name, restart):
     assert np.array_equal(u_host, u_graph)
     assert np.array_equal(u_graph, u_again)
     s.close()
+
+
+@pytest.mark.parametrize("name,tol", [("ellipsoid_2400", 1e-10), ("ellipsoid_9600", 1e-10),
+                                      ("ellipsoid_9600", 1e-8)])
+def test_residual_update_keeps_true_residual(ctx, name, tol):
+    """With opts.residual_update the residual after a small correction d is taken
+    as r - A32 d.  The true residual of the returned sigma, recomputed here from
+    sigma with float-float applies (f - sigma - R~ sigma - sum w sigma), still
+    meets the tolerance, and the solution agrees with the always-recompute mode."""
+    import paper_2401_12501_gb300 as pm
+    wl = make_workload(name)
+    res = {}
+    for upd in (0, 1):
+        o = pm.default_opts()
+        o.residual_update = upd
+        s = pm.Surface.from_fixture(ctx, wl.surface, o)
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        u, info, sig = s.solve(wl.f, tol=tol, prec="fp32", return_sigma=True)
+        Rs = s.apply_R(sig, "ff")
+        r = wl.f - (sig + Rs + np.dot(wl.surface.weights, sig))
+        res[upd] = (u, info[0], np.linalg.norm(r) / np.linalg.norm(wl.f))
+        s.close()
+    u0, i0, t0 = res[0]
+    u1, i1, t1 = res[1]
+    assert i0.residual_updates == 0
+    assert i1.residual_updates >= 1 and i1.refinements >= 2
+    assert t1 <= tol and t0 <= tol, (t0, t1)
+    assert abs(t1 - i1.residual) <= 0.2 * tol                 # the reported residual is the true one
+    assert rel_l2(u1, u0, wl.surface.weights) < 10 * tol
