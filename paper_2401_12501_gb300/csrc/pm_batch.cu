@@ -599,21 +599,26 @@ __global__ void k_brotate(int nrhs, double* __restrict__ H, int ldh, int m, int 
     if (threadIdx.x == 0) *all_done = any_active ? 0 : 1;
 }
 
+// per right-hand side: y = H^{-1} g by back substitution and ynorm = |y|_2 (the
+// norm of the cycle's correction V y, V orthonormal)
 __global__ void k_bbacksolve(int nrhs, const double* __restrict__ H, int ldh, int m,
                              const double* __restrict__ g, const int* __restrict__ iters,
-                             double* __restrict__ y) {
+                             double* __restrict__ y, double* __restrict__ ynorm) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrhs) return;
     const int n = iters[r];
     const double* Hr = H + (size_t)r * m * ldh;
     const double* gr = g + (size_t)r * (m + 1);
     double* yr = y + (size_t)r * m;
+    double s2 = 0.0;
     for (int i = n - 1; i >= 0; --i) {
         double t = gr[i];
         for (int j = i + 1; j < n; ++j) t -= Hr[(size_t)j * ldh + i] * yr[j];
         const double d = Hr[(size_t)i * ldh + i];
         yr[i] = (d != 0.0) ? t / d : 0.0;
+        s2 += yr[i] * yr[i];
     }
+    ynorm[r] = sqrt(s2);
 }
 
 __global__ void k_badd_combo(const double* __restrict__ V, long long col_stride,
@@ -634,6 +639,13 @@ __global__ void k_bresidual(const double* __restrict__ b, const double* __restri
     const int r = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) out[(size_t)r * N + i] = b[(size_t)r * N + i] - Ax[(size_t)r * N + i];
+}
+
+// y -= x (every right-hand side)
+__global__ void k_bsubv(double* __restrict__ y, const double* __restrict__ x, int N) {
+    const int r = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) y[(size_t)r * N + i] -= x[(size_t)r * N + i];
 }
 
 __global__ void k_baxpy(double* __restrict__ y, const double* __restrict__ x, int N) {
@@ -665,7 +677,9 @@ struct PmBatchSolveWork {
     double *w = nullptr, *tmp = nullptr, *r = nullptr, *res = nullptr, *delta = nullptr;
     double *sig = nullptr, *f = nullptr, *u = nullptr;
     int *done = nullptr, *iters = nullptr, *all_done = nullptr;
+    double* ynorm = nullptr;          // [nrhs] |y| of the last cycle
     double* pinned = nullptr;
+    double* pinned_y = nullptr;       // [nrhs] host copy of ynorm
     int* pinned_i = nullptr;
 };
 
@@ -676,6 +690,8 @@ void pm_batch_solve_free(pm_surface* s) {
     pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.dots); pm_dfree(W.w);
     pm_dfree(W.tmp); pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig);
     pm_dfree(W.f); pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.all_done);
+    pm_dfree(W.ynorm);
+    if (W.pinned_y) cudaFreeHost(W.pinned_y);
     if (W.pinned) cudaFreeHost(W.pinned);
     if (W.pinned_i) cudaFreeHost(W.pinned_i);
     delete s->bsolve;
@@ -718,6 +734,8 @@ static pm_status bsolve_work(pm_surface* s, int nrhs, PmBatchSolveWork** out) {
     PM_TRY(pm_dmalloc(&W.done, nrhs));
     PM_TRY(pm_dmalloc(&W.iters, nrhs));
     PM_TRY(pm_dmalloc(&W.all_done, 1));
+    PM_TRY(pm_dmalloc(&W.ynorm, nrhs));
+    PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_y, sizeof(double) * (size_t)nrhs));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, sizeof(double) * 8 * (size_t)nrhs));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_i, sizeof(int) * (2 * (size_t)nrhs + 4)));
     *out = &W;
@@ -774,8 +792,10 @@ struct BSolver {
     }
 
     // lockstep restarted GMRES on A d_r = b_r from d = 0 (operator in prec); x += d.
+    // dnorm (optional): per right-hand side, bound on |x_new - x_old| (sum of the cycles' |y|)
     pm_status gmres(const double* b, double* x, pm_precision prec, const std::vector<double>& tol_abs,
-                    int max_iter, int* iters_used) {
+                    int max_iter, int* iters_used, std::vector<double>* dnorm = nullptr) {
+        if (dnorm) dnorm->assign(nrhs, 0.0);
         const int m = W.m, N = W.N;
         const long long ldV = (long long)(m + 1) * N;
         const int ldh = m + 2;
@@ -825,18 +845,22 @@ struct BSolver {
                 s->launch_total += 5;
             }
             s->skip_flag = nullptr;
-            k_bbacksolve<<<pm_ceil_div(nrhs, 64), 64, 0, st>>>(nrhs, W.H, ldh, m, W.g, W.iters, W.y);
+            k_bbacksolve<<<pm_ceil_div(nrhs, 64), 64, 0, st>>>(nrhs, W.H, ldh, m, W.g, W.iters, W.y,
+                                                                W.ynorm);
             k_badd_combo<<<dim3(grid_n, nrhs), 256, 0, st>>>(W.V, N, ldV, W.iters, W.y, m, W.delta, N);
             s->launch_total += 2;
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int) * nrhs,
                                         cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + nrhs, W.done, sizeof(int) * nrhs,
                                         cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_y, W.ynorm, sizeof(double) * nrhs,
+                                        cudaMemcpyDeviceToHost, st));
             PM_CUDA_TRY(cudaStreamSynchronize(st));
             int it = 0, all = 1;
             for (int r = 0; r < nrhs; ++r) {
                 it = std::max(it, W.pinned_i[r]);
                 all &= W.pinned_i[nrhs + r];
+                if (dnorm && W.pinned_i[r] > 0) (*dnorm)[r] += W.pinned_y[r];
             }
             total += it;
             if (all || it == 0) break;
@@ -900,16 +924,27 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
     }
     PM_TRY(S.norms(W.f, fnorm.data()));
     PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * (size_t)nrhs * N, st));
-    int iters = 0, refinements = 0;
+    int iters = 0, refinements = 0, updated = 0;
     std::vector<double> relres(nrhs, 0.0);
     const bool accurate_inner = (prec == PM_PREC_FP64 || prec == PM_PREC_FF);
-    std::vector<double> tabs(nrhs);
+    std::vector<double> tabs(nrhs), dn;
+    bool have_update = false;
     for (;;) {
         std::vector<double> rn(nrhs);
+        // after a correction d: r - A32 d is the true residual to within 0.1 tol |f_r|
+        // when kOpRelErr |d_r| <= 0.1 tol |f_r| for every right-hand side (pm_solve.cu)
+        bool small = have_update && s->opts.residual_update && !accurate_inner;
+        for (int r = 0; small && r < nrhs; ++r) small = kOpRelErr * dn[r] <= 0.1 * tol * fnorm[r];
         if (refinements == 0) {
             PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * (size_t)nrhs * N,
                                         cudaMemcpyDeviceToDevice, st));
             rn = fnorm;
+        } else if (small) {
+            PM_TRY(S.apply_A(W.delta, N, W.w, prec, nullptr));
+            k_bsubv<<<dim3(S.grid_n, nrhs), 256, 0, st>>>(W.res, W.w, N);
+            s->launch_total += 1;
+            PM_TRY(S.norms(W.res, rn.data()));
+            ++updated;
         } else {
             PM_TRY(S.true_residual(W.f, W.sig, W.res));
             PM_TRY(S.norms(W.res, rn.data()));
@@ -928,7 +963,8 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
             tabs[r] = (relres[r] <= tol) ? 1e300 : inner * rn[r];
         }
         int it = 0;
-        PM_TRY(S.gmres(W.res, W.sig, prec, tabs, maxit - iters, &it));
+        PM_TRY(S.gmres(W.res, W.sig, prec, tabs, maxit - iters, &it, &dn));
+        have_update = true;
         iters += it;
         ++refinements;
         if (it == 0) break;
@@ -963,7 +999,7 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
             info[r].residual = relres[r];
             info[r].removed_mean = removed[r];
             info[r].seconds = secs;
-            info[r].residual_updates = 0;
+            info[r].residual_updates = updated;
         }
     return result;
 }

@@ -211,6 +211,13 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
 
 void pm_solve_free(pm_surface* s);
 
+// Bound on the relative error of a float32 (or FMM) operator apply against the
+// float64 operator, |(A32 - A) v| <= kOpRelErr |v|: measured errors are below
+// 7e-6 (float32 direct sums and FMM, relative to |A v|, |A| = O(1) for the
+// second-kind operator); the bound keeps a margin.  Used to decide when a
+// refinement residual may be updated with a float32 apply (pm_solve.cu, pm_batch.cu).
+constexpr double kOpRelErr = 1e-5;
+
 // symmetric tile-pair float-float sums (pm_symsum.cu); partial slices capped at this size
 constexpr double kSymPartialCap = 1024.0 * 1024.0 * 1024.0;
 int pm_sym_tiles(const pm_surface* s);

@@ -34,12 +34,6 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// Bound on the relative error of a float32 (or FMM) operator apply against the
-// float64 operator, |(A32 - A) v| <= kOpRelErr |v|: measured errors are below
-// 7e-6 (float32 direct sums and FMM, relative to |A v|, |A| = O(1) for the
-// second-kind operator); the bound keeps a margin.
-constexpr double kOpRelErr = 1e-5;
-
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;

@@ -107,3 +107,25 @@ def test_full_size_star_batch_residuals(ctx):
         u1, i1 = s.solve(F[r], tol=1e-10, prec="fp32")
         assert np.sqrt(np.dot(w, (U[r] - u1) ** 2) / np.dot(w, u1 ** 2)) < 1e-8
     s.close()
+
+
+def test_batched_residual_update_keeps_true_residuals(ctx):
+    """Batched refinement with residual updates (r - A32 d after small corrections):
+    every right-hand side's true residual, recomputed from sigma with float-float
+    applies, meets the tolerance and matches the reported one to 0.2 tol."""
+    import paper_2401_12501_gb300 as pm
+    s_surf, coeffs, F = star_batch(m=4, p=8, n_rhs=8, n_coeff=1)
+    o = pm.default_opts()
+    s = pm.Surface.from_fixture(ctx, s_surf, o)
+    s.set_coeff(coeffs[0].a, coeffs[0].grad_a)
+    tol = 1e-10
+    u, infos, sig = s.solve(np.ascontiguousarray(F), tol=tol, prec="fp32", return_sigma=True)
+    w = s_surf.weights
+    Rs = s.apply_R(sig, "ff")
+    for r in range(F.shape[0]):
+        res = F[r] - (sig[r] + Rs[r] + np.dot(w, sig[r]))
+        t = np.linalg.norm(res) / np.linalg.norm(F[r])
+        assert t <= tol, (r, t)
+        assert abs(t - infos[r].residual) <= 0.2 * tol
+    assert infos[0].residual_updates >= 1
+    s.close()
