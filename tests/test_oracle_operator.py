@@ -12,13 +12,18 @@
   (Sec. 7.2 procedure, variable-a right-hand side grad a . grad v + a Lap_G v)
   is recovered.
 * Dilation of the near-field weights (Sec. 3 conjecture, item 3).
+* Null space (Sec. 3): on the sphere I + R~ has exactly one near-zero singular
+  value and the rank-one term removes it; on a torus with a = 1 the null vector
+  is alpha - rho (rho: distance to the rotation axis), so (I + R~) 1 and
+  (I + R~) rho are parallel, with alpha not the mean of rho.
 """
 
 import numpy as np
 import pytest
 
 from conftest import oracle_processes
-from oracle.operator import Discretization, NearField, apply_K, apply_R
+from oracle.operator import (Discretization, NearField, apply_K, apply_R,
+                             second_kind_matrix)
 from oracle.solve import gmres, relative_l2, solve
 from workloads import make_workload, real_sph_harm
 
@@ -129,3 +134,29 @@ def test_gmres_matches_dense_solve():
     b = rng.standard_normal(60)
     x, it, rr = gmres(lambda v: A @ v, b, tol=1e-13, restart=10)
     assert np.abs(x - np.linalg.solve(A, b)).max() < 1e-11
+
+
+def test_sphere_single_null_singular_value(sphere):
+    _, d, nf = sphere
+    A = second_kind_matrix(d, nf)
+    sv0 = np.linalg.svd(A - np.outer(np.ones(d.N), d.w), compute_uv=False)
+    assert sv0[-1] < 1e-6 and sv0[-2] > 0.5                  # one null direction, I + R~
+    assert np.linalg.svd(A, compute_uv=False)[-1] > 0.5       # removed by the rank-one term
+
+
+def test_torus_null_vector_alpha_minus_rho():
+    from workloads.surfaces import torus
+    s = torus(12, 4, 6)
+    N = s.N
+    d = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights,
+                       np.ones(N), np.zeros((N, 3)), s.npatch, s.p, near_tol=1e-10)
+    nf = NearField(d, processes=oracle_processes())
+    one = np.ones(N)
+    rho = np.hypot(s.nodes[:, 0], s.nodes[:, 1])
+    y1 = one + apply_R(d, nf, one)
+    yr = rho + apply_R(d, nf, rho)
+    alpha = np.dot(y1, yr) / np.dot(y1, y1)
+    # parallel to discretisation accuracy on 12 x 4 patches of 6 x 6 nodes (~1 %)
+    assert np.linalg.norm(yr - alpha * y1) < 0.03 * np.linalg.norm(yr)
+    assert np.linalg.norm(y1) > 0.5 * np.sqrt(N)               # 1 itself is not in the null space
+    assert abs(alpha - np.dot(s.weights, rho) / s.weights.sum()) > 0.1
