@@ -636,84 +636,107 @@ struct Solver {
         return true;
     }
 
+    // Enqueue one GMRES cycle for A d = W.r from d = W.delta's current value plus the
+    // cycle's correction (W.delta += V y), with the operator in `prec`: at most `steps`
+    // Arnoldi steps, stopping once the residual estimate is below tol_abs.  No host
+    // synchronisation, except the done-flag reads of the host-issued form (profiling on).
+    // Afterwards W.iters, W.done and W.scal[7] = |y| describe the cycle.
+    pm_status launch_cycle(pm_precision prec, double tol_abs, int steps) {
+        const int m = W.m;
+        const long long ldv = W.N;
+        // the float32 strengths of each basis vector are written by the kernel
+        // that forms it (FP32 / FMM operators)
+        const bool fuse_prep = prec == PM_PREC_FP32 || prec == PM_PREC_FMM;
+        const bool graph = fuse_prep && !s->profiling && ensure_graph(prec);
+        float4* src32 = fuse_prep ? s->src32 : nullptr;
+        const int nb = W.narn, ld = m + 2;
+        W.pinned_par[0] = tol_abs;
+        W.pinned_par[1] = (double)steps;
+        PM_CUDA_TRY(cudaMemcpyAsync(W.par, W.pinned_par, 2 * sizeof(double),
+                                    cudaMemcpyHostToDevice, st));
+        if (graph) {
+            PM_CUDA_TRY(cudaGraphLaunch(W.exec, st));
+            s->launch_total += 4;                  // plus body_launches per step, counted on readback
+            return PM_OK;
+        }
+        k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
+        k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
+                                                W.iters, W.r, W.V, s->w, s->wa, src32,
+                                                s->sig32, s->pp, s->ppad, W.pb, W.N, 0, 0);
+        s->launch_total += 2;
+        s->skip_flag = W.done;
+        // launch the cycle in chunks; between chunks read the done flag so a
+        // converged cycle stops launching (kernels after convergence no-op)
+        const int chunk = (steps <= 8) ? steps : 4;
+        for (int k = 0; k < steps; ++k) {
+            if (k > 0 && k % chunk == 0) {
+                cudaError_t ce = cudaMemcpyAsync(W.pinned_i + 2, W.done, sizeof(int),
+                                                 cudaMemcpyDeviceToHost, st);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+                if (ce != cudaSuccess) {
+                    s->skip_flag = nullptr;
+                    pm_set_error("gmres: %s", cudaGetErrorString(ce));
+                    return PM_ERR_CUDA;
+                }
+                if (W.pinned_i[2]) break;
+            }
+            // W.tmp = R~ v_k (sources already prepared when fuse_prep)
+            pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V + (size_t)k * ldv, W.tmp, prec, st,
+                                         fuse_prep ? 1 : 0);
+            if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
+            // partials ping-pong between W.pb and W.pa
+            k_arn_first<<<nb, kArnThreads, 0, st>>>(W.tmp, W.pb, nb, ld, W.V, ldv, k, nullptr,
+                                                    W.w, W.pa, W.N, W.done);
+            k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, k, nullptr,
+                                                   0, W.w, W.pb, 0, W.N, W.done);
+            k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, k, nullptr,
+                                                   1, W.w, W.pa, 1, W.N, W.done);
+            k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
+                W.pa, nb, ld, W.H, m + 2, k, nullptr, 1, W.cs, W.sn, W.g, W.par, W.done, W.iters,
+                W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, W.N);
+            s->launch_total += 4;
+        }
+        s->skip_flag = nullptr;
+        PM_CUDA_TRY(cudaGetLastError());
+        k_backsolve<<<1, 1, 0, st>>>(W.H, m + 2, W.g, W.iters, W.y, W.scal + 7);
+        k_add_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, W.iters, W.y, W.delta, W.N);
+        s->launch_total += 2;
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+
+    // Enqueue the copies of the cycle's outcome (iterations, done flag, |y|) to the host.
+    pm_status enqueue_cycle_readback() {
+        PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + 1, W.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 7, W.scal + 7, sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+        return PM_OK;
+    }
+
+    // After the synchronisation: iterations of the cycle (launch accounting of the graph form).
+    int cycle_iterations(pm_precision prec) {
+        const int it = W.pinned_i[0];
+        const bool fuse_prep = prec == PM_PREC_FP32 || prec == PM_PREC_FMM;
+        if (fuse_prep && !s->profiling && W.exec) s->launch_total += (long long)it * W.body_launches;
+        return it;
+    }
+
     // Restarted GMRES(m) for A d = b from d = 0 with the operator in `prec`,
     // stopping when the residual estimate is below tol_abs; x += d.
     pm_status gmres(const double* b, double* x, pm_precision prec, double tol_abs, int max_iter,
                     int* iters_used, double* dnorm = nullptr) {
         double dn = 0.0;                    // bound on |x_new - x_old|: sum of the cycles' |y|
-        const int m = W.m;
-        const long long ldv = W.N;
         int total = 0;
-        // the float32 strengths of each basis vector are written by the kernel
-        // that forms it (FP32 / FMM operators)
-        const bool fuse_prep = prec == PM_PREC_FP32 || prec == PM_PREC_FMM;
-        const bool graph = fuse_prep && !s->profiling && ensure_graph(prec);
         PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * W.N, cudaMemcpyDeviceToDevice, st));
         PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * W.N, st));
-        float4* src32 = fuse_prep ? s->src32 : nullptr;
-        const int nb = W.narn, ld = m + 2;
         while (total < max_iter) {
-            const int steps = std::min(m, max_iter - total);
-            W.pinned_par[0] = tol_abs;
-            W.pinned_par[1] = (double)steps;
-            PM_CUDA_TRY(cudaMemcpyAsync(W.par, W.pinned_par, 2 * sizeof(double),
-                                        cudaMemcpyHostToDevice, st));
-            if (graph) {
-                PM_CUDA_TRY(cudaGraphLaunch(W.exec, st));
-            } else {
-                k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
-                k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
-                                                        W.iters, W.r, W.V, s->w, s->wa, src32,
-                                                        s->sig32, s->pp, s->ppad, W.pb, W.N, 0, 0);
-                s->launch_total += 2;
-                s->skip_flag = W.done;
-                // launch the cycle in chunks; between chunks read the done flag so a
-                // converged cycle stops launching (kernels after convergence no-op)
-                const int chunk = (steps <= 8) ? steps : 4;
-                for (int k = 0; k < steps; ++k) {
-                    if (k > 0 && k % chunk == 0) {
-                        cudaError_t ce = cudaMemcpyAsync(W.pinned_i + 2, W.done, sizeof(int),
-                                                         cudaMemcpyDeviceToHost, st);
-                        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-                        if (ce != cudaSuccess) {
-                            s->skip_flag = nullptr;
-                            pm_set_error("gmres: %s", cudaGetErrorString(ce));
-                            return PM_ERR_CUDA;
-                        }
-                        if (W.pinned_i[2]) break;
-                    }
-                    // W.tmp = R~ v_k (sources already prepared when fuse_prep)
-                    pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V + (size_t)k * ldv, W.tmp, prec,
-                                                 st, fuse_prep ? 1 : 0);
-                    if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
-                    // partials ping-pong between W.pb and W.pa
-                    k_arn_first<<<nb, kArnThreads, 0, st>>>(W.tmp, W.pb, nb, ld, W.V, ldv, k,
-                                                            nullptr, W.w, W.pa, W.N, W.done);
-                    k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, k,
-                                                           nullptr, 0, W.w, W.pb, 0, W.N, W.done);
-                    k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, k,
-                                                           nullptr, 1, W.w, W.pa, 1, W.N, W.done);
-                    k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
-                        W.pa, nb, ld, W.H, m + 2, k, nullptr, 1, W.cs, W.sn, W.g, W.par, W.done,
-                        W.iters, W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad,
-                        W.pb, W.N);
-                    s->launch_total += 4;
-                }
-                s->skip_flag = nullptr;
-                PM_CUDA_TRY(cudaGetLastError());
-                k_backsolve<<<1, 1, 0, st>>>(W.H, m + 2, W.g, W.iters, W.y, W.scal + 7);
-                k_add_combo<<<grid_n, 256, 0, st>>>(W.V, ldv, W.iters, W.y, W.delta, W.N);
-                s->launch_total += 2;
-            }
-            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + 1, W.done, sizeof(int), cudaMemcpyDeviceToHost, st));
-            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 7, W.scal + 7, sizeof(double),
-                                        cudaMemcpyDeviceToHost, st));
+            PM_TRY(launch_cycle(prec, tol_abs, std::min(W.m, max_iter - total)));
+            PM_TRY(enqueue_cycle_readback());
             PM_CUDA_TRY(cudaStreamSynchronize(st));
-            const int it = W.pinned_i[0];
+            const int it = cycle_iterations(prec);
             const int converged = W.pinned_i[1];
             if (it > 0) dn += W.pinned[7];
-            if (graph) s->launch_total += 4 + (long long)it * W.body_launches;
             total += it;
             if (converged || it == 0) break;
             // cycle exhausted: restart from the residual of the operator in use
@@ -726,6 +749,17 @@ struct Solver {
         PM_CUDA_TRY(cudaGetLastError());
         *iters_used = total;
         if (dnorm) *dnorm = dn;
+        return PM_OK;
+    }
+
+    // Enqueue u = K~ sigma in the residual precision minus its weighted mean (eq.
+    // representation), with 1/sw the reciprocal of sum w.
+    pm_status enqueue_representation(double inv_sw) {
+        PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig, W.u, residual_prec(), st));
+        PM_TRY(dots(s->w, 0, 1, W.u, W.scal + 6, nullptr));
+        k_add_shift<<<grid_n, 256, 0, st>>>(W.u, W.scal + 6, -inv_sw, W.N);
+        s->launch_total++;
+        PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
     }
 
@@ -755,35 +789,37 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     PM_CUDA_TRY(cudaMemcpyAsync(W.f, f, sizeof(double) * N, h2d, st));
 
-    // mean-zero check of f (Thm. LBsolvable): |sum w f| / (sqrt(sum w) ||f||_w)
+    // mean-zero check of f (Thm. LBsolvable): |sum w f| / (sqrt(sum w) ||f||_w), and |f|
     double sw = 0.0;
     for (double v : s->h_w) sw += v;
     k_mul<<<S.grid_n, 256, 0, st>>>(s->w, W.f, W.tmp, N);
     s->launch_total++;
     PM_TRY(S.dots(W.tmp, 0, 1, W.f, W.scal + 5, nullptr));      // sum w f^2
     PM_TRY(S.dots(s->w, 0, 1, W.f, W.scal + 4, nullptr));       // sum w f
+    PM_TRY(S.dots(W.f, 0, 1, W.f, W.scal + 1, nullptr));        // sum f^2
     PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.scal + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 2, W.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     const double wf = W.pinned[0], wff = W.pinned[1];
+    double fnorm = std::sqrt(W.pinned[2]);
     double removed = 0.0;
-    if (wff > 0.0 && std::fabs(wf) > s->opts.mean_tol * std::sqrt(sw * wff)) {
-        if (!(flags & PM_SOLVE_PROJECT_RHS)) {
-            pm_set_error("pm_solve: f has weighted mean %.3e (relative %.3e > %.1e); pass "
-                         "PM_SOLVE_PROJECT_RHS to subtract it", wf / sw,
-                         std::fabs(wf) / std::sqrt(sw * wff), s->opts.mean_tol);
-            return PM_ERR_RHS_NOT_MEAN_ZERO;
-        }
+    const bool nonzero_mean = wff > 0.0 && std::fabs(wf) > s->opts.mean_tol * std::sqrt(sw * wff);
+    if (nonzero_mean && !(flags & PM_SOLVE_PROJECT_RHS)) {
+        pm_set_error("pm_solve: f has weighted mean %.3e (relative %.3e > %.1e); pass "
+                     "PM_SOLVE_PROJECT_RHS to subtract it", wf / sw,
+                     std::fabs(wf) / std::sqrt(sw * wff), s->opts.mean_tol);
+        return PM_ERR_RHS_NOT_MEAN_ZERO;
     }
     if (flags & PM_SOLVE_PROJECT_RHS) {
         removed = wf / sw;
         k_add_shift<<<S.grid_n, 256, 0, st>>>(W.f, W.scal + 4, -1.0 / sw, N);
         s->launch_total++;
+        PM_TRY(S.norm2(W.f, &fnorm));
     }
-    double fnorm = 0.0;
-    PM_TRY(S.norm2(W.f, &fnorm));
     PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * N, st));
     int iters = 0, refinements = 0, updated = 0;
     double relres = 0.0;
+    bool u_current = false;            // W.u holds the representation of the current sigma
     pm_status result = PM_OK;
     if (fnorm > 0.0) {
         if (prec == PM_PREC_FP64 || prec == PM_PREC_FF) {
@@ -795,41 +831,64 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
             relres = rn / fnorm;
             refinements = 1;
         } else {
-            // iterative refinement: accurate residual, float32-operator GMRES correction.
-            // After a correction d the residual is f - A(sigma + d) = r - A d.  The true
-            // residual is recomputed in the residual precision unless d is so small that
-            // the float32 operator's error on it, at most kOpRelErr |d|, stays below a
-            // tenth of the tolerance: then r - A32 d is the true residual to within
-            // 0.1 tol |f| (opts.residual_update; |d| <= sum of the cycles' |y|).
-            double dnorm = 0.0;
-            bool have_update = false;
+            // Iterative refinement: one float32-operator GMRES cycle per refinement on
+            // the current residual, whose outcome is read with the next residual in one
+            // synchronisation.  After a correction d the residual is f - A(sigma + d) =
+            // r - A d.  It is recomputed in the residual precision after the first
+            // correction (d = sigma is O(|f|)); later it is taken as r - A32 d when the
+            // float32 operator's error on d, at most kOpRelErr |d| (|d| = |y|, orthonormal
+            // basis), stays below a tenth of the tolerance -- then it is the true residual
+            // to within 0.1 tol |f| (opts.residual_update) -- and recomputed otherwise.
+            // A cycle that stops before convergence (restart length or iteration budget)
+            // ends its refinement; the next one starts from the accurate residual.  When
+            // the cycle's target is below the overall tolerance the representation u is
+            // enqueued before the synchronisation too.
+            PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+            double rn = fnorm;
             for (;;) {
-                double rn = 0;
-                if (refinements == 0) {
-                    // sigma = 0: the residual is f itself
-                    PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * N,
-                                                cudaMemcpyDeviceToDevice, st));
-                    rn = fnorm;
-                } else if (have_update && s->opts.residual_update &&
-                           kOpRelErr * dnorm <= 0.1 * tol * fnorm) {
+                relres = rn / fnorm;
+                if (relres <= tol || refinements >= s->opts.max_refine || iters >= maxit) break;
+                const double inner = std::max(s->opts.inner_tol, 0.5 * tol * fnorm / rn);
+                const double tol_abs = inner * rn;
+                PM_CUDA_TRY(cudaMemcpyAsync(W.r, W.res, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+                PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * N, st));
+                PM_TRY(S.launch_cycle(prec, tol_abs, std::min(W.m, maxit - iters)));
+                k_axpy<<<S.grid_n, 256, 0, st>>>(W.sig, W.delta, 1.0, N);
+                s->launch_total++;
+                const bool predict_update = s->opts.residual_update && refinements >= 1;
+                if (predict_update) {
                     PM_TRY(S.apply_A(W.delta, W.w, prec, nullptr));
                     k_axpy<<<S.grid_n, 256, 0, st>>>(W.res, W.w, -1.0, N);
                     s->launch_total++;
-                    PM_TRY(S.norm2(W.res, &rn));
-                    ++updated;
                 } else {
                     PM_TRY(S.true_residual(W.f, W.sig, W.res));
-                    PM_TRY(S.norm2(W.res, &rn));
                 }
-                relres = rn / fnorm;
-                if (relres <= tol || refinements >= s->opts.max_refine || iters >= maxit) break;
-                int it = 0;
-                const double inner = std::max(s->opts.inner_tol, 0.5 * tol * fnorm / rn);
-                PM_TRY(S.gmres(W.res, W.sig, prec, inner * rn, maxit - iters, &it, &dnorm));
-                have_update = true;
+                PM_TRY(S.dots(W.res, 0, 1, W.res, W.scal + 1, nullptr));
+                const bool predict_final = tol_abs <= tol * fnorm;
+                if (predict_final) PM_TRY(S.enqueue_representation(1.0 / sw));
+                PM_TRY(S.enqueue_cycle_readback());
+                PM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 1, W.scal + 1, sizeof(double),
+                                            cudaMemcpyDeviceToHost, st));
+                PM_CUDA_TRY(cudaStreamSynchronize(st));
+                const int it = S.cycle_iterations(prec);
+                const double dnorm = W.pinned[7];
+                rn = std::sqrt(W.pinned[1]);
                 iters += it;
                 ++refinements;
-                if (it == 0) break;
+                u_current = predict_final;
+                if (predict_update) {
+                    if (kOpRelErr * dnorm > 0.1 * tol * fnorm) {
+                        // the correction was not small: recompute the true residual
+                        PM_TRY(S.true_residual(W.f, W.sig, W.res));
+                        PM_TRY(S.norm2(W.res, &rn));
+                    } else {
+                        ++updated;
+                    }
+                }
+                if (it == 0) {
+                    relres = rn / fnorm;
+                    break;
+                }
             }
         }
         if (!(relres <= tol)) {
@@ -839,11 +898,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
         }
     }
     // u = K~ sigma (accurate), then subtract its weighted mean (eq. representation)
-    PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig, W.u, S.residual_prec(), st));
-    PM_TRY(S.dots(s->w, 0, 1, W.u, W.scal + 6, nullptr));
-    k_add_shift<<<S.grid_n, 256, 0, st>>>(W.u, W.scal + 6, -1.0 / sw, N);
-    s->launch_total++;
-    PM_CUDA_TRY(cudaGetLastError());
+    if (!u_current) PM_TRY(S.enqueue_representation(1.0 / sw));
     PM_CUDA_TRY(cudaMemcpyAsync(u, W.u, sizeof(double) * N, d2h, st));
     if (sigma_out)
         PM_CUDA_TRY(cudaMemcpyAsync(sigma_out, W.sig, sizeof(double) * N, d2h, st));
@@ -853,8 +908,8 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
         info->refinements = refinements;
         info->residual = relres;
         info->removed_mean = removed;
-        info->residual_updates = updated;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->residual_updates = updated;
     }
     return result;
 }
