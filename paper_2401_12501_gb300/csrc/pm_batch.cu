@@ -186,6 +186,67 @@ k_near_multi32(int N, int ppad, int npatch, const int* __restrict__ row_ptr,
     if (lane == 0) out[r * ld_out + i] = (double)hi + (double)lo;
 }
 
+// The same sums, one block per (patch, chunk of 32 right-hand sides): the rows of a
+// patch share most of their near patches, so the block stages sigma of the union of
+// its rows' near patches for its 32 right-hand sides in shared memory ([node][rhs],
+// row stride 33 so that both the staging writes and the lane-per-rhs reads avoid bank
+// conflicts), and each warp walks its rows' correction blocks with broadcast loads of
+// the values, lane = right-hand side.  Each correction value is read once per 32
+// right-hand sides instead of once per right-hand side.
+constexpr int kPatchRhs = 32;
+
+__global__ void __launch_bounds__(256)
+k_near_multi32_patch(int N, int pp, int ppad, int npatch, const int* __restrict__ row_ptr,
+                     const int* __restrict__ blk_u, const int* __restrict__ pu_ptr,
+                     const int* __restrict__ pu_list, const float* __restrict__ vals,
+                     const float* __restrict__ sig32, const float2* __restrict__ partial,
+                     int nsplit, int nrhs, double* __restrict__ out, long long ld_out,
+                     const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ float shs[];                     // [u * ppad + k][33]
+    const int P = blockIdx.x;
+    const int r0 = blockIdx.y * kPatchRhs;
+    const int nr = min(kPatchRhs, nrhs - r0);
+    const int u0 = pu_ptr[P], U = pu_ptr[P + 1] - u0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // stage: index e = ((u * 32 + rr) * ppad + k): k fastest, contiguous in global memory
+    const int total = U * kPatchRhs * ppad;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k = e % ppad, t = e / ppad;
+        const int rr = t % kPatchRhs, u = t / kPatchRhs;
+        float v = 0.f;
+        if (rr < nr && k < pp)
+            v = sig32[(size_t)(r0 + rr) * npatch * ppad + (size_t)pu_list[u0 + u] * ppad + k];
+        shs[(u * ppad + k) * 33 + rr] = v;
+    }
+    __syncthreads();
+    const int r = r0 + lane;
+    const bool act = lane < nr;
+    const int q4 = ppad >> 2;
+    for (int t = warp; t < pp; t += blockDim.x >> 5) {
+        const int i = P * pp + t;
+        float hi = 0.f, lo = 0.f;
+        if (act)
+            for (int sp = 0; sp < nsplit; ++sp) {
+                const float2 v = partial[((size_t)r * nsplit + sp) * N + i];
+                two_sum_acc(hi, lo, v.x);
+                lo += v.y;
+            }
+        float acc = 0.f;
+        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+            const float4* c4 = reinterpret_cast<const float4*>(vals + (size_t)b * ppad);
+            const float* su = shs + blk_u[b] * ppad * 33 + lane;
+            for (int k4 = 0; k4 < q4; ++k4) {
+                const float4 c = __ldg(c4 + k4);
+                const float* sk = su + 4 * k4 * 33;
+                acc = fmaf(c.x, sk[0], fmaf(c.y, sk[33], fmaf(c.z, sk[66], fmaf(c.w, sk[99], acc))));
+            }
+        }
+        two_sum_acc(hi, lo, acc);
+        if (act) out[r * ld_out + i] = (double)hi + (double)lo;
+    }
+}
+
 // ------------------------------------------------------------------ float-float batched sums
 // (arithmetic and the coordinate split in pm_ff.cuh)
 using pmff::ff;
@@ -346,6 +407,11 @@ struct PmBatchWork {
     float2* sff = nullptr;     // [cap][N]
     float2* part = nullptr;    // [cap][nsplit_max][N]
     int nsplit_max = 0;
+    // patch-blocked near field: per patch the union of its rows' near patches, per
+    // correction block its index in that union (built once from the CSR)
+    int *pu_ptr = nullptr, *pu_list = nullptr, *blk_u = nullptr;
+    int umax = 0;
+    bool patch_tried = false;
 };
 
 void pm_batch_free(pm_surface* s) {
@@ -354,6 +420,9 @@ void pm_batch_free(pm_surface* s) {
     pm_dfree(s->batch->sig32);
     pm_dfree(s->batch->sff);
     pm_dfree(s->batch->part);
+    pm_dfree(s->batch->pu_ptr);
+    pm_dfree(s->batch->pu_list);
+    pm_dfree(s->batch->blk_u);
     delete s->batch;
     s->batch = nullptr;
 }
@@ -379,6 +448,43 @@ static int batch_splits(const pm_surface* s, int nrhs, int rb) {
     const int want = 8 * s->ctx->num_sms;
     int ns = (want + tblocks / 2) / tblocks;
     return std::max(1, std::min(ns, std::min(8, std::max(1, s->N / 256))));
+}
+
+// Near-patch unions of every patch (see k_near_multi32_patch); umax = 0 when the
+// largest union's staging would not fit in shared memory (the per-row kernel is used).
+static pm_status build_patch_unions(pm_surface* s, PmBatchWork& B) {
+    B.patch_tried = true;
+    const int N = s->N, np = s->npatch, pp = s->pp;
+    std::vector<int> rp(N + 1), bp(s->nblk);
+    PM_CUDA_TRY(cudaMemcpy(rp.data(), s->row_ptr, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost));
+    PM_CUDA_TRY(cudaMemcpy(bp.data(), s->blk_patch, sizeof(int) * s->nblk, cudaMemcpyDeviceToHost));
+    std::vector<int> ptr(np + 1, 0), list, bu(s->nblk, 0);
+    int umax = 0;
+    for (int P = 0; P < np; ++P) {
+        std::vector<int> un;
+        for (int i = P * pp; i < (P + 1) * pp; ++i)
+            for (int b = rp[i]; b < rp[i + 1]; ++b) un.push_back(bp[b]);
+        std::sort(un.begin(), un.end());
+        un.erase(std::unique(un.begin(), un.end()), un.end());
+        for (int i = P * pp; i < (P + 1) * pp; ++i)
+            for (int b = rp[i]; b < rp[i + 1]; ++b)
+                bu[b] = (int)(std::lower_bound(un.begin(), un.end(), bp[b]) - un.begin());
+        list.insert(list.end(), un.begin(), un.end());
+        ptr[P + 1] = (int)list.size();
+        umax = std::max(umax, (int)un.size());
+    }
+    const size_t smem = (size_t)umax * s->ppad * 33 * sizeof(float);
+    if (smem > 200 * 1024) return PM_OK;               // too large: keep the per-row kernel
+    PM_TRY(pm_dmalloc(&B.pu_ptr, ptr.size()));
+    PM_TRY(pm_dmalloc(&B.pu_list, std::max<size_t>(1, list.size())));
+    PM_TRY(pm_dmalloc(&B.blk_u, std::max<size_t>(1, bu.size())));
+    PM_CUDA_TRY(cudaMemcpy(B.pu_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(B.pu_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(B.blk_u, bu.data(), sizeof(int) * bu.size(), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_near_multi32_patch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    B.umax = umax;
+    return PM_OK;
 }
 
 // out[r*ld_out + i] = (R~ or K~) sigma_r, r < nrhs; sigma_r at sigma + r*ld_sigma.
@@ -430,11 +536,20 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
                 k_direct_multi32<false><<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N,
                                                                chunk, s->eps2, B.part, ns, skip);
         }
+        if (!B.patch_tried) PM_TRY(build_patch_unions(s, B));
         PhaseTimer t(s, PM_PHASE_NEAR, st);
-        dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
-        k_near_multi32<<<gn, 256, 0, st>>>(N, s->ppad, s->npatch, s->row_ptr, s->blk_patch,
-                                           kernel_K ? s->cK32 : s->cR32, B.sig32, B.part, ns, out,
-                                           ld_out, skip);
+        if (B.umax > 0) {
+            const dim3 gn(s->npatch, pm_ceil_div(nrhs, kPatchRhs));
+            const size_t smem = (size_t)B.umax * s->ppad * 33 * sizeof(float);
+            k_near_multi32_patch<<<gn, 256, smem, st>>>(
+                N, s->pp, s->ppad, s->npatch, s->row_ptr, B.blk_u, B.pu_ptr, B.pu_list,
+                kernel_K ? s->cK32 : s->cR32, B.sig32, B.part, ns, nrhs, out, ld_out, skip);
+        } else {
+            dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
+            k_near_multi32<<<gn, 256, 0, st>>>(N, s->ppad, s->npatch, s->row_ptr, s->blk_patch,
+                                               kernel_K ? s->cK32 : s->cR32, B.sig32, B.part, ns,
+                                               out, ld_out, skip);
+        }
     }
     s->launch_total += 3;
     PM_CUDA_TRY(cudaGetLastError());
