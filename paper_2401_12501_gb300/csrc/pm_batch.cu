@@ -474,15 +474,18 @@ static pm_status build_patch_unions(pm_surface* s, PmBatchWork& B) {
         umax = std::max(umax, (int)un.size());
     }
     const size_t smem = (size_t)umax * s->ppad * 33 * sizeof(float);
-    if (smem > 200 * 1024) return PM_OK;               // too large: keep the per-row kernel
+    constexpr int kSmemCap = 200 * 1024;
+    if (smem > (size_t)kSmemCap) return PM_OK;         // too large: keep the per-row kernel
     PM_TRY(pm_dmalloc(&B.pu_ptr, ptr.size()));
     PM_TRY(pm_dmalloc(&B.pu_list, std::max<size_t>(1, list.size())));
     PM_TRY(pm_dmalloc(&B.blk_u, std::max<size_t>(1, bu.size())));
     PM_CUDA_TRY(cudaMemcpy(B.pu_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice));
     PM_CUDA_TRY(cudaMemcpy(B.pu_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
     PM_CUDA_TRY(cudaMemcpy(B.blk_u, bu.data(), sizeof(int) * bu.size(), cudaMemcpyHostToDevice));
+    // the attribute is process-wide: always the same cap, so that surfaces prepared by
+    // different threads never lower it under one another's launches
     PM_CUDA_TRY(cudaFuncSetAttribute(k_near_multi32_patch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+                                     kSmemCap));
     B.umax = umax;
     return PM_OK;
 }
