@@ -76,7 +76,8 @@ typedef struct {
                                Sec. 6.1.2 uses 1.5                                     */
     double theta_tol;       /* self rule: absolute tolerance of the adaptive theta panels
                                on int L(theta)^2 (Sec. 6.1.1 criterion); 1e-14          */
-    double theta_max_width; /* self rule: largest theta panel (radians); pi/16          */
+    double theta_max_width; /* self rule: largest theta panel (radians); 0 (default) =
+                               pi/16 for p <= 10, pi/24 for p = 11                       */
     double near_eta;        /* near rule: split a sub-square while the target is within
                                2*near_eta*(its corner radius) of its centre; 1.0       */
     int near_max_depth;     /* near rule: deepest subdivision level; 12                 */

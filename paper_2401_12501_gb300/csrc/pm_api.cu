@@ -50,7 +50,7 @@ extern "C" void pm_default_opts(pm_opts* o) {
     if (!o) return;
     o->near_factor = 1.5;
     o->theta_tol = 1e-14;
-    o->theta_max_width = M_PI / 16;
+    o->theta_max_width = 0.0;          // automatic: pi/16, or pi/24 for p = 11 (surface create)
     o->near_eta = 1.0;
     o->near_max_depth = 12;
     o->near_max_leaves = 512;
@@ -385,7 +385,12 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     // self-rule theta plan (geometry of the reference square only)
     std::vector<int> off;
     std::vector<double> ang, wts, len;
-    pm_theta_plan(T, s->opts.theta_tol, s->opts.theta_max_width, off, ang, wts, len);
+    // Largest theta panel: the self-rule integrand carries the degree p - 1 Lagrange
+    // basis along each ray; pi/16 panels integrate it to ~1e-13 up to p = 10, p = 11
+    // needs pi/24 (pi/16 leaves ~5e-7 in the self weights).
+    const double theta_w = s->opts.theta_max_width > 0.0 ? s->opts.theta_max_width
+                                                         : (p >= 11 ? M_PI / 24 : M_PI / 16);
+    pm_theta_plan(T, s->opts.theta_tol, theta_w, off, ang, wts, len);
     s->nth_total = (int)ang.size();
     PM_STEP(pm_dmalloc(&s->th_off, off.size()));
     PM_STEP(pm_dmalloc(&s->th_ang, ang.size()));

@@ -249,3 +249,31 @@ def test_symmetric_tile_pair_sums_match_one_sided(ctx, name):
         assert np.array_equal(y1, f1(sig, prec))            # fixed-order reductions
     for s in surf.values():
         s.close()
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 11])
+def test_patch_orders_against_oracle_rows(ctx, p):
+    """Every supported patch order class: p = 3 (smallest tables), odd p with padded
+    float32 rows (p^2 = 25, 49 not a multiple of 4), p = 11 (the largest the library
+    accepts).  Ellipsoid (1, 1.5, 2), 24 patches, variable coefficient; the float64,
+    float32 and float-float applies against the oracle on sampled rows."""
+    import paper_2401_12501_gb300 as pm
+    from oracle.operator import Discretization, NearField, apply_K, apply_R
+    from workloads.coefficients import ellipsoid_coefficient
+    from workloads.surfaces import cubed_sphere
+    surf = cubed_sphere(2, p, axes=(1.0, 1.5, 2.0))
+    co = ellipsoid_coefficient(surf)
+    s = pm.Surface.from_fixture(ctx, surf)
+    s.set_coeff(co.a, co.grad_a)
+    rng = np.random.default_rng(30 + p)
+    rows = sorted(set([0, surf.N - 1, p * p - 1, p * p] + [int(i) for i in rng.integers(0, surf.N, 8)]))
+    d = Discretization(surf.nodes, surf.normals, surf.tangents, surf.curvature, surf.weights,
+                       co.a, co.grad_a, surf.npatch, surf.p)
+    nf = NearField(d, rows=rows, processes=oracle_processes())
+    sigma = rng.standard_normal(surf.N) + 1.0
+    oR, oK = apply_R(d, nf, sigma, rows), apply_K(d, nf, sigma, rows)
+    for prec, tol in (("fp64", 1e-10), ("ff", 1e-10), ("fp32", 1e-5)):
+        yR, yK = s.apply_R(sigma, prec)[rows], s.apply_K(sigma, prec)[rows]
+        assert np.abs(yR - oR).max() <= tol * np.abs(oR).max(), (p, prec)
+        assert np.abs(yK - oK).max() <= tol * np.abs(oK).max(), (p, prec)
+    s.close()

@@ -201,3 +201,11 @@ def test_residual_update_keeps_true_residual(ctx, name, tol):
     assert t1 <= tol and t0 <= tol, (t0, t1)
     assert abs(t1 - i1.residual) <= 0.2 * tol                 # the reported residual is the true one
     assert rel_l2(u1, u0, wl.surface.weights) < 10 * tol
+
+
+def test_zero_right_hand_side(ctx):
+    """f = 0: u = 0 and sigma = 0 exactly, no iterations, residual 0, no error."""
+    wl, s = setup(ctx, "ellipsoid_small")
+    u, info, sig = s.solve(np.zeros(wl.N), tol=1e-10, return_sigma=True)
+    assert np.all(u == 0.0) and np.all(sig == 0.0)
+    assert info[0].iterations == 0 and info[0].residual == 0.0
