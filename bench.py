@@ -152,6 +152,24 @@ def run_oracle_subprocess(workload: str, seconds: float):
 PHASES = ["prep", "direct_R32", "direct_K32", "near", "vec", "direct_ff_or_64"]
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest value over the ranks of the job (a replica job takes as long as
+    its slowest replica); the value itself for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, pairs_per_step, ms_per_step):
+    """Whole-job smooth-sum pairs per second (Gpairs/s): every replica runs the same
+    step, so the job evaluates world * pairs_per_step pairs per step time."""
+    return world * pairs_per_step / (ms_per_step * 1e-3) / 1e9
+
+
 def _nvtx_push(name):
     try:
         import torch
@@ -236,11 +254,7 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
     launches_timed = surf.profile_read(len(PHASES))[1]
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
 
     # phase split: the same steps again with per-phase events (event records
     # cannot sit inside the graph-driven GMRES cycle, so this pass issues its
@@ -266,7 +280,7 @@ def run_gpu(args, rank, world, local_rank):
     it = statistics.mean(i.iterations for i in infos)
     rf = statistics.mean(i.refinements for i in infos)
     applies = it + rf + 1
-    value = world * applies * pairs / (ms_per_step * 1e-3) / 1e9
+    value = job_throughput(world, applies * pairs, ms_per_step)
     solves_per_s = world * 1e3 / ms_per_step
 
     # end-to-end through the C ABI with host (pinned) buffers: f in, u out
@@ -277,7 +291,7 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(args.steps):
         u, _ = surf.solve(f_h.numpy(), tol=tol, prec="fp32")
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_value = world * applies * pairs / e2e_s / 1e9
+    e2e_value = job_throughput(world, applies * pairs, e2e_s * 1e3)
 
     # isolated float32 remainder apply (inputs resident, L2 flushed)
     sig = torch.from_numpy(np.random.default_rng(1).standard_normal(N)).to(dev)

@@ -251,7 +251,7 @@ def test_symmetric_tile_pair_sums_match_one_sided(ctx, name):
         s.close()
 
 
-@pytest.mark.parametrize("p", [3, 5, 7, 11])
+@pytest.mark.parametrize("p", [2, 3, 5, 7, 11])
 def test_patch_orders_against_oracle_rows(ctx, p):
     """Every supported patch order class: p = 3 (smallest tables), odd p with padded
     float32 rows (p^2 = 25, 49 not a multiple of 4), p = 11 (the largest the library
