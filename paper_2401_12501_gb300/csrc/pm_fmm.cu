@@ -394,14 +394,65 @@ k_fmm_l2p(DevTree t, const float4* __restrict__ tgt, const float* __restrict__ L
 // the box size h, through  r = h (d + (t_l - t_m) / 2)  between target point l
 // and source point m.  The kernels are homogeneous: r_a r_b / r^4 and r_a / r^2
 // scale as h^-2 and h^-1, lg2 r^2 = lg2 u^2 + 2 lg2 h.  So one unit-box operator
-// per offset serves every level: rows c * 512 + l (kernel c, target point l),
-// columns m, column-major.  For each offset the columns of all box pairs with
-// that offset are gathered into B, one strided-batched GEMM forms C = A_d B_d
-// for all offsets, and each target box sums its V-list columns of C, scaled for
-// its level, in V-list order.
-constexpr int kNOff = 316;
+// per offset serves every level.
+//
+// The offsets fall into 16 classes under the 48 signed axis permutations g of
+// the cube, (g v)_a = s_a v_{pi(a)}: every d is g d_c for a canonical d_c with
+// d_c,x >= d_c,y >= d_c,z >= 0.  The Chebyshev grid is closed under g (the
+// points are symmetric about 0), so with the point map g.l (axis a of g.l is
+// axis pi(a) of l, mirrored k -> n-1-k where s_a < 0) one has
+// r(d, g.l', g.m') = g r(d_c, l', m'), hence
+//   sum_m phi_ab(r(d, l, m)) M[m] = s_a s_b  [A_{d_c} Mt]_{pi(a) pi(b)} (g^-1 . l),
+//   Mt[m'] = M[g.m'],
+// and likewise s_a [.]_{pi(a)} for r_a / r^2; the log kernel is invariant.
+// Only the 16 canonical operators are stored (rows c * 512 + l for kernel c and
+// target point l, columns m, column-major).  The multipoles of all V-list pairs
+// of one class are gathered, permuted into the canonical frame, as the columns
+// of B; one GEMM per class forms C = A_c B; each target box sums its V-list
+// columns of C, mapped back through g and scaled for its level, in V-list order.
+constexpr int kNClass = 16;
 
-__global__ void k_fmm_build_op(int which_K, const int3* __restrict__ offs, float* __restrict__ A) {
+__host__ __device__ __forceinline__ int3 canonical_offset(int c) {
+    // enumeration of d_c = (i, j, k), i in {2, 3}, i >= j >= k >= 0
+    int n = 0;
+    for (int i = 2; i <= 3; ++i)
+        for (int j = 0; j <= i; ++j)
+            for (int k = 0; k <= j; ++k) {
+                if (n == c) return make_int3(i, j, k);
+                ++n;
+            }
+    return make_int3(0, 0, 0);
+}
+
+// symmetry code: bits 0-1 pi(0), 2-3 pi(1), 4-5 pi(2), bit 6 + a set where s_a = -1
+__device__ __forceinline__ int sym_pi(int g, int a) { return (g >> (2 * a)) & 3; }
+__device__ __forceinline__ bool sym_neg(int g, int a) { return (g >> (6 + a)) & 1; }
+
+// g.m: axis a of the result is axis pi(a) of m, mirrored where s_a < 0
+__device__ __forceinline__ int sym_apply(int g, int m) {
+    const int mi[3] = {m / (kFmmN * kFmmN), (m / kFmmN) % kFmmN, m % kFmmN};
+    int o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int v = mi[sym_pi(g, a)];
+        o[a] = sym_neg(g, a) ? kFmmN - 1 - v : v;
+    }
+    return (o[0] * kFmmN + o[1]) * kFmmN + o[2];
+}
+
+// g^-1.l: axis pi(a) of the result is axis a of l, mirrored where s_a < 0
+__device__ __forceinline__ int sym_apply_inv(int g, int l) {
+    const int li[3] = {l / (kFmmN * kFmmN), (l / kFmmN) % kFmmN, l % kFmmN};
+    int o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int v = sym_neg(g, a) ? kFmmN - 1 - li[a] : li[a];
+        o[sym_pi(g, a)] = v;
+    }
+    return (o[0] * kFmmN + o[1]) * kFmmN + o[2];
+}
+
+__global__ void k_fmm_build_op(int which_K, float* __restrict__ A) {
     const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
     const int o = blockIdx.y;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -410,7 +461,7 @@ __global__ void k_fmm_build_op(int which_K, const int3* __restrict__ offs, float
     const int c = row / kFmmN3, l = row % kFmmN3;
     const int l1 = l / (kFmmN * kFmmN), l2 = (l / kFmmN) % kFmmN, l3 = l % kFmmN;
     const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
-    const int3 d = offs[o];
+    const int3 d = canonical_offset(o);
     auto cheb = [](int k) { return cos(M_PI * (2 * k + 1) / (2.0 * kFmmN)); };
     const double ux = d.x + 0.5 * (cheb(l1) - cheb(m1));
     const double uy = d.y + 0.5 * (cheb(l2) - cheb(m2));
@@ -427,14 +478,20 @@ __global__ void k_fmm_build_op(int which_K, const int3* __restrict__ offs, float
     A[(size_t)o * rows * kFmmN3 + e] = (float)v;
 }
 
-// B[:, vcol[e]] = M of the e-th V-list source (one block per V-list entry)
+// B[:, vcol[e]] = M of the e-th V-list source in its class's frame:
+// B[m', vcol[e]] = M_S[g.m'] (one block per V-list entry)
 __global__ void __launch_bounds__(kThreads)
-k_fmm_m2l_gather(const int* __restrict__ v_list, const int* __restrict__ vcol, int e0,
-                 const float* __restrict__ M, float* __restrict__ B, const int* __restrict__ skip) {
+k_fmm_m2l_gather(const int* __restrict__ v_list, const int* __restrict__ vcol,
+                 const int* __restrict__ vsym, const float* __restrict__ M,
+                 float* __restrict__ B, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int e = e0 + blockIdx.x;
+    __shared__ float sm[kFmmN3];
+    const int e = blockIdx.x;
     const int m = threadIdx.x;
-    if (m < kFmmN3) B[(size_t)vcol[e] * kFmmN3 + m] = M[(size_t)v_list[e] * kFmmN3 + m];
+    const float* Ms = M + (size_t)v_list[e] * kFmmN3;
+    if (m < kFmmN3) sm[m] = Ms[m];
+    __syncthreads();
+    if (m < kFmmN3) B[(size_t)vcol[e] * kFmmN3 + m] = sm[sym_apply(vsym[e], m)];
 }
 
 // sum of a box's multipole values (the log kernel's level term), fixed order
@@ -455,37 +512,56 @@ k_fmm_msum(int box0, const float* __restrict__ M, float* __restrict__ msum,
     }
 }
 
-// L_T[c][l] = sum over V(T), in V-list order, of scale_c(h) C[c * 512 + l, vcol[e]]
-// (+ 2 lg2(h) msum_S for the log kernel); one block per target box of level >= 2.
+// L_T[c][l] = sum over V(T), in V-list order, of scale_c(h) times the entry of
+// C's column vcol[e] that g maps to (c, l) (+ 2 lg2(h) msum_S for the log
+// kernel); one block per (target box of level >= 2, kernel c).  The permuted
+// reads of a column component stay within its 2 KB, which the block's warps
+// read whole (through L1).
 template <bool KERNEL_K>
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* __restrict__ vcol,
-                  const float* __restrict__ msum, float* __restrict__ Lc,
-                  const int* __restrict__ skip) {
+                  const int* __restrict__ vsym, const float* __restrict__ msum,
+                  float* __restrict__ Lc, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int box = box0 + blockIdx.x;
+    constexpr int C = KERNEL_K ? 1 : 9;
+    constexpr int rows = C * kFmmN3;
+    const int box = box0 + blockIdx.x, q = blockIdx.y;
+    const int l = threadIdx.x;
+    if (l >= kFmmN3) return;
     int lev = 0;
     while (lev + 1 <= t.depth && t.lev_off[lev + 1] <= box) ++lev;
     const float h = t.L0 / (float)(1 << lev);
-    constexpr int C = KERNEL_K ? 1 : 9;
-    constexpr int rows = C * kFmmN3;
-    const int l = threadIdx.x;
-    if (l >= kFmmN3) return;
     const int e0 = t.v_off[box], e1 = t.v_off[box + 1];
+    // kernel q reads kernel (pi(a), pi(b)) of the canonical frame, sign s_a s_b
+    // (q < 6: the pair (a, b) = (pa[q], pb[q])), or pi(a), sign s_a (q = 6 + a)
+    const int qa = q < 6 ? (q < 3 ? 0 : (q < 5 ? 1 : 2)) : q - 6;
+    const int qb = q < 6 ? (q < 3 ? q : (q < 5 ? q - 2 : 2)) : -1;
+    float acc = 0.f;
+    for (int e = e0; e < e1; ++e) {
+        const int g = vsym[e];
+        const int lp = sym_apply_inv(g, l);
+        const float* col = Cm + (size_t)vcol[e] * rows;
+        if (KERNEL_K) {
+            acc += __ldg(col + lp);
+        } else if (qb >= 0) {
+            const int x = sym_pi(g, qa), y = sym_pi(g, qb);
+            const int lo = min(x, y), hi = max(x, y);
+            const int qc = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+            const float v = __ldg(col + qc * kFmmN3 + lp);
+            acc += (sym_neg(g, qa) != sym_neg(g, qb)) ? -v : v;
+        } else {
+            const float v = __ldg(col + (6 + sym_pi(g, qa)) * kFmmN3 + lp);
+            acc += sym_neg(g, qa) ? -v : v;
+        }
+    }
     if (KERNEL_K) {
         const float lh = 2.f * log2f(h);
-        float acc = 0.f;
-        for (int e = e0; e < e1; ++e)
-            acc += Cm[(size_t)vcol[e] * rows + l] + lh * msum[t.v_list[e]];
-        Lc[(size_t)box * kFmmN3 + l] = acc;
+        float ms = 0.f;
+        for (int e = e0; e < e1; ++e) ms += msum[t.v_list[e]];
+        Lc[(size_t)box * kFmmN3 + l] = acc + lh * ms;
     } else {
-        const float s2 = 1.f / (h * h), s1 = 1.f / h;
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            float acc = 0.f;
-            for (int e = e0; e < e1; ++e) acc += Cm[(size_t)vcol[e] * rows + q * kFmmN3 + l];
-            Lc[((size_t)box * C + q) * kFmmN3 + l] = acc * (q < 6 ? s2 : s1);
-        }
+        const float sc = q < 6 ? 1.f / (h * h) : 1.f / h;
+        Lc[((size_t)box * C + q) * kFmmN3 + l] = acc * sc;
     }
 }
 
@@ -506,15 +582,17 @@ struct PmFmmTree {
     float* M = nullptr;
     float* Lc = nullptr;     // [nbox][9][512]
     long long p2p_pairs = 0, m2l_pairs = 0;
-    // M2L as GEMMs: V-list entry -> column (offset * nmax + rank within the offset)
-    int nmax = 0, nv = 0;
-    int* vcol = nullptr;
+    // M2L as GEMMs: V-list entry -> column (class start + rank within the class)
+    // and the symmetry g that maps its offset to the class's canonical offset
+    int nv = 0;
+    std::vector<int> cls_start;   // [kNClass + 1]
+    int *vcol = nullptr, *vsym = nullptr;
     float *Bm = nullptr, *Cm = nullptr, *msum = nullptr;
     cublasHandle_t blas = nullptr;
     void* blas_ws = nullptr;
     ~PmFmmTree() {
         if (blas) cublasDestroy(blas);
-        pm_dfree(vcol); pm_dfree(Bm); pm_dfree(Cm); pm_dfree(msum);
+        pm_dfree(vcol); pm_dfree(vsym); pm_dfree(Bm); pm_dfree(Cm); pm_dfree(msum);
         if (blas_ws) cudaFree(blas_ws);
         pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
         pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
@@ -541,19 +619,28 @@ struct KeyHash {
     }
 };
 
-// index of a V-list offset d (max |d_i| in {2, 3}) in 0..315, or -1
-int off_index(int dx, int dy, int dz) {
-    if (std::max({std::abs(dx), std::abs(dy), std::abs(dz)}) < 2 || std::abs(dx) > 3 ||
-        std::abs(dy) > 3 || std::abs(dz) > 3)
-        return -1;
-    int k = 0;
-    for (int x = -3; x <= 3; ++x)
-        for (int y = -3; y <= 3; ++y)
-            for (int z = -3; z <= 3; ++z) {
-                if (std::max({std::abs(x), std::abs(y), std::abs(z)}) < 2) continue;
-                if (x == dx && y == dy && z == dz) return k;
-                ++k;
-            }
+// Class of a V-list offset d (max |d_i| in {2, 3}) and the symmetry code g with
+// d = g d_c (see the M2L section); -1 when d is not a V-list offset.  Axes are
+// ranked by |d_a| (descending, ties by axis) to give pi; s_a is the sign of d_a.
+int offset_class(int3 d, int* sym) {
+    const int ad[3] = {std::abs(d.x), std::abs(d.y), std::abs(d.z)};
+    if (std::max({ad[0], ad[1], ad[2]}) < 2 || std::max({ad[0], ad[1], ad[2]}) > 3) return -1;
+    int order[3] = {0, 1, 2};
+    std::stable_sort(order, order + 3, [&](int a, int b) { return ad[a] > ad[b]; });
+    int pi[3];
+    for (int k = 0; k < 3; ++k) pi[order[k]] = k;
+    const int dv[3] = {d.x, d.y, d.z};
+    int g = 0;
+    for (int a = 0; a < 3; ++a) {
+        g |= pi[a] << (2 * a);
+        if (dv[a] < 0) g |= 1 << (6 + a);
+    }
+    *sym = g;
+    const int3 dc = make_int3(ad[order[0]], ad[order[1]], ad[order[2]]);
+    for (int c = 0; c < kNClass; ++c) {
+        const int3 o = canonical_offset(c);
+        if (o.x == dc.x && o.y == dc.y && o.z == dc.z) return c;
+    }
     return -1;
 }
 
@@ -789,25 +876,28 @@ pm_status pm_fmm_build(pm_surface* s) {
     PM_TRY(up(&T->u_off, u_off));
     PM_TRY(up(&T->u_list, u_list));
     PM_TRY(up(&T->box_ijk, ijk));
-    // M2L columns: group the V-list entries by offset
+    // M2L columns: group the V-list entries by offset class
     {
-        std::vector<int> cnt_o(kNOff, 0), rank(v_list.size());
+        const size_t nv = v_list.size();
+        std::vector<int> cls(nv), rank(nv), vsym(nv), cnt(kNClass, 0);
         for (int b = 0; b < T->nbox; ++b)
             for (int e = v_off[b]; e < v_off[b + 1]; ++e) {
                 const int3 dt = ijk[b], ds = ijk[v_list[e]];
-                const int o = off_index(dt.x - ds.x, dt.y - ds.y, dt.z - ds.z);
-                if (o < 0) {
+                const int c = offset_class(make_int3(dt.x - ds.x, dt.y - ds.y, dt.z - ds.z), &vsym[e]);
+                if (c < 0) {
                     pm_set_error("pm_fmm_build: V-list offset outside the interaction range");
                     return PM_ERR_INTERNAL;
                 }
-                rank[e] = (o << 20) | cnt_o[o]++;      // (offset, rank) packed, rank < 2^20
+                cls[e] = c;
+                rank[e] = cnt[c]++;
             }
-        T->nmax = std::max(1, *std::max_element(cnt_o.begin(), cnt_o.end()));
-        std::vector<int> vcol(v_list.size());
-        for (size_t e = 0; e < v_list.size(); ++e)
-            vcol[e] = (rank[e] >> 20) * T->nmax + (rank[e] & ((1 << 20) - 1));
-        T->nv = (int)v_list.size();
+        T->cls_start.assign(kNClass + 1, 0);
+        for (int c = 0; c < kNClass; ++c) T->cls_start[c + 1] = T->cls_start[c] + cnt[c];
+        std::vector<int> vcol(nv);
+        for (size_t e = 0; e < nv; ++e) vcol[e] = T->cls_start[cls[e]] + rank[e];
+        T->nv = (int)nv;
         PM_TRY(up(&T->vcol, vcol));
+        PM_TRY(up(&T->vsym, vsym));
     }
     PM_TRY(pm_dmalloc(&T->sorted, N));
     PM_TRY(pm_dmalloc(&T->M, (size_t)T->nbox * kFmmN3));
@@ -847,28 +937,17 @@ pm_status ensure_m2l_ops(pm_surface* s, int which_K, float** out) {
     float*& A = which_K ? c->fmm_opK : c->fmm_opR;
     if (!A) {
         const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
-        std::vector<int3> offs;
-        for (int x = -3; x <= 3; ++x)
-            for (int y = -3; y <= 3; ++y)
-                for (int z = -3; z <= 3; ++z)
-                    if (std::max({std::abs(x), std::abs(y), std::abs(z)}) >= 2)
-                        offs.push_back(make_int3(x, y, z));
         float* tmp = nullptr;
-        int3* doffs = nullptr;
-        PM_TRY(pm_dmalloc(&tmp, (size_t)kNOff * rows * kFmmN3));
-        PM_TRY(pm_dmalloc(&doffs, offs.size()));
+        PM_TRY(pm_dmalloc(&tmp, (size_t)kNClass * rows * kFmmN3));
         cudaStream_t bs = nullptr;
-        cudaError_t ce = cudaMemcpy(doffs, offs.data(), sizeof(int3) * offs.size(),
-                                    cudaMemcpyHostToDevice);
-        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        cudaError_t ce = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
         if (ce == cudaSuccess) {
-            const dim3 g(pm_ceil_div((long long)rows * kFmmN3, 256), kNOff);
-            k_fmm_build_op<<<g, 256, 0, bs>>>(which_K, doffs, tmp);
+            const dim3 g(pm_ceil_div((long long)rows * kFmmN3, 256), kNClass);
+            k_fmm_build_op<<<g, 256, 0, bs>>>(which_K, tmp);
             ce = cudaGetLastError();
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs);
         }
         if (bs) cudaStreamDestroy(bs);
-        pm_dfree(doffs);
         if (ce != cudaSuccess) {
             pm_dfree(tmp);
             pm_set_error("FMM M2L operators: %s", cudaGetErrorString(ce));
@@ -904,9 +983,8 @@ pm_status ensure_m2l_gemm(PmFmmTree* T) {
         }
     }
     if (!T->Bm) {
-        const size_t cols = (size_t)kNOff * T->nmax;
+        const size_t cols = (size_t)std::max(1, T->nv);
         PM_TRY(pm_dmalloc(&T->Bm, cols * kFmmN3));
-        PM_CUDA_TRY(cudaMemset(T->Bm, 0, sizeof(float) * cols * kFmmN3));   // padding columns
         PM_TRY(pm_dmalloc(&T->Cm, cols * 9 * kFmmN3));
         PM_TRY(pm_dmalloc(&T->msum, (size_t)T->nbox));
     }
@@ -955,25 +1033,33 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
         const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
         if (which_K && nm2l > 0) k_fmm_msum<<<nm2l, kThreads, 0, st>>>(b2, T->M, T->msum, skip);
         if (T->nv > 0)
-            k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, 0, T->M, T->Bm, skip);
+            k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, T->vsym, T->M, T->Bm,
+                                                         skip);
         PM_CUDA_TRY(cudaGetLastError());
         const float one = 1.f, zero = 0.f;
-        if (cublasSetStream(T->blas, st) != CUBLAS_STATUS_SUCCESS ||
-            cublasGemmStridedBatchedEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, T->nmax, kFmmN3,
-                                       &one, A, CUDA_R_32F, rows, (long long)rows * kFmmN3,
-                                       T->Bm, CUDA_R_32F, kFmmN3, (long long)kFmmN3 * T->nmax,
-                                       &zero, T->Cm, CUDA_R_32F, rows, (long long)rows * T->nmax,
-                                       kNOff, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-                                       CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
-            pm_set_error("FMM: M2L GEMM (float32 emulated on bfloat16) failed");
+        if (cublasSetStream(T->blas, st) != CUBLAS_STATUS_SUCCESS) {
+            pm_set_error("FMM: cublasSetStream failed");
             return PM_ERR_CUDA;
         }
+        for (int c = 0; c < kNClass; ++c) {
+            const int c0 = T->cls_start[c], nc = T->cls_start[c + 1] - c0;
+            if (nc == 0) continue;
+            if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, nc, kFmmN3, &one,
+                             A + (size_t)c * rows * kFmmN3, CUDA_R_32F, rows,
+                             T->Bm + (size_t)c0 * kFmmN3, CUDA_R_32F, kFmmN3, &zero,
+                             T->Cm + (size_t)c0 * rows, CUDA_R_32F, rows,
+                             CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                             CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
+                pm_set_error("FMM: M2L GEMM (float32 emulated on bfloat16) failed");
+                return PM_ERR_CUDA;
+            }
+        }
         if (which_K)
-            k_fmm_m2l_scatter<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->Cm, T->vcol, T->msum,
-                                                               T->Lc, skip);
+            k_fmm_m2l_scatter<true><<<dim3(nm2l, 1), kThreads, 0, st>>>(
+                t, b2, T->Cm, T->vcol, T->vsym, T->msum, T->Lc, skip);
         else
-            k_fmm_m2l_scatter<false><<<nm2l, kThreads, 0, st>>>(t, b2, T->Cm, T->vcol, T->msum,
-                                                                T->Lc, skip);
+            k_fmm_m2l_scatter<false><<<dim3(nm2l, 9), kThreads, 0, st>>>(
+                t, b2, T->Cm, T->vcol, T->vsym, T->msum, T->Lc, skip);
         s->launch_total += 2 + (which_K ? 1 : 0);
     } else if (which_K) {
         k_fmm_m2l<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);

@@ -70,8 +70,8 @@ struct pm_ctx {
     // FMM M2L operators for unit boxes, one per V-list offset, shared by all
     // surfaces of the context; built on first use (pm_fmm.cu)
     std::mutex fmm_mu;
-    float* fmm_opR = nullptr;     // [316][9*512][512] column-major per offset
-    float* fmm_opK = nullptr;     // [316][512][512]
+    float* fmm_opR = nullptr;     // [16][9*512][512] column-major per canonical offset
+    float* fmm_opK = nullptr;     // [16][512][512]
 };
 
 struct PmSolveWork;
