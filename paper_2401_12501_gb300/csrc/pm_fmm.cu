@@ -104,6 +104,7 @@ struct DevTree {
     const int* v_list;
     const int* u_off;         // [nleaf+1] CSR of U lists (leaf ids)
     const int* u_list;
+    const int* p2p_order;     // P2P blocks (leaf, target chunk, e), largest first
 };
 
 __device__ __forceinline__ float3 box_center(const DevTree& t, int lev, int3 ijk) {
@@ -158,13 +159,52 @@ k_fmm_p2m(DevTree t, const float4* __restrict__ pts, float* __restrict__ M,
     if (m < kFmmN3) M[(size_t)box * kFmmN3 + m] = acc;
 }
 
+// The transfer between a parent box and its child o = (ox, oy, oz) is the tensor
+// product T[ox] x T[oy] x T[oz] of 8 x 8 matrices (T[o][m][k] = l_m of child
+// point k in parent coordinates), applied as three 1-D passes in shared memory
+// (3 x 8 instead of 512 multiply-adds per value).  Thread (i1, i2, i3) of the
+// 512 computes one value per pass.
+//   UP   (M2M, contract child points k):   out[m] = sum_k  prod_a T[o_a][m_a][k_a] in[k]
+//   DOWN (L2L, contract parent basis m):   out[k] = sum_m  prod_a T[o_a][m_a][k_a] in[m]
+template <bool UP>
+__device__ __forceinline__ float transfer3(const float (*sT)[kFmmN][kFmmN], int ox, int oy, int oz,
+                                           float* s0, float* s1, int i1, int i2, int i3) {
+    // s0 holds the input; returns this thread's output value; s0 and s1 are overwritten
+    const int k = (i1 * kFmmN + i2) * kFmmN + i3;
+    float v = 0.f;
+#pragma unroll
+    for (int j = 0; j < kFmmN; ++j)
+        v = fmaf(UP ? sT[oz][i3][j] : sT[oz][j][i3], s0[(i1 * kFmmN + i2) * kFmmN + j], v);
+    s1[k] = v;
+    __syncthreads();
+    v = 0.f;
+#pragma unroll
+    for (int j = 0; j < kFmmN; ++j)
+        v = fmaf(UP ? sT[oy][i2][j] : sT[oy][j][i2], s1[(i1 * kFmmN + j) * kFmmN + i3], v);
+    s0[k] = v;
+    __syncthreads();
+    v = 0.f;
+#pragma unroll
+    for (int j = 0; j < kFmmN; ++j)
+        v = fmaf(UP ? sT[ox][i1][j] : sT[ox][j][i1], s0[(j * kFmmN + i2) * kFmmN + i3], v);
+    return v;
+}
+
+__device__ __forceinline__ void load_transfer(float (*sT)[kFmmN][kFmmN]) {
+    for (int e = threadIdx.x; e < 2 * kFmmN * kFmmN; e += blockDim.x)
+        (&sT[0][0][0])[e] = (&cF.T[0][0][0])[e];
+}
+
 // M2M for the boxes of one level: M_P = sum_children T(child) M_child
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2m(DevTree t, int lev, float* __restrict__ M, const int* __restrict__ skip) {
     if (skip && *skip) return;
+    static_assert(kThreads == kFmmN3, "one thread per expansion point");
     const int box = t.lev_off[lev] + blockIdx.x;
     const int m = threadIdx.x;
-    __shared__ float sM[kFmmN3];
+    __shared__ float sT[2][kFmmN][kFmmN];
+    __shared__ float s0[kFmmN3], s1[kFmmN3];
+    load_transfer(sT);
     const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
     const int3 pijk = t.box_ijk[box];
     float acc = 0.f;
@@ -173,15 +213,11 @@ k_fmm_m2m(DevTree t, int lev, float* __restrict__ M, const int* __restrict__ ski
         const int3 cijk = t.box_ijk[ch];
         const int ox = cijk.x - 2 * pijk.x, oy = cijk.y - 2 * pijk.y, oz = cijk.z - 2 * pijk.z;
         __syncthreads();
-        if (m < kFmmN3) sM[m] = M[(size_t)ch * kFmmN3 + m];
+        s0[m] = M[(size_t)ch * kFmmN3 + m];
         __syncthreads();
-        if (m < kFmmN3)
-            for (int k = 0; k < kFmmN3; ++k) {
-                const int k1 = k / (kFmmN * kFmmN), k2 = (k / kFmmN) % kFmmN, k3 = k % kFmmN;
-                acc = fmaf(cF.T[ox][m1][k1] * cF.T[oy][m2][k2], cF.T[oz][m3][k3] * sM[k], acc);
-            }
+        acc += transfer3<true>(sT, ox, oy, oz, s0, s1, m1, m2, m3);
     }
-    if (m < kFmmN3) M[(size_t)box * kFmmN3 + m] = acc;
+    M[(size_t)box * kFmmN3 + m] = acc;
 }
 
 // M2L: one block per target box (any level >= 2), thread per target Chebyshev point;
@@ -254,87 +290,89 @@ k_fmm_l2l(DevTree t, int lev, float* __restrict__ Lc, const int* __restrict__ sk
     const int k = threadIdx.x;
     const int3 cijk = t.box_ijk[box], pijk = t.box_ijk[par];
     const int ox = cijk.x - 2 * pijk.x, oy = cijk.y - 2 * pijk.y, oz = cijk.z - 2 * pijk.z;
-    __shared__ float sL[kFmmN3];
+    __shared__ float sT[2][kFmmN][kFmmN];
+    __shared__ float s0[kFmmN3], s1[kFmmN3];
+    load_transfer(sT);
     const int k1 = k / (kFmmN * kFmmN), k2 = (k / kFmmN) % kFmmN, k3 = k % kFmmN;
     for (int q = 0; q < C; ++q) {
         __syncthreads();
-        if (k < kFmmN3) sL[k] = Lc[((size_t)par * C + q) * kFmmN3 + k];
+        s0[k] = Lc[((size_t)par * C + q) * kFmmN3 + k];
         __syncthreads();
-        if (k < kFmmN3) {
-            float acc = 0.f;
-            for (int m = 0; m < kFmmN3; ++m) {
-                const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
-                acc = fmaf(cF.T[ox][m1][k1] * cF.T[oy][m2][k2], cF.T[oz][m3][k3] * sL[m], acc);
-            }
-            Lc[((size_t)box * C + q) * kFmmN3 + k] += acc;
-        }
+        Lc[((size_t)box * C + q) * kFmmN3 + k] += transfer3<false>(sT, ox, oy, oz, s0, s1, k1, k2, k3);
     }
 }
 
-// P2P for one (leaf, U-list neighbour) pair, blockIdx = (leaf, e): the exact
-// kernel between the leaf's targets and the sources of the e-th leaf of its U
-// list (the leaf itself included), written as (hi, lo) to partial slice e of
-// each target (zeros when the leaf has fewer than e + 1 neighbours).  Splitting
-// the near field by neighbour gives ~27 blocks per leaf of similar work.
-constexpr int kP2PThreads = 256;
+// P2P for one (leaf, U-list neighbour, target chunk) triple, decoded from
+// p2p_order[blockIdx.x]: the exact kernel between up to 128 of the leaf's
+// targets and the sources of the e-th leaf of its U list (the leaf itself
+// included), written as (hi, lo) to partial slice e of each target (zeros when
+// the leaf has fewer than e + 1 neighbours).  Splitting the near field by
+// neighbour and by target chunk bounds every block's work by 128 x (leaf size)
+// pairs; the blocks run largest first.
+constexpr int kP2PThreads = 128;               // one target per thread, one chunk per block
 constexpr int kP2PStage = 512;                 // sources staged in shared memory per pass
 constexpr int kUMax = 27;                      // U list: the 3 x 3 x 3 leaves around a leaf
+constexpr int kP2PMaxChunks = 32;              // kMaxLeafPts / kP2PThreads
+static_assert(kMaxLeafPts <= kP2PThreads * kP2PMaxChunks, "chunk field of the P2P block code");
+
+__host__ __device__ __forceinline__ int p2p_code(int leaf, int chunk, int e) {
+    return (leaf << 10) | (chunk << 5) | e;
+}
 
 template <bool KERNEL_K>
 __global__ void __launch_bounds__(kP2PThreads)
 k_fmm_p2p(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ tgt, float eps2,
           float2* __restrict__ out, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int leaf = blockIdx.x, e = blockIdx.y;
-    const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
+    const int code = t.p2p_order[blockIdx.x];
+    const int leaf = code >> 10, chunk = (code >> 5) & 31, e = code & 31;
+    const int p1 = t.box_first[leaf + 1];
+    const int i = t.box_first[leaf] + chunk * kP2PThreads + threadIdx.x;
+    const bool active = i < p1;
     const int ne = t.u_off[leaf + 1] - t.u_off[leaf];
     float2* slice = out + (size_t)e * t.N;
     if (e >= ne) {
-        for (int i = p0 + threadIdx.x; i < p1; i += kP2PThreads) slice[t.perm[i]] = make_float2(0.f, 0.f);
+        if (active) slice[t.perm[i]] = make_float2(0.f, 0.f);
         return;
     }
     const int ul = t.u_list[t.u_off[leaf] + e];
     const int q0 = t.box_first[ul], q1 = t.box_first[ul + 1];
     __shared__ float4 sP[kP2PStage];
-    for (int tb = p0; tb < p1; tb += kP2PThreads) {
-        const int i = tb + threadIdx.x;
-        const bool active = i < p1;
-        float4 X = make_float4(0.f, 0.f, 0.f, 0.f), NN = X, MM = X;
-        int orig = 0;
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), NN = X, MM = X;
+    int orig = 0;
+    if (active) {
+        orig = t.perm[i];
+        X = tgt[orig];
+        NN = tgt[t.N + orig];
+        MM = tgt[2 * t.N + orig];
+    }
+    float hi = 0.f, lo = 0.f;
+    for (int qb = q0; qb < q1; qb += kP2PStage) {
+        const int cnt = min(kP2PStage, q1 - qb);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += kP2PThreads) sP[j] = pts[qb + j];
+        __syncthreads();
+        float part = 0.f;
         if (active) {
-            orig = t.perm[i];
-            X = tgt[orig];
-            NN = tgt[t.N + orig];
-            MM = tgt[2 * t.N + orig];
-        }
-        float hi = 0.f, lo = 0.f;
-        for (int qb = q0; qb < q1; qb += kP2PStage) {
-            const int cnt = min(kP2PStage, q1 - qb);
-            __syncthreads();
-            for (int j = threadIdx.x; j < cnt; j += kP2PThreads) sP[j] = pts[qb + j];
-            __syncthreads();
-            float part = 0.f;
-            if (active) {
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 s = sP[j];
-                    const float dx = X.x - s.x, dy = X.y - s.y, dz = X.z - s.z;
-                    if (KERNEL_K) {
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float lg = (qb + j == i) ? 0.f : lg2_approx(r2);
-                        part = fmaf(s.w, lg, part);
-                    } else {
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                        const float inv = rcp_approx(r2);
-                        const float nr = fmaf(NN.x, dx, fmaf(NN.y, dy, NN.z * dz));
-                        const float mr = fmaf(MM.x, dx, fmaf(MM.y, dy, MM.z * dz));
-                        part = fmaf(s.w, fmaf(nr, nr * inv, mr) * inv, part);
-                    }
+            for (int j = 0; j < cnt; ++j) {
+                const float4 s = sP[j];
+                const float dx = X.x - s.x, dy = X.y - s.y, dz = X.z - s.z;
+                if (KERNEL_K) {
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float lg = (qb + j == i) ? 0.f : lg2_approx(r2);
+                    part = fmaf(s.w, lg, part);
+                } else {
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                    const float inv = rcp_approx(r2);
+                    const float nr = fmaf(NN.x, dx, fmaf(NN.y, dy, NN.z * dz));
+                    const float mr = fmaf(MM.x, dx, fmaf(MM.y, dy, MM.z * dz));
+                    part = fmaf(s.w, fmaf(nr, nr * inv, mr) * inv, part);
                 }
             }
-            two_sum_acc(hi, lo, KERNEL_K ? part * (float)(M_LN2 / (4.0 * M_PI)) : part);
         }
-        if (active) slice[orig] = make_float2(hi, lo);
+        two_sum_acc(hi, lo, KERNEL_K ? part * (float)(M_LN2 / (4.0 * M_PI)) : part);
     }
+    if (active) slice[orig] = make_float2(hi, lo);
 }
 
 // L2P for one leaf: phi_c(x) = sum_l S_l(x) L[c][l] and the target combination,
@@ -537,6 +575,7 @@ k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* 
     const int qa = q < 6 ? (q < 3 ? 0 : (q < 5 ? 1 : 2)) : q - 6;
     const int qb = q < 6 ? (q < 3 ? q : (q < 5 ? q - 2 : 2)) : -1;
     float acc = 0.f;
+#pragma unroll 8
     for (int e = e0; e < e1; ++e) {
         const int g = vsym[e];
         const int lp = sym_apply_inv(g, l);
@@ -576,7 +615,7 @@ struct PmFmmTree {
     // device arrays
     int *perm = nullptr, *lev_off_d = nullptr, *box_first = nullptr, *parent = nullptr;
     int *child_off = nullptr, *child = nullptr, *v_off = nullptr, *v_list = nullptr;
-    int *u_off = nullptr, *u_list = nullptr;
+    int *u_off = nullptr, *u_list = nullptr, *p2p_order = nullptr;
     int3* box_ijk = nullptr;
     float4* sorted = nullptr;
     float* M = nullptr;
@@ -584,7 +623,7 @@ struct PmFmmTree {
     long long p2p_pairs = 0, m2l_pairs = 0;
     // M2L as GEMMs: V-list entry -> column (class start + rank within the class)
     // and the symmetry g that maps its offset to the class's canonical offset
-    int nv = 0;
+    int nv = 0, np2p = 0;
     std::vector<int> cls_start;   // [kNClass + 1]
     int *vcol = nullptr, *vsym = nullptr;
     float *Bm = nullptr, *Cm = nullptr, *msum = nullptr;
@@ -596,7 +635,7 @@ struct PmFmmTree {
         if (blas_ws) cudaFree(blas_ws);
         pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
         pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
-        pm_dfree(u_off); pm_dfree(u_list); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
+        pm_dfree(u_off); pm_dfree(u_list); pm_dfree(p2p_order); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
         pm_dfree(Lc);
     }
 };
@@ -853,6 +892,33 @@ pm_status pm_fmm_build(pm_surface* s) {
                 }
         u_off[b + 1] = (int)u_list.size();
     }
+    // P2P blocks: (leaf, neighbour, chunk of 128 targets), by decreasing pair
+    // count; the blocks that only clear a slice (e beyond the leaf's U list) go last
+    std::vector<int> p2p_order;
+    {
+        std::vector<long long> work;
+        for (int b = 0; b < T->nleaf; ++b) {
+            const int ne = u_off[b + 1] - u_off[b];
+            const int nch = (cnt[b] + kP2PThreads - 1) / kP2PThreads;
+            if (nch > kP2PMaxChunks) {
+                pm_set_error("pm_fmm_build: leaf with %d points exceeds the P2P chunk range", cnt[b]);
+                return PM_ERR_INTERNAL;
+            }
+            for (int ch = 0; ch < nch; ++ch)
+                for (int e = 0; e < kUMax; ++e) {
+                    const long long nt = std::min(kP2PThreads, cnt[b] - ch * kP2PThreads);
+                    p2p_order.push_back(p2p_code(b, ch, e));
+                    work.push_back(e < ne ? nt * cnt[u_list[u_off[b] + e]] : -1);
+                }
+        }
+        std::vector<int> idx(p2p_order.size());
+        for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work[x] > work[y]; });
+        std::vector<int> sorted(idx.size());
+        for (size_t k = 0; k < idx.size(); ++k) sorted[k] = p2p_order[idx[k]];
+        p2p_order.swap(sorted);
+        T->np2p = (int)p2p_order.size();
+    }
     T->p2p_pairs = (long long)s->fmm_stats[0];
     T->m2l_pairs = (long long)s->fmm_stats[1];
     s->fmm_stats[2] = depth;
@@ -875,6 +941,7 @@ pm_status pm_fmm_build(pm_surface* s) {
     PM_TRY(up(&T->v_list, v_list));
     PM_TRY(up(&T->u_off, u_off));
     PM_TRY(up(&T->u_list, u_list));
+    PM_TRY(up(&T->p2p_order, p2p_order));
     PM_TRY(up(&T->box_ijk, ijk));
     // M2L columns: group the V-list entries by offset class
     {
@@ -1017,6 +1084,7 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     t.v_list = T->v_list;
     t.u_off = T->u_off;
     t.u_list = T->u_list;
+    t.p2p_order = T->p2p_order;
     const int* skip = s->skip_flag;
     const int depth = T->depth;
     k_fmm_gather<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->src32, T->perm, s->N, T->sorted, skip);
@@ -1074,7 +1142,7 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
             k_fmm_l2l<9><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
     }
     float2* out = reinterpret_cast<float2*>(s->partial);
-    const dim3 g2(T->nleaf, kUMax);
+    const int g2 = T->np2p;
     if (which_K) {
         k_fmm_p2p<true><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
         k_fmm_l2p<true><<<T->nleaf, kThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
