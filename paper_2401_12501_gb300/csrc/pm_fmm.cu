@@ -105,6 +105,7 @@ struct DevTree {
     const int* u_off;         // [nleaf+1] CSR of U lists (leaf ids)
     const int* u_list;
     const int* p2p_order;     // P2P blocks (leaf, target chunk, e), largest first
+    const int* leaf_chunks;   // L2P blocks (leaf << 5 | chunk of 128 targets)
 };
 
 __device__ __forceinline__ float3 box_center(const DevTree& t, int lev, int3 ijk) {
@@ -121,42 +122,66 @@ __global__ void k_fmm_gather(const float4* __restrict__ src, const int* __restri
     if (i < N) sorted[i] = src[perm[i]];
 }
 
-// P2M: one block per leaf, thread per Chebyshev point
+// P2M: one block per leaf.  M[m1][m2][m3] = sum_j s_j l_m1(x_j) l_m2(y_j) l_m3(z_j):
+// thread (g, m1, m2) of the 512 accumulates the 8 values m3 over the points of
+// group g (every 8th point of each staged batch); the 8 groups' partial sums are
+// added in group order at the end.
+constexpr int kP2MBatch = 256;
 __global__ void __launch_bounds__(kThreads)
 k_fmm_p2m(DevTree t, const float4* __restrict__ pts, float* __restrict__ M,
           const int* __restrict__ skip) {
     if (skip && *skip) return;
+    static_assert(kThreads == 8 * kFmmN * kFmmN, "8 point groups x (m1, m2)");
     const int leaf = blockIdx.x;
     const int box = t.lev_off[t.depth] + leaf;
     const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
     const float h = t.L0 / (float)(1 << t.depth);
     const float3 c = box_center(t, t.depth, t.box_ijk[box]);
     const float sc = 2.f / h;
-    __shared__ float sL[64][3 * kFmmN];
-    __shared__ float sS[64];
-    const int m = threadIdx.x;
-    const int m1 = m / (kFmmN * kFmmN), m2 = (m / kFmmN) % kFmmN, m3 = m % kFmmN;
-    float acc = 0.f;
-    for (int base = p0; base < p1; base += 64) {
-        const int cnt = min(64, p1 - base);
+    __shared__ __align__(16) float sB[kP2MBatch][3 * kFmmN];   // s_j l(x_j) | l(y_j) | l(z_j); reused for the reduction
+    const int g = threadIdx.x >> 6, m1 = (threadIdx.x >> 3) & 7, m2 = threadIdx.x & 7;
+    float acc[kFmmN];
+#pragma unroll
+    for (int k = 0; k < kFmmN; ++k) acc[k] = 0.f;
+    for (int base = p0; base < p1; base += kP2MBatch) {
+        const int cnt = min(kP2MBatch, p1 - base);
         __syncthreads();
         if (threadIdx.x < cnt) {
             const float4 q = pts[base + threadIdx.x];
             float l[kFmmN];
             cheb_basis((q.x - c.x) * sc, l);
-            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][a] = l[a];
+#pragma unroll
+            for (int a = 0; a < kFmmN; ++a) sB[threadIdx.x][a] = q.w * l[a];
             cheb_basis((q.y - c.y) * sc, l);
-            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][kFmmN + a] = l[a];
+#pragma unroll
+            for (int a = 0; a < kFmmN; ++a) sB[threadIdx.x][kFmmN + a] = l[a];
             cheb_basis((q.z - c.z) * sc, l);
-            for (int a = 0; a < kFmmN; ++a) sL[threadIdx.x][2 * kFmmN + a] = l[a];
-            sS[threadIdx.x] = q.w;
+#pragma unroll
+            for (int a = 0; a < kFmmN; ++a) sB[threadIdx.x][2 * kFmmN + a] = l[a];
         }
         __syncthreads();
-        if (m < kFmmN3)
-            for (int j = 0; j < cnt; ++j)
-                acc = fmaf(sS[j] * sL[j][m1], sL[j][kFmmN + m2] * sL[j][2 * kFmmN + m3], acc);
+        for (int j = g; j < cnt; j += 8) {
+            const float w = sB[j][m1] * sB[j][kFmmN + m2];
+            const float4 z0 = *reinterpret_cast<const float4*>(&sB[j][2 * kFmmN]);
+            const float4 z1 = *reinterpret_cast<const float4*>(&sB[j][2 * kFmmN + 4]);
+            acc[0] = fmaf(w, z0.x, acc[0]); acc[1] = fmaf(w, z0.y, acc[1]);
+            acc[2] = fmaf(w, z0.z, acc[2]); acc[3] = fmaf(w, z0.w, acc[3]);
+            acc[4] = fmaf(w, z1.x, acc[4]); acc[5] = fmaf(w, z1.y, acc[5]);
+            acc[6] = fmaf(w, z1.z, acc[6]); acc[7] = fmaf(w, z1.w, acc[7]);
+        }
     }
-    if (m < kFmmN3) M[(size_t)box * kFmmN3 + m] = acc;
+    // reduce the 8 groups in order: red[g][m], m = (m1 * 8 + m2) * 8 + m3
+    __syncthreads();
+    float* red = &sB[0][0];
+    static_assert(kP2MBatch * 3 * kFmmN >= 8 * kFmmN3, "reduction buffer");
+#pragma unroll
+    for (int k = 0; k < kFmmN; ++k) red[g * kFmmN3 + ((m1 * kFmmN + m2) * kFmmN + k)] = acc[k];
+    __syncthreads();
+    const int m = threadIdx.x;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v += red[q * kFmmN3 + m];
+    M[(size_t)box * kFmmN3 + m] = v;
 }
 
 // The transfer between a parent box and its child o = (ox, oy, oz) is the tensor
@@ -375,55 +400,73 @@ k_fmm_p2p(DevTree t, const float4* __restrict__ pts, const float4* __restrict__ 
     if (active) slice[orig] = make_float2(hi, lo);
 }
 
-// L2P for one leaf: phi_c(x) = sum_l S_l(x) L[c][l] and the target combination,
-// written to partial slice kUMax of each target.
+// L2P for one (leaf, chunk of 128 targets) = leaf_chunks[blockIdx.x]:
+// phi_c(x) = sum_l S_l(x) L[c][l] and the target combination, written to
+// partial slice kUMax of each target.
+constexpr int kL2PThreads = 128;
+static_assert(kMaxLeafPts <= kL2PThreads * 32, "chunk field of the L2P block code");
 template <bool KERNEL_K>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kL2PThreads)
 k_fmm_l2p(DevTree t, const float4* __restrict__ tgt, const float* __restrict__ Lc,
           float2* __restrict__ out, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int leaf = blockIdx.x;
+    const int code = t.leaf_chunks[blockIdx.x];
+    const int leaf = code >> 5, chunk = code & 31;
     const int box = t.lev_off[t.depth] + leaf;
-    const int p0 = t.box_first[leaf], p1 = t.box_first[leaf + 1];
+    const int p1 = t.box_first[leaf + 1];
+    const int i = t.box_first[leaf] + chunk * kL2PThreads + threadIdx.x;
     const float h = t.L0 / (float)(1 << t.depth);
     const float3 c = box_center(t, t.depth, t.box_ijk[box]);
     const float sc = 2.f / h;
     constexpr int C = KERNEL_K ? 1 : 9;
-    __shared__ float sLoc[C * kFmmN3];
-    for (int q = threadIdx.x; q < C * kFmmN3; q += kThreads) sLoc[q] = Lc[(size_t)box * C * kFmmN3 + q];
+    __shared__ __align__(16) float sLoc[C * kFmmN3];
+    const float4* src = reinterpret_cast<const float4*>(Lc + (size_t)box * C * kFmmN3);
+    for (int q = threadIdx.x; q < C * kFmmN3 / 4; q += kL2PThreads)
+        reinterpret_cast<float4*>(sLoc)[q] = src[q];
     __syncthreads();
+    if (i >= p1) return;
     float2* slice = out + (size_t)kUMax * t.N;
-    for (int i = p0 + threadIdx.x; i < p1; i += kThreads) {
-        const int orig = t.perm[i];
-        const float4 X = tgt[orig], NN = tgt[t.N + orig], MM = tgt[2 * t.N + orig];
-        float bx[kFmmN], by[kFmmN], bz[kFmmN];
-        cheb_basis((X.x - c.x) * sc, bx);
-        cheb_basis((X.y - c.y) * sc, by);
-        cheb_basis((X.z - c.z) * sc, bz);
-        float phi[C];
+    const int orig = t.perm[i];
+    const float4 X = tgt[orig], NN = tgt[t.N + orig], MM = tgt[2 * t.N + orig];
+    float bx[kFmmN], by[kFmmN], bz[kFmmN];
+    cheb_basis((X.x - c.x) * sc, bx);
+    cheb_basis((X.y - c.y) * sc, by);
+    cheb_basis((X.z - c.z) * sc, bz);
+    float phi[C];
 #pragma unroll
-        for (int q = 0; q < C; ++q) phi[q] = 0.f;
-        for (int l1 = 0; l1 < kFmmN; ++l1)
-            for (int l2 = 0; l2 < kFmmN; ++l2) {
-                const float w12 = bx[l1] * by[l2];
+    for (int q = 0; q < C; ++q) phi[q] = 0.f;
+    for (int l1 = 0; l1 < kFmmN; ++l1) {
+        float b1 = bx[0];   // bx[l1] without a runtime-indexed array
 #pragma unroll
-                for (int l3 = 0; l3 < kFmmN; ++l3) {
-                    const float w = w12 * bz[l3];
-                    const int l = (l1 * kFmmN + l2) * kFmmN + l3;
+        for (int k = 1; k < kFmmN; ++k) b1 = (k == l1) ? bx[k] : b1;
 #pragma unroll
-                    for (int q = 0; q < C; ++q) phi[q] = fmaf(w, sLoc[q * kFmmN3 + l], phi[q]);
-                }
+        for (int l2 = 0; l2 < kFmmN; ++l2) {
+            const float w12 = b1 * by[l2];
+            float w[kFmmN];
+#pragma unroll
+            for (int l3 = 0; l3 < kFmmN; ++l3) w[l3] = w12 * bz[l3];
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                const float4* row =
+                    reinterpret_cast<const float4*>(sLoc + q * kFmmN3 + (l1 * kFmmN + l2) * kFmmN);
+                const float4 a0 = row[0], a1 = row[1];
+                float v = phi[q];
+                v = fmaf(w[0], a0.x, v); v = fmaf(w[1], a0.y, v); v = fmaf(w[2], a0.z, v);
+                v = fmaf(w[3], a0.w, v); v = fmaf(w[4], a1.x, v); v = fmaf(w[5], a1.y, v);
+                v = fmaf(w[6], a1.z, v); v = fmaf(w[7], a1.w, v);
+                phi[q] = v;
             }
-        float far;
-        if (KERNEL_K) {
-            far = phi[0] * (float)(M_LN2 / (4.0 * M_PI));
-        } else {
-            far = NN.x * NN.x * phi[0] + NN.y * NN.y * phi[3] + NN.z * NN.z * phi[5] +
-                  2.f * (NN.x * NN.y * phi[1] + NN.x * NN.z * phi[2] + NN.y * NN.z * phi[4]) +
-                  MM.x * phi[6] + MM.y * phi[7] + MM.z * phi[8];
         }
-        slice[orig] = make_float2(far, 0.f);
     }
+    float far;
+    if (KERNEL_K) {
+        far = phi[0] * (float)(M_LN2 / (4.0 * M_PI));
+    } else {
+        far = NN.x * NN.x * phi[0] + NN.y * NN.y * phi[3] + NN.z * NN.z * phi[5] +
+              2.f * (NN.x * NN.y * phi[1] + NN.x * NN.z * phi[2] + NN.y * NN.z * phi[4]) +
+              MM.x * phi[6] + MM.y * phi[7] + MM.z * phi[8];
+    }
+    slice[orig] = make_float2(far, 0.f);
 }
 
 // ---------------------------------------------------------------- M2L as GEMMs
@@ -550,22 +593,27 @@ k_fmm_msum(int box0, const float* __restrict__ M, float* __restrict__ msum,
     }
 }
 
-// L_T[c][l] = sum over V(T), in V-list order, of scale_c(h) times the entry of
-// C's column vcol[e] that g maps to (c, l) (+ 2 lg2(h) msum_S for the log
-// kernel); one block per (target box of level >= 2, kernel c).  The permuted
-// reads of a column component stay within its 2 KB, which the block's warps
-// read whole (through L1).
+// L_T[c][l] = sum over V(T) of scale_c(h) times the entry of C's column vcol[e]
+// that g maps to (c, l) (+ 2 lg2(h) msum_S for the log kernel); one block per
+// (target box of level >= 2, kernel c).  Warp w takes the V-list entries
+// e0 + w, e0 + w + 16, ... (each lane 16 of the 512 points; the permuted reads
+// of one 2 KB column component go through L1), and the 16 warps' partial sums
+// are added in warp order.
+constexpr int kScatWarps = kThreads / 32;
+constexpr int kScatPerLane = kFmmN3 / 32;
+
 template <bool KERNEL_K>
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* __restrict__ vcol,
                   const int* __restrict__ vsym, const float* __restrict__ msum,
                   float* __restrict__ Lc, const int* __restrict__ skip) {
     if (skip && *skip) return;
+    static_assert(kThreads == kFmmN3, "one thread per expansion point in the final sum");
     constexpr int C = KERNEL_K ? 1 : 9;
     constexpr int rows = C * kFmmN3;
+    __shared__ float red[kScatWarps][kFmmN3];
     const int box = box0 + blockIdx.x, q = blockIdx.y;
-    const int l = threadIdx.x;
-    if (l >= kFmmN3) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lev = 0;
     while (lev + 1 <= t.depth && t.lev_off[lev + 1] <= box) ++lev;
     const float h = t.L0 / (float)(1 << lev);
@@ -574,33 +622,46 @@ k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* 
     // (q < 6: the pair (a, b) = (pa[q], pb[q])), or pi(a), sign s_a (q = 6 + a)
     const int qa = q < 6 ? (q < 3 ? 0 : (q < 5 ? 1 : 2)) : q - 6;
     const int qb = q < 6 ? (q < 3 ? q : (q < 5 ? q - 2 : 2)) : -1;
-    float acc = 0.f;
-#pragma unroll 8
-    for (int e = e0; e < e1; ++e) {
+    float acc[kScatPerLane];
+#pragma unroll
+    for (int k = 0; k < kScatPerLane; ++k) acc[k] = 0.f;
+    for (int e = e0 + warp; e < e1; e += kScatWarps) {
         const int g = vsym[e];
-        const int lp = sym_apply_inv(g, l);
-        const float* col = Cm + (size_t)vcol[e] * rows;
-        if (KERNEL_K) {
-            acc += __ldg(col + lp);
-        } else if (qb >= 0) {
-            const int x = sym_pi(g, qa), y = sym_pi(g, qb);
-            const int lo = min(x, y), hi = max(x, y);
-            const int qc = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-            const float v = __ldg(col + qc * kFmmN3 + lp);
-            acc += (sym_neg(g, qa) != sym_neg(g, qb)) ? -v : v;
-        } else {
-            const float v = __ldg(col + (6 + sym_pi(g, qa)) * kFmmN3 + lp);
-            acc += sym_neg(g, qa) ? -v : v;
+        int qc = 0;
+        bool neg = false;
+        if (!KERNEL_K) {
+            if (qb >= 0) {
+                const int x = sym_pi(g, qa), y = sym_pi(g, qb);
+                const int lo = min(x, y), hi = max(x, y);
+                qc = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+                neg = sym_neg(g, qa) != sym_neg(g, qb);
+            } else {
+                qc = 6 + sym_pi(g, qa);
+                neg = sym_neg(g, qa);
+            }
+        }
+        const float* col = Cm + (size_t)vcol[e] * rows + qc * kFmmN3;
+#pragma unroll
+        for (int k = 0; k < kScatPerLane; ++k) {
+            const float v = __ldg(col + sym_apply_inv(g, lane + 32 * k));
+            acc[k] += neg ? -v : v;
         }
     }
+#pragma unroll
+    for (int k = 0; k < kScatPerLane; ++k) red[warp][lane + 32 * k] = acc[k];
+    __syncthreads();
+    const int l = threadIdx.x;
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kScatWarps; ++w) v += red[w][l];
     if (KERNEL_K) {
         const float lh = 2.f * log2f(h);
         float ms = 0.f;
         for (int e = e0; e < e1; ++e) ms += msum[t.v_list[e]];
-        Lc[(size_t)box * kFmmN3 + l] = acc + lh * ms;
+        Lc[(size_t)box * kFmmN3 + l] = v + lh * ms;
     } else {
-        const float sc = q < 6 ? 1.f / (h * h) : 1.f / h;
-        Lc[((size_t)box * C + q) * kFmmN3 + l] = acc * sc;
+        const float scale = q < 6 ? 1.f / (h * h) : 1.f / h;
+        Lc[((size_t)box * C + q) * kFmmN3 + l] = v * scale;
     }
 }
 
@@ -615,7 +676,7 @@ struct PmFmmTree {
     // device arrays
     int *perm = nullptr, *lev_off_d = nullptr, *box_first = nullptr, *parent = nullptr;
     int *child_off = nullptr, *child = nullptr, *v_off = nullptr, *v_list = nullptr;
-    int *u_off = nullptr, *u_list = nullptr, *p2p_order = nullptr;
+    int *u_off = nullptr, *u_list = nullptr, *p2p_order = nullptr, *leaf_chunks = nullptr;
     int3* box_ijk = nullptr;
     float4* sorted = nullptr;
     float* M = nullptr;
@@ -623,7 +684,7 @@ struct PmFmmTree {
     long long p2p_pairs = 0, m2l_pairs = 0;
     // M2L as GEMMs: V-list entry -> column (class start + rank within the class)
     // and the symmetry g that maps its offset to the class's canonical offset
-    int nv = 0, np2p = 0;
+    int nv = 0, np2p = 0, nchunks = 0;
     std::vector<int> cls_start;   // [kNClass + 1]
     int *vcol = nullptr, *vsym = nullptr;
     float *Bm = nullptr, *Cm = nullptr, *msum = nullptr;
@@ -635,7 +696,7 @@ struct PmFmmTree {
         if (blas_ws) cudaFree(blas_ws);
         pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
         pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
-        pm_dfree(u_off); pm_dfree(u_list); pm_dfree(p2p_order); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
+        pm_dfree(u_off); pm_dfree(u_list); pm_dfree(p2p_order); pm_dfree(leaf_chunks); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
         pm_dfree(Lc);
     }
 };
@@ -919,6 +980,10 @@ pm_status pm_fmm_build(pm_surface* s) {
         p2p_order.swap(sorted);
         T->np2p = (int)p2p_order.size();
     }
+    std::vector<int> leaf_chunks;
+    for (int b = 0; b < T->nleaf; ++b)
+        for (int ch = 0; ch * kL2PThreads < cnt[b]; ++ch) leaf_chunks.push_back((b << 5) | ch);
+    T->nchunks = (int)leaf_chunks.size();
     T->p2p_pairs = (long long)s->fmm_stats[0];
     T->m2l_pairs = (long long)s->fmm_stats[1];
     s->fmm_stats[2] = depth;
@@ -942,6 +1007,7 @@ pm_status pm_fmm_build(pm_surface* s) {
     PM_TRY(up(&T->u_off, u_off));
     PM_TRY(up(&T->u_list, u_list));
     PM_TRY(up(&T->p2p_order, p2p_order));
+    PM_TRY(up(&T->leaf_chunks, leaf_chunks));
     PM_TRY(up(&T->box_ijk, ijk));
     // M2L columns: group the V-list entries by offset class
     {
@@ -1085,6 +1151,7 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     t.u_off = T->u_off;
     t.u_list = T->u_list;
     t.p2p_order = T->p2p_order;
+    t.leaf_chunks = T->leaf_chunks;
     const int* skip = s->skip_flag;
     const int depth = T->depth;
     k_fmm_gather<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->src32, T->perm, s->N, T->sorted, skip);
@@ -1145,10 +1212,10 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     const int g2 = T->np2p;
     if (which_K) {
         k_fmm_p2p<true><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
-        k_fmm_l2p<true><<<T->nleaf, kThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
+        k_fmm_l2p<true><<<T->nchunks, kL2PThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
     } else {
         k_fmm_p2p<false><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
-        k_fmm_l2p<false><<<T->nleaf, kThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
+        k_fmm_l2p<false><<<T->nchunks, kL2PThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
     }
     s->launch_total += 5 + 2 * std::max(0, depth - 2);
     PM_CUDA_TRY(cudaGetLastError());
