@@ -464,10 +464,12 @@ def run_fmm(args, dev):
     m2l_pairs = st["m2l_box_pairs"]
     res = {"workload": "torus_98304", "N": wl.N, "near_build_s": round(t_build, 3),
            "m2l": "one operator GEMM per offset class (16 classes of the 316 offsets under the "
-                  "cube's signed axis permutations) on the tensor cores (float32 emulated on "
-                  "bfloat16, float32 accumulation)",
+                  "cube's signed axis permutations) on the bfloat16 tensor cores with float32 "
+                  "accumulation: float32 operands split in three bfloat16 parts, the six "
+                  "products of order <= 2^-16 as one GEMM over K = 3072",
            "m2l_gemm_flops_per_apply": 2.0 * 9 * 512 * 512 * m2l_pairs,
-           "m2l_operator_bytes_per_apply": 16 * 9 * 512 * 512 * 4,
+           "m2l_bf16_flops_executed_per_apply": 6 * 2.0 * 9 * 512 * 512 * m2l_pairs,
+           "m2l_operator_bytes_per_apply": 16 * 9 * 512 * 3072 * 2,
            "solve_tol_1e-8": {p: {"ms": round(v[0] * 1e3, 2), "iterations": v[2].iterations,
                                   "refinements": v[2].refinements,
                                   "residual": v[2].residual} for p, v in solves.items()},

@@ -490,8 +490,30 @@ k_fmm_l2p(DevTree t, const float4* __restrict__ tgt, const float* __restrict__ L
 // target point l, columns m, column-major).  The multipoles of all V-list pairs
 // of one class are gathered, permuted into the canonical frame, as the columns
 // of B; one GEMM per class forms C = A_c B; each target box sums its V-list
-// columns of C, mapped back through g and scaled for its level, in V-list order.
+// columns of C, mapped back through g and scaled for its level.
+//
+// The GEMM runs on the bfloat16 tensor cores with float32 accumulation: each
+// float32 value x is split as x0 + x1 + x2 (xk = bf16 of the remainder after
+// the previous parts, 24 significand bits in all), and the six products
+// a_i b_j with i + j <= 2 are summed as one GEMM over K = 6 x 512 with
+// A' = [a2 a1 a0 a1 a0 a0] (split once, when the operators are built) and
+// B' = [b0; b1; b2; b0; b1; b0] (split by the gather): smallest products first,
+// so that they are accumulated before the large ones.  The dropped products
+// are below 2^-23 of |a||b|.
 constexpr int kNClass = 16;
+constexpr int kSplitK = 6 * kFmmN3;
+__host__ __device__ __forceinline__ int split_part_a(int blk) { return (0x001012 >> (4 * blk)) & 0xF; }
+__host__ __device__ __forceinline__ int split_part_b(int blk) { return (0x010210 >> (4 * blk)) & 0xF; }
+
+// the k-th bfloat16 part of x (k = 0, 1, 2): x0 = bf16(x), x1 = bf16(x - x0), ...
+__device__ __forceinline__ __nv_bfloat16 split_part(float x, int k) {
+    __nv_bfloat16 p = __float2bfloat16_rn(x);
+    for (int j = 0; j < k; ++j) {
+        x -= __bfloat162float(p);
+        p = __float2bfloat16_rn(x);
+    }
+    return p;
+}
 
 __host__ __device__ __forceinline__ int3 canonical_offset(int c) {
     // enumeration of d_c = (i, j, k), i in {2, 3}, i >= j >= k >= 0
@@ -559,20 +581,39 @@ __global__ void k_fmm_build_op(int which_K, float* __restrict__ A) {
     A[(size_t)o * rows * kFmmN3 + e] = (float)v;
 }
 
-// B[:, vcol[e]] = M of the e-th V-list source in its class's frame:
-// B[m', vcol[e]] = M_S[g.m'] (one block per V-list entry)
+// A'[o][row][kk] = part split_part_a(kk / 512) of A[o][row][kk % 512] (column-major)
+__global__ void k_fmm_split_op(int rows, const float* __restrict__ A, __nv_bfloat16* __restrict__ As) {
+    const int o = blockIdx.y;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)rows * kSplitK) return;
+    const int row = (int)(e % rows), kk = (int)(e / rows);
+    const float a = A[((size_t)o * kFmmN3 + kk % kFmmN3) * rows + row];
+    As[(size_t)o * rows * kSplitK + e] = split_part(a, split_part_a(kk / kFmmN3));
+}
+
+// B'[:, vcol[e]] = split multipole of the e-th V-list source in its class's frame:
+// B'[kk, vcol[e]] = part split_part_b(kk / 512) of M_S[g.(kk % 512)]
+// (one block per V-list entry)
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2l_gather(const int* __restrict__ v_list, const int* __restrict__ vcol,
                  const int* __restrict__ vsym, const float* __restrict__ M,
-                 float* __restrict__ B, const int* __restrict__ skip) {
+                 __nv_bfloat16* __restrict__ B, const int* __restrict__ skip) {
     if (skip && *skip) return;
+    static_assert(kThreads == kFmmN3, "one thread per expansion point");
     __shared__ float sm[kFmmN3];
     const int e = blockIdx.x;
     const int m = threadIdx.x;
-    const float* Ms = M + (size_t)v_list[e] * kFmmN3;
-    if (m < kFmmN3) sm[m] = Ms[m];
+    sm[m] = M[(size_t)v_list[e] * kFmmN3 + m];
     __syncthreads();
-    if (m < kFmmN3) B[(size_t)vcol[e] * kFmmN3 + m] = sm[sym_apply(vsym[e], m)];
+    const float x = sm[sym_apply(vsym[e], m)];
+    const __nv_bfloat16 x0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(x0);
+    const __nv_bfloat16 x1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
+    const __nv_bfloat16 parts[3] = {x0, x1, x2};
+    __nv_bfloat16* col = B + (size_t)vcol[e] * kSplitK;
+#pragma unroll
+    for (int blk = 0; blk < 6; ++blk) col[blk * kFmmN3 + m] = parts[split_part_b(blk)];
 }
 
 // sum of a box's multipole values (the log kernel's level term), fixed order
@@ -687,7 +728,8 @@ struct PmFmmTree {
     int nv = 0, np2p = 0, nchunks = 0;
     std::vector<int> cls_start;   // [kNClass + 1]
     int *vcol = nullptr, *vsym = nullptr;
-    float *Bm = nullptr, *Cm = nullptr, *msum = nullptr;
+    __nv_bfloat16* Bm = nullptr;   // [nv][3072] split multipoles (column-major B')
+    float *Cm = nullptr, *msum = nullptr;
     cublasHandle_t blas = nullptr;
     void* blas_ws = nullptr;
     ~PmFmmTree() {
@@ -1064,37 +1106,48 @@ pm_status pm_fmm_build(pm_surface* s) {
 namespace {
 
 // Unit-box M2L operators of the context (one set per kernel family), built once.
-pm_status ensure_m2l_ops(pm_surface* s, int which_K, float** out) {
+pm_status ensure_m2l_ops(pm_surface* s, int which_K, __nv_bfloat16** out) {
     pm_ctx* c = s->ctx;
     std::lock_guard<std::mutex> lk(c->fmm_mu);
-    float*& A = which_K ? c->fmm_opK : c->fmm_opR;
+    __nv_bfloat16*& A = which_K ? c->fmm_opK : c->fmm_opR;
     if (!A) {
         const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
         float* tmp = nullptr;
+        __nv_bfloat16* split = nullptr;
         PM_TRY(pm_dmalloc(&tmp, (size_t)kNClass * rows * kFmmN3));
+        const pm_status st = pm_dmalloc(&split, (size_t)kNClass * rows * kSplitK);
+        if (st != PM_OK) {
+            pm_dfree(tmp);
+            return st;
+        }
         cudaStream_t bs = nullptr;
         cudaError_t ce = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
         if (ce == cudaSuccess) {
             const dim3 g(pm_ceil_div((long long)rows * kFmmN3, 256), kNClass);
             k_fmm_build_op<<<g, 256, 0, bs>>>(which_K, tmp);
             ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) {
+            const dim3 g(pm_ceil_div((long long)rows * kSplitK, 256), kNClass);
+            k_fmm_split_op<<<g, 256, 0, bs>>>(rows, tmp, split);
+            ce = cudaGetLastError();
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs);
         }
         if (bs) cudaStreamDestroy(bs);
+        pm_dfree(tmp);
         if (ce != cudaSuccess) {
-            pm_dfree(tmp);
+            pm_dfree(split);
             pm_set_error("FMM M2L operators: %s", cudaGetErrorString(ce));
             return PM_ERR_CUDA;
         }
-        A = tmp;
+        A = split;
     }
     *out = A;
     return PM_OK;
 }
 
-// cuBLAS handle (float32 emulated on bfloat16 tensor cores, always), its
-// workspace (set explicitly so that the GEMM can be captured in a graph) and the
-// gathered multipole and result matrices of the tree.
+// cuBLAS handle, its workspace (set explicitly so that the GEMM can be captured
+// in a graph) and the gathered multipole and result matrices of the tree.
 pm_status ensure_m2l_gemm(PmFmmTree* T) {
     if (!T->blas) {
         if (cublasCreate(&T->blas) != CUBLAS_STATUS_SUCCESS) {
@@ -1104,20 +1157,14 @@ pm_status ensure_m2l_gemm(PmFmmTree* T) {
         }
         const size_t ws = 64u << 20;
         PM_CUDA_TRY(cudaMalloc(&T->blas_ws, ws));
-        // operators and multipoles are finite by construction (finite strengths), so the
-        // emulation's scan for infinities and NaNs in A and B is skipped
-        if (cublasSetWorkspace(T->blas, T->blas_ws, ws) != CUBLAS_STATUS_SUCCESS ||
-            cublasSetEmulationStrategy(T->blas, CUBLAS_EMULATION_STRATEGY_EAGER) !=
-                CUBLAS_STATUS_SUCCESS ||
-            cublasSetEmulationSpecialValuesSupport(T->blas, CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE) !=
-                CUBLAS_STATUS_SUCCESS) {
-            pm_set_error("FMM: cuBLAS workspace / emulation setup failed");
+        if (cublasSetWorkspace(T->blas, T->blas_ws, ws) != CUBLAS_STATUS_SUCCESS) {
+            pm_set_error("FMM: cuBLAS workspace setup failed");
             return PM_ERR_CUDA;
         }
     }
     if (!T->Bm) {
         const size_t cols = (size_t)std::max(1, T->nv);
-        PM_TRY(pm_dmalloc(&T->Bm, cols * kFmmN3));
+        PM_TRY(pm_dmalloc(&T->Bm, cols * kSplitK));
         PM_TRY(pm_dmalloc(&T->Cm, cols * 9 * kFmmN3));
         PM_TRY(pm_dmalloc(&T->msum, (size_t)T->nbox));
     }
@@ -1162,7 +1209,7 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     }
     const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
     if (s->opts.fmm_tensor_m2l) {
-        float* A = nullptr;
+        __nv_bfloat16* A = nullptr;
         PM_TRY(ensure_m2l_ops(s, which_K, &A));
         PM_TRY(ensure_m2l_gemm(T));
         const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
@@ -1179,13 +1226,12 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
         for (int c = 0; c < kNClass; ++c) {
             const int c0 = T->cls_start[c], nc = T->cls_start[c + 1] - c0;
             if (nc == 0) continue;
-            if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, nc, kFmmN3, &one,
-                             A + (size_t)c * rows * kFmmN3, CUDA_R_32F, rows,
-                             T->Bm + (size_t)c0 * kFmmN3, CUDA_R_32F, kFmmN3, &zero,
-                             T->Cm + (size_t)c0 * rows, CUDA_R_32F, rows,
-                             CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+            if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, nc, kSplitK, &one,
+                             A + (size_t)c * rows * kSplitK, CUDA_R_16BF, rows,
+                             T->Bm + (size_t)c0 * kSplitK, CUDA_R_16BF, kSplitK, &zero,
+                             T->Cm + (size_t)c0 * rows, CUDA_R_32F, rows, CUBLAS_COMPUTE_32F,
                              CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
-                pm_set_error("FMM: M2L GEMM (float32 emulated on bfloat16) failed");
+                pm_set_error("FMM: M2L GEMM (split bfloat16) failed");
                 return PM_ERR_CUDA;
             }
         }

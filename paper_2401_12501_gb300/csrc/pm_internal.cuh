@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -70,8 +71,10 @@ struct pm_ctx {
     // FMM M2L operators for unit boxes, one per V-list offset, shared by all
     // surfaces of the context; built on first use (pm_fmm.cu)
     std::mutex fmm_mu;
-    float* fmm_opR = nullptr;     // [16][9*512][512] column-major per canonical offset
-    float* fmm_opK = nullptr;     // [16][512][512]
+    // M2L operators per canonical offset, column-major [rows][3072] in bfloat16:
+    // the float32 operator's 3-way split (a0, a1, a2) as column blocks a2 a1 a0 a1 a0 a0
+    __nv_bfloat16* fmm_opR = nullptr;   // rows = 9 * 512
+    __nv_bfloat16* fmm_opK = nullptr;   // rows = 512
 };
 
 struct PmSolveWork;
