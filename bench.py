@@ -213,6 +213,8 @@ def run_gpu(args, rank, world, local_rank):
     t_build = time.perf_counter() - t0
     surf.set_coeff(wl.coeff.a, wl.coeff.grad_a)
     nblk = surf.info()[1]
+    # launch shape of the float32 sums picked by the autotuner (untimed, before warm-up)
+    tune = surf.autotune(nrhs=1, prec="fp32", reps=5)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -359,6 +361,9 @@ def run_gpu(args, rank, world, local_rank):
                    "value_definition": "smooth-sum pairs evaluated per second over the solve "
                                        "step = (Arnoldi steps + refinements + 1) * N^2 / time",
                    "near_blocks": nblk, "near_build_s": round(t_build, 3),
+                   "autotune": {"knobs": tune["knobs"], "apply_ms": round(tune["best_ms"], 4),
+                                "builtin_apply_ms": round(tune["default_ms"], 4),
+                                "candidates": tune["candidates"]},
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": round(solves_per_s, 2),
@@ -395,6 +400,9 @@ def run_batched(args, dev):
     s = pm.Surface.from_fixture(ctx, s_surf)
     t_build = time.perf_counter() - t0
     s.set_coeff(coeffs[0].a, coeffs[0].grad_a)
+    # launch shapes picked by the autotuner: one right-hand side (plain solves) and 64
+    tune1 = s.autotune(nrhs=1, prec="fp32", reps=3)
+    tune64 = s.autotune(nrhs=64, prec="fp32", reps=3)
     Fd = torch.from_numpy(F).to(dev)
     s.solve(Fd[0], tol=args.tol, prec="fp32")
     torch.cuda.synchronize()
@@ -419,7 +427,11 @@ def run_batched(args, dev):
             "batched_solves_per_s": round(64 / t_batch, 2),
             "speedup_vs_plain": round(t_plain * 64 / t_batch, 2),
             "max_residual": max(i.residual for i in info),
-            "lockstep_arnoldi_steps": info[0].iterations}
+            "lockstep_arnoldi_steps": info[0].iterations,
+            "autotune": {t: {"knobs": {k: v for k, v in r["knobs"].items() if v},
+                             "apply_ms": round(r["best_ms"], 3),
+                             "builtin_apply_ms": round(r["default_ms"], 3)}
+                         for t, r in (("nrhs_1", tune1), ("nrhs_64", tune64))}}
 
 
 def run_fmm(args, dev):
@@ -434,6 +446,9 @@ def run_fmm(args, dev):
     s = pm.Surface.from_fixture(ctx, wl.surface)
     t_build = time.perf_counter() - t0
     s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+    # octree depth and direct-sum launch shape picked by the autotuner
+    tune_fmm = s.autotune(nrhs=1, prec="fmm", reps=3)
+    tune_32 = s.autotune(nrhs=1, prec="fp32", reps=3)
     st = s.fmm_stats()
     sig = torch.from_numpy(np.random.default_rng(3).standard_normal(wl.N)).to(dev)
     out = {}
@@ -475,6 +490,11 @@ def run_fmm(args, dev):
                                   "residual": v[2].residual} for p, v in solves.items()},
            "solve_u_rel_diff_fmm_vs_fp32": float(np.sqrt(np.dot(w, du * du) /
                                                          np.dot(w, solves["fp32"][1] ** 2))),
+           "autotune": {t: {"knobs": {k: v for k, v in r["knobs"].items() if v},
+                            "apply_ms": round(r["best_ms"], 3),
+                            "builtin_apply_ms": round(r["default_ms"], 3),
+                            "candidates": r["candidates"]}
+                        for t, r in (("fmm", tune_fmm), ("fp32", tune_32))},
            "fmm_tree": st, "apply_R_ms": {k: round(v[0] * 1e3, 3) for k, v in out.items()},
            "rel_err_vs_float_float": {k: float(np.linalg.norm(v[1] - ex) / np.linalg.norm(ex))
                                       for k, v in out.items() if k != "ff"},

@@ -104,10 +104,12 @@ typedef struct {
                                r - A32 d as the next residual when 1e-5 |d| (the float32
                                operator's error bound on d) is below 0.1 tol |f|, instead of
                                recomputing f - A sigma in residual_prec; 1 (default) or 0 */
-    int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as per-offset operator GEMMs on
-                               the tensor cores (float32 emulated on bfloat16, float32
-                               accumulation; operators ~3.3 GB per context, built once)
-                               (default); 0 = M2L evaluated directly on the float32 pipe */
+    int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as one operator GEMM per offset
+                               class (16 classes of the 316 V-list offsets under the cube's
+                               signed axis permutations) on the bfloat16 tensor cores, float32
+                               operands split in three bfloat16 parts, float32 accumulation;
+                               operators ~0.5 GB per context, built once (default);
+                               0 = M2L evaluated directly on the float32 pipe            */
 } pm_opts;
 
 void pm_default_opts(pm_opts* opts);
@@ -143,6 +145,53 @@ void pm_surface_destroy(pm_surface* s);
  * direct_blocks_per_sm in 0..16 (0 = automatic choice).
  */
 pm_status pm_surface_tune(pm_surface* s, int direct_tpt, int direct_blocks_per_sm);
+
+/*
+ * Launch-shape knobs of a surface's applies: the autotuner's search space.
+ * 0 in any field selects the built-in choice.  None changes a result beyond
+ * float32 summation order; none recomputes quadrature.
+ */
+typedef struct {
+    int direct_tpt;           /* float32 sums, one right-hand side: targets per thread, 1/2/4 (2) */
+    int direct_blocks_per_sm; /* float32 sums, one right-hand side: source splits chosen for
+                                 about this many blocks per SM, 1..16 (12)                  */
+    int batch_rhs_per_block;  /* batched float32 sums: right-hand sides per block, 8/16/32 (16) */
+    int batch_blocks_per_sm;  /* batched float32 sums: blocks aimed at per SM, 1..16 (8)     */
+    int fmm_depth;            /* PM_PREC_FMM: octree depth 2..8 (cost model); a change drops
+                                 the surface's tree, rebuilt at the next FMM apply          */
+} pm_knobs;
+
+/* Set (all fields, validated first: PM_ERR_INVALID_ARG leaves the surface
+ * unchanged) or read the surface's knobs. */
+pm_status pm_surface_set_knobs(pm_surface* s, const pm_knobs* k);
+pm_status pm_surface_get_knobs(const pm_surface* s, pm_knobs* k);
+
+typedef struct {
+    pm_knobs best;        /* fastest configuration found; now set on the surface      */
+    double best_ms;       /* its time per remainder apply (median of the repetitions)  */
+    double default_ms;    /* time per apply with the built-in choice (a candidate too) */
+    int candidates;       /* configurations timed                                     */
+} pm_tune_result;
+
+/*
+ * Autotuner: times remainder applies (smooth sums + near field) of nrhs
+ * right-hand sides in precision prec for every candidate launch shape and keeps
+ * the fastest.  prec = PM_PREC_FP32, nrhs = 1: direct_tpt x direct_blocks_per_sm
+ * ({1,2,4} x {4,8,12,16}); PM_PREC_FP32, nrhs > 1: batch_rhs_per_block x
+ * batch_blocks_per_sm ({8,16,32} x {4,8,12,16}); PM_PREC_FMM (nrhs = 1): the
+ * cost model's depth and its two neighbours (depths whose leaves exceed the
+ * P2P limit are skipped).  Each candidate: one warm-up apply, then reps
+ * (1..100) applies timed with CUDA events on a private stream; the median
+ * counts.  The input is a fixed smooth density, allocated and freed here.
+ * Requires pm_surface_set_coeff.  On an error the knobs in force before the
+ * call are restored.  out may not be NULL.
+ */
+pm_status pm_surface_autotune(pm_surface* s, int nrhs, pm_precision prec, int reps,
+                              pm_tune_result* out);
+
+/* Device name (NUL-terminated, truncated to len - 1 bytes) and SM count of the
+ * context's GPU; either pointer may be NULL.  Keys autotuner caches. */
+pm_status pm_ctx_info(const pm_ctx* ctx, char* name, int len, int* num_sms);
 
 /*
  * FMM tree statistics (builds the tree on first use): stats[0] = adjacent-leaf

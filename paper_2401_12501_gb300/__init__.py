@@ -11,7 +11,7 @@ import ctypes as C
 
 import numpy as np
 
-from . import _lib
+from . import _lib, tunecache
 from ._lib import (PM_PART_NEAR_K, PM_PART_NEAR_R, PM_PART_SMOOTH_K,  # noqa: F401
                    PM_PART_SMOOTH_R, PM_PREC_FF, PM_PREC_FMM, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
                    PM_SOLVE_DEVICE_PTRS, PM_SOLVE_PROJECT_RHS, PmError, PmSolveInfo,
@@ -40,6 +40,13 @@ class Context:
         check(_lib.lib().pm_ctx_create(int(device), C.byref(h)), "pm_ctx_create")
         self.handle = h
         self.device = int(device)
+
+    def info(self):
+        """(device name, SM count) of the context's GPU."""
+        buf = C.create_string_buffer(256)
+        sms = C.c_int()
+        check(_lib.lib().pm_ctx_info(self.handle, buf, len(buf), C.byref(sms)), "pm_ctx_info")
+        return buf.value.decode(errors="replace"), sms.value
 
     def close(self):
         if self.handle:
@@ -102,6 +109,44 @@ class Surface:
     def tune(self, direct_tpt=0, direct_blocks_per_sm=0):
         check(_lib.lib().pm_surface_tune(self.handle, int(direct_tpt), int(direct_blocks_per_sm)),
               "pm_surface_tune")
+
+    def knobs(self) -> dict:
+        """The surface's launch-shape knobs (pm_knobs; 0 = built-in choice)."""
+        k = _lib.PmKnobs()
+        check(_lib.lib().pm_surface_get_knobs(self.handle, C.byref(k)), "pm_surface_get_knobs")
+        return {f: getattr(k, f) for f in tunecache.KNOB_FIELDS}
+
+    def set_knobs(self, **kw):
+        """Set knobs by name; the others keep their current values."""
+        cur = self.knobs()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown knobs {sorted(unknown)}")
+        cur.update({k: int(v) for k, v in kw.items()})
+        k = _lib.PmKnobs(**cur)
+        check(_lib.lib().pm_surface_set_knobs(self.handle, C.byref(k)), "pm_surface_set_knobs")
+
+    def autotune(self, nrhs: int = 1, prec: str = "fp32", reps: int = 5, cache: str | None = None):
+        """Time the candidate launch shapes of this surface's remainder apply
+        (pm_surface_autotune) and keep the fastest.  With a cache path, a stored
+        result for the same (GPU, size bucket, nrhs, precision) is applied
+        instead of timing, and a new result is stored."""
+        gpu, _ = self.ctx.info()
+        key = tunecache.tune_key(gpu, self.N, nrhs, prec)
+        if cache is not None:
+            hit = tunecache.load(cache).get(key)
+            if tunecache.valid_entry(hit):
+                self.set_knobs(**hit["knobs"])
+                return dict(hit, cached=True, key=key)
+        r = _lib.PmTuneResult()
+        check(_lib.lib().pm_surface_autotune(self.handle, int(nrhs), PRECISIONS[prec], int(reps),
+                                             C.byref(r)), "pm_surface_autotune")
+        entry = {"knobs": {f: getattr(r.best, f) for f in tunecache.KNOB_FIELDS},
+                 "best_ms": r.best_ms, "default_ms": r.default_ms, "candidates": r.candidates,
+                 "N": self.N}
+        if cache is not None:
+            tunecache.store(cache, key, entry)
+        return dict(entry, cached=False, key=key)
 
     def info(self):
         n, nb = C.c_int(), C.c_int()

@@ -34,7 +34,8 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
            "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
            "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
-           "pm_server_poll", "pm_server_wait", "pm_server_stats"]
+           "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_surface_set_knobs",
+           "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -55,6 +56,17 @@ class PmSolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
                 ("residual", C.c_double), ("removed_mean", C.c_double),
                 ("seconds", C.c_double), ("residual_updates", C.c_int)]
+
+
+class PmKnobs(C.Structure):
+    _fields_ = [("direct_tpt", C.c_int), ("direct_blocks_per_sm", C.c_int),
+                ("batch_rhs_per_block", C.c_int), ("batch_blocks_per_sm", C.c_int),
+                ("fmm_depth", C.c_int)]
+
+
+class PmTuneResult(C.Structure):
+    _fields_ = [("best", PmKnobs), ("best_ms", C.c_double), ("default_ms", C.c_double),
+                ("candidates", C.c_int)]
 
 
 class PmError(RuntimeError):
@@ -79,6 +91,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.argtypes = [P]
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
+    lib.pm_surface_set_knobs.argtypes = [P, C.POINTER(PmKnobs)]
+    lib.pm_surface_get_knobs.argtypes = [P, C.POINTER(PmKnobs)]
+    lib.pm_surface_autotune.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(PmTuneResult)]
+    lib.pm_ctx_info.argtypes = [P, C.c_char_p, C.c_int, C.POINTER(C.c_int)]
     lib.pm_surface_fmm_stats.argtypes = [P, P]
     lib.pm_server_create.argtypes = [P, C.c_size_t, C.c_int, C.c_int, C.POINTER(P)]
     lib.pm_server_destroy.argtypes = [P]

@@ -23,7 +23,7 @@
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kRB = 16;         // right-hand sides per block (float32)
+constexpr int kRB = 16;         // right-hand sides per block (float32) unless tuned (8, 16 or 32)
 constexpr int kRBff = 16;       // right-hand sides per block (float-float)
 constexpr int kTile = 256;
 constexpr int kStage = 512;
@@ -60,19 +60,25 @@ __global__ void k_prep32_multi(const double* __restrict__ sigma, long long ld_si
     sig32[((size_t)r * npatch + P) * ppad + (j - P * pp)] = (float)v;
 }
 
-// float32 smooth sums for a group of kRB right-hand sides (blockIdx.z)
-template <bool KERNEL_K>
+// float32 smooth sums for a group of RB right-hand sides (blockIdx.z); sources are
+// staged kStage (RB <= 16) or kStage / 2 (RB = 32) at a time
+template <int RB>
+constexpr int multi_stage() { return RB <= 16 ? kStage : kStage / 2; }
+
+template <bool KERNEL_K, int RB>
 __global__ void __launch_bounds__(kThreads)
 k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, int nrhs,
                  const float4* __restrict__ tgt, int N, int chunk, float eps2,
                  float2* __restrict__ partial, int nsplit, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    __shared__ float4 sP[kStage];
-    __shared__ float4 sS[kStage][kRB / 4];      // strengths of kRB right-hand sides per source
+    static_assert(RB % 4 == 0 && RB >= 4 && RB <= 32, "RB right-hand sides in float4 groups");
+    constexpr int kSt = multi_stage<RB>();
+    __shared__ float4 sP[kSt];
+    __shared__ float4 sS[kSt][RB / 4];          // strengths of RB right-hand sides per source
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kThreads + tid;
-    const int r0 = blockIdx.z * kRB;
-    const int nr = min(kRB, nrhs - r0);
+    const int r0 = blockIdx.z * RB;
+    const int nr = min(RB, nrhs - r0);
     const int tbase = blockIdx.x * kThreads, tend = tbase + kThreads;
     float tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0, mx = 0, my = 0, mz = 0;
     if (i < N) {
@@ -84,30 +90,30 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
             mx = c.x; my = c.y; mz = c.z;
         }
     }
-    float hi[kRB], lo[kRB];
+    float hi[RB], lo[RB];
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) hi[q] = lo[q] = 0.f;
+    for (int q = 0; q < RB; ++q) hi[q] = lo[q] = 0.f;
     const int s0 = blockIdx.y * chunk;
     const int s1 = min(s0 + chunk, N);
-    for (int base = s0; base < s1; base += kStage) {
-        const int len = min(kStage, s1 - base);
+    for (int base = s0; base < s1; base += kSt) {
+        const int len = min(kSt, s1 - base);
         __syncthreads();
         for (int j = tid; j < len; j += kThreads) {
             sP[j] = pos[base + j];
-            float v[kRB];
+            float v[RB];
 #pragma unroll
-            for (int q = 0; q < kRB; ++q) v[q] = (q < nr) ? s[(size_t)(r0 + q) * N + base + j] : 0.f;
+            for (int q = 0; q < RB; ++q) v[q] = (q < nr) ? s[(size_t)(r0 + q) * N + base + j] : 0.f;
 #pragma unroll
-            for (int q = 0; q < kRB / 4; ++q)
+            for (int q = 0; q < RB / 4; ++q)
                 sS[j][q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncthreads();
         for (int j0 = 0; j0 < len; j0 += kTile) {
             const int j1 = min(j0 + kTile, len);
             const bool own = KERNEL_K && !(base + j1 <= tbase || base + j0 >= tend);
-            float part[kRB];
+            float part[RB];
 #pragma unroll
-            for (int q = 0; q < kRB; ++q) part[q] = 0.f;
+            for (int q = 0; q < RB; ++q) part[q] = 0.f;
 #pragma unroll 2
             for (int j = j0; j < j1; ++j) {
                 const float4 p = sP[j];
@@ -124,7 +130,7 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
                     gfac = inv * fmaf(nr2, nr2 * inv, mr);
                 }
 #pragma unroll
-                for (int q = 0; q < kRB / 4; ++q) {
+                for (int q = 0; q < RB / 4; ++q) {
                     const float4 sv = sS[j][q];
                     part[4 * q] = fmaf(sv.x, gfac, part[4 * q]);
                     part[4 * q + 1] = fmaf(sv.y, gfac, part[4 * q + 1]);
@@ -133,13 +139,13 @@ k_direct_multi32(const float4* __restrict__ pos, const float* __restrict__ s, in
                 }
             }
 #pragma unroll
-            for (int q = 0; q < kRB; ++q) two_sum_acc(hi[q], lo[q], part[q]);
+            for (int q = 0; q < RB; ++q) two_sum_acc(hi[q], lo[q], part[q]);
         }
     }
     if (i < N) {
         const float sc = KERNEL_K ? (float)(M_LN2 / (4.0 * M_PI)) : 1.f;
 #pragma unroll
-        for (int q = 0; q < kRB; ++q)
+        for (int q = 0; q < RB; ++q)
             if (q < nr)
                 partial[((size_t)(r0 + q) * nsplit + blockIdx.y) * N + i] =
                     make_float2(hi[q] * sc, lo[q] * sc);
@@ -443,9 +449,18 @@ static pm_status batch_ensure(pm_surface* s, int nrhs) {
     return PM_OK;
 }
 
-static int batch_splits(const pm_surface* s, int nrhs, int rb) {
+// launch shape of the batched float32 sums (tunable): right-hand sides per block
+// and blocks aimed at per SM
+static int batch_rb(const pm_surface* s) {
+    return (s->batch_rb == 8 || s->batch_rb == 32) ? s->batch_rb : kRB;
+}
+static int batch_bps(const pm_surface* s) {
+    return (s->batch_bps >= 1 && s->batch_bps <= 16) ? s->batch_bps : 8;
+}
+
+static int batch_splits(const pm_surface* s, int nrhs, int rb, int bps) {
     const int tblocks = pm_ceil_div(s->N, kThreads) * pm_ceil_div(nrhs, rb);
-    const int want = 8 * s->ctx->num_sms;
+    const int want = bps * s->ctx->num_sms;
     int ns = (want + tblocks / 2) / tblocks;
     return std::max(1, std::min(ns, std::min(8, std::max(1, s->N / 256))));
 }
@@ -500,7 +515,7 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
     const int* skip = s->skip_flag;
     dim3 gp(pm_ceil_div(N, 256), nrhs);
     if (prec == PM_PREC_FF) {
-        const int ns = batch_splits(s, nrhs, kRBff);
+        const int ns = batch_splits(s, nrhs, kRBff, 8);
         {
             PhaseTimer t(s, PM_PHASE_PREP, st);
             k_prep_ff_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.sff, N, skip);
@@ -522,7 +537,8 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
                                            kernel_K ? s->cK64 : s->cR64, sigma, ld_sigma, B.part,
                                            ns, out, ld_out, skip);
     } else {
-        const int ns = batch_splits(s, nrhs, kRB);
+        const int rb = batch_rb(s);
+        const int ns = batch_splits(s, nrhs, rb, batch_bps(s));
         {
             PhaseTimer t(s, PM_PHASE_PREP, st);
             k_prep32_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.s32, N, s->pp, s->ppad,
@@ -530,14 +546,18 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
         }
         {
             PhaseTimer t(s, kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R, st);
-            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, kRB));
+            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, rb));
             const int chunk = pm_ceil_div(N, ns);
-            if (kernel_K)
-                k_direct_multi32<true><<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N,
-                                                              chunk, s->eps2, B.part, ns, skip);
+            auto launch = [&](auto kern) {
+                kern<<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N, chunk, s->eps2,
+                                             B.part, ns, skip);
+            };
+            if (rb == 8)
+                kernel_K ? launch(k_direct_multi32<true, 8>) : launch(k_direct_multi32<false, 8>);
+            else if (rb == 32)
+                kernel_K ? launch(k_direct_multi32<true, 32>) : launch(k_direct_multi32<false, 32>);
             else
-                k_direct_multi32<false><<<g, kThreads, 0, st>>>(s->src32, B.s32, nrhs, s->tgt32, N,
-                                                               chunk, s->eps2, B.part, ns, skip);
+                kernel_K ? launch(k_direct_multi32<true, kRB>) : launch(k_direct_multi32<false, kRB>);
         }
         if (!B.patch_tried) PM_TRY(build_patch_unions(s, B));
         PhaseTimer t(s, PM_PHASE_NEAR, st);

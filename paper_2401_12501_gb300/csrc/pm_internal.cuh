@@ -68,7 +68,7 @@ struct pm_ctx {
     int device = 0;
     int num_sms = 0;
     cudaDeviceProp prop{};
-    // FMM M2L operators for unit boxes, one per V-list offset, shared by all
+    // FMM M2L operators for unit boxes, one per offset class, shared by all
     // surfaces of the context; built on first use (pm_fmm.cu)
     std::mutex fmm_mu;
     // M2L operators per canonical offset, column-major [rows][3072] in bfloat16:
@@ -151,6 +151,10 @@ struct pm_surface {
     PmBatchSolveWork* bsolve = nullptr;
     double fmm_stats[4] = {0, 0, 0, 0};
     const int* skip_flag = nullptr;
+
+    // launch-shape knobs beyond pm_opts (pm_surface_set_knobs / pm_surface_autotune)
+    int batch_rb = 0;             // right-hand sides per block of the batched float32 sums (0 = 16)
+    int batch_bps = 0;            // blocks aimed at per SM by the batched float32 sums (0 = 8)
 
     // scratch
     double* partial = nullptr;    // [max_split*N]

@@ -1,0 +1,118 @@
+"""The autotuner (pm_surface_autotune): every candidate launch shape gives the
+same operator (float32 rounding of another summation order), the chosen shape
+is at least as fast as the built-in one, and the cache reproduces the choice."""
+
+import numpy as np
+import pytest
+
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_12501_gb300 as pm
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+_S = {}
+
+
+def surf(ctx, name):
+    import paper_2401_12501_gb300 as pm
+    if name not in _S:
+        wl = make_workload(name)
+        s = pm.Surface.from_fixture(ctx, wl.surface)
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        _S[name] = (wl, s)
+    return _S[name]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_single_rhs_autotune(ctx):
+    wl, s = surf(ctx, "ellipsoid_2400")
+    sigma = np.random.default_rng(3).standard_normal(wl.N)
+    ref = s.apply_R(sigma, "ff")
+    s.set_knobs(direct_tpt=0, direct_blocks_per_sm=0)
+    before = s.apply_R(sigma, "fp32")
+    r = s.autotune(nrhs=1, prec="fp32", reps=3)
+    assert r["candidates"] == 13 and not r["cached"]
+    assert r["best_ms"] <= r["default_ms"]
+    assert s.knobs() == r["knobs"]
+    after = s.apply_R(sigma, "fp32")
+    assert rel(after, ref) < 2e-6 and rel(before, ref) < 2e-6
+
+
+@pytest.mark.parametrize("tpt,bps", [(1, 4), (2, 16), (4, 8)])
+def test_every_direct_shape_gives_the_same_operator(ctx, tpt, bps):
+    wl, s = surf(ctx, "ellipsoid_2400")
+    sigma = np.random.default_rng(4).standard_normal(wl.N)
+    ref = s.apply_R(sigma, "ff")
+    s.set_knobs(direct_tpt=tpt, direct_blocks_per_sm=bps)
+    assert rel(s.apply_R(sigma, "fp32"), ref) < 2e-6
+    s.set_knobs(direct_tpt=0, direct_blocks_per_sm=0)
+
+
+def test_batched_autotune_and_rhs_per_block(ctx):
+    wl, s = surf(ctx, "ellipsoid_2400")
+    nrhs = 40                                  # not a multiple of 16 or 32: ragged last group
+    sig = np.random.default_rng(5).standard_normal((nrhs, wl.N))
+    ref = s.apply_R(sig, "ff")
+    outs = {}
+    for rb in (8, 16, 32):
+        s.set_knobs(batch_rhs_per_block=rb, batch_blocks_per_sm=0)
+        outs[rb] = s.apply_R(sig, "fp32")
+        for q in range(nrhs):
+            assert rel(outs[rb][q], ref[q]) < 2e-6, (rb, q)
+    r = s.autotune(nrhs=nrhs, prec="fp32", reps=3)
+    assert r["candidates"] == 13
+    assert r["knobs"]["batch_rhs_per_block"] in (8, 16, 32)
+    assert r["best_ms"] <= r["default_ms"]
+    out = s.apply_R(sig, "fp32")
+    assert max(rel(out[q], ref[q]) for q in range(nrhs)) < 2e-6
+
+
+def test_fmm_depth_autotune(ctx):
+    wl, s = surf(ctx, "ellipsoid_9600")
+    sigma = np.random.default_rng(6).standard_normal(wl.N) + 1.0
+    import paper_2401_12501_gb300 as pm
+    exact = s.apply_part(pm.PM_PART_SMOOTH_R, sigma, "ff")
+    r = s.autotune(nrhs=1, prec="fmm", reps=3)
+    assert r["candidates"] >= 2
+    d = r["knobs"]["fmm_depth"]
+    assert d == 0 or 2 <= d <= 8
+    fmm = s.apply_part(pm.PM_PART_SMOOTH_R, sigma, "fmm")
+    assert rel(fmm, exact) < 1e-5
+    if d:
+        assert s.fmm_stats()["depth"] == d
+
+
+def test_invalid_knobs_leave_the_surface_unchanged(ctx):
+    import paper_2401_12501_gb300 as pm
+    _, s = surf(ctx, "ellipsoid_2400")
+    before = s.knobs()
+    for bad in ({"batch_rhs_per_block": 12}, {"direct_tpt": 3}, {"fmm_depth": 1},
+                {"direct_blocks_per_sm": 17}):
+        with pytest.raises(pm.PmError):
+            s.set_knobs(**bad)
+        assert s.knobs() == before
+
+
+def test_cache_reproduces_the_choice(ctx, tmp_path):
+    wl, s = surf(ctx, "ellipsoid_2400")
+    path = str(tmp_path / "tune.json")
+    first = s.autotune(nrhs=1, prec="fp32", reps=3, cache=path)
+    assert not first["cached"]
+    s.set_knobs(direct_tpt=0, direct_blocks_per_sm=0)
+    second = s.autotune(nrhs=1, prec="fp32", reps=3, cache=path)
+    assert second["cached"] and second["knobs"] == first["knobs"]
+    assert s.knobs() == first["knobs"]

@@ -51,22 +51,29 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.pm_ctx_create(0, None) == 1           # PM_ERR_INVALID_ARG
     assert lib.pm_surface_info(None, None, None) == 1
     assert lib.pm_profile_enable(None, 1) == 1
+    assert lib.pm_surface_set_knobs(None, None) == 1
+    assert lib.pm_surface_get_knobs(None, None) == 1
+    assert lib.pm_surface_autotune(None, 1, 1, 5, None) == 1
+    assert lib.pm_ctx_info(None, None, 0, None) == 1
 
 
 def _header_struct_fields(name):
     src = open(os.path.join(ROOT, "include", "parametrix.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     body = dict((n, b) for b, n in re.findall(r"typedef struct \{([^{}]*)\}\s*(\w+)\s*;", src))[name]
-    return re.findall(r"\b(int|double|size_t)\s+(\w+)\s*;", body)
+    return re.findall(r"\b(int|double|size_t|pm_knobs)\s+(\w+)\s*;", body)
 
 
-@pytest.mark.parametrize("cname,pyname", [("pm_opts", "PmOpts"), ("pm_solve_info", "PmSolveInfo")])
+@pytest.mark.parametrize("cname,pyname", [("pm_opts", "PmOpts"), ("pm_solve_info", "PmSolveInfo"),
+                                          ("pm_knobs", "PmKnobs"),
+                                          ("pm_tune_result", "PmTuneResult")])
 def test_struct_layouts_match_header(cname, pyname):
     """The ctypes mirrors of the option and info structs list the header's fields
     in the same order with the same C types (no compute calls)."""
     import ctypes as C
     from paper_2401_12501_gb300 import _lib
-    ctype = {"int": C.c_int, "double": C.c_double, "size_t": C.c_size_t}
+    ctype = {"int": C.c_int, "double": C.c_double, "size_t": C.c_size_t,
+             "pm_knobs": _lib.PmKnobs}
     fields = _header_struct_fields(cname)
     py = getattr(_lib, pyname)._fields_
     assert [n for _, n in fields] == [n for n, _ in py]
