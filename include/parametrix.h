@@ -140,6 +140,17 @@ pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p,
 void pm_surface_destroy(pm_surface* s);
 
 /*
+ * A second surface on src's geometry: it shares src's nodes, normals, near-field
+ * structure and quadrature weights (read-only once built; nothing is recomputed
+ * or copied) and has its own coefficient, sum buffers, solver state and FMM tree.
+ * Options and knobs are copied from src.  Call pm_surface_set_coeff on it before
+ * applying or solving.  The shared buffers are freed with the last surface that
+ * uses them, so src may be destroyed first.  PM_ERR_INVALID_ARG for NULL
+ * arguments; PM_ERR_OOM / PM_ERR_CUDA if its own buffers cannot be allocated.
+ */
+pm_status pm_surface_clone(const pm_surface* src, pm_surface** out);
+
+/*
  * Change the float32 smooth-sum launch shape of an existing surface (the
  * autotuner's knobs; no quadrature is recomputed).  direct_tpt in {0,1,2,4},
  * direct_blocks_per_sm in 0..16 (0 = automatic choice).

@@ -80,6 +80,16 @@ class Surface:
         return cls(ctx, surf.npatch, surf.p, surf.nodes, surf.normals, surf.tangents,
                    surf.curvature, surf.weights, opts)
 
+    def clone(self) -> "Surface":
+        """A surface on the same geometry sharing the near-field quadrature
+        (pm_surface_clone): set its own coefficient with set_coeff."""
+        h = C.c_void_p()
+        check(_lib.lib().pm_surface_clone(self.handle, C.byref(h)), "pm_surface_clone")
+        c = object.__new__(Surface)
+        c.ctx, c.npatch, c.p, c.N = self.ctx, self.npatch, self.p, self.N
+        c.handle = h
+        return c
+
     def close(self):
         if self.handle:
             _lib.lib().pm_surface_destroy(self.handle)

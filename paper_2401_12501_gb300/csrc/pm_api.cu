@@ -261,9 +261,36 @@ extern "C" void pm_ctx_destroy(pm_ctx* c) {
 }
 
 // ----------------------------------------------------------------------------- surfaces
+// Buffers a surface shares with its clones: built once, read-only afterwards.
+#define PM_SHARED_FIELDS(X)                                                          \
+    X(x) X(n) X(H) X(w) X(J) X(npatch_n) X(centroid) X(radius) X(row_ptr) X(blk_patch) \
+    X(blk_row) X(W_lb) X(W_g) X(W_k) X(dev_err) X(th_off) X(th_ang) X(th_w) X(th_L)
+
+PmSharedBuffers::~PmSharedBuffers() {
+    cudaSetDevice(device);
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static void share_buffers(pm_surface* s) {
+    auto sb = std::make_shared<PmSharedBuffers>();
+    sb->device = s->ctx->device;
+#define PM_X(f) sb->ptrs.push_back((void*)s->f);
+    PM_SHARED_FIELDS(PM_X)
+#undef PM_X
+    s->shared = sb;
+}
+
 static void free_surface(pm_surface* s) {
     if (!s) return;
     if (s->ctx) cudaSetDevice(s->ctx->device);
+    if (s->shared) {
+        // the shared buffers go with the last surface that holds them
+#define PM_X(f) s->f = nullptr;
+        PM_SHARED_FIELDS(PM_X)
+#undef PM_X
+        s->shared.reset();
+    }
     pm_solve_free(s);
     pm_fmm_free(s);
     pm_batch_free(s);
@@ -286,6 +313,22 @@ static void free_surface(pm_surface* s) {
 }
 
 extern "C" void pm_surface_destroy(pm_surface* s) { free_surface(s); }
+
+// per-surface scratch of the smooth sums (a clone allocates its own)
+static pm_status alloc_scratch(pm_surface* s) {
+    const size_t N = s->N;
+    s->max_split = std::max(32, pm_sym_tiles(s));     // one slice per tile for the symmetric sums
+    PM_TRY(pm_dmalloc(&s->partial, (size_t)s->max_split * N));
+    PM_TRY(pm_dmalloc(&s->sig32, (size_t)s->npatch * s->ppad));
+    PM_CUDA_TRY(cudaMemset(s->sig32, 0, sizeof(float) * (size_t)s->npatch * s->ppad));
+    PM_TRY(pm_dmalloc(&s->src32, s->Npad));
+    PM_TRY(pm_dmalloc(&s->src64, s->Npad));
+    PM_CUDA_TRY(cudaMemset(s->src32, 0, sizeof(float4) * s->Npad));
+    PM_CUDA_TRY(cudaMemset(s->src64, 0, sizeof(pm_d4) * s->Npad));
+    PM_TRY(pm_dmalloc(&s->tgt32, 3 * N));
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    return PM_OK;
+}
 
 static bool all_finite(const double* v, size_t n) {
     for (size_t i = 0; i < n; ++i)
@@ -402,20 +445,50 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     PM_CSTEP(cudaMemcpy(s->th_L, len.data(), sizeof(double) * len.size(), cudaMemcpyHostToDevice));
 
     PM_STEP(pm_near_build(s, T));
-
-    // scratch for the smooth sums
-    s->max_split = std::max(32, pm_sym_tiles(s));     // one slice per tile for the symmetric sums
-    PM_STEP(pm_dmalloc(&s->partial, (size_t)s->max_split * N));
-    PM_STEP(pm_dmalloc(&s->sig32, (size_t)npatch * s->ppad));
-    PM_CSTEP(cudaMemset(s->sig32, 0, sizeof(float) * (size_t)npatch * s->ppad));
-    PM_STEP(pm_dmalloc(&s->src32, s->Npad));
-    PM_STEP(pm_dmalloc(&s->src64, s->Npad));
-    PM_CSTEP(cudaMemset(s->src32, 0, sizeof(float4) * s->Npad));
-    PM_CSTEP(cudaMemset(s->src64, 0, sizeof(pm_d4) * s->Npad));
-    PM_STEP(pm_dmalloc(&s->tgt32, 3 * (size_t)N));
-    PM_CSTEP(cudaDeviceSynchronize());
+    PM_STEP(alloc_scratch(s));
 #undef PM_STEP
 #undef PM_CSTEP
+    share_buffers(s);
+    *out = s;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
+    if (!out) { pm_set_error("pm_surface_clone: out is NULL"); return PM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!src || !src->shared) {
+        pm_set_error("pm_surface_clone: NULL or unbuilt source surface");
+        return PM_ERR_INVALID_ARG;
+    }
+    PM_CUDA_TRY(cudaSetDevice(src->ctx->device));
+    pm_surface* s = new pm_surface();
+    s->ctx = src->ctx;
+    s->opts = src->opts;
+    s->npatch = src->npatch;
+    s->p = src->p;
+    s->pp = src->pp;
+    s->ppad = src->ppad;
+    s->N = src->N;
+    s->Npad = src->Npad;
+    s->scale = src->scale;
+    s->h_far = src->h_far;
+    s->eps2 = src->eps2;
+    s->h_x = src->h_x;
+    s->h_w = src->h_w;
+    s->h_tg = src->h_tg;
+    s->nblk = src->nblk;
+    s->nth_total = src->nth_total;
+    s->batch_rb = src->batch_rb;
+    s->batch_bps = src->batch_bps;
+#define PM_X(f) s->f = src->f;
+    PM_SHARED_FIELDS(PM_X)
+#undef PM_X
+    s->shared = src->shared;
+    const pm_status st = alloc_scratch(s);
+    if (st != PM_OK) {
+        free_surface(s);
+        return st;
+    }
     *out = s;
     return PM_OK;
 }

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -75,6 +76,15 @@ struct pm_ctx {
     // the float32 operator's 3-way split (a0, a1, a2) as column blocks a2 a1 a0 a1 a0 a0
     __nv_bfloat16* fmm_opR = nullptr;   // rows = 9 * 512
     __nv_bfloat16* fmm_opK = nullptr;   // rows = 512
+};
+
+// Device buffers fixed once a surface is built (geometry, near-field CSR and
+// quadrature weights, self-rule plan): shared by a surface and its clones
+// (pm_surface_clone) and freed with the last of them.
+struct PmSharedBuffers {
+    int device = 0;
+    std::vector<void*> ptrs;
+    ~PmSharedBuffers();
 };
 
 struct PmSolveWork;
@@ -151,6 +161,9 @@ struct pm_surface {
     PmBatchSolveWork* bsolve = nullptr;
     double fmm_stats[4] = {0, 0, 0, 0};
     const int* skip_flag = nullptr;
+
+    // owner of the buffers listed in PM_SHARED_FIELDS (pm_api.cu) once the surface is built
+    std::shared_ptr<PmSharedBuffers> shared;
 
     // launch-shape knobs beyond pm_opts (pm_surface_set_knobs / pm_surface_autotune)
     int batch_rb = 0;             // right-hand sides per block of the batched float32 sums (0 = 16)

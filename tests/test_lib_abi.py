@@ -55,6 +55,7 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.pm_surface_get_knobs(None, None) == 1
     assert lib.pm_surface_autotune(None, 1, 1, 5, None) == 1
     assert lib.pm_ctx_info(None, None, 0, None) == 1
+    assert lib.pm_surface_clone(None, None) == 1
 
 
 def _header_struct_fields(name):
