@@ -628,7 +628,9 @@ def run_served(args, dev):
                 dt = arrivals[i] - (time.perf_counter() - t_start)
                 if dt > 0:
                     time.sleep(dt)
-                tickets[i] = sv.submit(ops[draws[i][0]][1], rhs[i], tol=args.serve_tol)
+                op = ops[draws[i][0]][1]
+                prec = "fmm" if op.N >= args.serve_fmm_min else "fp32"
+                tickets[i] = sv.submit(op, rhs[i], tol=args.serve_tol, prec=prec)
 
         c = th.Thread(target=client)
         c.start()
@@ -662,6 +664,7 @@ def run_served(args, dev):
     return {"requests": n_req, "arrival_rate_per_s": rate, "seed": 0,
             "operators": len(ops), "geometries": len(geo), "node_range": [sizes[0], sizes[-1]],
             "n_max_drawn": args.serve_nmax, "tol": args.serve_tol,
+            "fmm_applies_from_n": args.serve_fmm_min,
             "near_build_s_total": round(sum(builds), 3),
             "near_build_s_max": round(max(builds), 3),
             "continuous_batching": served, "one_at_a_time": plain,
@@ -692,6 +695,8 @@ def main():
     ap.add_argument("--serve-nmax", type=int, default=30000)
     ap.add_argument("--serve-tol", type=float, default=1e-8)
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--serve-fmm-min", type=int, default=40000,
+                    help="served operators with at least this many nodes use FMM applies")
     args = ap.parse_args()
 
     if args.oracle_leg:

@@ -336,7 +336,9 @@ pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int
  * used by the caller until every request on them has been waited for.
  *   hbm_budget_bytes  device bytes the server may reserve for admitted requests
  *   max_batch         right-hand sides per batch (1 = one request at a time)
- * pm_server_submit copies f (host, [N]) and returns a ticket; PM_ERR_OOM if one
+ * pm_server_submit copies f (host, [N]) and returns a ticket; prec is the solve's
+ * operator precision (FP64, FP32, FF or FMM; PM_ERR_INVALID_ARG otherwise), and a
+ * batch only joins requests of one operator and one precision; PM_ERR_OOM if one
  * request alone exceeds the budget.  pm_server_wait blocks until the ticket is
  * done (timeout_ms < 0: no limit; PM_ERR_TIMEOUT otherwise), copies u (host,
  * [N]) and the solve info, reports the submit-to-finish latency, and releases

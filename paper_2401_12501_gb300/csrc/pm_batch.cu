@@ -509,6 +509,10 @@ static pm_status build_patch_unions(pm_surface* s, PmBatchWork& B) {
 pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long long ld_sigma,
                          double* out, long long ld_out, int nrhs, pm_precision prec,
                          cudaStream_t st) {
+    if (prec != PM_PREC_FP32 && prec != PM_PREC_FF) {
+        pm_set_error("batched apply: precision %d has no multi-RHS form", (int)prec);
+        return PM_ERR_INVALID_ARG;
+    }
     PM_TRY(batch_ensure(s, nrhs));
     PmBatchWork& B = *s->batch;
     const int N = s->N;
@@ -907,7 +911,8 @@ struct BSolver {
     // out_r = A v_r (I + R~ + 1 w^T) for all r
     pm_status apply_A(const double* v, long long ldv, double* out, pm_precision prec,
                       const int* done) {
-        if (prec == PM_PREC_FP64) {
+        if (prec == PM_PREC_FP64 || prec == PM_PREC_FMM) {
+            // no multi-RHS form: one apply per right-hand side
             for (int r = 0; r < nrhs; ++r)
                 PM_TRY(pm_apply_dev(s, 0, 1, 1, v + r * ldv, W.tmp + (size_t)r * W.N, prec, st));
         } else {

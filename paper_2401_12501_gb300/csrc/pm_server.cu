@@ -92,11 +92,18 @@ void worker_main(pm_server* sv, int index) {
                         break;
                     }
                 if (op) {
-                    // admit its waiting requests in arrival order while memory allows
+                    // admit its waiting requests of the oldest one's precision in arrival
+                    // order while memory allows (a batch is solved in one precision)
+                    pm_precision prec = PM_PREC_FP32;
+                    for (Request* r : sv->queue)
+                        if (r->op == op) {
+                            prec = r->prec;
+                            break;
+                        }
                     for (auto it = sv->queue.begin(); it != sv->queue.end() &&
                                                       (int)batch.size() < sv->max_batch;) {
                         Request* r = *it;
-                        if (r->op == op && sv->in_use + r->bytes <= sv->budget) {
+                        if (r->op == op && r->prec == prec && sv->in_use + r->bytes <= sv->budget) {
                             sv->in_use += r->bytes;
                             r->taken = true;
                             batch.push_back(r);
@@ -189,8 +196,10 @@ extern "C" void pm_server_destroy(pm_server* sv) {
 
 extern "C" pm_status pm_server_submit(pm_server* sv, pm_surface* op, const double* f, double tol,
                                       pm_precision prec, unsigned long long* ticket) {
-    if (!sv || !op || !f || !ticket || !(tol > 0)) {
-        pm_set_error("pm_server_submit: bad argument");
+    if (!sv || !op || !f || !ticket || !(tol > 0) ||
+        !(prec == PM_PREC_FP64 || prec == PM_PREC_FP32 || prec == PM_PREC_FF ||
+          prec == PM_PREC_FMM)) {
+        pm_set_error("pm_server_submit: bad argument (NULL, tol <= 0 or unknown precision)");
         return PM_ERR_INVALID_ARG;
     }
     if (!op->has_coeff) {

@@ -72,6 +72,33 @@ def test_mixed_requests_match_standalone(ops):
         assert lat > 0
 
 
+def test_precisions_are_not_mixed_in_a_batch(ops):
+    """Requests on one operator in different precisions: each is solved in its own
+    precision (a batch joins one precision only) and matches the standalone solve."""
+    import paper_2401_12501_gb300 as pm
+    ctx, lst = ops
+    wl, s = lst[0]
+    fs = rhs_set(wl, 6, 7)
+    precs = ["fp32", "fmm", "ff", "fp32", "fmm", "ff"]
+    sv = pm.Server(ctx, hbm_budget_bytes=2 << 30, max_batch=16, n_workers=2)
+    tickets = [sv.submit(s, f, tol=1e-11, prec=p) for f, p in zip(fs, precs)]
+    res = [sv.wait(t) for t in tickets]
+    st = sv.stats()
+    sv.close()
+    assert st["solved"] == len(fs)
+    w = wl.surface.weights
+    for f, p, (u, info, _) in zip(fs, precs, res):
+        alone, ai = s.solve(f, tol=1e-11, prec=p)
+        assert info.residual <= 1e-11
+        assert np.sqrt(np.dot(w, (u - alone) ** 2) / np.dot(w, alone ** 2)) < 1e-9
+    sv = pm.Server(ctx, hbm_budget_bytes=2 << 30)
+    try:
+        with pytest.raises(pm.PmError):
+            sv.submit(s, fs[0], tol=1e-8, prec=7)          # unknown precision
+    finally:
+        sv.close()
+
+
 def test_budget_for_one_request_serialises(ops):
     import paper_2401_12501_gb300 as pm
     ctx, lst = ops
