@@ -486,6 +486,66 @@ def run_batched(args, dev):
                          "nrhs_64": knobs(tune64)}}
 
 
+def run_paper(args, dev):
+    """The paper's own test problems (Sec. 7), a = 1: error of the solution against
+    the exact one and time per solve at the finest resolution of each; the N-body
+    accuracy test of the fast apply on the 58,752-node wavy torus (Sec. 6.2)."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import paper_problem
+    ctx = pm.Context(dev.index or 0)
+    out = {"tol": args.tol, "problems": {}}
+    for name, precs in (("sphere_paper_6144", ("fp32",)), ("ellipsoid_paper_24576", ("fp32",)),
+                        ("wavy_torus_58752", ("fp32", "fmm"))):
+        wl, uex = paper_problem(name)
+        t0 = time.perf_counter()
+        s = pm.Surface.from_fixture(ctx, wl.surface)
+        t_build = time.perf_counter() - t0
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        w = wl.surface.weights
+        fd = torch.from_numpy(wl.f.copy()).to(dev)
+        row = {"N": wl.N, "near_build_s": round(t_build, 3), "description": wl.description}
+        for prec in precs:
+            s.solve(fd, tol=args.tol, prec=prec)
+            torch.cuda.synchronize()
+            reps = 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                u, info = s.solve(fd, tol=args.tol, prec=prec)
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / reps
+            u = u.cpu().numpy()
+            row[prec] = {"solve_ms": round(t * 1e3, 3), "iterations": info[0].iterations,
+                         "residual": info[0].residual,
+                         "rel_l2_error_vs_exact": float(np.sqrt(np.dot(w, (u - uex) ** 2) /
+                                                                np.dot(w, uex ** 2)))}
+        if name == "wavy_torus_58752":
+            sig = torch.from_numpy(wl.surface.nodes[:, 0] +
+                                   np.random.default_rng(0).standard_normal(wl.N)).to(dev)
+            nb = {}
+            for part, key in ((pm.PM_PART_SMOOTH_K, "parametrix"), (pm.PM_PART_SMOOTH_R, "remainder")):
+                ex = s.apply_part(part, sig, "ff").cpu().numpy()
+                res = {}
+                for prec in ("fmm", "fp32"):
+                    y = s.apply_part(part, sig, prec)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(3):
+                        y = s.apply_part(part, sig, prec)
+                    torch.cuda.synchronize()
+                    y = y.cpu().numpy()
+                    res[prec] = {"ms": round((time.perf_counter() - t0) / 3 * 1e3, 3),
+                                 "rel_l2_error_vs_float_float":
+                                     float(np.linalg.norm(y - ex) / np.linalg.norm(ex))}
+                nb[key] = res
+            out["nbody_wavy_torus_58752"] = {"sigma": "x_1 + N(0,1) (seed 0)", **nb,
+                                             "fmm_tree": s.fmm_stats()}
+        out["problems"][name] = row
+        s.close()
+    return out
+
+
 def run_fmm(args, dev):
     """98,304-node torus: float32 apply with the Chebyshev FMM vs the direct sum."""
     import numpy as np
@@ -686,8 +746,8 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--extras", default="batched,fmm,served",
-                    help="comma-separated extra measurements to run (batched, fmm, served)")
+    ap.add_argument("--extras", default="batched,fmm,served,paper",
+                    help="comma-separated extra measurements to run (batched, fmm, served, paper)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -739,7 +799,8 @@ def main():
         dev = torch.device("cuda", local_rank)
         want = set(args.extras.split(","))
         for name, key, fn in (("batched", "batched_star_24576", run_batched),
-                              ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served)):
+                              ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served),
+                              ("paper", "paper_problems", run_paper)):
             if name not in want:
                 continue
             try:

@@ -76,7 +76,8 @@ def test_near_structure_and_corrections(ctx, name):
             assert np.abs(cK[b] - CK).max() <= 1e-10 * sK, (i, P)
 
 
-@pytest.mark.parametrize("name", ["sphere_384", "ellipsoid_small"])
+@pytest.mark.parametrize("name", ["sphere_384", "ellipsoid_small", "wavy_torus_small",
+                                  "ellipsoid_paper_small"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
 def test_full_apply_parity(ctx, name, prec, tol):
     from oracle.operator import apply_K, apply_R
@@ -98,7 +99,8 @@ def test_smooth_parts(ctx, prec, tol):
     assert rel(s.apply_part(pm.PM_PART_SMOOTH_K, sigma, prec), d.smooth_apply("K", sigma)) < tol
 
 
-@pytest.mark.parametrize("name", ["sphere_1536", "ellipsoid_9600", "torus_98304"])
+@pytest.mark.parametrize("name", ["sphere_1536", "ellipsoid_9600", "torus_98304",
+                                  "wavy_torus_58752"])
 def test_sampled_rows_full_size(ctx, name):
     """Full-size workloads: sampled rows computed one by one by the oracle."""
     from oracle.operator import apply_K, apply_R

@@ -13,6 +13,7 @@ from .surfaces import (  # noqa: F401
     cubed_sphere,
     torus,
     star_surface,
+    wavy_torus,
     gauss_legendre,
 )
 from .coefficients import (  # noqa: F401
@@ -28,10 +29,13 @@ from .rhs import (  # noqa: F401
     sphere_harmonic_rhs,
     random_harmonic_rhs,
     torus_rhs,
+    newtonian_problem,
+    four_harmonic_problem,
 )
 from .configs import (  # noqa: F401
     Workload,
     make_workload,
+    paper_problem,
     star_batch,
     WORKLOADS,
 )

@@ -13,6 +13,15 @@ Full-size workloads (the paper-style test problems at production size):
                       f = cos(3 phi) sin(theta), mean zero.
 
 Reduced versions of the same families (``*_small``) keep the oracle fast.
+
+The paper's own test problems (Sec. 7), a = 1:
+
+* ``wavy_torus_<N>``      r = ((3 + cos v + 0.6 cos 5u) cos u, (...) sin u, sin v),
+                          f from the Newtonian potential centred at (-3, -3, 4)
+                          (manufactured solution; ``paper_problem`` returns u too).
+* ``ellipsoid_paper_<N>`` semi-axes (4.5, 2.25, 3), same manufactured solution.
+* ``sphere_paper_<N>``    unit sphere, f = random combination of Y_1^0, Y_3^3,
+                          Y_10^6, Y_10^7 (exact u from the eigenvalues).
 """
 
 from __future__ import annotations
@@ -23,8 +32,9 @@ import numpy as np
 
 from .coefficients import (Coefficient, constant_coefficient, ellipsoid_coefficient,
                            smooth_random_coefficient, torus_coefficient)
-from .rhs import random_harmonic_rhs, sphere_harmonic_rhs, torus_rhs
-from .surfaces import Surface, cubed_sphere, star_surface, torus
+from .rhs import (four_harmonic_problem, newtonian_problem, random_harmonic_rhs,
+                  sphere_harmonic_rhs, torus_rhs)
+from .surfaces import Surface, cubed_sphere, star_surface, torus, wavy_torus
 
 
 @dataclass
@@ -91,11 +101,43 @@ WORKLOADS = {
                        star_surface(8, 8)),
                    "star rho=1+0.3 sin(3 theta) cos(2 phi), 6x8x8 patches, 8x8 nodes (24,576), "
                    "a=1+0.4 tanh(g) seed 0, f=mean-zero N(0,1) combination of Y_l^m, l<=12"),
+    "wavy_torus_small": (lambda: _paper("wavy", wavy_torus(9, 3, 6)),
+                         "wavy torus, 9x3 patches, 6x6 nodes (972), a=1, Newtonian f"),
+    "wavy_torus_12288": (lambda: _paper("wavy", wavy_torus(24, 8, 8)),
+                         "wavy torus, 24x8 patches, 8x8 nodes (12,288), a=1, Newtonian f"),
+    "wavy_torus_58752": (lambda: _paper("wavy", wavy_torus(51, 18, 8)),
+                         "wavy torus, 51x18 patches, 8x8 nodes (58,752), a=1, Newtonian f"),
+    "ellipsoid_paper_small": (lambda: _paper("ell", cubed_sphere(2, 6, axes=(4.5, 2.25, 3.0))),
+                              "ellipsoid (4.5, 2.25, 3), 6x2x2 patches, 6x6 nodes (864), a=1"),
+    "ellipsoid_paper_6144": (lambda: _paper("ell", cubed_sphere(4, 8, axes=(4.5, 2.25, 3.0))),
+                             "ellipsoid (4.5, 2.25, 3), 6x4x4 patches, 8x8 nodes (6,144), a=1"),
+    "ellipsoid_paper_24576": (lambda: _paper("ell", cubed_sphere(8, 8, axes=(4.5, 2.25, 3.0))),
+                              "ellipsoid (4.5, 2.25, 3), 6x8x8 patches, 8x8 nodes (24,576), a=1"),
+    "sphere_paper_1536": (lambda: _paper("sph", cubed_sphere(2, 8)),
+                          "unit sphere, 6x2x2 patches, 8x8 nodes, f = Y_1^0, Y_3^3, Y_10^6, Y_10^7"),
+    "sphere_paper_6144": (lambda: _paper("sph", cubed_sphere(4, 8)),
+                          "unit sphere, 6x4x4 patches, 8x8 nodes, f = Y_1^0, Y_3^3, Y_10^6, Y_10^7"),
     "star_small": (lambda: (lambda s: (s, smooth_random_coefficient(s, 0),
                                        random_harmonic_rhs(s, 0, n_terms=168, lmax=12)))(
                        star_surface(2, 6)),
                    "star, 6x2x2 patches, 6x6 nodes (864)"),
 }
+
+
+def _paper(kind, s):
+    c = constant_coefficient(s)
+    f, _ = four_harmonic_problem(s) if kind == "sph" else newtonian_problem(s, c)
+    return s, c, f
+
+
+def paper_problem(name: str):
+    """(Workload, exact u) of one of the paper's test problems."""
+    wl = make_workload(name)
+    if name.startswith("sphere_paper"):
+        _, u = four_harmonic_problem(wl.surface)
+    else:
+        _, u = newtonian_problem(wl.surface, wl.coeff)
+    return wl, u
 
 
 def make_workload(name: str) -> Workload:

@@ -79,3 +79,43 @@ def torus_rhs(surf: Surface) -> np.ndarray:
     """f = cos(3 phi) sin(theta) on the torus, projected to mean zero."""
     th, ph = surf.params["theta"], surf.params["phi"]
     return project_mean_zero(np.cos(3 * ph) * np.sin(th), surf.weights)
+
+
+def newtonian_problem(surf: Surface, coeff, x0=(-3.0, -3.0, 4.0)):
+    """Manufactured solution of the paper's Laplace-Beltrami test (Sec. 7.2):
+    u = v|_Gamma minus its mean, v(x) = -1 / |x - x0| (harmonic off x0), and
+
+        f = div_Gamma(a grad_Gamma v) = grad_Gamma a . grad_Gamma v + a Lap_Gamma v,
+        Lap_Gamma v = Lap v - 2 H dv/dn - d2v/dn2   (Lap v = 0)
+
+    from the closed-form gradient and Hessian of v (a = 1 gives the paper's
+    problem).  Returns (f projected to mean zero, u)."""
+    x0 = np.asarray(x0, dtype=np.float64)
+    d = surf.nodes - x0
+    rho = np.linalg.norm(d, axis=1)
+    v = -1.0 / rho
+    grad = d / rho[:, None] ** 3
+    n = surf.normals
+    dn = np.sum(grad * n, 1)
+    dnn = 1.0 / rho ** 3 - 3.0 * np.sum(d * n, 1) ** 2 / rho ** 5
+    lap_g = -2.0 * surf.curvature * dn - dnn
+    grad_g = grad - n * dn[:, None]
+    f = np.sum(coeff.grad_a * grad_g, 1) + coeff.a * lap_g
+    w = surf.weights
+    return project_mean_zero(f, w), v - np.dot(w, v) / np.sum(w)
+
+
+def four_harmonic_problem(surf: Surface, seed: int = 0):
+    """The paper's unit-sphere test (Sec. 7.1): f a random (N(0,1), seeded)
+    combination of Y_1^0, Y_3^3, Y_10^6, Y_10^7, and u = the same combination
+    with each term divided by its eigenvalue -l(l+1) (a = 1).  Returns (f, u)."""
+    rng = np.random.default_rng(seed)
+    terms = [(1, 0), (3, 3), (10, 6), (10, 7)]
+    coef = rng.standard_normal(len(terms))
+    f = np.zeros(surf.N)
+    u = np.zeros(surf.N)
+    for c, (l, m) in zip(coef, terms):
+        y = real_sph_harm(l, m, surf.nodes)
+        f += c * y
+        u -= c * y / (l * (l + 1))
+    return f, u

@@ -263,3 +263,55 @@ def star_surface(m: int, p: int, amp: float = 0.3) -> Surface:
                    tangents=np.concatenate([yu, yv], -1), curvature=H, weights=w,
                    gauss_curvature=KG, params={"theta": th, "phi": ph, "amp": amp},
                    area=None, volume=None, genus=0)
+
+
+def wavy_torus(n_u: int, n_v: int, p: int, amp: float = 0.6) -> Surface:
+    """The paper's wavy torus (Sec. 7): r(u, v) = (rho cos u, rho sin u, sin v),
+    rho = 3 + cos v + amp cos 5u (amp = 0.6), (u, v) in [0, 2 pi)^2.
+
+    u (n_u patches) and v (n_v patches) run along the patch coordinates as in
+    ``torus``; tangents, the outward normal r_u x r_v / |r_u x r_v| and the mean
+    and Gauss curvatures come from the closed-form first and second derivatives.
+    Each half-plane at angle u cuts a unit disk centred at radius 3 + 0.6 cos 5u,
+    so the enclosed volume is the integral of pi (3 + amp cos 5u) du = 6 pi^2.
+    """
+    t, wt = gauss_legendre(p)
+    du_p = 2 * np.pi / n_u
+    dv_p = 2 * np.pi / n_v
+    a = np.arange(n_u)[:, None, None, None]
+    b = np.arange(n_v)[None, :, None, None]
+    u = (a + 0.5) * du_p + 0.5 * du_p * t[None, None, :, None] + 0 * b
+    v = (b + 0.5) * dv_p + 0.5 * dv_p * t[None, None, None, :] + 0 * a
+    u, v = np.broadcast_arrays(u, v)
+    cu, su, cv, sv = np.cos(u), np.sin(u), np.cos(v), np.sin(v)
+    rho = 3 + cv + amp * np.cos(5 * u)
+    rho_u = -5.0 * amp * np.sin(5 * u)
+    rho_uu = -25.0 * amp * np.cos(5 * u)
+    rho_v, rho_vv = -sv, -cv
+    z0 = 0 * u
+    X = np.stack([rho * cu, rho * su, sv], -1)
+    X_u = np.stack([rho_u * cu - rho * su, rho_u * su + rho * cu, z0], -1)
+    X_v = np.stack([rho_v * cu, rho_v * su, cv], -1)
+    X_uu = np.stack([rho_uu * cu - 2 * rho_u * su - rho * cu,
+                     rho_uu * su + 2 * rho_u * cu - rho * su, z0], -1)
+    X_uv = np.stack([-rho_v * su, rho_v * cu, z0], -1)
+    X_vv = np.stack([rho_vv * cu, rho_vv * su, -sv], -1)
+    nrm = np.cross(X_u, X_v)
+    nrm /= np.linalg.norm(nrm, axis=-1, keepdims=True)
+    E, F, G = (np.sum(X_u * X_u, -1), np.sum(X_u * X_v, -1), np.sum(X_v * X_v, -1))
+    e, f, g = (np.sum(X_uu * nrm, -1), np.sum(X_uv * nrm, -1), np.sum(X_vv * nrm, -1))
+    H = -(e * G - 2 * f * F + g * E) / (2 * (E * G - F * F))
+    KG = (e * g - f * f) / (E * G - F * F)
+    yu = X_u * (0.5 * du_p)
+    yv = X_v * (0.5 * dv_p)
+    jac = np.linalg.norm(np.cross(yu, yv), axis=-1)
+    w = wt[:, None] * wt[None, :] * jac
+    npatch = n_u * n_v
+    N = npatch * p * p
+    return Surface(
+        kind="wavy_torus", npatch=npatch, p=p,
+        nodes=X.reshape(N, 3), normals=nrm.reshape(N, 3),
+        tangents=np.concatenate([yu, yv], -1).reshape(N, 6),
+        curvature=H.reshape(N), weights=w.reshape(N), gauss_curvature=KG.reshape(N),
+        params={"u": u.reshape(N), "v": v.reshape(N)},
+        area=None, volume=6 * np.pi ** 2, genus=1)
