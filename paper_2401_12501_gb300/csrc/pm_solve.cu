@@ -268,14 +268,14 @@ k_arn_first(const double* __restrict__ y, const double* __restrict__ pw, int nbl
     col_dots_sh(V, ldv, k + 1, w_sh, r0, min(kArnThreads, N - r0), pout + (size_t)blockIdx.x * ld);
 }
 
-// (2)/(3) h = sum of the partial dots; block 0 stores the Hessenberg column k
-// (accumulate: adds the second pass); w -= V h; then this block's partial dots
-// V_j . w (last == 0) or w . w (last == 1).
+// (2) h1 = sum of the partial dots; block 0 stores it as Hessenberg column k;
+// w -= V h1; then this block's partial dots V_j . w (j <= k) and w . w (column
+// k + 1), all from the same w.
 __global__ void __launch_bounds__(kArnThreads)
 k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __restrict__ V,
            long long ldv, double* __restrict__ H, int ldh, int k_arg,
-           const int* __restrict__ k_dev, int accumulate, double* __restrict__ w,
-           double* __restrict__ pout, int last, int N, const int* __restrict__ done) {
+           const int* __restrict__ k_dev, double* __restrict__ w, double* __restrict__ pout,
+           int N, const int* __restrict__ done) {
     __shared__ double h_sh[kArnMaxCols];
     __shared__ double w_sh[kArnThreads];
     __shared__ double red[32];
@@ -285,8 +285,7 @@ k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __res
     double* hk = H + (size_t)k * ldh;
     reduce_cols_sh(pin, nblk, ld, ncols, h_sh);
     if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < ncols; j += blockDim.x)
-            hk[j] = accumulate ? hk[j] + h_sh[j] : h_sh[j];
+        for (int j = threadIdx.x; j < ncols; j += blockDim.x) hk[j] = h_sh[j];
     const int r0 = blockIdx.x * kArnThreads, i = r0 + threadIdx.x;
     double wi = 0.0;
     if (i < N) {
@@ -294,61 +293,77 @@ k_arn_pass(const double* __restrict__ pin, int nblk, int ld, const double* __res
         for (int j = 0; j < ncols; ++j) wi -= V[(size_t)j * ldv + i] * h_sh[j];
         w[i] = wi;
     }
-    if (!last) {
-        w_sh[threadIdx.x] = wi;
-        __syncthreads();
-        col_dots_sh(V, ldv, ncols, w_sh, r0, min(kArnThreads, N - r0),
-                    pout + (size_t)blockIdx.x * ld);
-    } else {
-        const double t = block_sum(wi * wi, red);
-        if (threadIdx.x == 0) pout[(size_t)blockIdx.x * ld] = t;
-    }
+    w_sh[threadIdx.x] = wi;
+    const double t = block_sum(wi * wi, red);     // synchronises the block (w_sh complete)
+    if (threadIdx.x == 0) pout[(size_t)blockIdx.x * ld + ncols] = t;
+    col_dots_sh(V, ldv, ncols, w_sh, r0, min(kArnThreads, N - r0),
+                pout + (size_t)blockIdx.x * ld);
 }
 
-// (4) |w| from the partials; v_{k+1} = w / |w| with the next apply's prep and
-// wq . v_{k+1} partials.  givens: block 0 also applies the Givens update (may
-// set done); otherwise k_arn_advance does it after this kernel.
+// (3) Second Gram-Schmidt correction and normalisation in one kernel: h2 and
+// |w1|^2 from the partials of (2) (w1 = w after the first correction); block 0
+// adds h2 to Hessenberg column k; w2 = w1 - V h2; |w2| = sqrt(|w1|^2 - |h2|^2)
+// (V orthonormal, so no further reduction is needed; h2 is of rounding size
+// against w1, so the difference does not cancel); v_{k+1} = w2 / |w2| with the
+// next apply's prep and wq . v_{k+1} partials.  givens: block 0 also applies
+// the Givens update (may set done); otherwise k_arn_advance does it with the
+// |w2| left in *hn_out.
 __global__ void __launch_bounds__(kArnThreads)
-k_arn_normalize(const double* __restrict__ pin, int nblk, int ld, double* __restrict__ H,
-                int ldh, int k_arg, const int* __restrict__ k_dev, int givens,
-                double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
-                const double* __restrict__ par, int* __restrict__ done, int* __restrict__ iters,
-                const double* __restrict__ w, double* __restrict__ V, long long ldv,
-                const double* __restrict__ wq, const double* __restrict__ wa,
-                float4* __restrict__ src32, float* __restrict__ sig32, int pp, int ppad,
-                double* __restrict__ pw, int N) {
+k_arn_finish(const double* __restrict__ pin, int nblk, int ld, const double* __restrict__ Vr,
+             long long ldv, double* __restrict__ H, int ldh, int k_arg,
+             const int* __restrict__ k_dev, int givens, double* __restrict__ cs,
+             double* __restrict__ sn, double* __restrict__ g, const double* __restrict__ par,
+             int* __restrict__ done, int* __restrict__ iters, double* __restrict__ w,
+             double* __restrict__ hn_out, double* __restrict__ V, const double* __restrict__ wq,
+             const double* __restrict__ wa, float4* __restrict__ src32,
+             float* __restrict__ sig32, int pp, int ppad, double* __restrict__ pw, int N) {
+    __shared__ double h_sh[kArnMaxCols + 1];
     __shared__ double red[32];
-    __shared__ double nrm[1];
     if (block_done(done)) return;
     const int k = step_index(k_arg, k_dev);
-    reduce_cols_sh(pin, nblk, ld, 1, nrm);
-    const double hn = sqrt(nrm[0]);
-    if (givens && blockIdx.x == 0 && threadIdx.x == 0)
-        givens_update(H, ldh, k, cs, sn, g, hn, par[0], done, iters);
+    const int ncols = k + 1;
+    reduce_cols_sh(pin, nblk, ld, ncols + 1, h_sh);
+    double s2 = 0.0;
+    for (int j = 0; j < ncols; ++j) s2 += h_sh[j] * h_sh[j];
+    const double hn2 = h_sh[ncols] - s2;
+    const double hn = hn2 > 0.0 ? sqrt(hn2) : 0.0;
+    if (blockIdx.x == 0) {
+        double* hk = H + (size_t)k * ldh;
+        for (int j = threadIdx.x; j < ncols; j += blockDim.x) hk[j] += h_sh[j];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *hn_out = hn;
+            if (givens) givens_update(H, ldh, k, cs, sn, g, hn, par[0], done, iters);
+        }
+    }
+    const int i = blockIdx.x * kArnThreads + threadIdx.x;
+    if (i < N) {
+        double wi = w[i];
+        for (int j = 0; j < ncols; ++j) wi -= Vr[(size_t)j * ldv + i] * h_sh[j];
+        w[i] = wi;
+    }
     scale_prep_wdot(w, hn > 0.0 ? 1.0 / hn : 0.0, V + (size_t)(k + 1) * ldv, wq, wa, src32,
                     sig32, pp, ppad, pw + (size_t)blockIdx.x * ld, N, red);
 }
 
-// Graph-driven cycles: the Givens update of step k = *iters (one warp; the same
-// fixed-order reduction of |w|^2 as k_arn_normalize), then the loop condition:
+// Graph-driven cycles: the Givens update of step k = *iters with the |w2| that
+// k_arn_finish left in *hn_in, then the loop condition:
 // continue while not converged and fewer than par[1] steps were taken.  The
 // condition is written on every path, so the loop always ends: at the latest
 // after par[1] <= restart steps, since *iters grows by one per step.
-__global__ void k_arn_advance(const double* __restrict__ pin, int nblk, int ld,
-                              double* __restrict__ H, int ldh, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g,
-                              const double* __restrict__ par, int* __restrict__ done,
-                              int* __restrict__ iters, cudaGraphConditionalHandle cond) {
-    __shared__ double nrm[1];
+__global__ void k_arn_advance(const double* __restrict__ hn_in, double* __restrict__ H, int ldh,
+                              double* __restrict__ cs, double* __restrict__ sn,
+                              double* __restrict__ g, const double* __restrict__ par,
+                              int* __restrict__ done, int* __restrict__ iters,
+                              cudaGraphConditionalHandle cond) {
     const bool was_done = block_done(done);
-    if (!was_done) reduce_cols_sh(pin, nblk, ld, 1, nrm);
     if (threadIdx.x != 0) return;
     if (was_done) {
         cudaGraphSetConditional(cond, 0u);
         return;
     }
     const int k = *iters;
-    givens_update(H, ldh, k, cs, sn, g, sqrt(nrm[0]), par[0], done, iters);
+    givens_update(H, ldh, k, cs, sn, g, *hn_in, par[0], done, iters);
     cudaGraphSetConditional(cond, (!*done && (double)(k + 1) < par[1]) ? 1u : 0u);
 }
 
@@ -387,6 +402,8 @@ struct Work {
     double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr;
     double *part = nullptr, *scal = nullptr, *hcol = nullptr;
     double *pa = nullptr, *pb = nullptr;      // per-block partials of the fused Arnoldi kernels
+    double* pc = nullptr;                     // per-block partials of wq . v (rank-one term)
+    double* hn = nullptr;                     // |w2| of the last step (graph-driven Givens)
     double *w = nullptr, *tmp = nullptr, *r = nullptr, *res = nullptr, *delta = nullptr;
     double *sig = nullptr, *f = nullptr, *u = nullptr;
     int *done = nullptr, *iters = nullptr;
@@ -416,7 +433,7 @@ void pm_solve_free(pm_surface* s) {
     pm_dfree(W.V); pm_dfree(W.H); pm_dfree(W.cs); pm_dfree(W.sn); pm_dfree(W.g); pm_dfree(W.y);
     pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.w); pm_dfree(W.tmp);
     pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig); pm_dfree(W.f);
-    pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.pa); pm_dfree(W.pb);
+    pm_dfree(W.u); pm_dfree(W.done); pm_dfree(W.iters); pm_dfree(W.pa); pm_dfree(W.pb); pm_dfree(W.pc); pm_dfree(W.hn);
     pm_dfree(W.par);
     if (W.exec) cudaGraphExecDestroy(W.exec);
     if (W.graph) cudaGraphDestroy(W.graph);
@@ -454,6 +471,8 @@ pm_status get_work(pm_surface* s, Work** out) {
     W.narn = pm_ceil_div(N, kArnThreads);
     PM_TRY(pm_dmalloc(&W.pa, (size_t)W.narn * (m + 2)));
     PM_TRY(pm_dmalloc(&W.pb, (size_t)W.narn * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.pc, (size_t)W.narn * (m + 2)));
+    PM_TRY(pm_dmalloc(&W.hn, 1));
     PM_TRY(pm_dmalloc(&W.scal, 8));
     PM_TRY(pm_dmalloc(&W.hcol, m + 2));
     PM_TRY(pm_dmalloc(&W.w, N));
@@ -550,7 +569,7 @@ struct Solver {
             k_sq_partial<<<nb, kArnThreads, 0, cs>>>(W.r, N, W.pa, ld);
             k_arn_start<<<nb, kArnThreads, 0, cs>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
                                                     W.iters, W.r, W.V, s->w, s->wa, src32, s->sig32,
-                                                    s->pp, s->ppad, W.pb, N, 1, cond);
+                                                    s->pp, s->ppad, W.pc, N, 1, cond);
             ce = cudaGetLastError();
         }
         const cudaGraphNode_t* deps = nullptr;
@@ -576,18 +595,17 @@ struct Solver {
                 s->skip_flag = W.done;
                 const pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V, W.tmp, prec, bs, 1);
                 s->skip_flag = nullptr;
-                W.body_launches = (int)(s->launch_total - before) + 5;
+                W.body_launches = (int)(s->launch_total - before) + 4;
                 s->launch_total = before;
-                k_arn_first<<<nb, kArnThreads, 0, bs>>>(W.tmp, W.pb, nb, ld, W.V, ldv, 0, W.iters,
+                k_arn_first<<<nb, kArnThreads, 0, bs>>>(W.tmp, W.pc, nb, ld, W.V, ldv, 0, W.iters,
                                                         W.w, W.pa, N, W.done);
                 k_arn_pass<<<nb, kArnThreads, 0, bs>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, 0,
-                                                       W.iters, 0, W.w, W.pb, 0, N, W.done);
-                k_arn_pass<<<nb, kArnThreads, 0, bs>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, 0,
-                                                       W.iters, 1, W.w, W.pa, 1, N, W.done);
-                k_arn_normalize<<<nb, kArnThreads, 0, bs>>>(
-                    W.pa, nb, ld, W.H, m + 2, 0, W.iters, 0, W.cs, W.sn, W.g, W.par, W.done,
-                    W.iters, W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, N);
-                k_arn_advance<<<1, 32, 0, bs>>>(W.pa, nb, ld, W.H, m + 2, W.cs, W.sn, W.g, W.par,
+                                                       W.iters, W.w, W.pb, N, W.done);
+                k_arn_finish<<<nb, kArnThreads, 0, bs>>>(
+                    W.pb, nb, ld, W.V, ldv, W.H, m + 2, 0, W.iters, 0, W.cs, W.sn, W.g, W.par,
+                    W.done, W.iters, W.w, W.hn, W.V, s->w, s->wa, src32, s->sig32, s->pp, s->ppad,
+                    W.pc, N);
+                k_arn_advance<<<1, 32, 0, bs>>>(W.hn, W.H, m + 2, W.cs, W.sn, W.g, W.par,
                                                 W.done, W.iters, cond);
                 ce = cudaGetLastError();
                 cudaGraph_t body_out = nullptr;
@@ -662,7 +680,7 @@ struct Solver {
         k_sq_partial<<<nb, kArnThreads, 0, st>>>(W.r, W.N, W.pa, ld);
         k_arn_start<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.g, m, W.scal, W.par, W.done,
                                                 W.iters, W.r, W.V, s->w, s->wa, src32,
-                                                s->sig32, s->pp, s->ppad, W.pb, W.N, 0, 0);
+                                                s->sig32, s->pp, s->ppad, W.pc, W.N, 0, 0);
         s->launch_total += 2;
         s->skip_flag = W.done;
         // launch the cycle in chunks; between chunks read the done flag so a
@@ -684,17 +702,16 @@ struct Solver {
             pm_status stt = pm_apply_dev(s, 0, 1, 1, W.V + (size_t)k * ldv, W.tmp, prec, st,
                                          fuse_prep ? 1 : 0);
             if (stt != PM_OK) { s->skip_flag = nullptr; return stt; }
-            // partials ping-pong between W.pb and W.pa
-            k_arn_first<<<nb, kArnThreads, 0, st>>>(W.tmp, W.pb, nb, ld, W.V, ldv, k, nullptr,
+            // partials: first -> pa, pass -> pb, finish -> pc (each kernel reduces the
+            // previous one's buffer in every block, so it never writes the one it reads)
+            k_arn_first<<<nb, kArnThreads, 0, st>>>(W.tmp, W.pc, nb, ld, W.V, ldv, k, nullptr,
                                                     W.w, W.pa, W.N, W.done);
             k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pa, nb, ld, W.V, ldv, W.H, m + 2, k, nullptr,
-                                                   0, W.w, W.pb, 0, W.N, W.done);
-            k_arn_pass<<<nb, kArnThreads, 0, st>>>(W.pb, nb, ld, W.V, ldv, W.H, m + 2, k, nullptr,
-                                                   1, W.w, W.pa, 1, W.N, W.done);
-            k_arn_normalize<<<nb, kArnThreads, 0, st>>>(
-                W.pa, nb, ld, W.H, m + 2, k, nullptr, 1, W.cs, W.sn, W.g, W.par, W.done, W.iters,
-                W.w, W.V, ldv, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pb, W.N);
-            s->launch_total += 4;
+                                                   W.w, W.pb, W.N, W.done);
+            k_arn_finish<<<nb, kArnThreads, 0, st>>>(
+                W.pb, nb, ld, W.V, ldv, W.H, m + 2, k, nullptr, 1, W.cs, W.sn, W.g, W.par, W.done,
+                W.iters, W.w, W.hn, W.V, s->w, s->wa, src32, s->sig32, s->pp, s->ppad, W.pc, W.N);
+            s->launch_total += 3;
         }
         s->skip_flag = nullptr;
         PM_CUDA_TRY(cudaGetLastError());
