@@ -351,8 +351,9 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 operator applies (compensated sums) + float-float residuals/representation "
-                 "+ f64 Krylov basis and near field",
+        "dtype": "f32",
+        "dtype_detail": "f32 operator applies (compensated sums) + float-float residuals/"
+                        "representation + f64 Krylov basis and near field",
         "data": "synthetic", "impl": "gb300",
         "config": {"workload": args.workload, "N": N,
                    "step": "one solve of div(a grad u) = f to relative residual "
