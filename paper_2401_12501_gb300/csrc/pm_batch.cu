@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kRB = 16;         // right-hand sides per block (float32) unless tuned (8, 16 or 32)
-constexpr int kRBff = 16;       // right-hand sides per block (float-float)
+constexpr int kRBff = 16;       // right-hand sides per block (float-float); 8 for batches of <= 8
 constexpr int kTile = 256;
 constexpr int kStage = 512;
 
@@ -281,7 +281,7 @@ __global__ void k_prep_ff_multi(const double* __restrict__ sigma, long long ld_s
 // src_ff: source coordinates (their .w strengths are not read; sff holds the
 // strengths of every right-hand side) -- plain float-float pairs for the
 // remainder, the grid split for the parametrix (pm_ffsum.cu)
-template <bool KERNEL_K>
+template <bool KERNEL_K, int RB>
 __global__ void __launch_bounds__(kThreads)
 k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ sff, int nrhs,
                   const float4* __restrict__ tg, const float4* __restrict__ log_tab, int N,
@@ -290,12 +290,12 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
     if (skip && *skip) return;
     constexpr int kSt = 256;
     __shared__ float4 sh[2 * kSt];
-    __shared__ float2 sS[kRBff][kSt];
+    __shared__ float2 sS[RB][kSt];
     __shared__ float4 stab[128];
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kThreads + tid;
-    const int r0 = blockIdx.z * kRBff;
-    const int nr = min(kRBff, nrhs - r0);
+    const int r0 = blockIdx.z * RB;
+    const int nr = min(RB, nrhs - r0);
     const int tbase = blockIdx.x * kThreads, tend = tbase + kThreads;
     if (KERNEL_K)
         for (int k = tid; k < 128; k += kThreads) stab[k] = log_tab[k];
@@ -312,9 +312,9 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
         NP[0] = ff{v[2].x, v[3].x}; NP[1] = ff{v[2].y, v[3].y}; NP[2] = ff{v[2].z, v[3].z};
         MM[0] = ff{v[4].x, v[5].x}; MM[1] = ff{v[4].y, v[5].y}; MM[2] = ff{v[4].z, v[5].z};
     }
-    ff acc[kRBff];
+    ff acc[RB];
 #pragma unroll
-    for (int q = 0; q < kRBff; ++q) acc[q] = ff{0.f, 0.f};
+    for (int q = 0; q < RB; ++q) acc[q] = ff{0.f, 0.f};
     const int s0 = blockIdx.y * chunk;
     const int s1 = min(s0 + chunk, N);
     for (int base = s0; base < s1; base += kSt) {
@@ -323,7 +323,7 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
         for (int j = tid; j < 2 * len; j += kThreads) sh[j] = src_ff[2 * (size_t)base + j];
         for (int j = tid; j < len; j += kThreads)
 #pragma unroll
-            for (int q = 0; q < kRBff; ++q)
+            for (int q = 0; q < RB; ++q)
                 sS[q][j] = (q < nr) ? sff[(size_t)(r0 + q) * N + base + j] : make_float2(0.f, 0.f);
         __syncthreads();
         const bool own = !(base + len <= tbase || base >= tend);
@@ -348,7 +348,7 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
                 gfac = ff_mul(inv, inner);
             }
 #pragma unroll
-            for (int q = 0; q < kRBff; ++q) {
+            for (int q = 0; q < RB; ++q) {
                 // s * g in float-float (product and its error), then a lazy
                 // float-float accumulation: TwoSum on the high parts, all error
                 // terms summed in the low part (renormalised at the end)
@@ -365,7 +365,7 @@ k_direct_multi_ff(const float4* __restrict__ src_ff, const float2* __restrict__ 
     }
     if (i < N) {
 #pragma unroll
-        for (int q = 0; q < kRBff; ++q) {
+        for (int q = 0; q < RB; ++q) {
             if (q >= nr) continue;
             ff v;
             fast_two_sum(acc[q].h, acc[q].l, v.h, v.l);
@@ -519,21 +519,28 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
     const int* skip = s->skip_flag;
     dim3 gp(pm_ceil_div(N, 256), nrhs);
     if (prec == PM_PREC_FF) {
-        const int ns = batch_splits(s, nrhs, kRBff, 8);
+        // 8 right-hand sides per block when the batch has no more: the per-RHS
+        // float-float work runs over every slot of a block
+        const int rbff = nrhs <= 8 ? 8 : kRBff;
+        const int ns = batch_splits(s, nrhs, rbff, 8);
         {
             PhaseTimer t(s, PM_PHASE_PREP, st);
             k_prep_ff_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.sff, N, skip);
         }
         {
             PhaseTimer t(s, PM_PHASE_DIRECT64, st);
-            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, kRBff));
+            dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, rbff));
             const int chunk = pm_ceil_div(N, ns);
-            if (kernel_K)
-                k_direct_multi_ff<true><<<g, kThreads, 0, st>>>(s->src_kg, B.sff, nrhs, s->tgt_ff,
-                                                               s->log_tab, N, chunk, B.part, ns, skip);
+            const float4* srcv = kernel_K ? s->src_kg : s->src_ff;
+            auto launch = [&](auto kern) {
+                kern<<<g, kThreads, 0, st>>>(srcv, B.sff, nrhs, s->tgt_ff, s->log_tab, N, chunk,
+                                             B.part, ns, skip);
+            };
+            if (rbff == 8)
+                kernel_K ? launch(k_direct_multi_ff<true, 8>) : launch(k_direct_multi_ff<false, 8>);
             else
-                k_direct_multi_ff<false><<<g, kThreads, 0, st>>>(s->src_ff, B.sff, nrhs, s->tgt_ff,
-                                                                s->log_tab, N, chunk, B.part, ns, skip);
+                kernel_K ? launch(k_direct_multi_ff<true, kRBff>)
+                         : launch(k_direct_multi_ff<false, kRBff>);
         }
         PhaseTimer t(s, PM_PHASE_NEAR, st);
         dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
