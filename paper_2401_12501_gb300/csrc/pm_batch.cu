@@ -201,6 +201,10 @@ k_near_multi32(int N, int ppad, int npatch, const int* __restrict__ row_ptr,
 // right-hand sides instead of once per right-hand side.
 constexpr int kPatchRhs = 32;
 
+// R right-hand sides per block (R = 32, or 8 for small batches): lane = sub-row *
+// R + rhs, so a warp takes 32 / R rows at a time and no lane idles when the
+// batch has only 8 right-hand sides.  Shared memory: [u * ppad + k][R + 1].
+template <int R>
 __global__ void __launch_bounds__(256)
 k_near_multi32_patch(int N, int pp, int ppad, int npatch, const int* __restrict__ row_ptr,
                      const int* __restrict__ blk_u, const int* __restrict__ pu_ptr,
@@ -209,47 +213,54 @@ k_near_multi32_patch(int N, int pp, int ppad, int npatch, const int* __restrict_
                      int nsplit, int nrhs, double* __restrict__ out, long long ld_out,
                      const int* __restrict__ skip) {
     if (skip && *skip) return;
-    extern __shared__ float shs[];                     // [u * ppad + k][33]
+    static_assert(32 % R == 0, "R divides the warp");
+    constexpr int kSub = 32 / R;                        // rows per warp step
+    constexpr int kLd = R + 1;
+    extern __shared__ float shs[];
     const int P = blockIdx.x;
-    const int r0 = blockIdx.y * kPatchRhs;
-    const int nr = min(kPatchRhs, nrhs - r0);
+    const int r0 = blockIdx.y * R;
+    const int nr = min(R, nrhs - r0);
     const int u0 = pu_ptr[P], U = pu_ptr[P + 1] - u0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // stage: index e = ((u * 32 + rr) * ppad + k): k fastest, contiguous in global memory
-    const int total = U * kPatchRhs * ppad;
+    // stage: index e = ((u * R + rr) * ppad + k): k fastest, contiguous in global memory
+    const int total = U * R * ppad;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int k = e % ppad, t = e / ppad;
-        const int rr = t % kPatchRhs, u = t / kPatchRhs;
+        const int rr = t % R, u = t / R;
         float v = 0.f;
         if (rr < nr && k < pp)
             v = sig32[(size_t)(r0 + rr) * npatch * ppad + (size_t)pu_list[u0 + u] * ppad + k];
-        shs[(u * ppad + k) * 33 + rr] = v;
+        shs[(u * ppad + k) * kLd + rr] = v;
     }
     __syncthreads();
-    const int r = r0 + lane;
-    const bool act = lane < nr;
+    const int sub = lane / R, rr = lane - sub * R;
+    const int r = r0 + rr;
+    const bool act = rr < nr;
     const int q4 = ppad >> 2;
-    for (int t = warp; t < pp; t += blockDim.x >> 5) {
-        const int i = P * pp + t;
+    for (int t0 = warp * kSub; t0 < pp; t0 += (blockDim.x >> 5) * kSub) {
+        const int t = t0 + sub;
+        const bool row_ok = t < pp;
+        const int i = P * pp + (row_ok ? t : 0);
         float hi = 0.f, lo = 0.f;
-        if (act)
+        if (act && row_ok)
             for (int sp = 0; sp < nsplit; ++sp) {
                 const float2 v = partial[((size_t)r * nsplit + sp) * N + i];
                 two_sum_acc(hi, lo, v.x);
                 lo += v.y;
             }
         float acc = 0.f;
-        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        const int b0 = row_ok ? row_ptr[i] : 0, b1 = row_ok ? row_ptr[i + 1] : 0;
+        for (int b = b0; b < b1; ++b) {
             const float4* c4 = reinterpret_cast<const float4*>(vals + (size_t)b * ppad);
-            const float* su = shs + blk_u[b] * ppad * 33 + lane;
+            const float* su = shs + blk_u[b] * ppad * kLd + rr;
             for (int k4 = 0; k4 < q4; ++k4) {
                 const float4 c = __ldg(c4 + k4);
-                const float* sk = su + 4 * k4 * 33;
-                acc = fmaf(c.x, sk[0], fmaf(c.y, sk[33], fmaf(c.z, sk[66], fmaf(c.w, sk[99], acc))));
+                const float* sk = su + 4 * k4 * kLd;
+                acc = fmaf(c.x, sk[0], fmaf(c.y, sk[kLd], fmaf(c.z, sk[2 * kLd], fmaf(c.w, sk[3 * kLd], acc))));
             }
         }
         two_sum_acc(hi, lo, acc);
-        if (act) out[r * ld_out + i] = (double)hi + (double)lo;
+        if (act && row_ok) out[r * ld_out + i] = (double)hi + (double)lo;
     }
 }
 
@@ -499,8 +510,10 @@ static pm_status build_patch_unions(pm_surface* s, PmBatchWork& B) {
     PM_CUDA_TRY(cudaMemcpy(B.blk_u, bu.data(), sizeof(int) * bu.size(), cudaMemcpyHostToDevice));
     // the attribute is process-wide: always the same cap, so that surfaces prepared by
     // different threads never lower it under one another's launches
-    PM_CUDA_TRY(cudaFuncSetAttribute(k_near_multi32_patch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemCap));
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_near_multi32_patch<kPatchRhs>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_near_multi32_patch<8>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemCap));
     B.umax = umax;
     return PM_OK;
 }
@@ -573,11 +586,19 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
         if (!B.patch_tried) PM_TRY(build_patch_unions(s, B));
         PhaseTimer t(s, PM_PHASE_NEAR, st);
         if (B.umax > 0) {
-            const dim3 gn(s->npatch, pm_ceil_div(nrhs, kPatchRhs));
-            const size_t smem = (size_t)B.umax * s->ppad * 33 * sizeof(float);
-            k_near_multi32_patch<<<gn, 256, smem, st>>>(
-                N, s->pp, s->ppad, s->npatch, s->row_ptr, B.blk_u, B.pu_ptr, B.pu_list,
-                kernel_K ? s->cK32 : s->cR32, B.sig32, B.part, ns, nrhs, out, ld_out, skip);
+            // 8 right-hand sides per block for batches of at most 8 (four rows per warp)
+            const int rp = nrhs <= 8 ? 8 : kPatchRhs;
+            const dim3 gn(s->npatch, pm_ceil_div(nrhs, rp));
+            const size_t smem = (size_t)B.umax * s->ppad * (rp + 1) * sizeof(float);
+            auto launch = [&](auto kern) {
+                kern<<<gn, 256, smem, st>>>(N, s->pp, s->ppad, s->npatch, s->row_ptr, B.blk_u,
+                                            B.pu_ptr, B.pu_list, kernel_K ? s->cK32 : s->cR32,
+                                            B.sig32, B.part, ns, nrhs, out, ld_out, skip);
+            };
+            if (rp == 8)
+                launch(k_near_multi32_patch<8>);
+            else
+                launch(k_near_multi32_patch<kPatchRhs>);
         } else {
             dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs);
             k_near_multi32<<<gn, 256, 0, st>>>(N, s->ppad, s->npatch, s->row_ptr, s->blk_patch,
