@@ -504,16 +504,20 @@ __global__ void k_combine(int nblk, int pp, int ppad, const int* __restrict__ bl
 }
 
 // ------------------------------------------------------------------ correction SpMV
-// One warp per target row: out_i = sum_s partial[s][i] + sum_b C[b, :] . sigma[patch_b].
-// float32 path: the row's blocks are contiguous, so the warp walks the flat
-// list of float4 values (four loads in flight per lane); the split partials
-// (hi, lo) and the lane sums are combined with TwoSum in float32.
+// L lanes per target row: out_i = sum_s partial[s][i] + sum_b C[b, :] .
+// sigma[patch_b].  L = 32 (a warp per row) while all rows fit in one wave of
+// warps; beyond that L = 8, so that every warp keeps the load chains of four
+// rows in flight (the kernel is bound by load latency, not bandwidth).  float32 path: the row's blocks are contiguous, so the row's
+// lanes walk the flat list of float4 values (four loads in flight per lane);
+// the split partials (hi, lo) and the lane sums are combined with TwoSum in
+// float32.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     const float bp = s - a;
     e = (a - (s - bp)) + (b - bp);
 }
 
+template <int L>
 __global__ void __launch_bounds__(256)
 k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
                const int* __restrict__ blk_patch, const float* __restrict__ vals,
@@ -521,30 +525,31 @@ k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
                int nsplit, int use_near, double* __restrict__ out,
                const int* __restrict__ skip) {
     if (skip && *skip) return;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= N) return;
-    const int i = warp;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / L;               // row of this lane group
+    const int hl = threadIdx.x % L;     // lane within the group
+    const bool row_ok = i < N;
     float hi = 0.f, lo = 0.f;
-    for (int sp = lane; sp < nsplit; sp += 32) {
-        const float2 v = partial[(size_t)sp * N + i];
-        float s, e;
-        two_sum(hi, v.x, s, e);
-        hi = s;
-        lo += e + v.y;
-    }
-    if (use_near) {
+    if (row_ok)
+        for (int sp = hl; sp < nsplit; sp += L) {
+            const float2 v = partial[(size_t)sp * N + i];
+            float s, e;
+            two_sum(hi, v.x, s, e);
+            hi = s;
+            lo += e + v.y;
+        }
+    if (use_near && row_ok) {
         const int q4 = ppad >> 2;
         const int rb = row_ptr[i];
         const int total = (row_ptr[i + 1] - rb) * q4;
         const float4* v4 = reinterpret_cast<const float4*>(vals) + (size_t)rb * q4;
         const float4* s4 = reinterpret_cast<const float4*>(sig32);
         float acc = 0.f;
-        for (int e0 = 0; e0 < total; e0 += 128) {
+        for (int e0 = 0; e0 < total; e0 += 4 * L) {
             float4 v[4], x[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = e0 + u * 32 + lane;
+                const int e = e0 + u * L + hl;
                 if (e < total) {
                     const int b = e / q4;
                     v[u] = __ldg(v4 + e);
@@ -563,15 +568,16 @@ k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
         hi = s;
         lo += e;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
-        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    // reduce within the lane group (xor offsets < L stay inside it)
+    for (int o = L / 2; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
         float s, e;
         two_sum(hi, h2, s, e);
         hi = s;
         lo += e + l2;
     }
-    if (lane == 0) out[i] = (double)hi + (double)lo;
+    if (row_ok && hl == 0) out[i] = (double)hi + (double)lo;
 }
 
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
@@ -686,7 +692,9 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
                         int use_near, int nsplit, pm_precision prec, cudaStream_t st) {
     const int N = s->N;
     const int threads = 256;
-    const int blocks = pm_ceil_div((long long)N * 32, threads);
+    const int blocks = pm_ceil_div((long long)N * 32, threads);       // float64: warp per row
+    // float32: a lane group per row, a warp while the rows fit in one wave of warps
+    const bool one_wave = (long long)N * 32 <= (long long)s->ctx->num_sms * 2048;
     if (prec == PM_PREC_FP64 || prec == PM_PREC_FF)
         k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK64 : s->cR64, sigma,
@@ -694,10 +702,10 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
                                                    use_near, out,
                                                    s->skip_flag);
     else
-        k_near_apply32<<<blocks, threads, 0, st>>>(N, s->ppad, s->row_ptr, s->blk_patch,
-                                                   which_K ? s->cK32 : s->cR32, s->sig32,
-                                                   reinterpret_cast<const float2*>(s->partial),
-                                                   nsplit, use_near, out, s->skip_flag);
+        (one_wave ? k_near_apply32<32> : k_near_apply32<8>)
+            <<<pm_ceil_div((long long)N * (one_wave ? 32 : 8), threads), threads, 0, st>>>(
+                N, s->ppad, s->row_ptr, s->blk_patch, which_K ? s->cK32 : s->cR32, s->sig32,
+                reinterpret_cast<const float2*>(s->partial), nsplit, use_near, out, s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
