@@ -214,7 +214,7 @@ def run_gpu(args, rank, world, local_rank):
     surf.set_coeff(wl.coeff.a, wl.coeff.grad_a)
     nblk = surf.info()[1]
     # launch shape of the float32 sums picked by the autotuner (untimed, before warm-up)
-    tune = surf.autotune(nrhs=1, prec="fp32", reps=5)
+    tune = surf.autotune(nrhs=1, prec="fp32", reps=5) if not args.no_autotune else _builtin(surf)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -362,8 +362,8 @@ def run_gpu(args, rank, world, local_rank):
                    "value_definition": "smooth-sum pairs evaluated per second over the solve "
                                        "step = (Arnoldi steps + refinements + 1) * N^2 / time",
                    "near_blocks": nblk, "near_build_s": round(t_build, 3),
-                   "autotune": {"knobs": tune["knobs"], "apply_ms": round(tune["best_ms"], 4),
-                                "builtin_apply_ms": round(tune["default_ms"], 4),
+                   "autotune": {"knobs": tune["knobs"], "apply_ms": _r(tune["best_ms"], 4),
+                                "builtin_apply_ms": _r(tune["default_ms"], 4),
                                 "candidates": tune["candidates"]},
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -390,6 +390,16 @@ def run_gpu(args, rank, world, local_rank):
 
 
 # ----------------------------------------------------------------------------- other configs
+def _builtin(s):
+    """The autotuner's report for the built-in launch shapes (used with --no-autotune)."""
+    return {"knobs": s.knobs(), "best_ms": None, "default_ms": None,
+            "candidates": 0, "cached": False, "key": "built-in"}
+
+
+def _r(v, nd):
+    return None if v is None else round(v, nd)
+
+
 def run_batched(args, dev):
     """24,576-node star with 8 coefficient fields and 64 right-hand sides (RHS r on
     field r mod 8): 8 operators on one geometry (one near-field build, 7 clones),
@@ -408,8 +418,9 @@ def run_batched(args, dev):
     s0.set_coeff(coeffs[0].a, coeffs[0].grad_a)
     # launch shapes picked by the autotuner (copied to the clones): one right-hand
     # side, 8 per field; the 64-RHS shape is tuned on its own below
-    tune1 = s0.autotune(nrhs=1, prec="fp32", reps=3)
-    tune8 = s0.autotune(nrhs=n_rhs // n_field, prec="fp32", reps=3)
+    tune1 = s0.autotune(nrhs=1, prec="fp32", reps=3) if not args.no_autotune else _builtin(s0)
+    tune8 = (s0.autotune(nrhs=n_rhs // n_field, prec="fp32", reps=3) if not args.no_autotune
+             else _builtin(s0))
     t0 = time.perf_counter()
     ops = [s0] + [s0.clone() for _ in range(n_field - 1)]
     t_clone = time.perf_counter() - t0
@@ -456,7 +467,8 @@ def run_batched(args, dev):
     t_served, res_served = serve_all(64, 4)
 
     # all 64 right-hand sides on field 0
-    tune64 = ops[0].autotune(nrhs=n_rhs, prec="fp32", reps=3)
+    tune64 = (ops[0].autotune(nrhs=n_rhs, prec="fp32", reps=3) if not args.no_autotune
+              else _builtin(ops[0]))
     ops[0].solve(Fd, tol=args.tol, prec="fp32")
     torch.cuda.synchronize()
     reps = 3
@@ -468,8 +480,8 @@ def run_batched(args, dev):
     for op in ops:
         op.close()
     knobs = lambda r: {"knobs": {k: v for k, v in r["knobs"].items() if v},
-                       "apply_ms": round(r["best_ms"], 3),
-                       "builtin_apply_ms": round(r["default_ms"], 3)}
+                       "apply_ms": _r(r["best_ms"], 3),
+                       "builtin_apply_ms": _r(r["default_ms"], 3)}
     return {"workload": "star_24576: 8 coefficient fields a = 1 + 0.4 tanh(g) (seeds 0-7) x "
                         "64 right-hand sides (seeds 0-63), RHS r on field r mod 8",
             "N": s_surf.N, "near_build_s": round(t_build, 3),
@@ -560,8 +572,8 @@ def run_fmm(args, dev):
     t_build = time.perf_counter() - t0
     s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
     # octree depth and direct-sum launch shape picked by the autotuner
-    tune_fmm = s.autotune(nrhs=1, prec="fmm", reps=3)
-    tune_32 = s.autotune(nrhs=1, prec="fp32", reps=3)
+    tune_fmm = s.autotune(nrhs=1, prec="fmm", reps=3) if not args.no_autotune else _builtin(s)
+    tune_32 = s.autotune(nrhs=1, prec="fp32", reps=3) if not args.no_autotune else _builtin(s)
     st = s.fmm_stats()
     sig = torch.from_numpy(np.random.default_rng(3).standard_normal(wl.N)).to(dev)
     out = {}
@@ -604,8 +616,8 @@ def run_fmm(args, dev):
            "solve_u_rel_diff_fmm_vs_fp32": float(np.sqrt(np.dot(w, du * du) /
                                                          np.dot(w, solves["fp32"][1] ** 2))),
            "autotune": {t: {"knobs": {k: v for k, v in r["knobs"].items() if v},
-                            "apply_ms": round(r["best_ms"], 3),
-                            "builtin_apply_ms": round(r["default_ms"], 3),
+                            "apply_ms": _r(r["best_ms"], 3),
+                            "builtin_apply_ms": _r(r["default_ms"], 3),
                             "candidates": r["candidates"]}
                         for t, r in (("fmm", tune_fmm), ("fp32", tune_32))},
            "fmm_tree": st, "apply_R_ms": {k: round(v[0] * 1e3, 3) for k, v in out.items()},
@@ -747,6 +759,9 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in launch shapes (for profiler runs, whose timings "
+                         "would mislead the autotuner)")
     ap.add_argument("--extras", default="batched,fmm,served,paper",
                     help="comma-separated extra measurements to run (batched, fmm, served, paper)")
     ap.add_argument("--no-extra", action="store_true",
