@@ -173,7 +173,8 @@ typedef struct {
 } pm_knobs;
 
 /* Set (all fields, validated first: PM_ERR_INVALID_ARG leaves the surface
- * unchanged) or read the surface's knobs. */
+ * unchanged) or read the surface's knobs.  Setting synchronises the device; no
+ * other call may use the surface meanwhile (applies, solves, server requests). */
 pm_status pm_surface_set_knobs(pm_surface* s, const pm_knobs* k);
 pm_status pm_surface_get_knobs(const pm_surface* s, pm_knobs* k);
 
@@ -194,8 +195,9 @@ typedef struct {
  * P2P limit are skipped).  Each candidate: one warm-up apply, then reps
  * (1..100) applies timed with CUDA events on a private stream; the median
  * counts.  The input is a fixed smooth density, allocated and freed here.
- * Requires pm_surface_set_coeff.  On an error the knobs in force before the
- * call are restored.  out may not be NULL.
+ * Requires pm_surface_set_coeff; no other call may use the surface meanwhile.
+ * On an error the knobs in force before the call are restored.  out may not be
+ * NULL.
  */
 pm_status pm_surface_autotune(pm_surface* s, int nrhs, pm_precision prec, int reps,
                               pm_tune_result* out);
