@@ -34,7 +34,7 @@ def test_clone_matches_a_fresh_surface(ctx):
     assert c.info() == fresh.info()
     sigma = np.random.default_rng(8).standard_normal(wl.N)
     before = s0.apply_R(sigma, "fp64")
-    for prec in ("fp64", "ff", "fp32"):
+    for prec in ("fp64", "ff", "fp32", "fmm"):
         assert np.array_equal(c.apply_R(sigma, prec), fresh.apply_R(sigma, prec)), prec
         assert np.array_equal(c.apply_K(sigma, prec), fresh.apply_K(sigma, prec)), prec
     assert np.array_equal(s0.apply_R(sigma, "fp64"), before)      # the original keeps its coefficient
@@ -45,6 +45,11 @@ def test_clone_matches_a_fresh_surface(ctx):
     u2, i2 = fresh.solve(f, tol=1e-10)
     assert i1[0].iterations == i2[0].iterations
     assert np.array_equal(u1, u2)
+    F = np.stack([f, np.roll(f, 17) - np.dot(wl.surface.weights, np.roll(f, 17)) /
+                  wl.surface.weights.sum()])
+    U1, _ = c.solve(F, tol=1e-10)                                 # batched lockstep solve
+    U2, _ = fresh.solve(F, tol=1e-10)
+    assert np.array_equal(U1, U2)
     c2 = c.clone()                                                # a clone of a clone
     c2.set_coeff(co.a, co.grad_a)
     assert np.array_equal(c2.apply_R(sigma, "ff"), fresh.apply_R(sigma, "ff"))
