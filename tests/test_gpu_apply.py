@@ -279,3 +279,18 @@ def test_patch_orders_against_oracle_rows(ctx, p):
         assert np.abs(yR - oR).max() <= tol * np.abs(oR).max(), (p, prec)
         assert np.abs(yK - oK).max() <= tol * np.abs(oK).max(), (p, prec)
     s.close()
+
+
+@pytest.mark.parametrize("name", ["ellipsoid_small", "wavy_torus_small"])
+def test_stored_oracle_values(ctx, name):
+    """The CUDA path against the oracle values stored in tests/golden/ (written by
+    tests/golden/make_golden.py from the oracle alone), at the stored rows."""
+    from conftest import golden
+    case = golden("oracle_applies.json")["cases"][name]
+    _, s = gpu_surface(ctx, name)
+    sigma = np.random.default_rng(2024).standard_normal(case["N"]) + 1.0
+    rows = case["rows"]
+    R, K = np.array(case["R"]), np.array(case["K"])
+    for prec, tol in (("fp64", 1e-10), ("ff", 1e-10), ("fp32", 1e-5)):
+        assert np.abs(s.apply_R(sigma, prec)[rows] - R).max() <= tol * np.abs(R).max(), prec
+        assert np.abs(s.apply_K(sigma, prec)[rows] - K).max() <= tol * np.abs(K).max(), prec

@@ -67,6 +67,14 @@ def test_remainder_equals_surface_operator_of_parametrix():
         assert abs(fd - val) < 1e-5 * max(1.0, abs(val)), (fd, val)
 
 
+def _sphere_constant():
+    from conftest import golden
+    return golden("closed_forms.json")["sphere_remainder_constant"]["value"]   # -1/(4 pi)
+
+
+R_SPHERE = _sphere_constant()
+
+
 def test_sphere_remainder_is_constant():
     s = cubed_sphere(1, 6)
     rng = np.random.default_rng(0)
@@ -75,7 +83,7 @@ def test_sphere_remainder_is_constant():
         ys = np.delete(s.nodes, k, axis=0)
         v = remainder(s.nodes[k], s.normals[k], s.curvature[k], 1.0, np.zeros(3), ys,
                       np.ones(len(ys)))
-        assert np.abs(v + 1 / (4 * np.pi)).max() < 1e-13
+        assert np.abs(v - R_SPHERE).max() < 1e-13
 
 
 @pytest.mark.parametrize("alpha", [0.0, 0.4, np.pi / 4, 1.1, np.pi / 2])

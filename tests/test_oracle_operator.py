@@ -21,7 +21,7 @@
 import numpy as np
 import pytest
 
-from conftest import oracle_processes
+from conftest import golden, oracle_processes
 from oracle.operator import (Discretization, NearField, apply_K, apply_R,
                              second_kind_matrix)
 from oracle.solve import gmres, relative_l2, solve
@@ -66,13 +66,16 @@ def test_sphere_null_vector(sphere):
 def test_sphere_funk_hecke(sphere, l, m):
     _, d, nf = sphere
     Y = real_sph_harm(l, m, d.x)
-    assert relative_l2(apply_K(d, nf, Y), -Y / (l * (l + 1)), d.w) < 2e-5
+    ev = golden("closed_forms.json")["sphere_parametrix_eigenvalues"]
+    lam = ev["value"][ev["l"].index(l)]                     # -1/(l(l+1))
+    assert relative_l2(apply_K(d, nf, Y), lam * Y, d.w) < 2e-5
 
 
 def test_sphere_parametrix_of_constant(sphere):
     _, d, nf = sphere
     K1 = apply_K(d, nf, np.ones(d.N))
-    assert np.abs(K1 - (2 * np.log(2) - 1)).max() < 1e-6
+    c = golden("closed_forms.json")["sphere_parametrix_constant"]["value"]   # 2 ln 2 - 1
+    assert np.abs(K1 - c).max() < 1e-6
 
 
 def test_sphere_solve_eigenfunction(sphere):
