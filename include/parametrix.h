@@ -324,6 +324,18 @@ pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int
                             double* out);
 
 /*
+ * Self-test of the FMM's M2L offset classes (host code only, no device call):
+ * for the 343 box offsets d = (dx, dy, dz) in [-3, 3]^3, entry
+ * k = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3) of cls[343] receives the class
+ * (0..15) of a V-list offset (max |d_i| in {2, 3}) or -1, and sym[343] the
+ * signed axis permutation g with d = g d_c: bits 0-1, 2-3, 4-5 = pi(0..2),
+ * bit 6 + a set where s_a = -1, (g v)_a = s_a v_pi(a).  canon[48] receives the
+ * 16 canonical offsets d_c (x >= y >= z >= 0) as (x, y, z) triples.
+ * PM_ERR_INVALID_ARG for NULL arrays.
+ */
+pm_status pm_selftest_fmm_classes(int* cls, int* sym, int* canon);
+
+/*
  * Serving: continuous batching of solve requests over many operators.
  *
  * An operator is a pm_surface whose coefficient is set.  pm_server_create starts

@@ -1173,6 +1173,28 @@ pm_status ensure_m2l_gemm(PmFmmTree* T) {
 
 }  // namespace
 
+extern "C" pm_status pm_selftest_fmm_classes(int* cls, int* sym, int* canon) {
+    if (!cls || !sym || !canon) {
+        pm_set_error("pm_selftest_fmm_classes: NULL argument");
+        return PM_ERR_INVALID_ARG;
+    }
+    for (int c = 0; c < kNClass; ++c) {
+        const int3 o = canonical_offset(c);
+        canon[3 * c] = o.x;
+        canon[3 * c + 1] = o.y;
+        canon[3 * c + 2] = o.z;
+    }
+    for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dz = -3; dz <= 3; ++dz) {
+                const int k = ((dx + 3) * 7 + (dy + 3)) * 7 + (dz + 3);
+                int g = 0;
+                cls[k] = offset_class(make_int3(dx, dy, dz), &g);
+                sym[k] = cls[k] >= 0 ? g : 0;
+            }
+    return PM_OK;
+}
+
 // Partial slices the FMM writes per target (U-list neighbours + far field).
 int pm_fmm_splits() { return kUMax + 1; }
 

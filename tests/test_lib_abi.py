@@ -79,3 +79,41 @@ def test_struct_layouts_match_header(cname, pyname):
     py = getattr(_lib, pyname)._fields_
     assert [n for _, n in fields] == [n for n, _ in py]
     assert [ctype[t] for t, _ in fields] == [t for _, t in py]
+
+
+def test_fmm_offset_classes(lib):
+    """The FMM's M2L symmetry reduction (host code, no GPU): the 316 V-list offsets of
+    [-3, 3]^3 (max |d_i| in {2, 3}) fall into 16 classes; for each offset the returned
+    signed axis permutation g maps the class's canonical offset d_c onto it,
+    (g v)_a = s_a v_pi(a); every class holds exactly the orbit of d_c under the 48
+    signed permutations of the cube; other offsets are rejected."""
+    import itertools
+    import numpy as np
+    from paper_2401_12501_gb300._lib import ptr
+    cls = np.zeros(343, np.int32)
+    sym = np.zeros(343, np.int32)
+    canon = np.zeros(48, np.int32)
+    assert lib.pm_selftest_fmm_classes(ptr(cls), ptr(sym), ptr(canon)) == 0
+    canon = canon.reshape(16, 3)
+    assert len({tuple(c) for c in canon}) == 16
+    assert all(c[0] >= c[1] >= c[2] >= 0 and c[0] in (2, 3) for c in canon)
+    members = {c: set() for c in range(16)}
+    for d in itertools.product(range(-3, 4), repeat=3):
+        k = ((d[0] + 3) * 7 + (d[1] + 3)) * 7 + (d[2] + 3)
+        if max(map(abs, d)) < 2:
+            assert cls[k] == -1
+            continue
+        c = int(cls[k])
+        assert 0 <= c < 16
+        g = int(sym[k])
+        pi = [(g >> (2 * a)) & 3 for a in range(3)]
+        s = [-1 if (g >> (6 + a)) & 1 else 1 for a in range(3)]
+        assert sorted(pi) == [0, 1, 2]
+        assert tuple(s[a] * canon[c][pi[a]] for a in range(3)) == d
+        members[c].add(d)
+    assert sum(len(m) for m in members.values()) == 316
+    for c, m in members.items():
+        orbit = {tuple(sg[a] * canon[c][p[a]] for a in range(3))
+                 for p in itertools.permutations(range(3))
+                 for sg in itertools.product((1, -1), repeat=3)}
+        assert m == orbit, c
