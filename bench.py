@@ -136,6 +136,20 @@ def oracle_rate(workload: str, seconds: float = 12.0):
     return rate, desc
 
 
+def reference_line(args, vals, desc):
+    """The reference arm's JSON line: the oracle's rate (mean over the timed steps)."""
+    v = statistics.mean(vals[args.warmup:]) if len(vals) > args.warmup else vals[-1]
+    return {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "impl": "reference",
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_oracle_subprocess(workload: str, seconds: float):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -793,16 +807,7 @@ def main():
             r = run_oracle_subprocess(args.workload, max(2.0, 60.0 / (args.steps + args.warmup)))
             vals.append(r["value"])
             desc = r["sample"]
-        v = statistics.mean(vals[args.warmup:]) if len(vals) > args.warmup else vals[-1]
-        print(json.dumps({
-            "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "impl": "reference",
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": desc},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }))
+        print(json.dumps(reference_line(args, vals, desc)))
         return
 
     if world > 1:
