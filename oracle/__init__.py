@@ -12,7 +12,9 @@ surface PDEs"):
 * kernels.py   -- the parametrix K = log r / (2 pi a(x')) (Sec. 4.2, eq.
   diff_param) and its remainder R for c = 0, b = 0 (Thm. parametrix, eq.
   explicit_remainder), which reduces to R_LB (Thm. parametrixLB, eq.
-  explicit_remainderLB) for constant a.
+  explicit_remainderLB) for constant a; and for c != 0 the Hankel Green's
+  function G = -(i / 4a) H0(sqrt(c/a) r), the remainder with its c terms
+  and the constant-coefficient form of the Corollary (eq. bdd_remainder_helm).
 * patch.py     -- tensor Lagrange interpolation of node data on a quad patch
   (the quad analogue of the interpolation in Sec. 6.1.1 remark / 6.1.2).
 * quadrature.py-- the three quadrature classes of Sec. 6.1: smooth (6.1.3),
@@ -20,7 +22,8 @@ surface PDEs"):
   adaptive subdivision (6.1.2), plus the "near" test of Sec. 6.1.2.
 * operator.py  -- the Nystrom operators R~ and K~ (Sec. 6.1, eq. IEsum):
   dense smooth sums plus near-field corrections; the second-kind operator
-  I + R~ + (rank one) of Sec. 3 (null-space removal by adding int sigma).
+  I + R~ + (rank one) of Sec. 3 (null-space removal by adding int sigma),
+  or I + R~ when c != 0 (complex weights).
 * solve.py     -- restarted GMRES and dense LU, the solve of eq. IE and the
   representation u = K[sigma] (eq. representation) with the mean projection.
 
@@ -28,5 +31,7 @@ Readings of points the paper leaves open are listed in the design notes; the
 ones that change arithmetic are restated in the docstrings where they apply.
 Parity status: kernels, smooth sums, self rule, near rule, operators and the
 solve are each pinned by tests against closed forms or independent library
-quadrature (tests/test_oracle_*.py).
+quadrature (tests/test_oracle_*.py); the c != 0 kernels, operators and solve
+by tests/test_oracle_helmholtz.py (Funk-Hecke eigenvalues on the sphere, the
+Corollary's closed form, K0, finite differences, a manufactured solution).
 """

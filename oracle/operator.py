@@ -18,13 +18,19 @@ removed by adding int sigma (Sec. 3, following the one-dimensional update
 discussed there) is  A sigma = sigma + R~ sigma + (sum_j w_j sigma_j) 1.
 The scale of the rank-one term is not fixed by the paper; any non-zero
 multiple gives the same solution for mean-zero f.
+
+c != 0 (Sec. 4.2, Thm. second_kind): the kernels are those of eq. diff_param
+and eq. explicit_remainder with the Hankel Green's function (kernels.py), the
+weights and corrections are complex, and the second-kind operator is
+I + R~ with no rank-one term (eq. IE has no null space away from the
+eigenvalues of the surface operator).
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-from .kernels import INV_2PI, INV_PI
+from .kernels import INV_2PI, INV_PI, parametrix_c, remainder_c
 from .patch import PatchInterpolant
 from .quadrature import NEAR_FACTOR, near_weights, self_weights
 
@@ -33,13 +39,18 @@ class Discretization:
     """Surface nodes + coefficient, with the near-field structure of Sec. 6.1."""
 
     def __init__(self, nodes, normals, tangents, curvature, weights, a, grad_a,
-                 npatch, p, self_opts=None, near_tol=1e-13, jac=None):
+                 npatch, p, self_opts=None, near_tol=1e-13, jac=None, c=None):
         self.x = np.asarray(nodes, dtype=np.float64)
         self.n = np.asarray(normals, dtype=np.float64)
         self.H = np.asarray(curvature, dtype=np.float64)
         self.w = np.asarray(weights, dtype=np.float64)
         self.a = np.asarray(a, dtype=np.float64)
         self.g = np.asarray(grad_a, dtype=np.float64)
+        # c at the nodes (complex allowed); None or all zero is the c = 0 path
+        self.c = None
+        if c is not None and np.any(np.asarray(c) != 0):
+            self.c = np.asarray(c, dtype=np.complex128) * np.ones(len(self.a))
+        self.dtype = np.float64 if self.c is None else np.complex128
         self.npatch, self.p = int(npatch), int(p)
         self.N = self.npatch * self.p * self.p
         if jac is None:
@@ -80,10 +91,14 @@ class Discretization:
         out = []
         for P in self.near_patches(i):
             args = (self.x[i], self.n[i], self.H[i], self.a[i], self.g[i])
+            cq = {}
+            if self.c is not None:
+                sl = slice(P * pp, (P + 1) * pp)
+                cq = {"c_x": self.c[i], "q": (self.c[sl] / self.a[sl]).reshape(self.p, self.p)}
             if P == own:
-                WR, WK = self_weights(self.patches[P], u0, v0, *args, **self.self_opts)
+                WR, WK = self_weights(self.patches[P], u0, v0, *args, **self.self_opts, **cq)
             else:
-                WR, WK, _ = near_weights(self.patches[P], *args, tol=self.near_tol)
+                WR, WK, _ = near_weights(self.patches[P], *args, tol=self.near_tol, **cq)
             out.append((P, WR, WK))
         return out
 
@@ -103,11 +118,16 @@ class Discretization:
 
     # ---------------------------------------------------------------- kernels
     def kernel_R(self, i, k):
-        """R(x_i, x_k) (eq. explicit_remainder, c = 0); 0 where k == i."""
+        """R(x_i, x_k) (eq. explicit_remainder); 0 where k == i."""
         k = np.atleast_1d(k)
         r = self.x[i] - self.x[k]
         r2 = np.sum(r * r, axis=1)
         same = r2 == 0.0
+        if self.c is not None:
+            kk = np.where(same, (k + 1) % self.N, k)        # any other node; zeroed below
+            val = remainder_c(self.x[i], self.n[i], self.H[i], self.a[i], self.g[i],
+                              self.c[i], self.x[kk], self.a[kk], self.c[kk])
+            return np.where(same, 0.0, val)
         r2 = np.where(same, 1.0, r2)
         q = (r @ self.n[i]) / r2
         val = (self.a[i] * (INV_PI * q * q - self.H[i] * INV_PI * q)
@@ -120,6 +140,10 @@ class Discretization:
         r = self.x[i] - self.x[k]
         r2 = np.sum(r * r, axis=1)
         same = r2 == 0.0
+        if self.c is not None:
+            kk = np.where(same, (k + 1) % self.N, k)
+            val = parametrix_c(self.x[i], self.x[kk], self.a[kk], self.c[kk])
+            return np.where(same, 0.0, val)
         val = INV_2PI * 0.5 * np.log(np.where(same, 1.0, r2)) / self.a[k]
         return np.where(same, 0.0, val)
 
@@ -134,8 +158,8 @@ class Discretization:
     def smooth_apply(self, which, sigma, rows=None, chunk=256):
         """sum_{j != i} w_j F(x_i, x_j) sigma_j for the given target rows."""
         rows = np.arange(self.N) if rows is None else np.asarray(rows)
-        sigma = np.asarray(sigma, dtype=np.float64)
-        out = np.empty((len(rows),) + sigma.shape[1:])
+        sigma = np.asarray(sigma)
+        out = np.empty((len(rows),) + sigma.shape[1:], np.result_type(self.dtype, sigma))
         for s in range(0, len(rows), chunk):
             M = self.smooth_matrix(which, rows[s:s + chunk])
             out[s:s + chunk] = M @ sigma
@@ -158,8 +182,8 @@ class NearField:
         """sum over near k of C_{ik} sigma_k for the stored rows (or a subset)."""
         rows = self.rows if rows is None else [int(i) for i in rows]
         pp = self.disc.p ** 2
-        sigma = np.asarray(sigma, dtype=np.float64)
-        out = np.zeros((len(rows),) + sigma.shape[1:])
+        sigma = np.asarray(sigma)
+        out = np.zeros((len(rows),) + sigma.shape[1:], np.result_type(self.disc.dtype, sigma))
         idx = 1 if which == "R" else 2
         for r, i in enumerate(rows):
             for ent in self.corr[i]:
@@ -170,7 +194,7 @@ class NearField:
     def dense(self, which):
         """Dense correction matrix [N, N] (requires all rows)."""
         N, pp = self.disc.N, self.disc.p ** 2
-        C = np.zeros((N, N))
+        C = np.zeros((N, N), self.disc.dtype)
         idx = 1 if which == "R" else 2
         for i in self.rows:
             for ent in self.corr[i]:
@@ -195,10 +219,14 @@ def apply_K(disc: Discretization, near: NearField, sigma, rows=None):
 
 
 def second_kind_matrix(disc: Discretization, near: NearField):
-    """Dense A = I + R~ + 1 w^T (Sec. 3 null-space removal), for small N."""
+    """Dense A = I + R~ + 1 w^T (Sec. 3 null-space removal), for small N.
+
+    With c != 0 the matrix is I + R~ (eq. IE).
+    """
     A = disc.smooth_matrix("R") + near.dense("R")
     A[np.diag_indices(disc.N)] += 1.0
-    A += np.outer(np.ones(disc.N), disc.w)
+    if disc.c is None:
+        A += np.outer(np.ones(disc.N), disc.w)
     return A
 
 
@@ -219,7 +247,7 @@ def _pool_map(disc, rows, processes):
     import multiprocessing as mp
     J = np.concatenate([pt.J.ravel() for pt in disc.patches])
     args = (disc.x, disc.n, None, disc.H, disc.w, disc.a, disc.g, disc.npatch, disc.p)
-    kw = {"self_opts": disc.self_opts, "near_tol": disc.near_tol, "jac": J}
+    kw = {"self_opts": disc.self_opts, "near_tol": disc.near_tol, "jac": J, "c": disc.c}
     # group rows by local node index so each worker reuses its cached polar rules
     pp = disc.p * disc.p
     order = sorted(rows, key=lambda i: (i % pp, i))

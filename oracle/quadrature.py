@@ -40,7 +40,7 @@ from functools import lru_cache
 import numpy as np
 from numpy.polynomial.legendre import leggauss
 
-from .kernels import parametrix_scaled, remainder_scaled
+from .kernels import parametrix_scaled, remainder_scaled, scaled_pair_c, wavenumber
 from .patch import PatchInterpolant, lagrange_basis
 
 _T16, _W16 = leggauss(16)
@@ -134,7 +134,7 @@ def polar_rule(u0, v0, levels=16, h_max=0.5, max_width=np.pi / 24):
 
 
 def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
-                 levels=16, h_max=0.5, max_width=np.pi / 24):
+                 levels=16, h_max=0.5, max_width=np.pi / 24, c_x=None, q=None):
     """Singular-quadrature weights of the target's own patch (eq. radial_int).
 
     Returns (W_R, W_K), each [p*p] in node order a*p + b, with
@@ -150,6 +150,11 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
     two coincide; with an interpolated patch an O(delta) mismatch between the
     given normal and the patch would add a delta^2/r^2 term to R and make its
     polar integral diverge logarithmically.
+
+    c != 0: c_x is c at the target and q [p, p] holds c/a at the patch's
+    nodes; q is interpolated to each quadrature point and the kernels use
+    k = sqrt(q) there (a(y) K = g(r; k(y)), see kernels.py).  The weights are
+    then complex.
     """
     n_patch = patch.normal_at(u0, v0)
     u, v, w = polar_rule(u0, v0, levels, h_max, max_width)
@@ -160,14 +165,20 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
     D = (patch.X - x).reshape(p, 3 * p)
     r = -np.sum((Lu @ D).reshape(-1, p, 3) * Lv[:, :, None], axis=1)
     zero = np.zeros(3)
-    fr = w * J * remainder_scaled(zero, n_patch, H, a_x, g_x, -r)
-    fk = w * J * parametrix_scaled(zero, -r)
+    if q is None:
+        fr = w * J * remainder_scaled(zero, n_patch, H, a_x, g_x, -r)
+        fk = w * J * parametrix_scaled(zero, -r)
+    else:
+        k = wavenumber(np.sum((Lu @ q) * Lv, axis=1), 1.0)
+        aR, aK = scaled_pair_c(zero, n_patch, H, a_x, g_x, c_x, -r, k)
+        fr, fk = w * J * aR, w * J * aK
     WR = (Lu * fr[:, None]).T @ Lv
     WK = (Lu * fk[:, None]).T @ Lv
     return WR.ravel(), WK.ravel()
 
 
-def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1):
+def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1,
+                 c_x=None, q=None):
     """16 x 16 tensor Gauss rule for the weights over one sub-square."""
     uq, wu = gl_panel(u0, u1)
     vq, wv = gl_panel(v0, v1)
@@ -176,20 +187,28 @@ def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1):
     y = np.einsum("qa,abc,rb->qrc", Lu, patch.X, Lv)
     J = np.einsum("qa,ab,rb->qr", Lu, patch.J, Lv)
     ww = wu[:, None] * wv[None, :] * J
-    fr = ww * remainder_scaled(x, n, H, a_x, g_x, y)
-    fk = ww * parametrix_scaled(x, y)
+    if q is None:
+        fr = ww * remainder_scaled(x, n, H, a_x, g_x, y)
+        fk = ww * parametrix_scaled(x, y)
+    else:
+        k = wavenumber(np.einsum("qa,ab,rb->qr", Lu, q, Lv), 1.0)
+        aR, aK = scaled_pair_c(x, n, H, a_x, g_x, c_x, y, k)
+        fr, fk = ww * aR, ww * aK
     WR = np.einsum("qr,qa,rb->ab", fr, Lu, Lv)
     WK = np.einsum("qr,qa,rb->ab", fk, Lu, Lv)
     return np.stack([WR.ravel(), WK.ravel()])
 
 
-def near_weights(patch: PatchInterpolant, x, n, H, a_x, g_x, tol=1e-13, max_depth=16):
+def near_weights(patch: PatchInterpolant, x, n, H, a_x, g_x, tol=1e-13, max_depth=16,
+                 c_x=None, q=None):
     """Nearly singular weights of a near (non-self) patch by adaptive subdivision.
 
     Returns (W_R, W_K) as in self_weights.  Also returns the number of
     accepted squares via the attribute-free tuple (W_R, W_K, nsq).
+    c_x and q as in self_weights.
     """
-    root = _square_rule(patch, x, n, H, a_x, g_x, -1.0, 1.0, -1.0, 1.0)
+    cq = {"c_x": c_x, "q": q}
+    root = _square_rule(patch, x, n, H, a_x, g_x, -1.0, 1.0, -1.0, 1.0, **cq)
     scale = np.maximum(np.max(np.abs(root), axis=1), 1e-300)[:, None]
     count = [0]
 
@@ -197,7 +216,7 @@ def near_weights(patch: PatchInterpolant, x, n, H, a_x, g_x, tol=1e-13, max_dept
         u0, u1, v0, v1 = sq
         um, vm = 0.5 * (u0 + u1), 0.5 * (v0 + v1)
         kids = ((u0, um, v0, vm), (um, u1, v0, vm), (u0, um, vm, v1), (um, u1, vm, v1))
-        ests = [_square_rule(patch, x, n, H, a_x, g_x, *k) for k in kids]
+        ests = [_square_rule(patch, x, n, H, a_x, g_x, *k, **cq) for k in kids]
         total = ests[0] + ests[1] + ests[2] + ests[3]
         if depth >= max_depth or np.max(np.abs(total - est) / scale) <= tol:
             count[0] += 4

@@ -6,8 +6,13 @@ u = K[sigma].  The discrete system adds the rank-one term (sum_j w_j sigma_j) 1
 (Sec. 3 null-space removal) so that A = I + R~ + 1 w^T is invertible; the
 solution u is then projected to mean zero, u - (sum w u)/(sum w).
 
+c != 0 (Thm. second_kind): sigma + R[sigma] = f has no null space, so f is
+not projected, no rank-one term is added and u = K[sigma] is returned as is.
+
 Two solvers: dense LU (numpy.linalg.solve) and restarted GMRES (Saad and
-Schultz), the Krylov method the paper couples with its fast apply (Sec. 6).
+Schultz), the Krylov method the paper couples with its fast apply (Sec. 6);
+GMRES runs in complex arithmetic (Hermitian inner products, complex Givens
+rotations) when the operator or the right-hand side is complex.
 """
 
 from __future__ import annotations
@@ -23,7 +28,7 @@ def weighted_mean(v, w):
 
 def relative_l2(a, b, w):
     """Relative L2 error ||a - b|| / ||b|| in the surface (quadrature-weighted) norm."""
-    return float(np.sqrt(np.dot(w, (a - b) ** 2) / np.dot(w, b ** 2)))
+    return float(np.sqrt(np.dot(w, np.abs(a - b) ** 2) / np.dot(w, np.abs(b) ** 2)))
 
 
 def gmres(matvec, b, tol=1e-12, restart=50, maxit=2000, x0=None):
@@ -31,45 +36,52 @@ def gmres(matvec, b, tol=1e-12, restart=50, maxit=2000, x0=None):
 
     Stops when ||b - A x||_2 / ||b||_2 <= tol (the Arnoldi residual estimate,
     confirmed with a true residual at each restart).  Returns (x, iters, relres).
+    Real input stays real; complex b or x0 (or a complex matvec) runs in
+    complex arithmetic with the rotation [[conj(c), conj(s)], [-s, c]].
     """
-    b = np.asarray(b, dtype=np.float64)
+    b = np.asarray(b)
+    dt = np.result_type(b, np.float64, *(() if x0 is None else (np.asarray(x0),)))
+    b = b.astype(dt)
     n = b.shape[0]
-    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    x = np.zeros(n, dt) if x0 is None else np.array(x0, dtype=dt)
     bnorm = np.linalg.norm(b)
     if bnorm == 0.0:
         return x, 0, 0.0
     iters = 0
     while True:
         r = b - matvec(x)
+        if np.iscomplexobj(r) and dt != r.dtype:
+            dt = r.dtype
+            x = x.astype(dt)
         beta = np.linalg.norm(r)
         if beta / bnorm <= tol or iters >= maxit:
             return x, iters, beta / bnorm
         m = restart
-        V = np.zeros((m + 1, n))
-        Hs = np.zeros((m + 1, m))
-        cs, sn = np.zeros(m), np.zeros(m)
-        g = np.zeros(m + 1)
+        V = np.zeros((m + 1, n), dt)
+        Hs = np.zeros((m + 1, m), dt)
+        cs, sn = np.zeros(m, dt), np.zeros(m, dt)
+        g = np.zeros(m + 1, dt)
         g[0] = beta
         V[0] = r / beta
         k_used = 0
         for k in range(m):
             w = matvec(V[k])
             for j in range(k + 1):
-                Hs[j, k] = np.dot(V[j], w)
+                Hs[j, k] = np.vdot(V[j], w)
                 w = w - Hs[j, k] * V[j]
             Hs[k + 1, k] = np.linalg.norm(w)
-            if Hs[k + 1, k] > 0:
+            if Hs[k + 1, k] != 0:
                 V[k + 1] = w / Hs[k + 1, k]
             for j in range(k):
-                t = cs[j] * Hs[j, k] + sn[j] * Hs[j + 1, k]
+                t = np.conj(cs[j]) * Hs[j, k] + np.conj(sn[j]) * Hs[j + 1, k]
                 Hs[j + 1, k] = -sn[j] * Hs[j, k] + cs[j] * Hs[j + 1, k]
                 Hs[j, k] = t
-            den = np.hypot(Hs[k, k], Hs[k + 1, k])
+            den = np.hypot(abs(Hs[k, k]), abs(Hs[k + 1, k]))
             cs[k], sn[k] = Hs[k, k] / den, Hs[k + 1, k] / den
             Hs[k, k] = den
             Hs[k + 1, k] = 0.0
             g[k + 1] = -sn[k] * g[k]
-            g[k] = cs[k] * g[k]
+            g[k] = np.conj(cs[k]) * g[k]
             iters += 1
             k_used = k + 1
             if abs(g[k + 1]) / bnorm <= tol or iters >= maxit:
@@ -80,11 +92,14 @@ def gmres(matvec, b, tol=1e-12, restart=50, maxit=2000, x0=None):
 
 def solve(disc: Discretization, near: NearField, f, method="lu", tol=1e-12,
           project_rhs=True, return_sigma=False):
-    """u with div(a grad u) = f, u mean zero (Thm. second_kind, Sec. 3).
+    """u with div(a grad u) + c u = f (Thm. second_kind, Sec. 3).
 
-    f is projected to mean zero first when project_rhs (Thm. LBsolvable needs
-    a mean-zero right-hand side).
+    c = 0: u is mean zero, and f is projected to mean zero first when
+    project_rhs (Thm. LBsolvable needs a mean-zero right-hand side).
+    c != 0: A = I + R~ and u = K~ sigma, with f taken as given.
     """
+    if disc.c is not None:
+        return _solve_c(disc, near, f, method, tol, return_sigma)
     f = np.asarray(f, dtype=np.float64)
     w = disc.w
     if project_rhs:
@@ -100,6 +115,21 @@ def solve(disc: Discretization, near: NearField, f, method="lu", tol=1e-12,
         info = {"iters": it, "relres": rr}
     u = apply_K(disc, near, sigma)
     u = u - weighted_mean(u, w)
+    if return_sigma:
+        return u, sigma, info
+    return u
+
+
+def _solve_c(disc, near, f, method, tol, return_sigma):
+    """eq. IE and eq. representation for c != 0 (no null space, no projection)."""
+    f = np.asarray(f, dtype=np.complex128)
+    if method == "lu":
+        sigma = np.linalg.solve(second_kind_matrix(disc, near), f)
+        info = {"iters": 0}
+    else:
+        sigma, it, rr = gmres(lambda s: s + apply_R(disc, near, s), f, tol=tol)
+        info = {"iters": it, "relres": rr}
+    u = apply_K(disc, near, sigma)
     if return_sigma:
         return u, sigma, info
     return u
