@@ -336,6 +336,18 @@ pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int
 pm_status pm_selftest_fmm_classes(int* cls, int* sym, int* canon);
 
 /*
+ * Self-test of the library's planar Green's function for c != 0 (host code only,
+ * no device call; the same functions are compiled for the device).  Sec. 4.2,
+ * eq. diff_param: with q = c/a (real, non-zero) and g = a G the Green's function
+ * of Delta_2 + q, writes for each of the n radii r[i] > 0 (host, float64)
+ * out[6 i .. 6 i + 5] = Re g, Im g, Re g', Im g', Re g'', Im g'' (host, float64),
+ * g = -(i/4) H0(sqrt(q) r) for q > 0 and -K0(sqrt(-q) r) / (2 pi) for q < 0
+ * (unit source strength: 2 pi r g' -> 1 as r -> 0).  PM_ERR_INVALID_ARG for NULL
+ * arrays, n < 0, q zero or not finite, or a radius that is not finite and positive.
+ */
+pm_status pm_selftest_green(const double* r, int n, double q, double* out);
+
+/*
  * Serving: continuous batching of solve requests over many operators.
  *
  * An operator is a pm_surface whose coefficient is set.  pm_server_create starts

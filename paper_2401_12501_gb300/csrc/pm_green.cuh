@@ -1,0 +1,113 @@
+// Planar Green's function of a~ Delta_2 + c~ for c~ != 0 (Sec. 4.2, eq. diff_param),
+// in double precision, callable from host and device code.
+//
+// With q = c~/a~ real and non-zero, g(r) = a~ G(r; a~, c~) is the Green's function
+// of Delta_2 + q, (Delta_2 + q) g = delta:
+//
+//   q > 0, k = sqrt(q):       g = -(i/4) H0(k r),   H0 = J0 + i Y0 (outgoing);
+//   q < 0, kappa = sqrt(-q):  g = -K0(kappa r) / (2 pi)             (decaying).
+//
+// The sign is the one with unit source strength (2 pi r g'(r) -> 1 as r -> 0), so
+// g continues log(r)/(2 pi) of the c~ = 0 case; the paper prints the opposite sign,
+// which has source strength -1 under its own small-argument form of H0.
+// Radial derivatives, from H0' = -H1, H0'' = -H0 + H1/z, K0' = -K1,
+// K1' = -K0 - K1/z:
+//
+//   q > 0:  g'  = (i k / 4) H1(k r),
+//           g'' = (i k^2 / 4) (H0(k r) - H1(k r) / (k r));
+//   q < 0:  g'  =  kappa K1(kappa r) / (2 pi),
+//           g'' = -kappa^2 (K0(kappa r) + K1(kappa r) / (kappa r)) / (2 pi).
+//
+// J0, Y0, J1, Y1 are the math library's (j0, y0, j1, y1).  K0 and K1 are
+// evaluated here:
+//   x < 1:  the ascending series (Abramowitz & Stegun 9.6.13 and 9.6.11 with n = 1)
+//             K0(x) = -(ln(x/2) + gamma) I0(x) + sum_{j>=1} H_j t^j / (j!)^2,
+//             K1(x) = 1/x + ln(x/2) I1(x)
+//                     - (x/4) sum_{j>=0} (psi(j+1) + psi(j+2)) t^j / (j! (j+1)!),
+//           t = x^2/4, H_j the harmonic numbers, psi(j+1) = -gamma + H_j;
+//   x >= 1: the trapezoid rule on the integral representation
+//             e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2)) cosh(nu t) dt
+//           (A&S 9.6.24), whose integrand is analytic in the strip |Im t| < pi/2,
+//           so the rule converges geometrically: with step h the error is
+//           O(exp(x - pi^2/h)); h = min(1/4, pi^2/(40 + x)) keeps it below 1e-16
+//           relative, and the sum stops where the integrand is below e^-40.
+//           At most 26 terms for x up to 700.
+#pragma once
+
+#include <math.h>
+
+namespace pm_green {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEulerGamma = 0.57721566490153286061;
+
+// K0(x), K1(x) for x > 0.
+__host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
+{
+    if (x < 1.0) {
+        const double t = 0.25 * x * x;
+        double a0 = 1.0;        // t^j / (j!)^2
+        double a1 = 1.0;        // t^j / (j! (j+1)!)
+        double harm = 0.0;      // H_j
+        double i0 = 0.0, i1s = 0.0, s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < 24; ++j) {
+            const double psi1 = -kEulerGamma + harm;               // psi(j+1)
+            const double psi2 = psi1 + 1.0 / (j + 1);              // psi(j+2)
+            i0 += a0;
+            i1s += a1;
+            s0 += psi1 * a0;
+            s1 += (psi1 + psi2) * a1;
+            harm += 1.0 / (j + 1);
+            a0 *= t / ((j + 1.0) * (j + 1.0));
+            a1 *= t / ((j + 1.0) * (j + 2.0));
+        }
+        const double lg = log(0.5 * x);
+        *k0v = -lg * i0 + s0;
+        *k1v = 1.0 / x + lg * (0.5 * x * i1s) - 0.25 * x * s1;
+        return;
+    }
+    const double h = fmin(0.25, kPi * kPi / (40.0 + x));
+    const double tmax = acosh(1.0 + 40.0 / x);
+    const int n = (int)ceil(tmax / h);
+    double s0 = 0.5, s1 = 0.5;
+    for (int j = 1; j <= n; ++j) {
+        const double sh = sinh(0.5 * j * h);
+        const double e = exp(-2.0 * x * sh * sh);
+        s0 += e;
+        s1 += e * (1.0 + 2.0 * sh * sh);                           // cosh t
+    }
+    const double ex = exp(-x);
+    *k0v = h * s0 * ex;
+    *k1v = h * s1 * ex;
+}
+
+// (g, g', g'') at r > 0 for q = c~/a~ real and non-zero, as (re, im) pairs:
+// out[0..1] = g, out[2..3] = g', out[4..5] = g''.
+__host__ __device__ inline void green_scaled(double r, double q, double* out)
+{
+    if (q > 0.0) {
+        const double k = sqrt(q);
+        const double z = k * r;
+        const double J0 = j0(z), Y0 = y0(z), J1 = j1(z), Y1 = y1(z);
+        out[0] = 0.25 * Y0;                      // -(i/4)(J0 + i Y0)
+        out[1] = -0.25 * J0;
+        out[2] = -0.25 * k * Y1;                 // (i k/4)(J1 + i Y1)
+        out[3] = 0.25 * k * J1;
+        out[4] = -0.25 * k * k * (Y0 - Y1 / z);  // (i k^2/4)(H0 - H1/z)
+        out[5] = 0.25 * k * k * (J0 - J1 / z);
+    } else {
+        const double kap = sqrt(-q);
+        const double z = kap * r;
+        double K0, K1;
+        bessel_k01(z, &K0, &K1);
+        const double inv2pi = 0.5 / kPi;
+        out[0] = -K0 * inv2pi;
+        out[1] = 0.0;
+        out[2] = kap * K1 * inv2pi;
+        out[3] = 0.0;
+        out[4] = -kap * kap * (K0 + K1 / z) * inv2pi;
+        out[5] = 0.0;
+    }
+}
+
+}  // namespace pm_green

@@ -117,3 +117,32 @@ def test_fmm_offset_classes(lib):
                  for p in itertools.permutations(range(3))
                  for sg in itertools.product((1, -1), repeat=3)}
         assert m == orbit, c
+
+
+def test_green_function_c_nonzero(lib):
+    """The library's double-precision g, g', g'' for c != 0 (pm_green.cuh, host code,
+    no GPU) against the oracle's scipy evaluation: Helmholtz (q > 0, J/Y from the
+    math library) and modified Helmholtz (q < 0, the library's own K0/K1: ascending
+    series below 1, trapezoid rule on the integral representation above), across
+    both K0/K1 branches and far into the decay; invalid arguments are rejected."""
+    import numpy as np
+    from oracle.kernels import green_scaled
+    from paper_2401_12501_gb300._lib import ptr
+    r = np.concatenate([np.geomspace(1e-6, 60.0, 301), [0.5, 0.999, 1.0, 1.001, 2.0]])
+    for q in (4.0, 0.37, -4.0, -0.05, -30.0):
+        out = np.zeros((len(r), 6))
+        assert lib.pm_selftest_green(ptr(r), len(r), q, ptr(out)) == 0
+        k = np.sqrt(complex(q))
+        ref = green_scaled(r, k)
+        for m, (g, name) in enumerate(zip(ref, ("g", "g'", "g''"))):
+            got = out[:, 2 * m] + 1j * out[:, 2 * m + 1]
+            # relative to |g| where it is not near a zero of J or Y, absolute otherwise
+            scale = np.maximum(np.abs(g), 1e-3 * np.abs(g).max() if q > 0 else 0.0)
+            err = np.abs(got - g) / np.maximum(scale, 1e-300)
+            assert err.max() < 1e-12, (q, name, err.max(), r[err.argmax()])
+    out = np.zeros(6)
+    bad = [(np.array([1.0]), 0.0), (np.array([1.0]), np.inf), (np.array([0.0]), 1.0),
+           (np.array([-1.0]), -1.0), (np.array([np.nan]), 2.0)]
+    for rr, q in bad:
+        assert lib.pm_selftest_green(ptr(rr), 1, q, ptr(out)) == 1
+    assert lib.pm_selftest_green(None, 1, 1.0, ptr(out)) == 1
