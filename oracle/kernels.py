@@ -190,3 +190,35 @@ def remainder_scaled_c(x, n, H, a_x, g_x, c_x, y, k_y):
 def parametrix_scaled_c(x, y, k_y):
     """a(y) K(x, y) = g(|x - y|; k_y)."""
     return green_scaled(np.linalg.norm(x - y, axis=-1), k_y)[0]
+
+
+# ---------------------------------------------------------------------------
+# Advection, b != 0 (Sec. 4.3, Thm. advectionparametrix, eq. adv_remainder)
+#
+# The parametrix is unchanged and the remainder gains the advection term:
+#   R_b(x, y) = R(x, y) + b(x) . grad_Gamma K(x, y),
+# with grad_Gamma = grad - n(x) (n(x) . grad) acting on x and grad K = G'(r) r^.
+# (The theorem points at eq. bdd_remainder_helm for R; read as the general R of
+# eq. explicit_remainder, of which that equation is the constant-coefficient case.)
+# ---------------------------------------------------------------------------
+
+
+def advection_term(x, n, b_x, y, a_y, c_y=None):
+    """b(x) . grad_Gamma K(x, y) for sources y [..., 3] (c_y None: c = 0)."""
+    rv = x - y
+    r = np.linalg.norm(rv, axis=-1)
+    if c_y is None:
+        G1 = INV_2PI / (np.asarray(a_y) * r)
+    else:
+        G1 = green(r, a_y, c_y)[1]
+    bt = b_x - n * (b_x @ n)
+    return G1 * (rv @ bt) / r
+
+
+def advection_scaled(x, n, b_x, y, k_y=None):
+    """a(y) b(x) . grad_Gamma K(x, y) = g'(r; k_y) b_t . r^ (k_y None: c = 0)."""
+    rv = x - y
+    r = np.linalg.norm(rv, axis=-1)
+    g1 = INV_2PI / r if k_y is None else green_scaled(r, k_y)[1]
+    bt = b_x - n * (b_x @ n)
+    return g1 * (rv @ bt) / r

@@ -24,13 +24,17 @@ and eq. explicit_remainder with the Hankel Green's function (kernels.py), the
 weights and corrections are complex, and the second-kind operator is
 I + R~ with no rank-one term (eq. IE has no null space away from the
 eigenvalues of the surface operator).
+
+b != 0 (Sec. 4.3, eq. adv_remainder, eq. IE_adv): R is replaced by
+R_b = R + b . grad_Gamma K in the smooth sums and the quadratures; K and the
+second-kind structure are unchanged.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-from .kernels import INV_2PI, INV_PI, parametrix_c, remainder_c
+from .kernels import INV_2PI, INV_PI, advection_term, parametrix_c, remainder_c
 from .patch import PatchInterpolant
 from .quadrature import NEAR_FACTOR, near_weights, self_weights
 
@@ -39,7 +43,7 @@ class Discretization:
     """Surface nodes + coefficient, with the near-field structure of Sec. 6.1."""
 
     def __init__(self, nodes, normals, tangents, curvature, weights, a, grad_a,
-                 npatch, p, self_opts=None, near_tol=1e-13, jac=None, c=None):
+                 npatch, p, self_opts=None, near_tol=1e-13, jac=None, c=None, b=None):
         self.x = np.asarray(nodes, dtype=np.float64)
         self.n = np.asarray(normals, dtype=np.float64)
         self.H = np.asarray(curvature, dtype=np.float64)
@@ -51,6 +55,8 @@ class Discretization:
         if c is not None and np.any(np.asarray(c) != 0):
             self.c = np.asarray(c, dtype=np.complex128) * np.ones(len(self.a))
         self.dtype = np.float64 if self.c is None else np.complex128
+        # tangential advection field b at the nodes [N, 3], or None
+        self.b = None if b is None else np.asarray(b, dtype=np.float64)
         self.npatch, self.p = int(npatch), int(p)
         self.N = self.npatch * self.p * self.p
         if jac is None:
@@ -95,6 +101,8 @@ class Discretization:
             if self.c is not None:
                 sl = slice(P * pp, (P + 1) * pp)
                 cq = {"c_x": self.c[i], "q": (self.c[sl] / self.a[sl]).reshape(self.p, self.p)}
+            if self.b is not None:
+                cq["b_x"] = self.b[i]
             if P == own:
                 WR, WK = self_weights(self.patches[P], u0, v0, *args, **self.self_opts, **cq)
             else:
@@ -118,16 +126,29 @@ class Discretization:
 
     # ---------------------------------------------------------------- kernels
     def kernel_R(self, i, k):
-        """R(x_i, x_k) (eq. explicit_remainder); 0 where k == i."""
+        """R(x_i, x_k) (eq. explicit_remainder; R_b of eq. adv_remainder when b is set); 0 where k == i."""
         k = np.atleast_1d(k)
         r = self.x[i] - self.x[k]
         r2 = np.sum(r * r, axis=1)
         same = r2 == 0.0
-        if self.c is not None:
+        if self.c is not None or self.b is not None:
             kk = np.where(same, (k + 1) % self.N, k)        # any other node; zeroed below
-            val = remainder_c(self.x[i], self.n[i], self.H[i], self.a[i], self.g[i],
-                              self.c[i], self.x[kk], self.a[kk], self.c[kk])
+            if self.c is not None:
+                val = remainder_c(self.x[i], self.n[i], self.H[i], self.a[i], self.g[i],
+                                  self.c[i], self.x[kk], self.a[kk], self.c[kk])
+            else:
+                val = self._remainder_c0(i, kk)
+            if self.b is not None:
+                val = val + advection_term(self.x[i], self.n[i], self.b[i], self.x[kk],
+                                           self.a[kk], None if self.c is None else self.c[kk])
             return np.where(same, 0.0, val)
+        return self._remainder_c0(i, k)
+
+    def _remainder_c0(self, i, k):
+        """R(x_i, x_k) with c = 0 for k != i (the closed form of the module docstring)."""
+        r = self.x[i] - self.x[k]
+        r2 = np.sum(r * r, axis=1)
+        same = r2 == 0.0
         r2 = np.where(same, 1.0, r2)
         q = (r @ self.n[i]) / r2
         val = (self.a[i] * (INV_PI * q * q - self.H[i] * INV_PI * q)
@@ -247,7 +268,8 @@ def _pool_map(disc, rows, processes):
     import multiprocessing as mp
     J = np.concatenate([pt.J.ravel() for pt in disc.patches])
     args = (disc.x, disc.n, None, disc.H, disc.w, disc.a, disc.g, disc.npatch, disc.p)
-    kw = {"self_opts": disc.self_opts, "near_tol": disc.near_tol, "jac": J, "c": disc.c}
+    kw = {"self_opts": disc.self_opts, "near_tol": disc.near_tol, "jac": J, "c": disc.c,
+          "b": disc.b}
     # group rows by local node index so each worker reuses its cached polar rules
     pp = disc.p * disc.p
     order = sorted(rows, key=lambda i: (i % pp, i))

@@ -40,7 +40,8 @@ from functools import lru_cache
 import numpy as np
 from numpy.polynomial.legendre import leggauss
 
-from .kernels import parametrix_scaled, remainder_scaled, scaled_pair_c, wavenumber
+from .kernels import (advection_scaled, parametrix_scaled, remainder_scaled, scaled_pair_c,
+                      wavenumber)
 from .patch import PatchInterpolant, lagrange_basis
 
 _T16, _W16 = leggauss(16)
@@ -134,7 +135,7 @@ def polar_rule(u0, v0, levels=16, h_max=0.5, max_width=np.pi / 24):
 
 
 def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
-                 levels=16, h_max=0.5, max_width=np.pi / 24, c_x=None, q=None):
+                 levels=16, h_max=0.5, max_width=np.pi / 24, c_x=None, q=None, b_x=None):
     """Singular-quadrature weights of the target's own patch (eq. radial_int).
 
     Returns (W_R, W_K), each [p*p] in node order a*p + b, with
@@ -146,7 +147,7 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
     kernel keeps its precision as y~ -> x.
     The integration surface is the interpolated patch y~, so the normal in
     q = n.r/r^2 is that patch's own unit normal at the target (the argument
-    n is not used here).  With the exact parametrisation of Sec. 6.1.1 the
+    n serves only the advection term below).  With the exact parametrisation of Sec. 6.1.1 the
     two coincide; with an interpolated patch an O(delta) mismatch between the
     given normal and the patch would add a delta^2/r^2 term to R and make its
     polar integral diverge logarithmically.
@@ -155,6 +156,12 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
     nodes; q is interpolated to each quadrature point and the kernels use
     k = sqrt(q) there (a(y) K = g(r; k(y)), see kernels.py).  The weights are
     then complex.
+
+    b_x (b != 0, eq. adv_remainder): the advection field at the target; the
+    remainder weights then integrate a(y) R_b = a(y) R + a(y) b . grad_G K.
+    grad_G there is taken with the given normal n at the target (b is tangential
+    to it): the advection term is a first derivative at x, so unlike the
+    curvature terms it has no delta^2/r^2 sensitivity to the patch normal.
     """
     n_patch = patch.normal_at(u0, v0)
     u, v, w = polar_rule(u0, v0, levels, h_max, max_width)
@@ -165,6 +172,7 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
     D = (patch.X - x).reshape(p, 3 * p)
     r = -np.sum((Lu @ D).reshape(-1, p, 3) * Lv[:, :, None], axis=1)
     zero = np.zeros(3)
+    k = None
     if q is None:
         fr = w * J * remainder_scaled(zero, n_patch, H, a_x, g_x, -r)
         fk = w * J * parametrix_scaled(zero, -r)
@@ -172,13 +180,15 @@ def self_weights(patch: PatchInterpolant, u0, v0, x, n, H, a_x, g_x,
         k = wavenumber(np.sum((Lu @ q) * Lv, axis=1), 1.0)
         aR, aK = scaled_pair_c(zero, n_patch, H, a_x, g_x, c_x, -r, k)
         fr, fk = w * J * aR, w * J * aK
+    if b_x is not None:
+        fr = fr + w * J * advection_scaled(zero, n, b_x, -r, k)
     WR = (Lu * fr[:, None]).T @ Lv
     WK = (Lu * fk[:, None]).T @ Lv
     return WR.ravel(), WK.ravel()
 
 
 def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1,
-                 c_x=None, q=None):
+                 c_x=None, q=None, b_x=None):
     """16 x 16 tensor Gauss rule for the weights over one sub-square."""
     uq, wu = gl_panel(u0, u1)
     vq, wv = gl_panel(v0, v1)
@@ -187,6 +197,7 @@ def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1,
     y = np.einsum("qa,abc,rb->qrc", Lu, patch.X, Lv)
     J = np.einsum("qa,ab,rb->qr", Lu, patch.J, Lv)
     ww = wu[:, None] * wv[None, :] * J
+    k = None
     if q is None:
         fr = ww * remainder_scaled(x, n, H, a_x, g_x, y)
         fk = ww * parametrix_scaled(x, y)
@@ -194,20 +205,22 @@ def _square_rule(patch: PatchInterpolant, x, n, H, a_x, g_x, u0, u1, v0, v1,
         k = wavenumber(np.einsum("qa,ab,rb->qr", Lu, q, Lv), 1.0)
         aR, aK = scaled_pair_c(x, n, H, a_x, g_x, c_x, y, k)
         fr, fk = ww * aR, ww * aK
+    if b_x is not None:
+        fr = fr + ww * advection_scaled(x, n, b_x, y, k)
     WR = np.einsum("qr,qa,rb->ab", fr, Lu, Lv)
     WK = np.einsum("qr,qa,rb->ab", fk, Lu, Lv)
     return np.stack([WR.ravel(), WK.ravel()])
 
 
 def near_weights(patch: PatchInterpolant, x, n, H, a_x, g_x, tol=1e-13, max_depth=16,
-                 c_x=None, q=None):
+                 c_x=None, q=None, b_x=None):
     """Nearly singular weights of a near (non-self) patch by adaptive subdivision.
 
     Returns (W_R, W_K) as in self_weights.  Also returns the number of
     accepted squares via the attribute-free tuple (W_R, W_K, nsq).
-    c_x and q as in self_weights.
+    c_x, q and b_x as in self_weights.
     """
-    cq = {"c_x": c_x, "q": q}
+    cq = {"c_x": c_x, "q": q, "b_x": b_x}
     root = _square_rule(patch, x, n, H, a_x, g_x, -1.0, 1.0, -1.0, 1.0, **cq)
     scale = np.maximum(np.max(np.abs(root), axis=1), 1e-300)[:, None]
     count = [0]

@@ -209,3 +209,38 @@ def test_zero_right_hand_side(ctx):
     u, info, sig = s.solve(np.zeros(wl.N), tol=1e-10, return_sigma=True)
     assert np.all(u == 0.0) and np.all(sig == 0.0)
     assert info[0].iterations == 0 and info[0].residual == 0.0
+
+
+def test_advection_through_the_gradient_input(ctx):
+    """b != 0 with c = 0 (Sec. 4.3, eq. adv_remainder): for tangential b, R_b is R
+    with grad_G a replaced by grad_G a + b, so the library evaluates R~_b when
+    pm_surface_set_coeff is given that sum.  Checked against the oracle's literal
+    R + b . grad_G K on the 864-node ellipsoid with its variable a and the
+    divergence-free b = n x grad_G psi, psi = x y + z/2: applies (float64 1e-11,
+    float32 2e-6 relative L2) and solves (1e-8), as for b = 0."""
+    import paper_2401_12501_gb300 as pm
+    from oracle.operator import Discretization, NearField, apply_R
+    from oracle.solve import solve
+    wl = make_workload("ellipsoid_small")
+    x, n = wl.surface.nodes, wl.surface.normals
+    gpsi = np.stack([x[:, 1], x[:, 0], np.full(len(x), 0.5)], 1)
+    gpsi -= n * np.sum(gpsi * n, 1, keepdims=True)
+    b = np.cross(n, gpsi)
+    d = Discretization.from_workload(wl, b=b)
+    nf = NearField(d, processes=oracle_processes())
+    s = pm.Surface.from_fixture(ctx, wl.surface)
+    try:
+        s.set_coeff(wl.coeff.a, wl.coeff.grad_a + b)
+        w = wl.surface.weights
+        sigma = np.random.default_rng(6).standard_normal(wl.N) + 1.0
+        ref = apply_R(d, nf, sigma)
+        for prec, tol in (("fp64", 1e-11), ("fp32", 2e-6)):
+            assert rel_l2(s.apply_R(sigma, prec), ref, w) < tol, prec
+        uo, so, _ = solve(d, nf, wl.f, return_sigma=True)
+        for prec in ("fp64", "fp32"):
+            u, info, sig = s.solve(wl.f, tol=1e-11, prec=prec, return_sigma=True)
+            assert info[0].residual <= 1e-11
+            assert rel_l2(u, uo, w) < 1e-8, prec
+            assert rel_l2(sig, so, w) < 1e-8, prec
+    finally:
+        s.close()
