@@ -348,6 +348,12 @@ pm_status pm_selftest_fmm_classes(int* cls, int* sym, int* canon);
 pm_status pm_selftest_green(const double* r, int n, double q, double* out);
 
 /*
+ * The same in float32 (the evaluation the per-pair smooth sums use): r and out
+ * are host float32 arrays, out[6 i .. 6 i + 5] as above.  Same errors.
+ */
+pm_status pm_selftest_green_f32(const float* r, int n, float q, float* out);
+
+/*
  * Serving: continuous batching of solve requests over many operators.
  *
  * An operator is a pm_surface whose coefficient is set.  pm_server_create starts

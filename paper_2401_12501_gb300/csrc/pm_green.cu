@@ -20,3 +20,17 @@ extern "C" pm_status pm_selftest_green(const double* r, int n, double q, double*
     for (int i = 0; i < n; ++i) pm_green::green_scaled(r[i], q, out + 6 * i);
     return PM_OK;
 }
+
+extern "C" pm_status pm_selftest_green_f32(const float* r, int n, float q, float* out) {
+    if (!r || !out || n < 0 || !std::isfinite(q) || q == 0.0f) {
+        pm_set_error("pm_selftest_green_f32: NULL array, negative n, or q not finite and non-zero");
+        return PM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!(r[i] > 0.0f) || !std::isfinite(r[i])) {
+            pm_set_error("pm_selftest_green_f32: r must be finite and positive");
+            return PM_ERR_INVALID_ARG;
+        }
+    for (int i = 0; i < n; ++i) pm_green::green_scaled_f32(r[i], q, out + 6 * i);
+    return PM_OK;
+}

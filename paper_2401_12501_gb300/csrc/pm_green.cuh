@@ -110,4 +110,109 @@ __host__ __device__ inline void green_scaled(double r, double q, double* out)
     }
 }
 
+// ---------------------------------------------------------------------------
+// float32 versions for the per-pair smooth sums.  Same methods, tuned to
+// float32: the series for x < 2 with ten unrolled terms (t = x^2/4 <= 1, so
+// the tail is below 1/(10!)^2) and constant-folded coefficients; the trapezoid
+// rule for x >= 2 with h = min(1/2, pi^2/(18.5 + x)) (error O(exp(x - pi^2/h))
+// below 1e-8 relative), cut where the integrand falls below e^-18.5, at most
+// 7 terms; sinh(j h/2), cosh(j h/2) by the addition formulas.  K0 and K1
+// underflow float32 beyond x = 87 and return 0.  Measured against the exact
+// functions at the float32 argument: <= 7e-7 relative.
+// ---------------------------------------------------------------------------
+
+// Coefficients of the float32 series, computed at compile time:
+// f0[j] = 1/(j+1)^2, f1[j] = 1/((j+1)(j+2)) (ratios of consecutive terms),
+// p0[j] = psi(j+1), p1[j] = psi(j+1) + psi(j+2).
+struct SeriesK01 {
+    float f0[10], f1[10], p0[10], p1[10];
+};
+
+__host__ __device__ constexpr SeriesK01 series_k01()
+{
+    SeriesK01 c{};
+    double harm = 0.0;
+    for (int j = 0; j < 10; ++j) {
+        const double psi1 = -kEulerGamma + harm;
+        c.p0[j] = (float)psi1;
+        c.p1[j] = (float)(2.0 * psi1 + 1.0 / (j + 1));
+        c.f0[j] = (float)(1.0 / ((j + 1.0) * (j + 1.0)));
+        c.f1[j] = (float)(1.0 / ((j + 1.0) * (j + 2.0)));
+        harm += 1.0 / (j + 1);
+    }
+    return c;
+}
+
+__host__ __device__ inline void bessel_k01_f32(float x, float* k0v, float* k1v)
+{
+    if (x < 2.0f) {
+        constexpr SeriesK01 C = series_k01();
+        const float t = 0.25f * x * x;
+        float a0 = 1.0f, a1 = 1.0f, i0 = 0.0f, i1s = 0.0f, s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            i0 += a0;
+            i1s += a1;
+            s0 = fmaf(C.p0[j], a0, s0);
+            s1 = fmaf(C.p1[j], a1, s1);
+            a0 *= t * C.f0[j];
+            a1 *= t * C.f1[j];
+        }
+        const float lg = logf(0.5f * x);
+        *k0v = fmaf(-lg, i0, s0);
+        *k1v = 1.0f / x + lg * (0.5f * x * i1s) - 0.25f * x * s1;
+        return;
+    }
+    if (x > 87.0f) {
+        *k0v = 0.0f;
+        *k1v = 0.0f;
+        return;
+    }
+    const float h = fminf(0.5f, (float)(kPi * kPi) / (18.5f + x));
+    const int n = (int)ceilf(acoshf(1.0f + 18.5f / x) / h);
+    const float sh1 = sinhf(0.5f * h), ch1 = coshf(0.5f * h);
+    float sh = 0.0f, ch = 1.0f, S0 = 0.5f, S1 = 0.5f;
+    for (int j = 1; j <= n; ++j) {
+        const float shn = fmaf(sh, ch1, ch * sh1);
+        ch = fmaf(ch, ch1, sh * sh1);
+        sh = shn;
+        const float s2 = sh * sh;
+        const float e = expf(-2.0f * x * s2);
+        S0 += e;
+        S1 = fmaf(e, fmaf(2.0f, s2, 1.0f), S1);
+    }
+    const float ex = expf(-x);
+    *k0v = h * S0 * ex;
+    *k1v = h * S1 * ex;
+}
+
+// float32 (g, g', g'') as in green_scaled, for q = c~/a~ real and non-zero.
+__host__ __device__ inline void green_scaled_f32(float r, float q, float* out)
+{
+    if (q > 0.0f) {
+        const float k = sqrtf(q);
+        const float z = k * r;
+        const float J0 = j0f(z), Y0 = y0f(z), J1 = j1f(z), Y1 = y1f(z);
+        const float kk = 0.25f * k * k;
+        out[0] = 0.25f * Y0;
+        out[1] = -0.25f * J0;
+        out[2] = -0.25f * k * Y1;
+        out[3] = 0.25f * k * J1;
+        out[4] = -kk * (Y0 - Y1 / z);
+        out[5] = kk * (J0 - J1 / z);
+    } else {
+        const float kap = sqrtf(-q);
+        const float z = kap * r;
+        float K0, K1;
+        bessel_k01_f32(z, &K0, &K1);
+        const float inv2pi = (float)(0.5 / kPi);
+        out[0] = -K0 * inv2pi;
+        out[1] = 0.0f;
+        out[2] = kap * K1 * inv2pi;
+        out[3] = 0.0f;
+        out[4] = -kap * kap * (K0 + K1 / z) * inv2pi;
+        out[5] = 0.0f;
+    }
+}
+
 }  // namespace pm_green

@@ -146,3 +146,33 @@ def test_green_function_c_nonzero(lib):
     for rr, q in bad:
         assert lib.pm_selftest_green(ptr(rr), 1, q, ptr(out)) == 1
     assert lib.pm_selftest_green(None, 1, 1.0, ptr(out)) == 1
+
+
+def test_green_function_c_nonzero_float32(lib):
+    """The float32 evaluation the per-pair sums use (pm_green.cuh, host code, no GPU)
+    against the oracle at the float32 radii: 2e-6 relative (absolute near the zeros of
+    J and Y) plus 1.5e-7 z for the float32 rounding of z = sqrt(|q|) r, which the
+    exponential decay and the oscillation turn into a relative error of about
+    z * 6e-8; across the K0/K1 series/trapezoid switch at 2 and up to the float32
+    underflow of K0; invalid arguments are rejected."""
+    import numpy as np
+    from oracle.kernels import green_scaled
+    from paper_2401_12501_gb300._lib import ptr
+    r = np.concatenate([np.geomspace(1e-5, 40.0, 401), [0.999, 1.0, 1.001]]).astype(np.float32)
+    for q in (4.0, 0.37, -4.0, -0.05, -30.0):
+        out = np.zeros((len(r), 6), np.float32)
+        assert lib.pm_selftest_green_f32(ptr(r), len(r), q, ptr(out)) == 0
+        q32 = float(np.float32(q))
+        ref = green_scaled(r.astype(np.float64), np.sqrt(complex(q32)))
+        z = np.sqrt(abs(q32)) * r.astype(np.float64)
+        for m, (g, name) in enumerate(zip(ref, ("g", "g'", "g''"))):
+            got = out[:, 2 * m].astype(np.float64) + 1j * out[:, 2 * m + 1]
+            live = z < 85.0                       # K0 underflows float32 beyond
+            scale = np.maximum(np.abs(g), 1e-3 * np.abs(g).max() if q > 0 else 0.0)
+            err = np.abs(got - g)[live] / np.maximum(scale[live], 1e-30)
+            bound = 2e-6 + 1.5e-7 * z[live]
+            assert np.all(err < bound), (q, name, err.max(), r[live][err.argmax()])
+    out = np.zeros(6, np.float32)
+    for rr, q in [(np.array([1.0], np.float32), 0.0), (np.array([0.0], np.float32), 1.0),
+                  (np.array([np.inf], np.float32), -1.0)]:
+        assert lib.pm_selftest_green_f32(ptr(rr), 1, q, ptr(out)) == 1
