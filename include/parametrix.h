@@ -354,6 +354,20 @@ pm_status pm_selftest_green(const double* r, int n, double q, double* out);
 pm_status pm_selftest_green_f32(const float* r, int n, float q, float* out);
 
 /*
+ * Self-test of the float32 per-pair arithmetic of the c != 0 smooth sums (host code
+ * only): for real c != 0, out[4 i .. 4 i + 3] = Re, Im of
+ * sum_{j != i} a_j R(x_i, x_j) s_j and of sum_{j != i} a_j K(x_i, x_j) s_j
+ * (eq. explicit_remainder with its c terms, eq. diff_param), each pair in float32,
+ * summed in float64.  Host arrays: x, n, gb [N*3] (gb = grad_G a, plus b for
+ * advection), H, a, c [N] float32; s [N*2] float32 complex (s_j = w_j sigma_j / a_j);
+ * out [N*4] float64.  O(N^2).  PM_ERR_INVALID_ARG for NULL arrays, N < 0, a <= 0, or
+ * c zero or not finite.
+ */
+pm_status pm_selftest_smooth_c_f32(int N, const float* x, const float* n, const float* H,
+                                   const float* a, const float* gb, const float* c,
+                                   const float* s, double* out);
+
+/*
  * Serving: continuous batching of solve requests over many operators.
  *
  * An operator is a pm_surface whose coefficient is set.  pm_server_create starts

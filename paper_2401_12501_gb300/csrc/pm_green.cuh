@@ -215,4 +215,34 @@ __host__ __device__ inline void green_scaled_f32(float r, float q, float* out)
     }
 }
 
+// One source's float32 contribution to the smooth sums of R and K for real c != 0
+// (eq. explicit_remainder with a(y) G = g(r; k_y), k_y^2 = q = c(y)/a(y)):
+//   a(y) R = gb . r^ g' - a(x) (g'' - g'/r) (n.r)^2/r^2 - 2 a(x) H(x) (n.r^) g'
+//            + (c(x) - a(x) q) g,        a(y) K = g,
+// gb = grad_G a(x) (+ b(x) for advection).  The source weight s = w sigma / a(y)
+// is complex; acc[0..3] += Re, Im of a(y) R s and of a(y) K s.
+__host__ __device__ inline void pair_rk_c_f32(float rx, float ry, float rz, float nx, float ny,
+                                              float nz, float H, float a, float gbx, float gby,
+                                              float gbz, float c, float q, float s_re, float s_im,
+                                              float* acc)
+{
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float r = sqrtf(r2);
+    const float inv_r = 1.0f / r;
+    float g[6];
+    green_scaled_f32(r, q, g);
+    const float nr = fmaf(nx, rx, fmaf(ny, ry, nz * rz)) * inv_r;       // n . r^
+    const float gr = fmaf(gbx, rx, fmaf(gby, ry, gbz * rz)) * inv_r;    // gb . r^
+    const float t2 = a * nr * nr;                                        // a (n.r)^2 / r^2
+    const float t1 = fmaf(-2.0f * a * H, nr, gr);                        // gb.r^ - 2 a H n.r^
+    const float t0 = fmaf(-a, q, c);                                     // c(x) - a(x) q
+    // a(y) R = t1 g' - t2 (g'' - g'/r) + t0 g, componentwise in (re, im)
+    const float R_re = fmaf(t1, g[2], fmaf(-t2, fmaf(-g[2], inv_r, g[4]), t0 * g[0]));
+    const float R_im = fmaf(t1, g[3], fmaf(-t2, fmaf(-g[3], inv_r, g[5]), t0 * g[1]));
+    acc[0] += R_re * s_re - R_im * s_im;
+    acc[1] += R_re * s_im + R_im * s_re;
+    acc[2] += g[0] * s_re - g[1] * s_im;
+    acc[3] += g[0] * s_im + g[1] * s_re;
+}
+
 }  // namespace pm_green

@@ -176,3 +176,40 @@ def test_green_function_c_nonzero_float32(lib):
     for rr, q in [(np.array([1.0], np.float32), 0.0), (np.array([0.0], np.float32), 1.0),
                   (np.array([np.inf], np.float32), -1.0)]:
         assert lib.pm_selftest_green_f32(ptr(rr), 1, q, ptr(out)) == 1
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_smooth_sum_c_nonzero_pair_arithmetic(lib, sign):
+    """The float32 per-pair arithmetic of the c != 0 smooth sums (host loop, no GPU)
+    against the oracle's smooth sums Sum_{j != i} w_j R(x_i, x_j) sigma_j and the same
+    for K, on the 384-node ellipsoid with variable a, a tangential advection field
+    added to grad_G a, variable real c of one sign (Helmholtz or modified Helmholtz)
+    and a complex sigma: 1e-6 relative L2 (measured 3.5e-7 for R, 2.6e-7 for K)."""
+    import numpy as np
+    from oracle.operator import Discretization
+    from paper_2401_12501_gb300._lib import ptr
+    from workloads import cubed_sphere
+    from workloads.coefficients import ellipsoid_coefficient
+    s = cubed_sphere(1, 8, axes=(1.0, 1.5, 2.0))
+    co = ellipsoid_coefficient(s)
+    N = len(s.weights)
+    c = sign * (2.0 + np.exp(s.nodes[:, 0] / 2))
+    b = np.cross(s.normals, np.array([0.3, -0.2, 1.0]))
+    d = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights,
+                       co.a, co.grad_a, s.npatch, s.p, c=c, b=b)
+    rng = np.random.default_rng(8)
+    sigma = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    refR = d.smooth_apply("R", sigma)
+    refK = d.smooth_apply("K", sigma)
+    f32 = lambda v: np.ascontiguousarray(v, dtype=np.float32)
+    sw = s.weights * sigma / co.a
+    sc = f32(np.stack([sw.real, sw.imag], 1))
+    out = np.zeros((N, 4))
+    # the library reads these during the call: keep every buffer referenced
+    bufs = [f32(v) for v in (s.nodes, s.normals, s.curvature, co.a, co.grad_a + b, c)]
+    assert lib.pm_selftest_smooth_c_f32(N, *[ptr(v) for v in bufs], ptr(sc), ptr(out)) == 0
+    gotR = out[:, 0] + 1j * out[:, 1]
+    gotK = out[:, 2] + 1j * out[:, 3]
+    rel = lambda u, v: np.linalg.norm(u - v) / np.linalg.norm(v)
+    assert rel(gotR, refR) < 1e-6, rel(gotR, refR)
+    assert rel(gotK, refK) < 1e-6, rel(gotK, refK)
