@@ -72,10 +72,14 @@ def parametrix(x, y, a_y):
 # reproduces the Corollary's constant-coefficient formula (eq.
 # bdd_remainder_helm) exactly.
 #
-# Branch (Sec. 4.2 wedge assumption): k is the root of k^2 = c~/a~ with
-# Im k >= 0 (and k > 0 when c~/a~ > 0), so g decays for c~/a~ < 0, where
-# g(r; i kappa) = -K0(kappa r) / (2 pi) is real, and is outgoing for
-# c~/a~ > 0.
+# Branch (Sec. 4.2: the cut of the square root lies outside the wedge that
+# holds c): k = |q|^(1/2) exp(i arg(q)/2) with arg(q) in (-pi/2, 3pi/2], q = c~/a~,
+# i.e. the cut runs along the negative imaginary axis of q.  On the real axis
+# k > 0 for q > 0 (outgoing) and k = i sqrt(-q) for q < 0, where g(r; i kappa)
+# = -K0(kappa r) / (2 pi) decays and is real; k is continuous across both real
+# half-axes, so a field c whose imaginary part changes sign (the paper's
+# 4 (1 + 0.2 y + 0.2 i sin x)) or whose real part passes through zero (2x) has
+# a continuous kernel.  (The root with Im k >= 0 would put the cut on q > 0.)
 #
 # Radial derivatives (H0' = -H1, H0'' = -H0 + H1/z):
 #   g'(r)  = (i k / 4) H1(k r)
@@ -87,12 +91,12 @@ from scipy.special import hankel1 as _hankel1
 
 
 def wavenumber(c, a):
-    """k with k^2 = c/a and Im k >= 0 (k >= 0 when c/a is real and positive)."""
+    """k with k^2 = c/a on the branch arg(k) = arg(c/a)/2, arg(c/a) in (-pi/2, 3pi/2]."""
     q = np.asarray(c, dtype=np.complex128) / np.asarray(a, dtype=np.float64)
-    k = np.sqrt(q)
-    # numpy's principal root already has Re k >= 0; flip to the Im k >= 0 root
-    # (only differs for q on the negative real axis with a -0.0 imaginary part)
-    return np.where(k.imag < 0, -k, k)
+    k = np.sqrt(q)                      # principal: arg(q) in (-pi, pi]
+    # arg(q) in (-pi, -pi/2] (a -0.0 imaginary part counts as negative) moves to
+    # (pi, 3pi/2], which negates the root
+    return np.where(np.signbit(q.imag) & (q.real <= 0), -k, k)
 
 
 def green_scaled(r, k):
