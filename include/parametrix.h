@@ -224,6 +224,12 @@ pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);
  *                 interpolant of a (eq. gradg)
  * Combines the stored quadrature weights into the near-field corrections of
  * R and K; no quadrature is recomputed.
+ * Advection (Sec. 4.3, eq. adv_remainder): for div_G(a grad_G u) + b . grad_G u = f
+ * with a tangential field b, pass grad_a = grad_G a + b.  The advection term
+ * b . grad_G K of the remainder has the form of its grad_G a term, so every apply
+ * and solve then uses R_b.  For b with non-zero surface divergence the range is no
+ * longer the mean-zero functions: solve with PM_SOLVE_PROJECT_RHS (the rank-one
+ * term still selects the solution; u is returned with zero mean).
  */
 pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const double* grad_a);
 
