@@ -374,6 +374,22 @@ pm_status pm_selftest_smooth_c_f32(int N, const float* x, const float* n, const 
                                    const float* s, double* out);
 
 /*
+ * Device float32 smooth sums for real c != 0 (Sec. 6.1.3 smooth rule with the
+ * kernels of eq. explicit_remainder and eq. diff_param): the same quantities as
+ * pm_selftest_smooth_c_f32, from DEVICE arrays in the same layouts, each target's
+ * sum compensated (TwoSum per 128 sources) and written to out [N*4] (device,
+ * float64) on the given stream (NULL: the default stream).  Requires a > 0 and
+ * c != 0 at every node (c = 0 is the library's c = 0 path) and distinct node
+ * positions.  Asynchronous; PM_ERR_INVALID_ARG for NULL arrays or N outside
+ * 1..2^26, PM_ERR_CUDA if the launch fails.  Its per-pair arithmetic is the
+ * host-tested pair function above; the kernel itself has not yet been run on a
+ * GPU.
+ */
+pm_status pm_smooth_c_f32(int N, const float* x, const float* n, const float* H,
+                          const float* a, const float* gb, const float* c, const float* s,
+                          double* out, void* stream);
+
+/*
  * Serving: continuous batching of solve requests over many operators.
  *
  * An operator is a pm_surface whose coefficient is set.  pm_server_create starts

@@ -37,7 +37,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_surface_set_knobs",
            "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info", "pm_surface_clone",
            "pm_selftest_fmm_classes", "pm_selftest_green",
-           "pm_selftest_green_f32", "pm_selftest_smooth_c_f32"]
+           "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
 
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_selftest_green.argtypes = [P, C.c_int, C.c_double, P]
     lib.pm_selftest_green_f32.argtypes = [P, C.c_int, C.c_float, P]
     lib.pm_selftest_smooth_c_f32.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
+    lib.pm_smooth_c_f32.argtypes = [C.c_int, P, P, P, P, P, P, P, P, P]
     lib.pm_surface_destroy.restype = None
     lib.pm_surface_tune.argtypes = [P, C.c_int, C.c_int]
     lib.pm_surface_set_knobs.argtypes = [P, C.POINTER(PmKnobs)]
