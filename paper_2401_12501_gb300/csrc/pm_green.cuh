@@ -44,6 +44,10 @@ constexpr double kEulerGamma = 0.57721566490153286061;
 // K0(x), K1(x) for x > 0.
 __host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
 {
+    if (x != x) {                       // NaN passes through (no term count from it)
+        *k0v = *k1v = x;
+        return;
+    }
     if (x < 1.0) {
         const double t = 0.25 * x * x;
         double a0 = 1.0;        // t^j / (j!)^2
@@ -68,7 +72,7 @@ __host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
     }
     const double h = fmin(0.25, kPi * kPi / (40.0 + x));
     const double tmax = acosh(1.0 + 40.0 / x);
-    const int n = (int)ceil(tmax / h);
+    const int n = (int)fmin(64.0, ceil(tmax / h));          // <= 26 for x <= 700
     double s0 = 0.5, s1 = 0.5;
     for (int j = 1; j <= n; ++j) {
         const double sh = sinh(0.5 * j * h);
@@ -163,13 +167,12 @@ __host__ __device__ inline void bessel_k01_f32(float x, float* k0v, float* k1v)
         *k1v = 1.0f / x + lg * (0.5f * x * i1s) - 0.25f * x * s1;
         return;
     }
-    if (x > 87.0f) {
-        *k0v = 0.0f;
-        *k1v = 0.0f;
+    if (!(x <= 87.0f)) {                // underflow, or NaN passed through
+        *k0v = *k1v = (x > 87.0f) ? 0.0f : x;
         return;
     }
     const float h = fminf(0.5f, (float)(kPi * kPi) / (18.5f + x));
-    const int n = (int)ceilf(acoshf(1.0f + 18.5f / x) / h);
+    const int n = (int)fminf(16.0f, ceilf(acoshf(1.0f + 18.5f / x) / h));   // <= 7 here
     const float sh1 = sinhf(0.5f * h), ch1 = coshf(0.5f * h);
     float sh = 0.0f, ch = 1.0f, S0 = 0.5f, S1 = 0.5f;
     for (int j = 1; j <= n; ++j) {
