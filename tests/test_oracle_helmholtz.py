@@ -13,6 +13,7 @@ What the paper and the mathematics fix independently of the code:
   finite differences of K in ambient space (eq. diff_remainder) on a torus
   with variable a and variable complex c.
 * c -> 0 recovers the c = 0 remainder of Thm. parametrixLB.
+* Dilation: Gamma -> s Gamma with c is Gamma with s^2 c (K unchanged, R times s^-2).
 * Unit sphere, constant a and c (Sec. 7.1: adding c shifts the eigenvalues
   -a l(l+1) of the surface operator): K and R are zonal, so by the
   Funk-Hecke formula Y_l^m is an eigenfunction of both, with eigenvalues
@@ -144,6 +145,32 @@ def test_remainder_equals_surface_operator_of_parametrix_c():
         assert abs(fd - val) < 1e-5 * max(1.0, abs(val)), (fd, val)
         assert abs(sc / ay[0] - val) < 1e-13 * max(1.0, abs(val))
         checked += 1
+
+
+def test_dilation_scales_c():
+    """Dilating Gamma by s turns a Delta + c into a Delta + s^2 c on the original
+    surface: K_{s Gamma, c}(s x, s y) = K_{Gamma, s^2 c}(x, y) (no log shift when
+    c != 0) and s^2 R_{s Gamma, c}(s x, s y) = R_{Gamma, s^2 c}(x, y), with H and
+    grad_G a scaling as 1/s.  A term of eq. explicit_remainder with a wrong power
+    of k or r breaks it."""
+    rng = np.random.default_rng(13)
+    for sc in (0.5, 3.0):
+        for _ in range(5):
+            th, ph = rng.uniform(0, 2 * np.pi, 2)
+            x, n, H, _, _, _ = _torus_point(2.0, 0.7, th, ph)
+            y = np.array([_torus_point(2.0, 0.7, *rng.uniform(0, 2 * np.pi, 2))[0]
+                          for _ in range(4)])
+            ay = 1.0 + rng.random(4)
+            cy = rng.standard_normal(4) + 0.5j * rng.standard_normal(4)
+            cx = 1.3 - 0.4j
+            gG = rng.standard_normal(3)
+            gG -= n * (gG @ n)
+            K1 = parametrix_c(sc * x, sc * y, ay, cy)
+            K2 = parametrix_c(x, y, ay, sc ** 2 * cy)
+            assert np.abs(K1 - K2).max() < 1e-13 * np.abs(K2).max()
+            R1 = remainder_c(sc * x, n, H / sc, 1.7, gG / sc, cx, sc * y, ay, cy)
+            R2 = remainder_c(x, n, H, 1.7, gG, sc ** 2 * cx, y, ay, sc ** 2 * cy)
+            assert np.abs(sc ** 2 * R1 - R2).max() < 1e-12 * np.abs(R2).max()
 
 
 def test_remainder_tends_to_the_c_zero_remainder():
