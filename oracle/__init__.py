@@ -24,6 +24,10 @@ surface PDEs"):
   dense smooth sums plus near-field corrections; the second-kind operator
   I + R~ + (rank one) of Sec. 3 (null-space removal by adding int sigma),
   or I + R~ when c != 0 (complex weights).
+* triangle.py  -- triangle patches (Sec. 6.1): the Koornwinder basis on the
+  simplex and order-p Vioreanu-Rokhlin nodes and weights, generated from the
+  published method (the paper's precomputed table is not available); not
+  yet used by the operators, which work on quad patches.
 * solve.py     -- restarted GMRES and dense LU, the solve of eq. IE and the
   representation u = K[sigma] (eq. representation) with the mean projection.
 
