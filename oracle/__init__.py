@@ -26,8 +26,10 @@ surface PDEs"):
   or I + R~ when c != 0 (complex weights).
 * triangle.py  -- triangle patches (Sec. 6.1): the Koornwinder basis on the
   simplex and order-p Vioreanu-Rokhlin nodes and weights, generated from the
-  published method (the paper's precomputed table is not available); not
-  yet used by the operators, which work on quad patches.
+  published method (the paper's precomputed table is not available).
+* triangle_operator.py -- the Nystrom operators on curved triangle patches
+  given by their parameterisations (Sec. 6.1): polar self rule over the
+  simplex, adaptive subdivision near rule, same correction form as operator.py.
 * solve.py     -- restarted GMRES and dense LU, the solve of eq. IE and the
   representation u = K[sigma] (eq. representation) with the mean projection.
 

@@ -202,7 +202,7 @@ class NearField:
     def apply(self, which, sigma, rows=None):
         """sum over near k of C_{ik} sigma_k for the stored rows (or a subset)."""
         rows = self.rows if rows is None else [int(i) for i in rows]
-        pp = self.disc.p ** 2
+        pp = getattr(self.disc, "pp", self.disc.p ** 2)     # nodes per patch
         sigma = np.asarray(sigma)
         out = np.zeros((len(rows),) + sigma.shape[1:], np.result_type(self.disc.dtype, sigma))
         idx = 1 if which == "R" else 2
@@ -214,7 +214,7 @@ class NearField:
 
     def dense(self, which):
         """Dense correction matrix [N, N] (requires all rows)."""
-        N, pp = self.disc.N, self.disc.p ** 2
+        N, pp = self.disc.N, getattr(self.disc, "pp", self.disc.p ** 2)
         C = np.zeros((N, N), self.disc.dtype)
         idx = 1 if which == "R" else 2
         for i in self.rows:

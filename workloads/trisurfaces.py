@@ -1,0 +1,56 @@
+"""Closed test surfaces as curved triangle patches over the simplex T0.
+
+``icosphere(level)``: the unit sphere as the radial projection of the
+icosahedron's faces, each split ``4**level`` ways by edge midpoints.  Patch P
+is the map y_P(u, v) = q / |q|, q = A + u (B - A) + v (C - A) of T0 onto the
+sphere (A, B, C the flat triangle's vertices, ordered so that the normal
+y_u x y_v points outward), with the closed-form derivatives
+y_u = (e1 - y (y . e1)) / |q|, e1 = B - A, and likewise y_v with e2 = C - A.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def _icosahedron():
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    V = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+                  [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    return [V[list(f)] for f in F]
+
+
+def _split(tri):
+    a, b, c = tri
+    ab, bc, ca = 0.5 * (a + b), 0.5 * (b + c), 0.5 * (c + a)
+    return [np.array(t) for t in ((a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca))]
+
+
+def icosphere(level: int = 0):
+    """(npatch, ymap) with ymap(P, u, v) -> (y, y_u, y_v), each [len(u), 3]."""
+    tris = _icosahedron()
+    for _ in range(level):
+        tris = [t for tri in tris for t in _split(tri)]
+    flat = []
+    for a, b, c in tris:
+        if np.dot(np.cross(b - a, c - a), a + b + c) < 0:
+            b, c = c, b
+        flat.append((a, b - a, c - a))
+
+    def ymap(P, u, v):
+        a, e1, e2 = flat[P]
+        u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+        v = np.atleast_1d(np.asarray(v, dtype=np.float64))
+        q = a + u[:, None] * e1 + v[:, None] * e2
+        rq = np.linalg.norm(q, axis=1, keepdims=True)
+        y = q / rq
+        yu = (e1 - y * (y @ e1)[:, None]) / rq
+        yv = (e2 - y * (y @ e2)[:, None]) / rq
+        return y, yu, yv
+
+    return len(flat), ymap
