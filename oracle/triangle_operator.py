@@ -119,6 +119,8 @@ class TriDiscretization:
                  near_tol=1e-13):
         self.ymap, self.npatch, self.p = ymap, int(npatch), int(p)
         self.dtype = np.float64
+        self.c = None                       # c = 0, b = 0 on triangles (solve.py reads these)
+        self.b = None
         self.tu, self.tv, self.tw = vioreanu_rokhlin(self.p)
         self.pp = len(self.tu)
         self.N = self.npatch * self.pp
@@ -232,8 +234,65 @@ class TriDiscretization:
             out.append((P, CR, CK))
         return out
 
+    def smooth_matrix(self, which, rows=None):
+        """Dense smooth-rule matrix [len(rows), N]: w_j F(x_i, x_j), zero diagonal."""
+        rows = np.arange(self.N) if rows is None else np.asarray(rows)
+        fn = self.kernel_R if which == "R" else self.kernel_K
+        allk = np.arange(self.N)
+        return np.stack([self.w * fn(i, allk) for i in rows])
+
     def smooth_apply(self, which, sigma, rows=None):
         rows = np.arange(self.N) if rows is None else np.asarray(rows)
         fn = self.kernel_R if which == "R" else self.kernel_K
         allk = np.arange(self.N)
         return np.array([np.dot(self.w * fn(i, allk), sigma) for i in rows])
+
+
+# -------------------------------------------------------------------- process pool
+_WORKER_TRI = None
+
+
+def _init_tri_worker(disc):
+    global _WORKER_TRI
+    _WORKER_TRI = disc
+
+
+def _tri_rows(rows):
+    return [_WORKER_TRI.row_corrections(i) for i in rows]
+
+
+def tri_near_field(disc: TriDiscretization, rows=None, processes=None):
+    """NearField (operator.py) of a triangle discretisation, rows built by spawned workers."""
+    import multiprocessing as mp
+    import os
+    from .operator import NearField
+    rows = np.arange(disc.N) if rows is None else np.asarray(rows)
+    nf = NearField.__new__(NearField)
+    nf.disc = disc
+    nf.rows = [int(i) for i in rows]
+    if not processes or processes <= 1:
+        nf.corr = {i: disc.row_corrections(i) for i in nf.rows}
+        return nf
+    order = sorted(nf.rows, key=lambda i: (i % disc.pp, i))   # polar rules reused per worker
+    nch = processes * 4
+    size = (len(order) + nch - 1) // nch
+    chunks = [order[k:k + size] for k in range(0, len(order), size)]
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(processes, initializer=_init_tri_worker,
+                                          initargs=(disc,)) as pool:
+            res = pool.map(_tri_rows, chunks)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    nf.corr = {}
+    for ch, rr in zip(chunks, res):
+        for i, r in zip(ch, rr):
+            nf.corr[i] = r
+    return nf

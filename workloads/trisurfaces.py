@@ -31,6 +31,24 @@ def _split(tri):
     return [np.array(t) for t in ((a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca))]
 
 
+class SphereTriangles:
+    """Patch maps of the projected triangles (picklable, for worker processes)."""
+
+    def __init__(self, flat):
+        self.flat = flat
+
+    def __call__(self, P, u, v):
+        a, e1, e2 = self.flat[P]
+        u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+        v = np.atleast_1d(np.asarray(v, dtype=np.float64))
+        q = a + u[:, None] * e1 + v[:, None] * e2
+        rq = np.linalg.norm(q, axis=1, keepdims=True)
+        y = q / rq
+        yu = (e1 - y * (y @ e1)[:, None]) / rq
+        yv = (e2 - y * (y @ e2)[:, None]) / rq
+        return y, yu, yv
+
+
 def icosphere(level: int = 0):
     """(npatch, ymap) with ymap(P, u, v) -> (y, y_u, y_v), each [len(u), 3]."""
     tris = _icosahedron()
@@ -41,16 +59,4 @@ def icosphere(level: int = 0):
         if np.dot(np.cross(b - a, c - a), a + b + c) < 0:
             b, c = c, b
         flat.append((a, b - a, c - a))
-
-    def ymap(P, u, v):
-        a, e1, e2 = flat[P]
-        u = np.atleast_1d(np.asarray(u, dtype=np.float64))
-        v = np.atleast_1d(np.asarray(v, dtype=np.float64))
-        q = a + u[:, None] * e1 + v[:, None] * e2
-        rq = np.linalg.norm(q, axis=1, keepdims=True)
-        y = q / rq
-        yu = (e1 - y * (y @ e1)[:, None]) / rq
-        yv = (e2 - y * (y @ e2)[:, None]) / rq
-        return y, yu, yv
-
-    return len(flat), ymap
+    return len(flat), SphereTriangles(flat)
