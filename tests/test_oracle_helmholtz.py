@@ -14,6 +14,8 @@ What the paper and the mathematics fix independently of the code:
   with variable a and variable complex c.
 * c -> 0 recovers the c = 0 remainder of Thm. parametrixLB.
 * Dilation: Gamma -> s Gamma with c is Gamma with s^2 c (K unchanged, R times s^-2).
+* Sec. 4.2's theorem on the zero set of c: K and R grow like log c(x') as c(x') -> 0
+  (K - log(k)/(2 pi a) and R - c(x) log(k)/(2 pi a) converge).
 * Unit sphere, constant a and c (Sec. 7.1: adding c shifts the eigenvalues
   -a l(l+1) of the surface operator): K and R are zonal, so by the
   Funk-Hecke formula Y_l^m is an eigenfunction of both, with eigenvalues
@@ -145,6 +147,30 @@ def test_remainder_equals_surface_operator_of_parametrix_c():
         assert abs(fd - val) < 1e-5 * max(1.0, abs(val)), (fd, val)
         assert abs(sc / ay[0] - val) < 1e-13 * max(1.0, abs(val))
         checked += 1
+
+
+def test_kernels_grow_like_log_c_as_c_vanishes():
+    """Sec. 4.2 theorem on Gamma_c = {c = 0}: K and R are O(log c(x')) as c(x') -> 0.
+    With k = sqrt(c/a), K = -(i/4a) H0(k r) = (log k + log r - log 2 + gamma)/(2 pi a)
+    - i/(4a) + o(1), so K - log(k)/(2 pi a) tends to that constant; R's c-term
+    (c(x) - a(x) c(y)/a(y)) G tends to c(x) G, so R - c(x) log(k)/(2 pi a) converges
+    (measured: R itself falls by c(x) ln(10)/(2 pi a) per factor 100 in c)."""
+    x = np.array([0.3, -0.2, 0.9])
+    n = np.array([0.0, 0.0, 1.0])
+    y = np.array([[1.1, 0.4, 0.2]])
+    a, cx = 1.7, 0.3
+    r = np.linalg.norm(x - y)
+    lim = (np.log(r) - np.log(2.0) + np.euler_gamma) / (2 * np.pi * a) - 0.25j / a
+    shifted = []
+    for c in (1e-4, 1e-6, 1e-8, 1e-10):
+        k = np.sqrt(c / a)
+        K = parametrix_c(x, y, np.array([a]), np.array([c]))[0]
+        assert abs(K - np.log(k) / (2 * np.pi * a) - lim) < 10 * c, c
+        R = remainder_c(x, n, 0.5, a, np.zeros(3), cx, y, np.array([a]), np.array([c]))[0]
+        shifted.append(R - cx * np.log(k) / (2 * np.pi * a))
+    steps = np.abs(np.diff(shifted))
+    assert steps[-1] < 1e-6 and steps[0] > steps[-1]
+    assert abs(shifted[0] - shifted[-1]) < 1e-3 * abs(shifted[-1])
 
 
 def test_dilation_scales_c():
