@@ -30,6 +30,9 @@ surface PDEs"):
 * triangle_operator.py -- the Nystrom operators on curved triangle patches
   given by their parameterisations (Sec. 6.1): polar self rule over the
   simplex, adaptive subdivision near rule, same correction form as operator.py.
+* edge.py      -- the edge potentials of the boundary-value systems (Sec. 5) on
+  planar curves with the trapezoid rule: single layer, its normal derivative
+  K'_gamma on the curve, double layer N_gamma; their limits from inside Gamma.
 * solve.py     -- restarted GMRES and dense LU, the solve of eq. IE and the
   representation u = K[sigma] (eq. representation) with the mean projection.
 
