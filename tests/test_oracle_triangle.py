@@ -10,6 +10,9 @@
   for p = 2..8.
 * The interpolant c = U sigma of Sec. 6.1.2 reproduces the node values and
   converges spectrally for a smooth function.
+* The operators on curved triangles (unit sphere as projected icosahedron
+  triangles): R~ 1 = -1, R~ Y = 0, K~ Y = -Y/(l(l+1)) at sampled rows, and a
+  variable-coefficient manufactured solve.
 """
 
 from math import factorial
