@@ -5,7 +5,7 @@ Sum_{j != i} w_j R(x_i, x_j) sigma_j and Sum_{j != i} w_j K(x_i, x_j) sigma_j
 (eq. explicit_remainder with its c terms, eq. diff_param) and (2) the library's
 host loop over the same per-pair function (pm_selftest_smooth_c_f32).  384-node
 ellipsoid, variable a, an advection field added to grad_G a, variable real c of
-either sign, complex sigma.  Tolerances: 1e-5 relative L2 against the oracle (the
+either sign (k r < 5.7 for every pair), complex sigma.  Tolerances: 1e-5 relative L2 against the oracle (the
 float32 bound), 5e-6 against the host loop (the device and host math libraries
 differ in the last bits of j0f/y0f/j1f/y1f and expf/logf).
 """
@@ -29,7 +29,10 @@ def test_smooth_c_f32_matches_oracle(sign):
     s = cubed_sphere(1, 8, axes=(1.0, 1.5, 2.0))
     co = ellipsoid_coefficient(s)
     N = len(s.weights)
-    c = sign * (2.0 + np.exp(s.nodes[:, 0] / 2))
+    # |c| scaled so that k r < 5.7 for every pair: the device's j0f / y0f are then in
+    # their few-ulp range (they are bounded in absolute terms beyond 8); the modified
+    # Helmholtz case still spans both branches of the K0/K1 evaluation (switch at 2)
+    c = sign * 0.5 * (2.0 + np.exp(s.nodes[:, 0] / 2))
     b = np.cross(s.normals, np.array([0.3, -0.2, 1.0]))
     d = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights,
                        co.a, co.grad_a, s.npatch, s.p, c=c, b=b)
