@@ -115,3 +115,21 @@ def ellipse(n: int, A: float, B: float) -> PlanarCurve:
     return PlanarCurve(lambda t: np.stack([A * np.cos(t), B * np.sin(t)], 1),
                        lambda t: np.stack([-A * np.sin(t), B * np.cos(t)], 1),
                        lambda t: np.stack([-A * np.cos(t), -B * np.sin(t)], 1), n)
+
+
+def neumann_edge_solve(curve: PlanarCurve, f_gamma, a=1.0):
+    """mu of eq. NeuBVPsystem's second row on a flat Gamma with f = 0 (so sigma = 0):
+    -mu/(2a) + K'_gamma[mu] = f_gamma.  That operator has a one-dimensional null
+    space and its range is orthogonal to the constants, so the data must satisfy
+    int f_gamma ds = 0 (the Neumann compatibility condition) and the rank-one term
+    (int mu ds) 1 added here selects the solution with int mu ds = 0; u = K_gamma[mu]
+    is then determined up to the constant the Neumann problem leaves free.
+    Dense Nystrom matrix, LU."""
+    n = len(curve.t)
+    A = np.empty((n, n))
+    eye = np.eye(n)
+    for j in range(n):
+        A[:, j] = k_prime_on_curve(curve, eye[j], a)
+    A -= eye / (2 * a)
+    A += np.outer(np.ones(n), curve.w)
+    return np.linalg.solve(A, f_gamma)
