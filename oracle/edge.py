@@ -133,3 +133,17 @@ def neumann_edge_solve(curve: PlanarCurve, f_gamma, a=1.0):
     A -= eye / (2 * a)
     A += np.outer(np.ones(n), curve.w)
     return np.linalg.solve(A, f_gamma)
+
+
+def dirichlet_edge_solve(curve: PlanarCurve, f_gamma, a=1.0, jump_sign=1.0):
+    """mu of the Dirichlet trace row on a flat Gamma with f = 0 (so sigma = 0):
+    jump_sign * mu/(2a) + N_gamma[mu](on gamma) = f_gamma, u = N_gamma[mu] inside.
+    jump_sign = +1 is reading of the module docstring; -1 is the sign printed in
+    Sec. 5.3 (kept as a parameter so that the pin can show it fails)."""
+    n = len(curve.t)
+    A = np.empty((n, n))
+    eye = np.eye(n)
+    for j in range(n):
+        A[:, j] = double_layer_on_curve(curve, eye[j], a)
+    A += jump_sign * eye / (2 * a)
+    return np.linalg.solve(A, f_gamma)
