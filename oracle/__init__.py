@@ -42,5 +42,8 @@ Parity status: kernels, smooth sums, self rule, near rule, operators and the
 solve are each pinned by tests against closed forms or independent library
 quadrature (tests/test_oracle_*.py); the c != 0 kernels, operators and solve
 by tests/test_oracle_helmholtz.py (Funk-Hecke eigenvalues on the sphere, the
-Corollary's closed form, K0, finite differences, a manufactured solution).
+Corollary's closed form, K0, finite differences, manufactured solutions); the
+advection term by tests/test_oracle_advection.py; the triangle rule and
+operators by tests/test_oracle_triangle.py; the edge operators by
+tests/test_oracle_edge.py (plane potential theory, Gauss's lemma).
 """
