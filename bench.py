@@ -618,12 +618,13 @@ def run_fmm(args, dev):
     m2l_pairs = st["m2l_box_pairs"]
     res = {"workload": "torus_98304", "N": wl.N, "near_build_s": round(t_build, 3),
            "m2l": "one operator GEMM per offset class (16 classes of the 316 offsets under the "
-                  "cube's signed axis permutations) on the bfloat16 tensor cores with float32 "
-                  "accumulation: float32 operands split in three bfloat16 parts, the six "
-                  "products of order <= 2^-16 as one GEMM over K = 3072",
+                  "cube's signed axis permutations), all classes in one launch of the library's "
+                  "tcgen05 kernel (TMEM accumulators, TMA-staged tiles) with float32 "
+                  "accumulation: float32 operands scaled by powers of two and split in two "
+                  "float16 parts, the three products of order <= 2^-11 as one GEMM over K = 1536",
            "m2l_gemm_flops_per_apply": 2.0 * 9 * 512 * 512 * m2l_pairs,
-           "m2l_bf16_flops_executed_per_apply": 6 * 2.0 * 9 * 512 * 512 * m2l_pairs,
-           "m2l_operator_bytes_per_apply": 16 * 9 * 512 * 3072 * 2,
+           "m2l_f16_flops_executed_per_apply": 3 * 2.0 * 9 * 512 * 512 * m2l_pairs,
+           "m2l_operator_bytes_per_apply": 16 * 9 * 512 * 1536 * 2,
            "solve_tol_1e-8": {p: {"ms": round(v[0] * 1e3, 2), "iterations": v[2].iterations,
                                   "refinements": v[2].refinements,
                                   "residual": v[2].residual} for p, v in solves.items()},
@@ -762,6 +763,25 @@ def run_served(args, dev):
 
 
 
+def run_micro_tc_gemm(args):
+    """The M2L product of the 98,304-node torus at its full size on the library's
+    tcgen05 GEMM alone: A = the remainder operators' 9 x 512 rows, K = 3 x 512
+    (two float16 parts, three products), 11,392 columns (the torus's V-list box
+    pairs at depth 3), seeded normal operands."""
+    import numpy as np
+    import paper_2401_12501_gb300 as pm
+    rows, K, ncols = 4608, 1536, 11392
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((rows, K)).astype(np.float16).view(np.uint16)
+    B = rng.standard_normal((ncols, K)).astype(np.float16).view(np.uint16)
+    ctx = pm.Context(0)
+    _, ms = ctx.selftest_tc_gemm(A, B, reps=max(1, args.steps))
+    ctx.close()
+    fl = 2.0 * rows * K * ncols
+    print(json.dumps({"micro": "tc_gemm", "shape": [rows, ncols, K], "dtype": "f16",
+                      "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -787,8 +807,13 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
+    ap.add_argument("--micro", choices=["tc_gemm"], default=None,
+                    help="time one kernel alone instead of the solve step (profiling aid)")
     args = ap.parse_args()
 
+    if args.micro == "tc_gemm":
+        run_micro_tc_gemm(args)
+        return
     if args.oracle_leg:
         rate, desc = oracle_rate(args.workload, args.oracle_seconds)
         print(json.dumps({"value": rate, "sample": desc}))

@@ -106,10 +106,12 @@ typedef struct {
                                recomputing f - A sigma in residual_prec; 1 (default) or 0 */
     int fmm_tensor_m2l;     /* PM_PREC_FMM far field: 1 = M2L as one operator GEMM per offset
                                class (16 classes of the 316 V-list offsets under the cube's
-                               signed axis permutations) on the bfloat16 tensor cores, float32
-                               operands split in three bfloat16 parts, float32 accumulation;
-                               operators ~0.5 GB per context, built once (default);
-                               0 = M2L evaluated directly on the float32 pipe            */
+                               signed axis permutations) on the float16 tensor cores (the
+                               library's own tcgen05 kernel), float32 operands scaled by
+                               powers of two and split in two float16 parts (three
+                               products), float32 accumulation; operators ~0.25 GB per
+                               context, built once (default); 0 = M2L evaluated directly
+                               on the float32 pipe                                        */
 } pm_opts;
 
 void pm_default_opts(pm_opts* opts);
@@ -340,6 +342,25 @@ pm_status pm_selftest_fflog(pm_surface* s, const float* xh, const float* xl, int
  * PM_ERR_INVALID_ARG for NULL arrays.
  */
 pm_status pm_selftest_fmm_classes(int* cls, int* sym, int* canon);
+
+/*
+ * Self-test of the tensor-core GEMM that carries the FMM's M2L (Sec. 6.2: the
+ * far field as one dense operator product per offset class), on sm_103a
+ * tcgen05 MMAs with float32 accumulators in tensor memory and TMA-staged
+ * operand tiles:  C[j * rows + r] = sum_k A[r * K + k] * B[j * K + k]  for
+ * r < rows, j < ncols.  Host arrays: A [rows * K] and B [ncols * K] hold
+ * float16 (bf16 = 0) or bfloat16 (bf16 = 1) bit patterns, K-major; C
+ * [ncols * rows] float32 receives the product (column j's rows contiguous).
+ * The library allocates and frees the device copies.  reps > 0 runs the
+ * product reps more times and writes the mean device time of one launch (ms)
+ * to *ms.  PM_ERR_INVALID_ARG unless rows is a positive multiple of 128, K of
+ * 64 and ncols >= 1 (or for NULL arrays, or reps > 0 with ms NULL);
+ * PM_ERR_TIMEOUT if a bounded wait inside the kernel ran out (the kernel then
+ * returns early and C is not valid); PM_ERR_CUDA for a failed CUDA call.
+ */
+pm_status pm_selftest_tc_gemm(pm_ctx* ctx, const unsigned short* A, const unsigned short* B,
+                              float* C, int rows, int K, int ncols, int bf16, int reps,
+                              double* ms);
 
 /*
  * Self-test of the library's planar Green's function for c != 0 (host code only,

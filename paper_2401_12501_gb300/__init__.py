@@ -48,6 +48,23 @@ class Context:
         check(_lib.lib().pm_ctx_info(self.handle, buf, len(buf), C.byref(sms)), "pm_ctx_info")
         return buf.value.decode(errors="replace"), sms.value
 
+    def selftest_tc_gemm(self, A, B, bf16: bool = False, reps: int = 0):
+        """C = A B^T on the library's tcgen05 GEMM (pm_selftest_tc_gemm).  A [rows, K]
+        and B [ncols, K] are uint16 arrays of float16 (or bfloat16) bit patterns;
+        returns C as float32 [ncols, rows] and, with reps > 0, the mean ms per launch."""
+        A = np.ascontiguousarray(A, dtype=np.uint16)
+        B = np.ascontiguousarray(B, dtype=np.uint16)
+        rows, K = A.shape
+        ncols = B.shape[0]
+        if B.shape[1] != K:
+            raise ValueError("A and B need the same K")
+        out = np.empty((ncols, rows), dtype=np.float32)
+        ms = C.c_double(0.0)
+        check(_lib.lib().pm_selftest_tc_gemm(self.handle, ptr(A), ptr(B), ptr(out), rows, K,
+                                             ncols, int(bool(bf16)), int(reps), C.byref(ms)),
+              "pm_selftest_tc_gemm")
+        return out, ms.value
+
     def close(self):
         if self.handle:
             _lib.lib().pm_ctx_destroy(self.handle)

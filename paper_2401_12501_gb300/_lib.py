@@ -36,7 +36,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
            "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_surface_set_knobs",
            "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info", "pm_surface_clone",
-           "pm_selftest_fmm_classes", "pm_selftest_green",
+           "pm_selftest_fmm_classes", "pm_selftest_tc_gemm", "pm_selftest_green",
            "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64) = range(6)
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_destroy.argtypes = [P]
     lib.pm_surface_clone.argtypes = [P, C.POINTER(P)]
     lib.pm_selftest_fmm_classes.argtypes = [P, P, P]
+    lib.pm_selftest_tc_gemm.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.POINTER(C.c_double)]
     lib.pm_selftest_green.argtypes = [P, C.c_int, C.c_double, P]
     lib.pm_selftest_green_f32.argtypes = [P, C.c_int, C.c_float, P]
     lib.pm_selftest_smooth_c_f32.argtypes = [C.c_int, P, P, P, P, P, P, P, P]

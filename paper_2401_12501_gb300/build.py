@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libparametrix.so")
-SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_direct.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tune.cu"]
+SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_direct.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tcgemm.cu", "pm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -57,7 +57,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
     if jobs or force or _newer(LIB, objs):
-        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs, "-lcublas"])
+        run([nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs])
     return LIB
 
 

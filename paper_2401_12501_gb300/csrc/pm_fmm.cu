@@ -29,8 +29,6 @@
 // (CSR) is added by the regular correction kernel.
 #include "pm_internal.cuh"
 
-#include <cublas_v2.h>
-
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -492,28 +490,22 @@ k_fmm_l2p(DevTree t, const float4* __restrict__ tgt, const float* __restrict__ L
 // of B; one GEMM per class forms C = A_c B; each target box sums its V-list
 // columns of C, mapped back through g and scaled for its level.
 //
-// The GEMM runs on the bfloat16 tensor cores with float32 accumulation: each
-// float32 value x is split as x0 + x1 + x2 (xk = bf16 of the remainder after
-// the previous parts, 24 significand bits in all), and the six products
-// a_i b_j with i + j <= 2 are summed as one GEMM over K = 6 x 512 with
-// A' = [a2 a1 a0 a1 a0 a0] (split once, when the operators are built) and
-// B' = [b0; b1; b2; b0; b1; b0] (split by the gather): smallest products first,
-// so that they are accumulated before the large ones.  The dropped products
-// are below 2^-23 of |a||b|.
+// The GEMM runs on the float16 tensor cores (tcgen05, pm_tcgemm.cu) with
+// float32 accumulation.  Each float32 operand x, scaled by a power of two into
+// the upper float16 range, is split as x0 + x1 (x0 = fp16(x), x1 = fp16(x - x0):
+// 22 significand bits, |x - x0 - x1| <= 2^-22 |x|), and the three products
+// a1 b0 + a0 b1 + a0 b0 are one GEMM over K = 3 x 512 with A' = [a1 a0 a0] and
+// B' = [b0; b1; b0]: the small products first, so that they are accumulated
+// before the large one.  The dropped product a1 b1 is below 2^-22 |a||b|.
+// Scales: the operators are stored times 2^12 (their entries are below 6 in
+// magnitude, so the parts stay normal float16 down to 2^-15 of the largest
+// entry); each gathered multipole column is scaled by 2^e so that its largest
+// value lies in [2^14, 2^15), and the scatter multiplies the column by
+// 2^-(e + 12).  Powers of two: the scaling itself is exact.
 constexpr int kNClass = 16;
-constexpr int kSplitK = 6 * kFmmN3;
-__host__ __device__ __forceinline__ int split_part_a(int blk) { return (0x001012 >> (4 * blk)) & 0xF; }
-__host__ __device__ __forceinline__ int split_part_b(int blk) { return (0x010210 >> (4 * blk)) & 0xF; }
-
-// the k-th bfloat16 part of x (k = 0, 1, 2): x0 = bf16(x), x1 = bf16(x - x0), ...
-__device__ __forceinline__ __nv_bfloat16 split_part(float x, int k) {
-    __nv_bfloat16 p = __float2bfloat16_rn(x);
-    for (int j = 0; j < k; ++j) {
-        x -= __bfloat162float(p);
-        p = __float2bfloat16_rn(x);
-    }
-    return p;
-}
+constexpr int kSplitK = 3 * kFmmN3;
+constexpr float kOpScale = 4096.f;   // 2^12
+constexpr int kOpScaleExp = 12;
 
 __host__ __device__ __forceinline__ int3 canonical_offset(int c) {
     // enumeration of d_c = (i, j, k), i in {2, 3}, i >= j >= k >= 0
@@ -581,39 +573,56 @@ __global__ void k_fmm_build_op(int which_K, float* __restrict__ A) {
     A[(size_t)o * rows * kFmmN3 + e] = (float)v;
 }
 
-// A'[o][row][kk] = part split_part_a(kk / 512) of A[o][row][kk % 512] (column-major)
-__global__ void k_fmm_split_op(int rows, const float* __restrict__ A, __nv_bfloat16* __restrict__ As) {
+// A'[o][row][kk] (K-major): part a1 for kk < 512, a0 otherwise, of 2^12 A[o][row][kk % 512]
+// (A column-major [m][rows])
+__global__ void k_fmm_split_op(int rows, const float* __restrict__ A, __half* __restrict__ As) {
     const int o = blockIdx.y;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)rows * kSplitK) return;
-    const int row = (int)(e % rows), kk = (int)(e / rows);
-    const float a = A[((size_t)o * kFmmN3 + kk % kFmmN3) * rows + row];
-    As[(size_t)o * rows * kSplitK + e] = split_part(a, split_part_a(kk / kFmmN3));
+    const int row = (int)(e / kSplitK), kk = (int)(e % kSplitK);
+    const float a = A[((size_t)o * kFmmN3 + kk % kFmmN3) * rows + row] * kOpScale;
+    const __half a0 = __float2half_rn(a);
+    As[(size_t)o * rows * kSplitK + e] = kk < kFmmN3 ? __float2half_rn(a - __half2float(a0)) : a0;
 }
 
-// B'[:, vcol[e]] = split multipole of the e-th V-list source in its class's frame:
-// B'[kk, vcol[e]] = part split_part_b(kk / 512) of M_S[g.(kk % 512)]
-// (one block per V-list entry)
+// B'[vcol[e]][:] = split multipole of the e-th V-list source in its class's
+// frame, scaled by 2^s (s: the column's largest |value| into [2^14, 2^15)):
+// B'[vcol[e]][kk] = part (b0, b1, b0)[kk / 512] of 2^s M_S[g.(kk % 512)];
+// colscale[vcol[e]] = 2^-(s + 12) undoes both scales (one block per V-list entry)
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2l_gather(const int* __restrict__ v_list, const int* __restrict__ vcol,
                  const int* __restrict__ vsym, const float* __restrict__ M,
-                 __nv_bfloat16* __restrict__ B, const int* __restrict__ skip) {
+                 __half* __restrict__ B, float* __restrict__ colscale,
+                 const int* __restrict__ skip) {
     if (skip && *skip) return;
     static_assert(kThreads == kFmmN3, "one thread per expansion point");
     __shared__ float sm[kFmmN3];
+    __shared__ float smax[kThreads / 32];
     const int e = blockIdx.x;
     const int m = threadIdx.x;
-    sm[m] = M[(size_t)v_list[e] * kFmmN3 + m];
+    const float v = M[(size_t)v_list[e] * kFmmN3 + m];
+    sm[m] = v;
+    float mx = fabsf(v);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((m & 31) == 0) smax[m >> 5] = mx;
     __syncthreads();
-    const float x = sm[sym_apply(vsym[e], m)];
-    const __nv_bfloat16 x0 = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(x0);
-    const __nv_bfloat16 x1 = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 x2 = __float2bfloat16_rn(r1 - __bfloat162float(x1));
-    const __nv_bfloat16 parts[3] = {x0, x1, x2};
-    __nv_bfloat16* col = B + (size_t)vcol[e] * kSplitK;
+    mx = smax[0];
 #pragma unroll
-    for (int blk = 0; blk < 6; ++blk) col[blk * kFmmN3 + m] = parts[split_part_b(blk)];
+    for (int w = 1; w < kThreads / 32; ++w) mx = fmaxf(mx, smax[w]);
+    int ex = 0;
+    if (mx > 0.f && mx <= 3.0e38f) {
+        int E;
+        frexpf(mx, &E);   // mx = f 2^E, f in [0.5, 1)
+        ex = min(100, max(-100, 15 - E));
+    }
+    const float x = ldexpf(sm[sym_apply(vsym[e], m)], ex);
+    const __half x0 = __float2half_rn(x);
+    const __half x1 = __float2half_rn(x - __half2float(x0));
+    __half* col = B + (size_t)vcol[e] * kSplitK;
+    col[m] = x0;
+    col[kFmmN3 + m] = x1;
+    col[2 * kFmmN3 + m] = x0;
+    if (m == 0) colscale[vcol[e]] = ldexpf(1.f, -(ex + kOpScaleExp));
 }
 
 // sum of a box's multipole values (the log kernel's level term), fixed order
@@ -646,8 +655,9 @@ constexpr int kScatPerLane = kFmmN3 / 32;
 template <bool KERNEL_K>
 __global__ void __launch_bounds__(kThreads)
 k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* __restrict__ vcol,
-                  const int* __restrict__ vsym, const float* __restrict__ msum,
-                  float* __restrict__ Lc, const int* __restrict__ skip) {
+                  const int* __restrict__ vsym, const float* __restrict__ colscale,
+                  const float* __restrict__ msum, float* __restrict__ Lc,
+                  const int* __restrict__ skip) {
     if (skip && *skip) return;
     static_assert(kThreads == kFmmN3, "one thread per expansion point in the final sum");
     constexpr int C = KERNEL_K ? 1 : 9;
@@ -681,12 +691,13 @@ k_fmm_m2l_scatter(DevTree t, int box0, const float* __restrict__ Cm, const int* 
                 neg = sym_neg(g, qa);
             }
         }
-        const float* col = Cm + (size_t)vcol[e] * rows + qc * kFmmN3;
+        const int ce = vcol[e];
+        const float* col = Cm + (size_t)ce * rows + qc * kFmmN3;
+        const float cs = __ldg(colscale + ce);
+        const float sc = neg ? -cs : cs;
 #pragma unroll
-        for (int k = 0; k < kScatPerLane; ++k) {
-            const float v = __ldg(col + sym_apply_inv(g, lane + 32 * k));
-            acc[k] += neg ? -v : v;
-        }
+        for (int k = 0; k < kScatPerLane; ++k)
+            acc[k] = fmaf(__ldg(col + sym_apply_inv(g, lane + 32 * k)), sc, acc[k]);
     }
 #pragma unroll
     for (int k = 0; k < kScatPerLane; ++k) red[warp][lane + 32 * k] = acc[k];
@@ -728,14 +739,15 @@ struct PmFmmTree {
     int nv = 0, np2p = 0, nchunks = 0;
     std::vector<int> cls_start;   // [kNClass + 1]
     int *vcol = nullptr, *vsym = nullptr;
-    __nv_bfloat16* Bm = nullptr;   // [nv][3072] split multipoles (column-major B')
-    float *Cm = nullptr, *msum = nullptr;
-    cublasHandle_t blas = nullptr;
-    void* blas_ws = nullptr;
+    __half* Bm = nullptr;          // [nv][1536] split multipoles (K-major B')
+    float *Cm = nullptr, *msum = nullptr, *colscale = nullptr;
+    PmTcGemm gemm[2];              // tensor-core M2L plans: remainder (0), parametrix (1)
+    bool gemm_ready[2] = {false, false};
     ~PmFmmTree() {
-        if (blas) cublasDestroy(blas);
+        pm_tcgemm_free(&gemm[0]);
+        pm_tcgemm_free(&gemm[1]);
         pm_dfree(vcol); pm_dfree(vsym); pm_dfree(Bm); pm_dfree(Cm); pm_dfree(msum);
-        if (blas_ws) cudaFree(blas_ws);
+        pm_dfree(colscale);
         pm_dfree(perm); pm_dfree(lev_off_d); pm_dfree(box_first); pm_dfree(parent);
         pm_dfree(child_off); pm_dfree(child); pm_dfree(v_off); pm_dfree(v_list);
         pm_dfree(u_off); pm_dfree(u_list); pm_dfree(p2p_order); pm_dfree(leaf_chunks); pm_dfree(box_ijk); pm_dfree(sorted); pm_dfree(M);
@@ -746,6 +758,13 @@ struct PmFmmTree {
 void pm_fmm_free(pm_surface* s) {
     delete s->fmm;
     s->fmm = nullptr;
+}
+
+pm_status pm_fmm_check(pm_surface* s) {
+    if (!s->fmm) return PM_OK;
+    for (int k = 0; k < 2; ++k)
+        if (s->fmm->gemm_ready[k]) PM_TRY(pm_tcgemm_check(&s->fmm->gemm[k]));
+    return PM_OK;
 }
 
 namespace {
@@ -1106,14 +1125,14 @@ pm_status pm_fmm_build(pm_surface* s) {
 namespace {
 
 // Unit-box M2L operators of the context (one set per kernel family), built once.
-pm_status ensure_m2l_ops(pm_surface* s, int which_K, __nv_bfloat16** out) {
+pm_status ensure_m2l_ops(pm_surface* s, int which_K, __half** out) {
     pm_ctx* c = s->ctx;
     std::lock_guard<std::mutex> lk(c->fmm_mu);
-    __nv_bfloat16*& A = which_K ? c->fmm_opK : c->fmm_opR;
+    __half*& A = which_K ? c->fmm_opK : c->fmm_opR;
     if (!A) {
         const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
         float* tmp = nullptr;
-        __nv_bfloat16* split = nullptr;
+        __half* split = nullptr;
         PM_TRY(pm_dmalloc(&tmp, (size_t)kNClass * rows * kFmmN3));
         const pm_status st = pm_dmalloc(&split, (size_t)kNClass * rows * kSplitK);
         if (st != PM_OK) {
@@ -1146,27 +1165,36 @@ pm_status ensure_m2l_ops(pm_surface* s, int which_K, __nv_bfloat16** out) {
     return PM_OK;
 }
 
-// cuBLAS handle, its workspace (set explicitly so that the GEMM can be captured
-// in a graph) and the gathered multipole and result matrices of the tree.
-pm_status ensure_m2l_gemm(PmFmmTree* T) {
-    if (!T->blas) {
-        if (cublasCreate(&T->blas) != CUBLAS_STATUS_SUCCESS) {
-            T->blas = nullptr;
-            pm_set_error("FMM: cublasCreate failed");
-            return PM_ERR_CUDA;
-        }
-        const size_t ws = 64u << 20;
-        PM_CUDA_TRY(cudaMalloc(&T->blas_ws, ws));
-        if (cublasSetWorkspace(T->blas, T->blas_ws, ws) != CUBLAS_STATUS_SUCCESS) {
-            pm_set_error("FMM: cuBLAS workspace setup failed");
-            return PM_ERR_CUDA;
-        }
-    }
+// The gathered multipole and result matrices of the tree and its GEMM plan for
+// one kernel family: tiles of 128 operator rows x 256 V-list columns, class by
+// class (each class's columns start at cls_start[c]; the last tile of a class
+// is narrower), ordered class, column tile, row tile so that the CTAs working
+// at one time share a class's operator in L2.
+pm_status ensure_m2l_gemm(pm_surface* s, PmFmmTree* T, int which_K, const __half* A) {
     if (!T->Bm) {
         const size_t cols = (size_t)std::max(1, T->nv);
         PM_TRY(pm_dmalloc(&T->Bm, cols * kSplitK));
         PM_TRY(pm_dmalloc(&T->Cm, cols * 9 * kFmmN3));
+        PM_TRY(pm_dmalloc(&T->colscale, cols));
         PM_TRY(pm_dmalloc(&T->msum, (size_t)T->nbox));
+    }
+    if (!T->gemm_ready[which_K]) {
+        const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
+        std::vector<int> tiles;
+        for (int c = 0; c < kNClass; ++c) {
+            const int c0 = T->cls_start[c], nc = T->cls_start[c + 1] - c0;
+            for (int n0 = 0; n0 < nc; n0 += 256)
+                for (int m0 = 0; m0 < rows; m0 += 128) {
+                    tiles.push_back(c * rows + m0);
+                    tiles.push_back(c0 + n0);
+                    tiles.push_back(std::min(256, nc - n0));
+                    tiles.push_back(m0);
+                }
+        }
+        PM_TRY(pm_tcgemm_init(&T->gemm[which_K], A, (long long)kNClass * rows, T->Bm,
+                              std::max(1, T->nv), kSplitK, 0, tiles, T->Cm, rows,
+                              std::max(1, T->nv)));
+        T->gemm_ready[which_K] = true;
     }
     return PM_OK;
 }
@@ -1231,39 +1259,22 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     }
     const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
     if (s->opts.fmm_tensor_m2l) {
-        __nv_bfloat16* A = nullptr;
+        __half* A = nullptr;
         PM_TRY(ensure_m2l_ops(s, which_K, &A));
-        PM_TRY(ensure_m2l_gemm(T));
-        const int rows = which_K ? kFmmN3 : 9 * kFmmN3;
+        PM_TRY(ensure_m2l_gemm(s, T, which_K, A));
         if (which_K && nm2l > 0) k_fmm_msum<<<nm2l, kThreads, 0, st>>>(b2, T->M, T->msum, skip);
         if (T->nv > 0)
             k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, T->vsym, T->M, T->Bm,
-                                                         skip);
+                                                         T->colscale, skip);
         PM_CUDA_TRY(cudaGetLastError());
-        const float one = 1.f, zero = 0.f;
-        if (cublasSetStream(T->blas, st) != CUBLAS_STATUS_SUCCESS) {
-            pm_set_error("FMM: cublasSetStream failed");
-            return PM_ERR_CUDA;
-        }
-        for (int c = 0; c < kNClass; ++c) {
-            const int c0 = T->cls_start[c], nc = T->cls_start[c + 1] - c0;
-            if (nc == 0) continue;
-            if (cublasGemmEx(T->blas, CUBLAS_OP_N, CUBLAS_OP_N, rows, nc, kSplitK, &one,
-                             A + (size_t)c * rows * kSplitK, CUDA_R_16BF, rows,
-                             T->Bm + (size_t)c0 * kSplitK, CUDA_R_16BF, kSplitK, &zero,
-                             T->Cm + (size_t)c0 * rows, CUDA_R_32F, rows, CUBLAS_COMPUTE_32F,
-                             CUBLAS_GEMM_DEFAULT) != CUBLAS_STATUS_SUCCESS) {
-                pm_set_error("FMM: M2L GEMM (split bfloat16) failed");
-                return PM_ERR_CUDA;
-            }
-        }
+        PM_TRY(pm_tcgemm_run(&T->gemm[which_K], s->ctx->num_sms, skip, st));
         if (which_K)
             k_fmm_m2l_scatter<true><<<dim3(nm2l, 1), kThreads, 0, st>>>(
-                t, b2, T->Cm, T->vcol, T->vsym, T->msum, T->Lc, skip);
+                t, b2, T->Cm, T->vcol, T->vsym, T->colscale, T->msum, T->Lc, skip);
         else
             k_fmm_m2l_scatter<false><<<dim3(nm2l, 9), kThreads, 0, st>>>(
-                t, b2, T->Cm, T->vcol, T->vsym, T->msum, T->Lc, skip);
-        s->launch_total += 2 + (which_K ? 1 : 0);
+                t, b2, T->Cm, T->vcol, T->vsym, T->colscale, T->msum, T->Lc, skip);
+        s->launch_total += 3 + (which_K ? 1 : 0);
     } else if (which_K) {
         k_fmm_m2l<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
     } else {

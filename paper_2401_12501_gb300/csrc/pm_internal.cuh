@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -37,6 +38,7 @@ enum : int {
     PM_DEV_LEAF_OVERFLOW = 1,   // near rule exceeded its leaf budget
     PM_DEV_BAD_INDEX = 2,       // an index check failed
     PM_DEV_NONFINITE = 3,       // a non-finite quadrature value
+    PM_DEV_TIMEOUT = 4,         // a bounded wait (mbarrier, flag) ran out
 };
 
 // (x, y, z, s) in float64, 32-byte aligned for one 256-bit access
@@ -72,10 +74,11 @@ struct pm_ctx {
     // FMM M2L operators for unit boxes, one per offset class, shared by all
     // surfaces of the context; built on first use (pm_fmm.cu)
     std::mutex fmm_mu;
-    // M2L operators per canonical offset, column-major [rows][3072] in bfloat16:
-    // the float32 operator's 3-way split (a0, a1, a2) as column blocks a2 a1 a0 a1 a0 a0
-    __nv_bfloat16* fmm_opR = nullptr;   // rows = 9 * 512
-    __nv_bfloat16* fmm_opK = nullptr;   // rows = 512
+    // M2L operators per canonical offset, K-major [rows][1536] in float16: the
+    // float32 operator times 2^12, split in two float16 parts (a0, a1), as K
+    // blocks a1 a0 a0 (pm_fmm.cu)
+    __half* fmm_opR = nullptr;   // rows = 9 * 512
+    __half* fmm_opK = nullptr;   // rows = 512
 };
 
 // Device buffers fixed once a surface is built (geometry, near-field CSR and
@@ -213,6 +216,26 @@ pm_status pm_fmm_build(pm_surface* s);
 int pm_fmm_splits();
 pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st);
 void pm_fmm_free(pm_surface* s);
+pm_status pm_fmm_check(pm_surface* s);   // reads the tensor-core M2L error words (synchronises)
+
+// tensor-core GEMM (pm_tcgemm.cu): C[(bcol0 + j) * ldc + crow0 + r] =
+// sum_k A[arow0 + r][k] B[bcol0 + j][k] for r < 128, j < ncols over a list of
+// tiles (arow0, bcol0, ncols <= 256, crow0); A, B 16-bit K-major, C float32.
+struct PmTcGemm {
+    alignas(64) unsigned char mapA[128];   // CUtensorMap of A (box 64 x 128)
+    alignas(64) unsigned char mapB[128];   // CUtensorMap of B (box 64 x 256)
+    int* tiles = nullptr;                  // [4 * ntiles] device
+    int* err = nullptr;                    // device error word (PM_DEV_TIMEOUT)
+    int ntiles = 0, nkb = 0, bf16 = 0;
+    float* C = nullptr;
+    long long ldc = 0;
+};
+pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const void* B,
+                         long long b_rows, int K, int bf16, const std::vector<int>& tiles,
+                         float* C, long long ldc, long long c_cols);
+pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st);
+pm_status pm_tcgemm_check(const PmTcGemm* g);
+void pm_tcgemm_free(PmTcGemm* g);
 
 // batched applies and solves (pm_batch.cu)
 pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long long ld_sigma,

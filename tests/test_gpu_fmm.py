@@ -3,8 +3,9 @@
 The FMM replaces the far part of the smooth sums by 8x8x8-point Chebyshev
 interpolation between boxes; its error against the exact sum is bounded by
 the per-config tolerance for float32-class applies (at most 1e-5 relative).
-The M2L step runs as per-offset operator GEMMs on the tensor cores (float32
-emulated on bfloat16) by default, or evaluated directly on the float32 pipe.
+The M2L step runs as per-offset-class operator GEMMs on the library's tcgen05
+tensor-core kernel (float32 operands as two float16 parts) by default, or
+evaluated directly on the float32 pipe.
 """
 
 import numpy as np
@@ -119,6 +120,8 @@ def test_tensor_core_m2l_matches_direct_m2l(ctx, name):
                    s.apply_part(pm.PM_PART_SMOOTH_K, sigma, "fmm"),
                    s.apply_part(pm.PM_PART_SMOOTH_R, sigma, "fmm"))
         s.close()
+    # the two far fields differ by float32 rounding (~1e-7 per value, summed over the
+    # V lists) plus the dropped split product (2^-22 per term): a few 1e-6 relative
     for k in (0, 1):
-        assert rel(out[1][k], out[0][k]) < 2e-6, (k, rel(out[1][k], out[0][k]))
+        assert rel(out[1][k], out[0][k]) < 5e-6, (k, rel(out[1][k], out[0][k]))
     assert np.array_equal(out[1][0], out[1][2])            # deterministic
