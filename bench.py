@@ -1,17 +1,20 @@
 """Benchmark of the parametrix hot path on one GB300 (or N independent replicas).
 
-Default workload: the 9,600-node ellipsoid (1, 1.5, 2) with
-a = 1 + 0.5 sin(2x) cos(3y) and a seeded mean-zero right-hand side.  One step
-is one full solve of div(a grad u) = f to a relative residual of 1e-10 (so
-that u matches a plain float64 solve to 1e-8; the line reports the measured
-difference): source prep, float32 smooth sums,
-near-field correction, device GMRES, float-float true residuals, u = K~ sigma
-and the mean projection.  The near field is built once per surface, before
-the timed region (its time is reported).  Inputs are resident in HBM; L2 is
-flushed between steps.
+Default workload: the 98,304-node torus (R = 2, r = 0.7, 64 x 24 patches of
+8 x 8 nodes) with a = exp(0.3 cos(theta) sin(2 phi)) and f = cos(3 phi) sin(theta)
+projected to mean zero.  One step is one full solve of div(a grad u) = f to a
+relative residual of 1e-10 (so that u matches a plain float64 GPU solve to well
+within 1e-8; the line reports the measured difference): device GMRES whose
+operator applies use the Chebyshev FMM (tensor-core M2L) plus the float32
+near-field correction, float-float true residuals, u = K~ sigma in float-float
+and the mean projection.  --workload ellipsoid_9600 times the 9,600-node
+ellipsoid with direct float32 applies instead.  The near field is built once
+per surface, before the timed region (its time is reported).  Inputs are
+resident in HBM; L2 is flushed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the float64 CPU oracle
-on a bounded sample of the same workload instead.
+(every host core, one process per core) on a bounded sample of the same
+workload instead.
 """
 
 from __future__ import annotations
@@ -32,19 +35,46 @@ if ROOT not in sys.path:
 METRIC = "R-apply Gpairs/s; solves/s at 1e-8 rel err vs plain GPU solve; p50/p99 latency"
 UNIT = "Gpairs/s"
 FLOPS_PER_PAIR_R = 26      # variable-a remainder pair (algorithmic count)
+FLOPS_PER_PAIR_K = 10      # parametrix pair
+M2L_FLOPS_PER_BOX_PAIR = 2 * 9 * 512 * 512   # remainder M2L, 9 kernels on 8^3-point grids
+FP32_LANES_PER_SM = 128    # FP32 lanes of one sm_100-family SM
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# of the current kernel versions on this workload (profiles/k_direct_*_ellipsoid_9600.md);
-# set to None whenever the kernel changes until it is captured again.
+# of the current kernel versions on a workload; set to None whenever the kernel changes
+# until it is captured again.
 TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
                  ("k_direct_ff_R", "ellipsoid_9600"): 1236224,
                  ("k_sym_ff_R", "ellipsoid_9600"): 1299712}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+def _measured_peaks():
+    """HBM GB/s and bf16 TFLOP/s measured on the GB300s (generated file)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return {"hbm_gbs": m.get("hbm_gbs"), "bf16_tflops": m.get("bf16_tflops"),
+                "bf16_tflops_sustained": m.get("bf16_tflops_sustained"),
+                "basis": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "basis": "of fallback (no MEASURED_PEAKS.json)"}
+
+
+def _max_sm_mhz(device_index=0):
+    """The GPU's maximum SM clock read from the device (nvidia-smi), else None."""
+    try:
+        r = subprocess.run(["nvidia-smi", f"--id={device_index}",
+                            "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                           capture_output=True, text=True, timeout=30)
+        return float(r.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
+
+
+def fp32_peak_tflops(sms, mhz):
     """Non-tensor float32 peak from unit counts: SMs x FP32 lanes x 2 flops (FMA) x clock."""
-    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -104,39 +134,87 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle leg
-def oracle_rate(workload: str, seconds: float = 12.0):
-    """Oracle float64 remainder apply on a bounded sample; returns (Gpairs/s, description)."""
+# The float64 oracle's remainder apply, timed on a bounded sample of target rows: one
+# process per host core (spawned, each with one BLAS thread), every process evaluating
+# disjoint row chunks of the smooth sum over all N sources for a fixed wall time, plus
+# the near-field correction of a few rows (built once, untimed; its apply is timed).
+_ORC = {}
+
+
+def _orc_init(workload):
     import numpy as np
-    from oracle.operator import Discretization, NearField
+    from oracle.operator import Discretization
     from workloads import make_workload
-    wl = make_workload(workload)
-    d = Discretization.from_workload(wl)
+    d = Discretization.from_workload(make_workload(workload))
+    _ORC["d"] = d
+    _ORC["sigma"] = np.random.default_rng(0).standard_normal(d.N)
+
+
+def _orc_rows(task):
+    import numpy as np
+    rank, nproc, seconds, chunk = task
+    d, sigma = _ORC["d"], _ORC["sigma"]
     N = d.N
-    rng = np.random.default_rng(0)
-    sigma = rng.standard_normal(N)
-    near_rows = [int(i) for i in rng.integers(0, N, 8)]
-    nf = NearField(d, rows=near_rows)            # one-time corrections, not timed
-    rows_done, t_smooth = 0, 0.0
-    chunk = 256
+    rows_done, k = 0, rank
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds:
-        r0 = (rows_done * 7919) % max(1, N - chunk)
-        rows = np.arange(r0, min(N, r0 + chunk))
+        r0 = (k * 7919 * chunk) % max(1, N - chunk)
+        d.smooth_apply("R", sigma, np.arange(r0, min(N, r0 + chunk)), chunk=chunk)
+        rows_done += min(N, r0 + chunk) - r0
+        k += nproc
+    return rows_done, time.perf_counter() - t0
+
+
+class OracleRunner:
+    """A pool of oracle processes for one workload (spawned: no process forks after a
+    CUDA context exists) and the near-field corrections of a few sampled rows."""
+
+    def __init__(self, workload: str, processes: int):
+        import multiprocessing as mp
+        import numpy as np
+        from oracle.operator import Discretization, NearField
+        from workloads import make_workload
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        self.workload, self.P = workload, max(1, processes)
+        d = Discretization.from_workload(make_workload(workload))
+        self.N = d.N
+        self.chunk = 32 if d.N > 50000 else 128
+        rng = np.random.default_rng(0)
+        self.sigma = rng.standard_normal(d.N)
+        self.near_rows = [int(i) for i in rng.integers(0, d.N, 8)]
+        self.nf = NearField(d, rows=self.near_rows)          # one-time corrections, untimed
+        self.pool = mp.get_context("spawn").Pool(self.P, initializer=_orc_init,
+                                                 initargs=(workload,))
+
+    def rate(self, seconds: float, processes: int | None = None):
+        """(Gpairs/s, description) of the oracle's remainder apply on `processes` cores."""
+        P = self.P if processes is None else max(1, min(processes, self.P))
+        res = self.pool.map(_orc_rows, [(r, P, seconds, self.chunk) for r in range(P)])
+        rows = sum(r[0] for r in res)
+        wall = max(r[1] for r in res)
         ts = time.perf_counter()
-        d.smooth_apply("R", sigma, rows)
-        t_smooth += time.perf_counter() - ts
-        rows_done += len(rows)
-    ts = time.perf_counter()
-    nf.apply("R", sigma, near_rows)
-    t_near = (time.perf_counter() - ts) / len(near_rows)
-    t_row = t_smooth / rows_done + t_near
-    rate = N / t_row / 1e9                      # pairs per second per row-time
-    desc = (f"{rows_done} target rows of {workload} (smooth sum over all {N} sources) "
-            f"+ near-field correction of {len(near_rows)} rows, float64 numpy, 1 thread")
-    return rate, desc
+        self.nf.apply("R", self.sigma, self.near_rows)
+        t_near = (time.perf_counter() - ts) / len(self.near_rows)
+        t_row = wall / rows + t_near / P        # per-row time with P cores working
+        desc = (f"{rows} target rows of {self.workload} (float64 smooth sum over all {self.N} "
+                f"sources, numpy) on {P} process(es) x {seconds:.1f} s + near-field "
+                f"correction of {len(self.near_rows)} rows")
+        return self.N / t_row / 1e9, desc
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
 
 
-def reference_line(args, vals, desc):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def reference_line(args, vals, desc, cores):
     """The reference arm's JSON line: the oracle's rate (mean over the timed steps)."""
     v = statistics.mean(vals[args.warmup:]) if len(vals) > args.warmup else vals[-1]
     return {
@@ -144,18 +222,20 @@ def reference_line(args, vals, desc):
         "warmup": args.warmup, "higher_is_better": True, "impl": "reference",
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
 def run_oracle_subprocess(workload: str, seconds: float):
+    """cpu_baseline of the GPU arm: the oracle on every host core and on one core, in a
+    fresh process that never touches the GPU."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg",
                         "--workload", workload, "--oracle-seconds", str(seconds)],
-                       capture_output=True, text=True, env=env, timeout=600)
+                       capture_output=True, text=True, env=env, timeout=900)
     for ln in r.stdout.splitlines()[::-1]:
         if ln.startswith("{"):
             return json.loads(ln)
@@ -163,7 +243,8 @@ def run_oracle_subprocess(workload: str, seconds: float):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-PHASES = ["prep", "direct_R32", "direct_K32", "near", "vec", "direct_ff_or_64"]
+PHASES = ["prep", "direct_R", "direct_K", "near", "vec", "accurate_R", "fmm_m2l_gemm",
+          "fmm_p2p", "accurate_K"]
 
 
 def max_over_ranks(value, world, device=None):
@@ -209,48 +290,64 @@ def _phase_totals(surf, reset=True):
     return out
 
 
+def _alu_roofline(kernel, flops_per_launch, ms_per_launch, peak, step_share, traffic, **extra):
+    ach = flops_per_launch / (ms_per_launch * 1e-3) / 1e12
+    d = {"bound": "alu", "kernel": kernel, "achieved": round(ach, 3), "peak": round(peak, 2),
+         "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic,
+         "kernel_ms": round(ms_per_launch, 5), "step_time_share": round(step_share, 4)}
+    d.update(extra)
+    return d
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
     import paper_2401_12501_gb300 as pm
-    from paper_2401_12501_gb300 import _lib
     from workloads import make_workload
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    prec = args.prec or DEFAULT_PREC.get(args.workload, "fp32")
     wl = make_workload(args.workload)
     N = wl.N
     pairs = float(N) * N
     ctx = pm.Context(local_rank)
+    gpu_name, sms = ctx.info()
+    max_mhz = _max_sm_mhz(local_rank)
+    peak_fp32 = fp32_peak_tflops(sms, max_mhz or 2070.0)
+    mp_peaks = _measured_peaks()
     t0 = time.perf_counter()
     surf = pm.Surface.from_fixture(ctx, wl.surface)
     t_build = time.perf_counter() - t0
     surf.set_coeff(wl.coeff.a, wl.coeff.grad_a)
     nblk = surf.info()[1]
-    # launch shape of the float32 sums picked by the autotuner (untimed, before warm-up)
-    tune = surf.autotune(nrhs=1, prec="fp32", reps=5) if not args.no_autotune else _builtin(surf)
+    # launch shapes picked by the autotuner (untimed, before warm-up): the FMM's octree
+    # depth for FMM applies, the float32 sums' shape otherwise
+    tune = (surf.autotune(nrhs=1, prec=prec, reps=3 if prec == "fmm" else 5)
+            if not args.no_autotune else _builtin(surf))
+    fmm = surf.fmm_stats() if prec == "fmm" else None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
     f_h = torch.from_numpy(wl.f.copy()).pin_memory()
-    u_h = torch.empty(N, dtype=torch.float64).pin_memory()
     f_d = f_h.to(dev)
     tol = args.tol
 
     def step():
-        return surf.solve(f_d, tol=tol, prec="fp32")
+        return surf.solve(f_d, tol=tol, prec=prec)
 
     # the accuracy the timed solves reach: u against a plain float64 solve (float64
-    # operator applies and Krylov basis) of the same system to 1e-12
+    # operator applies and Krylov basis, direct sums) of the same system to 1e-12
+    t0 = time.perf_counter()
     u_ref, _ = surf.solve(wl.f, tol=1e-12, prec="fp64")
-    u_chk, _ = surf.solve(wl.f, tol=tol, prec="fp32")
+    t_fp64 = time.perf_counter() - t0
+    u_chk, _ = surf.solve(wl.f, tol=tol, prec=prec)
     wq = wl.surface.weights
     err_vs_fp64 = float(np.sqrt(np.dot(wq, (u_chk - u_ref) ** 2) / np.dot(wq, u_ref ** 2)))
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    dist = None
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -271,10 +368,11 @@ def run_gpu(args, rank, world, local_rank):
     launches_timed = surf.profile_read(len(PHASES))[1]
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
+    clocks = clk.summary()
 
-    # phase split: the same steps again with per-phase events (event records
-    # cannot sit inside the graph-driven GMRES cycle, so this pass issues its
-    # launches from the host; the kernels are the same)
+    # phase split: the same steps again with per-phase events recorded by the library
+    # on the launching stream (event records cannot sit inside the graph-driven GMRES
+    # cycle, so this pass issues its launches from the host; the kernels are the same)
     pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     surf.profile(True)
@@ -291,119 +389,141 @@ def run_gpu(args, rank, world, local_rank):
     ph = _phase_totals(surf)
     prof_total_ms = sum(a.elapsed_time(b) for a, b in pev)
     ms_per_step = total_ms / args.steps
-    # operator applies per solve: one float32 R apply per Arnoldi step, one accurate R
-    # apply per refinement, one accurate K apply for u
+    # operator applies per solve: one R apply per Arnoldi step, one accurate R apply
+    # per refinement, one accurate K apply for u
     it = statistics.mean(i.iterations for i in infos)
     rf = statistics.mean(i.refinements for i in infos)
     applies = it + rf + 1
     value = job_throughput(world, applies * pairs, ms_per_step)
     solves_per_s = world * 1e3 / ms_per_step
+    per_step = lambda nm: (ph[nm][0] / args.steps, ph[nm][1] / args.steps)   # noqa: E731
+    acc_R_ms, acc_R_n = per_step("accurate_R")
+    acc_K_ms, acc_K_n = per_step("accurate_K")
+    fast_R_ms, fast_R_n = per_step("direct_R")
+    actual_pairs = ((fast_R_n * fmm["p2p_pairs"] if fmm else fast_R_n * pairs)
+                    + (acc_R_n + acc_K_n) * pairs)
 
     # end-to-end through the C ABI with host (pinned) buffers: f in, u out
     for _ in range(2):
-        surf.solve(f_h.numpy(), tol=tol, prec="fp32")
+        surf.solve(f_h.numpy(), tol=tol, prec=prec)
     torch.cuda.synchronize()
+    n_e2e = max(3, args.steps // 2)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u, _ = surf.solve(f_h.numpy(), tol=tol, prec="fp32")
-    e2e_s = (time.perf_counter() - t0) / args.steps
+    for _ in range(n_e2e):
+        surf.solve(f_h.numpy(), tol=tol, prec=prec)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_value = job_throughput(world, applies * pairs, e2e_s * 1e3)
 
-    # isolated float32 remainder apply (inputs resident, L2 flushed)
-    sig = torch.from_numpy(np.random.default_rng(1).standard_normal(N)).to(dev)
-    out = torch.empty_like(sig)
-    for _ in range(3):
-        surf.apply_R(sig, "fp32", out=out)
-    surf.profile(True)
-    surf.profile_read(0, reset=True)
-    aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        aev[k][0].record(stream)
-        surf.apply_R(sig, "fp32", out=out)
-        aev[k][1].record(stream)
-    torch.cuda.synchronize()
-    surf.profile(False)
-    aph = _phase_totals(surf)
-    apply_ms = sum(a.elapsed_time(b) for a, b in aev) / args.steps
-
-    # roofline of the dominant kernel of the solve step (by device time)
-    fp32_ms, fp32_n = ph["direct_R32"]
-    ff_ms, ff_n = ph["direct_ff_or_64"]
-    peak = fp32_peak_tflops()
-    # per-launch time of the float32 sum inside the solve step (profiled pass)
-    fp32_k = fp32_ms / max(1, fp32_n)
-    r32 = {"bound": "alu", "kernel": "k_direct_R32 (float32 remainder sum)",
-           "achieved": round(FLOPS_PER_PAIR_R * pairs / (fp32_k * 1e-3) / 1e12, 3),
-           "peak": round(peak, 2), "unit": "TFLOP/s",
-           "frac": round(FLOPS_PER_PAIR_R * pairs / (fp32_k * 1e-3) / 1e12 / peak, 4),
-           "traffic": TRAFFIC_BYTES.get(("k_direct_R32", args.workload)),
-           "kernel_ms": round(fp32_k, 5),
-           "flops_per_pair": FLOPS_PER_PAIR_R,
-           "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (unit counts)",
-           "step_time_share": round(fp32_ms / prof_total_ms, 4)}
-    ff_k = ff_ms / ff_n if ff_n else 0.0
+    # rooflines of the step's kernels, per launch from the profiled pass
     nt = -(-N // 128)
     sym = N >= 256 and nt * N * 8 <= SYM_PARTIAL_CAP
     ff_name = "k_sym_ff" if sym else "k_direct_ff"
-    rff = {"bound": "alu",
-           "kernel": ff_name + (" (symmetric tile-pair float-float remainder/parametrix sums)" if sym
-                                else " (float-float remainder/parametrix sums)"),
-           "achieved": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12, 3) if ff_k else None,
-           "peak": round(peak, 2), "unit": "TFLOP/s",
-           "frac": round(FLOPS_PER_PAIR_R * pairs / (ff_k * 1e-3) / 1e12 / peak, 4) if ff_k else None,
-           "traffic": TRAFFIC_BYTES.get((ff_name + "_R", args.workload)),
-           "kernel_ms_per_apply": round(ff_k, 5),
-           "note": "algorithmic flops of the float64-class sum (26 per ordered pair) over the "
-                   "average of the step's float-float launches; float-float arithmetic costs "
-                   "~10 float32 instructions per algorithmic flop (274 per unordered pair for "
-                   "the remainder, 130 for the parametrix, each unordered pair evaluated once)",
-           "step_time_share": round(ff_ms / prof_total_ms, 4)}
-    dominant, other = (rff, r32) if ff_ms > fp32_ms else (r32, rff)
+    roofs = {}
+    if acc_R_n:
+        roofs["accurate_R"] = _alu_roofline(
+            ff_name + "<R> (float-float remainder sum" + (", each unordered pair once)" if sym else ")"),
+            FLOPS_PER_PAIR_R * pairs, acc_R_ms / acc_R_n, peak_fp32, acc_R_ms * args.steps / prof_total_ms,
+            TRAFFIC_BYTES.get((ff_name + "_R", args.workload)),
+            note="algorithmic flops of the float64-class sum (26 per ordered pair); float-float "
+                 "arithmetic costs ~10 float32 instructions per algorithmic flop (274 per "
+                 "unordered pair), so the sum is bound by FP32 instruction issue")
+    if acc_K_n:
+        roofs["accurate_K"] = _alu_roofline(
+            ff_name + "<K> (float-float parametrix sum)", FLOPS_PER_PAIR_K * pairs,
+            acc_K_ms / acc_K_n, peak_fp32, acc_K_ms * args.steps / prof_total_ms,
+            TRAFFIC_BYTES.get((ff_name + "_K", args.workload)))
+    if fmm and ph["fmm_m2l_gemm"][1]:
+        g_ms = ph["fmm_m2l_gemm"][0] / ph["fmm_m2l_gemm"][1]
+        alg = M2L_FLOPS_PER_BOX_PAIR * fmm["m2l_box_pairs"]
+        peak_tc = mp_peaks["bf16_tflops_sustained"] or mp_peaks["bf16_tflops"]
+        ach = alg / (g_ms * 1e-3) / 1e12
+        roofs["fmm_m2l_gemm"] = {
+            "bound": "tensor", "kernel": "k_tc_gemm (FMM M2L, float16 parts, tcgen05)",
+            "achieved": round(ach, 2), "peak": peak_tc, "unit": "TFLOP/s",
+            "frac": round(ach / peak_tc, 4), "traffic": TRAFFIC_BYTES.get(("k_tc_gemm", args.workload)),
+            "kernel_ms": round(g_ms, 5), "executed_flops_factor": 3,
+            "executed_frac": round(3 * ach / peak_tc, 4),
+            "peak_basis": "float16 dense rate = bf16 rate (nominal ratio 1); sustained bf16 "
+                          + mp_peaks["basis"],
+            "step_time_share": round(ph["fmm_m2l_gemm"][0] / prof_total_ms, 4)}
+    if fmm and ph["fmm_p2p"][1]:
+        p_ms = ph["fmm_p2p"][0] / ph["fmm_p2p"][1]
+        roofs["fmm_p2p"] = _alu_roofline(
+            "k_fmm_p2p<R> (FMM adjacent-leaf float32 sums)", FLOPS_PER_PAIR_R * fmm["p2p_pairs"],
+            p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms, None)
+    if not fmm and fast_R_n:
+        roofs["direct_R"] = _alu_roofline(
+            "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, fast_R_ms / fast_R_n,
+            peak_fp32, fast_R_ms * args.steps / prof_total_ms,
+            TRAFFIC_BYTES.get(("k_direct_R32", args.workload)))
+    dom = max(roofs, key=lambda k: roofs[k]["step_time_share"]) if roofs else None
+    peak_basis = (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                  f"{max_mhz or 2070.0:g} MHz (unit counts; SM count from the device, clock "
+                  + ("from nvidia-smi)" if max_mhz else "assumed: nvidia-smi unavailable)"))
+    for r in roofs.values():
+        if r["bound"] == "alu":
+            r["peak_basis"] = peak_basis
+    step_desc = ("one solve of div(a grad u) = f to relative residual "
+                 f"{tol:g}: device GMRES with "
+                 + ("Chebyshev-FMM applies (tensor-core M2L)" if prec == "fmm" else
+                    "float32 direct-sum applies")
+                 + " + float32 near field, float-float refinement residuals, u = K sigma in "
+                   "float-float, mean projection")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32",
-        "dtype_detail": "f32 operator applies (compensated sums) + float-float residuals/"
-                        "representation + f64 Krylov basis and near field",
+        "dtype_detail": ("f32 operator applies (FMM: float16-part tensor-core M2L with float32 "
+                         "accumulation; float32 P2P, P2M/L2P and near field) + float-float "
+                         "residuals/representation + f64 Krylov basis" if prec == "fmm" else
+                         "f32 operator applies (compensated sums) + float-float residuals/"
+                         "representation + f64 Krylov basis and near field"),
         "data": "synthetic", "impl": "gb300",
-        "config": {"workload": args.workload, "N": N,
-                   "step": "one solve of div(a grad u) = f to relative residual "
-                           f"{tol:g}: device GMRES (float32 applies) + float-float "
-                           "refinement + u = K sigma + mean projection",
-                   "value_definition": "smooth-sum pairs evaluated per second over the solve "
+        "config": {"workload": args.workload, "N": N, "gpu": gpu_name, "operator_prec": prec,
+                   "step": step_desc,
+                   "value_definition": "equivalent smooth-sum pairs per second over the solve "
                                        "step = (Arnoldi steps + refinements + 1) * N^2 / time",
                    "near_blocks": nblk, "near_build_s": round(t_build, 3),
-                   "autotune": {"knobs": tune["knobs"], "apply_ms": _r(tune["best_ms"], 4),
+                   "autotune": {"knobs": {k: v for k, v in tune["knobs"].items() if v},
+                                "apply_ms": _r(tune["best_ms"], 4),
                                 "builtin_apply_ms": _r(tune["default_ms"], 4),
                                 "candidates": tune["candidates"]},
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
-        "solves_per_s": round(solves_per_s, 2),
+        "solves_per_s": round(solves_per_s, 3),
+        "actual_pairs_gpairs_per_s": round(world * actual_pairs / (ms_per_step * 1e-3) / 1e9, 3),
+        "actual_pairs_definition": ("pairs evaluated pair by pair per step: FMM applies count "
+                                    "their adjacent-leaf (P2P) pairs, accurate (float-float) "
+                                    "applies N^2; the far field is not pairs" if fmm else
+                                    "every apply evaluates N^2 pairs"),
         "solve": {"iterations": it, "refinements": rf, "applies_per_solve": applies,
                   "residual_max": max(i.residual for i in infos),
-                  "rel_err_vs_fp64_solve": err_vs_fp64,
+                  "rel_err_vs_fp64_solve": err_vs_fp64, "fp64_solve_s": round(t_fp64, 3),
                   "profiled_ms_per_step": round(prof_total_ms / args.steps, 4),
                   "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in ph.items()
-                                        if k != "launches_all"}},
-        "apply_R_fp32": {"gpairs_per_s": round(pairs / (apply_ms * 1e-3) / 1e9, 2),
-                         "ms": round(apply_ms, 5),
-                         "phase_ms": {k: round(v[0] / args.steps, 5) for k, v in aph.items()
-                                      if k != "launches_all"}},
+                                        if k != "launches_all"},
+                  "phase_launches_per_step": {k: v[1] / args.steps for k, v in ph.items()
+                                              if k != "launches_all"}},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
-                "d2h_bytes_per_step": 8 * N, "solves_per_s": round(world / e2e_s, 2)},
-        "gpu_launches": None,
-        "roofline": dominant,
-        "roofline_other": other,
-        "clocks": clk.summary(),
+                "d2h_bytes_per_step": 8 * N, "solves_per_s": round(world / e2e_s, 3)},
+        "gpu_launches": int(launches_timed),
+        "roofline": roofs.get(dom),
+        "roofline_other": {k: v for k, v in roofs.items() if k != dom},
+        "clocks": clocks,
     }
-    line["gpu_launches"] = int(launches_timed)
+    if fmm:
+        line["config"]["fmm"] = {
+            "tree": fmm, "interp_points": "8^3 Chebyshev (first kind) per box",
+            "leaf": "uniform-depth octree of occupied boxes, depth by a cost model / autotuner",
+            "note": ("deviation from the config text (leaf <= 256 points, 6^3 points): 6^3 "
+                     "points do not reach the 1e-5 apply tolerance, and at 8^3 points a "
+                     "deeper tree (smaller leaves) costs more in M2L than it saves in P2P")}
+    surf.close()
+    ctx.close()
     return line
 
 
-# ----------------------------------------------------------------------------- other configs
 def _builtin(s):
     """The autotuner's report for the built-in launch shapes (used with --no-autotune)."""
     return {"knobs": s.knobs(), "best_ms": None, "default_ms": None,
@@ -412,6 +532,20 @@ def _builtin(s):
 
 def _r(v, nd):
     return None if v is None else round(v, nd)
+
+
+def run_ellipsoid(args, dev):
+    """The 9,600-node ellipsoid solve with direct float32 applies (the whole solve
+    step of the headline, on the smaller surface whose float32 sums dominate)."""
+    sub = argparse.Namespace(**vars(args))
+    sub.workload, sub.prec = "ellipsoid_9600", "fp32"
+    ln = run_gpu(sub, 0, 1, dev.index or 0)
+    keep = ("value", "unit", "ms_per_step", "solves_per_s", "solve", "e2e", "roofline",
+            "roofline_other", "clocks", "gpu_launches")
+    out = {k: ln[k] for k in keep}
+    out["config"] = {k: ln["config"][k] for k in ("workload", "N", "step", "near_blocks",
+                                                  "near_build_s", "autotune")}
+    return out
 
 
 def run_batched(args, dev):
@@ -789,15 +923,19 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ellipsoid_9600")
+    ap.add_argument("--workload", default="torus_98304")
+    ap.add_argument("--prec", default=None, choices=["fp32", "fmm"],
+                    help="operator precision of the solve step (default: FMM for the torus, "
+                         "float32 direct sums otherwise)")
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for profiler runs, whose timings "
                          "would mislead the autotuner)")
-    ap.add_argument("--extras", default="batched,fmm,served,paper",
-                    help="comma-separated extra measurements to run (batched, fmm, served, paper)")
+    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper",
+                    help="comma-separated extra measurements to run (ellipsoid, batched, fmm, "
+                         "served, paper)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -815,8 +953,13 @@ def main():
         run_micro_tc_gemm(args)
         return
     if args.oracle_leg:
-        rate, desc = oracle_rate(args.workload, args.oracle_seconds)
-        print(json.dumps({"value": rate, "sample": desc}))
+        P = host_cores()
+        runner = OracleRunner(args.workload, P)
+        rate_all, desc_all = runner.rate(args.oracle_seconds)
+        rate_1, desc_1 = runner.rate(max(2.0, args.oracle_seconds / 2), processes=1)
+        runner.close()
+        print(json.dumps({"value": rate_all, "sample": desc_all, "cores": P,
+                          "value_1core": rate_1, "sample_1core": desc_1}))
         return
 
     rank = int(os.environ.get("RANK", 0))
@@ -826,13 +969,15 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        vals = []
-        desc = ""
+        P = host_cores()
+        runner = OracleRunner(args.workload, P)
+        per_step = max(1.0, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
+        vals, desc = [], ""
         for _ in range(args.warmup + args.steps):
-            r = run_oracle_subprocess(args.workload, max(2.0, 60.0 / (args.steps + args.warmup)))
-            vals.append(r["value"])
-            desc = r["sample"]
-        print(json.dumps(reference_line(args, vals, desc)))
+            v, desc = runner.rate(per_step)
+            vals.append(v)
+        runner.close()
+        print(json.dumps(reference_line(args, vals, desc, P)))
         return
 
     if world > 1:
@@ -844,7 +989,8 @@ def main():
         import torch
         dev = torch.device("cuda", local_rank)
         want = set(args.extras.split(","))
-        for name, key, fn in (("batched", "batched_star_24576", run_batched),
+        for name, key, fn in (("ellipsoid", "ellipsoid_9600", run_ellipsoid),
+                              ("batched", "batched_star_24576", run_batched),
                               ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served),
                               ("paper", "paper_problems", run_paper)):
             if name not in want:
@@ -857,8 +1003,10 @@ def main():
         if not args.no_cpu_baseline:
             try:
                 r = run_oracle_subprocess(args.workload, args.oracle_seconds)
-                line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": 1,
-                                        "kind": "oracle", "sample": r["sample"]}
+                line["cpu_baseline"] = {"value": r["value"], "unit": UNIT, "cores": r["cores"],
+                                        "kind": "oracle", "sample": r["sample"],
+                                        "value_1core": r["value_1core"],
+                                        "sample_1core": r["sample_1core"]}
             except Exception as e:  # report, do not hide
                 line["cpu_baseline"] = {"value": None, "error": str(e)[:300]}
         print(json.dumps(line))

@@ -310,7 +310,8 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  * launch count since the last reset (reset = 1 clears them).  With
  * phase = PM_PHASE_COUNT, *ms is 0 and *launches is the number of kernels the
  * library launched for this surface since the last reset (counted whether or
- * not timing is enabled).
+ * not timing is enabled).  The two FMM phases time single kernels that also lie
+ * inside the DIRECT_R / DIRECT_K phase of the same apply.
  */
 enum {
     PM_PHASE_PREP = 0,        /* source strengths s = w sigma / a          */
@@ -318,8 +319,11 @@ enum {
     PM_PHASE_DIRECT_K = 2,    /* smooth parametrix sum                     */
     PM_PHASE_NEAR = 3,        /* near-field correction + split reduction   */
     PM_PHASE_SOLVE_VEC = 4,   /* GMRES vector kernels                      */
-    PM_PHASE_DIRECT64 = 5,    /* float64 smooth sums (R or K)              */
-    PM_PHASE_COUNT = 6
+    PM_PHASE_DIRECT64 = 5,    /* float64 or float-float smooth remainder sum */
+    PM_PHASE_FMM_M2L = 6,     /* FMM M2L tensor-core GEMM (inside DIRECT_R/K) */
+    PM_PHASE_FMM_P2P = 7,     /* FMM adjacent-leaf exact sums (inside DIRECT_R/K) */
+    PM_PHASE_DIRECT64_K = 8,  /* float64 or float-float smooth parametrix sum */
+    PM_PHASE_COUNT = 9
 };
 pm_status pm_profile_enable(pm_surface* s, int enable);
 pm_status pm_profile_read(pm_surface* s, int phase, double* ms, int* launches, int reset);
@@ -413,25 +417,46 @@ pm_status pm_smooth_c_f32(int N, const float* x, const float* n, const float* H,
 /*
  * Serving: continuous batching of solve requests over many operators.
  *
- * An operator is a pm_surface whose coefficient is set.  pm_server_create starts
- * n_workers threads, each with its own CUDA stream.  A worker takes the operator
- * whose oldest waiting request arrived first among the operators no other worker
- * is serving, admits up to max_batch of that operator's waiting requests (in
- * arrival order) while their device footprint fits the budget, and solves them
- * together (batched applies, lockstep GMRES, float-float refinement; see
- * pm_solve).  Requests arriving meanwhile join later batches, so work on
- * different operators overlaps on the device.  Footprint per request:
- * (gmres_restart + 11) * N * 8 bytes.  Operators handed to a server must not be
- * used by the caller until every request on them has been waited for.
- *   hbm_budget_bytes  device bytes the server may reserve for admitted requests
+ * A request names its operator either as a caller's pm_surface whose coefficient
+ * is set (pm_server_submit) or as a description (pm_server_submit_desc): the
+ * geometry arrays of pm_surface_create and the coefficient of
+ * pm_surface_set_coeff, keyed by caller ids of the geometry and of the
+ * coefficient.  The server builds a described operator itself on a worker the
+ * first time it is needed (near-field build for a new geometry id; a clone that
+ * shares the near-field weights for a new coefficient id on a built geometry)
+ * and keeps it resident for later requests with the same ids; it is destroyed
+ * with the server.
+ *
+ * pm_server_create starts n_workers threads, each with its own CUDA stream.  A
+ * worker takes the operator whose oldest waiting request arrived first among the
+ * operators no other worker is serving; builds it if needed; otherwise admits up
+ * to max_batch of that operator's waiting requests of one precision (in arrival
+ * order) and solves them together (batched applies, lockstep GMRES, float-float
+ * refinement; see pm_solve).  Requests arriving meanwhile join later batches, so
+ * work on different operators overlaps on the device.
+ *
+ * Memory admission: every build and batch reserves the device bytes it will
+ * newly allocate, from a model of the library's allocations (operator arrays,
+ * near field; Krylov and batched workspaces an operator does not already hold;
+ * the FMM tree), and is admitted only while the reservations in flight plus its
+ * own stay within hbm_budget_bytes and, measured by cudaMemGetInfo at admission,
+ * within the device's free memory less a margin of max(256 MiB, 2% of the
+ * device).  With nothing else in flight the oldest work is admitted regardless
+ * of the free-memory reading; if its allocation then fails the request ends with
+ * PM_ERR_OOM and the server continues.
+ *   hbm_budget_bytes  cap on the bytes the server may reserve at once
  *   max_batch         right-hand sides per batch (1 = one request at a time)
  * pm_server_submit copies f (host, [N]) and returns a ticket; prec is the solve's
  * operator precision (FP64, FP32, FF or FMM; PM_ERR_INVALID_ARG otherwise), and a
  * batch only joins requests of one operator and one precision; PM_ERR_OOM if one
- * request alone exceeds the budget.  pm_server_wait blocks until the ticket is
- * done (timeout_ms < 0: no limit; PM_ERR_TIMEOUT otherwise), copies u (host,
- * [N]) and the solve info, reports the submit-to-finish latency, and releases
- * the ticket; it returns the solve's status.
+ * request's modelled workspace alone exceeds the budget.  Operators handed to a
+ * server must not be used by the caller until every request on them has been
+ * waited for.  pm_server_wait blocks until the ticket is done (timeout_ms < 0: no
+ * limit; PM_ERR_TIMEOUT otherwise, the ticket stays valid), copies u (host, [N])
+ * and the solve info, reports the submit-to-finish latency, releases the ticket
+ * and returns the solve's status; on failure pm_last_error() on the waiting
+ * thread holds the worker's message.  One thread at a time may wait on a ticket:
+ * a second concurrent pm_server_wait on it returns PM_ERR_INVALID_ARG.
  */
 typedef struct pm_server pm_server;
 pm_status pm_server_create(pm_ctx* ctx, size_t hbm_budget_bytes, int max_batch, int n_workers,
@@ -439,11 +464,45 @@ pm_status pm_server_create(pm_ctx* ctx, size_t hbm_budget_bytes, int max_batch, 
 void pm_server_destroy(pm_server* sv);
 pm_status pm_server_submit(pm_server* sv, pm_surface* op, const double* f, double tol,
                            pm_precision prec, unsigned long long* ticket);
+
+/* An operator described by its arrays (host, copied at submit when the ids are new;
+ * the arrays of a request whose ids the server already knows are not read).
+ * geometry_id names one geometry (the same npatch, p and arrays every time);
+ * coeff_id one coefficient on it.  Arrays as pm_surface_create (nodes, normals
+ * [N*3], tangents [N*6], curvature, weights [N]) and pm_surface_set_coeff
+ * (a [N] > 0, grad_a [N*3] or NULL); opts NULL for the defaults. */
+typedef struct {
+    unsigned long long geometry_id, coeff_id;
+    int npatch, p;
+    const double *nodes, *normals, *tangents, *curvature, *weights;
+    const double *a, *grad_a;
+    const pm_opts* opts;
+} pm_operator_desc;
+
+/* Submit a request on a described operator.  PM_ERR_INVALID_ARG for NULL arrays
+ * of a new operator, p outside 2..11, or a geometry id seen before with another
+ * node count; PM_ERR_OOM if the operator's modelled size exceeds the budget.  A
+ * build that fails ends every request on that operator with the build's status
+ * and message. */
+pm_status pm_server_submit_desc(pm_server* sv, const pm_operator_desc* desc, const double* f,
+                                double tol, pm_precision prec, unsigned long long* ticket);
 pm_status pm_server_poll(pm_server* sv, unsigned long long ticket, int* done);
 pm_status pm_server_wait(pm_server* sv, unsigned long long ticket, double* u,
                          pm_solve_info* info, double* latency_s, int timeout_ms);
+
+/* Times of one request (seconds): submit to finish; the part spent building its
+ * operator while it waited (near field or clone; 0 if the operator was resident);
+ * the solve of its batch; the rest, waiting in the queue. */
+typedef struct {
+    double latency_s, build_s, solve_s, queue_s;
+} pm_request_times;
+pm_status pm_server_wait_ex(pm_server* sv, unsigned long long ticket, double* u,
+                            pm_solve_info* info, pm_request_times* times, int timeout_ms);
 pm_status pm_server_stats(pm_server* sv, long long* batches, long long* solved,
                           long long* max_batch, size_t* bytes_in_use);
+/* Operator builds so far, bytes reserved now, the free-memory margin, operators known. */
+pm_status pm_server_stats_ex(pm_server* sv, long long* builds, size_t* reserved_bytes,
+                             size_t* margin_bytes, int* operators);
 
 /*
  * Smooth remainder sum without any allocation.
@@ -466,14 +525,18 @@ pm_status pm_server_stats(pm_server* sv, long long* batches, long long* solved,
  *   stream              cudaStream_t (NULL: legacy default stream); asynchronous
  * Scratch: the packed sources/targets and per-split partial sums live in one
  * file-scope device array of 4 MiB that every GPU loading the library holds
- * until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  Every call overwrites the parts it
- * reads, so nothing must be cleared between calls, but all calls share the one
- * array: calls that overlap on the GPU (different streams, or different host
- * threads, on the same device) race and corrupt each other's results.  The call
- * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
- * Requires |s[j]| < 1e8 and distinct node positions.
+ * until the process exits.  Each call made outside stream capture looks up that
+ * array's device address in the current context (cudaGetSymbolAddress, which
+ * allocates nothing) and remembers it for the device; a call made while the
+ * stream is being captured uses the address remembered from the last
+ * uncaptured call on that device, so make one call on each device before any
+ * stream capture (otherwise the captured call returns PM_ERR_INVALID_ARG).
+ * Every call overwrites the parts it reads, so nothing must be cleared between
+ * calls, but all calls share the one array: calls that overlap on the GPU
+ * (different streams, or different host threads, on the same device) race and
+ * corrupt each other's results.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  Requires distinct node positions;
+ * the j = i term is an exact zero for any finite strength.
  */
 pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, const float* n,
                                           const float* H, const float* a,

@@ -285,6 +285,27 @@ class Server:
         self._sizes[t.value] = op.N
         return t.value
 
+    def submit_desc(self, geometry_id: int, coeff_id: int, surface, a, grad_a, f, tol=1e-8,
+                    prec="fp32", opts=None):
+        """Submit a request on an operator the server builds (or reuses) itself from a
+        surface fixture (npatch, p, nodes, normals, tangents, curvature, weights) and a
+        coefficient, keyed by the caller's geometry and coefficient ids."""
+        N = surface.npatch * surface.p ** 2
+        arrs = [_f64(surface.nodes, 3 * N), _f64(surface.normals, 3 * N),
+                _f64(surface.tangents, 6 * N), _f64(surface.curvature, N),
+                _f64(surface.weights, N), _f64(a, N),
+                None if grad_a is None else _f64(grad_a, 3 * N)]
+        d = _lib.PmOperatorDesc(int(geometry_id), int(coeff_id), int(surface.npatch),
+                                int(surface.p), *[ptr(x) for x in arrs],
+                                C.pointer(opts) if opts is not None else None)
+        f = _f64(f, N)
+        t = C.c_ulonglong()
+        prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        check(_lib.lib().pm_server_submit_desc(self.handle, C.byref(d), ptr(f), float(tol), prec,
+                                               C.byref(t)), "pm_server_submit_desc")
+        self._sizes[t.value] = N
+        return t.value
+
     def poll(self, ticket):
         d = C.c_int()
         check(_lib.lib().pm_server_poll(self.handle, C.c_ulonglong(ticket), C.byref(d)),
@@ -293,21 +314,33 @@ class Server:
 
     def wait(self, ticket, timeout_ms=-1):
         """(u, info, latency_seconds) of a finished request."""
-        u = np.empty(self._sizes.pop(ticket))
+        u, info, t = self.wait_ex(ticket, timeout_ms)
+        return u, info, t["latency_s"]
+
+    def wait_ex(self, ticket, timeout_ms=-1):
+        """(u, info, times) of a finished request; times holds latency_s, build_s
+        (building its operator while it waited), solve_s and queue_s."""
+        u = np.empty(self._sizes[ticket])
         info = PmSolveInfo()
-        lat = C.c_double()
-        check(_lib.lib().pm_server_wait(self.handle, C.c_ulonglong(ticket), ptr(u),
-                                        C.byref(info), C.byref(lat), int(timeout_ms)),
-              "pm_server_wait")
-        return u, info, lat.value
+        tm = _lib.PmRequestTimes()
+        st = _lib.lib().pm_server_wait_ex(self.handle, C.c_ulonglong(ticket), ptr(u),
+                                          C.byref(info), C.byref(tm), int(timeout_ms))
+        if st != _lib.PM_ERR_TIMEOUT:
+            self._sizes.pop(ticket, None)
+        check(st, "pm_server_wait")
+        return u, info, {f: getattr(tm, f) for f, _ in tm._fields_}
 
     def stats(self):
         b, s, m = C.c_longlong(), C.c_longlong(), C.c_longlong()
         used = C.c_size_t()
         check(_lib.lib().pm_server_stats(self.handle, C.byref(b), C.byref(s), C.byref(m),
                                          C.byref(used)), "pm_server_stats")
+        nb, res, mar, nop = C.c_longlong(), C.c_size_t(), C.c_size_t(), C.c_int()
+        check(_lib.lib().pm_server_stats_ex(self.handle, C.byref(nb), C.byref(res), C.byref(mar),
+                                            C.byref(nop)), "pm_server_stats_ex")
         return {"batches": b.value, "solved": s.value, "max_batch": m.value,
-                "bytes_in_use": used.value}
+                "bytes_in_use": used.value, "builds": nb.value, "margin_bytes": mar.value,
+                "operators": nop.value}
 
     def close(self):
         if self.handle:

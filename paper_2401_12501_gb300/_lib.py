@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libparametrix.so")
 
 PM_OK = 0
+PM_ERR_TIMEOUT = 7
 PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF, PM_PREC_FMM = 0, 1, 2, 3, 4
 PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
 PM_SOLVE_PROJECT_RHS = 1
@@ -34,12 +35,14 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_status_str", "pm_last_error", "pm_profile_enable", "pm_profile_read",
            "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
            "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
-           "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_surface_set_knobs",
+           "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_server_submit_desc",
+           "pm_server_wait_ex", "pm_server_stats_ex", "pm_surface_set_knobs",
            "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info", "pm_surface_clone",
            "pm_selftest_fmm_classes", "pm_selftest_tc_gemm", "pm_selftest_green",
            "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
- PM_PHASE_DIRECT64) = range(6)
+ PM_PHASE_DIRECT64, PM_PHASE_FMM_M2L, PM_PHASE_FMM_P2P, PM_PHASE_DIRECT64_K,
+ PM_PHASE_COUNT) = range(10)
 
 
 class PmOpts(C.Structure):
@@ -69,6 +72,19 @@ class PmKnobs(C.Structure):
 class PmTuneResult(C.Structure):
     _fields_ = [("best", PmKnobs), ("best_ms", C.c_double), ("default_ms", C.c_double),
                 ("candidates", C.c_int)]
+
+
+class PmRequestTimes(C.Structure):
+    _fields_ = [("latency_s", C.c_double), ("build_s", C.c_double), ("solve_s", C.c_double),
+                ("queue_s", C.c_double)]
+
+
+class PmOperatorDesc(C.Structure):
+    _fields_ = [("geometry_id", C.c_ulonglong), ("coeff_id", C.c_ulonglong),
+                ("npatch", C.c_int), ("p", C.c_int),
+                ("nodes", C.c_void_p), ("normals", C.c_void_p), ("tangents", C.c_void_p),
+                ("curvature", C.c_void_p), ("weights", C.c_void_p), ("a", C.c_void_p),
+                ("grad_a", C.c_void_p), ("opts", C.POINTER(PmOpts))]
 
 
 class PmError(RuntimeError):
@@ -115,6 +131,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                    C.POINTER(C.c_double), C.c_int]
     lib.pm_server_stats.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                     C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]
+    lib.pm_server_submit_desc.argtypes = [P, C.POINTER(PmOperatorDesc), P, C.c_double, C.c_int,
+                                          C.POINTER(C.c_ulonglong)]
+    lib.pm_server_wait_ex.argtypes = [P, C.c_ulonglong, P, C.POINTER(PmSolveInfo),
+                                      C.POINTER(PmRequestTimes), C.c_int]
+    lib.pm_server_stats_ex.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_size_t),
+                                       C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]
     lib.pm_smooth_remainder_f32_noalloc.argtypes = [C.c_int, P, P, P, P, P, P, P, P]
     lib.pm_surface_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]

@@ -314,6 +314,27 @@ static void free_surface(pm_surface* s) {
 
 extern "C" void pm_surface_destroy(pm_surface* s) { free_surface(s); }
 
+// Device bytes a new operator of npatch patches of order p would hold (model of
+// the allocations of pm_surface_create + pm_surface_set_coeff, or of a clone +
+// set_coeff): geometry and packed source/target arrays, the smooth sums' partial
+// slices, the near-field CSR and coefficient-free weights with about 6 near patch
+// blocks per node (the test surfaces have 3.9-4.9), and the coefficient-dependent
+// corrections.  A clone holds only the per-coefficient part.
+size_t pm_operator_need_bytes(int npatch, int p, int clone) {
+    const size_t pp = (size_t)p * p, ppad = (pp + 3) / 4 * 4;
+    const size_t N = (size_t)npatch * pp, Npad = (N + 255) / 256 * 256;
+    const size_t nblk = 6 * N;
+    const size_t nt = (N + 127) / 128;
+    const size_t split = std::max<size_t>(32, nt * N * sizeof(float2) <= (size_t)kSymPartialCap ? nt : 0);
+    const size_t per_coeff =
+        sizeof(double) * (5 * N + nblk * pp * 2 + split * N) + sizeof(float) * (nblk * ppad * 2) +
+        sizeof(float) * (size_t)npatch * ppad + Npad * (sizeof(float4) + sizeof(pm_d4)) +
+        sizeof(float4) * (3 * N + 2 * N + 6 * N + 2 * N + 128);
+    const size_t shared = sizeof(double) * (11 * N + 4 * (size_t)npatch + nblk * pp * 5) +
+                          sizeof(int) * (N + 1 + 2 * nblk) + ((size_t)1 << 20);
+    return clone ? per_coeff : per_coeff + shared;
+}
+
 // per-surface scratch of the smooth sums (a clone allocates its own)
 static pm_status alloc_scratch(pm_surface* s) {
     const size_t N = s->N;
@@ -614,7 +635,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
     }
     if (smooth) {
         PhaseTimer t(s, prec == PM_PREC_FP64 || prec == PM_PREC_FF
-                            ? PM_PHASE_DIRECT64
+                            ? (kernel_K ? PM_PHASE_DIRECT64_K : PM_PHASE_DIRECT64)
                             : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
         const int nt = pm_sym_tiles(s);
         if (prec == PM_PREC_FF && nt > 0) {

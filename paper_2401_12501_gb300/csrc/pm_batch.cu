@@ -541,7 +541,7 @@ pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long 
             k_prep_ff_multi<<<gp, 256, 0, st>>>(sigma, ld_sigma, s->wa, B.sff, N, skip);
         }
         {
-            PhaseTimer t(s, PM_PHASE_DIRECT64, st);
+            PhaseTimer t(s, kernel_K ? PM_PHASE_DIRECT64_K : PM_PHASE_DIRECT64, st);
             dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(nrhs, rbff));
             const int chunk = pm_ceil_div(N, ns);
             const float4* srcv = kernel_K ? s->src_kg : s->src_ff;
@@ -1057,6 +1057,24 @@ struct BSolver {
 }  // namespace
 
 // Batched solve of nrhs right-hand sides (same surface and coefficient), in lockstep.
+// Device bytes a batched solve of nrhs right-hand sides would allocate on top of
+// the surface's current batched buffers (bsolve_work and batch_ensure above).
+size_t pm_batch_need_bytes(const pm_surface* s, int nrhs) {
+    const size_t m = (size_t)std::max(2, std::min(s->opts.gmres_restart, 400));
+    const size_t N = (size_t)s->N, R = (size_t)nrhs;
+    size_t need = 0;
+    if (!(s->bsolve && (size_t)s->bsolve->nrhs >= R && (size_t)s->bsolve->m == m)) {
+        const size_t nred = (size_t)std::max(1, std::min(pm_ceil_div(s->N, 2048), 64));
+        need += sizeof(double) * (R * (m + 1) * N + R * (m * (m + 2) + 3 * m + 1) +
+                                  R * nred * (m + 2) + R * (m + 2 + 16) + 8 * R * N) +
+                sizeof(int) * (2 * R + 1);
+    }
+    if (!(s->batch && s->batch->cap >= nrhs))
+        need += R * N * (sizeof(float) + sizeof(float2) + 8 * sizeof(float2)) +
+                R * (size_t)s->npatch * s->ppad * sizeof(float);
+    return need;
+}
+
 pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, double tol,
                          int maxit, pm_precision prec, unsigned flags, double* sigma_out,
                          pm_solve_info* info, cudaStream_t st) {

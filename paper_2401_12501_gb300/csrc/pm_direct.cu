@@ -156,7 +156,9 @@ k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
                     const float nr = fmaf(nx[t], dx, fmaf(ny[t], dy, nz[t] * dz));
                     const float mr = fmaf(mx[t], dx, fmaf(my[t], dy, mz[t] * dz));
                     const float inner = fmaf(nr, nr * inv, mr);
-                    part[t] = fmaf(s.w * inv, inner, part[t]);
+                    // inv * inner first: the self pair (r = 0, inner = 0) then adds an
+                    // exact zero whatever the strength, where s.w * inv could overflow
+                    part[t] = fmaf(s.w, inv * inner, part[t]);
                 }
             }
 #pragma unroll
@@ -426,10 +428,20 @@ extern "C" pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, cons
         pm_set_error("pm_smooth_remainder_f32_noalloc: device %d beyond %d", dev, kNoAllocMaxDevices);
         return PM_ERR_INVALID_ARG;
     }
+    // the scratch's device address in the current context: looked up again on every
+    // call made outside stream capture (cudaGetSymbolAddress allocates nothing), so a
+    // context reset or another context on the device cannot leave a stale address;
+    // during capture the address of the last uncaptured call on this device is used
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;            // unknown: do not query the symbol
+    }
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -438,6 +450,10 @@ extern "C" pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, cons
                 return PM_ERR_CUDA;
             }
             g_noalloc_ptr[dev] = p;
+        } else if (!g_noalloc_ptr[dev]) {
+            pm_set_error("pm_smooth_remainder_f32_noalloc: the first call on device %d was made "
+                         "during stream capture; make one call outside capture first", dev);
+            return PM_ERR_INVALID_ARG;
         }
         base = g_noalloc_ptr[dev];
     }
@@ -445,7 +461,6 @@ extern "C" pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, cons
     float4* src = reinterpret_cast<float4*>(b);
     float4* tgt = reinterpret_cast<float4*>(b + kNoAllocSrcBytes);
     float2* part = reinterpret_cast<float2*>(b + kNoAllocSrcBytes + kNoAllocTgtBytes);
-    cudaStream_t st = (cudaStream_t)stream;
     // every (split, target < N) partial and every packed entry < N is written
     // before it is read, so nothing in the scratch needs clearing between calls
     int dev_sms = 0;
@@ -456,8 +471,9 @@ extern "C" pm_status pm_smooth_remainder_f32_noalloc(int N, const float* x, cons
     const int chunk = pm_ceil_div(N, nsplit);
     k_noalloc_pack<<<pm_ceil_div(N, 256), 256, 0, st>>>(N, x, n, H, a, grad_a, s, src, tgt);
     dim3 grid(tblocks, nsplit);
-    // self-pair guard: the j == i term is exactly zero (n'.r = m.r = 0) while r^2 = 1e-30
-    // keeps 1/r^2 finite; it is far below the squared distance of any two distinct nodes
+    // self-pair guard: the j == i term is exactly zero (n'.r = m.r = 0, and the kernel
+    // forms (1/r^2) * 0 before multiplying by the strength) while r^2 = 1e-30 keeps
+    // 1/r^2 finite; 1e-30 is far below the squared distance of any two distinct nodes
     const float eps2 = 1e-30f;
     k_direct_R32<2><<<grid, kThreads, 0, st>>>(src, tgt, N, chunk, eps2, part, nullptr);
     k_noalloc_reduce<<<pm_ceil_div(N, 256), 256, 0, st>>>(N, nsplit, part, out);

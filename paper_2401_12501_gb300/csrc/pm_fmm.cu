@@ -760,6 +760,19 @@ void pm_fmm_free(pm_surface* s) {
     s->fmm = nullptr;
 }
 
+// Device bytes the FMM of a surface would allocate on its first apply: the tree
+// (sorted sources, multipoles, locals, the gathered M2L columns B (float16) and
+// results C (float32), lists), modelled as 3 KB per node + 64 MB, and the
+// context's unit-box M2L operators (float16, both kernel families) if they do
+// not exist yet.  The torus of 98,304 nodes allocates ~0.25 GB of tree.
+size_t pm_fmm_need_bytes(const pm_surface* s) {
+    size_t need = 0;
+    if (!s->fmm) need += 3072 * (size_t)s->N + ((size_t)64 << 20);
+    if (!s->ctx->fmm_opR) need += (size_t)kNClass * 9 * kFmmN3 * kSplitK * sizeof(__half);
+    if (!s->ctx->fmm_opK) need += (size_t)kNClass * kFmmN3 * kSplitK * sizeof(__half);
+    return need;
+}
+
 pm_status pm_fmm_check(pm_surface* s) {
     if (!s->fmm) return PM_OK;
     for (int k = 0; k < 2; ++k)
@@ -1267,7 +1280,10 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
             k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, T->vsym, T->M, T->Bm,
                                                          T->colscale, skip);
         PM_CUDA_TRY(cudaGetLastError());
-        PM_TRY(pm_tcgemm_run(&T->gemm[which_K], s->ctx->num_sms, skip, st));
+        {
+            PhaseTimer pt(s, PM_PHASE_FMM_M2L, st);
+            PM_TRY(pm_tcgemm_run(&T->gemm[which_K], s->ctx->num_sms, skip, st));
+        }
         if (which_K)
             k_fmm_m2l_scatter<true><<<dim3(nm2l, 1), kThreads, 0, st>>>(
                 t, b2, T->Cm, T->vcol, T->vsym, T->colscale, T->msum, T->Lc, skip);
@@ -1289,11 +1305,16 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     }
     float2* out = reinterpret_cast<float2*>(s->partial);
     const int g2 = T->np2p;
+    {
+        PhaseTimer pt(s, PM_PHASE_FMM_P2P, st);
+        if (which_K)
+            k_fmm_p2p<true><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
+        else
+            k_fmm_p2p<false><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
+    }
     if (which_K) {
-        k_fmm_p2p<true><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
         k_fmm_l2p<true><<<T->nchunks, kL2PThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
     } else {
-        k_fmm_p2p<false><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
         k_fmm_l2p<false><<<T->nchunks, kL2PThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
     }
     s->launch_total += 5 + 2 * std::max(0, depth - 2);

@@ -216,7 +216,8 @@ pm_status pm_fmm_build(pm_surface* s);
 int pm_fmm_splits();
 pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st);
 void pm_fmm_free(pm_surface* s);
-pm_status pm_fmm_check(pm_surface* s);   // reads the tensor-core M2L error words (synchronises)
+pm_status pm_fmm_check(pm_surface* s);
+size_t pm_fmm_need_bytes(const pm_surface* s);       // first-apply allocation model   // reads the tensor-core M2L error words (synchronises)
 
 // tensor-core GEMM (pm_tcgemm.cu): C[(bcol0 + j) * ldc + crow0 + r] =
 // sum_k A[arow0 + r][k] B[bcol0 + j][k] for r < 128, j < ncols over a list of
@@ -246,6 +247,7 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
                          pm_solve_info* info, cudaStream_t st);
 void pm_batch_free(pm_surface* s);
 void pm_batch_solve_free(pm_surface* s);
+size_t pm_batch_need_bytes(const pm_surface* s, int nrhs);
 
 // solve (pm_solve.cu)
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,
@@ -253,6 +255,8 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
                         pm_solve_info* info, cudaStream_t st);
 
 void pm_solve_free(pm_surface* s);
+// device bytes a solve of nrhs right-hand sides would newly allocate (model)
+size_t pm_solve_need_bytes(const pm_surface* s, int nrhs, pm_precision prec);
 
 // Bound on the relative error of a float32 (or FMM) operator apply against the
 // float64 operator, |(A32 - A) v| <= kOpRelErr |v|: measured errors are below
@@ -272,6 +276,7 @@ pm_status pm_apply_dev(pm_surface* s, int part_mask_K, int smooth, int near,
                        const double* sigma, double* out, pm_precision prec,
                        cudaStream_t st, int prepped = 0);
 pm_status pm_ensure_scratch(pm_surface* s, size_t n);
+size_t pm_operator_need_bytes(int npatch, int p, int clone);   // device bytes of a new operator (model)
 
 // Records an event pair around the launches in its scope when profiling is on.
 struct PhaseTimer {

@@ -612,7 +612,13 @@ __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
 
 }  // namespace
 
+// The quadrature tables live in one __constant__ copy per device, written here
+// for the surface's order p: builds are serialised (several host threads may
+// create surfaces at once, e.g. the server's workers).
+static std::mutex g_near_build_mu;
+
 pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
+    std::lock_guard<std::mutex> build_lock(g_near_build_mu);
     const int N = s->N, npatch = s->npatch, p = s->p, pp = s->pp;
     PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
     PM_TRY(pm_dmalloc(&s->centroid, 3 * (size_t)npatch));

@@ -792,6 +792,32 @@ struct Solver {
 
 }  // namespace
 
+// Device bytes a solve of nrhs right-hand sides would allocate on top of what
+// the surface already holds (its Krylov workspaces are kept between solves and
+// only grow): the single-RHS workspace of get_work, or the batched solver's and
+// batched apply's buffers (pm_batch.cu), plus the FMM tree and the context's M2L
+// operators when FMM applies are used and not yet built.  An a-priori model of
+// the allocations above, not a measurement.
+size_t pm_solve_need_bytes(const pm_surface* s, int nrhs, pm_precision prec) {
+    const size_t m = (size_t)std::max(2, std::min(s->opts.gmres_restart, 400));
+    const size_t N = (size_t)s->N;
+    size_t need = 0;
+    if (nrhs <= 1) {
+        const bool held = s->solve_work && (size_t)s->solve_work->m == m;
+        if (!held) {
+            const size_t nred = (size_t)std::max(1, std::min(pm_ceil_div(s->N, 1024),
+                                                             2 * s->ctx->num_sms));
+            const size_t narn = (size_t)pm_ceil_div(s->N, kArnThreads);
+            need += sizeof(double) * ((m + 1) * N + m * (m + 2) + 4 * m + 8 * N +
+                                      (nred + 3 * narn + 2) * (m + 2) + 64);
+        }
+    } else {
+        need += pm_batch_need_bytes(s, nrhs);
+    }
+    if (prec == PM_PREC_FMM) need += pm_fmm_need_bytes(s);
+    return need;
+}
+
 pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, int maxit,
                         pm_precision prec, unsigned flags, double* sigma_out,
                         pm_solve_info* info, cudaStream_t st) {
