@@ -777,124 +777,157 @@ def run_fmm(args, dev):
     return res
 
 
-def _snap_surface(family, n_target, rng):
-    """Snap a drawn size to a factor-of-2 ladder of surfaces of the family (p = 8).
+# Served geometries: a ladder over 1.5k-400k nodes, both patch orders and all four
+# families (family, p, surface parameters, N).  A request's size is drawn
+# log-uniformly over [1,500, 400,000] and snapped to the nearest rung in log N, so
+# the rung fixes its family and p; two coefficient fields per geometry.
+SERVE_LADDER = [("sphere", 8, 2, 1536), ("ellipsoid", 10, 4, 9600), ("star", 8, 8, 24576),
+                ("torus", 10, (32, 12), 38400), ("ellipsoid", 8, 16, 98304),
+                ("star", 10, 16, 153600), ("torus", 8, (128, 48), 393216)]
 
-    Sizes stay log-uniform in the drawn range, but operators recur, so a served
-    surface keeps its geometry and near field resident across requests."""
+
+def _ladder_surface(rung):
     from workloads import cubed_sphere, star_surface, torus
-    p = 8
-    ladder = 1536 * 2.0 ** np.arange(0, 12)
-    n_b = float(ladder[np.argmin(np.abs(np.log(ladder / n_target)))])
-    if family == "torus":
-        nph = max(3, int(round(np.sqrt(n_b / (p * p) * 3 / 8))))
-        nth = max(3, int(round(nph * 8 / 3)))
-        return ("torus", p, nth, nph), lambda: torus(nth, nph, p)
-    m = max(1, int(round(np.sqrt(n_b / (6 * p * p)))))
-    if family == "sphere":
-        return ("sphere", p, m), lambda: cubed_sphere(m, p)
-    if family == "ellipsoid":
-        return ("ellipsoid", p, m), lambda: cubed_sphere(m, p, axes=(1.0, 1.5, 2.0))
-    return ("star", p, m), lambda: star_surface(m, p)
-
-
-import numpy as np  # noqa: E402  (used by the serving helpers)
+    fam, p, par, _ = rung
+    if fam == "sphere":
+        return cubed_sphere(par, p)
+    if fam == "ellipsoid":
+        return cubed_sphere(par, p, axes=(1.0, 1.5, 2.0))
+    if fam == "star":
+        return star_surface(par, p)
+    return torus(par[0], par[1], p)
 
 
 def run_served(args, dev):
-    """Poisson arrivals of solve requests over a pool of operators; batched server
-    vs a one-request-at-a-time server on the same arrival trace."""
+    """Poisson arrivals of solve requests on operators the server builds itself from
+    their descriptions (near field per geometry, clone per further coefficient), FMM
+    applies from serve_fmm_min nodes, GMRES to serve_tol on the apply-precision
+    operator (no float-float refinement: float32/FMM applies + float64 GMRES).
+    One server: a cold run (operators built as their first requests arrive; build
+    time reported apart), then on the resident operators continuous batching vs one
+    request at a time, at the arrival rate and with every request at t = 0."""
     import threading as th
+    import numpy as np
     import paper_2401_12501_gb300 as pm
     from workloads import random_harmonic_rhs, smooth_random_coefficient
     rng = np.random.default_rng(0)
     n_req, rate = args.serve_requests, args.serve_rate
-    fams = ["sphere", "ellipsoid", "torus", "star"]
     lo, hi = np.log(1500.0), np.log(float(args.serve_nmax))
-    keys, draws = {}, []
+    logs = np.log([r[3] for r in SERVE_LADDER])
+    draws = []
     for _ in range(n_req):
-        fam = fams[int(rng.integers(0, 4))]
-        key, mk = _snap_surface(fam, float(np.exp(rng.uniform(lo, hi))), rng)
-        cseed = int(rng.integers(0, 2))
-        keys.setdefault((key, cseed), mk)
-        draws.append(((key, cseed), int(rng.integers(0, 1 << 30))))
+        n = float(np.exp(rng.uniform(lo, hi)))
+        k = int(np.argmin(np.abs(logs - np.log(n))))
+        draws.append((k, int(rng.integers(0, 2)), int(rng.integers(0, 1 << 30))))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    used = sorted({d[0] for d in draws})
+    surfs = {k: _ladder_surface(SERVE_LADDER[k]) for k in used}
+    coeffs = {(k, c): smooth_random_coefficient(surfs[k], c) for k in used for c in (0, 1)}
+    rhs = [random_harmonic_rhs(surfs[k], fs % 1000, n_terms=20, lmax=12) for k, _, fs in draws]
+    opts = pm.default_opts()
+    opts.residual_prec = pm.PM_PREC_FP32                # GMRES on the apply-precision operator
+    prec = ["fmm" if surfs[k].N >= args.serve_fmm_min else "fp32" for k, _, _ in draws]
     ctx = pm.Context(dev.index or 0)
-    ops, builds, rhs = {}, [], {}
-    geo = {}            # one near-field build per geometry; other coefficient seeds clone it
-    for k, mk in sorted(keys.items(), key=lambda kv: (str(kv[0][0]), kv[0][1])):
-        t0 = time.perf_counter()
-        if k[0] in geo:
-            surf, base = geo[k[0]]
-            op = base.clone()
-        else:
-            surf = mk()
-            op = pm.Surface.from_fixture(ctx, surf)
-            geo[k[0]] = (surf, op)
-        co = smooth_random_coefficient(surf, k[1])
-        op.set_coeff(co.a, co.grad_a)
-        builds.append(time.perf_counter() - t0)
-        ops[k] = (surf, op)
-    for i, (k, fseed) in enumerate(draws):
-        surf = ops[k][0]
-        rhs[i] = random_harmonic_rhs(surf, fseed % 1000, n_terms=20, lmax=12)
+    sv = pm.Server(ctx, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30), max_batch=64,
+                   n_workers=4)
 
-    def serve(max_batch, n_workers, arrivals=arrivals):
-        sv = pm.Server(ctx, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30),
-                       max_batch=max_batch, n_workers=n_workers)
+    def submit(i):
+        k, c, _ = draws[i]
+        co = coeffs[(k, c)]
+        return sv.submit_desc(k, c, surfs[k], co.a, co.grad_a, rhs[i], tol=args.serve_tol,
+                              prec=prec[i], opts=opts)
+
+    keep = {next(j for j, d in enumerate(draws) if d[0] == k): None for k in used}
+
+    def serve(max_batch, n_workers, arr, keep_u=False):
+        sv.configure(max_batch, n_workers)
+        b0 = sv.stats()["batches"]
         tickets = [None] * n_req
         t_start = time.perf_counter()
 
         def client():
             for i in range(n_req):
-                dt = arrivals[i] - (time.perf_counter() - t_start)
+                dt = arr[i] - (time.perf_counter() - t_start)
                 if dt > 0:
                     time.sleep(dt)
-                op = ops[draws[i][0]][1]
-                prec = "fmm" if op.N >= args.serve_fmm_min else "fp32"
-                tickets[i] = sv.submit(op, rhs[i], tol=args.serve_tol, prec=prec)
+                tickets[i] = submit(i)
 
         c = th.Thread(target=client)
         c.start()
-        lat, res = [], []
+        lat, lat_nb, builds, res, sizes = [], [], [], [], []
         for i in range(n_req):
             while tickets[i] is None:
                 time.sleep(0.0005)
-            u, info, l = sv.wait(tickets[i])
-            lat.append(l)
+            u, info, tm = sv.wait_ex(tickets[i])
+            if keep_u and i in keep:
+                keep[i] = u
+            lat.append(tm["latency_s"])
+            lat_nb.append(tm["latency_s"] - tm["build_s"])
+            builds.append(tm["build_s"])
             res.append(info.residual)
         c.join()
         wall = time.perf_counter() - t_start
         st = sv.stats()
-        sv.close()
-        lat = np.array(lat)
-        return {"p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
-                "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
-                "solves_per_s": round(n_req / wall, 2), "wall_s": round(wall, 3),
-                "batches": st["batches"], "max_batch": st["max_batch"],
-                "max_residual": float(max(res))}
+        lat, lat_nb = np.array(lat), np.array(lat_nb)
+        out = {"p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+               "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+               "solves_per_s": round(n_req / wall, 2), "wall_s": round(wall, 3),
+               "batches": st["batches"] - b0, "max_batch_seen": st["max_batch"],
+               "max_residual": float(max(res))}
+        if max(builds) > 0:
+            out["build_wait_s_total"] = round(float(sum(builds)), 3)
+            out["requests_waiting_on_a_build"] = int(sum(b > 0 for b in builds))
+            out["p50_latency_ms_excluding_build_wait"] = round(float(np.percentile(lat_nb, 50)) * 1e3, 2)
+            out["p99_latency_ms_excluding_build_wait"] = round(float(np.percentile(lat_nb, 99)) * 1e3, 2)
+        return out
 
-    served = serve(max_batch=64, n_workers=4)
-    plain = serve(max_batch=1, n_workers=1)
-    # the same requests all submitted at t = 0: throughput with a full queue
+    t0 = time.perf_counter()
+    cold = serve(64, 4, arrivals)
+    t_cold = time.perf_counter() - t0
+    n_builds = sv.stats()["builds"]
+    served = serve(64, 4, arrivals, keep_u=True)
+    plain = serve(1, 1, arrivals)
     zero = np.zeros(n_req)
-    sat_served = serve(max_batch=64, n_workers=4, arrivals=zero)
-    sat_plain = serve(max_batch=1, n_workers=1, arrivals=zero)
-    for _, op in ops.values():
-        op.close()
-    sizes = sorted(s.N for s, _ in ops.values())
+    sat_served = serve(64, 4, zero)
+    sat_plain = serve(1, 1, zero)
+    sv.close()
+    # accuracy of the served apply-precision solutions (one request per rung up to
+    # 100k nodes, from the continuous-batching run) against float-float refined
+    # solves of the same systems on caller-built operators
+    acc = {}
+    for i, u_op in keep.items():
+        k, c, _ = draws[i]
+        if surfs[k].N > 100000:
+            continue
+        co = coeffs[(k, c)]
+        s = pm.Surface.from_fixture(ctx, surfs[k])
+        s.set_coeff(co.a, co.grad_a)
+        u_ff, _ = s.solve(rhs[i], tol=1e-10, prec=prec[i])
+        s.close()
+        w = surfs[k].weights
+        acc[f"{SERVE_LADDER[k][0]}_{SERVE_LADDER[k][3]}_p{SERVE_LADDER[k][1]}"] = float(
+            np.sqrt(np.dot(w, (u_op - u_ff) ** 2) / np.dot(w, u_ff ** 2)))
+    ctx.close()
+    counts = {f"{SERVE_LADDER[k][0]}_{SERVE_LADDER[k][3]}_p{SERVE_LADDER[k][1]}":
+              sum(d[0] == k for d in draws) for k in used}
     return {"requests": n_req, "arrival_rate_per_s": rate, "seed": 0,
-            "operators": len(ops), "geometries": len(geo), "node_range": [sizes[0], sizes[-1]],
-            "n_max_drawn": args.serve_nmax, "tol": args.serve_tol,
-            "fmm_applies_from_n": args.serve_fmm_min,
-            "near_build_s_total": round(sum(builds), 3),
-            "near_build_s_max": round(max(builds), 3),
+            "geometries": len(used), "operators": 2 * len(used),
+            "node_range": [min(surfs[k].N for k in used), max(surfs[k].N for k in used)],
+            "patch_orders": sorted({SERVE_LADDER[k][1] for k in used}),
+            "requests_per_geometry": counts, "n_max_drawn": args.serve_nmax,
+            "tol": args.serve_tol, "fmm_applies_from_n": args.serve_fmm_min,
+            "solve": "GMRES (float64 basis) to tol on the float32 / FMM operator, "
+                     "no float-float refinement (opts.residual_prec = PM_PREC_FP32)",
+            "u_rel_err_vs_float_float_refined_solve": acc,
+            "admission": "by free HBM: cudaMemGetInfo less a margin, modelled bytes per "
+                         "build and batch, budget cap %.0f GiB" % args.serve_budget_gb,
+            "cold_run_with_in_server_builds": {**cold, "operator_builds_near_field_or_clone": n_builds,
+                                               "run_s": round(t_cold, 3)},
             "continuous_batching": served, "one_at_a_time": plain,
             "solves_per_s_ratio": round(served["solves_per_s"] / plain["solves_per_s"], 2),
             "saturated": {"continuous_batching": sat_served, "one_at_a_time": sat_plain,
                           "solves_per_s_ratio": round(sat_served["solves_per_s"]
                                                       / sat_plain["solves_per_s"], 2)}}
-
 
 
 def run_micro_tc_gemm(args):
@@ -940,9 +973,9 @@ def main():
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-nmax", type=int, default=30000)
+    ap.add_argument("--serve-nmax", type=int, default=400000)
     ap.add_argument("--serve-tol", type=float, default=1e-8)
-    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
     ap.add_argument("--micro", choices=["tc_gemm"], default=None,

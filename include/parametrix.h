@@ -88,7 +88,11 @@ typedef struct {
     double mean_tol;        /* pm_solve: |sum w f| / (sqrt(sum w) ||f||_w) above which f
                                is rejected as not mean zero; 1e-8                       */
     int residual_prec;      /* pm_solve: precision of true residuals and of u = K~ sigma
-                               (PM_PREC_FF or PM_PREC_FP64); default PM_PREC_FF         */
+                               (PM_PREC_FF or PM_PREC_FP64; default PM_PREC_FF).
+                               PM_PREC_FP32: a float32 or FMM solve takes both in its own
+                               operator precision -- GMRES (float64 basis) to tol on the
+                               float32 / FMM operator, no float-float refinement; u then
+                               carries that operator's error (~1e-5 relative)            */
     int fmm_depth;          /* PM_PREC_FMM: octree depth (2..8); 0 = chosen by a cost model */
     int batch_rhs;          /* nrhs > 1: 1 = batched kernels and lockstep GMRES over all
                                right-hand sides (default), 0 = one right-hand side at a time */
@@ -500,6 +504,11 @@ pm_status pm_server_wait_ex(pm_server* sv, unsigned long long ticket, double* u,
                             pm_solve_info* info, pm_request_times* times, int timeout_ms);
 pm_status pm_server_stats(pm_server* sv, long long* batches, long long* solved,
                           long long* max_batch, size_t* bytes_in_use);
+/* Change the batch limit and the number of workers that take new work (1 ..
+ * n_workers of pm_server_create; the others idle) for batches formed from now
+ * on; the operators the server holds stay resident.  PM_ERR_INVALID_ARG outside
+ * those ranges. */
+pm_status pm_server_configure(pm_server* sv, int max_batch, int active_workers);
 /* Operator builds so far, bytes reserved now, the free-memory margin, operators known. */
 pm_status pm_server_stats_ex(pm_server* sv, long long* builds, size_t* reserved_bytes,
                              size_t* margin_bytes, int* operators);

@@ -330,6 +330,11 @@ class Server:
         check(st, "pm_server_wait")
         return u, info, {f: getattr(tm, f) for f, _ in tm._fields_}
 
+    def configure(self, max_batch: int, active_workers: int):
+        """Batch limit and number of working workers for batches formed from now on."""
+        check(_lib.lib().pm_server_configure(self.handle, int(max_batch), int(active_workers)),
+              "pm_server_configure")
+
     def stats(self):
         b, s, m = C.c_longlong(), C.c_longlong(), C.c_longlong()
         used = C.c_size_t()

@@ -36,7 +36,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
            "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
            "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_server_submit_desc",
-           "pm_server_wait_ex", "pm_server_stats_ex", "pm_surface_set_knobs",
+           "pm_server_wait_ex", "pm_server_stats_ex", "pm_server_configure", "pm_surface_set_knobs",
            "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info", "pm_surface_clone",
            "pm_selftest_fmm_classes", "pm_selftest_tc_gemm", "pm_selftest_green",
            "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32"]
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                           C.POINTER(C.c_ulonglong)]
     lib.pm_server_wait_ex.argtypes = [P, C.c_ulonglong, P, C.POINTER(PmSolveInfo),
                                       C.POINTER(PmRequestTimes), C.c_int]
+    lib.pm_server_configure.argtypes = [P, C.c_int, C.c_int]
     lib.pm_server_stats_ex.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_size_t), C.POINTER(C.c_int)]
     lib.pm_selftest_fflog.argtypes = [P, P, P, C.c_int, P]

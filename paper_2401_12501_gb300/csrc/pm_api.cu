@@ -264,7 +264,8 @@ extern "C" void pm_ctx_destroy(pm_ctx* c) {
 // Buffers a surface shares with its clones: built once, read-only afterwards.
 #define PM_SHARED_FIELDS(X)                                                          \
     X(x) X(n) X(H) X(w) X(J) X(npatch_n) X(centroid) X(radius) X(row_ptr) X(blk_patch) \
-    X(blk_row) X(W_lb) X(W_g) X(W_k) X(dev_err) X(th_off) X(th_ang) X(th_w) X(th_L)
+    X(blk_row) X(W_lb) X(W_g) X(W_k) X(dev_err) X(th_off) X(th_ang) X(th_w) X(th_L)   \
+    X(nu_ptr) X(nu_list) X(nu_blk)
 
 PmSharedBuffers::~PmSharedBuffers() {
     cudaSetDevice(device);
@@ -299,6 +300,7 @@ static void free_surface(pm_surface* s) {
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);
     pm_dfree(s->W_lb); pm_dfree(s->W_g); pm_dfree(s->W_k); pm_dfree(s->dev_err);
+    pm_dfree(s->nu_ptr); pm_dfree(s->nu_list); pm_dfree(s->nu_blk);
     pm_dfree(s->th_off); pm_dfree(s->th_ang); pm_dfree(s->th_w); pm_dfree(s->th_L);
     pm_dfree(s->a); pm_dfree(s->g); pm_dfree(s->wa); pm_dfree(s->src32); pm_dfree(s->tgt32);
     pm_dfree(s->src64); pm_dfree(s->cR64); pm_dfree(s->cK64); pm_dfree(s->cR32);
@@ -498,6 +500,7 @@ extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
     s->h_w = src->h_w;
     s->h_tg = src->h_tg;
     s->nblk = src->nblk;
+    s->nu_max = src->nu_max;
     s->nth_total = src->nth_total;
     s->batch_rb = src->batch_rb;
     s->batch_bps = src->batch_bps;

@@ -920,9 +920,14 @@ struct BSolver {
     int nrhs;
     cudaStream_t st;
     int grid_n;
+    pm_precision op = PM_PREC_FF;   // the solve's operator precision
 
+    // precision of true residuals and of the representation (see pm_solve.cu)
     pm_precision residual_prec() const {
-        return s->opts.residual_prec == PM_PREC_FP64 ? PM_PREC_FP64 : PM_PREC_FF;
+        if (s->opts.residual_prec == PM_PREC_FP64) return PM_PREC_FP64;
+        if (s->opts.residual_prec == PM_PREC_FP32 && (op == PM_PREC_FP32 || op == PM_PREC_FMM))
+            return op;
+        return PM_PREC_FF;
     }
 
     // dst[r*lddst + j] = A_r,j . b_r for j < ncols
@@ -1084,6 +1089,7 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
     PmBatchSolveWork& W = *Wp;
     const int N = s->N;
     BSolver S{s, W, nrhs, st, pm_ceil_div(N, 256)};
+    S.op = prec;
     const bool dev = (flags & PM_SOLVE_DEVICE_PTRS) != 0;
     PM_CUDA_TRY(cudaMemcpyAsync(W.f, f, sizeof(double) * (size_t)nrhs * N,
                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -1166,11 +1172,12 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
             result = PM_ERR_NOT_CONVERGED;
         }
     // u = K~ sigma (accurate), minus its weighted mean
-    if (S.residual_prec() == PM_PREC_FP64) {
+    const pm_precision rp = S.residual_prec();
+    if (rp == PM_PREC_FP64 || rp == PM_PREC_FMM) {
         for (int r = 0; r < nrhs; ++r)
-            PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig + (size_t)r * N, W.u + (size_t)r * N, PM_PREC_FP64, st));
+            PM_TRY(pm_apply_dev(s, 1, 1, 1, W.sig + (size_t)r * N, W.u + (size_t)r * N, rp, st));
     } else {
-        PM_TRY(pm_apply_batch(s, 1, W.sig, N, W.u, N, nrhs, PM_PREC_FF, st));
+        PM_TRY(pm_apply_batch(s, 1, W.sig, N, W.u, N, nrhs, rp, st));
     }
     S.dots(s->w, 0, 0, 1, W.u, N, W.dots + 6, 8, nullptr);
     k_bshift<<<dim3(S.grid_n, nrhs), 256, 0, st>>>(W.u, W.dots + 6, 8, -1.0 / sw, N);

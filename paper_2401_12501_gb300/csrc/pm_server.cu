@@ -95,6 +95,7 @@ struct pm_server {
     std::map<unsigned long long, Operator*> geometry;  // first built operator of each geometry
     unsigned long long next_ticket = 1;
     int in_flight = 0;
+    int active_workers = 0;            // workers with an index below this take work
     bool stopping = false;
     std::vector<std::thread> workers;
     long long batches = 0, solved = 0, max_batch_seen = 0, builds = 0;
@@ -123,7 +124,7 @@ void finish_request(Request* r, pm_status st, const std::string& err) {
     r->t_end = Clock::now();
 }
 
-void worker_main(pm_server* sv) {
+void worker_main(pm_server* sv, int index) {
     cudaSetDevice(sv->ctx->device);
     cudaStream_t st = nullptr;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -140,6 +141,10 @@ void worker_main(pm_server* sv) {
                 if (sv->stopping) {
                     if (st) cudaStreamDestroy(st);
                     return;
+                }
+                if (index >= sv->active_workers) {
+                    sv->cv_work.wait(lk);
+                    continue;
                 }
                 // requests of operators whose build failed end with the build's status
                 for (auto it = sv->queue.begin(); it != sv->queue.end();) {
@@ -352,7 +357,8 @@ extern "C" pm_status pm_server_create(pm_ctx* ctx, size_t hbm_budget_bytes, int 
     sv->budget = hbm_budget_bytes;
     sv->margin = std::max<size_t>((size_t)256 << 20, tot / 50);
     sv->max_batch = max_batch;
-    for (int k = 0; k < n_workers; ++k) sv->workers.emplace_back(worker_main, sv);
+    sv->active_workers = n_workers;
+    for (int k = 0; k < n_workers; ++k) sv->workers.emplace_back(worker_main, sv, k);
     *out = sv;
     return PM_OK;
 }
@@ -526,6 +532,22 @@ extern "C" pm_status pm_server_stats(pm_server* sv, long long* batches, long lon
     if (solved) *solved = sv->solved;
     if (max_batch) *max_batch = sv->max_batch_seen;
     if (bytes_in_use) *bytes_in_use = sv->reserved;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_server_configure(pm_server* sv, int max_batch, int active_workers) {
+    if (!sv || max_batch < 1 || active_workers < 1 ||
+        active_workers > (int)sv->workers.size()) {
+        pm_set_error("pm_server_configure: max_batch >= 1 and 1 <= active_workers <= %d required",
+                     sv ? (int)sv->workers.size() : 0);
+        return PM_ERR_INVALID_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->max_batch = max_batch;
+        sv->active_workers = active_workers;
+    }
+    sv->cv_work.notify_all();
     return PM_OK;
 }
 

@@ -498,9 +498,15 @@ struct Solver {
     Work& W;
     cudaStream_t st;
     int grid_n;
+    pm_precision op = PM_PREC_FF;   // the solve's operator precision
 
+    // precision of true residuals and of the representation: float64 or float-float,
+    // or (opts.residual_prec = PM_PREC_FP32) the float32 / FMM operator itself
     pm_precision residual_prec() const {
-        return s->opts.residual_prec == PM_PREC_FP64 ? PM_PREC_FP64 : PM_PREC_FF;
+        if (s->opts.residual_prec == PM_PREC_FP64) return PM_PREC_FP64;
+        if (s->opts.residual_prec == PM_PREC_FP32 && (op == PM_PREC_FP32 || op == PM_PREC_FMM))
+            return op;
+        return PM_PREC_FF;
     }
 
     // dst[0..ncols) = columns(A) . b (deterministic two-pass reduction)
@@ -828,6 +834,7 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
     const int N = s->N;
     const bool dev = (flags & PM_SOLVE_DEVICE_PTRS) != 0;
     Solver S{s, W, st, pm_ceil_div(N, 256)};
+    S.op = prec;
     const cudaMemcpyKind h2d = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     PM_CUDA_TRY(cudaMemcpyAsync(W.f, f, sizeof(double) * N, h2d, st));

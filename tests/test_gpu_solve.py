@@ -244,3 +244,38 @@ def test_advection_through_the_gradient_input(ctx):
             assert rel_l2(sig, so, w) < 1e-8, prec
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fmm"])
+def test_operator_precision_residuals(ctx, prec):
+    """opts.residual_prec = PM_PREC_FP32: GMRES to tol on the float32 / FMM operator itself
+    (no float-float refinement).  The reported residual is that operator's, u differs from
+    the refined solve by the operator's error (a few 1e-6 relative, within the 1e-5 float32
+    apply tolerance), the solve is deterministic, and nrhs > 1 gives the same as solving
+    one at a time."""
+    import paper_2401_12501_gb300 as pm
+    wl = make_workload("ellipsoid_9600")
+    o = pm.default_opts()
+    o.residual_prec = pm.PM_PREC_FP32
+    s = pm.Surface.from_fixture(ctx, wl.surface, o)
+    ref = pm.Surface.from_fixture(ctx, wl.surface)
+    try:
+        for t in (s, ref):
+            t.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+        w = wl.surface.weights
+        u, info = s.solve(wl.f, tol=1e-8, prec=prec)
+        u2, _ = s.solve(wl.f, tol=1e-8, prec=prec)
+        u_ff, info_ff = ref.solve(wl.f, tol=1e-10, prec=prec)
+        assert info[0].residual <= 1e-8
+        assert np.array_equal(u, u2)
+        assert 1e-9 < rel_l2(u, u_ff, w) < 1e-5
+        F = np.stack([wl.f, np.roll(wl.f, 501)])
+        F -= (F @ w)[:, None] / w.sum()
+        U, infos = s.solve(F, tol=1e-8, prec=prec)
+        for k in range(2):
+            alone, _ = s.solve(F[k], tol=1e-8, prec=prec)
+            assert infos[k].residual <= 1e-8
+            assert rel_l2(U[k], alone, w) < 5e-7
+    finally:
+        s.close()
+        ref.close()
