@@ -609,10 +609,9 @@ constexpr size_t kPatchSmemCap = 96 * 1024;             // its largest sigma uni
 // contiguous range), L lanes per row.  The union of the patch rows' near patches'
 // sigma is staged in shared memory first, together with the rows' CSR offsets,
 // so every global load of a row (partial slices, correction values, each block's
-// union index) is independent of the others and of sigma: each lane issues all
-// of its loads (up to 4 partial slices and U float4 values per pass) before it
-// consumes any.  Rows are reduced within their lane group in a fixed order
-// (deterministic).
+// union index) is independent of the others and of sigma; a lane issues U float4
+// value loads (and their union indices) per pass before it consumes any.  Rows
+// are reduced within their lane group in a fixed order (deterministic).
 template <int L, int U>
 __global__ void __launch_bounds__(64 * L)
 k_near_patch32(int N, int pp, int ppad, int cta_per_patch, const int* __restrict__ row_ptr,
@@ -644,13 +643,14 @@ k_near_patch32(int N, int pp, int ppad, int cta_per_patch, const int* __restrict
         const int r = r0 + (int)threadIdx.x / L;
         const bool row_ok = r < pp;
         const int i = P * pp + (row_ok ? r : 0);
-        float2 pv[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int sp = hl + k * L;
-            pv[k] = (row_ok && sp < nsplit) ? __ldg(partial + (size_t)sp * N + i)
-                                            : make_float2(0.f, 0.f);
-        }
+        float hi = 0.f, lo = 0.f, s, e;
+        if (row_ok)
+            for (int sp = hl; sp < nsplit; sp += L) {
+                const float2 v = __ldg(partial + (size_t)sp * N + i);
+                two_sum(hi, v.x, s, e);
+                hi = s;
+                lo += e + v.y;
+            }
         float acc = 0.f;
         if (use_near && row_ok) {
             const int rb = srp[r];
@@ -660,37 +660,24 @@ k_near_patch32(int N, int pp, int ppad, int cta_per_patch, const int* __restrict
                 int xo[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int e = e0 + u * L + hl;
-                    if (e < total) {
-                        const int b = e / q4;
-                        v[u] = __ldg(v4 + (size_t)rb * q4 + e);
-                        xo[u] = __ldg(nu_blk + rb + b) * q4 + (e - b * q4);
+                    const int q = e0 + u * L + hl;
+                    if (q < total) {
+                        const int b = q / q4;
+                        v[u] = __ldg(v4 + (size_t)rb * q4 + q);
+                        xo[u] = __ldg(nu_blk + rb + b) * q4 + (q - b * q4);
                     } else {
                         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        xo[u] = 0;
+                        xo[u] = -1;
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const float4 x = sh4[xo[u]];
-                    acc = fmaf(v[u].x, x.x, fmaf(v[u].y, x.y, fmaf(v[u].z, x.z, fmaf(v[u].w, x.w, acc))));
-                }
+                for (int u = 0; u < U; ++u)
+                    if (xo[u] >= 0) {
+                        const float4 x = sh4[xo[u]];
+                        acc = fmaf(v[u].x, x.x, fmaf(v[u].y, x.y, fmaf(v[u].z, x.z, fmaf(v[u].w, x.w, acc))));
+                    }
             }
         }
-        float hi = 0.f, lo = 0.f, s, e;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            two_sum(hi, pv[k].x, s, e);
-            hi = s;
-            lo += e + pv[k].y;
-        }
-        if (row_ok)
-            for (int sp = hl + 4 * L; sp < nsplit; sp += L) {
-                const float2 v = __ldg(partial + (size_t)sp * N + i);
-                two_sum(hi, v.x, s, e);
-                hi = s;
-                lo += e + v.y;
-            }
         two_sum(hi, acc, s, e);
         hi = s;
         lo += e;
