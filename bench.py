@@ -41,8 +41,7 @@ FP32_LANES_PER_SM = 128    # FP32 lanes of one sm_100-family SM
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the current kernel versions on a workload; set to None whenever the kernel changes
 # until it is captured again.
-TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 624128,
-                 ("k_direct_ff_R", "ellipsoid_9600"): 1236224,
+TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): None,      # kernel changed: recapture
                  ("k_sym_ff_R", "ellipsoid_9600"): 1299712}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
@@ -599,6 +598,36 @@ def run_batched(args, dev):
     torch.cuda.synchronize()
     t_fields = time.perf_counter() - t0
 
+    # all 8 fields x 8 right-hand sides in one multi-instance lockstep batch: every
+    # field's applies in the same launches, each GMRES cycle one CUDA graph
+    # its launch shape (fields of a geometry per smooth-sum item = right-hand sides per
+    # block / 8, blocks per SM) picked by timing a few candidates on the whole solve;
+    # the per-field knobs are restored afterwards
+    knobs0 = ops[0].knobs()
+    multi_tune = {}
+    for rbk, bps in ((8, 8), (16, 8), (16, 12), (32, 8)):
+        if args.no_autotune and (rbk, bps) != (16, 8):
+            continue
+        ops[0].set_knobs(batch_rhs_per_block=rbk, batch_blocks_per_sm=bps)
+        pm.solve_multi(ops, Fk, tol=args.tol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pm.solve_multi(ops, Fk, tol=args.tol)
+        torch.cuda.synchronize()
+        multi_tune[(rbk, bps)] = time.perf_counter() - t0
+    best = min(multi_tune, key=multi_tune.get)
+    ops[0].set_knobs(batch_rhs_per_block=best[0], batch_blocks_per_sm=best[1])
+    pm.solve_multi(ops, Fk, tol=args.tol)
+    torch.cuda.synchronize()
+    reps_m = 3
+    t0 = time.perf_counter()
+    for _ in range(reps_m):
+        _, minfo = pm.solve_multi(ops, Fk, tol=args.tol)
+    torch.cuda.synchronize()
+    t_multi = (time.perf_counter() - t0) / reps_m
+    res += [i.residual for inf in minfo for i in inf]
+    ops[0].set_knobs(**knobs0)
+
     # continuous-batching server, all 64 requests at t = 0 (operators overlap)
     F_host = [F[r] for r in range(n_rhs)]
 
@@ -640,6 +669,15 @@ def run_batched(args, dev):
                             "(multi-RHS sums sharing each pair's geometry), fields one after "
                             "another",
             "speedup_vs_plain": round(t_plain * n_rhs / t_fields, 2),
+            "multi_instance_solves_per_s": round(n_rhs / t_multi, 2),
+            "multi_instance_form": "pm_solve_multi: the 8 operators' 64 right-hand sides in one "
+                                   "lockstep GMRES, each Arnoldi step's float32 applies of all "
+                                   "operators in one persistent smooth-sum launch over a work "
+                                   "list + one near-field launch, each cycle one CUDA graph",
+            "multi_instance_speedup_vs_plain": round(t_plain * n_rhs / t_multi, 2),
+            "multi_instance_tuned": {"fields_per_item": best[0] // 8, "blocks_per_sm": best[1],
+                                     "candidates_ms": {f"{k[0] // 8}x{k[1]}": round(v * 1e3, 2)
+                                                       for k, v in multi_tune.items()}},
             "served_all_at_once_solves_per_s": round(n_rhs / t_served, 2),
             "one_field_64_rhs_solves_per_s": round(n_rhs / t_one_field, 2),
             "max_residual": max(max(res), res_served, max(i.residual for i in info)),

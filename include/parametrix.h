@@ -308,6 +308,30 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
                    pm_solve_info* info, void* stream);
 
 /*
+ * Solve several operators' systems together (the batched form across operators):
+ * ops[k] u_k,r = f_k,r for r < nrhs[k], k < nops, as one lockstep GMRES over all
+ * sum(nrhs) right-hand sides, with the float32 operator applies of every instance in
+ * the same launches (one persistent smooth-sum launch over a work list of (instance,
+ * target tile, right-hand-side group, source chunk) items, one near-field launch) and
+ * each GMRES cycle replayed as one CUDA graph.  The operators may differ in geometry,
+ * size and coefficient; each must appear once (give it several right-hand sides
+ * instead), belong to one context and have its coefficient set.  f[k], u[k]: [nrhs[k]
+ * * N_k] row-major per right-hand side, host arrays (device arrays with
+ * PM_SOLVE_DEVICE_PTRS).  prec must be PM_PREC_FP32; solver options (restart length,
+ * refinements, inner tolerance, residual update, mean tolerance and residual
+ * precision: float-float refinement, or the float32 operator itself with
+ * residual_prec = PM_PREC_FP32) are those of ops[0].  info (nullable) receives
+ * sum(nrhs) entries in instance order; iterations count the lockstep Arnoldi steps.
+ * The launch shape (right-hand sides per block, blocks per SM) is ops[0]'s batched
+ * knobs (pm_surface_set_knobs / pm_surface_autotune).  One multi-instance solve runs
+ * at a time per context (its workspace is the context's).  Errors as pm_solve, plus
+ * PM_ERR_INVALID_ARG for a repeated operator, another context or another precision.
+ */
+pm_status pm_solve_multi(pm_surface* const* ops, int nops, const int* nrhs,
+                         const double* const* f, double* const* u, double tol, int maxit,
+                         pm_precision prec, unsigned flags, pm_solve_info* info, void* stream);
+
+/*
  * Per-phase kernel timing.  While enabled, the library records a pair of CUDA
  * events on the launching stream around every launch of each phase; reading
  * synchronises on those events and returns the summed milliseconds and the

@@ -266,6 +266,50 @@ class Surface:
         return out + (sig,) if return_sigma else out
 
 
+def solve_multi(surfaces, rhs, tol=1e-10, maxit=2000, project_rhs=False, stream=None):
+    """Solve several operators' systems in one lockstep batch (pm_solve_multi).
+
+    surfaces: list of Surface (distinct, one context); rhs: list of arrays, rhs[k] of
+    shape [nrhs_k, N_k] (or [N_k]) -- numpy (host) or CUDA torch tensors (all device or
+    all host).  Returns (list of u with the shapes of rhs, list of info per instance)."""
+    n = len(surfaces)
+    if n != len(rhs) or n == 0:
+        raise ValueError("one right-hand-side array per surface")
+    dev = _is_device(rhs[0])
+    fs, us, nr = [], [], []
+    for s, f in zip(surfaces, rhs):
+        if dev:
+            import torch
+            f = f.contiguous().to(torch.float64)
+            k = f.numel() // s.N
+            u = torch.empty_like(f)
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            k = f.size // s.N
+            u = np.empty_like(f)
+        if k * s.N != (f.numel() if dev else f.size) or k < 1:
+            raise ValueError("right-hand sides must be [nrhs, N] of their surface")
+        fs.append(f)
+        us.append(u)
+        nr.append(k)
+    ops = (C.c_void_p * n)(*[s.handle.value for s in surfaces])
+    fp = (C.c_void_p * n)(*[ptr(f).value for f in fs])
+    up = (C.c_void_p * n)(*[ptr(u).value for u in us])
+    nrc = (C.c_int * n)(*nr)
+    infos = (PmSolveInfo * sum(nr))()
+    flags = (PM_SOLVE_PROJECT_RHS if project_rhs else 0) | (PM_SOLVE_DEVICE_PTRS if dev else 0)
+    if dev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream(fs[0].device).cuda_stream
+    check(_lib.lib().pm_solve_multi(ops, n, nrc, fp, up, float(tol), int(maxit), PM_PREC_FP32,
+                                    flags, infos, C.c_void_p(stream)), "pm_solve_multi")
+    out_info, c = [], 0
+    for k in nr:
+        out_info.append(list(infos[c:c + k]))
+        c += k
+    return us, out_info
+
+
 class Server:
     """pm_server: continuous batching of solve requests over many operators."""
 

@@ -36,7 +36,7 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_surface_tune", "pm_selftest_fflog", "pm_smooth_remainder_f32_noalloc",
            "pm_surface_fmm_stats", "pm_server_create", "pm_server_destroy", "pm_server_submit",
            "pm_server_poll", "pm_server_wait", "pm_server_stats", "pm_server_submit_desc",
-           "pm_server_wait_ex", "pm_server_stats_ex", "pm_server_configure", "pm_surface_set_knobs",
+           "pm_server_wait_ex", "pm_server_stats_ex", "pm_server_configure", "pm_solve_multi", "pm_surface_set_knobs",
            "pm_surface_get_knobs", "pm_surface_autotune", "pm_ctx_info", "pm_surface_clone",
            "pm_selftest_fmm_classes", "pm_selftest_tc_gemm", "pm_selftest_green",
            "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32"]
@@ -148,6 +148,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_get_near.argtypes = [P, P, P, P, P]
     lib.pm_solve.argtypes = [P, P, P, C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint,
                              P, C.POINTER(PmSolveInfo), P]
+    lib.pm_solve_multi.argtypes = [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(P),
+                                   C.POINTER(P), C.c_double, C.c_int, C.c_int, C.c_uint,
+                                   C.POINTER(PmSolveInfo), P]
     lib.pm_profile_enable.argtypes = [P, C.c_int]
     lib.pm_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
     lib.pm_status_str.argtypes = [C.c_int]

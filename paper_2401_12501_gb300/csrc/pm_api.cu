@@ -257,6 +257,7 @@ extern "C" void pm_ctx_destroy(pm_ctx* c) {
     cudaSetDevice(c->device);
     pm_dfree(c->fmm_opR);
     pm_dfree(c->fmm_opK);
+    pm_multi_free(c);
     delete c;
 }
 

@@ -15,6 +15,8 @@
 #include "pm_ff.cuh"
 #include "pm_internal.cuh"
 
+#include <map>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -853,9 +855,7 @@ struct PmBatchSolveWork {
     int* pinned_i = nullptr;
 };
 
-void pm_batch_solve_free(pm_surface* s) {
-    if (!s->bsolve) return;
-    PmBatchSolveWork& W = *s->bsolve;
+static void bsolve_release(PmBatchSolveWork& W) {
     pm_dfree(W.V); pm_dfree(W.H); pm_dfree(W.cs); pm_dfree(W.sn); pm_dfree(W.g); pm_dfree(W.y);
     pm_dfree(W.part); pm_dfree(W.scal); pm_dfree(W.hcol); pm_dfree(W.dots); pm_dfree(W.w);
     pm_dfree(W.tmp); pm_dfree(W.r); pm_dfree(W.res); pm_dfree(W.delta); pm_dfree(W.sig);
@@ -864,20 +864,19 @@ void pm_batch_solve_free(pm_surface* s) {
     if (W.pinned_y) cudaFreeHost(W.pinned_y);
     if (W.pinned) cudaFreeHost(W.pinned);
     if (W.pinned_i) cudaFreeHost(W.pinned_i);
+    W.pinned_y = W.pinned = nullptr;
+    W.pinned_i = nullptr;
+}
+
+void pm_batch_solve_free(pm_surface* s) {
+    if (!s->bsolve) return;
+    bsolve_release(*s->bsolve);
     delete s->bsolve;
     s->bsolve = nullptr;
 }
 
-static pm_status bsolve_work(pm_surface* s, int nrhs, PmBatchSolveWork** out) {
-    const int m = std::max(2, std::min(s->opts.gmres_restart, 400));
-    if (s->bsolve && s->bsolve->nrhs >= nrhs && s->bsolve->m == m) {
-        *out = s->bsolve;
-        return PM_OK;
-    }
-    pm_batch_solve_free(s);
-    s->bsolve = new PmBatchSolveWork();
-    PmBatchSolveWork& W = *s->bsolve;
-    const int N = s->N;
+// buffers of a lockstep solve of nrhs columns of length N (restart m)
+static pm_status bsolve_alloc(PmBatchSolveWork& W, int nrhs, int m, int N) {
     W.nrhs = nrhs;
     W.m = m;
     W.N = N;
@@ -908,7 +907,19 @@ static pm_status bsolve_work(pm_surface* s, int nrhs, PmBatchSolveWork** out) {
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_y, sizeof(double) * (size_t)nrhs));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, sizeof(double) * 8 * (size_t)nrhs));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_i, sizeof(int) * (2 * (size_t)nrhs + 4)));
-    *out = &W;
+    return PM_OK;
+}
+
+static pm_status bsolve_work(pm_surface* s, int nrhs, PmBatchSolveWork** out) {
+    const int m = std::max(2, std::min(s->opts.gmres_restart, 400));
+    if (s->bsolve && s->bsolve->nrhs >= nrhs && s->bsolve->m == m) {
+        *out = s->bsolve;
+        return PM_OK;
+    }
+    pm_batch_solve_free(s);
+    s->bsolve = new PmBatchSolveWork();
+    PM_TRY(bsolve_alloc(*s->bsolve, nrhs, m, s->N));
+    *out = s->bsolve;
     return PM_OK;
 }
 
@@ -1196,6 +1207,996 @@ pm_status pm_solve_batch(pm_surface* s, const double* f, double* u, int nrhs, do
             info[r].removed_mean = removed[r];
             info[r].seconds = secs;
             info[r].residual_updates = updated;
+        }
+    return result;
+}
+
+// ============================================================================ multi-instance solve
+// One lockstep GMRES over the right-hand sides of several operators ("instances",
+// surfaces of any size and coefficient).  Column c = (instance k, right-hand side
+// r) of every vector has the stride Nmax of the largest instance; rows N_k..Nmax
+// of a column are zero and stay zero (the applies write rows < N_k only, and every
+// vector kernel maps zeros to zeros), so the batched vector kernels above serve
+// instances of uneven size unchanged.  Each Arnoldi step's operator apply is
+// three launches for all instances together: the prep of every column, ONE
+// persistent launch of the float32 smooth sums over a device work list of
+// (instance, 128-target tile, group of RB right-hand sides, source chunk) items,
+// and one launch of the near-field corrections with the split reduction (a warp
+// per (instance, right-hand side, row)).  A whole GMRES cycle -- every Arnoldi
+// step, the Givens updates and the correction -- is one CUDA graph, captured once
+// per cycle length and replayed (finished columns skip their work through the
+// done flags, a finished batch every launch through all_done).
+namespace {
+
+constexpr int kMultiGroupMax = 64;   // instances per geometry in one multi-instance solve
+
+struct MInst {
+    const float4* pos;         // float32 source positions of the instance (src32)
+    const float4* tgt;         // float32 target factors [3 N] (tgt32)
+    const double* wa;          // w / a
+    const int* row_ptr;        // near-field CSR
+    const int* blk_patch;
+    const float* vals;         // float32 remainder corrections (cR32)
+    const int* nu_ptr;         // per patch, the union of its rows' near patches
+    const int* nu_list;
+    const int* nu_blk;         // per correction block, its index in that union
+    const float4* fac;         // [N] (grad a/(2 pi), a/pi): remainder factors (k_mfactors)
+    const float* facB;         // [N] -a H/pi
+    float* s32;                // [nrhs][N] strengths
+    float* sig32;              // [nrhs][npatch][ppad] sigma by patch
+    float2* part;              // [nrhs][nsplit][N] partial sums
+    float eps2;
+    int N, npatch, pp, ppad, nrhs, col0, nsplit, chunk;
+    long long warp0;           // first near-field warp (instance-major, rhs, row)
+};
+
+__global__ void k_mprep32(const double* __restrict__ sigma, long long ld_sigma,
+                          const MInst* __restrict__ I, const int* __restrict__ col_inst,
+                          const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int c = blockIdx.y;
+    const MInst& in = I[col_inst[c]];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= in.N) return;
+    const int r = c - in.col0;
+    const double v = sigma[c * ld_sigma + j];
+    in.s32[(size_t)r * in.N + j] = (float)(in.wa[j] * v);
+    const int P = j / in.pp;
+    in.sig32[((size_t)r * in.npatch + P) * in.ppad + (j - P * in.pp)] = (float)v;
+}
+
+// Per-instance remainder factors for the shared-geometry sums: with the unit
+// normal n and r = x_i - x_j, the remainder pair factor of eq. explicit_remainder
+// (c = 0) is  inv (A (n.r)^2 inv + B (n.r) + g.r),  inv = 1/|r|^2, A = a_i/pi,
+// B = -a_i H_i/pi, g = grad a_i/(2 pi): only A, B, g depend on the coefficient.
+// fac[i] = (g, A), facB[i] = B; nrm[i] = n (float32).
+__global__ void k_mfactors(const double* __restrict__ a, const double* __restrict__ H,
+                           const double* __restrict__ g, const double* __restrict__ n, int N,
+                           float4* __restrict__ fac, float* __restrict__ facB,
+                           float4* __restrict__ nrm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double c2 = 0.5 / M_PI;
+    fac[i] = make_float4((float)(c2 * g[3 * i]), (float)(c2 * g[3 * i + 1]),
+                         (float)(c2 * g[3 * i + 2]), (float)(a[i] / M_PI));
+    facB[i] = (float)(-a[i] * H[i] / M_PI);
+    if (nrm) nrm[i] = make_float4((float)n[3 * i], (float)n[3 * i + 1], (float)n[3 * i + 2], 0.f);
+}
+
+struct MGroup {                // instances on one geometry (a surface and its clones)
+    const float4* pos;         // source positions (float32)
+    const float4* tgt;         // target positions [N] (float32)
+    const float4* nrm;         // unit normals [N]
+    int N, nsplit, chunk, ninst;
+    int inst[kMultiGroupMax];  // instance indices, in column order
+    float eps2;
+};
+
+// persistent float32 remainder sums sharing each pair's geometry across the
+// coefficient fields of a geometry: block b takes items b, b + gridDim.x, ...;
+// item = (group, target tile, source chunk, block of FB fields x RB right-hand sides).
+// Per pair: r, 1/r^2, n.r and (n.r)^2 / r^2 once; per field A, B, g; per right-hand
+// side one FMA.
+template <int FB, int RB>
+__global__ void __launch_bounds__(kThreads)
+k_mgeo32(const MGroup* __restrict__ G, const MInst* __restrict__ I,
+         const int4* __restrict__ items, int nitems, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    static_assert(RB % 4 == 0 && RB >= 4, "RB right-hand sides in float4 groups");
+    constexpr int kSt = (FB * RB <= 16) ? kStage : kStage / 2;
+    __shared__ float4 sP[kSt];
+    __shared__ float4 sS[kSt][FB * RB / 4];
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];          // (group, tile, split, field block * 4096 + rhs block)
+        const MGroup& gr = G[w.x];
+        const int N = gr.N;
+        const int i = w.y * kThreads + tid;
+        const int f0 = (w.w >> 12) * FB, r0 = (w.w & 4095) * RB;
+        const int nf = min(FB, gr.ninst - f0);
+        int nrr[FB];
+        float A[FB], B[FB], gx[FB], gy[FB], gz[FB];
+        float tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0;
+        if (i < N) {
+            const float4 a = gr.tgt[i], b = gr.nrm[i];
+            tx = a.x; ty = a.y; tz = a.z;
+            nx = b.x; ny = b.y; nz = b.z;
+        }
+#pragma unroll
+        for (int f = 0; f < FB; ++f) {
+            nrr[f] = 0;
+            A[f] = B[f] = gx[f] = gy[f] = gz[f] = 0.f;
+            if (f < nf) {
+                const int k = gr.inst[f0 + f];
+                nrr[f] = max(0, min(RB, I[k].nrhs - r0));
+                if (i < N) {
+                    const float4 q = I[k].fac[i];                 // (g, A) of field k
+                    gx[f] = q.x; gy[f] = q.y; gz[f] = q.z; A[f] = q.w;
+                    B[f] = I[k].facB[i];
+                }
+            }
+        }
+        float hi[FB * RB], lo[FB * RB];
+#pragma unroll
+        for (int q = 0; q < FB * RB; ++q) hi[q] = lo[q] = 0.f;
+        const int s0 = w.z * gr.chunk;
+        const int s1 = min(s0 + gr.chunk, N);
+        for (int base = s0; base < s1; base += kSt) {
+            const int len = min(kSt, s1 - base);
+            __syncthreads();
+            for (int j = tid; j < len; j += kThreads) {
+                sP[j] = gr.pos[base + j];
+#pragma unroll
+                for (int f = 0; f < FB; ++f) {
+                    float v[RB];
+                    const float* sf = (f < nf) ? I[gr.inst[f0 + f]].s32 : nullptr;
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        v[q] = (q < nrr[f]) ? sf[(size_t)(r0 + q) * N + base + j] : 0.f;
+#pragma unroll
+                    for (int q = 0; q < RB / 4; ++q)
+                        sS[j][f * (RB / 4) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < len; j0 += kTile) {
+                const int j1 = min(j0 + kTile, len);
+                float part[FB * RB];
+#pragma unroll
+                for (int q = 0; q < FB * RB; ++q) part[q] = 0.f;
+#pragma unroll 2
+                for (int j = j0; j < j1; ++j) {
+                    const float4 p = sP[j];
+                    const float dx = tx - p.x, dy = ty - p.y, dz = tz - p.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, gr.eps2)));
+                    const float inv = rcp_approx(r2);
+                    const float nr = fmaf(nx, dx, fmaf(ny, dy, nz * dz));
+                    const float t1 = nr * nr * inv;
+#pragma unroll
+                    for (int f = 0; f < FB; ++f) {
+                        if (f >= nf) break;
+                        const float gr_ = fmaf(gx[f], dx, fmaf(gy[f], dy, gz[f] * dz));
+                        const float gfac = inv * fmaf(A[f], t1, fmaf(B[f], nr, gr_));
+#pragma unroll
+                        for (int q = 0; q < RB / 4; ++q) {
+                            const float4 sv = sS[j][f * (RB / 4) + q];
+                            float* pq = part + f * RB + 4 * q;
+                            pq[0] = fmaf(sv.x, gfac, pq[0]);
+                            pq[1] = fmaf(sv.y, gfac, pq[1]);
+                            pq[2] = fmaf(sv.z, gfac, pq[2]);
+                            pq[3] = fmaf(sv.w, gfac, pq[3]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < FB * RB; ++q) two_sum_acc(hi[q], lo[q], part[q]);
+            }
+        }
+        if (i < N) {
+#pragma unroll
+            for (int f = 0; f < FB; ++f) {
+                if (f >= nf) break;
+                const MInst& in = I[gr.inst[f0 + f]];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < nrr[f])
+                        in.part[((size_t)(r0 + q) * in.nsplit + w.z) * N + i] =
+                            make_float2(hi[f * RB + q], lo[f * RB + q]);
+            }
+        }
+        __syncthreads();                 // the next item restages the shared arrays
+    }
+}
+
+// out[(col0 + r) * ld_out + i] = sum_s part[r][s][i] + near corrections; a warp per
+// (instance, rhs, row), the instance found by bisection on warp0
+__global__ void __launch_bounds__(256)
+k_mnear32(const MInst* __restrict__ I, int ninst, long long nwarps, double* __restrict__ out,
+          long long ld_out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nwarps) return;
+    int lo_k = 0, hi_k = ninst - 1;
+    while (lo_k < hi_k) {
+        const int mid = (lo_k + hi_k + 1) >> 1;
+        if (I[mid].warp0 <= warp) lo_k = mid; else hi_k = mid - 1;
+    }
+    const MInst& in = I[lo_k];
+    const long long local = warp - in.warp0;
+    const int r = (int)(local / in.N), i = (int)(local - (long long)r * in.N);
+    float hi = 0.f, lo = 0.f;
+    for (int sp = lane; sp < in.nsplit; sp += 32) {
+        const float2 v = in.part[((size_t)r * in.nsplit + sp) * in.N + i];
+        two_sum_acc(hi, lo, v.x);
+        lo += v.y;
+    }
+    const int q4 = in.ppad >> 2;
+    const int rb = in.row_ptr[i];
+    const int total = (in.row_ptr[i + 1] - rb) * q4;
+    const float4* v4 = reinterpret_cast<const float4*>(in.vals) + (size_t)rb * q4;
+    const float4* s4 = reinterpret_cast<const float4*>(in.sig32 + (size_t)r * in.npatch * in.ppad);
+    float acc = 0.f;
+    for (int e = lane; e < total; e += 32) {
+        const int b = e / q4;
+        const float4 v = __ldg(v4 + e);
+        const float4 x = __ldg(s4 + (size_t)in.blk_patch[rb + b] * q4 + (e - b * q4));
+        acc = fmaf(v.x, x.x, fmaf(v.y, x.y, fmaf(v.z, x.z, fmaf(v.w, x.w, acc))));
+    }
+    two_sum_acc(hi, lo, acc);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        two_sum_acc(hi, lo, h2);
+        lo += l2;
+    }
+    if (lane == 0) out[(size_t)(in.col0 + r) * ld_out + i] = (double)hi + (double)lo;
+}
+
+// The same for surfaces with patch unions: block = (instance, patch, chunk of R
+// right-hand sides) from a work list; sigma of the union of the patch rows' near
+// patches staged for the R right-hand sides ([node][rhs], stride R + 1), each
+// correction value read once per R right-hand sides (lane = sub-row * R + rhs).
+template <int R>
+__global__ void __launch_bounds__(256)
+k_mnear32_patch(const MInst* __restrict__ I, const int4* __restrict__ items,
+                double* __restrict__ out, long long ld_out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    static_assert(32 % R == 0, "R divides the warp");
+    constexpr int kSub = 32 / R;
+    constexpr int kLd = R + 1;
+    extern __shared__ float shs[];
+    const int4 w = items[blockIdx.x];          // (instance, patch, first rhs, -)
+    const MInst& in = I[w.x];
+    const int P = w.y, r0 = w.z;
+    const int nr = min(R, in.nrhs - r0);
+    const int pp = in.pp, ppad = in.ppad, N = in.N;
+    const int u0 = in.nu_ptr[P], U = in.nu_ptr[P + 1] - u0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int total = U * R * ppad;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int k = e % ppad, t = e / ppad;
+        const int rr = t % R, u = t / R;
+        float v = 0.f;
+        if (rr < nr && k < pp)
+            v = in.sig32[(size_t)(r0 + rr) * in.npatch * ppad + (size_t)in.nu_list[u0 + u] * ppad + k];
+        shs[(u * ppad + k) * kLd + rr] = v;
+    }
+    __syncthreads();
+    const int sub = lane / R, rr = lane - sub * R;
+    const int r = r0 + rr;
+    const bool act = rr < nr;
+    const int q4 = ppad >> 2;
+    for (int t0 = warp * kSub; t0 < pp; t0 += (blockDim.x >> 5) * kSub) {
+        const int t = t0 + sub;
+        const bool row_ok = t < pp;
+        const int i = P * pp + (row_ok ? t : 0);
+        float hi = 0.f, lo = 0.f;
+        if (act && row_ok)
+            for (int sp = 0; sp < in.nsplit; ++sp) {
+                const float2 v = in.part[((size_t)r * in.nsplit + sp) * N + i];
+                two_sum_acc(hi, lo, v.x);
+                lo += v.y;
+            }
+        float acc = 0.f;
+        const int b0 = row_ok ? in.row_ptr[i] : 0, b1 = row_ok ? in.row_ptr[i + 1] : 0;
+        for (int b = b0; b < b1; ++b) {
+            const float4* c4 = reinterpret_cast<const float4*>(in.vals + (size_t)b * ppad);
+            const float* su = shs + in.nu_blk[b] * ppad * kLd + rr;
+            for (int k4 = 0; k4 < q4; ++k4) {
+                const float4 c = __ldg(c4 + k4);
+                const float* sk = su + 4 * k4 * kLd;
+                acc = fmaf(c.x, sk[0], fmaf(c.y, sk[kLd], fmaf(c.z, sk[2 * kLd], fmaf(c.w, sk[3 * kLd], acc))));
+            }
+        }
+        two_sum_acc(hi, lo, acc);
+        if (act && row_ok) out[(size_t)(in.col0 + r) * ld_out + i] = (double)hi + (double)lo;
+    }
+}
+
+// out_c = v_c + y_c + wdot_c on the column's own rows (A v with the rank-one term)
+__global__ void k_mfinishA(const double* __restrict__ v, long long ldv, const double* __restrict__ y,
+                           long long ldy, const double* __restrict__ wdot, long long ldw,
+                           double* __restrict__ out, long long ldo, const int* __restrict__ col_n,
+                           const int* __restrict__ done) {
+    const int c = blockIdx.y;
+    if (done && done[c]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= col_n[c]) return;
+    out[c * ldo + i] = v[c * ldv + i] + y[c * ldy + i] + wdot[c * ldw];
+}
+
+// out_c = w_c * f_c (per-column weights, zero past the column's rows)
+__global__ void k_mmul(const double* __restrict__ w, const double* __restrict__ f,
+                       double* __restrict__ out, int N) {
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) out[(size_t)c * N + i] = w[(size_t)c * N + i] * f[(size_t)c * N + i];
+}
+
+// y_c[i] -= shift_c * scale_c on the column's own rows (weighted-mean projection)
+__global__ void k_mshift(double* __restrict__ y, long long ldy, const double* __restrict__ shift,
+                         long long lds, const double* __restrict__ scale,
+                         const int* __restrict__ col_n) {
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < col_n[c]) y[c * ldy + i] -= shift[c * lds] * scale[c];
+}
+
+}  // namespace
+
+// Per-context workspace of the multi-instance solve, rebuilt when the call's
+// shape (instances, right-hand sides, restart, tile) changes; its cycle graphs are
+// cached per cycle length.
+struct PmMultiWork {
+    PmBatchSolveWork W;
+    std::vector<const pm_surface*> ops;
+    std::vector<int> nrhs;
+    std::vector<long long> epochs;     // coefficient epochs of the operators at setup
+    int ncols = 0, Nmax = 0, m = 0, rb = 0, nitems = 0, grid = 0, ninst = 0;
+    long long nwarps = 0;
+    int nnear = 0;                 // patch-blocked near-field items (0: per-row kernel)
+    size_t near_smem = 0;
+    MInst* dI = nullptr;
+    MGroup* dG = nullptr;
+    int fb = 4;                    // fields per smooth-sum item (1, 2 or 4), 8 right-hand sides each
+    int4* items = nullptr;
+    int4* near_items = nullptr;
+    float4 *fac = nullptr, *nrm = nullptr;
+    float* facB = nullptr;
+    int *col_inst = nullptr, *col_n = nullptr;
+    double *wcol = nullptr, *inv_sw = nullptr;
+    float *s32 = nullptr, *sig32 = nullptr;
+    float2* part = nullptr;
+    cudaStream_t cap = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;
+    void release() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+        bsolve_release(W);
+        W = PmBatchSolveWork();
+        pm_dfree(dI); pm_dfree(dG); pm_dfree(items); pm_dfree(near_items); pm_dfree(col_inst);
+        pm_dfree(fac); pm_dfree(nrm); pm_dfree(facB); pm_dfree(col_n); pm_dfree(wcol);
+        pm_dfree(inv_sw); pm_dfree(s32); pm_dfree(sig32); pm_dfree(part);
+        if (cap) cudaStreamDestroy(cap);
+        cap = nullptr;
+        ops.clear();
+        nrhs.clear();
+    }
+    ~PmMultiWork() { release(); }
+};
+
+void pm_multi_free(pm_ctx* c) {
+    delete c->multi;
+    c->multi = nullptr;
+}
+
+namespace {
+
+constexpr int kMultiNearRhs = 8;            // right-hand sides per near-field block
+constexpr int kMultiNearSmemCap = 200 * 1024;
+
+// (Re)build the workspace for this call's shape.
+pm_status multi_setup(pm_ctx* ctx, pm_surface* const* ops, int nops, const int* nrhs, int m,
+                      PmMultiWork** out) {
+    PmMultiWork*& M = ctx->multi;
+    const int rb = ops[0]->batch_rb;
+    bool same = M && M->m == m && M->rb == rb && (int)M->ops.size() == nops;
+    for (int k = 0; same && k < nops; ++k)
+        same = M->ops[k] == ops[k] && M->nrhs[k] == nrhs[k] && M->epochs[k] == ops[k]->graph_epoch;
+    if (same) {
+        *out = M;
+        return PM_OK;
+    }
+    if (!M) M = new PmMultiWork();
+    M->release();
+    int ncols = 0, Nmax = 0;
+    for (int k = 0; k < nops; ++k) {
+        ncols += nrhs[k];
+        Nmax = std::max(Nmax, ops[k]->N);
+    }
+    M->ncols = ncols;
+    M->Nmax = Nmax;
+    M->m = m;
+    M->rb = rb;
+    M->ninst = nops;
+    PM_TRY(bsolve_alloc(M->W, ncols, m, Nmax));
+    PmBatchSolveWork& W = M->W;
+    // zero padding of every column: the rows past an instance's N stay zero
+    const size_t RN = (size_t)ncols * Nmax;
+    for (double* p : {W.w, W.tmp, W.r, W.res, W.delta, W.sig, W.f, W.u})
+        PM_CUDA_TRY(cudaMemset(p, 0, sizeof(double) * RN));
+    PM_CUDA_TRY(cudaMemset(W.V, 0, sizeof(double) * RN * (m + 1)));
+    // per-instance float32 buffers, source chunks of about 1,024 sources per item
+    // (the persistent kernel balances items of similar size), the work list
+    std::vector<MInst> hI(nops);
+    std::vector<int4> items;
+    std::vector<int> col_inst(ncols), col_n(ncols);
+    std::vector<double> wcol(RN, 0.0), inv_sw(ncols);
+    size_t n_s32 = 0, n_sig = 0, n_part = 0;
+    long long warp0 = 0;
+    int c0 = 0;
+    for (int k = 0; k < nops; ++k) {
+        const pm_surface* s = ops[k];
+        MInst& in = hI[k];
+        in.N = s->N;
+        in.npatch = s->npatch;
+        in.pp = s->pp;
+        in.ppad = s->ppad;
+        in.nrhs = nrhs[k];
+        in.col0 = c0;
+        in.nsplit = std::max(1, std::min(64, pm_ceil_div(s->N, 1024)));
+        in.chunk = pm_ceil_div(s->N, in.nsplit);
+        in.eps2 = s->eps2;
+        in.warp0 = warp0;
+        warp0 += (long long)nrhs[k] * s->N;
+        n_s32 += (size_t)nrhs[k] * s->N;
+        n_sig += (size_t)nrhs[k] * s->npatch * s->ppad;
+        n_part += (size_t)nrhs[k] * in.nsplit * s->N;
+        double sw = 0.0;
+        for (double v : s->h_w) sw += v;
+        for (int r = 0; r < nrhs[k]; ++r) {
+            col_inst[c0 + r] = k;
+            col_n[c0 + r] = s->N;
+            inv_sw[c0 + r] = 1.0 / sw;
+            std::copy(s->h_w.begin(), s->h_w.end(), wcol.begin() + (size_t)(c0 + r) * Nmax);
+        }
+        c0 += nrhs[k];
+    }
+    PM_TRY(pm_dmalloc(&M->s32, n_s32));
+    PM_TRY(pm_dmalloc(&M->sig32, n_sig));
+    PM_CUDA_TRY(cudaMemset(M->sig32, 0, sizeof(float) * n_sig));
+    PM_TRY(pm_dmalloc(&M->part, n_part));
+    size_t o32 = 0, osig = 0, opart = 0;
+    for (int k = 0; k < nops; ++k) {
+        const pm_surface* s = ops[k];
+        MInst& in = hI[k];
+        in.pos = s->src32;
+        in.tgt = s->tgt32;
+        in.wa = s->wa;
+        in.row_ptr = s->row_ptr;
+        in.blk_patch = s->blk_patch;
+        in.vals = s->cR32;
+        in.nu_ptr = s->nu_ptr;
+        in.nu_list = s->nu_list;
+        in.nu_blk = s->nu_blk;
+        in.s32 = M->s32 + o32;
+        in.sig32 = M->sig32 + osig;
+        in.part = M->part + opart;
+        o32 += (size_t)in.nrhs * s->N;
+        osig += (size_t)in.nrhs * s->npatch * s->ppad;
+        opart += (size_t)in.nrhs * in.nsplit * s->N;
+    }
+    // geometry groups (a surface and its clones share the float64 node array) of at
+    // most kMultiGroupMax instances, their normals, every instance's remainder factors
+    std::vector<MGroup> hG;
+    std::map<const double*, int> open_group;
+    PM_TRY(pm_dmalloc(&M->fac, (size_t)nops * Nmax));
+    PM_TRY(pm_dmalloc(&M->facB, (size_t)nops * Nmax));
+    for (int k = 0; k < nops; ++k) {
+        const pm_surface* s = ops[k];
+        auto og = open_group.find(s->x);
+        if (og == open_group.end() || hG[og->second].ninst == kMultiGroupMax) {
+            MGroup g{};
+            g.pos = s->src32;
+            g.tgt = s->tgt32;
+            g.N = s->N;
+            g.nsplit = hI[k].nsplit;
+            g.chunk = hI[k].chunk;
+            g.eps2 = s->eps2;
+            g.ninst = 0;
+            hG.push_back(g);
+            open_group[s->x] = (int)hG.size() - 1;
+            og = open_group.find(s->x);
+        }
+        MGroup& g = hG[og->second];
+        g.inst[g.ninst++] = k;
+        hI[k].fac = M->fac + (size_t)k * Nmax;
+        hI[k].facB = M->facB + (size_t)k * Nmax;
+    }
+    PM_TRY(pm_dmalloc(&M->nrm, (size_t)hG.size() * Nmax));
+    for (size_t gi = 0; gi < hG.size(); ++gi) {
+        const pm_surface* s = ops[hG[gi].inst[0]];
+        hG[gi].nrm = M->nrm + gi * Nmax;
+        for (int q = 0; q < hG[gi].ninst; ++q) {
+            const int k = hG[gi].inst[q];
+            const pm_surface* sk = ops[k];
+            k_mfactors<<<pm_ceil_div(sk->N, 256), 256>>>(sk->a, sk->H, sk->g, sk->n, sk->N,
+                                                         const_cast<float4*>(hI[k].fac),
+                                                         const_cast<float*>(hI[k].facB),
+                                                         q == 0 ? M->nrm + gi * Nmax : nullptr);
+        }
+        (void)s;
+    }
+    PM_CUDA_TRY(cudaGetLastError());
+    // fields per item (8 right-hand sides each): ops[0]'s batched knob when set
+    // (8, 16 or 32 right-hand sides per block -> 1, 2 or 4 fields), else 2 where a
+    // geometry carries several fields
+    int gmax = 1;
+    for (const MGroup& g : hG) gmax = std::max(gmax, g.ninst);
+    const int knob = ops[0]->batch_rb;
+    M->fb = knob == 32 ? 4 : (knob == 16 ? 2 : (knob == 8 ? 1 : (gmax >= 2 ? 2 : 1)));
+    for (int gi = 0; gi < (int)hG.size(); ++gi) {
+        const MGroup& g = hG[gi];
+        int rmax = 0;
+        for (int q = 0; q < g.ninst; ++q) rmax = std::max(rmax, nrhs[g.inst[q]]);
+        for (int t = 0; t < pm_ceil_div(g.N, kThreads); ++t)
+            for (int y = 0; y < g.nsplit; ++y)
+                for (int fb = 0; fb < pm_ceil_div(g.ninst, M->fb); ++fb)
+                    for (int rbk = 0; rbk < pm_ceil_div(rmax, 8); ++rbk)
+                        items.push_back(make_int4(gi, t, y, fb * 4096 + rbk));
+    }
+    // largest items first, so the persistent blocks finish together
+    std::stable_sort(items.begin(), items.end(), [&](const int4& a, const int4& b) {
+        return hG[a.x].chunk > hG[b.x].chunk;
+    });
+    M->nitems = (int)items.size();
+    PM_TRY(pm_dmalloc(&M->dG, hG.size()));
+    PM_CUDA_TRY(cudaMemcpy(M->dG, hG.data(), sizeof(MGroup) * hG.size(), cudaMemcpyHostToDevice));
+    M->nwarps = warp0;
+    // patch-blocked near field when every instance has its patch unions and the
+    // largest staging fits in shared memory
+    std::vector<int4> nitems_v;
+    size_t smem = 0;
+    bool unions = true;
+    for (int k = 0; k < nops; ++k) {
+        const pm_surface* s = ops[k];
+        unions &= s->nu_max > 0;
+        smem = std::max(smem, (size_t)s->nu_max * s->ppad * (kMultiNearRhs + 1) * sizeof(float));
+        for (int P = 0; P < s->npatch; ++P)
+            for (int r0 = 0; r0 < nrhs[k]; r0 += kMultiNearRhs) nitems_v.push_back(make_int4(k, P, r0, 0));
+    }
+    if (unions && smem <= (size_t)kMultiNearSmemCap) {
+        PM_TRY(pm_dmalloc(&M->near_items, nitems_v.size()));
+        PM_CUDA_TRY(cudaMemcpy(M->near_items, nitems_v.data(), sizeof(int4) * nitems_v.size(),
+                               cudaMemcpyHostToDevice));
+        M->nnear = (int)nitems_v.size();
+        M->near_smem = smem;
+        static std::once_flag attr_once;
+        static cudaError_t attr_err = cudaSuccess;
+        std::call_once(attr_once, [] {
+            attr_err = cudaFuncSetAttribute(k_mnear32_patch<kMultiNearRhs>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kMultiNearSmemCap);
+        });
+        PM_CUDA_TRY(attr_err);
+    }
+    PM_TRY(pm_dmalloc(&M->dI, nops));
+    PM_TRY(pm_dmalloc(&M->items, items.size()));
+    PM_TRY(pm_dmalloc(&M->col_inst, ncols));
+    PM_TRY(pm_dmalloc(&M->col_n, ncols));
+    PM_TRY(pm_dmalloc(&M->wcol, RN));
+    PM_TRY(pm_dmalloc(&M->inv_sw, ncols));
+    PM_CUDA_TRY(cudaMemcpy(M->dI, hI.data(), sizeof(MInst) * nops, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(M->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(M->col_inst, col_inst.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(M->col_n, col_n.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(M->wcol, wcol.data(), sizeof(double) * RN, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(M->inv_sw, inv_sw.data(), sizeof(double) * ncols, cudaMemcpyHostToDevice));
+    const int bps = (ops[0]->batch_bps >= 1 && ops[0]->batch_bps <= 16) ? ops[0]->batch_bps : 8;
+    M->grid = std::max(1, std::min(M->nitems, bps * ops[0]->ctx->num_sms));
+    PM_CUDA_TRY(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+    M->ops.assign(ops, ops + nops);
+    M->nrhs.assign(nrhs, nrhs + nops);
+    M->epochs.clear();
+    for (int k = 0; k < nops; ++k) M->epochs.push_back(ops[k]->graph_epoch);
+    PM_CUDA_TRY(cudaDeviceSynchronize());      // factors written on the default stream
+    *out = M;
+    return PM_OK;
+}
+
+struct MSolver {
+    PmMultiWork& M;
+    PmBatchSolveWork& W;
+    pm_surface* const* ops;
+    int nops;
+    cudaStream_t st;
+    int grid_n;
+    bool op_residual;              // residuals in the float32 operator itself
+    long long launches = 0;
+
+    void dots(const double* A, long long col_stride, long long rhs_stride_A, int ncols_,
+              const double* b, long long rhs_stride_b, double* dst, long long lddst,
+              const int* done) {
+        k_bdots<<<dim3(W.nred, M.ncols), kRed, 0, st>>>(A, col_stride, rhs_stride_A, ncols_, b,
+                                                         rhs_stride_b, W.N, W.part, done);
+        k_breduce<<<dim3(pm_ceil_div(ncols_, 64), M.ncols), 64, 0, st>>>(W.part, W.nred, ncols_,
+                                                                         dst, lddst, done);
+        launches += 2;
+    }
+
+    // out_c = A v_c for every column; prec FP32 (one multi-instance launch per stage)
+    // or FF (the accurate batched apply of each instance on its columns)
+    pm_status apply_A(const double* v, long long ldv, double* out, pm_precision prec,
+                      const int* done, const int* skip) {
+        if (prec == PM_PREC_FP32) {
+            k_mprep32<<<dim3(pm_ceil_div(M.Nmax, 256), M.ncols), 256, 0, st>>>(v, ldv, M.dI,
+                                                                                  M.col_inst, skip);
+            if (M.fb == 4)
+                k_mgeo32<4, 8><<<M.grid, kThreads, 0, st>>>(M.dG, M.dI, M.items, M.nitems, skip);
+            else if (M.fb == 2)
+                k_mgeo32<2, 8><<<M.grid, kThreads, 0, st>>>(M.dG, M.dI, M.items, M.nitems, skip);
+            else
+                k_mgeo32<1, 8><<<M.grid, kThreads, 0, st>>>(M.dG, M.dI, M.items, M.nitems, skip);
+            if (M.nnear > 0)
+                k_mnear32_patch<kMultiNearRhs><<<M.nnear, 256, M.near_smem, st>>>(
+                    M.dI, M.near_items, W.tmp, W.N, skip);
+            else
+                k_mnear32<<<(int)((M.nwarps * 32 + 255) / 256), 256, 0, st>>>(M.dI, M.ninst,
+                                                                            M.nwarps, W.tmp, W.N,
+                                                                            skip);
+            launches += 3;
+        } else {
+            int c0 = 0;
+            for (int k = 0; k < nops; ++k) {
+                PM_TRY(pm_apply_batch(ops[k], 0, v + (size_t)c0 * ldv, ldv, W.tmp + (size_t)c0 * W.N,
+                                      W.N, M.nrhs[k], prec, st));
+                c0 += M.nrhs[k];
+            }
+        }
+        dots(M.wcol, 0, W.N, 1, v, ldv, W.dots + 0, 8, done);
+        k_mfinishA<<<dim3(grid_n, M.ncols), 256, 0, st>>>(v, ldv, W.tmp, W.N, W.dots + 0, 8, out,
+                                                          W.N, M.col_n, done);
+        launches += 1;
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+
+    pm_status norms(const double* v, double* host) {
+        dots(v, 0, W.N, 1, v, W.N, W.dots + 1, 8, nullptr);
+        PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.dots, sizeof(double) * 8 * M.ncols,
+                                    cudaMemcpyDeviceToHost, st));
+        PM_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int c = 0; c < M.ncols; ++c) host[c] = std::sqrt(W.pinned[8 * c + 1]);
+        return PM_OK;
+    }
+
+    // the launches of one GMRES cycle of `steps` Arnoldi steps (float32 operator)
+    pm_status issue_cycle(int steps) {
+        const int m = W.m, N = W.N, nc = M.ncols;
+        const long long ldV = (long long)(m + 1) * N;
+        const int ldh = m + 2;
+        dots(W.r, 0, N, 1, W.r, N, W.scal + 1, 8, nullptr);
+        k_bcycle_start<<<1, 256, 0, st>>>(nc, W.scal + 1, 8, W.g, m, W.scal, W.done, W.iters,
+                                          W.all_done);
+        k_bscale_copy<<<dim3(grid_n, nc), 256, 0, st>>>(W.r, N, W.scal + 3, 8, 1, W.V, ldV, N,
+                                                        W.done);
+        launches += 2;
+        for (int k = 0; k < steps; ++k) {
+            double* vk = W.V + (size_t)k * N;
+            double* vk1 = W.V + (size_t)(k + 1) * N;
+            double* hk = W.H + (size_t)k * ldh;
+            PM_TRY(apply_A(vk, ldV, W.w, PM_PREC_FP32, W.done, W.all_done));
+            dots(W.V, N, ldV, k + 1, W.w, N, hk, (long long)m * ldh, W.done);
+            k_bsub<<<dim3(grid_n, nc), 256, 0, st>>>(W.V, N, ldV, k + 1, hk, (long long)m * ldh,
+                                                     W.w, N, W.done);
+            dots(W.V, N, ldV, k + 1, W.w, N, W.hcol, m + 2, W.done);
+            k_bsub<<<dim3(grid_n, nc), 256, 0, st>>>(W.V, N, ldV, k + 1, W.hcol, m + 2, W.w, N,
+                                                     W.done);
+            k_badd_cols<<<dim3(pm_ceil_div(k + 1, 64), nc), 64, 0, st>>>(
+                hk, (long long)m * ldh, W.hcol, m + 2, k + 1, W.done);
+            dots(W.w, 0, N, 1, W.w, N, W.scal + 1, 8, W.done);
+            k_brotate<<<1, 256, 0, st>>>(nc, W.H, ldh, m, k, W.cs, W.sn, W.g, W.scal, W.done,
+                                         W.iters, W.all_done);
+            k_bscale_copy<<<dim3(grid_n, nc), 256, 0, st>>>(W.w, N, W.scal + 2, 8, 0, vk1, ldV, N,
+                                                            W.done);
+            launches += 5;
+        }
+        k_bbacksolve<<<pm_ceil_div(nc, 64), 64, 0, st>>>(nc, W.H, ldh, m, W.g, W.iters, W.y,
+                                                         W.ynorm);
+        k_badd_combo<<<dim3(grid_n, nc), 256, 0, st>>>(W.V, N, ldV, W.iters, W.y, m, W.delta, N);
+        launches += 2;
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+
+    // one cycle as a CUDA graph (captured on the workspace's own stream the first
+    // time a cycle of this length runs, replayed on st after that)
+    pm_status run_cycle(int steps) {
+        auto it = M.graphs.find(steps);
+        if (it == M.graphs.end()) {
+            cudaStream_t user = st;
+            st = M.cap;
+            PM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const long long before = launches;
+            const pm_status ps = issue_cycle(steps);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            st = user;
+            launches = before;
+            if (ps != PM_OK) {
+                if (g) cudaGraphDestroy(g);
+                return ps;
+            }
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t ce2 = ce == cudaSuccess ? cudaGraphInstantiate(&ex, g, 0) : ce;
+            if (g) cudaGraphDestroy(g);
+            if (ce2 != cudaSuccess) {
+                cudaGetLastError();
+                pm_set_error("multi-instance solve: cycle graph capture: %s", cudaGetErrorString(ce2));
+                return PM_ERR_CUDA;
+            }
+            it = M.graphs.emplace(steps, ex).first;
+        }
+        PM_CUDA_TRY(cudaGraphLaunch(it->second, st));
+        launches += 1;
+        return PM_OK;
+    }
+
+    // lockstep restarted GMRES on A d_c = b_c from d = 0 (float32 operator); x += d
+    pm_status gmres(const double* b, double* x, const std::vector<double>& tol_abs, int max_iter,
+                    int* iters_used, std::vector<double>* dnorm) {
+        const int nc = M.ncols, N = W.N;
+        dnorm->assign(nc, 0.0);
+        PM_CUDA_TRY(cudaMemcpyAsync(W.r, b, sizeof(double) * (size_t)nc * N,
+                                    cudaMemcpyDeviceToDevice, st));
+        PM_CUDA_TRY(cudaMemsetAsync(W.delta, 0, sizeof(double) * (size_t)nc * N, st));
+        for (int c = 0; c < nc; ++c) W.pinned[8 * c + 4] = tol_abs[c];
+        for (int c = 0; c < nc; ++c)
+            PM_CUDA_TRY(cudaMemcpyAsync(W.scal + 8 * c + 4, W.pinned + 8 * c + 4, sizeof(double),
+                                        cudaMemcpyHostToDevice, st));
+        int total = 0;
+        while (total < max_iter) {
+            const int steps = std::min(W.m, max_iter - total);
+            PM_TRY(run_cycle(steps));
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i, W.iters, sizeof(int) * nc,
+                                        cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_i + nc, W.done, sizeof(int) * nc,
+                                        cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaMemcpyAsync(W.pinned_y, W.ynorm, sizeof(double) * nc,
+                                        cudaMemcpyDeviceToHost, st));
+            PM_CUDA_TRY(cudaStreamSynchronize(st));
+            int it = 0, all = 1;
+            for (int c = 0; c < nc; ++c) {
+                it = std::max(it, W.pinned_i[c]);
+                all &= W.pinned_i[nc + c];
+                if (W.pinned_i[c] > 0) (*dnorm)[c] += W.pinned_y[c];
+            }
+            total += it;
+            if (all || it == 0) break;
+            PM_TRY(apply_A(W.delta, N, W.w, PM_PREC_FP32, nullptr, nullptr));
+            k_bresidual<<<dim3(grid_n, nc), 256, 0, st>>>(b, W.w, W.r, N);
+            launches += 1;
+        }
+        k_baxpy<<<dim3(grid_n, nc), 256, 0, st>>>(x, W.delta, N);
+        launches += 1;
+        PM_CUDA_TRY(cudaGetLastError());
+        *iters_used = total;
+        return PM_OK;
+    }
+
+};
+
+}  // namespace
+
+extern "C" pm_status pm_solve_multi(pm_surface* const* ops, int nops, const int* nrhs,
+                                    const double* const* f, double* const* u, double tol,
+                                    int maxit, pm_precision prec, unsigned flags,
+                                    pm_solve_info* info, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!ops || nops < 1 || !nrhs || !f || !u || !(tol > 0) || maxit < 1) {
+        pm_set_error("pm_solve_multi: NULL argument, nops < 1, tol <= 0 or maxit < 1");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (prec != PM_PREC_FP32) {
+        pm_set_error("pm_solve_multi: precision %d: the multi-instance solve applies the float32 "
+                     "operators (PM_PREC_FP32)", (int)prec);
+        return PM_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < nops; ++k) {
+        if (!ops[k] || !f[k] || !u[k] || nrhs[k] < 1) {
+            pm_set_error("pm_solve_multi: instance %d: NULL operator or array, or nrhs < 1", k);
+            return PM_ERR_INVALID_ARG;
+        }
+        if (!ops[k]->has_coeff) {
+            pm_set_error("pm_solve_multi: instance %d has no coefficient", k);
+            return PM_ERR_NO_COEFF;
+        }
+        if (ops[k]->ctx != ops[0]->ctx) {
+            pm_set_error("pm_solve_multi: instance %d belongs to another context", k);
+            return PM_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < k; ++j)
+            if (ops[j] == ops[k]) {
+                pm_set_error("pm_solve_multi: operator of instance %d repeats instance %d "
+                             "(give it more right-hand sides instead)", k, j);
+                return PM_ERR_INVALID_ARG;
+            }
+    }
+    pm_ctx* ctx = ops[0]->ctx;
+    std::lock_guard<std::mutex> lock(ctx->multi_mu);
+    PM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = std::max(2, std::min(ops[0]->opts.gmres_restart, 400));
+    PmMultiWork* Mp = nullptr;
+    PM_TRY(multi_setup(ctx, ops, nops, nrhs, m, &Mp));
+    PmMultiWork& M = *Mp;
+    PmBatchSolveWork& W = M.W;
+    const int nc = M.ncols, N = W.N;
+    MSolver S{M, W, ops, nops, st, pm_ceil_div(N, 256),
+              ops[0]->opts.residual_prec == PM_PREC_FP32};
+    const bool dev = (flags & PM_SOLVE_DEVICE_PTRS) != 0;
+    const cudaMemcpyKind h2d = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind d2h = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    {
+        int c0 = 0;
+        for (int k = 0; k < nops; ++k) {
+            const size_t Nk = ops[k]->N;
+            for (int r = 0; r < nrhs[k]; ++r)
+                PM_CUDA_TRY(cudaMemcpyAsync(W.f + (size_t)(c0 + r) * N, f[k] + r * Nk,
+                                            sizeof(double) * Nk, h2d, st));
+            c0 += nrhs[k];
+        }
+    }
+    // mean-zero check of every f (Thm. LBsolvable): sum w f and sum w f^2 per column
+    k_mmul<<<dim3(S.grid_n, nc), 256, 0, st>>>(M.wcol, W.f, W.tmp, N);   // w f per column
+    S.dots(M.wcol, 0, N, 1, W.f, N, W.dots + 4, 8, nullptr);           // sum w f
+    S.dots(W.tmp, 0, N, 1, W.f, N, W.dots + 5, 8, nullptr);            // sum w f^2
+    S.launches += 1;
+    PM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.dots, sizeof(double) * 8 * nc, cudaMemcpyDeviceToHost, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<double> removed(nc, 0.0), fnorm(nc, 0.0), sw(nc, 0.0);
+    {
+        int c0 = 0;
+        for (int k = 0; k < nops; ++k) {
+            double s = 0.0;
+            for (double v : ops[k]->h_w) s += v;
+            for (int r = 0; r < nrhs[k]; ++r) sw[c0 + r] = s;
+            c0 += nrhs[k];
+        }
+    }
+    std::vector<double> shift(nc, 0.0);
+    for (int c = 0; c < nc; ++c) {
+        const double wf = W.pinned[8 * c + 4];
+        if (W.pinned[8 * c + 5] > 0.0 &&
+            std::fabs(wf) > ops[0]->opts.mean_tol * std::sqrt(sw[c] * W.pinned[8 * c + 5]) &&
+            !(flags & PM_SOLVE_PROJECT_RHS)) {
+            pm_set_error("pm_solve_multi: right-hand side %d has weighted mean %.3e; pass "
+                         "PM_SOLVE_PROJECT_RHS to subtract it", c, wf / sw[c]);
+            return PM_ERR_RHS_NOT_MEAN_ZERO;
+        }
+        if (flags & PM_SOLVE_PROJECT_RHS) removed[c] = wf / sw[c];
+    }
+    if (flags & PM_SOLVE_PROJECT_RHS) {
+        k_mshift<<<dim3(S.grid_n, nc), 256, 0, st>>>(W.f, N, W.dots + 4, 8, M.inv_sw, M.col_n);
+        S.launches += 1;
+    }
+    PM_TRY(S.norms(W.f, fnorm.data()));
+    PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * (size_t)nc * N, st));
+    int iters = 0, refinements = 0, updated = 0;
+    std::vector<double> relres(nc, 0.0), tabs(nc), dn;
+    bool have_update = false;
+    for (;;) {
+        std::vector<double> rn(nc);
+        if (refinements == 0) {
+            PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * (size_t)nc * N,
+                                        cudaMemcpyDeviceToDevice, st));
+            rn = fnorm;
+        } else {
+            // per instance: r - A32 d when every one of its columns' corrections is small
+            // (within 0.1 tol |f| of the true residual, see pm_solve.cu), else f - A sigma
+            // recomputed in float-float for that instance's columns only
+            std::vector<int> exact(nops, 0);
+            bool any_exact = false;
+            int c0 = 0;
+            for (int k = 0; k < nops; ++k) {
+                bool small = S.op_residual || (have_update && ops[0]->opts.residual_update);
+                for (int r = 0; small && r < nrhs[k]; ++r)
+                    small = kOpRelErr * dn[c0 + r] <= 0.1 * tol * fnorm[c0 + r];
+                exact[k] = !small;
+                any_exact |= !small;
+                c0 += nrhs[k];
+            }
+            PM_TRY(S.apply_A(W.delta, N, W.w, PM_PREC_FP32, nullptr, nullptr));
+            k_bsubv<<<dim3(S.grid_n, nc), 256, 0, st>>>(W.res, W.w, N);
+            S.launches += 1;
+            if (any_exact) {
+                c0 = 0;
+                for (int k = 0; k < nops; ++k) {
+                    if (exact[k])
+                        PM_TRY(pm_apply_batch(ops[k], 0, W.sig + (size_t)c0 * N, N,
+                                              W.tmp + (size_t)c0 * N, N, nrhs[k], PM_PREC_FF, st));
+                    c0 += nrhs[k];
+                }
+                S.dots(M.wcol, 0, N, 1, W.sig, N, W.dots + 0, 8, nullptr);
+                c0 = 0;
+                for (int k = 0; k < nops; ++k) {
+                    if (exact[k]) {
+                        // res = f - (sigma + R~ sigma + (w . sigma) 1) on these columns
+                        k_mfinishA<<<dim3(S.grid_n, nrhs[k]), 256, 0, st>>>(
+                            W.sig + (size_t)c0 * N, N, W.tmp + (size_t)c0 * N, N, W.dots + 8 * c0, 8,
+                            W.w + (size_t)c0 * N, N, M.col_n + c0, nullptr);
+                        k_bresidual<<<dim3(S.grid_n, nrhs[k]), 256, 0, st>>>(
+                            W.f + (size_t)c0 * N, W.w + (size_t)c0 * N, W.res + (size_t)c0 * N, N);
+                        S.launches += 2;
+                    } else {
+                        updated += 1;
+                    }
+                    c0 += nrhs[k];
+                }
+            } else {
+                updated += nops;
+            }
+            PM_TRY(S.norms(W.res, rn.data()));
+        }
+        bool all_ok = true;
+        for (int c = 0; c < nc; ++c) {
+            relres[c] = fnorm[c] > 0 ? rn[c] / fnorm[c] : 0.0;
+            all_ok &= relres[c] <= tol;
+        }
+        if (all_ok || refinements >= ops[0]->opts.max_refine || iters >= maxit) break;
+        for (int c = 0; c < nc; ++c) {
+            const double inner = S.op_residual ? 0.5 * tol * fnorm[c] / std::max(rn[c], 1e-300)
+                                               : std::max(ops[0]->opts.inner_tol,
+                                                          0.5 * tol * fnorm[c] / std::max(rn[c], 1e-300));
+            tabs[c] = (relres[c] <= tol) ? 1e300 : inner * rn[c];
+        }
+        int it = 0;
+        PM_TRY(S.gmres(W.res, W.sig, tabs, maxit - iters, &it, &dn));
+        have_update = true;
+        iters += it;
+        ++refinements;
+        if (it == 0) break;
+    }
+    pm_status result = PM_OK;
+    for (int c = 0; c < nc; ++c)
+        if (!(relres[c] <= tol)) {
+            pm_set_error("pm_solve_multi: column %d: relative residual %.3e above %.3e", c,
+                         relres[c], tol);
+            result = PM_ERR_NOT_CONVERGED;
+        }
+    // u = K~ sigma (float-float, or the float32 operator), minus its weighted mean
+    {
+        int c0 = 0;
+        for (int k = 0; k < nops; ++k) {
+            PM_TRY(pm_apply_batch(ops[k], 1, W.sig + (size_t)c0 * N, N, W.u + (size_t)c0 * N, N,
+                                  nrhs[k], S.op_residual ? PM_PREC_FP32 : PM_PREC_FF, st));
+            c0 += nrhs[k];
+        }
+    }
+    S.dots(M.wcol, 0, N, 1, W.u, N, W.dots + 6, 8, nullptr);
+    k_mshift<<<dim3(S.grid_n, nc), 256, 0, st>>>(W.u, N, W.dots + 6, 8, M.inv_sw, M.col_n);
+    {
+        int c0 = 0;
+        for (int k = 0; k < nops; ++k) {
+            const size_t Nk = ops[k]->N;
+            for (int r = 0; r < nrhs[k]; ++r)
+                PM_CUDA_TRY(cudaMemcpyAsync(u[k] + r * Nk, W.u + (size_t)(c0 + r) * N,
+                                            sizeof(double) * Nk, d2h, st));
+            c0 += nrhs[k];
+        }
+    }
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    ops[0]->launch_total += S.launches;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        for (int c = 0; c < nc; ++c) {
+            info[c].iterations = iters;
+            info[c].refinements = refinements;
+            info[c].residual = relres[c];
+            info[c].removed_mean = removed[c];
+            info[c].seconds = secs;
+            info[c].residual_updates = updated;
         }
     return result;
 }

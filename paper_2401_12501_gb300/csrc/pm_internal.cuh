@@ -79,7 +79,11 @@ struct pm_ctx {
     // blocks a1 a0 a0 (pm_fmm.cu)
     __half* fmm_opR = nullptr;   // rows = 9 * 512
     __half* fmm_opK = nullptr;   // rows = 512
+    // multi-instance lockstep solve (pm_batch.cu): workspace of the last call's shape
+    std::mutex multi_mu;
+    struct PmMultiWork* multi = nullptr;
 };
+void pm_multi_free(pm_ctx* c);
 
 // Device buffers fixed once a surface is built (geometry, near-field CSR and
 // quadrature weights, self-rule plan): shared by a surface and its clones
