@@ -144,8 +144,12 @@ __device__ __forceinline__ void sym_loop(const SymCtx<KERNEL_K>& C, int lane, in
     }
 }
 
+// 7 blocks of 128 threads per SM: the register cap (72) keeps 28 warps resident
+// against 24 at the unconstrained 80 registers, at the cost of 16 bytes of spill in
+// the remainder form; measured on the 98,304-node torus, 44.1 -> 41.1 ms (remainder),
+// 17.6 ms unchanged (parametrix); 8 blocks (64 registers, 76-byte spills) gave 43.6 ms.
 template <bool KERNEL_K>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 7)
 k_sym_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
          const float4* __restrict__ log_tab, int N, int nt, float far_h, float far_l,
          float2* __restrict__ partial, const int* __restrict__ skip) {
