@@ -127,7 +127,7 @@ struct pm_surface {
     double* W_g = nullptr;        // [3*nblk*pp] int r/(2 pi r^2) l_k J~ (component-major)
     double* W_k = nullptr;        // [nblk*pp] int log|r|/(2 pi) l_k J~
     int* dev_err = nullptr;       // device error word
-    // per patch, the union of its rows' near patches (for the patch-blocked SpMV):
+    // per patch, the union of its rows' near patches (multi-instance near field):
     // nu_list[nu_ptr[P] .. nu_ptr[P+1]) ascending; nu_blk[b] = index of blk_patch[b]
     // in its row's patch union; nu_max = the largest union (0: not built)
     int* nu_ptr = nullptr;        // [npatch+1]

@@ -600,98 +600,6 @@ k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
     if (row_ok && hl == 0) out[i] = (double)hi + (double)lo;
 }
 
-constexpr int kPatchLanes = 2;                          // lanes per row of k_near_patch32
-constexpr int kPatchUnroll = 4;                         // value loads in flight per lane and pass
-constexpr size_t kPatchSmemCap = 96 * 1024;             // its largest sigma union
-
-// Patch-blocked float32 correction SpMV: CTAs of 64 L threads take 64 rows of
-// one patch (a patch's rows are consecutive and their correction blocks one
-// contiguous range), L lanes per row.  The union of the patch rows' near patches'
-// sigma is staged in shared memory first, together with the rows' CSR offsets,
-// so every global load of a row (partial slices, correction values, each block's
-// union index) is independent of the others and of sigma; a lane issues U float4
-// value loads (and their union indices) per pass before it consumes any.  Rows
-// are reduced within their lane group in a fixed order (deterministic).
-template <int L, int U>
-__global__ void __launch_bounds__(64 * L)
-k_near_patch32(int N, int pp, int ppad, int cta_per_patch, const int* __restrict__ row_ptr,
-               const int* __restrict__ nu_ptr, const int* __restrict__ nu_list,
-               const int* __restrict__ nu_blk, const float* __restrict__ vals,
-               const float* __restrict__ sig32, const float2* __restrict__ partial,
-               int nsplit, int use_near, double* __restrict__ out,
-               const int* __restrict__ skip) {
-    if (skip && *skip) return;
-    constexpr int kRows = 64;                       // rows per pass of the CTA
-    extern __shared__ float4 sh4[];                 // [union size][ppad / 4]
-    __shared__ int srp[PM_MAX_P * PM_MAX_P + 1];
-    const int P = blockIdx.x / cta_per_patch;
-    const int part = blockIdx.x - P * cta_per_patch;
-    const int q4 = ppad >> 2;
-    if (use_near) {
-        const int u0 = nu_ptr[P], nu = nu_ptr[P + 1] - u0;
-        const float4* s4 = reinterpret_cast<const float4*>(sig32);
-        for (int e = threadIdx.x; e < nu * q4; e += blockDim.x) {
-            const int u = e / q4;
-            sh4[e] = __ldg(s4 + (size_t)nu_list[u0 + u] * q4 + (e - u * q4));
-        }
-    }
-    for (int t = threadIdx.x; t <= pp; t += blockDim.x) srp[t] = row_ptr[P * pp + t];
-    __syncthreads();
-    const int hl = threadIdx.x % L;
-    const float4* v4 = reinterpret_cast<const float4*>(vals);
-    for (int r0 = part * kRows; r0 < pp; r0 += cta_per_patch * kRows) {   // uniform trip count
-        const int r = r0 + (int)threadIdx.x / L;
-        const bool row_ok = r < pp;
-        const int i = P * pp + (row_ok ? r : 0);
-        float hi = 0.f, lo = 0.f, s, e;
-        if (row_ok)
-            for (int sp = hl; sp < nsplit; sp += L) {
-                const float2 v = __ldg(partial + (size_t)sp * N + i);
-                two_sum(hi, v.x, s, e);
-                hi = s;
-                lo += e + v.y;
-            }
-        float acc = 0.f;
-        if (use_near && row_ok) {
-            const int rb = srp[r];
-            const int total = (srp[r + 1] - rb) * q4;
-            for (int e0 = 0; e0 < total; e0 += U * L) {
-                float4 v[U];
-                int xo[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int q = e0 + u * L + hl;
-                    if (q < total) {
-                        const int b = q / q4;
-                        v[u] = __ldg(v4 + (size_t)rb * q4 + q);
-                        xo[u] = __ldg(nu_blk + rb + b) * q4 + (q - b * q4);
-                    } else {
-                        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        xo[u] = -1;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (xo[u] >= 0) {
-                        const float4 x = sh4[xo[u]];
-                        acc = fmaf(v[u].x, x.x, fmaf(v[u].y, x.y, fmaf(v[u].z, x.z, fmaf(v[u].w, x.w, acc))));
-                    }
-            }
-        }
-        two_sum(hi, acc, s, e);
-        hi = s;
-        lo += e;
-        for (int o = L / 2; o > 0; o >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-            two_sum(hi, h2, s, e);
-            hi = s;
-            lo += e + l2;
-        }
-        if (row_ok && hl == 0) out[i] = (double)hi + (double)lo;
-    }
-}
-
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
                                const int* __restrict__ blk_patch, const double* __restrict__ vals,
                                const double* __restrict__ sigma, const double* __restrict__ partial,
@@ -769,7 +677,8 @@ pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
                                                s->opts.near_factor, s->row_ptr, s->blk_patch,
                                                s->blk_row);
     PM_CUDA_TRY(cudaGetLastError());
-    // near-patch unions of every patch (patch-blocked SpMV, k_near_patch32)
+    // near-patch unions of every patch (the multi-instance solve's patch-blocked
+    // near field, pm_batch.cu k_mnear32_patch)
     {
         std::vector<int> bp(s->nblk);
         PM_CUDA_TRY(cudaMemcpy(bp.data(), s->blk_patch, sizeof(int) * s->nblk,
@@ -844,23 +753,7 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
                                                    s->partial, nsplit, prec == PM_PREC_FF ? 1 : 0,
                                                    use_near, out,
                                                    s->skip_flag);
-    else if (!one_wave && s->nu_max > 0 && s->npatch >= s->ctx->num_sms &&
-             (size_t)s->nu_max * s->ppad * sizeof(float) <= kPatchSmemCap) {
-        const size_t smem = (size_t)s->nu_max * s->ppad * sizeof(float);
-        static std::once_flag attr_once;
-        static cudaError_t attr_err = cudaSuccess;
-        std::call_once(attr_once, [] {
-            attr_err = cudaFuncSetAttribute(k_near_patch32<kPatchLanes, kPatchUnroll>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kPatchSmemCap);
-        });
-        PM_CUDA_TRY(attr_err);
-        const int cpp = pm_ceil_div(s->pp, 64);
-        k_near_patch32<kPatchLanes, kPatchUnroll><<<s->npatch * cpp, 64 * kPatchLanes, smem, st>>>(
-            N, s->pp, s->ppad, cpp, s->row_ptr, s->nu_ptr, s->nu_list, s->nu_blk,
-            which_K ? s->cK32 : s->cR32, s->sig32, reinterpret_cast<const float2*>(s->partial),
-            nsplit, use_near, out, s->skip_flag);
-    } else
+    else
         (one_wave ? k_near_apply32<32, 4> : k_near_apply32<8, 4>)
             <<<pm_ceil_div((long long)N * (one_wave ? 32 : 8), threads), threads, 0, st>>>(
                 N, s->ppad, s->row_ptr, s->blk_patch, which_K ? s->cK32 : s->cR32, s->sig32,
