@@ -41,8 +41,13 @@ FP32_LANES_PER_SM = 128    # FP32 lanes of one sm_100-family SM
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the current kernel versions on a workload; set to None whenever the kernel changes
 # until it is captured again.
-TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): None,      # kernel changed: recapture
-                 ("k_sym_ff_R", "ellipsoid_9600"): 1299712}
+TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 625408,
+                 ("k_sym_ff_R", "ellipsoid_9600"): 1849856,
+                 ("k_sym_ff_K", "ellipsoid_9600"): 356608,
+                 ("k_sym_ff_R", "torus_98304"): 567848192,
+                 ("k_sym_ff_K", "torus_98304"): 548400640,
+                 ("k_tc_gemm", "torus_98304"): 446360320,
+                 ("k_fmm_p2p", "torus_98304"): 6932992}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
 
@@ -449,7 +454,8 @@ def run_gpu(args, rank, world, local_rank):
         p_ms = ph["fmm_p2p"][0] / ph["fmm_p2p"][1]
         roofs["fmm_p2p"] = _alu_roofline(
             "k_fmm_p2p<R> (FMM adjacent-leaf float32 sums)", FLOPS_PER_PAIR_R * fmm["p2p_pairs"],
-            p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms, None)
+            p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms,
+            TRAFFIC_BYTES.get(("k_fmm_p2p", args.workload)))
     if not fmm and fast_R_n:
         roofs["direct_R"] = _alu_roofline(
             "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, fast_R_ms / fast_R_n,
