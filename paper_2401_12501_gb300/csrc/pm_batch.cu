@@ -1989,6 +1989,67 @@ struct MSolver {
 
 }  // namespace
 
+namespace {
+
+// u_c = K~ sigma_c (float-float) for the columns of several operators.  The
+// parametrix sum depends on an operator's coefficient only through the strengths
+// w sigma / a, so the columns of operators on one geometry (consecutive instances
+// sharing the node array) go through ONE float-float parametrix sum with every
+// column's own strengths; each operator then adds its own float64 corrections.
+// Other instances use the per-operator batched apply.
+pm_status multi_representation_ff(pm_surface* const* ops, int nops, const int* nrhs,
+                                  const double* sig, double* out, long long ld, cudaStream_t st) {
+    int k = 0, c0 = 0;
+    while (k < nops) {
+        int k1 = k + 1, cols = nrhs[k];
+        while (k1 < nops && ops[k1]->x == ops[k]->x) cols += nrhs[k1++];
+        pm_surface* s0 = ops[k];
+        if (k1 - k == 1) {
+            PM_TRY(pm_apply_batch(s0, 1, sig + (size_t)c0 * ld, ld, out + (size_t)c0 * ld, ld,
+                                  nrhs[k], PM_PREC_FF, st));
+        } else {
+            PM_TRY(batch_ensure(s0, cols));
+            PmBatchWork& B = *s0->batch;
+            const int N = s0->N;
+            const int rbff = cols <= 8 ? 8 : kRBff;
+            const int ns = batch_splits(s0, cols, rbff, 8);
+            int c = 0;
+            for (int q = k; q < k1; ++q) {
+                k_prep_ff_multi<<<dim3(pm_ceil_div(N, 256), nrhs[q]), 256, 0, st>>>(
+                    sig + (size_t)(c0 + c) * ld, ld, ops[q]->wa, B.sff + (size_t)c * N, N, nullptr);
+                c += nrhs[q];
+            }
+            const dim3 g(pm_ceil_div(N, kThreads), ns, pm_ceil_div(cols, rbff));
+            const int chunk = pm_ceil_div(N, ns);
+            if (rbff == 8)
+                k_direct_multi_ff<true, 8><<<g, kThreads, 0, st>>>(s0->src_kg, B.sff, cols, s0->tgt_ff,
+                                                                  s0->log_tab, N, chunk, B.part, ns,
+                                                                  nullptr);
+            else
+                k_direct_multi_ff<true, kRBff><<<g, kThreads, 0, st>>>(s0->src_kg, B.sff, cols,
+                                                                      s0->tgt_ff, s0->log_tab, N,
+                                                                      chunk, B.part, ns, nullptr);
+            c = 0;
+            for (int q = k; q < k1; ++q) {
+                const dim3 gn(pm_ceil_div((long long)N * 32, 256), nrhs[q]);
+                k_near_multi64<<<gn, 256, 0, st>>>(N, ops[q]->pp, ops[q]->row_ptr,
+                                                   ops[q]->blk_patch, ops[q]->cK64,
+                                                   sig + (size_t)(c0 + c) * ld, ld,
+                                                   B.part + (size_t)c * ns * N, ns,
+                                                   out + (size_t)(c0 + c) * ld, ld, nullptr);
+                c += nrhs[q];
+            }
+            s0->launch_total += 2 * (k1 - k) + 1;
+            PM_CUDA_TRY(cudaGetLastError());
+        }
+        c0 += cols;
+        k = k1;
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
 extern "C" pm_status pm_solve_multi(pm_surface* const* ops, int nops, const int* nrhs,
                                     const double* const* f, double* const* u, double tol,
                                     int maxit, pm_precision prec, unsigned flags,
@@ -2166,13 +2227,15 @@ extern "C" pm_status pm_solve_multi(pm_surface* const* ops, int nops, const int*
             result = PM_ERR_NOT_CONVERGED;
         }
     // u = K~ sigma (float-float, or the float32 operator), minus its weighted mean
-    {
+    if (S.op_residual) {
         int c0 = 0;
         for (int k = 0; k < nops; ++k) {
             PM_TRY(pm_apply_batch(ops[k], 1, W.sig + (size_t)c0 * N, N, W.u + (size_t)c0 * N, N,
-                                  nrhs[k], S.op_residual ? PM_PREC_FP32 : PM_PREC_FF, st));
+                                  nrhs[k], PM_PREC_FP32, st));
             c0 += nrhs[k];
         }
+    } else {
+        PM_TRY(multi_representation_ff(ops, nops, nrhs, W.sig, W.u, N, st));
     }
     S.dots(M.wcol, 0, N, 1, W.u, N, W.dots + 6, 8, nullptr);
     k_mshift<<<dim3(S.grid_n, nc), 256, 0, st>>>(W.u, N, W.dots + 6, 8, M.inv_sw, M.col_n);
