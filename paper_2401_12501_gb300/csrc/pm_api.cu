@@ -497,6 +497,7 @@ extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
     s->scale = src->scale;
     s->h_far = src->h_far;
     s->eps2 = src->eps2;
+    s->k32_centred = src->k32_centred;
     s->h_x = src->h_x;
     s->h_w = src->h_w;
     s->h_tg = src->h_tg;
@@ -652,7 +653,7 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
             nsplit = pm_fmm_splits();
             PM_TRY(pm_fmm_apply(s, kernel_K, st));
         } else {
-            nsplit = pm_direct_splits(s, prec);
+            nsplit = pm_direct_splits(s, prec, kernel_K);
             PM_TRY(pm_direct_sum(s, kernel_K, prec, nsplit, st));
         }
     }

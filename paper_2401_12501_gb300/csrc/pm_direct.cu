@@ -173,30 +173,95 @@ k_direct_R32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
 }
 
 // ------------------------------------------------------------------ float32 parametrix sum
-template <int TPT>
+// CENTRED: r^2 about a centre c of the block's targets (their mean).  With
+// a = x_i - c and b = x_j - c, r^2 = |a|^2 + |b|^2 - 2 a.b; sources are staged as
+// (-2b, s) and |b|^2, so a pair costs one add and three FMAs for r^2 (instead of
+// three subtractions, a multiply and two FMAs), one MUFU lg2 and one FMA: about
+// 6.5 issue slots a pair at 4 targets per thread, which leaves the MUFU rate
+// (16 lg2 per clock per SM) as the bound.  Rounding: the cancellation costs up
+// to ~8 eps R^2 in r^2 for a target tile of radius R, so a pair's log error is
+// ~12 eps R^2 / r^2; summed with weights w_j ~ dA over the surface that is
+// ~12 eps R^2 |sigma| int dA / r^2 ~ 75 eps R^2 log(R/h) |sigma| for node spacing h,
+// against a sum of order |sigma| |Gamma|.  The surface takes this form only when
+// every tile of 512 consecutive nodes has R^2 <= 0.03 |Gamma| (a relative error
+// below ~1e-6 by that bound) and R^2 <= r_min^2 / (80 eps) for the smallest
+// distance r_min between two nodes (r^2 stays positive and within 10 %); other
+// surfaces (patches in scattered order) take the plain form, CENTRED = false.
+// The self pair (in the centred form r^2 is a rounding residue, possibly
+// negative) is replaced by zero by index before it is used.
+template <int TPT, bool CENTRED>
 __global__ void __launch_bounds__(kThreads)
 k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int N, int chunk,
              float2* __restrict__ partial, const int* __restrict__ skip) {
     if (skip && *skip) return;
     __shared__ float4 sh[kStage];
+    __shared__ float sb2[CENTRED ? kStage : 1];
+    __shared__ float red[3][kThreads / 32];
     const int tid = threadIdx.x;
     const int tbase = blockIdx.x * kThreads * TPT;
     const int tend = tbase + kThreads * TPT;
-    float tx[TPT], ty[TPT], tz[TPT], hi[TPT], lo[TPT];
+    float tx[TPT], ty[TPT], tz[TPT], ta2[TPT], hi[TPT], lo[TPT];
+    float cx = 0.f, cy = 0.f, cz = 0.f;
 #pragma unroll
     for (int t = 0; t < TPT; ++t) {
         const int i = tbase + t * kThreads + tid;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < N) a = tgt[i];
+        if (i < N) {
+            a = tgt[i];
+            cx += a.x; cy += a.y; cz += a.z;
+        }
         tx[t] = a.x; ty[t] = a.y; tz[t] = a.z;
         hi[t] = 0.f; lo[t] = 0.f;
     }
+    if (CENTRED) {
+        // centre: the mean of the block's targets (padding rows excluded)
+        for (int o = 16; o > 0; o >>= 1) {
+            cx += __shfl_xor_sync(0xffffffffu, cx, o);
+            cy += __shfl_xor_sync(0xffffffffu, cy, o);
+            cz += __shfl_xor_sync(0xffffffffu, cz, o);
+        }
+        if ((tid & 31) == 0) {
+            red[0][tid >> 5] = cx;
+            red[1][tid >> 5] = cy;
+            red[2][tid >> 5] = cz;
+        }
+        __syncthreads();
+        cx = cy = cz = 0.f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            cx += red[0][w];
+            cy += red[1][w];
+            cz += red[2][w];
+        }
+        const float inv_n = 1.0f / (float)min(kThreads * TPT, N - tbase);
+        cx *= inv_n; cy *= inv_n; cz *= inv_n;
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            tx[t] -= cx; ty[t] -= cy; tz[t] -= cz;
+            ta2[t] = fmaf(tx[t], tx[t], fmaf(ty[t], ty[t], tz[t] * tz[t]));
+        }
+    }
+    // r^2 of target t and the staged source (s, b2)
+    auto pair_r2 = [&](int t, const float4& s, float b2) -> float {
+        if (CENTRED) return fmaf(tx[t], s.x, fmaf(ty[t], s.y, fmaf(tz[t], s.z, ta2[t] + b2)));
+        const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
+        return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    };
     const int s0 = blockIdx.y * chunk;
     const int s1 = min(s0 + chunk, N);
     for (int base = s0; base < s1; base += kStage) {
         const int len = min(kStage, s1 - base);
         __syncthreads();
-        for (int j = tid; j < len; j += kThreads) sh[j] = src[base + j];
+        for (int j = tid; j < len; j += kThreads) {
+            const float4 v = src[base + j];
+            if (CENTRED) {
+                const float bx = v.x - cx, by = v.y - cy, bz = v.z - cz;
+                sh[j] = make_float4(-2.f * bx, -2.f * by, -2.f * bz, v.w);
+                sb2[j] = fmaf(bx, bx, fmaf(by, by, bz * bz));
+            } else {
+                sh[j] = v;
+            }
+        }
         __syncthreads();
         for (int j0 = 0; j0 < len; j0 += kTile) {
             const int j1 = min(j0 + kTile, len);
@@ -208,20 +273,18 @@ k_direct_K32(const float4* __restrict__ src, const float4* __restrict__ tgt, int
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
                     const float4 s = sh[j];
+                    const float b2 = CENTRED ? sb2[j] : 0.f;
 #pragma unroll
-                    for (int t = 0; t < TPT; ++t) {
-                        const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        part[t] = fmaf(s.w, lg2_approx(r2), part[t]);
-                    }
+                    for (int t = 0; t < TPT; ++t)
+                        part[t] = fmaf(s.w, lg2_approx(pair_r2(t, s, b2)), part[t]);
                 }
             } else {
                 for (int j = j0; j < j1; ++j) {
                     const float4 s = sh[j];
+                    const float b2 = CENTRED ? sb2[j] : 0.f;
 #pragma unroll
                     for (int t = 0; t < TPT; ++t) {
-                        const float dx = tx[t] - s.x, dy = ty[t] - s.y, dz = tz[t] - s.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float r2 = pair_r2(t, s, b2);
                         const float l = (base + j == tbase + t * kThreads + tid) ? 0.f : lg2_approx(r2);
                         part[t] = fmaf(s.w, l, part[t]);
                     }
@@ -290,13 +353,17 @@ k_direct_64(const pm_d4* __restrict__ src, const double* __restrict__ x,
 
 }  // namespace
 
-static int direct_tpt(const pm_surface* s) {
+// Targets per thread of the float32 sums: the knob when set, else 2 for the
+// remainder (bound by its FP32 datapath, more targets only add registers) and
+// 4 for the parametrix (bound by the MUFU rate, more targets per staged source
+// take shared-memory reads off the issue slots the lg2s share).
+static int direct_tpt(const pm_surface* s, int which_K) {
     const int t = s->opts.direct_tpt;
-    return (t == 1 || t == 2 || t == 4) ? t : 2;
+    return (t == 1 || t == 2 || t == 4) ? t : (which_K ? 4 : 2);
 }
 
-int pm_direct_splits(const pm_surface* s, pm_precision prec) {
-    const int per_block = (prec == PM_PREC_FP64) ? kThreads : kThreads * direct_tpt(s);
+int pm_direct_splits(const pm_surface* s, pm_precision prec, int which_K) {
+    const int per_block = (prec == PM_PREC_FP64) ? kThreads : kThreads * direct_tpt(s, which_K);
     const int tblocks = pm_ceil_div(s->N, per_block);
     int bps = s->opts.direct_blocks_per_sm;
     if (bps < 1 || bps > 16) bps = 12;
@@ -338,14 +405,14 @@ pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nspli
                                                s->Npad, chunk, which_K, s->partial,
                                                s->skip_flag);
     } else {
-        const int tpt = direct_tpt(s);
+        const int tpt = direct_tpt(s, which_K);
         const int chunk = pm_ceil_div(N, nsplit);
         dim3 grid(pm_ceil_div(N, kThreads * tpt), nsplit);
         float2* part = reinterpret_cast<float2*>(s->partial);
 #define PM_LAUNCH(T)                                                                        \
         if (which_K)                                                                        \
-            k_direct_K32<T><<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, chunk, part,  \
-                                                       s->skip_flag);                       \
+            (s->k32_centred ? k_direct_K32<T, true> : k_direct_K32<T, false>)               \
+                <<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, chunk, part, s->skip_flag); \
         else                                                                                \
             k_direct_R32<T><<<grid, kThreads, 0, st>>>(s->src32, s->tgt32, N, chunk,        \
                                                        s->eps2, part, s->skip_flag);

@@ -106,6 +106,7 @@ struct pm_surface {
     double scale = 1.0;           // bounding-box diagonal (for the self-pair guard)
     double h_far = 0.0;           // largest |coordinate| (placement of padding sources)
     float eps2 = 0.f;             // r^2 guard of the float32 R sum
+    int k32_centred = 0;          // float32 parametrix sum in the centred form (pm_direct.cu)
 
     // float64 geometry (device)
     double* x = nullptr;          // [N*3]
@@ -208,7 +209,7 @@ void pm_patch_gradient(const pm_surface* s, const QuadTables& T, const double* a
                        double* grad);
 
 // smooth sums (pm_direct.cu)
-int pm_direct_splits(const pm_surface* s, pm_precision prec);
+int pm_direct_splits(const pm_surface* s, pm_precision prec, int which_K);
 pm_status pm_prep_sources(pm_surface* s, const double* sigma, pm_precision prec,
                           cudaStream_t st);
 pm_status pm_direct_sum(pm_surface* s, int which_K, pm_precision prec, int nsplit,

@@ -29,6 +29,7 @@
 #include "pm_internal.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -630,6 +631,56 @@ __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
     if (lane == 0) out[i] = acc;
 }
 
+// Smallest squared distance between a target and the other nodes of its near
+// patches (every node closer than a patch radius lies in one), as the bits of a
+// positive float, which order like the floats themselves.
+__global__ void k_near_min_dist(const double* __restrict__ x, const int* __restrict__ blk_row,
+                                const int* __restrict__ blk_patch, int pp,
+                                unsigned int* __restrict__ out) {
+    const int b = blockIdx.x;
+    const int i = blk_row[b], P = blk_patch[b];
+    double m = 1e300;
+    for (int k = threadIdx.x; k < pp; k += blockDim.x) {
+        const int j = P * pp + k;
+        if (j == i) continue;
+        const double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
+                     dz = x[3 * i + 2] - x[3 * j + 2];
+        m = fmin(m, dx * dx + dy * dy + dz * dz);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m < 1e300)
+        atomicMin(out, __float_as_uint((float)m));
+}
+
+// Largest squared distance of a node from the mean of its tile of `tile`
+// consecutive nodes (one block per tile, float bits as above).
+__global__ void k_tile_radius(const double* __restrict__ x, int N, int tile,
+                              unsigned int* __restrict__ out) {
+    __shared__ double red[3][32];
+    const int t0 = blockIdx.x * tile, t1 = min(t0 + tile, N);
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x)
+        for (int d = 0; d < 3; ++d) c[d] += x[3 * i + d];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int d = 0; d < 3; ++d) {
+        for (int o = 16; o > 0; o >>= 1) c[d] += __shfl_xor_sync(0xffffffffu, c[d], o);
+        if (lane == 0) red[d][wid] = c[d];
+    }
+    __syncthreads();
+    for (int d = 0; d < 3; ++d) {
+        c[d] = 0.0;
+        for (int w = 0; w < nw; ++w) c[d] += red[d][w];
+        c[d] /= (double)(t1 - t0);
+    }
+    double m = 0.0;
+    for (int i = t0 + threadIdx.x; i < t1; i += blockDim.x) {
+        const double dx = x[3 * i] - c[0], dy = x[3 * i + 1] - c[1], dz = x[3 * i + 2] - c[2];
+        m = fmax(m, dx * dx + dy * dy + dz * dz);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(out, __float_as_uint((float)m));
+}
+
 }  // namespace
 
 // The quadrature tables live in one __constant__ copy per device, written here
@@ -702,6 +753,34 @@ pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
         PM_CUDA_TRY(cudaMemcpy(s->nu_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
         PM_CUDA_TRY(cudaMemcpy(s->nu_blk, bu.data(), sizeof(int) * bu.size(), cudaMemcpyHostToDevice));
         s->nu_max = umax;
+    }
+    // Is the centred form of the float32 parametrix sum safe here (pm_direct.cu)?
+    // Every tile of 512 consecutive nodes must be compact: R^2 <= 0.03 |Gamma| and
+    // R^2 <= r_min^2 / (80 eps), eps = 2^-24, r_min the smallest node distance.
+    {
+        unsigned int* mm = nullptr;
+        PM_TRY(pm_dmalloc(&mm, 2));
+        const unsigned int init[2] = {0x7f7fffffu, 0u};      // FLT_MAX, +0
+        cudaError_t ce = cudaMemcpy(mm, init, sizeof(init), cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) {
+            k_near_min_dist<<<s->nblk, 64>>>(s->x, s->blk_row, s->blk_patch, pp, mm);
+            k_tile_radius<<<pm_ceil_div(N, 512), 256>>>(s->x, N, 512, mm + 1);
+            ce = cudaGetLastError();
+        }
+        unsigned int got[2] = {0u, 0u};
+        if (ce == cudaSuccess) ce = cudaMemcpy(got, mm, sizeof(got), cudaMemcpyDeviceToHost);
+        cudaFree(mm);
+        if (ce != cudaSuccess) {
+            pm_set_error("near build (tile radii): %s", cudaGetErrorString(ce));
+            return PM_ERR_CUDA;
+        }
+        float rmin2 = 0.f, tile2 = 0.f;
+        std::memcpy(&rmin2, &got[0], sizeof(float));
+        std::memcpy(&tile2, &got[1], sizeof(float));
+        double area = 0.0;
+        for (double v : s->h_w) area += v;
+        const double eps = std::ldexp(1.0, -24);
+        s->k32_centred = (N > 1 && tile2 <= 0.03 * area && (double)tile2 * 80.0 * eps <= rmin2) ? 1 : 0;
     }
     const size_t nv = (size_t)s->nblk * pp;
     PM_TRY(pm_dmalloc(&s->W_lb, nv));
