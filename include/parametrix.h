@@ -435,12 +435,59 @@ pm_status pm_selftest_smooth_c_f32(int N, const float* x, const float* n, const 
  * c != 0 at every node (c = 0 is the library's c = 0 path) and distinct node
  * positions.  Asynchronous; PM_ERR_INVALID_ARG for NULL arrays or N outside
  * 1..2^26, PM_ERR_CUDA if the launch fails.  Its per-pair arithmetic is the
- * host-tested pair function above; the kernel itself has not yet been run on a
- * GPU.
+ * host-tested pair function above.
  */
 pm_status pm_smooth_c_f32(int N, const float* x, const float* n, const float* H,
                           const float* a, const float* gb, const float* c, const float* s,
                           double* out, void* stream);
+
+/*
+ * Helmholtz and modified-Helmholtz surface problems, div_G(a grad_G u) + c u = f
+ * with c real (Sec. 4.2; Thm. second_kind with the parametrix of eq. diff_param
+ * and the remainder of eq. explicit_remainder).  With q = c/a the kernels use
+ * g(r; k), k^2 = q: -(i/4) H0(k r) where q > 0, -K0(sqrt(-q) r)/(2 pi) where q < 0,
+ * log(r)/(2 pi) where q = 0 exactly; the source's q enters through k(y) (at the
+ * nodes in the smooth rule, interpolated on the patch in the singular and near
+ * rules).  There is no null space: sigma + R~ sigma = f and u = K~ sigma, with no
+ * rank-one term and no mean condition on f or u.  Complex c is not supported.
+ *
+ * pm_surface_set_coeff_c: a [N] > 0, grad_a [N][3] or NULL (spectral, as in
+ * pm_surface_set_coeff), c [N] real and finite (host arrays, copied).  It sets a
+ * as pm_surface_set_coeff does and, when some c is non-zero, builds the complex
+ * float64 near-field corrections of the c != 0 operators (Sec. 6.1.1 polar rule
+ * with dyadically graded radial panels, Sec. 6.1.2 subdivision; synchronises).
+ * The surface is then in c mode: pm_apply_R/K/part, pm_solve, pm_solve_multi,
+ * the server and the autotuner refuse it (PM_ERR_INVALID_ARG) until
+ * pm_surface_set_coeff is called again.  All c == 0 is pm_surface_set_coeff.
+ * PM_ERR_INVALID_ARG for NULL a or c, non-finite c (and what pm_surface_set_coeff
+ * rejects), PM_ERR_INTERNAL if a near-field leaf budget is exceeded.
+ */
+pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, const double* grad_a,
+                                 const double* c);
+
+/*
+ * One apply of a c-mode surface in float64: out = R~ sigma (which_K = 0) or
+ * out = K~ sigma (which_K = 1).  sigma and out are complex [N][2] (re, im
+ * interleaved), host arrays (synchronous) or, with on_device = 1, device
+ * arrays (asynchronous on the stream; NULL: the default stream).
+ * PM_ERR_NO_COEFF if the surface is not in c mode, PM_ERR_INVALID_ARG for NULL
+ * arrays or which_K outside {0, 1}.
+ */
+pm_status pm_apply_c(pm_surface* s, int which_K, const double* sigma, double* out,
+                     int on_device, void* stream);
+
+/*
+ * Solve of a c-mode surface: GMRES(opts.gmres_restart) in complex float64 on
+ * sigma + R~ sigma = f from sigma = 0 until the true residual |f - A sigma| is at
+ * most tol |f| (checked after each restart cycle) or maxit Arnoldi steps, then
+ * u = K~ sigma.  f, u and sigma_out (nullable) are complex [N][2] host arrays;
+ * info (nullable): iterations, restart cycles (in .refinements), the final
+ * relative residual, removed_mean = 0.  PM_ERR_NOT_CONVERGED (u and info still
+ * written) when the tolerance is not met; PM_ERR_NO_COEFF if the surface is not
+ * in c mode; PM_ERR_INVALID_ARG for NULL f or u, tol <= 0 or maxit < 1.
+ */
+pm_status pm_solve_c(pm_surface* s, const double* f, double* u, double tol, int maxit,
+                     double* sigma_out, pm_solve_info* info);
 
 /*
  * Serving: continuous batching of solve requests over many operators.

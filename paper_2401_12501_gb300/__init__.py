@@ -186,6 +186,35 @@ class Surface:
         check(_lib.lib().pm_surface_set_coeff(self.handle, ptr(a), ptr(g)),
               "pm_surface_set_coeff")
 
+    def set_coeff_c(self, a, grad_a, c):
+        """a, grad_a as in set_coeff, and a real c [N] (div(a grad u) + c u = f)."""
+        if not np.isrealobj(c):
+            raise ValueError("set_coeff_c: c must be real (complex c is not supported)")
+        a = _f64(a, self.N)
+        g = None if grad_a is None else _f64(grad_a, 3 * self.N)
+        cc = np.ascontiguousarray(np.asarray(c, dtype=np.float64) * np.ones(self.N))
+        check(_lib.lib().pm_surface_set_coeff_c(self.handle, ptr(a), ptr(g), ptr(cc)),
+              "pm_surface_set_coeff_c")
+
+    def apply_c(self, sigma, which="R"):
+        """R~ sigma or K~ sigma of a c != 0 surface (complex128 [N])."""
+        sg = np.ascontiguousarray(np.asarray(sigma, dtype=np.complex128).reshape(self.N))
+        out = np.empty_like(sg)
+        check(_lib.lib().pm_apply_c(self.handle, 1 if which == "K" else 0, ptr(sg), ptr(out), 0,
+                                    None), "pm_apply_c")
+        return out
+
+    def solve_c(self, f, tol=1e-10, maxit=2000, return_sigma=False):
+        """u with div(a grad u) + c u = f on a c != 0 surface; returns (u, info[, sigma])."""
+        fc = np.ascontiguousarray(np.asarray(f, dtype=np.complex128).reshape(self.N))
+        u = np.empty_like(fc)
+        sig = np.empty_like(fc) if return_sigma else None
+        info = PmSolveInfo()
+        check(_lib.lib().pm_solve_c(self.handle, ptr(fc), ptr(u), float(tol), int(maxit),
+                                    ptr(sig), C.byref(info)), "pm_solve_c")
+        out = (u, info)
+        return out + (sig,) if return_sigma else out
+
     def _apply(self, fn, args, sigma, prec, stream, out=None):
         prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         dev = _is_device(sigma)

@@ -297,6 +297,7 @@ static void free_surface(pm_surface* s) {
     pm_fmm_free(s);
     pm_batch_free(s);
     pm_batch_solve_free(s);
+    pm_helm_free(s);
     pm_dfree(s->x); pm_dfree(s->n); pm_dfree(s->H); pm_dfree(s->w); pm_dfree(s->J);
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);
@@ -584,6 +585,7 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
     PM_TRY(pm_near_combine_coeff(s, st));
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     s->has_coeff = true;
+    s->has_c = 0;
     s->graph_epoch++;
     return PM_OK;
 }
@@ -676,6 +678,10 @@ static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
         return PM_ERR_INVALID_ARG;
     }
     if (!s->has_coeff) { pm_set_error("apply: call pm_surface_set_coeff first"); return PM_ERR_NO_COEFF; }
+    if (s->has_c) {
+        pm_set_error("apply: the surface has c != 0 (pm_surface_set_coeff_c): use pm_apply_c");
+        return PM_ERR_INVALID_ARG;
+    }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = s->N;
@@ -808,6 +814,10 @@ extern "C" pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrh
         return PM_ERR_INVALID_ARG;
     }
     if (!s->has_coeff) { pm_set_error("pm_solve: call pm_surface_set_coeff first"); return PM_ERR_NO_COEFF; }
+    if (s->has_c) {
+        pm_set_error("pm_solve: the surface has c != 0 (pm_surface_set_coeff_c): use pm_solve_c");
+        return PM_ERR_INVALID_ARG;
+    }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     const size_t N = s->N;
     if (nrhs > 1 && s->opts.batch_rhs)

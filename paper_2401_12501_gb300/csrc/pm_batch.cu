@@ -2073,6 +2073,10 @@ extern "C" pm_status pm_solve_multi(pm_surface* const* ops, int nops, const int*
             pm_set_error("pm_solve_multi: instance %d has no coefficient", k);
             return PM_ERR_NO_COEFF;
         }
+        if (ops[k]->has_c) {
+            pm_set_error("pm_solve_multi: instance %d has c != 0 (pm_solve_c solves it)", k);
+            return PM_ERR_INVALID_ARG;
+        }
         if (ops[k]->ctx != ops[0]->ctx) {
             pm_set_error("pm_solve_multi: instance %d belongs to another context", k);
             return PM_ERR_INVALID_ARG;

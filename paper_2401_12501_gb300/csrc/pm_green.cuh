@@ -114,6 +114,48 @@ __host__ __device__ inline void green_scaled(double r, double q, double* out)
     }
 }
 
+// green_scaled for any real q: q = 0 is the c~ = 0 Green's function log(r)/(2 pi)
+// (g' = 1/(2 pi r), g'' = -1/(2 pi r^2)).  A coefficient c whose sign changes
+// over the surface passes through q = 0, where the Helmholtz kernel has no limit
+// (it grows like log |q|, Sec. 4.2); the paper's G for c~ = 0 is taken there.
+__host__ __device__ inline void green_scaled_any(double r, double q, double* out)
+{
+    if (q != 0.0) {
+        green_scaled(r, q, out);
+        return;
+    }
+    const double inv2pi = 0.5 / kPi;
+    out[0] = log(r) * inv2pi;
+    out[2] = inv2pi / r;
+    out[4] = -inv2pi / (r * r);
+    out[1] = out[3] = out[5] = 0.0;
+}
+
+// One source's a(y) R and a(y) K for real q(y) = c(y)/a(y), as (re, im) pairs
+// out[0..1] = a(y) R, out[2..3] = a(y) K (eq. explicit_remainder with
+// a(y) G = g(r; k(y)), k(y)^2 = q(y)), r = x - y:
+//   a(y) R = (gb . r^) g' - a(x) (g'' - g'/r) (n.r^)^2 - 2 a(x) H(x) (n.r^) g'
+//            + (c(x) - a(x) q(y)) g,          a(y) K = g,
+// gb = grad_G a(x), n and H the target's normal and mean curvature.
+__host__ __device__ inline void pair_rk_c(double rx, double ry, double rz, double nx, double ny,
+                                          double nz, double H, double a, double gbx, double gby,
+                                          double gbz, double c, double q, double* out)
+{
+    const double r = sqrt(rx * rx + ry * ry + rz * rz);
+    const double inv_r = 1.0 / r;
+    double g[6];
+    green_scaled_any(r, q, g);
+    const double nr = (nx * rx + ny * ry + nz * rz) * inv_r;
+    const double gr = (gbx * rx + gby * ry + gbz * rz) * inv_r;
+    const double t2 = a * nr * nr;
+    const double t1 = gr - 2.0 * a * H * nr;
+    const double t0 = c - a * q;
+    out[0] = t1 * g[2] - t2 * (g[4] - g[2] * inv_r) + t0 * g[0];
+    out[1] = t1 * g[3] - t2 * (g[5] - g[3] * inv_r) + t0 * g[1];
+    out[2] = g[0];
+    out[3] = g[1];
+}
+
 // ---------------------------------------------------------------------------
 // float32 versions for the per-pair smooth sums.  Same methods, tuned to
 // float32: the series for x < 2 with ten unrolled terms (t = x^2/4 <= 1, so

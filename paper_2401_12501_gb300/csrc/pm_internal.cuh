@@ -98,6 +98,7 @@ struct PmSolveWork;
 struct PmFmmTree;
 struct PmBatchWork;
 struct PmBatchSolveWork;
+struct PmHelmWork;
 
 struct pm_surface {
     pm_ctx* ctx = nullptr;
@@ -159,6 +160,15 @@ struct pm_surface {
     double* cK64 = nullptr;       // [nblk*pp]
     float* cR32 = nullptr;        // [nblk*ppad]
     float* cK32 = nullptr;        // [nblk*ppad]
+
+    // c != 0 (pm_surface_set_coeff_c, pm_helm.cu): real c at the nodes, q = c/a,
+    // complex corrections of a(y) R and a(y) K (with the coefficients), work
+    int has_c = 0;
+    double* cc = nullptr;         // [N] c
+    double* qn = nullptr;         // [N] c/a
+    double2* cRc = nullptr;       // [nblk*pp]
+    double2* cKc = nullptr;       // [nblk*pp]
+    PmHelmWork* helm = nullptr;
 
     // per-phase timing (events recorded around launches while enabled)
     bool profiling = false;
@@ -249,6 +259,10 @@ pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const voi
 pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st);
 pm_status pm_tcgemm_check(const PmTcGemm* g);
 void pm_tcgemm_free(PmTcGemm* g);
+
+// c != 0 (pm_nearfield.cu: near field; pm_helm.cu: sums, solve)
+pm_status pm_near_build_c(pm_surface* s);
+void pm_helm_free(pm_surface* s);
 
 // batched applies and solves (pm_batch.cu)
 pm_status pm_apply_batch(pm_surface* s, int kernel_K, const double* sigma, long long ld_sigma,

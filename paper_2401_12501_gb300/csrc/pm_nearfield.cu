@@ -26,6 +26,7 @@
 // target lies within 2*eta*(corner radius) of its centre image, 16 x 16 Gauss
 // rule on each leaf (a geometric a-priori criterion standing in for the
 // adaptive error test of Sec. 6.1.2).
+#include "pm_green.cuh"
 #include "pm_internal.cuh"
 
 #include <algorithm>
@@ -292,6 +293,83 @@ __device__ __forceinline__ void sq_box(int code, double& u0, double& u1, double&
     v1 = v0 + h;
 }
 
+// Breadth-first quadtree subdivision of [-1,1]^2 for the target (xi0, xi1, xi2)
+// against the patch with node positions X: a square splits while the target
+// lies within 2 eta (corner radius) of its centre image, up to max_depth levels.
+// The leaves end in S.sorted in code order (deterministic); returns their count.
+// Called by all threads of the block; a leaf or level overflow sets *err.
+struct NearBfs {
+    int cur[kMaxLevel], next[kMaxLevel], leaf[kMaxLeaves], sorted[kMaxLeaves];
+    int nCur, nNext, nLeaf, overflow;
+};
+
+__device__ int near_leaves(const double* X, int p, double xi0, double xi1, double xi2,
+                           double eta, int max_depth, int max_leaves, NearBfs& S, int* err) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        S.cur[0] = sq_code(0, 0, 0);
+        S.nCur = 1;
+        S.nLeaf = 0;
+        S.overflow = 0;
+    }
+    __syncthreads();
+    const int leaf_cap = min(max_leaves, kMaxLeaves);
+    for (int lev = 0; lev <= max_depth; ++lev) {
+        if (tid == 0) S.nNext = 0;
+        __syncthreads();
+        for (int q = tid; q < S.nCur; q += blockDim.x) {
+            const int code = S.cur[q];
+            double u0, u1, v0, v1;
+            sq_box(code, u0, u1, v0, v1);
+            const double us[5] = {u0, u1, u1, u0, 0.5 * (u0 + u1)};
+            const double vs[5] = {v0, v0, v1, v1, 0.5 * (v0 + v1)};
+            double y[5][3];
+            for (int k = 0; k < 5; ++k) interp_pos(X, p, us[k], vs[k], y[k]);
+            double size = 0;
+            for (int k = 0; k < 4; ++k) {
+                const double dx = y[k][0] - y[4][0], dy = y[k][1] - y[4][1], dz = y[k][2] - y[4][2];
+                size = fmax(size, sqrt(dx * dx + dy * dy + dz * dz));
+            }
+            const double dx = xi0 - y[4][0], dy = xi1 - y[4][1], dz = xi2 - y[4][2];
+            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            const bool split = (lev < max_depth) && (dist < 2.0 * eta * size);
+            if (split) {
+                const int slot = atomicAdd(&S.nNext, 4);
+                if (slot + 4 <= kMaxLevel) {
+                    const int l1 = lev + 1, iu = (code >> 12) & 0xfff, iv = code & 0xfff;
+                    S.next[slot] = sq_code(l1, 2 * iu, 2 * iv);
+                    S.next[slot + 1] = sq_code(l1, 2 * iu + 1, 2 * iv);
+                    S.next[slot + 2] = sq_code(l1, 2 * iu, 2 * iv + 1);
+                    S.next[slot + 3] = sq_code(l1, 2 * iu + 1, 2 * iv + 1);
+                } else {
+                    S.overflow = 1;
+                }
+            } else {
+                const int slot = atomicAdd(&S.nLeaf, 1);
+                if (slot < leaf_cap) S.leaf[slot] = code; else S.overflow = 1;
+            }
+        }
+        __syncthreads();
+        const int nn_ = min(S.nNext, kMaxLevel);
+        for (int q = tid; q < nn_; q += blockDim.x) S.cur[q] = S.next[q];
+        __syncthreads();
+        if (tid == 0) S.nCur = nn_;
+        __syncthreads();
+        if (S.nCur == 0) break;
+    }
+    const int nleaves = min(S.nLeaf, leaf_cap);
+    if (S.overflow && tid == 0) atomicExch(err, PM_DEV_LEAF_OVERFLOW);
+    // deterministic leaf order: rank sort by code
+    for (int q = tid; q < nleaves; q += blockDim.x) {
+        const int c = S.leaf[q];
+        int rank = 0;
+        for (int t = 0; t < nleaves; ++t) rank += (S.leaf[t] < c);
+        S.sorted[rank] = c;
+    }
+    __syncthreads();
+    return nleaves;
+}
+
 __global__ void __launch_bounds__(kQThreads)
 k_near_quad(int p, int nblk, const double* __restrict__ x, const double* __restrict__ J,
             const double* __restrict__ n, const double* __restrict__ H,
@@ -310,8 +388,7 @@ k_near_quad(int p, int nblk, const double* __restrict__ x, const double* __restr
     __shared__ double sLu[PM_GL16 * PM_MAX_P], sLv[PM_GL16 * PM_MAX_P];
     __shared__ double sZ[4 * PM_MAX_P * PM_GL16];     // [4][a][r]
     __shared__ double sF[5 * PM_GL16 * PM_GL16];      // [5][q*16 + r]
-    __shared__ int sCur[kMaxLevel], sNext[kMaxLevel], sLeaf[kMaxLeaves], sSorted[kMaxLeaves];
-    __shared__ int nCur, nNext, nLeaf, overflow;
+    __shared__ NearBfs bfs;
     const double* X = x + (size_t)3 * P * pp;
     const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
     for (int k = tid; k < pp; k += kQThreads) {
@@ -321,75 +398,14 @@ k_near_quad(int p, int nblk, const double* __restrict__ x, const double* __restr
         sD[2 * pp + k] = x[3 * gk + 2] - xi2;
         sJ[k] = J[gk];
     }
-    if (tid == 0) {
-        sCur[0] = sq_code(0, 0, 0);
-        nCur = 1;
-        nLeaf = 0;
-        overflow = 0;
-    }
-    __syncthreads();
-    const int leaf_cap = min(max_leaves, kMaxLeaves);
-    // breadth-first subdivision
-    for (int lev = 0; lev <= max_depth; ++lev) {
-        if (tid == 0) nNext = 0;
-        __syncthreads();
-        for (int s = tid; s < nCur; s += kQThreads) {
-            const int code = sCur[s];
-            double u0, u1, v0, v1;
-            sq_box(code, u0, u1, v0, v1);
-            const double us[5] = {u0, u1, u1, u0, 0.5 * (u0 + u1)};
-            const double vs[5] = {v0, v0, v1, v1, 0.5 * (v0 + v1)};
-            double y[5][3];
-            for (int k = 0; k < 5; ++k) interp_pos(X, p, us[k], vs[k], y[k]);
-            double size = 0;
-            for (int k = 0; k < 4; ++k) {
-                const double dx = y[k][0] - y[4][0], dy = y[k][1] - y[4][1], dz = y[k][2] - y[4][2];
-                size = fmax(size, sqrt(dx * dx + dy * dy + dz * dz));
-            }
-            const double dx = xi0 - y[4][0], dy = xi1 - y[4][1], dz = xi2 - y[4][2];
-            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
-            const bool split = (lev < max_depth) && (dist < 2.0 * eta * size);
-            if (split) {
-                const int slot = atomicAdd(&nNext, 4);
-                if (slot + 4 <= kMaxLevel) {
-                    const int l1 = lev + 1, iu = (code >> 12) & 0xfff, iv = code & 0xfff;
-                    sNext[slot] = sq_code(l1, 2 * iu, 2 * iv);
-                    sNext[slot + 1] = sq_code(l1, 2 * iu + 1, 2 * iv);
-                    sNext[slot + 2] = sq_code(l1, 2 * iu, 2 * iv + 1);
-                    sNext[slot + 3] = sq_code(l1, 2 * iu + 1, 2 * iv + 1);
-                } else {
-                    overflow = 1;
-                }
-            } else {
-                const int slot = atomicAdd(&nLeaf, 1);
-                if (slot < leaf_cap) sLeaf[slot] = code; else overflow = 1;
-            }
-        }
-        __syncthreads();
-        const int nn_ = min(nNext, kMaxLevel);
-        for (int s = tid; s < nn_; s += kQThreads) sCur[s] = sNext[s];
-        __syncthreads();
-        if (tid == 0) nCur = nn_;
-        __syncthreads();
-        if (nCur == 0) break;
-    }
-    const int nleaves = min(nLeaf, leaf_cap);
-    if (overflow && tid == 0) atomicExch(err, PM_DEV_LEAF_OVERFLOW);
-    // deterministic leaf order: rank sort by code
-    for (int s = tid; s < nleaves; s += kQThreads) {
-        const int c = sLeaf[s];
-        int rank = 0;
-        for (int t = 0; t < nleaves; ++t) rank += (sLeaf[t] < c);
-        sSorted[rank] = c;
-    }
-    __syncthreads();
+    const int nleaves = near_leaves(X, p, xi0, xi1, xi2, eta, max_depth, max_leaves, bfs, err);
     const int a_own = tid / p, b_own = tid - (tid / p) * p;
     double acc[5] = {0, 0, 0, 0, 0};
     const double n0 = n[3 * i], n1 = n[3 * i + 1], n2 = n[3 * i + 2];
     const double Hi = H[i];
     for (int L = 0; L < nleaves; ++L) {
         double u0, u1, v0, v1;
-        sq_box(sSorted[L], u0, u1, v0, v1);
+        sq_box(bfs.sorted[L], u0, u1, v0, v1);
         const double hu = 0.5 * (u1 - u0), hv = 0.5 * (v1 - v0);
         if (tid < PM_GL16) lagrange(u0 + hu * (cT.g16t[tid] + 1.0), p, sLu + tid * p);
         else if (tid < 2 * PM_GL16)
@@ -502,6 +518,242 @@ __global__ void k_combine(int nblk, int pp, int ppad, const int* __restrict__ bl
     cK64[o] = ck;
     cR32[e] = (float)cr;
     cK32[e] = (float)ck;
+}
+
+// ------------------------------------------------------------------ c != 0 quadrature
+// Weights of a(y) R and a(y) K for real c (eq. explicit_remainder with
+// a(y) G = g(r; k(y)), pm_green.cuh), complex as (re, im):
+//   W^R_ik = int a(y) R(x_i, y) l_k J~ du dv,  W^K_ik = int g(|x_i - y|; k(y)) l_k J~ du dv.
+// The kernels depend on the source through k(y)^2 = q(y) = c(y)/a(y), which is
+// interpolated on the patch from its nodes with the tensor Lagrange basis, so
+// these weights hold the coefficients and are built per coefficient field.
+// Self patch: the polar rule of k_self_quad, with dyadic radial panels
+// [0, L 2^-12], [L 2^-12, L 2^-11], ..., [L/2, L] in place of the product-log
+// panel: here g = log(r) A(r) + B(r) with A = J0(kr) or I0(kr) not constant, and
+// R has r log r terms (Thm. remainder); each graded panel sees an analytic
+// integrand, and the innermost one carries O(L^2 2^-24 log) of the integral.
+constexpr int kSelfLevelsC = 12;
+constexpr int kSelfPanelsC = kSelfLevelsC + 1;
+
+__global__ void __launch_bounds__(kQThreads)
+k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restrict__ J,
+              const double* __restrict__ nn, const double* __restrict__ H,
+              const double* __restrict__ a, const double* __restrict__ g,
+              const double* __restrict__ c, const double* __restrict__ qn,
+              const int* __restrict__ th_off, const double* __restrict__ th_ang,
+              const double* __restrict__ th_w, const double* __restrict__ th_L,
+              const int* __restrict__ row_ptr, double2* __restrict__ WR,
+              double2* __restrict__ WK) {
+    extern __shared__ double sm[];
+    const int pp = p * p;
+    double* sD = sm;                       // [3][pp]
+    double* sJ = sD + 3 * pp;              // [pp]
+    double* sQ = sJ + pp;                  // [pp]
+    double* sLu = sQ + pp;                 // [128][p]
+    double* sLv = sLu + kQThreads * p;     // [128][p]
+    double* sF = sLv + kQThreads * p;      // [4][128]
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int P = i / pp, loc = i - P * pp;
+    const double u0 = cT.t[loc / p], v0 = cT.t[loc % p];
+    const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
+    for (int k = tid; k < pp; k += kQThreads) {
+        const size_t gk = (size_t)P * pp + k;
+        sD[k] = x[3 * gk] - xi0;
+        sD[pp + k] = x[3 * gk + 1] - xi1;
+        sD[2 * pp + k] = x[3 * gk + 2] - xi2;
+        sJ[k] = J[gk];
+        sQ[k] = qn[gk];
+    }
+    const double n0 = nn[3 * i], n1 = nn[3 * i + 1], n2 = nn[3 * i + 2];
+    const double Hi = H[i], ai = a[i], ci = c[i];
+    const double g0 = g[3 * i], g1 = g[3 * i + 1], g2 = g[3 * i + 2];
+    const int t0 = th_off[loc], t1 = th_off[loc + 1];
+    const int npts = (t1 - t0) * (kSelfPanelsC * PM_GL16);
+    double acc[4] = {0, 0, 0, 0};
+    const int a_own = tid / p, b_own = tid - (tid / p) * p;
+    __syncthreads();
+    for (int base = 0; base < npts; base += kQThreads) {
+        const int q = base + tid;
+        double* lu = sLu + tid * p;
+        double* lv = sLv + tid * p;
+        double f[4] = {0, 0, 0, 0};
+        if (q < npts) {
+            const int kth = t0 + q / (kSelfPanelsC * PM_GL16);
+            const int rj = q % (kSelfPanelsC * PM_GL16);
+            const int panel = rj / PM_GL16, node = rj % PM_GL16;
+            const double L = th_L[kth];
+            const double lo = panel == 0 ? 0.0 : ldexp(L, panel - kSelfPanelsC);
+            const double h = ldexp(L, panel - kSelfLevelsC) - lo;
+            const double r = lo + 0.5 * h * (cT.g16t[node] + 1.0);
+            const double wr = 0.5 * h * cT.g16w[node];
+            double sn, cs;
+            sincos(th_ang[kth], &sn, &cs);
+            lagrange(u0 + r * cs, p, lu);
+            lagrange(v0 + r * sn, p, lv);
+            double d0 = 0, d1 = 0, d2 = 0, jj = 0, qq = 0;
+            for (int aa = 0; aa < p; ++aa) {
+                double z0 = 0, z1 = 0, z2 = 0, zj = 0, zq = 0;
+                for (int bb = 0; bb < p; ++bb) {
+                    const double l = lv[bb];
+                    const int k = aa * p + bb;
+                    z0 += sD[k] * l;
+                    z1 += sD[pp + k] * l;
+                    z2 += sD[2 * pp + k] * l;
+                    zj += sJ[k] * l;
+                    zq += sQ[k] * l;
+                }
+                d0 += lu[aa] * z0;
+                d1 += lu[aa] * z1;
+                d2 += lu[aa] * z2;
+                jj += lu[aa] * zj;
+                qq += lu[aa] * zq;
+            }
+            double out[4];
+            pm_green::pair_rk_c(-d0, -d1, -d2, n0, n1, n2, Hi, ai, g0, g1, g2, ci, qq, out);
+            const double bw = th_w[kth] * wr * r * jj;
+            for (int k = 0; k < 4; ++k) f[k] = bw * out[k];
+        } else {
+            for (int aa = 0; aa < p; ++aa) { lu[aa] = 0.0; lv[aa] = 0.0; }
+        }
+        for (int k = 0; k < 4; ++k) sF[k * kQThreads + tid] = f[k];
+        __syncthreads();
+        if (tid < pp) {
+            const int lim = min(kQThreads, npts - base);
+            for (int e = 0; e < lim; ++e) {
+                const double cc = sLu[e * p + a_own] * sLv[e * p + b_own];
+                for (int k = 0; k < 4; ++k) acc[k] += sF[k * kQThreads + e] * cc;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < pp) {
+        const size_t o = (size_t)row_ptr[i] * pp + tid;     // own patch: the row's first block
+        WR[o] = make_double2(acc[0], acc[1]);
+        WK[o] = make_double2(acc[2], acc[3]);
+    }
+}
+
+// Near, non-self patches: the subdivision of k_near_quad, 16 x 16 Gauss points
+// per leaf, the target's given normal.
+__global__ void __launch_bounds__(kQThreads)
+k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
+              const double* __restrict__ n, const double* __restrict__ H,
+              const double* __restrict__ a, const double* __restrict__ g,
+              const double* __restrict__ c, const double* __restrict__ qn,
+              const int* __restrict__ blk_row, const int* __restrict__ blk_patch,
+              const int* __restrict__ row_ptr, double eta, int max_depth, int max_leaves,
+              double2* __restrict__ WR, double2* __restrict__ WK, int* __restrict__ err) {
+    const int b = blockIdx.x;
+    const int i = blk_row[b];
+    if (b == row_ptr[i]) return;   // the self block is done by k_self_quad_c
+    const int P = blk_patch[b];
+    const int pp = p * p;
+    const int tid = threadIdx.x;
+    __shared__ double sD[3 * PM_MAX_P * PM_MAX_P];
+    __shared__ double sJ[PM_MAX_P * PM_MAX_P];
+    __shared__ double sQ[PM_MAX_P * PM_MAX_P];
+    __shared__ double sLu[PM_GL16 * PM_MAX_P], sLv[PM_GL16 * PM_MAX_P];
+    __shared__ double sZ[5 * PM_MAX_P * PM_GL16];     // [5][a][r]
+    __shared__ double sF[4 * PM_GL16 * PM_GL16];      // [4][q*16 + r]
+    __shared__ NearBfs bfs;
+    const double* X = x + (size_t)3 * P * pp;
+    const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
+    for (int k = tid; k < pp; k += kQThreads) {
+        const size_t gk = (size_t)P * pp + k;
+        sD[k] = x[3 * gk] - xi0;
+        sD[pp + k] = x[3 * gk + 1] - xi1;
+        sD[2 * pp + k] = x[3 * gk + 2] - xi2;
+        sJ[k] = J[gk];
+        sQ[k] = qn[gk];
+    }
+    const int nleaves = near_leaves(X, p, xi0, xi1, xi2, eta, max_depth, max_leaves, bfs, err);
+    const int a_own = tid / p, b_own = tid - (tid / p) * p;
+    double acc[4] = {0, 0, 0, 0};
+    const double n0 = n[3 * i], n1 = n[3 * i + 1], n2 = n[3 * i + 2];
+    const double Hi = H[i], ai = a[i], ci = c[i];
+    const double g0 = g[3 * i], g1 = g[3 * i + 1], g2 = g[3 * i + 2];
+    constexpr int kQ2 = PM_GL16 * PM_GL16;
+    for (int L = 0; L < nleaves; ++L) {
+        double u0, u1, v0, v1;
+        sq_box(bfs.sorted[L], u0, u1, v0, v1);
+        const double hu = 0.5 * (u1 - u0), hv = 0.5 * (v1 - v0);
+        if (tid < PM_GL16) lagrange(u0 + hu * (cT.g16t[tid] + 1.0), p, sLu + tid * p);
+        else if (tid < 2 * PM_GL16)
+            lagrange(v0 + hv * (cT.g16t[tid - PM_GL16] + 1.0), p, sLv + (tid - PM_GL16) * p);
+        __syncthreads();
+        // Z[f][a][r] = sum_b F_f[a][b] l_b(v_r) for F = D (3 components), J, q
+        for (int e = tid; e < 5 * p * PM_GL16; e += kQThreads) {
+            const int cf = e / (p * PM_GL16), rem = e - cf * p * PM_GL16;
+            const int aa = rem / PM_GL16, r = rem - aa * PM_GL16;
+            const double* src = (cf < 3) ? (sD + cf * pp) : (cf == 3 ? sJ : sQ);
+            double z = 0;
+            for (int bb = 0; bb < p; ++bb) z += src[aa * p + bb] * sLv[r * p + bb];
+            sZ[(cf * p + aa) * PM_GL16 + r] = z;
+        }
+        __syncthreads();
+        for (int e = tid; e < kQ2; e += kQThreads) {
+            const int qn_ = e / PM_GL16, r = e - qn_ * PM_GL16;
+            double v5[5] = {0, 0, 0, 0, 0};
+            for (int aa = 0; aa < p; ++aa) {
+                const double l = sLu[qn_ * p + aa];
+                for (int cf = 0; cf < 5; ++cf) v5[cf] += l * sZ[(cf * p + aa) * PM_GL16 + r];
+            }
+            double out[4];
+            pm_green::pair_rk_c(-v5[0], -v5[1], -v5[2], n0, n1, n2, Hi, ai, g0, g1, g2, ci, v5[4],
+                                out);
+            const double wgt = hu * cT.g16w[qn_] * hv * cT.g16w[r] * v5[3];
+            for (int k = 0; k < 4; ++k) sF[k * kQ2 + e] = wgt * out[k];
+        }
+        __syncthreads();
+        if (tid < pp) {
+            for (int r = 0; r < PM_GL16; ++r) {
+                double t4[4] = {0, 0, 0, 0};
+                for (int qn_ = 0; qn_ < PM_GL16; ++qn_) {
+                    const double l = sLu[qn_ * p + a_own];
+                    const int e = qn_ * PM_GL16 + r;
+                    for (int k = 0; k < 4; ++k) t4[k] += sF[k * kQ2 + e] * l;
+                }
+                const double lb = sLv[r * p + b_own];
+                for (int k = 0; k < 4; ++k) acc[k] += t4[k] * lb;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < pp) {
+        const size_t o = (size_t)b * pp + tid;
+        WR[o] = make_double2(acc[0], acc[1]);
+        WK[o] = make_double2(acc[2], acc[3]);
+    }
+}
+
+// Corrections in place: C = (W - w_j a(y)G(x_i, x_j)) / a_j off the diagonal (the
+// smooth rule's term of the node), C_ii = W_ii / a_i; they multiply sigma_j.
+__global__ void k_combine_c(int nblk, int pp, const int* __restrict__ blk_row,
+                            const int* __restrict__ blk_patch, const double* __restrict__ x,
+                            const double* __restrict__ n, const double* __restrict__ H,
+                            const double* __restrict__ w, const double* __restrict__ a,
+                            const double* __restrict__ g, const double* __restrict__ c,
+                            const double* __restrict__ qn, double2* __restrict__ CR,
+                            double2* __restrict__ CK) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)nblk * pp) return;
+    const int b = (int)(e / pp), k = (int)(e - (size_t)b * pp);
+    const int i = blk_row[b], j = blk_patch[b] * pp + k;
+    double2 wr = CR[e], wk = CK[e];
+    const double inv_a = 1.0 / a[j];
+    if (j != i) {
+        double out[4];
+        pm_green::pair_rk_c(x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
+                            x[3 * i + 2] - x[3 * j + 2], n[3 * i], n[3 * i + 1], n[3 * i + 2],
+                            H[i], a[i], g[3 * i], g[3 * i + 1], g[3 * i + 2], c[i], qn[j], out);
+        wr.x -= w[j] * out[0];
+        wr.y -= w[j] * out[1];
+        wk.x -= w[j] * out[2];
+        wk.y -= w[j] * out[3];
+    }
+    CR[e] = make_double2(wr.x * inv_a, wr.y * inv_a);
+    CK[e] = make_double2(wk.x * inv_a, wk.y * inv_a);
 }
 
 // ------------------------------------------------------------------ correction SpMV
@@ -838,5 +1090,42 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
                 N, s->ppad, s->row_ptr, s->blk_patch, which_K ? s->cK32 : s->cR32, s->sig32,
                 reinterpret_cast<const float2*>(s->partial), nsplit, use_near, out, s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+// Complex corrections of the c != 0 operators (weights with the coefficients,
+// then minus the smooth rule's node terms), into s->cRc, s->cKc.
+pm_status pm_near_build_c(pm_surface* s) {
+    std::lock_guard<std::mutex> build_lock(g_near_build_mu);
+    const int N = s->N, p = s->p, pp = s->pp;
+    QuadTables T;
+    pm_build_tables(p, &T);
+    PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
+    PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
+    const size_t smem = sizeof(double) * (5 * (size_t)pp + 2 * (size_t)kQThreads * p + 4 * kQThreads);
+    if (smem > 48 * 1024)
+        PM_CUDA_TRY(cudaFuncSetAttribute(k_self_quad_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    k_self_quad_c<<<N, kQThreads, smem>>>(N, p, s->x, s->J, s->npatch_n, s->H, s->a, s->g, s->cc,
+                                          s->qn, s->th_off, s->th_ang, s->th_w, s->th_L,
+                                          s->row_ptr, s->cRc, s->cKc);
+    PM_CUDA_TRY(cudaGetLastError());
+    k_near_quad_c<<<s->nblk, kQThreads>>>(p, s->x, s->J, s->n, s->H, s->a, s->g, s->cc, s->qn,
+                                          s->blk_row, s->blk_patch, s->row_ptr, s->opts.near_eta,
+                                          std::min(s->opts.near_max_depth, 12),
+                                          s->opts.near_max_leaves, s->cRc, s->cKc, s->dev_err);
+    PM_CUDA_TRY(cudaGetLastError());
+    const size_t ne = (size_t)s->nblk * pp;
+    k_combine_c<<<pm_ceil_div((long long)ne, 256), 256>>>(s->nblk, pp, s->blk_row, s->blk_patch,
+                                                          s->x, s->n, s->H, s->w, s->a, s->g,
+                                                          s->cc, s->qn, s->cRc, s->cKc);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    int herr = 0;
+    PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != PM_DEV_OK) {
+        pm_set_error("c != 0 near-field quadrature: device check %d failed (leaf budget exceeded)", herr);
+        return PM_ERR_INTERNAL;
+    }
     return PM_OK;
 }

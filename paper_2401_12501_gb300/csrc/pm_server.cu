@@ -391,6 +391,10 @@ extern "C" pm_status pm_server_submit(pm_server* sv, pm_surface* op, const doubl
         pm_set_error("pm_server_submit: operator has no coefficient");
         return PM_ERR_NO_COEFF;
     }
+    if (op->has_c) {
+        pm_set_error("pm_server_submit: operator has c != 0 (pm_solve_c solves it)");
+        return PM_ERR_INVALID_ARG;
+    }
     std::lock_guard<std::mutex> lk(sv->mu);
     Operator*& o = sv->borrowed[op];
     if (!o) {

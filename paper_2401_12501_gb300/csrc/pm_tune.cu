@@ -136,6 +136,10 @@ extern "C" pm_status pm_surface_autotune(pm_surface* s, int nrhs, pm_precision p
         pm_set_error("pm_surface_autotune: call pm_surface_set_coeff first");
         return PM_ERR_NO_COEFF;
     }
+    if (s->has_c) {
+        pm_set_error("pm_surface_autotune: the surface has c != 0");
+        return PM_ERR_INVALID_ARG;
+    }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     PM_CUDA_TRY(cudaDeviceSynchronize());
     const pm_knobs orig = knobs_of(s);

@@ -1,0 +1,228 @@
+"""c != 0 on the device (Sec. 4.2, Sec. 7.1, Sec. 7.4): pm_surface_set_coeff_c,
+pm_apply_c and pm_solve_c against the float64 oracle and the closed forms.
+
+* Applies: R~ sigma and K~ sigma (smooth rule + complex near-field corrections)
+  against the oracle's operators on small surfaces, for the modified-Helmholtz
+  sign (c/a < 0, real kernel), the Helmholtz sign (c/a > 0, complex kernel),
+  the paper's variable-coefficient example, and a variable Helmholtz-sign c
+  (k(y) interpolated over each patch in the complex kernel).
+* Unit sphere, a = 1 (Sec. 7.1): K~ Y_l = kappa_l Y_l and R~ Y_l = rho_l Y_l with
+  the Funk-Hecke values of the continuous kernels, and the solve returns
+  sum f_lm Y_l^m / (c - l(l+1)).
+* Sec. 7.4's real example (a linear in z, c = -4 - e^{x/2}) with the manufactured
+  v = -1/|x - x0|: the solve equals the oracle's LU solve and recovers v, with the
+  error falling as the surface is refined.
+"""
+
+import numpy as np
+import pytest
+
+from conftest import oracle_processes
+from workloads import cubed_sphere, real_sph_harm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2401_12501_gb300 as pm
+    c = pm.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_w(u, v, w):
+    return float(np.sqrt(np.dot(w, np.abs(u - v) ** 2) / np.dot(w, np.abs(v) ** 2)))
+
+
+def _e4_real(x, n):
+    """Sec. 7.4: a linear in z (1 to 3 over z in [-2, 2]), c = -4 - exp(x/2)."""
+    from workloads.coefficients import _tangential
+    ga = np.tile([0.0, 0.0, 0.5], (len(x), 1))
+    return 2.0 + 0.5 * x[:, 2], _tangential(ga, n), -4.0 - np.exp(x[:, 0] / 2)
+
+
+def _helmholtz_variable(x, n):
+    """a = 1 + e^z, c = 4 (1 + 0.2 y): the real part of the paper's complex
+    example (Sec. 7.4), Helmholtz sign everywhere, k(y) varying over each patch."""
+    from workloads.coefficients import _tangential
+    ez = np.exp(x[:, 2])
+    ga = np.stack([0 * ez, 0 * ez, ez], 1)
+    return 1.0 + ez, _tangential(ga, n), 4.0 * (1 + 0.2 * x[:, 1])
+
+
+def _constant(c):
+    def f(x, n):
+        N = len(x)
+        return np.ones(N), np.zeros((N, 3)), np.full(N, c)
+    return f
+
+
+def _gpu(ctx, s, coeffs):
+    import paper_2401_12501_gb300 as pm
+    a, ga, c = coeffs(s.nodes, s.normals)
+    S = pm.Surface.from_fixture(ctx, s)
+    S.set_coeff_c(a, ga, c)
+    return S, a, ga, c
+
+
+def _oracle(s, a, ga, c, rows=None):
+    from oracle.operator import Discretization, NearField
+    d = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights, a, ga,
+                       s.npatch, s.p, c=c)
+    return d, NearField(d, rows=rows, processes=oracle_processes())
+
+
+CASES = {
+    "sphere_216_c-4": (lambda: cubed_sphere(1, 6), _constant(-4.0)),
+    "sphere_216_c+4": (lambda: cubed_sphere(1, 6), _constant(4.0)),
+    "ellipsoid_216_sec74": (lambda: cubed_sphere(1, 6, axes=(1.0, 1.5, 2.0)), _e4_real),
+    "ellipsoid_216_helmholtz_variable": (lambda: cubed_sphere(1, 6, axes=(1.0, 1.5, 2.0)),
+                                         _helmholtz_variable),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_c_applies_match_oracle(ctx, case):
+    from oracle.operator import apply_K, apply_R
+    make, coeffs = CASES[case]
+    s = make()
+    S, a, ga, c = _gpu(ctx, s, coeffs)
+    d, nf = _oracle(s, a, ga, c)
+    rng = np.random.default_rng(21)
+    sigma = rng.standard_normal(s.N) + 0.5 + 1j * rng.standard_normal(s.N)
+    eR = rel(S.apply_c(sigma, "R"), apply_R(d, nf, sigma))
+    eK = rel(S.apply_c(sigma, "K"), apply_K(d, nf, sigma))
+    print(f"{case}: R {eR:.2e}, K {eK:.2e}")
+    assert eR < 1e-10, eR
+    assert eK < 1e-10, eK
+    # element-wise at the float64 tolerance, on the largest entries' scale
+    yR, oR = S.apply_c(sigma, "R"), apply_R(d, nf, sigma)
+    assert np.abs(yR - oR).max() <= 1e-10 * np.abs(oR).max()
+    S.close()
+
+
+@pytest.mark.parametrize("c", [-4.0, 4.0])
+def test_sphere_shifted_eigenvalues(ctx, c):
+    """Sec. 7.1: adding c shifts the eigenvalues -l(l+1) of the Laplace-Beltrami
+    operator; K~ and R~ reproduce the Funk-Hecke eigenvalues of the parametrix and
+    the remainder, and the solve divides each harmonic by c - l(l+1)."""
+    from test_oracle_helmholtz import sphere_eigenvalues
+    s = cubed_sphere(2, 8)                       # 1,536 nodes
+    S, *_ = _gpu(ctx, s, _constant(c))
+    for l, m in [(0, 0), (1, 0), (2, 1), (3, -3), (5, 4)]:
+        Y = real_sph_harm(l, m, s.nodes)
+        kap, rho = sphere_eigenvalues(1.0, c, l)
+        eK = np.abs(S.apply_c(Y, "K") - kap * Y).max()
+        eR = np.abs(S.apply_c(Y, "R") - rho * Y).max()
+        print(f"c={c} l={l}: K {eK:.2e} R {eR:.2e}")
+        assert eK < 1e-8, (l, eK)
+        assert eR < 1e-5, (l, eR)
+    terms = [(1, 0, 1.0), (3, 3, -0.5), (0, 0, 0.25), (2, -1, 0.7)]
+    f = sum(cf * real_sph_harm(l, m, s.nodes) for l, m, cf in terms)
+    uex = sum(cf * real_sph_harm(l, m, s.nodes) / (c - l * (l + 1)) for l, m, cf in terms)
+    u, info = S.solve_c(f, tol=1e-12)
+    err = rel_w(u, uex, s.weights)
+    print(f"c={c}: solve error {err:.2e}, {info.iterations} iterations, residual {info.residual:.1e}")
+    assert info.residual <= 1e-12
+    assert err < 1e-7, err                       # measured 6.8e-9 (c = -4), 1.5e-8 (c = 4)
+    assert np.abs(u.imag).max() < 1e-6 * np.abs(u).max()   # real c, real f: real u
+    S.close()
+
+
+@pytest.mark.parametrize("c", [-4.0, 4.0])
+def test_sphere_four_harmonic_problem(ctx, c):
+    """The paper's sphere test (Sec. 7.1): a random combination of Y_1^0, Y_3^3,
+    Y_10^6, Y_10^7 with c added, on the 6,144-node cubed sphere."""
+    from workloads import four_harmonic_problem
+    s = cubed_sphere(4, 8)
+    f, _ = four_harmonic_problem(s, seed=0)
+    rng = np.random.default_rng(0)
+    coef = rng.standard_normal(4)
+    uex = sum(cf * real_sph_harm(l, m, s.nodes) / (c - l * (l + 1))
+              for cf, (l, m) in zip(coef, [(1, 0), (3, 3), (10, 6), (10, 7)]))
+    S, *_ = _gpu(ctx, s, _constant(c))
+    u, info = S.solve_c(f, tol=1e-12)
+    err = rel_w(u, uex, s.weights)
+    print(f"c={c}: four-harmonic error {err:.2e}, {info.iterations} iterations")
+    assert info.residual <= 1e-12
+    assert err < 1e-7, err                       # measured 1.1e-8 (c = -4), 3.9e-9 (c = 4)
+    S.close()
+
+
+def _manufactured(s, a, ga, c):
+    """v = -1/|x - x0| and f = div_G(a grad_G v) + c v from the closed-form
+    gradient and Hessian of v (Lap v = 0), as in the oracle's Sec. 7.4 pin."""
+    x0 = np.array([-3.0, -3.0, 4.0])
+    dx = s.nodes - x0
+    rho = np.linalg.norm(dx, axis=1)
+    v = -1.0 / rho
+    grad = dx / rho[:, None] ** 3
+    dn = np.sum(grad * s.normals, 1)
+    dnn = 1.0 / rho ** 3 - 3 * np.sum(dx * s.normals, 1) ** 2 / rho ** 5
+    lap_G = -2 * s.curvature * dn - dnn
+    grad_G = grad - s.normals * dn[:, None]
+    return np.sum(ga * grad_G, 1) + a * lap_G + c * v, v
+
+
+def test_solve_matches_oracle_variable_coefficients(ctx):
+    """Sec. 7.4's real example on the 216-node ellipsoid: pm_solve_c's u equals the
+    oracle's LU solve (1e-8, the float64 solve gate) and the manufactured v
+    (the oracle measured 2.0e-4 at this size)."""
+    from oracle.solve import solve
+    s = cubed_sphere(1, 6, axes=(1.0, 1.5, 2.0))
+    S, a, ga, c = _gpu(ctx, s, _e4_real)
+    f, v = _manufactured(s, a, ga, c)
+    u, info = S.solve_c(f, tol=1e-13)
+    d, nf = _oracle(s, a, ga, c)
+    uo = solve(d, nf, f)
+    print(f"sec74 216: vs oracle {rel_w(u, uo, s.weights):.2e}, vs v {rel_w(u, v, s.weights):.2e}")
+    assert rel_w(u, uo, s.weights) < 1e-8        # measured 7.9e-13
+    assert rel_w(u, v, s.weights) < 1e-3         # measured 1.98e-4
+    assert np.abs(u.imag).max() < 1e-12 * np.abs(u).max()   # real c < 0: real kernels
+    S.close()
+
+
+def test_manufactured_solution_converges(ctx):
+    """The same problem on finer ellipsoids (8 x 8 nodes per patch): the error
+    against v falls with refinement."""
+    errs = []
+    for m in (1, 2, 3):
+        s = cubed_sphere(m, 8, axes=(1.0, 1.5, 2.0))
+        S, a, ga, c = _gpu(ctx, s, _e4_real)
+        f, v = _manufactured(s, a, ga, c)
+        u, info = S.solve_c(f, tol=1e-12)
+        errs.append(rel_w(u, v, s.weights))
+        print(f"N={s.N}: error {errs[-1]:.2e}, {info.iterations} iterations")
+        S.close()
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[-1] < 1e-8, errs                 # measured 2.1e-5, 2.4e-8, 1.05e-9
+
+
+def test_c_mode_entry_points(ctx):
+    """A c != 0 surface refuses the c = 0 entry points; set_coeff returns it to
+    c = 0, and an all-zero c is the c = 0 operator."""
+    import paper_2401_12501_gb300 as pm
+    s = cubed_sphere(1, 6)
+    S, a, ga, c = _gpu(ctx, s, _constant(-2.0))
+    sigma = np.ones(s.N)
+    with pytest.raises(pm.PmError):
+        S.apply_R(sigma, "fp64")
+    with pytest.raises(pm.PmError):
+        S.solve(np.zeros(s.N))
+    S.set_coeff(np.ones(s.N))
+    y0 = S.apply_R(sigma, "fp64")
+    with pytest.raises(pm.PmError):
+        S.apply_c(sigma, "R")
+    S.set_coeff_c(np.ones(s.N), None, np.zeros(s.N))
+    assert np.array_equal(S.apply_R(sigma, "fp64"), y0)
+    with pytest.raises(ValueError):
+        S.set_coeff_c(np.ones(s.N), None, np.full(s.N, 1.0 + 1.0j))
+    S.close()

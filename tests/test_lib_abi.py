@@ -56,6 +56,9 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.pm_surface_autotune(None, 1, 1, 5, None) == 1
     assert lib.pm_ctx_info(None, None, 0, None) == 1
     assert lib.pm_surface_clone(None, None) == 1
+    assert lib.pm_surface_set_coeff_c(None, None, None, None) == 1
+    assert lib.pm_apply_c(None, 0, None, None, 0, None) == 1
+    assert lib.pm_solve_c(None, None, None, 1e-8, 10, None, None) == 1
 
 
 def _header_struct_fields(name):
