@@ -751,6 +751,106 @@ def run_paper(args, dev):
     return out
 
 
+def run_micro_helmholtz(args):
+    """Three float64 c != 0 remainder applies on the 1,536-node unit sphere (a = 1,
+    c = --micro-c): the launches an ncu capture of k_direct_c64 looks at."""
+    import numpy as np
+    import paper_2401_12501_gb300 as pm
+    from workloads import cubed_sphere
+    ctx = pm.Context(0)
+    sf = cubed_sphere(2, 8)
+    s = pm.Surface.from_fixture(ctx, sf)
+    s.set_coeff_c(np.ones(sf.N), np.zeros((sf.N, 3)), np.full(sf.N, args.micro_c))
+    sig = np.random.default_rng(1).standard_normal(sf.N) + 0j
+    for _ in range(3):
+        y = s.apply_c(sig, "R")
+    print(json.dumps({"micro": "helmholtz", "c": args.micro_c, "N": sf.N,
+                      "max_abs": float(np.abs(y).max())}))
+    s.close()
+    ctx.close()
+
+
+def run_helmholtz(args, dev):
+    """c != 0 (Sec. 4.2) on the device in float64: the paper's sphere test with c
+    added (Sec. 7.1: four harmonics incl. l = 10, u = sum f_lm Y / (c - l(l+1))) and
+    its real variable-coefficient example (Sec. 7.4: a linear in z, c = -4 - e^{x/2},
+    manufactured v = -1/|x - x0|) on cubed-sphere ellipsoids; near-field build and
+    solve times, error against the exact solution, and the float64 smooth sum's
+    pair rate (the dominant kernel, k_direct_c64)."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import cubed_sphere, four_harmonic_problem, real_sph_harm
+    from workloads.coefficients import _tangential
+    ctx = pm.Context(dev.index or 0)
+    out = {"tol": 1e-12, "arithmetic": "complex float64", "problems": {}}
+
+    def e4(x, n):
+        ga = np.tile([0.0, 0.0, 0.5], (len(x), 1))
+        return 2.0 + 0.5 * x[:, 2], _tangential(ga, n), -4.0 - np.exp(x[:, 0] / 2)
+
+    def manufactured(sf, a, ga, c):
+        x0 = np.array([-3.0, -3.0, 4.0])
+        dx = sf.nodes - x0
+        rho = np.linalg.norm(dx, axis=1)
+        v = -1.0 / rho
+        grad = dx / rho[:, None] ** 3
+        dn = np.sum(grad * sf.normals, 1)
+        dnn = 1.0 / rho ** 3 - 3 * np.sum(dx * sf.normals, 1) ** 2 / rho ** 5
+        return (np.sum(ga * (grad - sf.normals * dn[:, None]), 1) +
+                a * (-2 * sf.curvature * dn - dnn) + c * v), v
+
+    cases = []
+    for cval in (-4.0, 4.0):
+        sf = cubed_sphere(4, 8)
+        f, _ = four_harmonic_problem(sf, seed=0)
+        coef = np.random.default_rng(0).standard_normal(4)
+        uex = sum(cf * real_sph_harm(l, m, sf.nodes) / (cval - l * (l + 1))
+                  for cf, (l, m) in zip(coef, [(1, 0), (3, 3), (10, 6), (10, 7)]))
+        N = sf.N
+        cases.append((f"sphere_{N}_c{cval:+g}", sf, np.ones(N), np.zeros((N, 3)),
+                      np.full(N, cval), f, uex))
+    for m in (3, 5):
+        sf = cubed_sphere(m, 8, axes=(1.0, 1.5, 2.0))
+        a, ga, c = e4(sf.nodes, sf.normals)
+        f, v = manufactured(sf, a, ga, c)
+        cases.append((f"ellipsoid_{sf.N}_sec74", sf, a, ga, c, f, v))
+    for name, sf, a, ga, c, f, uex in cases:
+        s = pm.Surface.from_fixture(ctx, sf)
+        t0 = time.perf_counter()
+        s.set_coeff_c(a, ga, c)
+        t_near = time.perf_counter() - t0
+        s.solve_c(f, tol=1e-12)
+        t0 = time.perf_counter()
+        reps = 2
+        for _ in range(reps):
+            u, info = s.solve_c(f, tol=1e-12)
+        t_solve = (time.perf_counter() - t0) / reps
+        w = sf.weights
+        err = float(np.sqrt(np.dot(w, np.abs(u - uex) ** 2) / np.dot(w, np.abs(uex) ** 2)))
+        # the float64 smooth sum alone (profile phases around its launches)
+        sig = np.random.default_rng(1).standard_normal(sf.N) + 0j
+        s.profile(True)
+        s.profile_read(0, reset=True)
+        for _ in range(3):
+            s.apply_c(sig, "R")
+        s.profile(False)
+        ms, nl = s.profile_read(pm._lib.PM_PHASE_DIRECT64)
+        near_ms, nn = s.profile_read(pm._lib.PM_PHASE_NEAR)
+        s.profile_read(0, reset=True)
+        pairs = sf.N * (sf.N - 1)
+        out["problems"][name] = {
+            "N": sf.N, "near_build_c_s": round(t_near, 3), "solve_ms": round(t_solve * 1e3, 2),
+            "iterations": info.iterations, "residual": info.residual,
+            "rel_l2_error_vs_exact": err,
+            "k_direct_c64_ms": round(ms / max(1, nl), 4),
+            "k_direct_c64_gpairs_per_s": round(pairs / (ms / max(1, nl)) / 1e6, 3),
+            "near_c_ms": round(near_ms / max(1, nn), 4)}
+        s.close()
+    ctx.close()
+    return out
+
+
 def run_fmm(args, dev):
     """98,304-node torus: float32 apply with the Chebyshev FMM vs the direct sum."""
     import numpy as np
@@ -1010,9 +1110,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for profiler runs, whose timings "
                          "would mislead the autotuner)")
-    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper",
+    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper,helmholtz",
                     help="comma-separated extra measurements to run (ellipsoid, batched, fmm, "
-                         "served, paper)")
+                         "served, paper, helmholtz)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -1022,12 +1122,17 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
-    ap.add_argument("--micro", choices=["tc_gemm"], default=None,
+    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz"], default=None,
                     help="time one kernel alone instead of the solve step (profiling aid)")
+    ap.add_argument("--micro-c", type=float, default=-4.0,
+                    help="c of --micro helmholtz (1,536-node unit sphere, a = 1)")
     args = ap.parse_args()
 
     if args.micro == "tc_gemm":
         run_micro_tc_gemm(args)
+        return
+    if args.micro == "helmholtz":
+        run_micro_helmholtz(args)
         return
     if args.oracle_leg:
         P = host_cores()
@@ -1069,7 +1174,8 @@ def main():
         for name, key, fn in (("ellipsoid", "ellipsoid_9600", run_ellipsoid),
                               ("batched", "batched_star_24576", run_batched),
                               ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served),
-                              ("paper", "paper_problems", run_paper)):
+                              ("paper", "paper_problems", run_paper),
+                              ("helmholtz", "helmholtz_c_nonzero", run_helmholtz)):
             if name not in want:
                 continue
             try:

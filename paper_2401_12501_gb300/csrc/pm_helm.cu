@@ -275,7 +275,10 @@ pm_status helm_apply(pm_surface* s, int which_K, const double2* sigma, double2* 
     PmHelmWork* W = nullptr;
     PM_TRY(helm_work(s, 0, &W));
     const int N = s->N;
-    k_prep_c<<<pm_ceil_div(N, kRT), kRT, 0, st>>>(sigma, s->wa, W->sv, N);
+    {
+        PhaseTimer t(s, PM_PHASE_PREP, st);
+        k_prep_c<<<pm_ceil_div(N, kRT), kRT, 0, st>>>(sigma, s->wa, W->sv, N);
+    }
     // source splits: about four blocks per SM, at least 64 sources a split
     const int tblocks = pm_ceil_div(N, kHT);
     int nsplit = pm_ceil_div(4 * s->ctx->num_sms, tblocks);
@@ -283,12 +286,17 @@ pm_status helm_apply(pm_surface* s, int which_K, const double2* sigma, double2* 
     const int chunk = pm_ceil_div(N, nsplit);
     dim3 grid(tblocks, nsplit);
     double2* part = reinterpret_cast<double2*>(s->partial);
-    if (which_K)
-        k_direct_c64<1><<<grid, kHT, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->cc, s->qn, W->sv,
-                                              N, chunk, part);
-    else
-        k_direct_c64<0><<<grid, kHT, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->cc, s->qn, W->sv,
-                                              N, chunk, part);
+    {
+        // the float64 phases of the c = 0 sums time the c != 0 sums too
+        PhaseTimer t(s, which_K ? PM_PHASE_DIRECT64_K : PM_PHASE_DIRECT64, st);
+        if (which_K)
+            k_direct_c64<1><<<grid, kHT, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->cc, s->qn,
+                                                  W->sv, N, chunk, part);
+        else
+            k_direct_c64<0><<<grid, kHT, 0, st>>>(s->x, s->n, s->H, s->a, s->g, s->cc, s->qn,
+                                                  W->sv, N, chunk, part);
+    }
+    PhaseTimer t(s, PM_PHASE_NEAR, st);
     k_near_apply_c64<<<pm_ceil_div((long long)N * 32, kRT), kRT, 0, st>>>(
         N, s->pp, s->row_ptr, s->blk_patch, which_K ? s->cKc : s->cRc, sigma, part, nsplit, out);
     PM_CUDA_TRY(cudaGetLastError());
