@@ -442,6 +442,40 @@ pm_status pm_smooth_c_f32(int N, const float* x, const float* n, const float* H,
                           double* out, void* stream);
 
 /*
+ * Triangle patches (Sec. 6.1): a closed surface of npatch curved triangles over the
+ * reference simplex T0 = {u, v >= 0, u + v <= 1}, each sampled at the same order-p
+ * rule of nt = p (p + 1) / 2 nodes (the paper's Vioreanu-Rokhlin nodes, or any
+ * unisolvent set inside T0 with positive weights), 2 <= p <= 8.
+ *   ref [nt][3]: the rule's (u, v, w) on T0 (host, copied);
+ *   nodes, normals [N][3], tangents [N][6] = (y_u, y_v), curvature [N] and weights [N]
+ *   as in pm_surface_create, N = npatch * nt, node k of patch P at row P * nt + k;
+ *   the weights must equal w_k |y_u x y_v| (relative 1e-8).
+ * The patch geometry, surface element and density are interpolated from the nodes
+ * in the polynomials of total degree <= p - 1 (Koornwinder basis, Sec. 6.1.2); the
+ * near-field rules are the polar self rule about the target's node (theta split at
+ * T0's vertex directions, Sec. 6.1.1) and midpoint subdivision of T0 into four
+ * triangles with a 16 x 16 collapsed Gauss rule (Sec. 6.1.2).  The result is a
+ * pm_surface like any other: pm_surface_set_coeff, the applies, pm_solve,
+ * pm_solve_multi, pm_surface_clone and the server accept it (grad_a = NULL
+ * differentiates a's interpolant); pm_surface_set_coeff_c refuses it.
+ * PM_ERR_INVALID_ARG for NULL arrays, p or npatch out of range, nodes outside T0,
+ * a non-unisolvent node set, weights or normals inconsistent with the tangents.
+ */
+pm_status pm_surface_create_tri(pm_ctx* ctx, int npatch, int p, const double* ref,
+                                const double* nodes, const double* normals,
+                                const double* tangents, const double* curvature,
+                                const double* weights, const pm_opts* opts, pm_surface** out);
+
+/*
+ * Host self-test of the triangle basis (no GPU): for the rule ref [nt][3] of order p,
+ * l [npts][nt] = the Lagrange basis of the nodes at the points (u[q], v[q]), and
+ * Du, Dv [nt][nt] = d l_k / du, d l_k / dv at node j (row j).  PM_ERR_INVALID_ARG as
+ * pm_surface_create_tri for the rule, or for NULL outputs.
+ */
+pm_status pm_selftest_tri_basis(int p, const double* ref, int npts, const double* u,
+                                const double* v, double* l, double* Du, double* Dv);
+
+/*
  * Helmholtz and modified-Helmholtz surface problems, div_G(a grad_G u) + c u = f
  * with c real (Sec. 4.2; Thm. second_kind with the parametrix of eq. diff_param
  * and the remainder of eq. explicit_remainder).  With q = c/a the kernels use

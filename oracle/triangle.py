@@ -77,6 +77,37 @@ def koornwinder(n: int, u, v):
     return _raw_basis(n, u, v) / _norms(n)[:, None]
 
 
+def koornwinder_grad(n: int, u, v):
+    """(d/du, d/dv) of koornwinder(n, u, v) for points with v < 1, same layout.
+
+    With xi = (2u + v - 1)/(1 - v), A = P_m(xi) (1 - v)^m and B = P_k^{(2m+1,0)}(2v - 1):
+      dA/du = 2 P_m'(xi) (1 - v)^(m-1),
+      dA/dv = [P_m'(xi) (1 + xi) - m P_m(xi)] (1 - v)^(m-1)    (d xi/dv = (1 + xi)/(1 - v)),
+      dB/dv = (k + 2m + 2) P_(k-1)^{(2m+2,1)}(2v - 1)           (derivative of a Jacobi polynomial).
+    """
+    from numpy.polynomial.legendre import legder
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    one_v = 1.0 - v
+    xi = (2.0 * u + v - 1.0) / one_v
+    du, dv = [], []
+    for deg in range(n + 1):
+        for k in range(deg + 1):
+            m = deg - k
+            c = np.zeros(m + 1)
+            c[m] = 1.0
+            Pm, dPm = legval(xi, c), legval(xi, legder(c)) if m > 0 else 0.0 * xi
+            t = 2.0 * v - 1.0
+            B = eval_jacobi(k, 2 * m + 1, 0.0, t)
+            dB = (k + 2 * m + 2) * eval_jacobi(k - 1, 2 * m + 2, 1.0, t) if k > 0 else 0.0 * t
+            pw = one_v ** (m - 1) if m > 0 else 0.0 * one_v
+            A = Pm * one_v ** m
+            du.append(2.0 * dPm * pw * B)
+            dv.append((dPm * (1.0 + xi) - m * Pm) * pw * B + A * dB)
+    nrm = _norms(n)[:, None]
+    return np.array(du) / nrm, np.array(dv) / nrm
+
+
 # Affine map T0 -> equilateral triangle with vertices on the unit circle at
 # angles 0, 2pi/3, 4pi/3 (u = v = 0 -> vertex 0, (1, 0) -> vertex 1, (0, 1) -> vertex 2).
 _E = np.array([[np.cos(a), np.sin(a)] for a in (0.0, 2 * np.pi / 3, 4 * np.pi / 3)])

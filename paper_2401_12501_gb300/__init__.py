@@ -94,8 +94,34 @@ class Surface:
 
     @classmethod
     def from_fixture(cls, ctx, surf, opts=None):
+        if hasattr(surf, "ref_u"):
+            return cls.create_tri(ctx, surf.npatch, surf.p, surf.ref_u, surf.ref_v, surf.ref_w,
+                                  surf.nodes, surf.normals, surf.tangents, surf.curvature,
+                                  surf.weights, opts)
         return cls(ctx, surf.npatch, surf.p, surf.nodes, surf.normals, surf.tangents,
                    surf.curvature, surf.weights, opts)
+
+    @classmethod
+    def create_tri(cls, ctx, npatch, p, ref_u, ref_v, ref_w, nodes, normals, tangents,
+                   curvature, weights, opts=None):
+        """Triangle patches (pm_surface_create_tri): the order-p rule (ref_u, ref_v, ref_w)
+        on T0 and the node data, N = npatch * p (p + 1) / 2."""
+        nt = p * (p + 1) // 2
+        N = npatch * nt
+        ref = np.ascontiguousarray(np.stack([ref_u, ref_v, ref_w], 1), dtype=np.float64)
+        if ref.shape != (nt, 3):
+            raise ValueError(f"the rule has {ref.shape[0]} nodes, order {p} needs {nt}")
+        arrs = [_f64(nodes, 3 * N), _f64(normals, 3 * N), _f64(tangents, 6 * N),
+                _f64(curvature, N), _f64(weights, N)]
+        h = C.c_void_p()
+        o = C.byref(opts) if opts is not None else None
+        check(_lib.lib().pm_surface_create_tri(ctx.handle, npatch, p, ptr(ref),
+                                               *[ptr(a) for a in arrs], o, C.byref(h)),
+              "pm_surface_create_tri")
+        s = object.__new__(cls)
+        s.ctx, s.npatch, s.p, s.N = ctx, npatch, p, N
+        s.handle = h
+        return s
 
     def clone(self) -> "Surface":
         """A surface on the same geometry sharing the near-field quadrature
@@ -248,9 +274,9 @@ class Surface:
         return self._apply(_lib.lib().pm_apply_part, (int(part),), sigma, prec, stream, out)
 
     def get_near(self, corrections=True):
-        """(row_ptr [N+1], blk_patch [nblk], corr_R, corr_K [nblk, p*p]) as numpy arrays."""
+        """(row_ptr [N+1], blk_patch [nblk], corr_R, corr_K [nblk, nodes per patch])."""
         N, nb = self.info()
-        pp = self.p * self.p
+        pp = N // self.npatch
         rp = np.empty(N + 1, dtype=np.int32)
         bp = np.empty(nb, dtype=np.int32)
         cr = np.empty((nb, pp)) if corrections else None

@@ -361,22 +361,31 @@ static bool all_finite(const double* v, size_t n) {
     return true;
 }
 
-extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const double* nodes,
-                                       const double* normals, const double* tangents,
-                                       const double* curvature, const double* weights,
-                                       const pm_opts* opts, pm_surface** out) {
-    if (!out) { pm_set_error("pm_surface_create: out is NULL"); return PM_ERR_INVALID_ARG; }
+// Quadrilateral patches (tri_ref == NULL: tensor Gauss-Legendre nodes of order p) or
+// triangle patches (tri_ref: the rule's nt = p (p + 1) / 2 reference nodes and weights).
+static pm_status create_impl(pm_ctx* ctx, int npatch, int p, const double* tri_ref,
+                             const double* nodes, const double* normals, const double* tangents,
+                             const double* curvature, const double* weights, const pm_opts* opts,
+                             pm_surface** out) {
+    const char* who = tri_ref ? "pm_surface_create_tri" : "pm_surface_create";
+    if (!out) { pm_set_error("%s: out is NULL", who); return PM_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!ctx || !nodes || !normals || !tangents || !curvature || !weights) {
-        pm_set_error("pm_surface_create: NULL argument");
+        pm_set_error("%s: NULL argument", who);
         return PM_ERR_INVALID_ARG;
     }
-    if (p < 2 || p > PM_MAX_P_API || npatch < 1 || (long long)npatch * p * p > (1LL << 26)) {
-        pm_set_error("pm_surface_create: need 2 <= p <= %d, npatch >= 1, N <= 2^26 (p=%d, npatch=%d)",
-                     PM_MAX_P_API, p, npatch);
+    const int pmax = tri_ref ? PM_TRI_MAX_P : PM_MAX_P_API;
+    const int pp = tri_ref ? p * (p + 1) / 2 : p * p;
+    if (p < 2 || p > pmax || npatch < 1 || (long long)npatch * pp > (1LL << 26)) {
+        pm_set_error("%s: need 2 <= p <= %d, npatch >= 1, N <= 2^26 (p=%d, npatch=%d)", who,
+                     pmax, p, npatch);
         return PM_ERR_INVALID_ARG;
     }
-    const int pp = p * p;
+    std::shared_ptr<PmTriTables> tri;
+    if (tri_ref) {
+        tri = std::make_shared<PmTriTables>();
+        PM_TRY(pm_tri_tables(p, tri_ref, tri.get()));
+    }
     const int N = npatch * pp;
     if (!all_finite(nodes, 3 * (size_t)N) || !all_finite(normals, 3 * (size_t)N) ||
         !all_finite(tangents, 6 * (size_t)N) || !all_finite(curvature, N) ||
@@ -397,16 +406,16 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
         double c2 = tu[0] * tv[1] - tu[1] * tv[0];
         J[k] = std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
         int loc = k % pp;
-        double wk = T.wt[loc / p] * T.wt[loc % p] * J[k];
+        double wk = (tri ? tri->w[loc] : T.wt[loc / p] * T.wt[loc % p]) * J[k];
         if (!(J[k] > 0) || std::fabs(wk - weights[k]) > 1e-8 * std::fabs(wk)) {
-            pm_set_error("pm_surface_create: weight %d (%g) is not omega_i omega_j |y_u x y_v| (%g)",
-                         k, weights[k], wk);
+            pm_set_error("%s: weight %d (%g) is not the rule's weight times |y_u x y_v| (%g)",
+                         who, k, weights[k], wk);
             return PM_ERR_INVALID_ARG;
         }
         double nn = 0;
         for (int c = 0; c < 3; ++c) nn += normals[3 * (size_t)k + c] * normals[3 * (size_t)k + c];
         if (std::fabs(nn - 1.0) > 1e-8) {
-            pm_set_error("pm_surface_create: normal %d is not a unit vector", k);
+            pm_set_error("%s: normal %d is not a unit vector", who, k);
             return PM_ERR_INVALID_ARG;
         }
         for (int c = 0; c < 3; ++c) {
@@ -421,6 +430,7 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     s->npatch = npatch;
     s->p = p;
     s->pp = pp;
+    s->tri = tri;
     s->ppad = (pp + 3) & ~3;
     s->N = N;
     s->Npad = pm_ceil_div(N, 256) * 256;
@@ -456,9 +466,14 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     // Largest theta panel: the self-rule integrand carries the degree p - 1 Lagrange
     // basis along each ray; pi/16 panels integrate it to ~1e-13 up to p = 10, p = 11
     // needs pi/24 (pi/16 leaves ~5e-7 in the self weights).
+    // On triangles the basis varies along a ray over a shorter length with a sharper
+    // turn at the vertices: pi/24 as for the highest quad orders.
     const double theta_w = s->opts.theta_max_width > 0.0 ? s->opts.theta_max_width
-                                                         : (p >= 11 ? M_PI / 24 : M_PI / 16);
-    pm_theta_plan(T, s->opts.theta_tol, theta_w, off, ang, wts, len);
+                                                         : (p >= 11 || tri ? M_PI / 24 : M_PI / 16);
+    if (tri)
+        pm_tri_theta_plan(*tri, T, s->opts.theta_tol, theta_w, off, ang, wts, len);
+    else
+        pm_theta_plan(T, s->opts.theta_tol, theta_w, off, ang, wts, len);
     s->nth_total = (int)ang.size();
     PM_STEP(pm_dmalloc(&s->th_off, off.size()));
     PM_STEP(pm_dmalloc(&s->th_ang, ang.size()));
@@ -469,13 +484,35 @@ extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const dou
     PM_CSTEP(cudaMemcpy(s->th_w, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice));
     PM_CSTEP(cudaMemcpy(s->th_L, len.data(), sizeof(double) * len.size(), cudaMemcpyHostToDevice));
 
-    PM_STEP(pm_near_build(s, T));
+    PM_STEP(tri ? pm_near_build_tri(s, T) : pm_near_build(s, T));
     PM_STEP(alloc_scratch(s));
 #undef PM_STEP
 #undef PM_CSTEP
     share_buffers(s);
     *out = s;
     return PM_OK;
+}
+
+extern "C" pm_status pm_surface_create(pm_ctx* ctx, int npatch, int p, const double* nodes,
+                                       const double* normals, const double* tangents,
+                                       const double* curvature, const double* weights,
+                                       const pm_opts* opts, pm_surface** out) {
+    return create_impl(ctx, npatch, p, nullptr, nodes, normals, tangents, curvature, weights,
+                       opts, out);
+}
+
+extern "C" pm_status pm_surface_create_tri(pm_ctx* ctx, int npatch, int p, const double* ref,
+                                           const double* nodes, const double* normals,
+                                           const double* tangents, const double* curvature,
+                                           const double* weights, const pm_opts* opts,
+                                           pm_surface** out) {
+    if (!ref) {
+        if (out) *out = nullptr;
+        pm_set_error("pm_surface_create_tri: NULL reference nodes");
+        return PM_ERR_INVALID_ARG;
+    }
+    return create_impl(ctx, npatch, p, ref, nodes, normals, tangents, curvature, weights, opts,
+                       out);
 }
 
 extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
@@ -499,6 +536,7 @@ extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
     s->h_far = src->h_far;
     s->eps2 = src->eps2;
     s->k32_centred = src->k32_centred;
+    s->tri = src->tri;
     s->h_x = src->h_x;
     s->h_w = src->h_w;
     s->h_tg = src->h_tg;
@@ -574,10 +612,14 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
     if (grad_a) {
         PM_CUDA_TRY(cudaMemcpy(s->g, grad_a, 3 * sizeof(double) * N, cudaMemcpyHostToDevice));
     } else {
-        QuadTables T;
-        pm_build_tables(s->p, &T);
         std::vector<double> gh(3 * (size_t)N);
-        pm_patch_gradient(s, T, a, gh.data());
+        if (s->tri) {
+            pm_tri_gradient(s, a, gh.data());
+        } else {
+            QuadTables T;
+            pm_build_tables(s->p, &T);
+            pm_patch_gradient(s, T, a, gh.data());
+        }
         PM_CUDA_TRY(cudaMemcpy(s->g, gh.data(), 3 * sizeof(double) * N, cudaMemcpyHostToDevice));
     }
     PM_TRY(pm_pack_targets(s, st));

@@ -351,6 +351,10 @@ extern "C" pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, cons
         pm_set_error("pm_surface_set_coeff_c: NULL argument");
         return PM_ERR_INVALID_ARG;
     }
+    if (s->tri) {
+        pm_set_error("pm_surface_set_coeff_c: c != 0 is built for quadrilateral patches only");
+        return PM_ERR_INVALID_ARG;
+    }
     const int N = s->N;
     bool any = false;
     for (int k = 0; k < N; ++k) {

@@ -50,6 +50,8 @@ struct alignas(32) pm_d4 {
 constexpr int PM_MAX_P = 16;
 constexpr int PM_MAX_P_API = 11;     // quadrature kernels give one basis entry per thread (p*p <= 128)
 constexpr int PM_GL16 = 16;          // points per quadrature panel
+constexpr int PM_TRI_MAX_P = 8;      // triangle patches: order p <= 8, p (p + 1) / 2 <= 36 nodes
+constexpr int PM_TRI_MAX_NT = 36;
 constexpr int PM_RADIAL_PANELS = 4;  // self rule: [0,L/8],[L/8,L/4],[L/4,L/2],[L/2,L]
 
 // Host-computed tables for the quadrature kernels (constant memory).
@@ -99,6 +101,15 @@ struct PmFmmTree;
 struct PmBatchWork;
 struct PmBatchSolveWork;
 struct PmHelmWork;
+
+// Triangle patches (pm_tri.cu): the reference nodes (u, v) and weights w of the
+// surface's rule on T0, U = V^-1 with V[j][n] = K_n(u_j, v_j) (Koornwinder basis,
+// the library's ordering) so that l_k = sum_n K_n U[n * nt + k], and the
+// derivative matrices Du[j * nt + k] = d l_k / du at node j (Dv likewise).
+struct PmTriTables {
+    int p = 0, nt = 0;
+    std::vector<double> u, v, w, U, Du, Dv;
+};
 
 struct pm_surface {
     pm_ctx* ctx = nullptr;
@@ -190,6 +201,9 @@ struct pm_surface {
     // owner of the buffers listed in PM_SHARED_FIELDS (pm_api.cu) once the surface is built
     std::shared_ptr<PmSharedBuffers> shared;
 
+    // triangle patches (pm_surface_create_tri); null for quadrilateral patches
+    std::shared_ptr<const PmTriTables> tri;
+
     // launch-shape knobs beyond pm_opts (pm_surface_set_knobs / pm_surface_autotune)
     int batch_rb = 0;             // right-hand sides per block of the batched float32 sums (0 = 16)
     int batch_bps = 0;            // blocks aimed at per SM by the batched float32 sums (0 = 8)
@@ -259,6 +273,18 @@ pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const voi
 pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st);
 pm_status pm_tcgemm_check(const PmTcGemm* g);
 void pm_tcgemm_free(PmTcGemm* g);
+
+// near-field CSR structure, patch unions and weight-set allocation after the
+// patch geometry (centroid, radius, npatch_n) is in place (pm_nearfield.cu)
+pm_status pm_near_structure(pm_surface* s);
+
+// triangle patches (pm_tri.cu)
+pm_status pm_tri_tables(int p, const double* ref_uvw, PmTriTables* T);
+void pm_tri_theta_plan(const PmTriTables& T, const QuadTables& Q, double tol, double max_width,
+                       std::vector<int>& off, std::vector<double>& ang, std::vector<double>& wts,
+                       std::vector<double>& len);
+pm_status pm_near_build_tri(pm_surface* s, const QuadTables& Q);
+void pm_tri_gradient(const pm_surface* s, const double* a, double* grad);
 
 // c != 0 (pm_nearfield.cu: near field; pm_helm.cu: sums, solve)
 pm_status pm_near_build_c(pm_surface* s);

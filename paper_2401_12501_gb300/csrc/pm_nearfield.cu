@@ -947,11 +947,43 @@ pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
     PM_TRY(pm_dmalloc(&s->centroid, 3 * (size_t)npatch));
     PM_TRY(pm_dmalloc(&s->radius, npatch));
     PM_TRY(pm_dmalloc(&s->npatch_n, 3 * (size_t)N));
+    k_patch_geom<<<pm_ceil_div(npatch, 128), 128>>>(s->x, npatch, p, s->centroid, s->radius);
+    k_node_normals<<<pm_ceil_div(N, 128), 128>>>(s->x, N, p, s->npatch_n);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_TRY(pm_near_structure(s));
+    const size_t smem = sizeof(double) * (4 * (size_t)pp + 2 * (size_t)kQThreads * p + 5 * kQThreads);
+    if (smem > 48 * 1024)
+        PM_CUDA_TRY(cudaFuncSetAttribute(k_self_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    k_self_quad<<<N, kQThreads, smem>>>(N, p, s->x, s->J, s->npatch_n, s->H, s->th_off,
+                                        s->th_ang, s->th_w, s->th_L, s->row_ptr, s->nblk,
+                                        s->W_lb, s->W_g, s->W_k);
+    PM_CUDA_TRY(cudaGetLastError());
+    k_near_quad<<<s->nblk, kQThreads>>>(p, s->nblk, s->x, s->J, s->n, s->H, s->blk_row,
+                                        s->blk_patch, s->row_ptr, s->opts.near_eta,
+                                        std::min(s->opts.near_max_depth, 12),
+                                        s->opts.near_max_leaves, s->W_lb, s->W_g, s->W_k,
+                                        s->dev_err);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    int herr = 0;
+    PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != PM_DEV_OK) {
+        pm_set_error("near-field quadrature: device check %d failed (leaf budget exceeded)", herr);
+        return PM_ERR_INTERNAL;
+    }
+    return PM_OK;
+}
+
+// The near-field structure from the patch centroids and radii: per target its
+// own patch first, then every patch within near_factor radii (CSR over blocks),
+// each patch's union of its rows' near patches, the compactness test of the
+// float32 parametrix sum's centred form, and the coefficient-free weight sets.
+pm_status pm_near_structure(pm_surface* s) {
+    const int N = s->N, npatch = s->npatch, pp = s->pp;
     PM_TRY(pm_dmalloc(&s->row_ptr, (size_t)N + 1));
     PM_TRY(pm_dmalloc(&s->dev_err, 1));
     PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
-    k_patch_geom<<<pm_ceil_div(npatch, 128), 128>>>(s->x, npatch, p, s->centroid, s->radius);
-    k_node_normals<<<pm_ceil_div(N, 128), 128>>>(s->x, N, p, s->npatch_n);
     int* count = nullptr;
     PM_TRY(pm_dmalloc(&count, N));
     k_near_count<<<pm_ceil_div(N, 128), 128>>>(s->x, s->centroid, s->radius, N, npatch, pp,
@@ -1038,27 +1070,6 @@ pm_status pm_near_build(pm_surface* s, const QuadTables& T) {
     PM_TRY(pm_dmalloc(&s->W_lb, nv));
     PM_TRY(pm_dmalloc(&s->W_g, 3 * nv));
     PM_TRY(pm_dmalloc(&s->W_k, nv));
-    const size_t smem = sizeof(double) * (4 * (size_t)pp + 2 * (size_t)kQThreads * p + 5 * kQThreads);
-    if (smem > 48 * 1024)
-        PM_CUDA_TRY(cudaFuncSetAttribute(k_self_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-    k_self_quad<<<N, kQThreads, smem>>>(N, p, s->x, s->J, s->npatch_n, s->H, s->th_off,
-                                        s->th_ang, s->th_w, s->th_L, s->row_ptr, s->nblk,
-                                        s->W_lb, s->W_g, s->W_k);
-    PM_CUDA_TRY(cudaGetLastError());
-    k_near_quad<<<s->nblk, kQThreads>>>(p, s->nblk, s->x, s->J, s->n, s->H, s->blk_row,
-                                        s->blk_patch, s->row_ptr, s->opts.near_eta,
-                                        std::min(s->opts.near_max_depth, 12),
-                                        s->opts.near_max_leaves, s->W_lb, s->W_g, s->W_k,
-                                        s->dev_err);
-    PM_CUDA_TRY(cudaGetLastError());
-    PM_CUDA_TRY(cudaDeviceSynchronize());
-    int herr = 0;
-    PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (herr != PM_DEV_OK) {
-        pm_set_error("near-field quadrature: device check %d failed (leaf budget exceeded)", herr);
-        return PM_ERR_INTERNAL;
-    }
     return PM_OK;
 }
 

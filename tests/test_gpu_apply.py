@@ -78,15 +78,20 @@ def test_near_structure_and_corrections(ctx, name):
 
 @pytest.mark.parametrize("name", ["sphere_384", "ellipsoid_small", "wavy_torus_small",
                                   "ellipsoid_paper_small"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-6)])
-def test_full_apply_parity(ctx, name, prec, tol):
+@pytest.mark.parametrize("prec,tol,tol_max", [("fp64", 1e-11, 1e-10), ("fp32", 2e-6, 1e-5)])
+def test_full_apply_parity(ctx, name, prec, tol, tol_max):
+    """Every row against the oracle: relative L2, and element by element on the scale
+    of the largest entry (an error local to a few nodes near patch edges would hide in
+    the norm alone)."""
     from oracle.operator import apply_K, apply_R
     wl, d, nf = oracle(name)
     _, s = gpu_surface(ctx, name)
     rng = np.random.default_rng(1)
     sigma = rng.standard_normal(d.N) + 1.0
-    assert rel(s.apply_R(sigma, prec), apply_R(d, nf, sigma)) < tol
-    assert rel(s.apply_K(sigma, prec), apply_K(d, nf, sigma)) < tol
+    for got, want in ((s.apply_R(sigma, prec), apply_R(d, nf, sigma)),
+                      (s.apply_K(sigma, prec), apply_K(d, nf, sigma))):
+        assert rel(got, want) < tol
+        assert np.abs(got - want).max() <= tol_max * np.abs(want).max()
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
