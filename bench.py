@@ -751,6 +751,51 @@ def run_paper(args, dev):
     return out
 
 
+def run_triangles(args, dev):
+    """Triangle patches (Sec. 6.1, the paper's own discretisation): the unit sphere
+    from 320 and 1,280 icosahedral triangles at the order-8 Vioreanu-Rokhlin nodes
+    (11,520 and 46,080 nodes), f = Y_3^2: near-field build time, solve time to 1e-10
+    (float32 direct applies; FMM applies on the larger surface as well) and the error
+    against u = -f/12; the smooth-sum kernels are those of the quadrilateral surfaces."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import real_sph_harm
+    from workloads.trisurfaces import tri_ellipsoid
+    ctx = pm.Context(dev.index or 0)
+    out = {"tol": args.tol, "rule": "Vioreanu-Rokhlin order 8 (36 nodes a triangle)",
+           "problems": {}}
+    for level, precs in ((2, ("fp32",)), (3, ("fp32", "fmm"))):
+        sf = tri_ellipsoid(level, 8)
+        t0 = time.perf_counter()
+        s = pm.Surface.from_fixture(ctx, sf)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        s.set_coeff(np.ones(sf.N))
+        Y = real_sph_harm(3, 2, sf.nodes)
+        fd = torch.from_numpy(Y.copy()).to(dev)
+        w = sf.weights
+        row = {"N": sf.N, "triangles": sf.npatch, "near_build_s": round(t_build, 3),
+               "near_blocks": s.info()[1]}
+        for prec in precs:
+            s.solve(fd, tol=args.tol, prec=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                u, info = s.solve(fd, tol=args.tol, prec=prec)
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) / 3
+            u = u.cpu().numpy()
+            row[prec] = {"solve_ms": round(t * 1e3, 3), "iterations": info[0].iterations,
+                         "residual": info[0].residual,
+                         "rel_l2_error_vs_exact": float(np.sqrt(np.dot(w, (u + Y / 12) ** 2) /
+                                                                np.dot(w, (Y / 12) ** 2)))}
+        out["problems"][f"tri_sphere_{sf.N}"] = row
+        s.close()
+    ctx.close()
+    return out
+
+
 def run_micro_helmholtz(args):
     """Three float64 c != 0 remainder applies on the 1,536-node unit sphere (a = 1,
     c = --micro-c): the launches an ncu capture of k_direct_c64 looks at."""
@@ -1110,9 +1155,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for profiler runs, whose timings "
                          "would mislead the autotuner)")
-    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper,helmholtz",
+    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper,helmholtz,triangles",
                     help="comma-separated extra measurements to run (ellipsoid, batched, fmm, "
-                         "served, paper, helmholtz)")
+                         "served, paper, helmholtz, triangles)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -1175,7 +1220,8 @@ def main():
                               ("batched", "batched_star_24576", run_batched),
                               ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served),
                               ("paper", "paper_problems", run_paper),
-                              ("helmholtz", "helmholtz_c_nonzero", run_helmholtz)):
+                              ("helmholtz", "helmholtz_c_nonzero", run_helmholtz),
+                              ("triangles", "triangle_patches", run_triangles)):
             if name not in want:
                 continue
             try:

@@ -19,19 +19,11 @@
 //           g'' = -kappa^2 (K0(kappa r) + K1(kappa r) / (kappa r)) / (2 pi).
 //
 // J0, Y0, J1, Y1 are the math library's (j0, y0, j1, y1).  K0 and K1 are
-// evaluated here:
-//   x < 1:  the ascending series (Abramowitz & Stegun 9.6.13 and 9.6.11 with n = 1)
-//             K0(x) = -(ln(x/2) + gamma) I0(x) + sum_{j>=1} H_j t^j / (j!)^2,
-//             K1(x) = 1/x + ln(x/2) I1(x)
-//                     - (x/4) sum_{j>=0} (psi(j+1) + psi(j+2)) t^j / (j! (j+1)!),
-//           t = x^2/4, H_j the harmonic numbers, psi(j+1) = -gamma + H_j;
-//   x >= 1: the trapezoid rule on the integral representation
-//             e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2)) cosh(nu t) dt
-//           (A&S 9.6.24), whose integrand is analytic in the strip |Im t| < pi/2,
-//           so the rule converges geometrically: with step h the error is
-//           O(exp(x - pi^2/h)); h = min(1/4, pi^2/(40 + x)) keeps it below 1e-16
-//           relative, and the sum stops where the integrand is below e^-40.
-//           At most 26 terms for x up to 700.
+// evaluated here (bessel_k01): the ascending series (Abramowitz & Stegun 9.6.13 and
+// 9.6.11 with n = 1) for x <= 2, with t = x^2/4, H_j the harmonic numbers and
+// psi(j+1) = -gamma + H_j; above 2 the trapezoid rule on the integral representation
+// A&S 9.6.24, whose integrand is analytic in the strip |Im t| < pi/2, so the rule
+// converges geometrically.
 #pragma once
 
 #include <math.h>
@@ -41,44 +33,75 @@ namespace pm_green {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kEulerGamma = 0.57721566490153286061;
 
+// Coefficients of the float64 series (x <= 2, t = x^2/4 <= 1), computed by the
+// compiler from their definitions: c0[j] = 1/(j!)^2, d0[j] = psi(j+1) c0[j],
+// c1[j] = 1/(j! (j+1)!), d1[j] = (psi(j+1) + psi(j+2)) c1[j], psi(j+1) = -gamma + H_j.
+// Fourteen terms: the last is below 1/(13!)^2 = 2.6e-20 at t = 1.
+constexpr int kSeriesK01d = 14;
+struct SeriesK01d {
+    double c0[kSeriesK01d], d0[kSeriesK01d], c1[kSeriesK01d], d1[kSeriesK01d];
+};
+
+__host__ __device__ constexpr SeriesK01d series_k01_d()
+{
+    SeriesK01d c{};
+    double f0 = 1.0, f1 = 1.0, harm = 0.0;      // 1/(j!)^2, 1/(j! (j+1)!), H_j
+    for (int j = 0; j < kSeriesK01d; ++j) {
+        const double psi1 = -kEulerGamma + harm;
+        const double psi2 = psi1 + 1.0 / (j + 1);
+        c.c0[j] = f0;
+        c.d0[j] = psi1 * f0;
+        c.c1[j] = f1;
+        c.d1[j] = (psi1 + psi2) * f1;
+        harm += 1.0 / (j + 1);
+        f0 /= (j + 1.0) * (j + 1.0);
+        f1 /= (j + 1.0) * (j + 2.0);
+    }
+    return c;
+}
+
 // K0(x), K1(x) for x > 0.
+//   x <= 2: K0 = -ln(x/2) I0 + sum_j psi(j+1) t^j/(j!)^2,
+//           K1 = 1/x + ln(x/2) I1 - (x/4) sum_j (psi(j+1) + psi(j+2)) t^j/(j! (j+1)!),
+//           t = x^2/4 (A&S 9.6.13, 9.6.11), four Horner sums of fourteen terms;
+//   x > 2:  the trapezoid rule on e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2)) cosh(nu t) dt
+//           with step h = min(1/4, pi^2/(40 + x)) (error O(exp(x - pi^2/h)) below 1e-16
+//           relative), sinh and cosh of j h/2 by the addition formulas, stopping once a
+//           term is below 1e-17 of the sum (at most 64 terms; 26 suffice up to x = 700).
 __host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
 {
     if (x != x) {                       // NaN passes through (no term count from it)
         *k0v = *k1v = x;
         return;
     }
-    if (x < 1.0) {
+    if (x <= 2.0) {
+        constexpr SeriesK01d C = series_k01_d();
         const double t = 0.25 * x * x;
-        double a0 = 1.0;        // t^j / (j!)^2
-        double a1 = 1.0;        // t^j / (j! (j+1)!)
-        double harm = 0.0;      // H_j
-        double i0 = 0.0, i1s = 0.0, s0 = 0.0, s1 = 0.0;
-        for (int j = 0; j < 24; ++j) {
-            const double psi1 = -kEulerGamma + harm;               // psi(j+1)
-            const double psi2 = psi1 + 1.0 / (j + 1);              // psi(j+2)
-            i0 += a0;
-            i1s += a1;
-            s0 += psi1 * a0;
-            s1 += (psi1 + psi2) * a1;
-            harm += 1.0 / (j + 1);
-            a0 *= t / ((j + 1.0) * (j + 1.0));
-            a1 *= t / ((j + 1.0) * (j + 2.0));
+        double i0 = C.c0[kSeriesK01d - 1], s0 = C.d0[kSeriesK01d - 1];
+        double i1s = C.c1[kSeriesK01d - 1], s1 = C.d1[kSeriesK01d - 1];
+        for (int j = kSeriesK01d - 2; j >= 0; --j) {
+            i0 = fma(i0, t, C.c0[j]);
+            s0 = fma(s0, t, C.d0[j]);
+            i1s = fma(i1s, t, C.c1[j]);
+            s1 = fma(s1, t, C.d1[j]);
         }
         const double lg = log(0.5 * x);
-        *k0v = -lg * i0 + s0;
+        *k0v = fma(-lg, i0, s0);
         *k1v = 1.0 / x + lg * (0.5 * x * i1s) - 0.25 * x * s1;
         return;
     }
     const double h = fmin(0.25, kPi * kPi / (40.0 + x));
-    const double tmax = acosh(1.0 + 40.0 / x);
-    const int n = (int)fmin(64.0, ceil(tmax / h));          // <= 26 for x <= 700
-    double s0 = 0.5, s1 = 0.5;
-    for (int j = 1; j <= n; ++j) {
-        const double sh = sinh(0.5 * j * h);
-        const double e = exp(-2.0 * x * sh * sh);
+    const double sh1 = sinh(0.5 * h), ch1 = cosh(0.5 * h);
+    double sh = 0.0, ch = 1.0, s0 = 0.5, s1 = 0.5;
+    for (int j = 1; j <= 64; ++j) {
+        const double shn = fma(sh, ch1, ch * sh1);
+        ch = fma(ch, ch1, sh * sh1);
+        sh = shn;
+        const double s2 = sh * sh;
+        const double e = exp(-2.0 * x * s2);
         s0 += e;
-        s1 += e * (1.0 + 2.0 * sh * sh);                           // cosh t
+        s1 = fma(e, fma(2.0, s2, 1.0), s1);           // cosh t = 1 + 2 sinh^2(t/2)
+        if (e < 1e-17 * s0) break;
     }
     const double ex = exp(-x);
     *k0v = h * s0 * ex;

@@ -126,13 +126,13 @@ def test_green_function_c_nonzero(lib):
     """The library's double-precision g, g', g'' for c != 0 (pm_green.cuh, host code,
     no GPU) against the oracle's scipy evaluation: Helmholtz (q > 0, J/Y from the
     math library) and modified Helmholtz (q < 0, the library's own K0/K1: ascending
-    series below 1, trapezoid rule on the integral representation above), across
+    series up to 2, trapezoid rule on the integral representation above), across
     both K0/K1 branches and far into the decay; invalid arguments are rejected."""
     import numpy as np
     from oracle.kernels import green_scaled
     from paper_2401_12501_gb300._lib import ptr
     r = np.concatenate([np.geomspace(1e-6, 60.0, 301), [0.5, 0.999, 1.0, 1.001, 2.0]])
-    for q in (4.0, 0.37, -4.0, -0.05, -30.0):
+    for q in (4.0, 0.37, -4.0, -1.0, -0.05, -30.0):
         out = np.zeros((len(r), 6))
         assert lib.pm_selftest_green(ptr(r), len(r), q, ptr(out)) == 0
         k = np.sqrt(complex(q))
