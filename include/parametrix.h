@@ -442,6 +442,21 @@ pm_status pm_smooth_c_f32(int N, const float* x, const float* n, const float* H,
                           double* out, void* stream);
 
 /*
+ * Consistency check of a built surface (the library's substitute for a memory
+ * checker): on the device, every index the apply kernels follow is verified
+ * against the array it addresses (near-field row pointers and block patch/row
+ * indices, own patch first, the per-patch near-field unions, the self-rule theta
+ * plan), and the stored geometry, weight sets and corrections (float64 and
+ * float32, complex for c != 0) are scanned for NaN and Inf.  Failed checks are
+ * recorded in a device word (first failure kept); nothing traps.  Synchronises.
+ * PM_OK, PM_ERR_INTERNAL with the failed check and index in pm_last_error(),
+ * PM_ERR_INVALID_ARG for NULL, PM_ERR_CUDA if a launch fails.  A library built
+ * with -DPM_BOUNDS_CHECK runs it before every pm_apply_R/K/part and scans each
+ * result for non-finite values.
+ */
+pm_status pm_surface_check(pm_surface* s);
+
+/*
  * Triangle patches (Sec. 6.1): a closed surface of npatch curved triangles over the
  * reference simplex T0 = {u, v >= 0, u + v <= 1}, each sampled at the same order-p
  * rule of nt = p (p + 1) / 2 nodes (the paper's Vioreanu-Rokhlin nodes, or any

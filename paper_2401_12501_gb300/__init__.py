@@ -212,6 +212,10 @@ class Surface:
         check(_lib.lib().pm_surface_set_coeff(self.handle, ptr(a), ptr(g)),
               "pm_surface_set_coeff")
 
+    def check(self):
+        """pm_surface_check: the near-field indices and stored data are consistent and finite."""
+        check(_lib.lib().pm_surface_check(self.handle), "pm_surface_check")
+
     def set_coeff_c(self, a, grad_a, c):
         """a, grad_a as in set_coeff, and a real c [N] (div(a grad u) + c u = f)."""
         if not np.isrealobj(c):

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libparametrix.so")
-SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_direct.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_helm.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tcgemm.cu", "pm_tri.cu", "pm_tune.cu"]
+CHECKED_LIB = os.path.join(HERE, "libparametrix_checked.so")
+SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_check.cu", "pm_direct.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_helm.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tcgemm.cu", "pm_tri.cu", "pm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -35,7 +36,18 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
+def build(verbose: bool = False, force: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile and link the library; checked=True builds libparametrix_checked.so with
+    -DPM_BOUNDS_CHECK (pm_surface_check before and a finite scan after every apply)
+    in its own object folder."""
+    if checked:
+        return _build(BUILD + "_checked", CHECKED_LIB, verbose, force,
+                      ("-DPM_BOUNDS_CHECK", *extra_flags))
+    return _build(BUILD, LIB, verbose, force, tuple(extra_flags))
+
+
+def _build(build_dir, lib_path, verbose, force, extra_flags) -> str:
+    BUILD, LIB = build_dir, lib_path
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "parametrix.h"))

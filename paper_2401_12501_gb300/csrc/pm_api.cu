@@ -707,9 +707,9 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
                          prec == PM_PREC_FMM ? PM_PREC_FP32 : prec, st);
 }
 
-static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
-                              const double* sigma, double* out, int nrhs, pm_precision prec,
-                              int on_device, void* stream) {
+static pm_status apply_impl(pm_surface* s, int kernel_K, int smooth, int near,
+                            const double* sigma, double* out, int nrhs, pm_precision prec,
+                            int on_device, void* stream) {
     if (!s || !sigma || !out || nrhs < 1) {
         pm_set_error("apply: NULL argument or nrhs < 1");
         return PM_ERR_INVALID_ARG;
@@ -759,6 +759,30 @@ static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
                                     cudaMemcpyDeviceToHost, st));
     }
     PM_CUDA_TRY(cudaStreamSynchronize(st));
+    return PM_OK;
+}
+
+// With -DPM_BOUNDS_CHECK every apply is bracketed by pm_surface_check and a finite
+// scan of its result (PM_ERR_INTERNAL on a failure, with the check's message).
+static pm_status apply_common(pm_surface* s, int kernel_K, int smooth, int near,
+                              const double* sigma, double* out, int nrhs, pm_precision prec,
+                              int on_device, void* stream) {
+#ifdef PM_BOUNDS_CHECK
+    if (s && s->row_ptr) PM_TRY(pm_surface_check(s));
+#endif
+    PM_TRY(apply_impl(s, kernel_K, smooth, near, sigma, out, nrhs, prec, on_device, stream));
+#ifdef PM_BOUNDS_CHECK
+    const size_t n = (size_t)s->N * nrhs;
+    if (on_device) {
+        PM_TRY(pm_check_finite(out, n, (cudaStream_t)stream, "apply result"));
+    } else {
+        for (size_t k = 0; k < n; ++k)
+            if (!std::isfinite(out[k])) {
+                pm_set_error("apply result: non-finite value at %zu", k);
+                return PM_ERR_INTERNAL;
+            }
+    }
+#endif
     return PM_OK;
 }
 

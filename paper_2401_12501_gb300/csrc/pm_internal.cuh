@@ -278,6 +278,10 @@ void pm_tcgemm_free(PmTcGemm* g);
 // patch geometry (centroid, radius, npatch_n) is in place (pm_nearfield.cu)
 pm_status pm_near_structure(pm_surface* s);
 
+// consistency checks (pm_check.cu): a finite scan of a device array
+pm_status pm_check_finite(const double* v, size_t n, cudaStream_t st, const char* what);
+extern "C" pm_status pm_surface_check(pm_surface* s);
+
 // triangle patches (pm_tri.cu)
 pm_status pm_tri_tables(int p, const double* ref_uvw, PmTriTables* T);
 void pm_tri_theta_plan(const PmTriTables& T, const QuadTables& Q, double tol, double max_width,

@@ -32,6 +32,7 @@
 #include "pm_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -103,8 +104,11 @@ struct pm_server {
 
 namespace {
 
-// free device memory now (the worker thread's device is the context's)
+// free device memory now (the worker thread's device is the context's).  The
+// environment variable PM_FAKE_HBM_BYTES, when set, replaces the reading (a
+// host-side stand-in for a full device, to exercise admission without using memory).
 size_t free_bytes() {
+    if (const char* fake = std::getenv("PM_FAKE_HBM_BYTES")) return (size_t)std::strtoull(fake, nullptr, 10);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
     return fr;

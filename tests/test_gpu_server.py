@@ -133,6 +133,32 @@ def test_budget_for_one_request_serialises(ops):
     s2.close()
 
 
+def test_full_device_admits_one_batch_at_a_time(ops):
+    """Admission against a device reported full (PM_FAKE_HBM_BYTES = 0 replaces the
+    free-memory reading on the host): nothing is admitted next to a batch in flight,
+    the oldest item still goes when the device is idle, so every request completes,
+    with the result it has alone."""
+    import os
+    import paper_2401_12501_gb300 as pm
+    ctx, lst = ops
+    os.environ["PM_FAKE_HBM_BYTES"] = "0"
+    try:
+        sv = pm.Server(ctx, hbm_budget_bytes=2 << 30, max_batch=4, n_workers=3)
+        reqs = [(idx, f) for idx, (wl, _) in enumerate(lst) for f in rhs_set(wl, 3, 40 + idx)]
+        ts = [sv.submit(lst[idx][1], f, tol=1e-11) for idx, f in reqs]
+        outs = [sv.wait(t) for t in ts]
+        st = sv.stats()
+        sv.close()
+    finally:
+        del os.environ["PM_FAKE_HBM_BYTES"]
+    assert st["solved"] == len(reqs)
+    for (idx, f), (u, info, _) in zip(reqs, outs):
+        alone, _ = lst[idx][1].solve(f, tol=1e-11)
+        w = lst[idx][0].surface.weights
+        assert info.residual <= 1e-11
+        assert np.sqrt(np.dot(w, (u - alone) ** 2) / np.dot(w, alone ** 2)) < 1e-9
+
+
 def test_failed_solve_reports_status_and_message(ops):
     """A request whose solve fails (f with a non-zero mean) ends with the solve's status,
     and the waiting thread's pm_last_error holds the worker's message."""

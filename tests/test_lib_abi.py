@@ -216,3 +216,15 @@ def test_smooth_sum_c_nonzero_pair_arithmetic(lib, sign):
     rel = lambda u, v: np.linalg.norm(u - v) / np.linalg.norm(v)
     assert rel(gotR, refR) < 1e-6, rel(gotR, refR)
     assert rel(gotK, refK) < 1e-6, rel(gotK, refK)
+
+
+def test_bounds_checked_build_compiles(tmp_path):
+    """The -DPM_BOUNDS_CHECK variant of the apply path compiles for sm_103a (no GPU
+    needed): pm_api.cu, where every apply is bracketed by pm_surface_check and a
+    finite scan of its result."""
+    import subprocess
+    from paper_2401_12501_gb300 import build
+    src = os.path.join(build.CSRC, "pm_api.cu")
+    r = subprocess.run([build.nvcc(), *build.ARCH, *build.FLAGS, "-DPM_BOUNDS_CHECK", "-c", src,
+                        "-o", str(tmp_path / "pm_api_checked.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
