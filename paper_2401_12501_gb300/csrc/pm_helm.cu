@@ -235,9 +235,30 @@ void pm_helm_free(pm_surface* s) {
 
 namespace {
 
+pm_status helm_work_alloc(pm_surface* s, int m);
+
 // Work buffers: the apply's (strengths, staging) always, the Krylov basis when
-// m > 0 (reallocated when the restart length changes).
+// m > 0 (reallocated when the restart length changes).  A failed allocation frees
+// the work, so a partly allocated one is never reused.
 pm_status helm_work(pm_surface* s, int m, PmHelmWork** out) {
+    const pm_status st = helm_work_alloc(s, m);
+    if (st != PM_OK) {
+        if (s->helm) {
+            PmHelmWork& W = *s->helm;
+            pm_dfree(W.V); pm_dfree(W.w); pm_dfree(W.tmp); pm_dfree(W.x); pm_dfree(W.f);
+            pm_dfree(W.r); pm_dfree(W.u); pm_dfree(W.sv); pm_dfree(W.io); pm_dfree(W.part);
+            pm_dfree(W.h); pm_dfree(W.y);
+            if (W.pinned) cudaFreeHost(W.pinned);
+            delete s->helm;
+            s->helm = nullptr;
+        }
+        return st;
+    }
+    *out = s->helm;
+    return PM_OK;
+}
+
+pm_status helm_work_alloc(pm_surface* s, int m) {
     if (!s->helm) s->helm = new PmHelmWork();
     PmHelmWork& W = *s->helm;
     const int N = s->N;
@@ -265,7 +286,6 @@ pm_status helm_work(pm_surface* s, int m, PmHelmWork** out) {
         PM_TRY(pm_dmalloc(&W.y, m + 1));
         PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, sizeof(double2) * (2 * (size_t)(m + 2) + 1)));
     }
-    *out = &W;
     return PM_OK;
 }
 

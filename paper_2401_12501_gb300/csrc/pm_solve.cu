@@ -448,12 +448,26 @@ void pm_solve_free(pm_surface* s) {
 
 namespace {
 
+pm_status alloc_work(pm_surface* s, int m);
+
+// The Krylov workspace for the current restart length; a failed allocation frees
+// whatever was allocated, so no partly built workspace is ever reused.
 pm_status get_work(pm_surface* s, Work** out) {
     const int m = std::max(2, std::min(s->opts.gmres_restart, 400));
     if (s->solve_work && s->solve_work->m == m) {
         *out = s->solve_work;
         return PM_OK;
     }
+    const pm_status st = alloc_work(s, m);
+    if (st != PM_OK) {
+        pm_solve_free(s);
+        return st;
+    }
+    *out = s->solve_work;
+    return PM_OK;
+}
+
+pm_status alloc_work(pm_surface* s, int m) {
     pm_solve_free(s);
     s->solve_work = new PmSolveWork();
     Work& W = *s->solve_work;
@@ -489,7 +503,6 @@ pm_status get_work(pm_surface* s, Work** out) {
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned, 8 * sizeof(double)));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_par, 2 * sizeof(double)));
     PM_CUDA_TRY(cudaMallocHost((void**)&W.pinned_i, 4 * sizeof(int)));
-    *out = &W;
     return PM_OK;
 }
 
