@@ -208,42 +208,54 @@ __device__ inline void tri_integrands(double rx, double ry, double rz, double n0
     f[4] = wgt * (0.5 * log(r2) + logc) * (0.5 / M_PI);
 }
 
-// Self patch: one block per target.
+// Self patch.  The polar points depend only on the target's node position in its
+// patch, so one block takes kTriG targets at the same position in consecutive
+// patches: each point's basis values (the costly part: nt^2 products with U) are
+// computed once for all of them, then each target's offsets and element give its
+// integrands.  The (target, node) accumulators are spread over the block's threads;
+// every target's sum runs over the points in the same order as with one target a
+// block.  Dynamic shared memory (doubles): basis [kTT][nt], integrands
+// [kTriG][5][kTT], offsets [kTriG][3][nt], elements [kTriG][nt].
+constexpr int kTriG = 8;
+constexpr int kTriAccPerThread = (kTriG * PM_TRI_MAX_NT + kTT - 1) / kTT;
+
 __global__ void __launch_bounds__(kTT)
-k_self_quad_tri(int N, const double* __restrict__ x, const double* __restrict__ J,
+k_self_quad_tri(int npatch, const double* __restrict__ x, const double* __restrict__ J,
                 const double* __restrict__ nn, const double* __restrict__ H,
                 const double* __restrict__ ref_u, const double* __restrict__ ref_v,
                 const int* __restrict__ th_off, const double* __restrict__ th_ang,
                 const double* __restrict__ th_w, const double* __restrict__ th_L,
                 const int* __restrict__ row_ptr, int nblk, double* __restrict__ W_lb,
                 double* __restrict__ W_g, double* __restrict__ W_k) {
-    __shared__ double sD[3 * PM_TRI_MAX_NT], sJ[PM_TRI_MAX_NT];
-    __shared__ double sL[kTT * PM_TRI_MAX_NT];
-    __shared__ double sF[5 * kTT];
+    extern __shared__ double sm[];
     const int nt = cTri.nt;
-    const int i = blockIdx.x, tid = threadIdx.x;
-    const int P = i / nt, loc = i - P * nt;
-    const double u0 = ref_u[loc], v0 = ref_v[loc];
-    const double xi0 = x[3 * i], xi1 = x[3 * i + 1], xi2 = x[3 * i + 2];
-    for (int k = tid; k < nt; k += kTT) {
-        const size_t gk = (size_t)P * nt + k;
-        sD[k] = x[3 * gk] - xi0;
-        sD[nt + k] = x[3 * gk + 1] - xi1;
-        sD[2 * nt + k] = x[3 * gk + 2] - xi2;
-        sJ[k] = J[gk];
+    const int loc = blockIdx.y, tid = threadIdx.x;   // x: patch groups (no 65,535 cap)
+    const int P0 = blockIdx.x * kTriG;
+    const int G = min(kTriG, npatch - P0);
+    double* sL = sm;                                   // [kTT][nt]
+    double* sF = sL + kTT * nt;                        // [kTriG][5][kTT]
+    double* sD = sF + kTriG * 5 * kTT;                 // [kTriG][3][nt]
+    double* sJ = sD + kTriG * 3 * nt;                  // [kTriG][nt]
+    for (int e = tid; e < G * nt; e += kTT) {
+        const int g = e / nt, k = e - (e / nt) * nt;
+        const size_t i = (size_t)(P0 + g) * nt + loc, gk = (size_t)(P0 + g) * nt + k;
+        sD[(g * 3 + 0) * nt + k] = x[3 * gk] - x[3 * i];
+        sD[(g * 3 + 1) * nt + k] = x[3 * gk + 1] - x[3 * i + 1];
+        sD[(g * 3 + 2) * nt + k] = x[3 * gk + 2] - x[3 * i + 2];
+        sJ[g * nt + k] = J[gk];
     }
-    const double n0 = nn[3 * i], n1 = nn[3 * i + 1], n2 = nn[3 * i + 2];
-    const double Hi = H[i];
+    const double u0 = ref_u[loc], v0 = ref_v[loc];
     const int t0 = th_off[loc], t1 = th_off[loc + 1];
     const int npts = (t1 - t0) * (PM_RADIAL_PANELS * PM_GL16);
     const double lo_f[4] = {0.0, 0.125, 0.25, 0.5};
     const double hi_f[4] = {0.125, 0.25, 0.5, 1.0};
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[kTriAccPerThread][5];
+    for (int m = 0; m < kTriAccPerThread; ++m)
+        for (int c = 0; c < 5; ++c) acc[m][c] = 0.0;
     __syncthreads();
     for (int base = 0; base < npts; base += kTT) {
         const int q = base + tid;
         double* l = sL + tid * nt;
-        double f[5] = {0, 0, 0, 0, 0};
         if (q < npts) {
             const int kth = t0 + q / (PM_RADIAL_PANELS * PM_GL16);
             const int rj = q % (PM_RADIAL_PANELS * PM_GL16);
@@ -255,30 +267,55 @@ k_self_quad_tri(int N, const double* __restrict__ x, const double* __restrict__ 
             double sn, cs;
             sincos(th_ang[kth], &sn, &cs);
             tri_basis(u0 + r * cs, v0 + r * sn, l);
-            double d0 = 0, d1 = 0, d2 = 0, jj = 0;
-            for (int k = 0; k < nt; ++k) {
-                d0 += l[k] * sD[k];
-                d1 += l[k] * sD[nt + k];
-                d2 += l[k] * sD[2 * nt + k];
-                jj += l[k] * sJ[k];
+            const double wpt = th_w[kth] * wr * r;
+            const double logc = panel == 0 ? cTri.logE[node] : 0.0;
+            for (int g = 0; g < kTriG; ++g) {
+                double f[5] = {0, 0, 0, 0, 0};
+                if (g < G) {
+                    const double* D = sD + g * 3 * nt;
+                    const double* Jg = sJ + g * nt;
+                    double d0 = 0, d1 = 0, d2 = 0, jj = 0;
+                    for (int k = 0; k < nt; ++k) {
+                        d0 += l[k] * D[k];
+                        d1 += l[k] * D[nt + k];
+                        d2 += l[k] * D[2 * nt + k];
+                        jj += l[k] * Jg[k];
+                    }
+                    const size_t i = (size_t)(P0 + g) * nt + loc;
+                    tri_integrands(-d0, -d1, -d2, nn[3 * i], nn[3 * i + 1], nn[3 * i + 2], H[i],
+                                   wpt * jj, logc, f);
+                }
+                for (int c = 0; c < 5; ++c) sF[(g * 5 + c) * kTT + tid] = f[c];
             }
-            tri_integrands(-d0, -d1, -d2, n0, n1, n2, Hi, th_w[kth] * wr * r * jj,
-                           panel == 0 ? cTri.logE[node] : 0.0, f);
         } else {
             for (int k = 0; k < nt; ++k) l[k] = 0.0;
+            for (int g = 0; g < kTriG; ++g)
+                for (int c = 0; c < 5; ++c) sF[(g * 5 + c) * kTT + tid] = 0.0;
         }
-        for (int c = 0; c < 5; ++c) sF[c * kTT + tid] = f[c];
         __syncthreads();
-        tri_accumulate(sL, sF, min(kTT, npts - base), nt, acc);
+        const int lim = min(kTT, npts - base);
+        for (int m = 0; m < kTriAccPerThread; ++m) {
+            const int pr = tid + m * kTT;
+            if (pr >= G * nt) break;
+            const int g = pr / nt, k = pr - (pr / nt) * nt;
+            for (int e = 0; e < lim; ++e) {
+                const double lv = sL[e * nt + k];
+                for (int c = 0; c < 5; ++c) acc[m][c] += sF[(g * 5 + c) * kTT + e] * lv;
+            }
+        }
         __syncthreads();
     }
-    if (tid < nt) {
-        const size_t b0 = (size_t)row_ptr[i];              // own patch: the row's first block
-        W_lb[b0 * nt + tid] = acc[0];
-        W_g[(0 * (size_t)nblk + b0) * nt + tid] = acc[1];
-        W_g[(1 * (size_t)nblk + b0) * nt + tid] = acc[2];
-        W_g[(2 * (size_t)nblk + b0) * nt + tid] = acc[3];
-        W_k[b0 * nt + tid] = acc[4];
+    for (int m = 0; m < kTriAccPerThread; ++m) {
+        const int pr = tid + m * kTT;
+        if (pr >= G * nt) break;
+        const int g = pr / nt, k = pr - (pr / nt) * nt;
+        const size_t i = (size_t)(P0 + g) * nt + loc;
+        const size_t b0 = (size_t)row_ptr[i];          // own patch: the row's first block
+        W_lb[b0 * nt + k] = acc[m][0];
+        W_g[(0 * (size_t)nblk + b0) * nt + k] = acc[m][1];
+        W_g[(1 * (size_t)nblk + b0) * nt + k] = acc[m][2];
+        W_g[(2 * (size_t)nblk + b0) * nt + k] = acc[m][3];
+        W_k[b0 * nt + k] = acc[m][4];
     }
 }
 
@@ -658,9 +695,18 @@ pm_status pm_near_build_tri(pm_surface* s, const QuadTables& Q) {
             break;
         }
         if ((st = pm_near_structure(s)) != PM_OK) break;
-        k_self_quad_tri<<<N, kTT>>>(N, s->x, s->J, s->npatch_n, s->H, ru, rv, s->th_off,
-                                    s->th_ang, s->th_w, s->th_L, s->row_ptr, s->nblk, s->W_lb,
-                                    s->W_g, s->W_k);
+        const size_t smem = sizeof(double) * ((size_t)kTT * nt + (size_t)kTriG * 5 * kTT +
+                                              (size_t)kTriG * 4 * nt);
+        ce = cudaFuncSetAttribute(k_self_quad_tri, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
+        if (ce != cudaSuccess) {
+            pm_set_error("triangle self rule: %s", cudaGetErrorString(ce));
+            st = PM_ERR_CUDA;
+            break;
+        }
+        k_self_quad_tri<<<dim3(pm_ceil_div(npatch, kTriG), nt), kTT, smem>>>(
+            npatch, s->x, s->J, s->npatch_n, s->H, ru, rv, s->th_off, s->th_ang, s->th_w,
+            s->th_L, s->row_ptr, s->nblk, s->W_lb, s->W_g, s->W_k);
         k_near_quad_tri<<<s->nblk, kTT>>>(s->nblk, s->x, s->J, s->n, s->H, s->blk_row,
                                           s->blk_patch, s->row_ptr, s->opts.near_eta,
                                           std::min(s->opts.near_max_depth, 12),

@@ -75,7 +75,8 @@ def test_batched_autotune_and_rhs_per_block(ctx):
             assert rel(outs[rb][q], ref[q]) < 2e-6, (rb, q)
     r = s.autotune(nrhs=nrhs, prec="fp32", reps=3)
     assert r["candidates"] == 13
-    assert r["knobs"]["batch_rhs_per_block"] in (8, 16, 32)
+    # 0 = the built-in shape, kept when no timed candidate beats it
+    assert r["knobs"]["batch_rhs_per_block"] in (0, 8, 16, 32)
     assert r["best_ms"] <= r["default_ms"]
     out = s.apply_R(sig, "fp32")
     assert max(rel(out[q], ref[q]) for q in range(nrhs)) < 2e-6
