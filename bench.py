@@ -818,8 +818,9 @@ def run_micro_helmholtz(args):
 def run_helmholtz(args, dev):
     """c != 0 (Sec. 4.2) on the device in float64: the paper's sphere test with c
     added (Sec. 7.1: four harmonics incl. l = 10, u = sum f_lm Y / (c - l(l+1))) and
-    its real variable-coefficient example (Sec. 7.4: a linear in z, c = -4 - e^{x/2},
-    manufactured v = -1/|x - x0|) on cubed-sphere ellipsoids; near-field build and
+    its variable-coefficient examples (Sec. 7.4: a linear in z, c = -4 - e^{x/2}; and
+    complex c = 4 (1 + 0.2 y + 0.2 i sin x) with a = 1 + e^z; manufactured
+    v = -1/|x - x0|) on cubed-sphere ellipsoids; near-field build and
     solve times, error against the exact solution, and the float64 smooth sum's
     pair rate (the dominant kernel, k_direct_c64)."""
     import numpy as np
@@ -860,6 +861,14 @@ def run_helmholtz(args, dev):
         a, ga, c = e4(sf.nodes, sf.normals)
         f, v = manufactured(sf, a, ga, c)
         cases.append((f"ellipsoid_{sf.N}_sec74", sf, a, ga, c, f, v))
+    # the paper's complex example: a = 1 + e^z, c = 4 (1 + 0.2 y + 0.2 i sin x)
+    sf = cubed_sphere(3, 8, axes=(1.0, 1.5, 2.0))
+    ez = np.exp(sf.nodes[:, 2])
+    a = 1.0 + ez
+    ga = _tangential(np.stack([0 * ez, 0 * ez, ez], 1), sf.normals)
+    c = 4.0 * (1 + 0.2 * sf.nodes[:, 1] + 0.2j * np.sin(sf.nodes[:, 0]))
+    f, v = manufactured(sf, a, ga, c)
+    cases.append((f"ellipsoid_{sf.N}_sec74_complex", sf, a, ga, c, f, v))
     for name, sf, a, ga, c, f, uex in cases:
         s = pm.Surface.from_fixture(ctx, sf)
         t0 = time.perf_counter()

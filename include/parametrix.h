@@ -491,17 +491,27 @@ pm_status pm_selftest_tri_basis(int p, const double* ref, int npts, const double
                                 const double* v, double* l, double* Du, double* Dv);
 
 /*
+ * Host self-test (no GPU) of the library's float64 g, g', g'' for complex q = c/a
+ * (as pm_selftest_green; the branch arg q in (-pi/2, 3pi/2], K0 and K1 at complex
+ * argument by their series and a deformed integration contour): out [n][6] =
+ * (re, im) of g, g', g''.  q_im = 0 is pm_selftest_green.  PM_ERR_INVALID_ARG for
+ * NULL arrays, n < 0, r <= 0 or not finite, q zero or not finite.
+ */
+pm_status pm_selftest_green_c(const double* r, int n, double q_re, double q_im, double* out);
+
+/*
  * Helmholtz and modified-Helmholtz surface problems, div_G(a grad_G u) + c u = f
- * with c real (Sec. 4.2; Thm. second_kind with the parametrix of eq. diff_param
- * and the remainder of eq. explicit_remainder).  With q = c/a the kernels use
- * g(r; k), k^2 = q: -(i/4) H0(k r) where q > 0, -K0(sqrt(-q) r)/(2 pi) where q < 0,
- * log(r)/(2 pi) where q = 0 exactly; the source's q enters through k(y) (at the
- * nodes in the smooth rule, interpolated on the patch in the singular and near
- * rules).  There is no null space: sigma + R~ sigma = f and u = K~ sigma, with no
- * rank-one term and no mean condition on f or u.  Complex c is not supported.
+ * with c real or complex (Sec. 4.2; Thm. second_kind with the parametrix of eq.
+ * diff_param and the remainder of eq. explicit_remainder).  With q = c/a the
+ * kernels use g(r; k) = -(i/4) H0(k r), k^2 = q on the branch arg q in
+ * (-pi/2, 3pi/2] (real q < 0: -K0(sqrt(-q) r)/(2 pi); complex q: K0, K1 at complex
+ * argument), and log(r)/(2 pi) where q = 0 exactly; the source's q enters through
+ * k(y) (at the nodes in the smooth rule, interpolated on the patch in the singular
+ * and near rules).  There is no null space: sigma + R~ sigma = f and
+ * u = K~ sigma, with no rank-one term and no mean condition on f or u.
  *
  * pm_surface_set_coeff_c: a [N] > 0, grad_a [N][3] or NULL (spectral, as in
- * pm_surface_set_coeff), c [N] real and finite (host arrays, copied).  It sets a
+ * pm_surface_set_coeff), c [N][2] complex (re, im) and finite (host arrays, copied).  It sets a
  * as pm_surface_set_coeff does and, when some c is non-zero, builds the complex
  * float64 near-field corrections of the c != 0 operators (Sec. 6.1.1 polar rule
  * with dyadically graded radial panels, Sec. 6.1.2 subdivision; synchronises).

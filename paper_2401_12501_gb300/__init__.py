@@ -217,12 +217,11 @@ class Surface:
         check(_lib.lib().pm_surface_check(self.handle), "pm_surface_check")
 
     def set_coeff_c(self, a, grad_a, c):
-        """a, grad_a as in set_coeff, and a real c [N] (div(a grad u) + c u = f)."""
-        if not np.isrealobj(c):
-            raise ValueError("set_coeff_c: c must be real (complex c is not supported)")
+        """a, grad_a as in set_coeff, and c [N] real or complex (div(a grad u) + c u = f)."""
         a = _f64(a, self.N)
         g = None if grad_a is None else _f64(grad_a, 3 * self.N)
-        cc = np.ascontiguousarray(np.asarray(c, dtype=np.float64) * np.ones(self.N))
+        cz = np.asarray(c, dtype=np.complex128) * np.ones(self.N)
+        cc = np.ascontiguousarray(np.stack([cz.real, cz.imag], 1))
         check(_lib.lib().pm_surface_set_coeff_c(self.handle, ptr(a), ptr(g), ptr(cc)),
               "pm_surface_set_coeff_c")
 

@@ -21,6 +21,29 @@ extern "C" pm_status pm_selftest_green(const double* r, int n, double q, double*
     return PM_OK;
 }
 
+extern "C" pm_status pm_selftest_green_c(const double* r, int n, double q_re, double q_im,
+                                         double* out) {
+    if (!r || !out || n < 0 || !std::isfinite(q_re) || !std::isfinite(q_im) ||
+        (q_re == 0.0 && q_im == 0.0)) {
+        pm_set_error("pm_selftest_green_c: NULL array, negative n, or q not finite and non-zero");
+        return PM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!(r[i] > 0.0) || !std::isfinite(r[i])) {
+            pm_set_error("pm_selftest_green_c: r must be finite and positive");
+            return PM_ERR_INVALID_ARG;
+        }
+    QuadTables T;
+    pm_build_tables(2, &T);
+    for (int i = 0; i < n; ++i) {
+        if (q_im == 0.0)
+            pm_green::green_scaled(r[i], q_re, out + 6 * i);
+        else
+            pm_green::green_scaled_cz(r[i], pm_green::cplx_d{q_re, q_im}, T.g16t, T.g16w, out + 6 * i);
+    }
+    return PM_OK;
+}
+
 extern "C" pm_status pm_selftest_green_f32(const float* r, int n, float q, float* out) {
     if (!r || !out || n < 0 || !std::isfinite(q) || q == 0.0f) {
         pm_set_error("pm_selftest_green_f32: NULL array, negative n, or q not finite and non-zero");

@@ -1,12 +1,13 @@
-// div_G(a grad_G u) + c u = f for real c != 0 (Sec. 4.2, Thm. second_kind):
+// div_G(a grad_G u) + c u = f for c != 0, real or complex (Sec. 4.2, Thm. second_kind):
 // the Helmholtz (c/a > 0) and modified-Helmholtz (c/a < 0) parametrices of
 // eq. diff_param, their remainder eq. explicit_remainder, the second-kind
 // equation sigma + R~ sigma = f and the representation u = K~ sigma.  With
 // c != 0 there is no null space: no rank-one term and no mean projection.
 //
 // Everything is complex (the Helmholtz kernel is -(i/4) H0(kr); the modified one
-// -K0(kappa r)/(2 pi) is real, but one path serves both signs and a c whose sign
-// changes over the surface).  Arithmetic is float64 throughout:
+// -K0(kappa r)/(2 pi) is real, but one path serves both signs, a c whose sign
+// changes over the surface and complex c, whose kernels take K0, K1 at complex
+// argument, pm_green.cuh).  Arithmetic is float64 throughout:
 //   - smooth sums: one thread per target, sources staged through shared memory,
 //     split over gridDim.y, g, g', g'' from pm_green.cuh at every pair;
 //   - near field: complex corrections from pm_nearfield.cu (pm_near_build_c);
@@ -25,6 +26,7 @@ namespace {
 
 using cplx = std::complex<double>;
 constexpr int kHT = 128;        // threads (targets) per block of the smooth sums
+__constant__ double cHG16[2 * PM_GL16];   // 16-point Gauss-Legendre nodes, weights (complex q)
 constexpr int kRT = 256;        // threads of the vector kernels
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -44,14 +46,16 @@ template <int WHICH>
 __global__ void __launch_bounds__(kHT)
 k_direct_c64(const double* __restrict__ x, const double* __restrict__ n,
              const double* __restrict__ H, const double* __restrict__ a,
-             const double* __restrict__ g, const double* __restrict__ c,
-             const double* __restrict__ qn, const double2* __restrict__ sv, int N, int chunk,
+             const double* __restrict__ g, const double2* __restrict__ c,
+             const double2* __restrict__ qn, const double2* __restrict__ sv, int N, int chunk,
              double2* __restrict__ partial) {
-    __shared__ double4 sx[kHT];          // source x, y, z, q
+    __shared__ double4 sx[kHT];          // source x, y, z, Re q
+    __shared__ double sqi[kHT];          // source Im q
     __shared__ double2 ss[kHT];          // source strength
     const int tid = threadIdx.x;
     const int i = blockIdx.x * kHT + tid;
-    double xi[3] = {0, 0, 0}, ni[3] = {0, 0, 1}, gi[3] = {0, 0, 0}, Hi = 0, ai = 1, ci = 0;
+    double xi[3] = {0, 0, 0}, ni[3] = {0, 0, 1}, gi[3] = {0, 0, 0}, Hi = 0, ai = 1;
+    pm_green::cplx_d ci = {0.0, 0.0};
     if (i < N) {
         for (int d = 0; d < 3; ++d) {
             xi[d] = x[3 * i + d];
@@ -60,7 +64,7 @@ k_direct_c64(const double* __restrict__ x, const double* __restrict__ n,
         }
         Hi = H[i];
         ai = a[i];
-        ci = c[i];
+        ci = {c[i].x, c[i].y};
     }
     double are = 0.0, aim = 0.0;
     const int s0 = blockIdx.y * chunk;
@@ -69,7 +73,8 @@ k_direct_c64(const double* __restrict__ x, const double* __restrict__ n,
         __syncthreads();
         const int j = base + tid;
         if (j < s1) {
-            sx[tid] = make_double4(x[3 * j], x[3 * j + 1], x[3 * j + 2], qn[j]);
+            sx[tid] = make_double4(x[3 * j], x[3 * j + 1], x[3 * j + 2], qn[j].x);
+            sqi[tid] = qn[j].y;
             ss[tid] = sv[j];
         }
         __syncthreads();
@@ -79,8 +84,9 @@ k_direct_c64(const double* __restrict__ x, const double* __restrict__ n,
                 if (base + jj == i) continue;
                 const double4 y = sx[jj];
                 double out[4];
-                pm_green::pair_rk_c(xi[0] - y.x, xi[1] - y.y, xi[2] - y.z, ni[0], ni[1], ni[2],
-                                    Hi, ai, gi[0], gi[1], gi[2], ci, y.w, out);
+                pm_green::pair_rk_cz(xi[0] - y.x, xi[1] - y.y, xi[2] - y.z, ni[0], ni[1], ni[2],
+                                     Hi, ai, gi[0], gi[1], gi[2], ci,
+                                     pm_green::cplx_d{y.w, sqi[jj]}, cHG16, cHG16 + PM_GL16, out);
                 const double2 kv = WHICH ? make_double2(out[2], out[3])
                                          : make_double2(out[0], out[1]);
                 const double2 t = cmul(kv, ss[jj]);
@@ -378,26 +384,40 @@ extern "C" pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, cons
     const int N = s->N;
     bool any = false;
     for (int k = 0; k < N; ++k) {
-        if (!std::isfinite(c[k])) {
-            pm_set_error("pm_surface_set_coeff_c: c[%d] = %g is not finite", k, c[k]);
+        if (!std::isfinite(c[2 * k]) || !std::isfinite(c[2 * k + 1])) {
+            pm_set_error("pm_surface_set_coeff_c: c[%d] = %g%+gi is not finite", k, c[2 * k],
+                         c[2 * k + 1]);
             return PM_ERR_INVALID_ARG;
         }
-        any = any || c[k] != 0.0;
+        any = any || c[2 * k] != 0.0 || c[2 * k + 1] != 0.0;
     }
     // a and grad_a are checked, copied and packed by the c = 0 path, which also
     // leaves c = 0 surfaces exactly as pm_surface_set_coeff does
     PM_TRY(pm_surface_set_coeff(s, a, grad_a));
     if (!any) return PM_OK;
-    std::vector<double> q(N);
-    for (int k = 0; k < N; ++k) q[k] = c[k] / a[k];
+    std::vector<double> q(2 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+        q[2 * k] = c[2 * k] / a[k];
+        q[2 * k + 1] = c[2 * k + 1] / a[k];
+    }
     if (!s->cc) {
         PM_TRY(pm_dmalloc(&s->cc, N));
         PM_TRY(pm_dmalloc(&s->qn, N));
         PM_TRY(pm_dmalloc(&s->cRc, (size_t)s->nblk * s->pp));
         PM_TRY(pm_dmalloc(&s->cKc, (size_t)s->nblk * s->pp));
     }
-    PM_CUDA_TRY(cudaMemcpy(s->cc, c, sizeof(double) * N, cudaMemcpyHostToDevice));
-    PM_CUDA_TRY(cudaMemcpy(s->qn, q.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(s->cc, c, sizeof(double2) * N, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(s->qn, q.data(), sizeof(double2) * N, cudaMemcpyHostToDevice));
+    {
+        QuadTables T;
+        pm_build_tables(2, &T);
+        double g16[2 * PM_GL16];
+        for (int k = 0; k < PM_GL16; ++k) {
+            g16[k] = T.g16t[k];
+            g16[PM_GL16 + k] = T.g16w[k];
+        }
+        PM_CUDA_TRY(cudaMemcpyToSymbol(cHG16, g16, sizeof(g16)));
+    }
     PM_TRY(pm_near_build_c(s));
     s->has_c = 1;
     s->graph_epoch++;

@@ -172,11 +172,11 @@ struct pm_surface {
     float* cR32 = nullptr;        // [nblk*ppad]
     float* cK32 = nullptr;        // [nblk*ppad]
 
-    // c != 0 (pm_surface_set_coeff_c, pm_helm.cu): real c at the nodes, q = c/a,
-    // complex corrections of a(y) R and a(y) K (with the coefficients), work
+    // c != 0 (pm_surface_set_coeff_c, pm_helm.cu): c at the nodes, q = c/a (complex,
+    // (re, im)), complex corrections of a(y) R and a(y) K (with the coefficients), work
     int has_c = 0;
-    double* cc = nullptr;         // [N] c
-    double* qn = nullptr;         // [N] c/a
+    double2* cc = nullptr;        // [N] c
+    double2* qn = nullptr;        // [N] c/a
     double2* cRc = nullptr;       // [nblk*pp]
     double2* cKc = nullptr;       // [nblk*pp]
     PmHelmWork* helm = nullptr;

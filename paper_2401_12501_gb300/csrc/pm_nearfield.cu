@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kQThreads)
 k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restrict__ J,
               const double* __restrict__ nn, const double* __restrict__ H,
               const double* __restrict__ a, const double* __restrict__ g,
-              const double* __restrict__ c, const double* __restrict__ qn,
+              const double2* __restrict__ c, const double2* __restrict__ qn,
               const int* __restrict__ th_off, const double* __restrict__ th_ang,
               const double* __restrict__ th_w, const double* __restrict__ th_L,
               const int* __restrict__ row_ptr, double2* __restrict__ WR,
@@ -548,8 +548,8 @@ k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restri
     const int pp = p * p;
     double* sD = sm;                       // [3][pp]
     double* sJ = sD + 3 * pp;              // [pp]
-    double* sQ = sJ + pp;                  // [pp]
-    double* sLu = sQ + pp;                 // [128][p]
+    double* sQ = sJ + pp;                  // [2][pp]: q = c/a, re and im
+    double* sLu = sQ + 2 * pp;             // [128][p]
     double* sLv = sLu + kQThreads * p;     // [128][p]
     double* sF = sLv + kQThreads * p;      // [4][128]
     const int i = blockIdx.x;
@@ -563,10 +563,12 @@ k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restri
         sD[pp + k] = x[3 * gk + 1] - xi1;
         sD[2 * pp + k] = x[3 * gk + 2] - xi2;
         sJ[k] = J[gk];
-        sQ[k] = qn[gk];
+        sQ[k] = qn[gk].x;
+        sQ[pp + k] = qn[gk].y;
     }
     const double n0 = nn[3 * i], n1 = nn[3 * i + 1], n2 = nn[3 * i + 2];
-    const double Hi = H[i], ai = a[i], ci = c[i];
+    const double Hi = H[i], ai = a[i];
+    const pm_green::cplx_d ci = {c[i].x, c[i].y};
     const double g0 = g[3 * i], g1 = g[3 * i + 1], g2 = g[3 * i + 2];
     const int t0 = th_off[loc], t1 = th_off[loc + 1];
     const int npts = (t1 - t0) * (kSelfPanelsC * PM_GL16);
@@ -591,9 +593,9 @@ k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restri
             sincos(th_ang[kth], &sn, &cs);
             lagrange(u0 + r * cs, p, lu);
             lagrange(v0 + r * sn, p, lv);
-            double d0 = 0, d1 = 0, d2 = 0, jj = 0, qq = 0;
+            double d0 = 0, d1 = 0, d2 = 0, jj = 0, qr = 0, qi = 0;
             for (int aa = 0; aa < p; ++aa) {
-                double z0 = 0, z1 = 0, z2 = 0, zj = 0, zq = 0;
+                double z0 = 0, z1 = 0, z2 = 0, zj = 0, zr = 0, zi = 0;
                 for (int bb = 0; bb < p; ++bb) {
                     const double l = lv[bb];
                     const int k = aa * p + bb;
@@ -601,16 +603,19 @@ k_self_quad_c(int N, int p, const double* __restrict__ x, const double* __restri
                     z1 += sD[pp + k] * l;
                     z2 += sD[2 * pp + k] * l;
                     zj += sJ[k] * l;
-                    zq += sQ[k] * l;
+                    zr += sQ[k] * l;
+                    zi += sQ[pp + k] * l;
                 }
                 d0 += lu[aa] * z0;
                 d1 += lu[aa] * z1;
                 d2 += lu[aa] * z2;
                 jj += lu[aa] * zj;
-                qq += lu[aa] * zq;
+                qr += lu[aa] * zr;
+                qi += lu[aa] * zi;
             }
             double out[4];
-            pm_green::pair_rk_c(-d0, -d1, -d2, n0, n1, n2, Hi, ai, g0, g1, g2, ci, qq, out);
+            pm_green::pair_rk_cz(-d0, -d1, -d2, n0, n1, n2, Hi, ai, g0, g1, g2, ci,
+                                 pm_green::cplx_d{qr, qi}, cT.g16t, cT.g16w, out);
             const double bw = th_w[kth] * wr * r * jj;
             for (int k = 0; k < 4; ++k) f[k] = bw * out[k];
         } else {
@@ -640,7 +645,7 @@ __global__ void __launch_bounds__(kQThreads)
 k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
               const double* __restrict__ n, const double* __restrict__ H,
               const double* __restrict__ a, const double* __restrict__ g,
-              const double* __restrict__ c, const double* __restrict__ qn,
+              const double2* __restrict__ c, const double2* __restrict__ qn,
               const int* __restrict__ blk_row, const int* __restrict__ blk_patch,
               const int* __restrict__ row_ptr, double eta, int max_depth, int max_leaves,
               double2* __restrict__ WR, double2* __restrict__ WK, int* __restrict__ err) {
@@ -650,11 +655,12 @@ k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
     const int P = blk_patch[b];
     const int pp = p * p;
     const int tid = threadIdx.x;
-    __shared__ double sD[3 * PM_MAX_P * PM_MAX_P];
-    __shared__ double sJ[PM_MAX_P * PM_MAX_P];
-    __shared__ double sQ[PM_MAX_P * PM_MAX_P];
-    __shared__ double sLu[PM_GL16 * PM_MAX_P], sLv[PM_GL16 * PM_MAX_P];
-    __shared__ double sZ[5 * PM_MAX_P * PM_GL16];     // [5][a][r]
+    // sized for the largest order a surface accepts (p <= PM_MAX_P_API)
+    __shared__ double sD[3 * PM_MAX_P_API * PM_MAX_P_API];
+    __shared__ double sJ[PM_MAX_P_API * PM_MAX_P_API];
+    __shared__ double sQ[2 * PM_MAX_P_API * PM_MAX_P_API];   // q = c/a: re, im
+    __shared__ double sLu[PM_GL16 * PM_MAX_P_API], sLv[PM_GL16 * PM_MAX_P_API];
+    __shared__ double sZ[6 * PM_MAX_P_API * PM_GL16];        // [6][a][r]
     __shared__ double sF[4 * PM_GL16 * PM_GL16];      // [4][q*16 + r]
     __shared__ NearBfs bfs;
     const double* X = x + (size_t)3 * P * pp;
@@ -665,13 +671,15 @@ k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
         sD[pp + k] = x[3 * gk + 1] - xi1;
         sD[2 * pp + k] = x[3 * gk + 2] - xi2;
         sJ[k] = J[gk];
-        sQ[k] = qn[gk];
+        sQ[k] = qn[gk].x;
+        sQ[pp + k] = qn[gk].y;
     }
     const int nleaves = near_leaves(X, p, xi0, xi1, xi2, eta, max_depth, max_leaves, bfs, err);
     const int a_own = tid / p, b_own = tid - (tid / p) * p;
     double acc[4] = {0, 0, 0, 0};
     const double n0 = n[3 * i], n1 = n[3 * i + 1], n2 = n[3 * i + 2];
-    const double Hi = H[i], ai = a[i], ci = c[i];
+    const double Hi = H[i], ai = a[i];
+    const pm_green::cplx_d ci = {c[i].x, c[i].y};
     const double g0 = g[3 * i], g1 = g[3 * i + 1], g2 = g[3 * i + 2];
     constexpr int kQ2 = PM_GL16 * PM_GL16;
     for (int L = 0; L < nleaves; ++L) {
@@ -682,11 +690,11 @@ k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
         else if (tid < 2 * PM_GL16)
             lagrange(v0 + hv * (cT.g16t[tid - PM_GL16] + 1.0), p, sLv + (tid - PM_GL16) * p);
         __syncthreads();
-        // Z[f][a][r] = sum_b F_f[a][b] l_b(v_r) for F = D (3 components), J, q
-        for (int e = tid; e < 5 * p * PM_GL16; e += kQThreads) {
+        // Z[f][a][r] = sum_b F_f[a][b] l_b(v_r) for F = D (3 components), J, q (re, im)
+        for (int e = tid; e < 6 * p * PM_GL16; e += kQThreads) {
             const int cf = e / (p * PM_GL16), rem = e - cf * p * PM_GL16;
             const int aa = rem / PM_GL16, r = rem - aa * PM_GL16;
-            const double* src = (cf < 3) ? (sD + cf * pp) : (cf == 3 ? sJ : sQ);
+            const double* src = (cf < 3) ? (sD + cf * pp) : (cf == 3 ? sJ : sQ + (cf - 4) * pp);
             double z = 0;
             for (int bb = 0; bb < p; ++bb) z += src[aa * p + bb] * sLv[r * p + bb];
             sZ[(cf * p + aa) * PM_GL16 + r] = z;
@@ -694,14 +702,14 @@ k_near_quad_c(int p, const double* __restrict__ x, const double* __restrict__ J,
         __syncthreads();
         for (int e = tid; e < kQ2; e += kQThreads) {
             const int qn_ = e / PM_GL16, r = e - qn_ * PM_GL16;
-            double v5[5] = {0, 0, 0, 0, 0};
+            double v5[6] = {0, 0, 0, 0, 0, 0};
             for (int aa = 0; aa < p; ++aa) {
                 const double l = sLu[qn_ * p + aa];
-                for (int cf = 0; cf < 5; ++cf) v5[cf] += l * sZ[(cf * p + aa) * PM_GL16 + r];
+                for (int cf = 0; cf < 6; ++cf) v5[cf] += l * sZ[(cf * p + aa) * PM_GL16 + r];
             }
             double out[4];
-            pm_green::pair_rk_c(-v5[0], -v5[1], -v5[2], n0, n1, n2, Hi, ai, g0, g1, g2, ci, v5[4],
-                                out);
+            pm_green::pair_rk_cz(-v5[0], -v5[1], -v5[2], n0, n1, n2, Hi, ai, g0, g1, g2, ci,
+                                 pm_green::cplx_d{v5[4], v5[5]}, cT.g16t, cT.g16w, out);
             const double wgt = hu * cT.g16w[qn_] * hv * cT.g16w[r] * v5[3];
             for (int k = 0; k < 4; ++k) sF[k * kQ2 + e] = wgt * out[k];
         }
@@ -733,8 +741,8 @@ __global__ void k_combine_c(int nblk, int pp, const int* __restrict__ blk_row,
                             const int* __restrict__ blk_patch, const double* __restrict__ x,
                             const double* __restrict__ n, const double* __restrict__ H,
                             const double* __restrict__ w, const double* __restrict__ a,
-                            const double* __restrict__ g, const double* __restrict__ c,
-                            const double* __restrict__ qn, double2* __restrict__ CR,
+                            const double* __restrict__ g, const double2* __restrict__ c,
+                            const double2* __restrict__ qn, double2* __restrict__ CR,
                             double2* __restrict__ CK) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)nblk * pp) return;
@@ -744,9 +752,11 @@ __global__ void k_combine_c(int nblk, int pp, const int* __restrict__ blk_row,
     const double inv_a = 1.0 / a[j];
     if (j != i) {
         double out[4];
-        pm_green::pair_rk_c(x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
-                            x[3 * i + 2] - x[3 * j + 2], n[3 * i], n[3 * i + 1], n[3 * i + 2],
-                            H[i], a[i], g[3 * i], g[3 * i + 1], g[3 * i + 2], c[i], qn[j], out);
+        pm_green::pair_rk_cz(x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
+                             x[3 * i + 2] - x[3 * j + 2], n[3 * i], n[3 * i + 1], n[3 * i + 2],
+                             H[i], a[i], g[3 * i], g[3 * i + 1], g[3 * i + 2],
+                             pm_green::cplx_d{c[i].x, c[i].y}, pm_green::cplx_d{qn[j].x, qn[j].y},
+                             cT.g16t, cT.g16w, out);
         wr.x -= w[j] * out[0];
         wr.y -= w[j] * out[1];
         wk.x -= w[j] * out[2];
@@ -1113,7 +1123,7 @@ pm_status pm_near_build_c(pm_surface* s) {
     pm_build_tables(p, &T);
     PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
     PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
-    const size_t smem = sizeof(double) * (5 * (size_t)pp + 2 * (size_t)kQThreads * p + 4 * kQThreads);
+    const size_t smem = sizeof(double) * (6 * (size_t)pp + 2 * (size_t)kQThreads * p + 4 * kQThreads);
     if (smem > 48 * 1024)
         PM_CUDA_TRY(cudaFuncSetAttribute(k_self_quad_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));

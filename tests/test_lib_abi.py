@@ -151,6 +151,28 @@ def test_green_function_c_nonzero(lib):
     assert lib.pm_selftest_green(None, 1, 1.0, ptr(out)) == 1
 
 
+def test_green_function_complex_c(lib):
+    """Complex q = c/a (the library's K0/K1 at complex argument: series below |w| = 2,
+    deformed contour above) against the oracle's scipy Hankel functions, on the
+    branch arg q in (-pi/2, 3pi/2] (reading 21): q in every quadrant, near the real
+    axes and with large |k r|."""
+    import numpy as np
+    from oracle.kernels import green_scaled, wavenumber
+    from paper_2401_12501_gb300._lib import ptr
+    r = np.concatenate([np.geomspace(1e-5, 12.0, 161), [0.3, 1.0, 2.5]])
+    for q in (4 + 1j, 4 - 1j, -4 + 0.5j, -4 - 0.5j, 2j, -2j, 0.3 + 2j, 4 + 1e-3j, -1 - 1e-3j,
+              9 + 3j, 0.01 + 0.02j):
+        out = np.zeros((len(r), 6))
+        assert lib.pm_selftest_green_c(ptr(r), len(r), q.real, q.imag, ptr(out)) == 0
+        ref = green_scaled(r, wavenumber(q, 1.0))
+        for m, name in enumerate(("g", "g'", "g''")):
+            got = out[:, 2 * m] + 1j * out[:, 2 * m + 1]
+            err = np.abs(got - ref[m]) / np.abs(ref[m])
+            assert err.max() < 1e-12, (q, name, err.max(), r[err.argmax()])
+    out = np.zeros(6)
+    assert lib.pm_selftest_green_c(ptr(np.array([1.0])), 1, 0.0, 0.0, ptr(out)) == 1
+
+
 def test_green_function_c_nonzero_float32(lib):
     """The float32 evaluation the per-pair sums use (pm_green.cuh, host code, no GPU)
     against the oracle at the float32 radii: 2e-6 relative (absolute near the zeros of
