@@ -796,6 +796,22 @@ def run_triangles(args, dev):
     return out
 
 
+def run_micro_tri(args):
+    """One triangle-patch surface build (the unit sphere from 80 triangles at the order-8
+    Vioreanu-Rokhlin nodes, 2,880 nodes): the launches an ncu capture of the triangle
+    near-field kernels looks at."""
+    import paper_2401_12501_gb300 as pm
+    from workloads.trisurfaces import tri_ellipsoid
+    ctx = pm.Context(0)
+    sf = tri_ellipsoid(1, 8)
+    t0 = time.perf_counter()
+    s = pm.Surface.from_fixture(ctx, sf)
+    print(json.dumps({"micro": "tri", "N": sf.N, "near_blocks": s.info()[1],
+                      "build_s": round(time.perf_counter() - t0, 3)}))
+    s.close()
+    ctx.close()
+
+
 def run_micro_helmholtz(args):
     """Three float64 c != 0 remainder applies on the 1,536-node unit sphere (a = 1,
     c = --micro-c): the launches an ncu capture of k_direct_c64 looks at."""
@@ -1176,7 +1192,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
-    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz"], default=None,
+    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz", "tri"], default=None,
                     help="time one kernel alone instead of the solve step (profiling aid)")
     ap.add_argument("--micro-c", type=float, default=-4.0,
                     help="c of --micro helmholtz (1,536-node unit sphere, a = 1)")
@@ -1187,6 +1203,9 @@ def main():
         return
     if args.micro == "helmholtz":
         run_micro_helmholtz(args)
+        return
+    if args.micro == "tri":
+        run_micro_tri(args)
         return
     if args.oracle_leg:
         P = host_cores()
