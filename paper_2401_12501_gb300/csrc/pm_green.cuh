@@ -28,6 +28,8 @@
 
 #include <math.h>
 
+#include <cmath>
+
 namespace pm_green {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -60,14 +62,88 @@ __host__ __device__ constexpr SeriesK01d series_k01_d()
     return c;
 }
 
+// Above x = 2, F_nu(x) = sqrt(x) e^x K_nu(x) is smooth in 1/x (it tends to sqrt(pi/2))
+// and is expanded in Chebyshev polynomials of z = 4/x - 1 in [-1, 1): 24 terms, whose
+// coefficients fall to rounding level by the twentieth.  The coefficients are
+// computed once on the host by interpolation at 64 Chebyshev points from reference
+// values of F: the trapezoid rule on e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2))
+// cosh(nu t) dt (A&S 9.6.24; analytic in the strip |Im t| < pi/2, so geometric
+// convergence, step min(1/4, pi^2/(40 + x))) below x = 40, and the asymptotic series
+// F_nu ~ sqrt(pi/2) sum_k a_k / x^k, a_k = a_{k-1} (4 nu^2 - (2k - 1)^2)/(8k)
+// (A&S 9.7.2) from x = 40, where its smallest term is below 1e-30.  Each translation
+// unit that launches kernels evaluating K0/K1 uploads them (upload_cheb_k01).
+constexpr int kChebK01 = 24;
+struct ChebK01 {
+    double c0[kChebK01], c1[kChebK01];
+};
+
+inline void scaled_k01_reference(double x, double* F0, double* F1)
+{
+    if (x >= 40.0) {
+        for (int nu = 0; nu < 2; ++nu) {
+            double a = 1.0, sum = 1.0;
+            for (int k = 1; k < 60; ++k) {
+                const double na = a * (4.0 * nu * nu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k * x);
+                if (std::fabs(na) >= std::fabs(a) || std::fabs(na) < 1e-30) break;
+                a = na;
+                sum += a;
+            }
+            (nu == 0 ? *F0 : *F1) = std::sqrt(0.5 * kPi) * sum;
+        }
+        return;
+    }
+    const double h = std::fmin(0.25, kPi * kPi / (40.0 + x));
+    double s0 = 0.5, s1 = 0.5;
+    for (int j = 1; j <= 400; ++j) {
+        const double sh = std::sinh(0.5 * j * h);
+        const double e = std::exp(-2.0 * x * sh * sh);
+        s0 += e;
+        s1 += e * (1.0 + 2.0 * sh * sh);
+        if (e < 1e-20 * s0) break;
+    }
+    *F0 = std::sqrt(x) * h * s0;
+    *F1 = std::sqrt(x) * h * s1;
+}
+
+inline const ChebK01& cheb_k01_host()
+{
+    static const ChebK01 table = [] {
+        constexpr int M = 64;
+        double F0[M], F1[M];
+        for (int j = 0; j < M; ++j) {
+            const double z = std::cos(kPi * (j + 0.5) / M);
+            scaled_k01_reference(4.0 / (z + 1.0), &F0[j], &F1[j]);
+        }
+        ChebK01 t{};
+        for (int k = 0; k < kChebK01; ++k) {
+            double a0 = 0.0, a1 = 0.0;
+            for (int j = 0; j < M; ++j) {
+                const double c = std::cos(k * kPi * (j + 0.5) / M);
+                a0 += F0[j] * c;
+                a1 += F1[j] * c;
+            }
+            t.c0[k] = (k == 0 ? 1.0 : 2.0) * a0 / M;
+            t.c1[k] = (k == 0 ? 1.0 : 2.0) * a1 / M;
+        }
+        return t;
+    }();
+    return table;
+}
+
+#ifdef __CUDACC__
+static __constant__ ChebK01 g_cheb_k01;      // this translation unit's device copy
+static inline cudaError_t upload_cheb_k01()
+{
+    return cudaMemcpyToSymbol(g_cheb_k01, &cheb_k01_host(), sizeof(ChebK01));
+}
+#endif
+
 // K0(x), K1(x) for x > 0.
 //   x <= 2: K0 = -ln(x/2) I0 + sum_j psi(j+1) t^j/(j!)^2,
 //           K1 = 1/x + ln(x/2) I1 - (x/4) sum_j (psi(j+1) + psi(j+2)) t^j/(j! (j+1)!),
 //           t = x^2/4 (A&S 9.6.13, 9.6.11), four Horner sums of fourteen terms;
-//   x > 2:  the trapezoid rule on e^x K_nu(x) = int_0^inf exp(-2 x sinh^2(t/2)) cosh(nu t) dt
-//           with step h = min(1/4, pi^2/(40 + x)) (error O(exp(x - pi^2/h)) below 1e-16
-//           relative), sinh and cosh of j h/2 by the addition formulas, stopping once a
-//           term is below 1e-17 of the sum (at most 64 terms; 26 suffice up to x = 700).
+//   x > 2:  K_nu = e^{-x} F_nu(x) / sqrt(x) with F_nu from its Chebyshev expansion
+//           (above), summed by Clenshaw's recurrence.
 __host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
 {
     if (x != x) {                       // NaN passes through (no term count from it)
@@ -90,22 +166,25 @@ __host__ __device__ inline void bessel_k01(double x, double* k0v, double* k1v)
         *k1v = 1.0 / x + lg * (0.5 * x * i1s) - 0.25 * x * s1;
         return;
     }
-    const double h = fmin(0.25, kPi * kPi / (40.0 + x));
-    const double sh1 = sinh(0.5 * h), ch1 = cosh(0.5 * h);
-    double sh = 0.0, ch = 1.0, s0 = 0.5, s1 = 0.5;
-    for (int j = 1; j <= 64; ++j) {
-        const double shn = fma(sh, ch1, ch * sh1);
-        ch = fma(ch, ch1, sh * sh1);
-        sh = shn;
-        const double s2 = sh * sh;
-        const double e = exp(-2.0 * x * s2);
-        s0 += e;
-        s1 = fma(e, fma(2.0, s2, 1.0), s1);           // cosh t = 1 + 2 sinh^2(t/2)
-        if (e < 1e-17 * s0) break;
+#ifdef __CUDA_ARCH__
+    const ChebK01& C = g_cheb_k01;
+#else
+    const ChebK01& C = cheb_k01_host();
+#endif
+    const double z = 4.0 / x - 1.0, z2 = 2.0 * z;
+    double b01 = 0.0, b02 = 0.0, b11 = 0.0, b12 = 0.0;   // Clenshaw: b_{k+1}, b_{k+2}
+    for (int k = kChebK01 - 1; k >= 1; --k) {
+        const double t0 = fma(z2, b01, C.c0[k] - b02);
+        const double t1 = fma(z2, b11, C.c1[k] - b12);
+        b02 = b01;
+        b01 = t0;
+        b12 = b11;
+        b11 = t1;
     }
-    const double ex = exp(-x);
-    *k0v = h * s0 * ex;
-    *k1v = h * s1 * ex;
+    const double F0 = fma(z, b01, C.c0[0] - b02), F1 = fma(z, b11, C.c1[0] - b12);
+    const double f = exp(-x) / sqrt(x);
+    *k0v = F0 * f;
+    *k1v = F1 * f;
 }
 
 // (g, g', g'') at r > 0 for q = c~/a~ real and non-zero, as (re, im) pairs:

@@ -417,6 +417,7 @@ extern "C" pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, cons
             g16[PM_GL16 + k] = T.g16w[k];
         }
         PM_CUDA_TRY(cudaMemcpyToSymbol(cHG16, g16, sizeof(g16)));
+        PM_CUDA_TRY(pm_green::upload_cheb_k01());
     }
     PM_TRY(pm_near_build_c(s));
     s->has_c = 1;

@@ -1122,6 +1122,7 @@ pm_status pm_near_build_c(pm_surface* s) {
     QuadTables T;
     pm_build_tables(p, &T);
     PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
+    PM_CUDA_TRY(pm_green::upload_cheb_k01());
     PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
     const size_t smem = sizeof(double) * (6 * (size_t)pp + 2 * (size_t)kQThreads * p + 4 * kQThreads);
     if (smem > 48 * 1024)
