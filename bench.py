@@ -7,7 +7,10 @@ relative residual of 1e-10 (so that u matches a plain float64 GPU solve to well
 within 1e-8; the line reports the measured difference): device GMRES whose
 operator applies use the Chebyshev FMM (tensor-core M2L) plus the float32
 near-field correction, float-float true residuals, u = K~ sigma in float-float
-and the mean projection.  --workload ellipsoid_9600 times the 9,600-node
+and the mean projection.  The float-float sums read the operator's float-float
+matrices, stored in HBM once per operator before the timed region (their build
+time and size are reported; --no-store-ff evaluates the pairs instead, and the
+line also reports that step's time).  --workload ellipsoid_9600 times the 9,600-node
 ellipsoid with direct float32 applies instead.  The near field is built once
 per surface, before the timed region (its time is reported).  Inputs are
 resident in HBM; L2 is flushed between steps.
@@ -47,7 +50,13 @@ TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 625408,
                  ("k_sym_ff_R", "torus_98304"): 567848192,
                  ("k_sym_ff_K", "torus_98304"): 548400640,
                  ("k_tc_gemm", "torus_98304"): 446360320,
-                 ("k_fmm_p2p", "torus_98304"): 6932992}
+                 ("k_fmm_p2p", "torus_98304"): 6932992,
+                 ("k_ffmat_gemv", "ellipsoid_9600"): 741096192,
+                 ("k_ffmat_symK_gemv", "ellipsoid_9600"): 377966848,
+                 # captured on the 9,600-node ellipsoid, scaled by entries (row layout) and
+                 # tiles (symmetric layout): traffic per entry does not depend on N
+                 ("k_ffmat_gemv", "torus_98304"): 77709568062,
+                 ("k_ffmat_symK_gemv", "torus_98304"): 39162139771}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
 
@@ -330,6 +339,21 @@ def run_gpu(args, rank, world, local_rank):
     tune = (surf.autotune(nrhs=1, prec=prec, reps=3 if prec == "fmm" else 5)
             if not args.no_autotune else _builtin(surf))
     fmm = surf.fmm_stats() if prec == "fmm" else None
+    # float-float matrices of both smooth kernels kept in HBM (pm_surface_store_ff): the
+    # refinement residual and u = K sigma then stream them instead of evaluating pairs
+    store = None
+    if not args.no_store_ff:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        t0 = time.perf_counter()
+        try:
+            surf.store_ff("RK")
+            t_store = time.perf_counter() - t0
+            store = {"kernels": surf.stored_ff(), "build_s": round(t_store, 4),
+                     "device_bytes": int(free0 - torch.cuda.mem_get_info(dev)[0])}
+        except pm._lib.PmError as e:
+            store = {"unavailable": str(e)}
+    stored = bool(store and store.get("kernels"))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -418,12 +442,68 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_value = job_throughput(world, applies * pairs, e2e_s * 1e3)
 
+    # the same step with the float-float sums evaluated pair by pair (matrices released)
+    computed_ff = None
+    if stored:
+        surf.store_ff("")
+        for _ in range(2):
+            step()
+        n_cmp = max(3, min(args.steps, 5))
+        cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_cmp)]
+        torch.cuda.synchronize()
+        for k in range(n_cmp):
+            flush.fill_(float(k))
+            cev[k][0].record(stream)
+            step()
+            cev[k][1].record(stream)
+        torch.cuda.synchronize()
+        computed_ff = {"ms_per_step": round(sum(a.elapsed_time(b) for a, b in cev) / n_cmp, 4),
+                       "steps": n_cmp,
+                       "note": "the float-float residual and representation sums evaluated pair "
+                               "by pair (symmetric tile-pair kernels) instead of read from the "
+                               "stored matrices; untimed build excluded either way"}
+
     # rooflines of the step's kernels, per launch from the profiled pass
     nt = -(-N // 128)
     sym = N >= 256 and nt * N * 8 <= SYM_PARTIAL_CAP
     ff_name = "k_sym_ff" if sym else "k_direct_ff"
     roofs = {}
-    if acc_R_n:
+    hbm_peak = mp_peaks["hbm_gbs"]
+    ld = -(-N // 64) * 64
+    if stored and acc_R_n:
+        byt = N * ld * 8 + 8 * ld + 8 * N
+        ms = acc_R_ms / acc_R_n
+        ach = byt / (ms * 1e-3) / 1e9
+        roofs["accurate_R"] = {
+            "bound": "hbm", "kernel": "k_ffmat_gemv (stored float-float remainder matrix, "
+                                      "float-float GEMV)",
+            "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(ach / hbm_peak, 4),
+            "traffic": TRAFFIC_BYTES.get(("k_ffmat_gemv", args.workload)),
+            "algorithmic_bytes": byt, "kernel_ms": round(ms, 5),
+            "peak_basis": "HBM copy bandwidth " + mp_peaks["basis"],
+            "step_time_share": round(acc_R_ms * args.steps / prof_total_ms, 4)}
+    if stored and acc_K_n:
+        ntk = -(-N // 128)
+        sym_k = N >= 256 and ntk * N * 8 <= SYM_PARTIAL_CAP
+        mat = ntk * (ntk + 1) // 2 * 128 * 128 * 8 if sym_k else N * ld * 8
+        byt = mat + 8 * ld + 8 * N
+        ms = acc_K_ms / acc_K_n
+        ach = byt / (ms * 1e-3) / 1e9
+        roofs["accurate_K"] = {
+            "bound": "hbm",
+            "kernel": ("k_ffmat_symK_gemv (stored symmetric float-float parametrix matrix, "
+                       "upper-triangle tiles; row and column sums per tile)" if sym_k else
+                       "k_ffmat_gemv (stored float-float parametrix matrix)"),
+            "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+            "frac": round(ach / hbm_peak, 4),
+            "traffic": TRAFFIC_BYTES.get(("k_ffmat_symK_gemv" if sym_k else "k_ffmat_gemv_K",
+                                          args.workload)),
+            "algorithmic_bytes": byt, "kernel_ms": round(ms, 5),
+            "peak_basis": "HBM copy bandwidth " + mp_peaks["basis"],
+            "step_time_share": round(acc_K_ms * args.steps / prof_total_ms, 4)}
+    if acc_R_n and not stored:
         roofs["accurate_R"] = _alu_roofline(
             ff_name + "<R> (float-float remainder sum" + (", each unordered pair once)" if sym else ")"),
             FLOPS_PER_PAIR_R * pairs, acc_R_ms / acc_R_n, peak_fp32, acc_R_ms * args.steps / prof_total_ms,
@@ -431,7 +511,7 @@ def run_gpu(args, rank, world, local_rank):
             note="algorithmic flops of the float64-class sum (26 per ordered pair); float-float "
                  "arithmetic costs ~10 float32 instructions per algorithmic flop (274 per "
                  "unordered pair), so the sum is bound by FP32 instruction issue")
-    if acc_K_n:
+    if acc_K_n and not stored:
         roofs["accurate_K"] = _alu_roofline(
             ff_name + "<K> (float-float parametrix sum)", FLOPS_PER_PAIR_K * pairs,
             acc_K_ms / acc_K_n, peak_fp32, acc_K_ms * args.steps / prof_total_ms,
@@ -473,7 +553,9 @@ def run_gpu(args, rank, world, local_rank):
                  + ("Chebyshev-FMM applies (tensor-core M2L)" if prec == "fmm" else
                     "float32 direct-sum applies")
                  + " + float32 near field, float-float refinement residuals, u = K sigma in "
-                   "float-float, mean projection")
+                   "float-float"
+                 + (" (both read from the operator's stored float-float matrices)" if stored
+                    else "") + ", mean projection")
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -490,6 +572,7 @@ def run_gpu(args, rank, world, local_rank):
                    "value_definition": "equivalent smooth-sum pairs per second over the solve "
                                        "step = (Arnoldi steps + refinements + 1) * N^2 / time",
                    "near_blocks": nblk, "near_build_s": round(t_build, 3),
+                   "stored_ff_matrices": store,
                    "autotune": {"knobs": {k: v for k, v in tune["knobs"].items() if v},
                                 "apply_ms": _r(tune["best_ms"], 4),
                                 "builtin_apply_ms": _r(tune["default_ms"], 4),
@@ -497,11 +580,14 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": round(solves_per_s, 3),
+        "computed_ff_step": computed_ff,
         "actual_pairs_gpairs_per_s": round(world * actual_pairs / (ms_per_step * 1e-3) / 1e9, 3),
         "actual_pairs_definition": ("pairs evaluated pair by pair per step: FMM applies count "
                                     "their adjacent-leaf (P2P) pairs, accurate (float-float) "
-                                    "applies N^2; the far field is not pairs" if fmm else
-                                    "every apply evaluates N^2 pairs"),
+                                    "applies N^2 (each pair's stored entry read once, or its "
+                                    "kernel evaluated); the far field is not pairs" if fmm else
+                                    "every apply evaluates (or reads the stored entry of) "
+                                    "N^2 pairs"),
         "solve": {"iterations": it, "refinements": rf, "applies_per_solve": applies,
                   "residual_max": max(i.residual for i in infos),
                   "rel_err_vs_fp64_solve": err_vs_fp64, "fp64_solve_s": round(t_fp64, 3),
@@ -794,6 +880,31 @@ def run_triangles(args, dev):
         s.close()
     ctx.close()
     return out
+
+
+def run_micro_ffmat(args):
+    """The stored float-float matrices of one surface (default the 9,600-node ellipsoid:
+    a 737 MB remainder matrix and a 369 MB symmetric parametrix matrix, both larger than
+    L2): the store, then one float-float remainder and one parametrix apply, the
+    launches an ncu capture of k_ffmat_gemv / k_ffmat_symK_gemv looks at."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import make_workload
+    name = args.workload if args.workload != "torus_98304" else "ellipsoid_9600"
+    wl = make_workload(name)
+    ctx = pm.Context(0)
+    s = pm.Surface.from_fixture(ctx, wl.surface)
+    s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+    s.store_ff("RK")
+    sig = torch.from_numpy(np.random.default_rng(2).standard_normal(wl.N) + 1.0).to("cuda:0")
+    y = s.apply_R(sig, "ff")
+    z = s.apply_K(sig, "ff")
+    torch.cuda.synchronize()
+    print(json.dumps({"micro": "ffmat", "workload": name, "N": wl.N,
+                      "finite": bool(torch.isfinite(y).all() and torch.isfinite(z).all())}))
+    s.close()
+    ctx.close()
 
 
 def run_micro_tri(args):
@@ -1177,6 +1288,9 @@ def main():
     ap.add_argument("--oracle-leg", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-store-ff", action="store_true",
+                    help="evaluate the float-float sums pair by pair instead of storing the "
+                         "operator's float-float matrices in HBM")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for profiler runs, whose timings "
                          "would mislead the autotuner)")
@@ -1192,7 +1306,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
-    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz", "tri"], default=None,
+    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz", "tri", "ffmat"], default=None,
                     help="time one kernel alone instead of the solve step (profiling aid)")
     ap.add_argument("--micro-c", type=float, default=-4.0,
                     help="c of --micro helmholtz (1,536-node unit sphere, a = 1)")
@@ -1206,6 +1320,9 @@ def main():
         return
     if args.micro == "tri":
         run_micro_tri(args)
+        return
+    if args.micro == "ffmat":
+        run_micro_ffmat(args)
         return
     if args.oracle_leg:
         P = host_cores()

@@ -219,6 +219,31 @@ pm_status pm_ctx_info(const pm_ctx* ctx, char* name, int len, int* num_sms);
  */
 pm_status pm_surface_fmm_stats(pm_surface* s, double stats[4]);
 
+/*
+ * Stored float-float smooth-sum matrices (Sec. 6.1, the smooth part of the
+ * Nystrom discretisation of eq. explicit_remainder and eq. diff_param).  which:
+ * bit 0 = the remainder kernel, bit 1 = the parametrix kernel, 0 = release both.
+ * Each stored kernel is evaluated once at every ordered pair (i, j != i) in the
+ * float-float arithmetic of the PM_PREC_FF sums and kept in device memory as
+ * (hi, lo) float pairs, N x ld entries (ld = N rounded up to 64), 8 bytes each:
+ * 77 GB per kernel at N = 98,304.  Every later PM_PREC_FF apply of a stored
+ * kernel (solves' refinement residuals and representation included) reads the
+ * matrix instead of evaluating the pairs; results agree with the unstored sums
+ * to float-float rounding.  pm_surface_set_coeff re-evaluates the stored
+ * remainder matrix (it carries the coefficient); the parametrix matrix depends
+ * on the geometry only.  Clones do not inherit stored matrices; a c != 0
+ * coefficient (pm_surface_set_coeff_c) releases them; pm_surface_destroy frees them.
+ * Requires pm_surface_set_coeff.  Refused with PM_ERR_OOM, storing nothing, when
+ * the matrices would not fit in the free device memory less a margin of
+ * max(1 GiB, 2 % of the device); any matrix stored before the call is released
+ * first.  Synchronises the device; no other call may use the surface meanwhile.
+ * PM_ERR_INVALID_ARG for a NULL surface, which outside 0..3 or a c != 0 surface.
+ */
+pm_status pm_surface_store_ff(pm_surface* s, int which);
+
+/* The kernels currently stored by pm_surface_store_ff (same bits; 0 for NULL). */
+int pm_surface_stored_ff(const pm_surface* s);
+
 /* Number of nodes N and near-field blocks (target, near patch) of a surface. */
 pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);
 

@@ -212,6 +212,22 @@ class Surface:
         check(_lib.lib().pm_surface_set_coeff(self.handle, ptr(a), ptr(g)),
               "pm_surface_set_coeff")
 
+    def store_ff(self, which: str = "RK"):
+        """pm_surface_store_ff: keep the float-float matrices of the remainder ("R") and/or
+        parametrix ("K") smooth sums in device memory, so that every "ff" apply of them
+        (solves' residuals and representation included) streams the matrix; "" releases
+        both.  8 bytes per entry: N x ceil(N / 64) * 64 entries for R; for K the upper
+        triangle of 128 x 128 tiles where the surface uses the symmetric sums, else N x ld."""
+        bits = (1 if "R" in which else 0) | (2 if "K" in which else 0)
+        if set(which) - {"R", "K"}:
+            raise ValueError(f"which must name R and/or K, got {which!r}")
+        check(_lib.lib().pm_surface_store_ff(self.handle, bits), "pm_surface_store_ff")
+
+    def stored_ff(self) -> str:
+        """The kernels whose float-float matrices are stored ("", "R", "K" or "RK")."""
+        b = _lib.lib().pm_surface_stored_ff(self.handle)
+        return ("R" if b & 1 else "") + ("K" if b & 2 else "")
+
     def check(self):
         """pm_surface_check: the near-field indices and stored data are consistent and finite."""
         check(_lib.lib().pm_surface_check(self.handle), "pm_surface_check")

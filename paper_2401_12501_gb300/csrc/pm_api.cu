@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 
@@ -283,6 +284,13 @@ static void share_buffers(pm_surface* s) {
     s->shared = sb;
 }
 
+size_t pm_free_hbm_bytes() {
+    if (const char* fake = std::getenv("PM_FAKE_HBM_BYTES")) return (size_t)std::strtoull(fake, nullptr, 10);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+    return fr;
+}
+
 static void free_surface(pm_surface* s) {
     if (!s) return;
     if (s->ctx) cudaSetDevice(s->ctx->device);
@@ -298,6 +306,7 @@ static void free_surface(pm_surface* s) {
     pm_batch_free(s);
     pm_batch_solve_free(s);
     pm_helm_free(s);
+    pm_ffmat_free(s);
     pm_dfree(s->x); pm_dfree(s->n); pm_dfree(s->H); pm_dfree(s->w); pm_dfree(s->J);
     pm_dfree(s->npatch_n); pm_dfree(s->centroid); pm_dfree(s->radius);
     pm_dfree(s->row_ptr); pm_dfree(s->blk_patch); pm_dfree(s->blk_row);
@@ -625,6 +634,7 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
     PM_TRY(pm_pack_targets(s, st));
     PM_TRY(pm_pack_ff(s, st));
     PM_TRY(pm_near_combine_coeff(s, st));
+    PM_TRY(pm_ffmat_refresh(s, st));
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     s->has_coeff = true;
     s->has_c = 0;
@@ -676,7 +686,9 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
     prepped = prepped && (prec == PM_PREC_FP32 || prec == PM_PREC_FMM);
     if ((smooth || near) && !prepped) {
         PhaseTimer t(s, PM_PHASE_PREP, st);
-        if (prec == PM_PREC_FF) {
+        if (prec == PM_PREC_FF && pm_ffmat_has(s, kernel_K)) {
+            PM_TRY(pm_ffmat_prep(s, sigma, st));
+        } else if (prec == PM_PREC_FF) {
             PM_TRY(pm_prep_ff(s, sigma, st));
         } else {
             PM_TRY(pm_prep_sources(s, sigma, prec == PM_PREC_FMM ? PM_PREC_FP32 : prec, st));
@@ -687,7 +699,9 @@ pm_status pm_apply_dev(pm_surface* s, int kernel_K, int smooth, int near, const 
                             ? (kernel_K ? PM_PHASE_DIRECT64_K : PM_PHASE_DIRECT64)
                             : (kernel_K ? PM_PHASE_DIRECT_K : PM_PHASE_DIRECT_R), st);
         const int nt = pm_sym_tiles(s);
-        if (prec == PM_PREC_FF && nt > 0) {
+        if (prec == PM_PREC_FF && pm_ffmat_has(s, kernel_K)) {
+            PM_TRY(pm_ffmat_apply(s, kernel_K, &nsplit, st));
+        } else if (prec == PM_PREC_FF && nt > 0) {
             nsplit = nt;
             PM_TRY(pm_sym_ff(s, kernel_K, st));
         } else if (prec == PM_PREC_FF) {

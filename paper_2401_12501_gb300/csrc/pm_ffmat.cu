@@ -1,0 +1,487 @@
+// Stored float-float smooth-sum matrices: the accurate applies as a streaming GEMV.
+//
+// The refinement residual f - A sigma and the representation u = K~ sigma need the
+// smooth sums y_i = sum_{j != i} s_j G(x_i, x_j) to float64-class accuracy, with
+// s_j = w_j sigma_j / a_j (Sec. 6.1; the smooth rule of the Nystrom discretisation).
+// Evaluated pair by pair in float-float (pm_symsum.cu) they cost ~140 FP32
+// instructions per ordered pair of the remainder and ~65 of the parametrix, issue-
+// bound.  Their matrices G_ij depend on the operator but not on sigma, so when HBM
+// holds them they are evaluated once, in the same float-float arithmetic, and stored
+// as (hi, lo) float pairs: 8 bytes per entry, N x ld entries per kernel (ld = N
+// rounded up to 64).  Every later float-float apply is then one pass over the
+// matrix, bound by HBM bandwidth: 8 bytes and ~11 FP32 instructions per entry.
+// The paper's method stores its operators too (compressed, in its interpolative
+// FMM); here the stored form is dense and exact to float-float rounding.
+//
+// Entries: remainder G_ij = (n'_i . r)^2 / r^4 + (m_i . r) / r^2 with r = x_i - x_j
+// (eq. explicit_remainder, c = 0, the target's coefficient factors n' and m of the
+// packed float-float targets); parametrix G_ij = log(r^2) / (4 pi) (eq. diff_param,
+// 1/a_j in s_j).  G_ii = 0 and the padding columns j >= N are 0.  The remainder
+// matrix depends on the coefficient a and is re-evaluated by set_coeff; the
+// parametrix matrix depends on the geometry only.
+//
+// The parametrix matrix is symmetric.  On surfaces that use the symmetric tile-pair
+// sums (pm_symsum.cu) only its upper triangle of 128 x 128 tiles is stored, half
+// the bytes, and one pass over a tile (a, b), a < b, gives both the row sums of tile
+// a against tile b's strengths and the column sums of tile b against tile a's, with
+// the same block schedule and partial-slice layout as those sums: a block's four
+// warps take 32 rows each; at step k of a 32-column sub-tile lane l reads the entry of
+// its row and column (l + k) mod 32, adds it times that column's strength to its row
+// sum and times its own row's strength to the column sum it carries, and the column
+// sums rotate one lane per step.  Entries are stored in the order the lanes read
+// them (two steps per 16-byte load, a warp's loads contiguous).
+//
+// GEMV: a block takes 32 rows (4 per warp) and one column segment; lane l of a warp
+// takes column pairs l, l + 32, ... of the segment, loads 16 bytes (two entries) of
+// each of its 4 rows and one 16-byte pair of strengths, and accumulates each row in
+// float-float (TwoProduct by FMA, TwoSum on the high words, the error terms summed
+// in the low word).  The warp's 32 partial sums of a row are added in a fixed
+// butterfly order; segment k writes partial slice k, which the float64 near-field
+// kernel adds with the corrections.  Results are bit-reproducible.
+#include "pm_ff.cuh"
+#include "pm_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+using namespace pmff;
+
+constexpr int kBuildRows = 8;        // rows per build block, one per warp
+constexpr int kBuildStage = 512;     // source columns staged in shared memory per step
+constexpr int kGemvWarps = 8;
+constexpr int kGemvRowsPerWarp = 4;
+constexpr int kGemvRows = kGemvWarps * kGemvRowsPerWarp;
+constexpr int kST = 128;             // symmetric layout: tile side (= the symmetric sums' tile)
+constexpr int kSTF4 = kST * kST / 2; // float4 (two entries) per tile
+
+// --------------------------------------------------------------------- build
+// Remainder (KERNEL_K = false): src = src_ff (plain float-float coordinates),
+// tg = tgt_ff (x, n', m pairs of the target).  Parametrix (KERNEL_K = true):
+// src = src_kg (grid-split coordinates; the target reads its own entry).
+// The per-pair arithmetic is that of the float-float sums (pm_ffsum.cu) without
+// the strength factor.
+template <bool KERNEL_K>
+__global__ void __launch_bounds__(kBuildRows * 32)
+k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
+              const float4* __restrict__ log_tab, int N, int ld, float2* __restrict__ M) {
+    __shared__ float4 sA[kBuildStage], sB[kBuildStage];
+    __shared__ float4 stab[KERNEL_K ? kLogTable : 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (KERNEL_K)
+        for (int k = tid; k < kLogTable; k += blockDim.x) stab[k] = log_tab[k];
+    const int i = blockIdx.x * kBuildRows + warp;
+    const bool row_ok = i < N;
+    const int ii = row_ok ? i : 0;
+    ff X[3], NP[3], MM[3];
+    if (KERNEL_K) {
+        const float4 a = src[2 * (size_t)ii], b = src[2 * (size_t)ii + 1];
+        X[0] = ff{a.x, b.x}; X[1] = ff{a.y, b.y}; X[2] = ff{a.z, b.z};
+    } else {
+        float4 v[6];
+        for (int q = 0; q < 6; ++q) v[q] = tg[6 * (size_t)ii + q];
+        X[0] = ff{v[0].x, v[1].x}; X[1] = ff{v[0].y, v[1].y}; X[2] = ff{v[0].z, v[1].z};
+        NP[0] = ff{v[2].x, v[3].x}; NP[1] = ff{v[2].y, v[3].y}; NP[2] = ff{v[2].z, v[3].z};
+        MM[0] = ff{v[4].x, v[5].x}; MM[1] = ff{v[4].y, v[5].y}; MM[2] = ff{v[4].z, v[5].z};
+    }
+    const ff scale = KERNEL_K ? ff_from_double(1.0 / (4.0 * M_PI)) : ff{1.f, 0.f};
+    float2* row = M + (size_t)ii * ld;
+    for (int base = 0; base < ld; base += kBuildStage) {
+        __syncthreads();
+        for (int k = tid; k < kBuildStage; k += blockDim.x) {
+            const int j = base + k;
+            if (j < N) {
+                sA[k] = src[2 * (size_t)j];
+                sB[k] = src[2 * (size_t)j + 1];
+            } else {
+                sA[k] = sB[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (!row_ok) continue;
+        const int kend = min(kBuildStage, ld - base);
+        for (int k = lane; k < kend; k += 32) {
+            const int j = base + k;
+            ff e{0.f, 0.f};
+            if (j < N && j != i) {
+                const float4 A = sA[k], B = sB[k];
+                const ff dx = KERNEL_K ? ff_grid_sub(X[0], A.x, B.x) : ff_sub(X[0], ff{A.x, B.x});
+                const ff dy = KERNEL_K ? ff_grid_sub(X[1], A.y, B.y) : ff_sub(X[1], ff{A.y, B.y});
+                const ff dz = KERNEL_K ? ff_grid_sub(X[2], A.z, B.z) : ff_sub(X[2], ff{A.z, B.z});
+                const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
+                if (KERNEL_K) {
+                    e = ff_mul(ff_norm(ff_log_lazy(r2, stab)), scale);
+                } else {
+                    const ff inv = ff_rcp_lazy(r2);
+                    const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
+                                                                  ff_mul_lazy(NP[1], dy)),
+                                                      ff_mul_lazy(NP[2], dz)));
+                    const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
+                                              ff_mul_lazy(MM[2], dz));
+                    const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, ff_mul_lazy(nr, inv)), mr));
+                    e = ff_mul(inv, inner);
+                }
+            }
+            __stcs(row + j, make_float2(e.h, e.l));
+        }
+    }
+}
+
+// Symmetric parametrix layout, block per tile pair (a, b) of pm_tile_pair: warp w,
+// sub-tile c, step k = 2 kk + h, lane l hold the entry of row a 128 + 32 w + l and
+// column b 128 + 32 c + ((l + k) mod 32) at float2 offset
+// ((((w 4 + c) 16 + kk) 32 + l) 2 + h) of the tile.
+__global__ void __launch_bounds__(kST)
+k_ffmat_symK_build(const float4* __restrict__ src, const float4* __restrict__ log_tab, int N,
+                   int nt, float4* __restrict__ T) {
+    __shared__ float4 sA[kST], sB[kST];
+    __shared__ float4 stab[kLogTable];
+    int a, b;
+    pm_tile_pair(blockIdx.x, nt, a, b);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int k = tid; k < kLogTable; k += kST) stab[k] = log_tab[k];
+    const int i = a * kST + tid, j = b * kST + tid;
+    if (j < N) {
+        sA[tid] = src[2 * (size_t)j];
+        sB[tid] = src[2 * (size_t)j + 1];
+    } else {
+        sA[tid] = sB[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    ff X[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    if (i < N) {
+        const float4 p0 = src[2 * (size_t)i], p1 = src[2 * (size_t)i + 1];
+        X[0] = ff{p0.x, p1.x}; X[1] = ff{p0.y, p1.y}; X[2] = ff{p0.z, p1.z};
+    }
+    __syncthreads();
+    const ff scale = ff_from_double(1.0 / (4.0 * M_PI));
+    float4* out = T + (size_t)blockIdx.x * kSTF4 + (size_t)w * (4 * 16 * 32) + lane;
+    for (int c = 0; c < 4; ++c) {
+        for (int kk = 0; kk < 16; ++kk) {
+            float v[4];
+            for (int h = 0; h < 2; ++h) {
+                const int q = c * 32 + ((lane + 2 * kk + h) & 31);
+                const int jj = b * kST + q;
+                ff e{0.f, 0.f};
+                if (i < N && jj < N && jj != i) {
+                    const float4 A = sA[q], B = sB[q];
+                    const ff dx = ff_grid_sub(X[0], A.x, B.x);
+                    const ff dy = ff_grid_sub(X[1], A.y, B.y);
+                    const ff dz = ff_grid_sub(X[2], A.z, B.z);
+                    const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)),
+                                              ff_sqr_lazy(dz));
+                    e = ff_mul(ff_norm(ff_log_lazy(r2, stab)), scale);
+                }
+                v[2 * h] = e.h;
+                v[2 * h + 1] = e.l;
+            }
+            __stcs(out + (c * 16 + kk) * 32, make_float4(v[0], v[1], v[2], v[3]));
+        }
+    }
+}
+
+// s_j = w_j sigma_j / a_j in float-float, [ld] (the padding entries stay zero)
+__global__ void k_ffmat_prep(const double* __restrict__ sigma, const double* __restrict__ wa,
+                             float2* __restrict__ sv, int N, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const ff s = ff_from_double(wa[j] * sigma[j]);
+    sv[j] = make_float2(s.h, s.l);
+}
+
+// ---------------------------------------------------------------------- GEMV
+// (S, E) += (mh + ml)(sh + sl): TwoProduct of the high words by FMA, the cross
+// terms into its error, TwoSum of the high words, every error term into E.
+__device__ __forceinline__ void ff_mac(float& S, float& E, float mh, float ml, float sh, float sl) {
+    const float p = mh * sh;
+    float e = fmaf(mh, sh, -p);
+    e = fmaf(mh, sl, e);
+    e = fmaf(ml, sh, e);
+    const float t = S + p;
+    const float bp = t - S;
+    E += ((S - (t - bp)) + (p - bp)) + e;
+    S = t;
+}
+
+__global__ void __launch_bounds__(kGemvWarps * 32)
+k_ffmat_gemv(const float4* __restrict__ M, long long ld2, const float4* __restrict__ sv, int N,
+             int cs, int ld, float2* __restrict__ partial, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = (blockIdx.x * kGemvWarps + warp) * kGemvRowsPerWarp;
+    if (r0 >= N) return;                                  // whole warp
+    const int nr = min(kGemvRowsPerWarp, N - r0);
+    const int q0 = (blockIdx.y * cs) >> 1, q1 = min(blockIdx.y * cs + cs, ld) >> 1;   // column pairs
+    const float4* Mr[kGemvRowsPerWarp];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) Mr[r] = M + (size_t)(r0 + min(r, nr - 1)) * ld2;
+    float S[kGemvRowsPerWarp], E[kGemvRowsPerWarp];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) S[r] = E[r] = 0.f;
+#pragma unroll 2
+    for (int q = q0 + lane; q < q1; q += 32) {
+        const float4 s = __ldg(sv + q);
+        float4 m[kGemvRowsPerWarp];
+#pragma unroll
+        for (int r = 0; r < kGemvRowsPerWarp; ++r) m[r] = __ldcs(Mr[r] + q);
+#pragma unroll
+        for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+            ff_mac(S[r], E[r], m[r].x, m[r].y, s.x, s.y);
+            ff_mac(S[r], E[r], m[r].z, m[r].w, s.z, s.w);
+        }
+    }
+    // butterfly over the lanes in float-float: every lane ends with the row sum
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float S2 = __shfl_xor_sync(0xffffffffu, S[r], o);
+            const float E2 = __shfl_xor_sync(0xffffffffu, E[r], o);
+            float t, e;
+            two_sum(S[r], S2, t, e);
+            E[r] = (E[r] + E2) + e;
+            S[r] = t;
+        }
+    }
+    float2* out = partial + (size_t)blockIdx.y * N + r0;
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r)
+        if (lane == r && r < nr) {
+            const ff v = ff_norm(ff{S[r], E[r]});
+            out[r] = make_float2(v.h, v.l);
+        }
+}
+
+// Symmetric parametrix GEMV over the stored upper-triangle tiles (layout above):
+// block (a, b) writes the row sums of tile a into partial slice b and, for a < b,
+// the column sums of tile b into slice a (the four warps' values added in warp
+// order), so every (slice, row) is written once, as by the symmetric sums.
+__global__ void __launch_bounds__(kST, 8)
+k_ffmat_symK_gemv(const float4* __restrict__ T, const float2* __restrict__ sv, int N, int nt,
+                  float2* __restrict__ partial, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ float2 ssb[kST];
+    __shared__ float2 csh[4][kST];
+    int a, b;
+    pm_tile_pair(blockIdx.x, nt, a, b);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int i = a * kST + tid, j = b * kST + tid;
+    ssb[tid] = j < N ? sv[j] : make_float2(0.f, 0.f);
+    const float2 si = i < N ? sv[i] : make_float2(0.f, 0.f);
+    __syncthreads();
+    const bool diag = (a == b);
+    const float4* tile = T + (size_t)blockIdx.x * kSTF4 + (size_t)w * (4 * 16 * 32) + lane;
+    const int nxt = (lane + 1) & 31;
+    float S = 0.f, E = 0.f;
+    float cS[4], cE[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float aS = 0.f, aE = 0.f;                  // column sum of the source evaluated next
+#pragma unroll 8
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 m = __ldcs(tile + (c * 16 + kk) * 32);
+            const float2 s0 = ssb[c * 32 + ((lane + 2 * kk) & 31)];
+            const float2 s1 = ssb[c * 32 + ((lane + 2 * kk + 1) & 31)];
+            ff_mac(S, E, m.x, m.y, s0.x, s0.y);
+            ff_mac(S, E, m.z, m.w, s1.x, s1.y);
+            if (!diag) {
+                ff_mac(aS, aE, m.x, m.y, si.x, si.y);
+                aS = __shfl_sync(0xffffffffu, aS, nxt);
+                aE = __shfl_sync(0xffffffffu, aE, nxt);
+                ff_mac(aS, aE, m.z, m.w, si.x, si.y);
+                aS = __shfl_sync(0xffffffffu, aS, nxt);
+                aE = __shfl_sync(0xffffffffu, aE, nxt);
+            }
+        }
+        cS[c] = aS;
+        cE[c] = aE;
+    }
+    if (i < N) {
+        const ff v = ff_norm(ff{S, E});
+        partial[(size_t)b * N + i] = make_float2(v.h, v.l);
+    }
+    if (diag) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) csh[w][c * 32 + lane] = make_float2(cS[c], cE[c]);
+    __syncthreads();
+    if (j < N) {
+        float t = csh[0][tid].x, e = csh[0][tid].y;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            float u, d;
+            two_sum(t, csh[q][tid].x, u, d);
+            e = (e + csh[q][tid].y) + d;
+            t = u;
+        }
+        const ff v = ff_norm(ff{t, e});
+        partial[(size_t)a * N + j] = make_float2(v.h, v.l);
+    }
+}
+
+// Column segments of the GEMV: about four waves of blocks, at most the surface's
+// partial slices, segments a multiple of 64 columns.
+void gemv_shape(const pm_surface* s, int* nseg, int* cs) {
+    const int rowblocks = pm_ceil_div(s->N, kGemvRows);
+    const int want = 16 * s->ctx->num_sms;
+    const int ld = (int)s->ffm_ld;
+    int S = std::max(1, std::min(pm_ceil_div(want, rowblocks), std::min(s->max_split, ld / 64)));
+    int c = pm_ceil_div(pm_ceil_div(ld, S), 64) * 64;
+    *cs = c;
+    *nseg = pm_ceil_div(ld, c);
+}
+
+pm_status build_one(pm_surface* s, int which_K, cudaStream_t st) {
+    float2* M = which_K ? s->ffm_K : s->ffm_R;
+    const int ld = (int)s->ffm_ld;
+    if (which_K && s->ffm_symK) {
+        const int nt = s->ffm_symK;
+        k_ffmat_symK_build<<<nt * (nt + 1) / 2, kST, 0, st>>>(s->src_kg, s->log_tab, s->N, nt,
+                                                               reinterpret_cast<float4*>(M));
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
+    const int blocks = pm_ceil_div(s->N, kBuildRows);
+    if (which_K)
+        k_ffmat_build<true><<<blocks, kBuildRows * 32, 0, st>>>(s->src_kg, s->tgt_ff, s->log_tab,
+                                                                s->N, ld, M);
+    else
+        k_ffmat_build<false><<<blocks, kBuildRows * 32, 0, st>>>(s->src_ff, s->tgt_ff, s->log_tab,
+                                                                 s->N, ld, M);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+}  // namespace
+
+// entries of the stored parametrix matrix: the symmetric tile layout when the
+// surface uses the symmetric sums, else N x ld
+static size_t k_entries(const pm_surface* s, int* nt_sym) {
+    const int nt = pm_sym_tiles(s);
+    *nt_sym = nt;
+    if (nt > 0) return (size_t)nt * (nt + 1) / 2 * kST * kST;
+    return (size_t)s->N * (size_t)(pm_ceil_div(s->N, 64) * 64);
+}
+
+size_t pm_ffmat_bytes(const pm_surface* s, int which) {
+    const size_t ld = (size_t)pm_ceil_div(s->N, 64) * 64;
+    int nt = 0;
+    size_t b = ld * sizeof(float2);
+    if (which & 1) b += (size_t)s->N * ld * sizeof(float2);
+    if (which & 2) b += k_entries(s, &nt) * sizeof(float2);
+    return b;
+}
+
+void pm_ffmat_free(pm_surface* s) {
+    pm_dfree(s->ffm_R);
+    pm_dfree(s->ffm_K);
+    pm_dfree(s->ffm_s);
+    s->ffm_ld = 0;
+    s->ffm_symK = 0;
+}
+
+bool pm_ffmat_has(const pm_surface* s, int which_K) {
+    return which_K ? s->ffm_K != nullptr : s->ffm_R != nullptr;
+}
+
+// Re-evaluates the stored remainder matrix after a coefficient change (the
+// packed float-float targets hold the new n' and m).
+pm_status pm_ffmat_refresh(pm_surface* s, cudaStream_t st) {
+    if (s->ffm_R) PM_TRY(build_one(s, 0, st));
+    return PM_OK;
+}
+
+pm_status pm_ffmat_prep(pm_surface* s, const double* sigma, cudaStream_t st) {
+    k_ffmat_prep<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(sigma, s->wa, s->ffm_s, s->N,
+                                                         s->skip_flag);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_ffmat_apply(pm_surface* s, int which_K, int* nsplit, cudaStream_t st) {
+    if (which_K && s->ffm_symK) {
+        const int nt = s->ffm_symK;
+        k_ffmat_symK_gemv<<<nt * (nt + 1) / 2, kST, 0, st>>>(
+            reinterpret_cast<const float4*>(s->ffm_K), s->ffm_s, s->N, nt,
+            reinterpret_cast<float2*>(s->partial), s->skip_flag);
+        PM_CUDA_TRY(cudaGetLastError());
+        *nsplit = nt;
+        return PM_OK;
+    }
+    int nseg = 0, cs = 0;
+    gemv_shape(s, &nseg, &cs);
+    const float2* M = which_K ? s->ffm_K : s->ffm_R;
+    dim3 grid(pm_ceil_div(s->N, kGemvRows), nseg);
+    k_ffmat_gemv<<<grid, kGemvWarps * 32, 0, st>>>(reinterpret_cast<const float4*>(M),
+                                                   s->ffm_ld / 2,
+                                                   reinterpret_cast<const float4*>(s->ffm_s), s->N,
+                                                   cs, (int)s->ffm_ld,
+                                                   reinterpret_cast<float2*>(s->partial), s->skip_flag);
+    PM_CUDA_TRY(cudaGetLastError());
+    *nsplit = nseg;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_surface_store_ff(pm_surface* s, int which) {
+    if (!s || which < 0 || which > 3) {
+        pm_set_error("pm_surface_store_ff: NULL surface or which outside 0..3");
+        return PM_ERR_INVALID_ARG;
+    }
+    PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    if (which == 0) {
+        pm_ffmat_free(s);
+        s->graph_epoch++;
+        return PM_OK;
+    }
+    if (!s->has_coeff) {
+        pm_set_error("pm_surface_store_ff: call pm_surface_set_coeff first");
+        return PM_ERR_NO_COEFF;
+    }
+    if (s->has_c) {
+        pm_set_error("pm_surface_store_ff: the surface has c != 0 (its sums are complex float64)");
+        return PM_ERR_INVALID_ARG;
+    }
+    pm_ffmat_free(s);
+    s->graph_epoch++;
+    const size_t need = pm_ffmat_bytes(s, which);
+    const size_t fr = pm_free_hbm_bytes();
+    size_t total = 0, fr_real = 0;
+    cudaMemGetInfo(&fr_real, &total);
+    const size_t margin = std::max<size_t>(1ull << 30, total / 50);
+    if (need + margin > fr) {
+        pm_set_error("pm_surface_store_ff: %.2f GB needed, %.2f GB free (less a %.2f GB margin)",
+                     need / 1e9, fr / 1e9, margin / 1e9);
+        return PM_ERR_OOM;
+    }
+    s->ffm_ld = (long long)pm_ceil_div(s->N, 64) * 64;
+    const size_t nent = (size_t)s->N * s->ffm_ld;
+    int nt_sym = 0;
+    const size_t nentK = k_entries(s, &nt_sym);
+    pm_status st = pm_dmalloc(&s->ffm_s, (size_t)s->ffm_ld);
+    if (st == PM_OK && (which & 1)) st = pm_dmalloc(&s->ffm_R, nent);
+    if (st == PM_OK && (which & 2)) {
+        st = pm_dmalloc(&s->ffm_K, nentK);
+        s->ffm_symK = nt_sym;
+    }
+    if (st == PM_OK && cudaMemset(s->ffm_s, 0, sizeof(float2) * s->ffm_ld) != cudaSuccess) {
+        pm_set_error("pm_surface_store_ff: cudaMemset failed");
+        st = PM_ERR_CUDA;
+    }
+    if (st == PM_OK && s->ffm_R) st = build_one(s, 0, 0);
+    if (st == PM_OK && s->ffm_K) st = build_one(s, 1, 0);
+    if (st == PM_OK) {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            pm_set_error("pm_surface_store_ff: %s", cudaGetErrorString(e));
+            st = PM_ERR_CUDA;
+        }
+    }
+    if (st != PM_OK) pm_ffmat_free(s);
+    return st;
+}
+
+extern "C" int pm_surface_stored_ff(const pm_surface* s) {
+    if (!s) return 0;
+    return (s->ffm_R ? 1 : 0) | (s->ffm_K ? 2 : 0);
+}

@@ -395,6 +395,7 @@ extern "C" pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, cons
     // leaves c = 0 surfaces exactly as pm_surface_set_coeff does
     PM_TRY(pm_surface_set_coeff(s, a, grad_a));
     if (!any) return PM_OK;
+    pm_ffmat_free(s);                          // the real float-float sums do not apply to c != 0
     std::vector<double> q(2 * (size_t)N);
     for (int k = 0; k < N; ++k) {
         q[2 * k] = c[2 * k] / a[k];

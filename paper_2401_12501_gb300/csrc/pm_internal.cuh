@@ -181,6 +181,16 @@ struct pm_surface {
     double2* cKc = nullptr;       // [nblk*pp]
     PmHelmWork* helm = nullptr;
 
+    // stored float-float smooth-sum matrices (pm_ffmat.cu, pm_surface_store_ff):
+    // [N][ffm_ld] (hi, lo) entries of the remainder and parametrix kernels, and the
+    // float-float strengths of the apply; null when not stored
+    float2* ffm_R = nullptr;
+    float2* ffm_K = nullptr;
+    float2* ffm_s = nullptr;      // [ffm_ld]
+    long long ffm_ld = 0;
+    int ffm_symK = 0;             // tiles of 128 per side when ffm_K holds the symmetric
+                                  // tile-pair layout (upper triangle only), else 0
+
     // per-phase timing (events recorded around launches while enabled)
     bool profiling = false;
     long long graph_epoch = 0;    // bumped when buffers or launch shapes captured in graphs change
@@ -246,6 +256,18 @@ pm_status pm_pack_ff(pm_surface* s, cudaStream_t st);
 pm_status pm_prep_ff(pm_surface* s, const double* sigma, cudaStream_t st);
 int pm_ff_splits(const pm_surface* s);
 pm_status pm_direct_ff(pm_surface* s, int which_K, int nsplit, cudaStream_t st);
+
+// stored float-float matrices (pm_ffmat.cu)
+size_t pm_ffmat_bytes(const pm_surface* s, int which);
+void pm_ffmat_free(pm_surface* s);
+bool pm_ffmat_has(const pm_surface* s, int which_K);
+pm_status pm_ffmat_refresh(pm_surface* s, cudaStream_t st);
+pm_status pm_ffmat_prep(pm_surface* s, const double* sigma, cudaStream_t st);
+pm_status pm_ffmat_apply(pm_surface* s, int which_K, int* nsplit, cudaStream_t st);
+
+// free device memory now (cudaMemGetInfo), or the value of the environment variable
+// PM_FAKE_HBM_BYTES when set (a host-side stand-in for a full device) (pm_api.cu)
+size_t pm_free_hbm_bytes();
 
 // Chebyshev FMM (pm_fmm.cu)
 pm_status pm_fmm_build(pm_surface* s);
@@ -324,6 +346,22 @@ constexpr double kOpRelErr = 1e-5;
 // symmetric tile-pair float-float sums (pm_symsum.cu); partial slices capped at this size
 constexpr double kSymPartialCap = 1024.0 * 1024.0 * 1024.0;
 int pm_sym_tiles(const pm_surface* s);
+
+// Tile pair (a, b), a <= b, of block p in the row-major upper triangle of the
+// nt x nt tile grid: row a holds nt - a blocks and S(a) = a nt - a (a - 1) / 2
+// blocks precede it.  The floating-point estimate is corrected by at most a
+// step or two; the loops are bounded by nt.  (Symmetric float-float sums and the
+// stored symmetric parametrix matrix.)
+__device__ __forceinline__ void pm_tile_pair(int p, int nt, int& a, int& b) {
+    const double B = 2.0 * nt + 1.0;
+    int x = (int)((B - sqrt(fmax(B * B - 8.0 * (double)p, 0.0))) * 0.5);
+    x = max(0, min(x, nt - 1));
+    auto S = [nt](int r) { return (long long)r * nt - (long long)r * (r - 1) / 2; };
+    for (int it = 0; it < nt && x > 0 && S(x) > p; ++it) --x;
+    for (int it = 0; it < nt && x + 1 < nt && S(x + 1) <= p; ++it) ++x;
+    a = x;
+    b = x + (int)(p - S(x));
+}
 pm_status pm_sym_ff(pm_surface* s, int which_K, cudaStream_t st);
 double pm_ff_grid(const pm_surface* s);
 

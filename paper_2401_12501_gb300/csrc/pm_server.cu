@@ -104,15 +104,9 @@ struct pm_server {
 
 namespace {
 
-// free device memory now (the worker thread's device is the context's).  The
-// environment variable PM_FAKE_HBM_BYTES, when set, replaces the reading (a
-// host-side stand-in for a full device, to exercise admission without using memory).
-size_t free_bytes() {
-    if (const char* fake = std::getenv("PM_FAKE_HBM_BYTES")) return (size_t)std::strtoull(fake, nullptr, 10);
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
-    return fr;
-}
+// free device memory now (the worker thread's device is the context's); the
+// environment variable PM_FAKE_HBM_BYTES, when set, replaces the reading
+size_t free_bytes() { return pm_free_hbm_bytes(); }
 
 bool can_reserve(pm_server* sv, size_t need) {
     if (sv->reserved + need > sv->budget) return sv->in_flight == 0 && need <= sv->budget;

@@ -41,21 +41,6 @@ using namespace pmff;
 constexpr int kT = 128;           // tile = block size
 constexpr int kW = kT / 32;       // warps per block
 
-// Tile pair (a, b), a <= b, of block p in the row-major upper triangle of the
-// nt x nt tile grid: row a holds nt - a blocks and S(a) = a nt - a (a - 1) / 2
-// blocks precede it.  The floating-point estimate is corrected by at most a
-// step or two; the loops are bounded by nt.
-__device__ __forceinline__ void tile_pair(int p, int nt, int& a, int& b) {
-    const double B = 2.0 * nt + 1.0;
-    int x = (int)((B - sqrt(fmax(B * B - 8.0 * (double)p, 0.0))) * 0.5);
-    x = max(0, min(x, nt - 1));
-    auto S = [nt](int r) { return (long long)r * nt - (long long)r * (r - 1) / 2; };
-    for (int it = 0; it < nt && x > 0 && S(x) > p; ++it) --x;
-    for (int it = 0; it < nt && x + 1 < nt && S(x + 1) <= p; ++it) ++x;
-    a = x;
-    b = x + (int)(p - S(x));
-}
-
 // ------------------------------------------------------------- float-float sums
 // Remainder (KERNEL_K = false): src = src_ff (float-float coordinates, strength
 // in .w), tg = tgt_ff (x, n', m pairs).  Parametrix (KERNEL_K = true): src =
@@ -160,7 +145,7 @@ k_sym_ff(const float4* __restrict__ src, const float4* __restrict__ tg,
     __shared__ float4 stab[KERNEL_K ? kLogTable : 1];
     __shared__ float2 csh[kW][kT];
     int a, b;
-    tile_pair(blockIdx.x, nt, a, b);
+    pm_tile_pair(blockIdx.x, nt, a, b);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int i = a * kT + tid;
     const int j = b * kT + tid;
