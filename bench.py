@@ -51,12 +51,13 @@ TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 625408,
                  ("k_sym_ff_K", "torus_98304"): 548400640,
                  ("k_tc_gemm", "torus_98304"): 446360320,
                  ("k_fmm_p2p", "torus_98304"): 6932992,
-                 ("k_ffmat_gemv", "ellipsoid_9600"): 741096192,
-                 ("k_ffmat_symK_gemv", "ellipsoid_9600"): 377966848,
-                 # captured on the 9,600-node ellipsoid, scaled by entries (row layout) and
-                 # tiles (symmetric layout): traffic per entry does not depend on N
-                 ("k_ffmat_gemv", "torus_98304"): 77709568062,
-                 ("k_ffmat_symK_gemv", "torus_98304"): 39162139771}
+                 # stored-matrix GEMVs: captured on the 9,600-node ellipsoid, scaled to the
+                 # torus by entries (row layout) and tiles (symmetric layout), since their
+                 # traffic per entry does not depend on N (None until captured)
+                 ("k_ffmat_gemv", "ellipsoid_9600"): 556227840,
+                 ("k_ffmat_symK_gemv", "ellipsoid_9600"): 284420096,
+                 ("k_ffmat_gemv", "torus_98304"): 58324716356,
+                 ("k_ffmat_symK_gemv", "torus_98304"): 29469514620}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
 
@@ -470,14 +471,14 @@ def run_gpu(args, rank, world, local_rank):
     ff_name = "k_sym_ff" if sym else "k_direct_ff"
     roofs = {}
     hbm_peak = mp_peaks["hbm_gbs"]
-    ld = -(-N // 64) * 64
+    ld = -(-N // 128) * 128
     if stored and acc_R_n:
-        byt = N * ld * 8 + 8 * ld + 8 * N
+        byt = N * ld * 6 + 8 * ld + 8 * N
         ms = acc_R_ms / acc_R_n
         ach = byt / (ms * 1e-3) / 1e9
         roofs["accurate_R"] = {
             "bound": "hbm", "kernel": "k_ffmat_gemv (stored float-float remainder matrix, "
-                                      "float-float GEMV)",
+                                      "6 bytes an entry, float-float GEMV)",
             "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(ach / hbm_peak, 4),
             "traffic": TRAFFIC_BYTES.get(("k_ffmat_gemv", args.workload)),
@@ -487,7 +488,7 @@ def run_gpu(args, rank, world, local_rank):
     if stored and acc_K_n:
         ntk = -(-N // 128)
         sym_k = N >= 256 and ntk * N * 8 <= SYM_PARTIAL_CAP
-        mat = ntk * (ntk + 1) // 2 * 128 * 128 * 8 if sym_k else N * ld * 8
+        mat = ntk * (ntk + 1) // 2 * 128 * 128 * 6 if sym_k else N * ld * 6
         byt = mat + 8 * ld + 8 * N
         ms = acc_K_ms / acc_K_n
         ach = byt / (ms * 1e-3) / 1e9

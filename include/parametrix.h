@@ -224,12 +224,16 @@ pm_status pm_surface_fmm_stats(pm_surface* s, double stats[4]);
  * Nystrom discretisation of eq. explicit_remainder and eq. diff_param).  which:
  * bit 0 = the remainder kernel, bit 1 = the parametrix kernel, 0 = release both.
  * Each stored kernel is evaluated once at every ordered pair (i, j != i) in the
- * float-float arithmetic of the PM_PREC_FF sums and kept in device memory as
- * (hi, lo) float pairs, N x ld entries (ld = N rounded up to 64), 8 bytes each:
- * 77 GB per kernel at N = 98,304.  Every later PM_PREC_FF apply of a stored
- * kernel (solves' refinement residuals and representation included) reads the
- * matrix instead of evaluating the pairs; results agree with the unstored sums
- * to float-float rounding.  pm_surface_set_coeff re-evaluates the stored
+ * float-float arithmetic of the PM_PREC_FF sums and kept in device memory in 6
+ * bytes: the high float and a 16-bit code of the low word, which restores the
+ * entry to within 2^-40 of its magnitude.  The remainder matrix takes N x ld
+ * entries (ld = N rounded up to 128); the parametrix matrix, which is symmetric,
+ * takes the upper triangle of 128 x 128 tiles on surfaces that use the symmetric
+ * float-float sums (opts.direct_symmetric, N >= 256), else N x ld entries: 58 GB
+ * and 29 GB at N = 98,304.  Every later PM_PREC_FF apply of a stored kernel
+ * (solves' refinement residuals and representation included) reads the matrix
+ * instead of evaluating the pairs; results agree with the unstored sums to about
+ * 2^-40 relative.  pm_surface_set_coeff re-evaluates the stored
  * remainder matrix (it carries the coefficient); the parametrix matrix depends
  * on the geometry only.  Clones do not inherit stored matrices; a c != 0
  * coefficient (pm_surface_set_coeff_c) releases them; pm_surface_destroy frees them.

@@ -216,8 +216,9 @@ class Surface:
         """pm_surface_store_ff: keep the float-float matrices of the remainder ("R") and/or
         parametrix ("K") smooth sums in device memory, so that every "ff" apply of them
         (solves' residuals and representation included) streams the matrix; "" releases
-        both.  8 bytes per entry: N x ceil(N / 64) * 64 entries for R; for K the upper
-        triangle of 128 x 128 tiles where the surface uses the symmetric sums, else N x ld."""
+        both.  6 bytes per entry (to 2^-40 relative): N x ceil(N / 128) * 128 entries for
+        R; for K the upper triangle of 128 x 128 tiles where the surface uses the symmetric
+        sums, else N x ld."""
         bits = (1 if "R" in which else 0) | (2 if "K" in which else 0)
         if set(which) - {"R", "K"}:
             raise ValueError(f"which must name R and/or K, got {which!r}")

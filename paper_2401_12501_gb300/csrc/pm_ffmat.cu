@@ -6,38 +6,44 @@
 // Evaluated pair by pair in float-float (pm_symsum.cu) they cost ~140 FP32
 // instructions per ordered pair of the remainder and ~65 of the parametrix, issue-
 // bound.  Their matrices G_ij depend on the operator but not on sigma, so when HBM
-// holds them they are evaluated once, in the same float-float arithmetic, and stored
-// as (hi, lo) float pairs: 8 bytes per entry, N x ld entries per kernel (ld = N
-// rounded up to 64).  Every later float-float apply is then one pass over the
-// matrix, bound by HBM bandwidth: 8 bytes and ~11 FP32 instructions per entry.
-// The paper's method stores its operators too (compressed, in its interpolative
-// FMM); here the stored form is dense and exact to float-float rounding.
+// holds them they are evaluated once, in the same float-float arithmetic, and kept;
+// every later float-float apply is then one pass over the matrix, bound by HBM
+// bandwidth.  The paper's method stores its operators too (compressed, in its
+// interpolative FMM); here the stored form is dense.
 //
 // Entries: remainder G_ij = (n'_i . r)^2 / r^4 + (m_i . r) / r^2 with r = x_i - x_j
 // (eq. explicit_remainder, c = 0, the target's coefficient factors n' and m of the
 // packed float-float targets); parametrix G_ij = log(r^2) / (4 pi) (eq. diff_param,
-// 1/a_j in s_j).  G_ii = 0 and the padding columns j >= N are 0.  The remainder
-// matrix depends on the coefficient a and is re-evaluated by set_coeff; the
-// parametrix matrix depends on the geometry only.
+// 1/a_j in s_j).  G_ii = 0 and padding entries are 0.  The remainder matrix depends
+// on the coefficient a and is re-evaluated by set_coeff; the parametrix matrix
+// depends on the geometry only.
 //
-// The parametrix matrix is symmetric.  On surfaces that use the symmetric tile-pair
-// sums (pm_symsum.cu) only its upper triangle of 128 x 128 tiles is stored, half
-// the bytes, and one pass over a tile (a, b), a < b, gives both the row sums of tile
-// a against tile b's strengths and the column sums of tile b against tile a's, with
-// the same block schedule and partial-slice layout as those sums: a block's four
-// warps take 32 rows each; at step k of a 32-column sub-tile lane l reads the entry of
-// its row and column (l + k) mod 32, adds it times that column's strength to its row
-// sum and times its own row's strength to the column sum it carries, and the column
-// sums rotate one lane per step.  Entries are stored in the order the lanes read
-// them (two steps per 16-byte load, a warp's loads contiguous).
+// Entry format, 6 bytes: the float-float value h + l (|l| <= ulp(h) / 2 <= 2^-24 |h|)
+// as the float h and the 16-bit integer q = round(l / (|h| 2^-39)), |q| <= 2^15 - 1,
+// so that h + q |h| 2^-39 is the value to within 2^-40 |h| (relative 9.1e-13 per
+// entry, against ~2^-46 of the float-float evaluation).  A matrix is two planes, the
+// floats and the 16-bit words, 4 + 2 bytes an entry instead of the 8 of a float pair.
 //
-// GEMV: a block takes 32 rows (4 per warp) and one column segment; lane l of a warp
-// takes column pairs l, l + 32, ... of the segment, loads 16 bytes (two entries) of
-// each of its 4 rows and one 16-byte pair of strengths, and accumulates each row in
-// float-float (TwoProduct by FMA, TwoSum on the high words, the error terms summed
-// in the low word).  The warp's 32 partial sums of a row are added in a fixed
-// butterfly order; segment k writes partial slice k, which the float64 near-field
-// kernel adds with the corrections.  Results are bit-reproducible.
+// Row layout (the remainder; the parametrix where the symmetric layout is not used):
+// [N][ld] per plane, ld = N rounded up to 128.  GEMV: a block takes 32 rows (4 per
+// warp) and one column segment; lane l takes column quads l, l + 32, ... of the
+// segment, loads 16 + 8 bytes (four entries) of each of its 4 rows and the four
+// columns' float-float strengths, and accumulates each row in float-float (TwoProduct
+// by FMA, TwoSum on the high words, the error terms summed in the low word).  The
+// warp's 32 partial sums of a row are added in a fixed butterfly order; segment k
+// writes partial slice k, which the float64 near-field kernel adds with the
+// corrections.  Results are bit-reproducible.
+//
+// Symmetric layout (the parametrix on surfaces that use the symmetric tile-pair sums,
+// pm_symsum.cu): only the upper triangle of 128 x 128 tiles is stored, half the
+// bytes, and one pass over a tile (a, b), a < b, gives both the row sums of tile a
+// against tile b's strengths and the column sums of tile b against tile a's, with the
+// same block schedule and partial-slice layout as those sums: a block's four warps
+// take 32 rows each; at step k of a 32-column sub-tile lane l reads the entry of its
+// row and column (l + k) mod 32, adds it times that column's strength to its row sum
+// and times its own row's strength to the column sum it carries, and the column sums
+// rotate one lane per step.  Entries are stored in the order the lanes read them (four
+// steps per load, a warp's loads contiguous).
 #include "pm_ff.cuh"
 #include "pm_internal.cuh"
 
@@ -53,8 +59,34 @@ constexpr int kBuildStage = 512;     // source columns staged in shared memory p
 constexpr int kGemvWarps = 8;
 constexpr int kGemvRowsPerWarp = 4;
 constexpr int kGemvRows = kGemvWarps * kGemvRowsPerWarp;
+constexpr int kLd = 128;             // row layout: ld is a multiple of this
 constexpr int kST = 128;             // symmetric layout: tile side (= the symmetric sums' tile)
-constexpr int kSTF4 = kST * kST / 2; // float4 (two entries) per tile
+constexpr size_t kTileHiBytes = (size_t)kST * kST * sizeof(float);
+constexpr size_t kTileBytes = (size_t)kST * kST * 6;
+
+// ------------------------------------------------------------------ entry format
+__device__ __forceinline__ int ff_q16(ff e) {
+    const float sc = fabsf(e.h) * 0x1p-39f;
+    const float r = sc > 0.f ? e.l / sc : 0.f;
+    return (int)fmaxf(-32767.f, fminf(32767.f, rintf(r)));
+}
+
+// the float value of a 16-bit integer through the float's significand (exact)
+__device__ __forceinline__ float q16_to_float(int q) {
+    return __int_as_float(0x4B400000 + q) - 12582912.0f;
+}
+
+// low word of the entry with high word h and packed 16-bit code q
+__device__ __forceinline__ float ff_lo(float h, int q) {
+    return q16_to_float(q) * (fabsf(h) * 0x1p-39f);
+}
+
+__device__ __forceinline__ int q_low(unsigned w) { return (int)(short)(w & 0xFFFFu); }
+__device__ __forceinline__ int q_high(unsigned w) { return (int)w >> 16; }
+
+__device__ __forceinline__ unsigned q_pack(int lo, int hi) {
+    return ((unsigned)lo & 0xFFFFu) | ((unsigned)hi << 16);
+}
 
 // --------------------------------------------------------------------- build
 // Remainder (KERNEL_K = false): src = src_ff (plain float-float coordinates),
@@ -63,9 +95,28 @@ constexpr int kSTF4 = kST * kST / 2; // float4 (two entries) per tile
 // The per-pair arithmetic is that of the float-float sums (pm_ffsum.cu) without
 // the strength factor.
 template <bool KERNEL_K>
+__device__ __forceinline__ ff pair_entry(const ff* X, const ff* NP, const ff* MM, float4 A,
+                                         float4 B, const float4* stab, ff scale) {
+    const ff dx = KERNEL_K ? ff_grid_sub(X[0], A.x, B.x) : ff_sub(X[0], ff{A.x, B.x});
+    const ff dy = KERNEL_K ? ff_grid_sub(X[1], A.y, B.y) : ff_sub(X[1], ff{A.y, B.y});
+    const ff dz = KERNEL_K ? ff_grid_sub(X[2], A.z, B.z) : ff_sub(X[2], ff{A.z, B.z});
+    const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
+    if (KERNEL_K) return ff_mul(ff_norm(ff_log_lazy(r2, stab)), scale);
+    const ff inv = ff_rcp_lazy(r2);
+    const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx), ff_mul_lazy(NP[1], dy)),
+                                      ff_mul_lazy(NP[2], dz)));
+    const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
+                              ff_mul_lazy(MM[2], dz));
+    const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, ff_mul_lazy(nr, inv)), mr));
+    return ff_mul(inv, inner);
+}
+
+// row layout: planes Mh [N][ld] (float) and Mq [N][ld] (16-bit codes)
+template <bool KERNEL_K>
 __global__ void __launch_bounds__(kBuildRows * 32)
 k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
-              const float4* __restrict__ log_tab, int N, int ld, float2* __restrict__ M) {
+              const float4* __restrict__ log_tab, int N, int ld, float* __restrict__ Mh,
+              short* __restrict__ Mq) {
     __shared__ float4 sA[kBuildStage], sB[kBuildStage];
     __shared__ float4 stab[KERNEL_K ? kLogTable : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -86,7 +137,8 @@ k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
         MM[0] = ff{v[4].x, v[5].x}; MM[1] = ff{v[4].y, v[5].y}; MM[2] = ff{v[4].z, v[5].z};
     }
     const ff scale = KERNEL_K ? ff_from_double(1.0 / (4.0 * M_PI)) : ff{1.f, 0.f};
-    float2* row = M + (size_t)ii * ld;
+    float* rowh = Mh + (size_t)ii * ld;
+    short* rowq = Mq + (size_t)ii * ld;
     for (int base = 0; base < ld; base += kBuildStage) {
         __syncthreads();
         for (int k = tid; k < kBuildStage; k += blockDim.x) {
@@ -104,37 +156,21 @@ k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
         for (int k = lane; k < kend; k += 32) {
             const int j = base + k;
             ff e{0.f, 0.f};
-            if (j < N && j != i) {
-                const float4 A = sA[k], B = sB[k];
-                const ff dx = KERNEL_K ? ff_grid_sub(X[0], A.x, B.x) : ff_sub(X[0], ff{A.x, B.x});
-                const ff dy = KERNEL_K ? ff_grid_sub(X[1], A.y, B.y) : ff_sub(X[1], ff{A.y, B.y});
-                const ff dz = KERNEL_K ? ff_grid_sub(X[2], A.z, B.z) : ff_sub(X[2], ff{A.z, B.z});
-                const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)), ff_sqr_lazy(dz));
-                if (KERNEL_K) {
-                    e = ff_mul(ff_norm(ff_log_lazy(r2, stab)), scale);
-                } else {
-                    const ff inv = ff_rcp_lazy(r2);
-                    const ff nr = ff_norm(ff_add_lazy(ff_add_lazy(ff_mul_lazy(NP[0], dx),
-                                                                  ff_mul_lazy(NP[1], dy)),
-                                                      ff_mul_lazy(NP[2], dz)));
-                    const ff mr = ff_add_lazy(ff_add_lazy(ff_mul_lazy(MM[0], dx), ff_mul_lazy(MM[1], dy)),
-                                              ff_mul_lazy(MM[2], dz));
-                    const ff inner = ff_norm(ff_add_lazy(ff_mul_lazy(nr, ff_mul_lazy(nr, inv)), mr));
-                    e = ff_mul(inv, inner);
-                }
-            }
-            __stcs(row + j, make_float2(e.h, e.l));
+            if (j < N && j != i) e = pair_entry<KERNEL_K>(X, NP, MM, sA[k], sB[k], stab, scale);
+            __stcs(rowh + j, e.h);
+            rowq[j] = (short)ff_q16(e);
         }
     }
 }
 
 // Symmetric parametrix layout, block per tile pair (a, b) of pm_tile_pair: warp w,
-// sub-tile c, step k = 2 kk + h, lane l hold the entry of row a 128 + 32 w + l and
-// column b 128 + 32 c + ((l + k) mod 32) at float2 offset
-// ((((w 4 + c) 16 + kk) 32 + l) 2 + h) of the tile.
+// sub-tile c, step k = 4 kq + t, lane l hold the entry of row a 128 + 32 w + l and
+// column b 128 + 32 c + ((l + k) mod 32); its float is element t of float4
+// (((w 4 + c) 8 + kq) 32 + l) of the tile's float plane, its code element t of the
+// same-numbered 8-byte group of the code plane that follows.
 __global__ void __launch_bounds__(kST)
 k_ffmat_symK_build(const float4* __restrict__ src, const float4* __restrict__ log_tab, int N,
-                   int nt, float4* __restrict__ T) {
+                   int nt, unsigned char* __restrict__ T) {
     __shared__ float4 sA[kST], sB[kST];
     __shared__ float4 stab[kLogTable];
     int a, b;
@@ -155,27 +191,25 @@ k_ffmat_symK_build(const float4* __restrict__ src, const float4* __restrict__ lo
     }
     __syncthreads();
     const ff scale = ff_from_double(1.0 / (4.0 * M_PI));
-    float4* out = T + (size_t)blockIdx.x * kSTF4 + (size_t)w * (4 * 16 * 32) + lane;
+    unsigned char* tile = T + (size_t)blockIdx.x * kTileBytes;
+    float4* oh = reinterpret_cast<float4*>(tile) + (size_t)w * (4 * 8 * 32) + lane;
+    uint2* oq = reinterpret_cast<uint2*>(tile + kTileHiBytes) + (size_t)w * (4 * 8 * 32) + lane;
     for (int c = 0; c < 4; ++c) {
-        for (int kk = 0; kk < 16; ++kk) {
-            float v[4];
-            for (int h = 0; h < 2; ++h) {
-                const int q = c * 32 + ((lane + 2 * kk + h) & 31);
-                const int jj = b * kST + q;
+        for (int kq = 0; kq < 8; ++kq) {
+            float h[4];
+            int q[4];
+            for (int t = 0; t < 4; ++t) {
+                const int col = c * 32 + ((lane + 4 * kq + t) & 31);
+                const int jj = b * kST + col;
                 ff e{0.f, 0.f};
-                if (i < N && jj < N && jj != i) {
-                    const float4 A = sA[q], B = sB[q];
-                    const ff dx = ff_grid_sub(X[0], A.x, B.x);
-                    const ff dy = ff_grid_sub(X[1], A.y, B.y);
-                    const ff dz = ff_grid_sub(X[2], A.z, B.z);
-                    const ff r2 = ff_add_lazy(ff_add_lazy(ff_sqr_lazy(dx), ff_sqr_lazy(dy)),
-                                              ff_sqr_lazy(dz));
-                    e = ff_mul(ff_norm(ff_log_lazy(r2, stab)), scale);
-                }
-                v[2 * h] = e.h;
-                v[2 * h + 1] = e.l;
+                if (i < N && jj < N && jj != i)
+                    e = pair_entry<true>(X, nullptr, nullptr, sA[col], sB[col], stab, scale);
+                h[t] = e.h;
+                q[t] = ff_q16(e);
             }
-            __stcs(out + (c * 16 + kk) * 32, make_float4(v[0], v[1], v[2], v[3]));
+            const int o = (c * 8 + kq) * 32;
+            __stcs(oh + o, make_float4(h[0], h[1], h[2], h[3]));
+            __stcs(oq + o, make_uint2(q_pack(q[0], q[1]), q_pack(q[2], q[3])));
         }
     }
 }
@@ -204,32 +238,49 @@ __device__ __forceinline__ void ff_mac(float& S, float& E, float mh, float ml, f
     S = t;
 }
 
+// four entries (floats h, codes w) of one row against four columns' strengths
+// sa = (s0 hi, lo, s1 hi, lo), sb = (s2, s3)
+__device__ __forceinline__ void ff_mac4(float& S, float& E, float4 h, uint2 w, float4 sa,
+                                        float4 sb) {
+    ff_mac(S, E, h.x, ff_lo(h.x, q_low(w.x)), sa.x, sa.y);
+    ff_mac(S, E, h.y, ff_lo(h.y, q_high(w.x)), sa.z, sa.w);
+    ff_mac(S, E, h.z, ff_lo(h.z, q_low(w.y)), sb.x, sb.y);
+    ff_mac(S, E, h.w, ff_lo(h.w, q_high(w.y)), sb.z, sb.w);
+}
+
 __global__ void __launch_bounds__(kGemvWarps * 32)
-k_ffmat_gemv(const float4* __restrict__ M, long long ld2, const float4* __restrict__ sv, int N,
-             int cs, int ld, float2* __restrict__ partial, const int* __restrict__ skip) {
+k_ffmat_gemv(const float4* __restrict__ Mh, const uint2* __restrict__ Mq, long long ldq,
+             const float4* __restrict__ sv, int N, int cs, int ld, float2* __restrict__ partial,
+             const int* __restrict__ skip) {
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = (blockIdx.x * kGemvWarps + warp) * kGemvRowsPerWarp;
     if (r0 >= N) return;                                  // whole warp
     const int nr = min(kGemvRowsPerWarp, N - r0);
-    const int q0 = (blockIdx.y * cs) >> 1, q1 = min(blockIdx.y * cs + cs, ld) >> 1;   // column pairs
-    const float4* Mr[kGemvRowsPerWarp];
+    const int q0 = (blockIdx.y * cs) >> 2, q1 = min(blockIdx.y * cs + cs, ld) >> 2;   // column quads
+    const float4* Hr[kGemvRowsPerWarp];
+    const uint2* Qr[kGemvRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kGemvRowsPerWarp; ++r) Mr[r] = M + (size_t)(r0 + min(r, nr - 1)) * ld2;
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+        const size_t row = (size_t)(r0 + min(r, nr - 1)) * ldq;
+        Hr[r] = Mh + row;
+        Qr[r] = Mq + row;
+    }
     float S[kGemvRowsPerWarp], E[kGemvRowsPerWarp];
 #pragma unroll
     for (int r = 0; r < kGemvRowsPerWarp; ++r) S[r] = E[r] = 0.f;
 #pragma unroll 2
     for (int q = q0 + lane; q < q1; q += 32) {
-        const float4 s = __ldg(sv + q);
-        float4 m[kGemvRowsPerWarp];
-#pragma unroll
-        for (int r = 0; r < kGemvRowsPerWarp; ++r) m[r] = __ldcs(Mr[r] + q);
+        const float4 sa = __ldg(sv + 2 * q), sb = __ldg(sv + 2 * q + 1);
+        float4 h[kGemvRowsPerWarp];
+        uint2 w[kGemvRowsPerWarp];
 #pragma unroll
         for (int r = 0; r < kGemvRowsPerWarp; ++r) {
-            ff_mac(S[r], E[r], m[r].x, m[r].y, s.x, s.y);
-            ff_mac(S[r], E[r], m[r].z, m[r].w, s.z, s.w);
+            h[r] = __ldcs(Hr[r] + q);
+            w[r] = __ldcs(Qr[r] + q);
         }
+#pragma unroll
+        for (int r = 0; r < kGemvRowsPerWarp; ++r) ff_mac4(S[r], E[r], h[r], w[r], sa, sb);
     }
     // butterfly over the lanes in float-float: every lane ends with the row sum
 #pragma unroll
@@ -258,8 +309,8 @@ k_ffmat_gemv(const float4* __restrict__ M, long long ld2, const float4* __restri
 // the column sums of tile b into slice a (the four warps' values added in warp
 // order), so every (slice, row) is written once, as by the symmetric sums.
 __global__ void __launch_bounds__(kST, 8)
-k_ffmat_symK_gemv(const float4* __restrict__ T, const float2* __restrict__ sv, int N, int nt,
-                  float2* __restrict__ partial, const int* __restrict__ skip) {
+k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict__ sv, int N,
+                  int nt, float2* __restrict__ partial, const int* __restrict__ skip) {
     if (skip && *skip) return;
     __shared__ float2 ssb[kST];
     __shared__ float2 csh[4][kST];
@@ -271,27 +322,32 @@ k_ffmat_symK_gemv(const float4* __restrict__ T, const float2* __restrict__ sv, i
     const float2 si = i < N ? sv[i] : make_float2(0.f, 0.f);
     __syncthreads();
     const bool diag = (a == b);
-    const float4* tile = T + (size_t)blockIdx.x * kSTF4 + (size_t)w * (4 * 16 * 32) + lane;
+    const unsigned char* tile = T + (size_t)blockIdx.x * kTileBytes;
+    const float4* th = reinterpret_cast<const float4*>(tile) + (size_t)w * (4 * 8 * 32) + lane;
+    const uint2* tq = reinterpret_cast<const uint2*>(tile + kTileHiBytes) + (size_t)w * (4 * 8 * 32) + lane;
     const int nxt = (lane + 1) & 31;
     float S = 0.f, E = 0.f;
     float cS[4], cE[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float aS = 0.f, aE = 0.f;                  // column sum of the source evaluated next
-#pragma unroll 8
-        for (int kk = 0; kk < 16; ++kk) {
-            const float4 m = __ldcs(tile + (c * 16 + kk) * 32);
-            const float2 s0 = ssb[c * 32 + ((lane + 2 * kk) & 31)];
-            const float2 s1 = ssb[c * 32 + ((lane + 2 * kk + 1) & 31)];
-            ff_mac(S, E, m.x, m.y, s0.x, s0.y);
-            ff_mac(S, E, m.z, m.w, s1.x, s1.y);
-            if (!diag) {
-                ff_mac(aS, aE, m.x, m.y, si.x, si.y);
-                aS = __shfl_sync(0xffffffffu, aS, nxt);
-                aE = __shfl_sync(0xffffffffu, aE, nxt);
-                ff_mac(aS, aE, m.z, m.w, si.x, si.y);
-                aS = __shfl_sync(0xffffffffu, aS, nxt);
-                aE = __shfl_sync(0xffffffffu, aE, nxt);
+#pragma unroll 4
+        for (int kq = 0; kq < 8; ++kq) {
+            const int o = (c * 8 + kq) * 32;
+            const float4 h4 = __ldcs(th + o);
+            const uint2 w2 = __ldcs(tq + o);
+            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+            const int qv[4] = {q_low(w2.x), q_high(w2.x), q_low(w2.y), q_high(w2.y)};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float h = hv[t], l = ff_lo(h, qv[t]);
+                const float2 sj = ssb[c * 32 + ((lane + 4 * kq + t) & 31)];
+                ff_mac(S, E, h, l, sj.x, sj.y);
+                if (!diag) {
+                    ff_mac(aS, aE, h, l, si.x, si.y);
+                    aS = __shfl_sync(0xffffffffu, aS, nxt);
+                    aE = __shfl_sync(0xffffffffu, aE, nxt);
+                }
             }
         }
         cS[c] = aS;
@@ -319,56 +375,63 @@ k_ffmat_symK_gemv(const float4* __restrict__ T, const float2* __restrict__ sv, i
     }
 }
 
-// Column segments of the GEMV: about four waves of blocks, at most the surface's
-// partial slices, segments a multiple of 64 columns.
+// Column segments of the row-layout GEMV: about four waves of blocks, at most the
+// surface's partial slices, segments a multiple of 128 columns.
 void gemv_shape(const pm_surface* s, int* nseg, int* cs) {
     const int rowblocks = pm_ceil_div(s->N, kGemvRows);
     const int want = 16 * s->ctx->num_sms;
     const int ld = (int)s->ffm_ld;
-    int S = std::max(1, std::min(pm_ceil_div(want, rowblocks), std::min(s->max_split, ld / 64)));
-    int c = pm_ceil_div(pm_ceil_div(ld, S), 64) * 64;
+    int S = std::max(1, std::min(pm_ceil_div(want, rowblocks), std::min(s->max_split, ld / kLd)));
+    int c = pm_ceil_div(pm_ceil_div(ld, S), kLd) * kLd;
     *cs = c;
     *nseg = pm_ceil_div(ld, c);
 }
 
+// planes of a row-layout matrix: the floats, then the codes
+float* plane_h(unsigned char* M) { return reinterpret_cast<float*>(M); }
+short* plane_q(unsigned char* M, const pm_surface* s) {
+    return reinterpret_cast<short*>(M + (size_t)s->N * s->ffm_ld * sizeof(float));
+}
+
 pm_status build_one(pm_surface* s, int which_K, cudaStream_t st) {
-    float2* M = which_K ? s->ffm_K : s->ffm_R;
+    unsigned char* M = which_K ? s->ffm_K : s->ffm_R;
     const int ld = (int)s->ffm_ld;
     if (which_K && s->ffm_symK) {
         const int nt = s->ffm_symK;
-        k_ffmat_symK_build<<<nt * (nt + 1) / 2, kST, 0, st>>>(s->src_kg, s->log_tab, s->N, nt,
-                                                               reinterpret_cast<float4*>(M));
+        k_ffmat_symK_build<<<nt * (nt + 1) / 2, kST, 0, st>>>(s->src_kg, s->log_tab, s->N, nt, M);
         PM_CUDA_TRY(cudaGetLastError());
         return PM_OK;
     }
     const int blocks = pm_ceil_div(s->N, kBuildRows);
     if (which_K)
         k_ffmat_build<true><<<blocks, kBuildRows * 32, 0, st>>>(s->src_kg, s->tgt_ff, s->log_tab,
-                                                                s->N, ld, M);
+                                                                s->N, ld, plane_h(M), plane_q(M, s));
     else
         k_ffmat_build<false><<<blocks, kBuildRows * 32, 0, st>>>(s->src_ff, s->tgt_ff, s->log_tab,
-                                                                 s->N, ld, M);
+                                                                 s->N, ld, plane_h(M), plane_q(M, s));
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
 
-}  // namespace
+long long row_ld(int N) { return (long long)pm_ceil_div(N, kLd) * kLd; }
 
-// entries of the stored parametrix matrix: the symmetric tile layout when the
-// surface uses the symmetric sums, else N x ld
-static size_t k_entries(const pm_surface* s, int* nt_sym) {
+// bytes of the stored parametrix matrix: the symmetric tile layout when the surface
+// uses the symmetric sums, else the row layout
+size_t k_bytes(const pm_surface* s, int* nt_sym) {
     const int nt = pm_sym_tiles(s);
     *nt_sym = nt;
-    if (nt > 0) return (size_t)nt * (nt + 1) / 2 * kST * kST;
-    return (size_t)s->N * (size_t)(pm_ceil_div(s->N, 64) * 64);
+    if (nt > 0) return (size_t)nt * (nt + 1) / 2 * kTileBytes;
+    return (size_t)s->N * (size_t)row_ld(s->N) * 6;
 }
 
+}  // namespace
+
 size_t pm_ffmat_bytes(const pm_surface* s, int which) {
-    const size_t ld = (size_t)pm_ceil_div(s->N, 64) * 64;
+    const size_t ld = (size_t)row_ld(s->N);
     int nt = 0;
     size_t b = ld * sizeof(float2);
-    if (which & 1) b += (size_t)s->N * ld * sizeof(float2);
-    if (which & 2) b += k_entries(s, &nt) * sizeof(float2);
+    if (which & 1) b += (size_t)s->N * ld * 6;
+    if (which & 2) b += k_bytes(s, &nt);
     return b;
 }
 
@@ -402,21 +465,19 @@ pm_status pm_ffmat_apply(pm_surface* s, int which_K, int* nsplit, cudaStream_t s
     if (which_K && s->ffm_symK) {
         const int nt = s->ffm_symK;
         k_ffmat_symK_gemv<<<nt * (nt + 1) / 2, kST, 0, st>>>(
-            reinterpret_cast<const float4*>(s->ffm_K), s->ffm_s, s->N, nt,
-            reinterpret_cast<float2*>(s->partial), s->skip_flag);
+            s->ffm_K, s->ffm_s, s->N, nt, reinterpret_cast<float2*>(s->partial), s->skip_flag);
         PM_CUDA_TRY(cudaGetLastError());
         *nsplit = nt;
         return PM_OK;
     }
     int nseg = 0, cs = 0;
     gemv_shape(s, &nseg, &cs);
-    const float2* M = which_K ? s->ffm_K : s->ffm_R;
+    unsigned char* M = which_K ? s->ffm_K : s->ffm_R;
     dim3 grid(pm_ceil_div(s->N, kGemvRows), nseg);
-    k_ffmat_gemv<<<grid, kGemvWarps * 32, 0, st>>>(reinterpret_cast<const float4*>(M),
-                                                   s->ffm_ld / 2,
-                                                   reinterpret_cast<const float4*>(s->ffm_s), s->N,
-                                                   cs, (int)s->ffm_ld,
-                                                   reinterpret_cast<float2*>(s->partial), s->skip_flag);
+    k_ffmat_gemv<<<grid, kGemvWarps * 32, 0, st>>>(
+        reinterpret_cast<const float4*>(plane_h(M)), reinterpret_cast<const uint2*>(plane_q(M, s)),
+        s->ffm_ld / 4, reinterpret_cast<const float4*>(s->ffm_s), s->N, cs, (int)s->ffm_ld,
+        reinterpret_cast<float2*>(s->partial), s->skip_flag);
     PM_CUDA_TRY(cudaGetLastError());
     *nsplit = nseg;
     return PM_OK;
@@ -454,14 +515,13 @@ extern "C" pm_status pm_surface_store_ff(pm_surface* s, int which) {
                      need / 1e9, fr / 1e9, margin / 1e9);
         return PM_ERR_OOM;
     }
-    s->ffm_ld = (long long)pm_ceil_div(s->N, 64) * 64;
-    const size_t nent = (size_t)s->N * s->ffm_ld;
+    s->ffm_ld = row_ld(s->N);
     int nt_sym = 0;
-    const size_t nentK = k_entries(s, &nt_sym);
+    const size_t bytesK = k_bytes(s, &nt_sym);
     pm_status st = pm_dmalloc(&s->ffm_s, (size_t)s->ffm_ld);
-    if (st == PM_OK && (which & 1)) st = pm_dmalloc(&s->ffm_R, nent);
+    if (st == PM_OK && (which & 1)) st = pm_dmalloc(&s->ffm_R, (size_t)s->N * s->ffm_ld * 6);
     if (st == PM_OK && (which & 2)) {
-        st = pm_dmalloc(&s->ffm_K, nentK);
+        st = pm_dmalloc(&s->ffm_K, bytesK);
         s->ffm_symK = nt_sym;
     }
     if (st == PM_OK && cudaMemset(s->ffm_s, 0, sizeof(float2) * s->ffm_ld) != cudaSuccess) {

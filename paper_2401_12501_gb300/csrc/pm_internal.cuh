@@ -181,11 +181,11 @@ struct pm_surface {
     double2* cKc = nullptr;       // [nblk*pp]
     PmHelmWork* helm = nullptr;
 
-    // stored float-float smooth-sum matrices (pm_ffmat.cu, pm_surface_store_ff):
-    // [N][ffm_ld] (hi, lo) entries of the remainder and parametrix kernels, and the
-    // float-float strengths of the apply; null when not stored
-    float2* ffm_R = nullptr;
-    float2* ffm_K = nullptr;
+    // stored float-float smooth-sum matrices (pm_ffmat.cu, pm_surface_store_ff): the
+    // remainder and parametrix entries (6-byte format, row or symmetric tile layout)
+    // and the float-float strengths of the apply; null when not stored
+    unsigned char* ffm_R = nullptr;
+    unsigned char* ffm_K = nullptr;
     float2* ffm_s = nullptr;      // [ffm_ld]
     long long ffm_ld = 0;
     int ffm_symK = 0;             // tiles of 128 per side when ffm_K holds the symmetric

@@ -3,8 +3,10 @@
 * The stored remainder and parametrix applies match the float64 oracle like the
   unstored float-float sums do (1e-11 relative L2; 864 and 384 nodes, ld = 896 and
   384: a ragged and an exact 64-column tail; the parametrix matrix in the symmetric
-  tile layout and in the row layout), the unstored float-float sums to float-float
-  rounding (5e-13 of the largest entry) and themselves bit for bit.
+  tile layout and in the row layout), the unstored float-float sums to 5e-12 of the
+  largest entry (the stored format keeps each entry to 2^-40 of its magnitude, against
+  ~2^-46 for the float-float evaluation; the errors have random signs, so a row's
+  error stays near 2^-40 |y|) and themselves bit for bit.
 * Full size (ellipsoid 9,600, the GEMV in the launch shape of the solve): sampled
   rows against the oracle at 1e-10 of the row maximum.
 * Storing one kernel leaves the other on the pair-by-pair path; release restores it;
@@ -88,8 +90,8 @@ def test_stored_apply_matches_oracle(ctx, name, sym):
     yR, yK = s.apply_R(sigma, "ff"), s.apply_K(sigma, "ff")
     assert rel(yR, apply_R(d, nf, sigma)) < 1e-11
     assert rel(yK, apply_K(d, nf, sigma)) < 1e-11
-    assert np.abs(yR - yR0).max() <= 5e-13 * np.abs(yR0).max()
-    assert np.abs(yK - yK0).max() <= 5e-13 * np.abs(yK0).max()
+    assert np.abs(yR - yR0).max() <= 5e-12 * np.abs(yR0).max()
+    assert np.abs(yK - yK0).max() <= 5e-12 * np.abs(yK0).max()
     assert np.array_equal(yR, s.apply_R(sigma, "ff"))          # fixed-order reductions
     assert np.array_equal(yK, s.apply_K(sigma, "ff"))
     s.close()
@@ -119,7 +121,7 @@ def test_partial_store_release_coefficient_and_clone(ctx):
     ref = {op: getattr(s, "apply_" + op)(sig, "ff") for op in "RK"}
 
     def close_to_ref(t, r):
-        return np.abs(t - r).max() <= 5e-13 * np.abs(r).max()
+        return np.abs(t - r).max() <= 5e-12 * np.abs(r).max()
 
     s.store_ff("R")
     assert s.stored_ff() == "R"
