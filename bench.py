@@ -429,7 +429,12 @@ def run_gpu(args, rank, world, local_rank):
     acc_R_ms, acc_R_n = per_step("accurate_R")
     acc_K_ms, acc_K_n = per_step("accurate_K")
     fast_R_ms, fast_R_n = per_step("direct_R")
-    actual_pairs = ((fast_R_n * fmm["p2p_pairs"] if fmm else fast_R_n * pairs)
+    # operator applies that did work: the profiled pass issues a cycle's steps from the
+    # host in chunks of 4 between reads of the done flag, so up to 3 launches a cycle
+    # after convergence return at once; per-launch times divide by the applies with work
+    # (one per Arnoldi step and one per residual update after the first refinement)
+    fast_R_eff = it + max(0.0, rf - 1)
+    actual_pairs = ((fast_R_eff * fmm["p2p_pairs"] if fmm else fast_R_eff * pairs)
                     + (acc_R_n + acc_K_n) * pairs)
 
     # end-to-end through the C ABI with host (pinned) buffers: f in, u out
@@ -518,7 +523,7 @@ def run_gpu(args, rank, world, local_rank):
             acc_K_ms / acc_K_n, peak_fp32, acc_K_ms * args.steps / prof_total_ms,
             TRAFFIC_BYTES.get((ff_name + "_K", args.workload)))
     if fmm and ph["fmm_m2l_gemm"][1]:
-        g_ms = ph["fmm_m2l_gemm"][0] / ph["fmm_m2l_gemm"][1]
+        g_ms = ph["fmm_m2l_gemm"][0] / args.steps / fast_R_eff
         alg = M2L_FLOPS_PER_BOX_PAIR * fmm["m2l_box_pairs"]
         peak_tc = mp_peaks["bf16_tflops_sustained"] or mp_peaks["bf16_tflops"]
         ach = alg / (g_ms * 1e-3) / 1e12
@@ -532,14 +537,14 @@ def run_gpu(args, rank, world, local_rank):
                           + mp_peaks["basis"],
             "step_time_share": round(ph["fmm_m2l_gemm"][0] / prof_total_ms, 4)}
     if fmm and ph["fmm_p2p"][1]:
-        p_ms = ph["fmm_p2p"][0] / ph["fmm_p2p"][1]
+        p_ms = ph["fmm_p2p"][0] / args.steps / fast_R_eff
         roofs["fmm_p2p"] = _alu_roofline(
             "k_fmm_p2p<R> (FMM adjacent-leaf float32 sums)", FLOPS_PER_PAIR_R * fmm["p2p_pairs"],
             p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms,
             TRAFFIC_BYTES.get(("k_fmm_p2p", args.workload)))
     if not fmm and fast_R_n:
         roofs["direct_R"] = _alu_roofline(
-            "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, fast_R_ms / fast_R_n,
+            "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, fast_R_ms / fast_R_eff,
             peak_fp32, fast_R_ms * args.steps / prof_total_ms,
             TRAFFIC_BYTES.get(("k_direct_R32", args.workload)))
     dom = max(roofs, key=lambda k: roofs[k]["step_time_share"]) if roofs else None
@@ -590,6 +595,7 @@ def run_gpu(args, rank, world, local_rank):
                                     "every apply evaluates (or reads the stored entry of) "
                                     "N^2 pairs"),
         "solve": {"iterations": it, "refinements": rf, "applies_per_solve": applies,
+                  "operator_applies_with_work": fast_R_eff,
                   "residual_max": max(i.residual for i in infos),
                   "rel_err_vs_fp64_solve": err_vs_fp64, "fp64_solve_s": round(t_fp64, 3),
                   "profiled_ms_per_step": round(prof_total_ms / args.steps, 4),
