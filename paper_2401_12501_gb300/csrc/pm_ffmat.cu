@@ -19,10 +19,11 @@
 // depends on the geometry only.
 //
 // Entry format, 6 bytes: the float-float value h + l (|l| <= ulp(h) / 2 <= 2^-24 |h|)
-// as the float h and the 16-bit integer q = round(l / (|h| 2^-39)), |q| <= 2^15 - 1,
-// so that h + q |h| 2^-39 is the value to within 2^-40 |h| (relative 9.1e-13 per
-// entry, against ~2^-46 of the float-float evaluation).  A matrix is two planes, the
-// floats and the 16-bit words, 4 + 2 bytes an entry instead of the 8 of a float pair.
+// as the float h and the 16-bit code u = q + 2^15 of the integer q = round(l / (h 2^-39)),
+// |q| <= 2^15 - 1, so that h + q h 2^-39 is the value to within 2^-40 |h| (relative
+// 9.1e-13 per entry, against ~2^-46 of the float-float evaluation).  q becomes a float
+// through the significand of 2^23 + u (one byte permutation).  A matrix is two planes,
+// the floats and the 16-bit codes, 4 + 2 bytes an entry instead of the 8 of a float pair.
 //
 // Row layout (the remainder; the parametrix where the symmetric layout is not used):
 // [N][ld] per plane, ld = N rounded up to 128.  GEMV: a block takes 32 rows (4 per
@@ -65,28 +66,29 @@ constexpr size_t kTileHiBytes = (size_t)kST * kST * sizeof(float);
 constexpr size_t kTileBytes = (size_t)kST * kST * 6;
 
 // ------------------------------------------------------------------ entry format
-__device__ __forceinline__ int ff_q16(ff e) {
-    const float sc = fabsf(e.h) * 0x1p-39f;
-    const float r = sc > 0.f ? e.l / sc : 0.f;
-    return (int)fmaxf(-32767.f, fminf(32767.f, rintf(r)));
+// 16-bit code u = q + 2^15 of the low word (see the file header)
+__device__ __forceinline__ unsigned ff_code(ff e) {
+    const float sc = e.h * 0x1p-39f;
+    const float r = sc != 0.f ? e.l / sc : 0.f;
+    return (unsigned)((int)fmaxf(-32767.f, fminf(32767.f, rintf(r))) + 32768);
 }
 
-// the float value of a 16-bit integer through the float's significand (exact)
-__device__ __forceinline__ float q16_to_float(int q) {
-    return __int_as_float(0x4B400000 + q) - 12582912.0f;
+// 2^23 + u as a float, for the code in the low (SEL_HIGH = false) or high half of w
+template <bool SEL_HIGH>
+__device__ __forceinline__ float code_float(unsigned w) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, SEL_HIGH ? 0x7632u : 0x7610u));
 }
 
-// low word of the entry with high word h and packed 16-bit code q
-__device__ __forceinline__ float ff_lo(float h, int q) {
-    return q16_to_float(q) * (fabsf(h) * 0x1p-39f);
+// q 2^-39 from 2^23 + u, exactly: (2^23 + u) 2^-39 - (2^23 + 2^15) 2^-39
+constexpr float kCodeScale = 0x1p-39f;
+constexpr float kCodeBias = -(0x1p-16f + 0x1p-24f);
+
+// low word of the entry with high word h and code word f = 2^23 + u
+__device__ __forceinline__ float ff_lo(float h, float f) {
+    return fmaf(f, kCodeScale, kCodeBias) * h;
 }
 
-__device__ __forceinline__ int q_low(unsigned w) { return (int)(short)(w & 0xFFFFu); }
-__device__ __forceinline__ int q_high(unsigned w) { return (int)w >> 16; }
-
-__device__ __forceinline__ unsigned q_pack(int lo, int hi) {
-    return ((unsigned)lo & 0xFFFFu) | ((unsigned)hi << 16);
-}
+__device__ __forceinline__ unsigned code_pack(unsigned lo, unsigned hi) { return lo | (hi << 16); }
 
 // --------------------------------------------------------------------- build
 // Remainder (KERNEL_K = false): src = src_ff (plain float-float coordinates),
@@ -116,7 +118,7 @@ template <bool KERNEL_K>
 __global__ void __launch_bounds__(kBuildRows * 32)
 k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
               const float4* __restrict__ log_tab, int N, int ld, float* __restrict__ Mh,
-              short* __restrict__ Mq) {
+              unsigned short* __restrict__ Mq) {
     __shared__ float4 sA[kBuildStage], sB[kBuildStage];
     __shared__ float4 stab[KERNEL_K ? kLogTable : 1];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -138,7 +140,7 @@ k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
     }
     const ff scale = KERNEL_K ? ff_from_double(1.0 / (4.0 * M_PI)) : ff{1.f, 0.f};
     float* rowh = Mh + (size_t)ii * ld;
-    short* rowq = Mq + (size_t)ii * ld;
+    unsigned short* rowq = Mq + (size_t)ii * ld;
     for (int base = 0; base < ld; base += kBuildStage) {
         __syncthreads();
         for (int k = tid; k < kBuildStage; k += blockDim.x) {
@@ -158,7 +160,7 @@ k_ffmat_build(const float4* __restrict__ src, const float4* __restrict__ tg,
             ff e{0.f, 0.f};
             if (j < N && j != i) e = pair_entry<KERNEL_K>(X, NP, MM, sA[k], sB[k], stab, scale);
             __stcs(rowh + j, e.h);
-            rowq[j] = (short)ff_q16(e);
+            rowq[j] = (unsigned short)ff_code(e);
         }
     }
 }
@@ -197,7 +199,7 @@ k_ffmat_symK_build(const float4* __restrict__ src, const float4* __restrict__ lo
     for (int c = 0; c < 4; ++c) {
         for (int kq = 0; kq < 8; ++kq) {
             float h[4];
-            int q[4];
+            unsigned q[4];
             for (int t = 0; t < 4; ++t) {
                 const int col = c * 32 + ((lane + 4 * kq + t) & 31);
                 const int jj = b * kST + col;
@@ -205,11 +207,11 @@ k_ffmat_symK_build(const float4* __restrict__ src, const float4* __restrict__ lo
                 if (i < N && jj < N && jj != i)
                     e = pair_entry<true>(X, nullptr, nullptr, sA[col], sB[col], stab, scale);
                 h[t] = e.h;
-                q[t] = ff_q16(e);
+                q[t] = ff_code(e);
             }
             const int o = (c * 8 + kq) * 32;
             __stcs(oh + o, make_float4(h[0], h[1], h[2], h[3]));
-            __stcs(oq + o, make_uint2(q_pack(q[0], q[1]), q_pack(q[2], q[3])));
+            __stcs(oq + o, make_uint2(code_pack(q[0], q[1]), code_pack(q[2], q[3])));
         }
     }
 }
@@ -242,10 +244,10 @@ __device__ __forceinline__ void ff_mac(float& S, float& E, float mh, float ml, f
 // sa = (s0 hi, lo, s1 hi, lo), sb = (s2, s3)
 __device__ __forceinline__ void ff_mac4(float& S, float& E, float4 h, uint2 w, float4 sa,
                                         float4 sb) {
-    ff_mac(S, E, h.x, ff_lo(h.x, q_low(w.x)), sa.x, sa.y);
-    ff_mac(S, E, h.y, ff_lo(h.y, q_high(w.x)), sa.z, sa.w);
-    ff_mac(S, E, h.z, ff_lo(h.z, q_low(w.y)), sb.x, sb.y);
-    ff_mac(S, E, h.w, ff_lo(h.w, q_high(w.y)), sb.z, sb.w);
+    ff_mac(S, E, h.x, ff_lo(h.x, code_float<false>(w.x)), sa.x, sa.y);
+    ff_mac(S, E, h.y, ff_lo(h.y, code_float<true>(w.x)), sa.z, sa.w);
+    ff_mac(S, E, h.z, ff_lo(h.z, code_float<false>(w.y)), sb.x, sb.y);
+    ff_mac(S, E, h.w, ff_lo(h.w, code_float<true>(w.y)), sb.z, sb.w);
 }
 
 __global__ void __launch_bounds__(kGemvWarps * 32)
@@ -304,57 +306,112 @@ k_ffmat_gemv(const float4* __restrict__ Mh, const uint2* __restrict__ Mq, long l
         }
 }
 
+// Packed float-float multiply-add on two independent chains (S.x, E.x), (S.y, E.y):
+// ff_mac on each, one f32x2 instruction per step of both.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ void ff_mac2(float2& S, float2& E, float2 h, float2 l, float2 sh,
+                                        float2 sl) {
+    const float2 p = __fmul2_rn(h, sh);
+    float2 e = __ffma2_rn(h, sh, neg2(p));
+    e = __ffma2_rn(h, sl, e);
+    e = __ffma2_rn(l, sh, e);
+    const float2 t = __fadd2_rn(S, p);
+    const float2 bp = __fadd2_rn(t, neg2(S));
+    const float2 d1 = __fadd2_rn(S, neg2(__fadd2_rn(t, neg2(bp))));
+    const float2 d2 = __fadd2_rn(p, neg2(bp));
+    E = __fadd2_rn(E, __fadd2_rn(__fadd2_rn(d1, d2), e));
+    S = t;
+}
+
+// (S, E) of one chain += (S2, E2) of another, in float-float
+__device__ __forceinline__ void ff_join(float& S, float& E, float S2, float E2) {
+    float t, d;
+    two_sum(S, S2, t, d);
+    E = (E + E2) + d;
+    S = t;
+}
+
 // Symmetric parametrix GEMV over the stored upper-triangle tiles (layout above):
 // block (a, b) writes the row sums of tile a into partial slice b and, for a < b,
 // the column sums of tile b into slice a (the four warps' values added in warp
-// order), so every (slice, row) is written once, as by the symmetric sums.
-__global__ void __launch_bounds__(kST, 8)
+// order), so every (slice, row) is written once, as by the symmetric sums.  A lane
+// takes two steps k, k + 1 at a time in packed f32x2 arithmetic: its row sum as two
+// chains (even and odd steps), and two column sums, for columns (l + k) and
+// (l + k + 1) mod 32, that rotate by two lanes per double step; after the 32 steps of
+// a sub-tile lane l holds column l's even chain and column l + 1's odd chain.  The
+// strengths of a sub-tile's 32 columns sit twice in a row in shared memory (and once
+// more shifted by one), so that the pair of a double step is one aligned 8-byte load.
+__global__ void __launch_bounds__(kST, 6)
 k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict__ sv, int N,
                   int nt, float2* __restrict__ partial, const int* __restrict__ skip) {
     if (skip && *skip) return;
-    __shared__ float2 ssb[kST];
+    // Dh[c][i] = hi of column c 32 + (i mod 32); Ph[c][i] = Dh[c][i + 1] (likewise lo)
+    __shared__ __align__(16) float Dh[4][64], Dl[4][64], Ph[4][64], Pl[4][64];
     __shared__ float2 csh[4][kST];
     int a, b;
     pm_tile_pair(blockIdx.x, nt, a, b);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int i = a * kST + tid, j = b * kST + tid;
-    ssb[tid] = j < N ? sv[j] : make_float2(0.f, 0.f);
+    {
+        const float2 sj = j < N ? sv[j] : make_float2(0.f, 0.f);   // column tid = 32 w + lane
+        const int pm = (lane + 31) & 31;
+        Dh[w][lane] = Dh[w][lane + 32] = sj.x;
+        Dl[w][lane] = Dl[w][lane + 32] = sj.y;
+        Ph[w][pm] = Ph[w][pm + 32] = sj.x;
+        Pl[w][pm] = Pl[w][pm + 32] = sj.y;
+    }
     const float2 si = i < N ? sv[i] : make_float2(0.f, 0.f);
     __syncthreads();
     const bool diag = (a == b);
     const unsigned char* tile = T + (size_t)blockIdx.x * kTileBytes;
     const float4* th = reinterpret_cast<const float4*>(tile) + (size_t)w * (4 * 8 * 32) + lane;
     const uint2* tq = reinterpret_cast<const uint2*>(tile + kTileHiBytes) + (size_t)w * (4 * 8 * 32) + lane;
-    const int nxt = (lane + 1) & 31;
-    float S = 0.f, E = 0.f;
+    const int nxt2 = (lane + 2) & 31, prv = (lane + 31) & 31;
+    const bool odd = lane & 1;
+    const float2 SIH = make_float2(si.x, si.x), SIL = make_float2(si.y, si.y);
+    const float2 CSC = make_float2(kCodeScale, kCodeScale), CBI = make_float2(kCodeBias, kCodeBias);
+    float2 RS = make_float2(0.f, 0.f), RE = make_float2(0.f, 0.f);
     float cS[4], cE[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        float aS = 0.f, aE = 0.f;                  // column sum of the source evaluated next
+        const float2* ph = reinterpret_cast<const float2*>(odd ? &Ph[c][lane - 1] : &Dh[c][lane]);
+        const float2* pl = reinterpret_cast<const float2*>(odd ? &Pl[c][lane - 1] : &Dl[c][lane]);
+        float2 CS = make_float2(0.f, 0.f), CE = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int kq = 0; kq < 8; ++kq) {
             const int o = (c * 8 + kq) * 32;
             const float4 h4 = __ldcs(th + o);
             const uint2 w2 = __ldcs(tq + o);
-            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
-            const int qv[4] = {q_low(w2.x), q_high(w2.x), q_low(w2.y), q_high(w2.y)};
+            const float2 H0 = make_float2(h4.x, h4.y), H1 = make_float2(h4.z, h4.w);
+            const float2 F0 = make_float2(code_float<false>(w2.x), code_float<true>(w2.x));
+            const float2 F1 = make_float2(code_float<false>(w2.y), code_float<true>(w2.y));
+            const float2 L0 = __fmul2_rn(__ffma2_rn(F0, CSC, CBI), H0);
+            const float2 L1 = __fmul2_rn(__ffma2_rn(F1, CSC, CBI), H1);
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float h = hv[t], l = ff_lo(h, qv[t]);
-                const float2 sj = ssb[c * 32 + ((lane + 4 * kq + t) & 31)];
-                ff_mac(S, E, h, l, sj.x, sj.y);
+            for (int half = 0; half < 2; ++half) {
+                const float2 H = half ? H1 : H0, L = half ? L1 : L0;
+                const int d = 2 * kq + half;
+                ff_mac2(RS, RE, H, L, ph[d], pl[d]);
                 if (!diag) {
-                    ff_mac(aS, aE, h, l, si.x, si.y);
-                    aS = __shfl_sync(0xffffffffu, aS, nxt);
-                    aE = __shfl_sync(0xffffffffu, aE, nxt);
+                    ff_mac2(CS, CE, H, L, SIH, SIL);
+                    CS.x = __shfl_sync(0xffffffffu, CS.x, nxt2);
+                    CS.y = __shfl_sync(0xffffffffu, CS.y, nxt2);
+                    CE.x = __shfl_sync(0xffffffffu, CE.x, nxt2);
+                    CE.y = __shfl_sync(0xffffffffu, CE.y, nxt2);
                 }
             }
         }
-        cS[c] = aS;
-        cE[c] = aE;
+        // column lane: its even chain here, its odd chain on the previous lane
+        float s = CS.x, e = CE.x;
+        ff_join(s, e, __shfl_sync(0xffffffffu, CS.y, prv), __shfl_sync(0xffffffffu, CE.y, prv));
+        cS[c] = s;
+        cE[c] = e;
     }
     if (i < N) {
-        const ff v = ff_norm(ff{S, E});
+        float s = RS.x, e = RE.x;
+        ff_join(s, e, RS.y, RE.y);
+        const ff v = ff_norm(ff{s, e});
         partial[(size_t)b * N + i] = make_float2(v.h, v.l);
     }
     if (diag) return;
@@ -364,12 +421,7 @@ k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict_
     if (j < N) {
         float t = csh[0][tid].x, e = csh[0][tid].y;
 #pragma unroll
-        for (int q = 1; q < 4; ++q) {
-            float u, d;
-            two_sum(t, csh[q][tid].x, u, d);
-            e = (e + csh[q][tid].y) + d;
-            t = u;
-        }
+        for (int q = 1; q < 4; ++q) ff_join(t, e, csh[q][tid].x, csh[q][tid].y);
         const ff v = ff_norm(ff{t, e});
         partial[(size_t)a * N + j] = make_float2(v.h, v.l);
     }
@@ -389,8 +441,8 @@ void gemv_shape(const pm_surface* s, int* nseg, int* cs) {
 
 // planes of a row-layout matrix: the floats, then the codes
 float* plane_h(unsigned char* M) { return reinterpret_cast<float*>(M); }
-short* plane_q(unsigned char* M, const pm_surface* s) {
-    return reinterpret_cast<short*>(M + (size_t)s->N * s->ffm_ld * sizeof(float));
+unsigned short* plane_q(unsigned char* M, const pm_surface* s) {
+    return reinterpret_cast<unsigned short*>(M + (size_t)s->N * s->ffm_ld * sizeof(float));
 }
 
 pm_status build_one(pm_surface* s, int which_K, cudaStream_t st) {
