@@ -914,6 +914,29 @@ def run_micro_ffmat(args):
     ctx.close()
 
 
+def run_micro_fmm(args):
+    """One FMM remainder and one parametrix apply on the 98,304-node torus (built
+    without stored matrices, ~2 GB on the device): the launches an ncu capture of the
+    FMM kernels (k_fmm_p2p, k_tc_gemm, ...) looks at."""
+    import numpy as np
+    import torch
+    import paper_2401_12501_gb300 as pm
+    from workloads import make_workload
+    wl = make_workload("torus_98304")
+    ctx = pm.Context(0)
+    s = pm.Surface.from_fixture(ctx, wl.surface)
+    s.set_coeff(wl.coeff.a, wl.coeff.grad_a)
+    sig = torch.from_numpy(np.random.default_rng(3).standard_normal(wl.N) + 1.0).to("cuda:0")
+    y = s.apply_R(sig, "fmm")
+    z = s.apply_K(sig, "fmm")
+    torch.cuda.synchronize()
+    print(json.dumps({"micro": "fmm", "workload": "torus_98304", "N": wl.N,
+                      "finite": bool(torch.isfinite(y).all() and torch.isfinite(z).all()),
+                      "tree": s.fmm_stats()}))
+    s.close()
+    ctx.close()
+
+
 def run_micro_tri(args):
     """One triangle-patch surface build (the unit sphere from 80 triangles at the order-8
     Vioreanu-Rokhlin nodes, 2,880 nodes): the launches an ncu capture of the triangle
@@ -1313,7 +1336,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--serve-fmm-min", type=int, default=40000,
                     help="served operators with at least this many nodes use FMM applies")
-    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz", "tri", "ffmat"], default=None,
+    ap.add_argument("--micro", choices=["tc_gemm", "helmholtz", "tri", "ffmat", "fmm"], default=None,
                     help="time one kernel alone instead of the solve step (profiling aid)")
     ap.add_argument("--micro-c", type=float, default=-4.0,
                     help="c of --micro helmholtz (1,536-node unit sphere, a = 1)")
@@ -1330,6 +1353,9 @@ def main():
         return
     if args.micro == "ffmat":
         run_micro_ffmat(args)
+        return
+    if args.micro == "fmm":
+        run_micro_fmm(args)
         return
     if args.oracle_leg:
         P = host_cores()
