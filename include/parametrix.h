@@ -248,6 +248,7 @@ pm_status pm_surface_store_ff(pm_surface* s, int which);
 /* The kernels currently stored by pm_surface_store_ff (same bits; 0 for NULL). */
 int pm_surface_stored_ff(const pm_surface* s);
 
+
 /* Number of nodes N and near-field blocks (target, near patch) of a surface. */
 pm_status pm_surface_info(const pm_surface* s, int* N, int* nblocks);
 
@@ -335,6 +336,52 @@ typedef struct {
 pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double tol,
                    int maxit, pm_precision prec, unsigned flags, double* sigma_out,
                    pm_solve_info* info, void* stream);
+
+/*
+ * Open-surface Neumann boundary-value problem (Sec. 5.2, eq. NeuBVPsystem):
+ * div_Gamma(a grad_Gamma u) = f on an open surface Gamma, nu . grad_Gamma u = f_gamma
+ * on its boundary gamma.  s is a surface built by pm_surface_create from Gamma's
+ * quadrilateral patches (its nodes interior to the patches) with
+ * pm_surface_set_coeff done (c = 0); it must outlive the handle.  gamma is ncurves
+ * closed curves; curve c is given at M[c] >= 2 edge nodes, the points at
+ * t_k = 2 pi (k + 1/2) / M[c] of a 2 pi-periodic parameter t, and at F[c] M[c]
+ * oversampled points t_j = 2 pi j / (F[c] M[c]) (Sec. 6.1.4's Fourier oversampling),
+ * curve after curve.  Me = sum M[c] edge nodes (at most 4,096), Fo = sum F[c] M[c]
+ * oversampled points.  Host arrays, copied by the call:
+ *   edge_x [Me][3], edge_d1 [Me][3] = dgamma/dt, edge_d2 [Me][3] = d2gamma/dt2,
+ *   edge_nu [Me][3] the unit binormal (tangent to Gamma, normal to gamma, pointing away
+ *   from Gamma), edge_a [Me] = a > 0 at the node, edge_patch [Me] the patch whose
+ *   edge holds the node and edge_uv [Me][2] the node's reference coordinates there
+ *   (one of them -1 or +1; nodes should avoid patch corners);
+ *   over_x [Fo][3], over_speed [Fo] = |dgamma/dt|, over_a [Fo] = a at the points.
+ * The system takes sigma at the surface's N nodes and mu at the Me edge nodes:
+ *   sigma + R~ sigma + R_gamma mu = f,  -mu/(2a) + K'_Gamma sigma + K'_gamma mu + sum_k w_k mu_k = f_gamma,
+ * u = K~ sigma + K_gamma mu, all in float64 (the rank-one term, w_k the trapezoid
+ * weights, removes the null space of the Neumann problem: u is unique up to a
+ * constant).  Creation computes the K'_Gamma quadrature of every edge node on the
+ * device.  PM_ERR_INVALID_ARG for NULL arguments, bad sizes or an edge node not on
+ * an edge of its patch; PM_ERR_NO_COEFF without a coefficient.
+ */
+typedef struct pm_bvp pm_bvp;
+pm_status pm_bvp_create(pm_surface* s, int ncurves, const int* M, const int* F,
+                        const double* edge_x, const double* edge_d1, const double* edge_d2,
+                        const double* edge_nu, const double* edge_a, const int* edge_patch,
+                        const double* edge_uv, const double* over_x, const double* over_speed,
+                        const double* over_a, pm_bvp** out);
+void pm_bvp_destroy(pm_bvp* b);
+
+/* The system's operator on host arrays sigma [N], mu [Me] (rank-one term included):
+ * out_s [N] the surface rows, out_e [Me] the edge rows. */
+pm_status pm_bvp_apply(pm_bvp* b, const double* sigma, const double* mu, double* out_s,
+                       double* out_e);
+
+/* Solve for f [N], f_gamma [Me] (host) by restarted GMRES (opts.gmres_restart,
+ * at most maxit iterations) to relative residual tol, then u [N] = K~ sigma +
+ * K_gamma mu; sigma [N] and mu [Me] are written when not NULL.  info as for pm_solve
+ * (refinements 0).  PM_ERR_NOT_CONVERGED (u, sigma, mu still written) when tol is
+ * not reached. */
+pm_status pm_bvp_solve(pm_bvp* b, const double* f, const double* f_gamma, double tol,
+                       int maxit, double* u, double* sigma, double* mu, pm_solve_info* info);
 
 /*
  * Solve several operators' systems together (the batched form across operators):

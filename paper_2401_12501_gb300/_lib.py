@@ -43,7 +43,8 @@ EXPORTS = ["pm_default_opts", "pm_ctx_create", "pm_ctx_destroy", "pm_surface_cre
            "pm_selftest_green_f32", "pm_selftest_smooth_c_f32", "pm_smooth_c_f32",
            "pm_surface_set_coeff_c", "pm_apply_c", "pm_solve_c", "pm_surface_create_tri",
            "pm_selftest_tri_basis", "pm_surface_check", "pm_selftest_green_c",
-           "pm_surface_store_ff", "pm_surface_stored_ff"]
+           "pm_surface_store_ff", "pm_surface_stored_ff", "pm_bvp_create", "pm_bvp_destroy",
+           "pm_bvp_apply", "pm_bvp_solve"]
 (PM_PHASE_PREP, PM_PHASE_DIRECT_R, PM_PHASE_DIRECT_K, PM_PHASE_NEAR, PM_PHASE_SOLVE_VEC,
  PM_PHASE_DIRECT64, PM_PHASE_FMM_M2L, PM_PHASE_FMM_P2P, PM_PHASE_DIRECT64_K,
  PM_PHASE_COUNT) = range(10)
@@ -153,6 +154,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_store_ff.argtypes = [P, C.c_int]
     lib.pm_surface_stored_ff.argtypes = [P]
     lib.pm_surface_stored_ff.restype = C.c_int
+    lib.pm_bvp_create.argtypes = [P, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, C.POINTER(P)]
+    lib.pm_bvp_destroy.argtypes = [P]
+    lib.pm_bvp_destroy.restype = None
+    lib.pm_bvp_apply.argtypes = [P, P, P, P, P]
+    lib.pm_bvp_solve.argtypes = [P, P, P, C.c_double, C.c_int, P, P, P, C.POINTER(PmSolveInfo)]
     lib.pm_selftest_green_c.argtypes = [P, C.c_int, C.c_double, C.c_double, P]
     lib.pm_apply_c.argtypes = [P, C.c_int, P, P, C.c_int, P]
     lib.pm_solve_c.argtypes = [P, P, P, C.c_double, C.c_int, P, C.POINTER(PmSolveInfo)]

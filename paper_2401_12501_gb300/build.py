@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libparametrix.so")
 CHECKED_LIB = os.path.join(HERE, "libparametrix_checked.so")
-SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_check.cu", "pm_direct.cu", "pm_ffmat.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_helm.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tcgemm.cu", "pm_tri.cu", "pm_tune.cu"]
+SOURCES = ["pm_api.cu", "pm_batch.cu", "pm_bvp.cu", "pm_check.cu", "pm_direct.cu", "pm_ffmat.cu", "pm_ffsum.cu", "pm_fmm.cu", "pm_green.cu", "pm_helm.cu", "pm_nearfield.cu", "pm_server.cu", "pm_solve.cu", "pm_symsum.cu", "pm_tcgemm.cu", "pm_tri.cu", "pm_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -943,6 +943,200 @@ __global__ void k_tile_radius(const double* __restrict__ x, int N, int tile,
     if (lane == 0) atomicMax(out, __float_as_uint((float)m));
 }
 
+
+// ------------------------------------------------------------------ boundary-value systems
+// K'_Gamma weights of an edge node x_e of an open surface (Sec. 5.2, Thm. NeumannBCsrep):
+// W_k = int_P nu_e . (x - y) / (2 pi |x - y|^2) l_k J~ du dv over a patch P near x_e
+// (the density sigma / a interpolated, as for the surface operators).  One block per
+// (edge node, patch) pair.  own != 0: x_e lies on an edge of P at reference point
+// (u0, v0); the rule is polar about the patch's own point x = y~(u0, v0) over the
+// directions that enter the square, theta cut at the corner directions and at most
+// pi/16 wide, two radial panels [0, L/4], [L/4, L], 16-point Gauss on each (after the
+// polar Jacobian the integrand is smooth).  own == 0: the quadtree near rule about
+// x = x_e as in k_near_quad.
+constexpr int kBvpPts = 128;          // quadrature points per pass of the polar rule
+
+__device__ double bvp_ray(double u0, double v0, double ct, double st) {
+    double L = 1e300;
+    if (ct > 1e-15) L = fmin(L, (1.0 - u0) / ct);
+    if (ct < -1e-15) L = fmin(L, (-1.0 - u0) / ct);
+    if (st > 1e-15) L = fmin(L, (1.0 - v0) / st);
+    if (st < -1e-15) L = fmin(L, (-1.0 - v0) / st);
+    return L;
+}
+
+__global__ void __launch_bounds__(kQThreads)
+k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
+              const int* __restrict__ blk_edge, const int* __restrict__ blk_patch,
+              const int* __restrict__ blk_own, const double* __restrict__ xe,
+              const double* __restrict__ nue, const double* __restrict__ uv, double eta,
+              int max_depth, int max_leaves, double* __restrict__ W, int* __restrict__ err) {
+    const int blk = blockIdx.x;
+    const int e = blk_edge[blk], P = blk_patch[blk];
+    const int pp = p * p, tid = threadIdx.x;
+    __shared__ double sD[3 * PM_MAX_P * PM_MAX_P];
+    __shared__ double sJ[PM_MAX_P * PM_MAX_P];
+    // polar rule: basis values of the pass's points; quadtree: basis values at the
+    // leaf's 16 Gauss abscissae in u and v, then the Z partial sums
+    __shared__ double sBuf[2 * kBvpPts * PM_MAX_P_API];
+    __shared__ double sF[PM_GL16 * PM_GL16];
+    __shared__ double sX[3];
+    __shared__ double sCut[8];
+    __shared__ int sNcut;
+    __shared__ NearBfs bfs;
+    const double* X = x + (size_t)3 * P * pp;
+    const double n0 = nue[3 * e], n1 = nue[3 * e + 1], n2 = nue[3 * e + 2];
+    const bool own = blk_own[blk] != 0;
+    const double u0 = uv[2 * e], v0 = uv[2 * e + 1];
+    if (tid == 0) {
+        if (own) {
+            double y[3];
+            interp_pos(X, p, u0, v0, y);
+            sX[0] = y[0]; sX[1] = y[1]; sX[2] = y[2];
+        } else {
+            sX[0] = xe[3 * e]; sX[1] = xe[3 * e + 1]; sX[2] = xe[3 * e + 2];
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < pp; k += kQThreads) {
+        const size_t gk = (size_t)P * pp + k;
+        sD[k] = x[3 * gk] - sX[0];
+        sD[pp + k] = x[3 * gk + 1] - sX[1];
+        sD[2 * pp + k] = x[3 * gk + 2] - sX[2];
+        sJ[k] = J[gk];
+    }
+    __syncthreads();
+    const int a_own = tid / p, b_own = tid - (tid / p) * p;
+    double acc = 0.0;
+    double* sLu = sBuf;
+    double* sLv = sBuf + kBvpPts * p;
+    if (own) {
+        // angular range of the directions entering [-1,1]^2 from the edge point
+        if (tid == 0) {
+            double lo, hi;
+            if (fabs(u0 + 1.0) < 1e-12) { lo = -0.5 * M_PI; hi = 0.5 * M_PI; }
+            else if (fabs(u0 - 1.0) < 1e-12) { lo = 0.5 * M_PI; hi = 1.5 * M_PI; }
+            else if (fabs(v0 + 1.0) < 1e-12) { lo = 0.0; hi = M_PI; }
+            else { lo = M_PI; hi = 2.0 * M_PI; }
+            int nc = 0;
+            sCut[nc++] = lo;
+            const double cu[4] = {1.0, -1.0, -1.0, 1.0}, cv[4] = {1.0, 1.0, -1.0, -1.0};
+            for (int c = 0; c < 4; ++c) {
+                const double th = atan2(cv[c] - v0, cu[c] - u0);
+                for (int k = -1; k <= 2; ++k) {
+                    const double tt = th + 2.0 * M_PI * k;
+                    if (tt > lo + 1e-12 && tt < hi - 1e-12 && nc < 7) sCut[nc++] = tt;
+                }
+            }
+            sCut[nc++] = hi;
+            for (int i = 1; i < nc; ++i)          // insertion sort
+                for (int j = i; j > 0 && sCut[j] < sCut[j - 1]; --j) {
+                    const double t = sCut[j]; sCut[j] = sCut[j - 1]; sCut[j - 1] = t;
+                }
+            sNcut = nc;
+        }
+        __syncthreads();
+        const int nc = sNcut;
+        for (int seg = 0; seg + 1 < nc; ++seg) {
+            const double A = sCut[seg], B = sCut[seg + 1];
+            const int nsub = max(1, (int)ceil((B - A) / (M_PI / 16.0) - 1e-9));
+            for (int sub = 0; sub < nsub; ++sub) {
+                const double s0 = A + (B - A) * sub / nsub, s1 = A + (B - A) * (sub + 1) / nsub;
+                const double hs = 0.5 * (s1 - s0);
+                for (int rp = 0; rp < 2; ++rp) {
+                    for (int half = 0; half < 2; ++half) {
+                        // point tid: theta node 8 half + tid / 16, radial node tid % 16
+                        {
+                            const int qt = 8 * half + tid / PM_GL16, qr = tid % PM_GL16;
+                            const double th = s0 + hs * (cT.g16t[qt] + 1.0);
+                            const double ct = cos(th), st = sin(th);
+                            const double L = bvp_ray(u0, v0, ct, st);
+                            const double r0 = rp == 0 ? 0.0 : 0.25 * L, r1 = rp == 0 ? 0.25 * L : L;
+                            const double hr = 0.5 * (r1 - r0);
+                            const double rho = r0 + hr * (cT.g16t[qr] + 1.0);
+                            const double u = u0 + rho * ct, v = v0 + rho * st;
+                            double* lu = sLu + tid * p;
+                            double* lv = sLv + tid * p;
+                            lagrange(u, p, lu);
+                            lagrange(v, p, lv);
+                            double d0 = 0, d1 = 0, d2 = 0, jj = 0;
+                            for (int a = 0; a < p; ++a) {
+                                double z0 = 0, z1 = 0, z2 = 0, zj = 0;
+                                for (int b = 0; b < p; ++b) {
+                                    const double l = lv[b];
+                                    z0 += sD[a * p + b] * l;
+                                    z1 += sD[pp + a * p + b] * l;
+                                    z2 += sD[2 * pp + a * p + b] * l;
+                                    zj += sJ[a * p + b] * l;
+                                }
+                                d0 += lu[a] * z0; d1 += lu[a] * z1; d2 += lu[a] * z2; jj += lu[a] * zj;
+                            }
+                            // r = x - y = -(y - x)
+                            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                            const double nr = -(n0 * d0 + n1 * d1 + n2 * d2);
+                            const double wgt = hs * cT.g16w[qt] * hr * cT.g16w[qr] * rho * jj;
+                            sF[tid] = r2 > 0.0 ? wgt * nr / r2 * (0.5 / M_PI) : 0.0;
+                        }
+                        __syncthreads();
+                        if (tid < pp)
+                            for (int q = 0; q < kBvpPts; ++q)
+                                acc += sF[q] * sLu[q * p + a_own] * sLv[q * p + b_own];
+                        __syncthreads();
+                    }
+                }
+            }
+        }
+    } else {
+        double* sLu16 = sBuf;
+        double* sLv16 = sBuf + PM_GL16 * p;
+        double* sZ = sBuf + 2 * PM_GL16 * p;             // [4][a][r]
+        double* sG = sF;
+        const int nleaves = near_leaves(X, p, sX[0], sX[1], sX[2], eta, max_depth, max_leaves, bfs,
+                                        err);
+        for (int Lf = 0; Lf < nleaves; ++Lf) {
+            double uu0, uu1, vv0, vv1;
+            sq_box(bfs.sorted[Lf], uu0, uu1, vv0, vv1);
+            const double hu = 0.5 * (uu1 - uu0), hv = 0.5 * (vv1 - vv0);
+            if (tid < PM_GL16) lagrange(uu0 + hu * (cT.g16t[tid] + 1.0), p, sLu16 + tid * p);
+            else if (tid < 2 * PM_GL16)
+                lagrange(vv0 + hv * (cT.g16t[tid - PM_GL16] + 1.0), p, sLv16 + (tid - PM_GL16) * p);
+            __syncthreads();
+            for (int q = tid; q < 4 * p * PM_GL16; q += kQThreads) {
+                const int c = q / (p * PM_GL16), rem = q - c * p * PM_GL16;
+                const int a = rem / PM_GL16, r = rem - a * PM_GL16;
+                const double* src = (c < 3) ? (sD + c * pp) : sJ;
+                double z = 0;
+                for (int bb = 0; bb < p; ++bb) z += src[a * p + bb] * sLv16[r * p + bb];
+                sZ[(c * p + a) * PM_GL16 + r] = z;
+            }
+            __syncthreads();
+            for (int q = tid; q < PM_GL16 * PM_GL16; q += kQThreads) {
+                const int qn = q / PM_GL16, r = q - qn * PM_GL16;
+                double d0 = 0, d1 = 0, d2 = 0, jj = 0;
+                for (int a = 0; a < p; ++a) {
+                    const double l = sLu16[qn * p + a];
+                    d0 += l * sZ[(0 * p + a) * PM_GL16 + r];
+                    d1 += l * sZ[(1 * p + a) * PM_GL16 + r];
+                    d2 += l * sZ[(2 * p + a) * PM_GL16 + r];
+                    jj += l * sZ[(3 * p + a) * PM_GL16 + r];
+                }
+                const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                const double nr = -(n0 * d0 + n1 * d1 + n2 * d2);
+                const double wgt = hu * cT.g16w[qn] * hv * cT.g16w[r] * jj;
+                sG[q] = wgt * nr / r2 * (0.5 / M_PI);
+            }
+            __syncthreads();
+            if (tid < pp)
+                for (int r = 0; r < PM_GL16; ++r) {
+                    double t = 0;
+                    for (int qn = 0; qn < PM_GL16; ++qn) t += sG[qn * PM_GL16 + r] * sLu16[qn * p + a_own];
+                    acc += t * sLv16[r * p + b_own];
+                }
+            __syncthreads();
+        }
+    }
+    if (tid < pp) W[(size_t)blk * pp + tid] = acc;
+}
 }  // namespace
 
 // The quadrature tables live in one __constant__ copy per device, written here
@@ -1147,6 +1341,31 @@ pm_status pm_near_build_c(pm_surface* s) {
     PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr != PM_DEV_OK) {
         pm_set_error("c != 0 near-field quadrature: device check %d failed (leaf budget exceeded)", herr);
+        return PM_ERR_INTERNAL;
+    }
+    return PM_OK;
+}
+
+// K'_Gamma weights of the edge nodes of a boundary-value system (pm_bvp.cu): one
+// block per (edge node, patch) pair of the device lists; W [nb][p*p].
+pm_status pm_bvp_kp_weights(pm_surface* s, int nb, const int* blk_edge, const int* blk_patch,
+                            const int* blk_own, const double* xe, const double* nue,
+                            const double* uv, double* W) {
+    std::lock_guard<std::mutex> build_lock(g_near_build_mu);
+    if (nb == 0) return PM_OK;
+    QuadTables T;
+    pm_build_tables(s->p, &T);
+    PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
+    PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
+    k_bvp_kp_quad<<<nb, kQThreads>>>(s->p, s->x, s->J, blk_edge, blk_patch, blk_own, xe, nue, uv,
+                                     s->opts.near_eta, std::min(s->opts.near_max_depth, 12),
+                                     s->opts.near_max_leaves, W, s->dev_err);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    int herr = 0;
+    PM_CUDA_TRY(cudaMemcpy(&herr, s->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr != PM_DEV_OK) {
+        pm_set_error("edge-node quadrature: device check %d failed (leaf budget exceeded)", herr);
         return PM_ERR_INTERNAL;
     }
     return PM_OK;

@@ -47,6 +47,7 @@ class EdgeCurve:
     xo: np.ndarray         # [F M, 3]
     nuo: np.ndarray        # [F M, 3]
     wo: np.ndarray         # [F M] trapezoid weights (2 pi / (F M)) |gamma'|
+    speedo: np.ndarray     # [F M] |gamma'| at the oversampled points
 
 
 @dataclass
@@ -78,9 +79,10 @@ def _curve(theta, sign, M, F, R, r) -> EdgeCurve:
     to = 2 * np.pi * np.arange(F * M) / (F * M)
     x, d1, d2, nu = geo(t)
     xo, d1o, _, nuo = geo(to)
+    so = np.linalg.norm(d1o, axis=1)
     return EdgeCurve(theta=theta, sign=sign, M=M, F=F, t=t, x=x, d1=d1, d2=d2, nu=nu,
                      w=(2 * np.pi / M) * np.linalg.norm(d1, axis=1), to=to, xo=xo, nuo=nuo,
-                     wo=(2 * np.pi / (F * M)) * np.linalg.norm(d1o, axis=1))
+                     wo=(2 * np.pi / (F * M)) * so, speedo=so)
 
 
 def torus_band(n_band: int, n_phi: int, p: int, M: int, F: int = 16, theta0: float = 0.0,
@@ -157,3 +159,19 @@ def newtonian_neumann(osurf: OpenSurface, coeff: Coefficient, x0=(-3.0, -3.0, 4.
         re = np.linalg.norm(de, axis=1)
         fg.append(np.sum(c.nu * de, 1) / re ** 3)
     return f, np.concatenate(fg), v
+
+
+def edge_patches(osurf: OpenSurface):
+    """(patch [Me], (u, v) [Me, 2]): the patch whose outer edge holds each edge node and the
+    node's reference coordinates there (u = -1 on the first circle, +1 on the second)."""
+    s = osurf.surface
+    nb, nphi = s.params["n_band"], s.params["n_phi"]
+    dph = 2 * np.pi / nphi
+    patch, uv = [], []
+    for ci, c in enumerate(osurf.curves):
+        b = np.floor(c.t / dph).astype(int)
+        v0 = (c.t - (b + 0.5) * dph) / (0.5 * dph)
+        a = 0 if ci == 0 else nb - 1
+        patch.append(a * nphi + b)
+        uv.append(np.stack([np.full(c.M, -1.0 if ci == 0 else 1.0), v0], 1))
+    return np.concatenate(patch).astype(np.int32), np.concatenate(uv)
