@@ -844,6 +844,47 @@ def run_paper(args, dev):
     return out
 
 
+def run_bvp(args, dev):
+    """Open-surface Neumann problems (Sec. 5.2): torus bands (R = 2, r = 0.7, theta in
+    [0, n_band pi/8]) with a = exp(0.2 x + 0.3 z), the manufactured Newtonian solution
+    u = -1/|x - x0|; edge nodes M per circle, Fourier oversampling F = 16.  Reports the
+    edge quadrature build, the float64 GMRES solve to 1e-12 and u's error against the
+    exact solution (up to the additive constant)."""
+    import numpy as np
+    import paper_2401_12501_gb300 as pm
+    from workloads.bvp import band_coefficient, edge_a, edge_patches, newtonian_neumann, torus_band
+    ctx = pm.Context(dev.index or 0)
+    out = {"problem": "Neumann, eq. NeuBVPsystem; float64", "cases": {}}
+    for nb, nphi, p, M in ((2, 4, 8, 32), (4, 8, 8, 64), (8, 16, 8, 128)):
+        os_ = torus_band(nb, nphi, p, M, 16)
+        co = band_coefficient(os_)
+        t0 = time.perf_counter()
+        s = pm.Surface.from_fixture(ctx, os_.surface)
+        s.set_coeff(co.a, co.grad_a)
+        t1 = time.perf_counter()
+        patch, uv = edge_patches(os_)
+        b = pm.NeumannBVP(s, os_.curves, edge_a(os_), edge_a(os_, True), patch, uv)
+        t2 = time.perf_counter()
+        f, fg, v = newtonian_neumann(os_, co)
+        b.solve(f, fg, tol=1e-12)
+        t3 = time.perf_counter()
+        u, info, _, _ = b.solve(f, fg, tol=1e-12)
+        t4 = time.perf_counter()
+        w = os_.surface.weights
+        e = (u - v) - np.dot(w, u - v) / w.sum()
+        vv = v - np.dot(w, v) / w.sum()
+        out["cases"][f"band_{s.N}_edge_{b.Me}"] = {
+            "N": s.N, "edge_nodes": b.Me, "oversampled": 16 * b.Me,
+            "surface_build_s": round(t1 - t0, 3), "edge_build_s": round(t2 - t1, 4),
+            "solve_s": round(t4 - t3, 4), "iterations": info.iterations,
+            "residual": info.residual,
+            "rel_l2_error_vs_exact": float(np.sqrt(np.dot(w, e * e) / np.dot(w, vv * vv)))}
+        b.close()
+        s.close()
+    ctx.close()
+    return out
+
+
 def run_triangles(args, dev):
     """Triangle patches (Sec. 6.1, the paper's own discretisation): the unit sphere
     from 320 and 1,280 icosahedral triangles at the order-8 Vioreanu-Rokhlin nodes
@@ -1324,9 +1365,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in launch shapes (for profiler runs, whose timings "
                          "would mislead the autotuner)")
-    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper,helmholtz,triangles",
+    ap.add_argument("--extras", default="ellipsoid,batched,fmm,served,paper,helmholtz,triangles,bvp",
                     help="comma-separated extra measurements to run (ellipsoid, batched, fmm, "
-                         "served, paper, helmholtz, triangles)")
+                         "served, paper, helmholtz, triangles, bvp)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FMM and served measurements")
     ap.add_argument("--serve-requests", type=int, default=1000)
@@ -1399,7 +1440,8 @@ def main():
                               ("fmm", "fmm_torus_98304", run_fmm), ("served", "served", run_served),
                               ("paper", "paper_problems", run_paper),
                               ("helmholtz", "helmholtz_c_nonzero", run_helmholtz),
-                              ("triangles", "triangle_patches", run_triangles)):
+                              ("triangles", "triangle_patches", run_triangles),
+                              ("bvp", "boundary_value_problems", run_bvp)):
             if name not in want:
                 continue
             try:

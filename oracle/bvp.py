@@ -90,9 +90,10 @@ def kprime_from_sources(xe, nue, xs, a_src):
 
 
 # ---------------------------------------------------------------- K'_Gamma corrections
-def _edge_polar_points(u0, v0, n_theta=24, n_rho=32, max_width=np.pi / 8):
-    """Polar rule about (u0, v0) on the boundary of [-1, 1]^2 over the directions that
-    enter the square: points (u, v) and weights (omega_theta omega_rho rho)."""
+def _edge_theta_rule(u0, v0, n_theta=24, max_width=np.pi / 8):
+    """Directions entering [-1, 1]^2 from (u0, v0) on its boundary: Gauss-Legendre in
+    theta on panels cut at the corner directions, at most max_width wide; returns
+    (cos theta, sin theta, weights, ray length L(theta) to the boundary)."""
     corners = np.array([[1.0, 1.0], [-1.0, 1.0], [-1.0, -1.0], [1.0, -1.0]])
     if abs(u0 + 1) < 1e-14:
         lo, hi = -np.pi / 2, np.pi / 2
@@ -111,25 +112,38 @@ def _edge_polar_points(u0, v0, n_theta=24, n_rho=32, max_width=np.pi / 8):
                 cuts.append(tt)
     cuts = np.sort(np.array(cuts))
     xt, wt = leggauss(n_theta)
-    xr, wr = leggauss(n_rho)
-    U, V, W = [], [], []
+    TH, WT = [], []
     for a, b in zip(cuts[:-1], cuts[1:]):
         nsub = max(1, int(np.ceil((b - a) / max_width)))
         edges = np.linspace(a, b, nsub + 1)
         for s0, s1 in zip(edges[:-1], edges[1:]):
-            th = 0.5 * (s0 + s1) + 0.5 * (s1 - s0) * xt
-            wth = 0.5 * (s1 - s0) * wt
-            ct, st = np.cos(th), np.sin(th)
-            with np.errstate(divide="ignore"):
-                Lu = np.where(ct > 0, (1 - u0) / ct, np.where(ct < 0, (-1 - u0) / ct, np.inf))
-                Lv = np.where(st > 0, (1 - v0) / st, np.where(st < 0, (-1 - v0) / st, np.inf))
-            L = np.minimum(Lu, Lv)
-            for q in range(n_theta):
-                rho = 0.5 * L[q] * (1 + xr)
-                U.append(u0 + rho * ct[q])
-                V.append(v0 + rho * st[q])
-                W.append(wth[q] * 0.5 * L[q] * wr * rho)
+            TH.append(0.5 * (s0 + s1) + 0.5 * (s1 - s0) * xt)
+            WT.append(0.5 * (s1 - s0) * wt)
+    th, wth = np.concatenate(TH), np.concatenate(WT)
+    ct, st = np.cos(th), np.sin(th)
+    with np.errstate(divide="ignore"):
+        Lu = np.where(ct > 0, (1 - u0) / ct, np.where(ct < 0, (-1 - u0) / ct, np.inf))
+        Lv = np.where(st > 0, (1 - v0) / st, np.where(st < 0, (-1 - v0) / st, np.inf))
+    return ct, st, wth, np.minimum(Lu, Lv)
+
+
+def _polar_points(u0, v0, ct, st, wth, L, panels, n_rho):
+    """Points (u, v) and weights (omega_theta omega_rho rho) with the radius on the
+    panels [a L, b L] of the given fractions."""
+    xr, wr = leggauss(n_rho)
+    U, V, W = [], [], []
+    for a, b in panels:
+        rho = (0.5 * (a + b) + 0.5 * (b - a) * xr)[None, :] * L[:, None]
+        U.append((u0 + rho * ct[:, None]).ravel())
+        V.append((v0 + rho * st[:, None]).ravel())
+        W.append(((0.5 * (b - a) * wr)[None, :] * L[:, None] * rho * wth[:, None]).ravel())
     return np.concatenate(U), np.concatenate(V), np.concatenate(W)
+
+
+def _edge_polar_points(u0, v0, n_theta=24, n_rho=32, max_width=np.pi / 8):
+    """Polar rule about (u0, v0) on the boundary of [-1, 1]^2 over the directions that
+    enter the square, one radial panel: points (u, v) and weights."""
+    return _polar_points(u0, v0, *_edge_theta_rule(u0, v0, n_theta, max_width), [(0.0, 1.0)], n_rho)
 
 
 def _kp_integrand(patch: PatchInterpolant, u, v, xe, nue):
@@ -139,6 +153,58 @@ def _kp_integrand(patch: PatchInterpolant, u, v, xe, nue):
     _, J, Lu, Lv = patch.evaluate(u, v)
     k = INV_2PI * (d @ nue) / r2 * J
     return (k[:, None, None] * Lu[:, :, None] * Lv[:, None, :]).reshape(len(u), -1)
+
+
+def _edge_polar_points_graded(u0, v0, levels=18, n_theta=24, n_rho=16, max_width=np.pi / 8):
+    """As _edge_polar_points with the radius on dyadic panels [2^-(k+1), 2^-k] L,
+    k < levels, and [0, 2^-levels L]: for integrands with a log r factor."""
+    edges = [0.0] + [2.0 ** (k - levels) for k in range(levels + 1)]
+    return _polar_points(u0, v0, *_edge_theta_rule(u0, v0, n_theta, max_width),
+                         list(zip(edges[:-1], edges[1:])), n_rho)
+
+
+def _k_integrand(patch: PatchInterpolant, u, v, xt):
+    """log|x_t - y| / (2 pi) J(u, v) times the tensor basis, [Q, p*p]."""
+    d = patch.offsets(u, v, xt)
+    r2 = np.sum(d * d, axis=1)
+    _, J, Lu, Lv = patch.evaluate(u, v)
+    k = INV_2PI * 0.5 * np.log(r2) * J
+    return (k[:, None, None] * Lu[:, :, None] * Lv[:, None, :]).reshape(len(u), -1)
+
+
+def k_edge_self_weights(patch: PatchInterpolant, u0, v0, **rule):
+    """W_k = int_patch log|x - y| / (2 pi) l_k J du dv about the patch's edge point
+    x = y~(u0, v0) (Dirichlet trace row, K_Gamma on gamma)."""
+    xt = patch.evaluate(np.array([u0]), np.array([v0]))[0][0]
+    u, v, w = _edge_polar_points_graded(u0, v0, **rule)
+    return w @ _k_integrand(patch, u, v, xt)
+
+
+def k_edge_near_weights(patch: PatchInterpolant, xe, tol=1e-13, max_depth=18):
+    """Adaptive subdivision for the log kernel (16 x 16 Gauss per square)."""
+    g, gw = leggauss(16)
+
+    def square(u0, u1, v0, v1):
+        uu = 0.5 * (u0 + u1) + 0.5 * (u1 - u0) * g
+        vv = 0.5 * (v0 + v1) + 0.5 * (v1 - v0) * g
+        U, V = np.meshgrid(uu, vv, indexing="ij")
+        Wq = np.outer(gw, gw).ravel() * 0.25 * (u1 - u0) * (v1 - v0)
+        return Wq @ _k_integrand(patch, U.ravel(), V.ravel(), xe)
+
+    root = square(-1.0, 1.0, -1.0, 1.0)
+    scale = max(np.max(np.abs(root)), 1e-300)
+
+    def rec(sq, est, depth):
+        u0, u1, v0, v1 = sq
+        um, vm = 0.5 * (u0 + u1), 0.5 * (v0 + v1)
+        kids = ((u0, um, v0, vm), (um, u1, v0, vm), (u0, um, vm, v1), (um, u1, vm, v1))
+        ests = [square(*k) for k in kids]
+        tot = ests[0] + ests[1] + ests[2] + ests[3]
+        if depth >= max_depth or np.max(np.abs(tot - est)) <= tol * scale:
+            return tot
+        return sum(rec(k, e, depth + 1) for k, e in zip(kids, ests))
+
+    return rec((-1.0, 1.0, -1.0, 1.0), root, 1)
 
 
 def kp_self_weights(patch: PatchInterpolant, u0, v0, xe, nue, **rule):
@@ -282,3 +348,103 @@ class NeumannBVP:
         z = np.linalg.solve(A, np.concatenate([f, f_gamma]))
         sigma, mu = z[:self.N], z[self.N:]
         return sigma, mu, self.represent(sigma, mu)
+
+
+# ---------------------------------------------------------------- Dirichlet (Sec. 5.3)
+def double_layer_from_sources(x, xs, nus, a):
+    """nu(x') . grad_x' K(x, x') = -nu(x') . (x - x') / (2 pi a |x - x'|^2), constant a."""
+    d = x[:, None, :] - xs[None, :, :]
+    r2 = np.sum(d * d, axis=2)
+    r2 = np.where(r2 == 0.0, np.inf, r2)
+    return -INV_2PI * np.einsum("ijk,jk->ij", d, nus) / r2 / a
+
+
+def t_kernel_from_sources(disc: Discretization, xs, nus):
+    """T(x, x') = nu(x') . grad_x' R(x, x') for constant a (the a's of R cancel):
+    R = [(n.r)^2 / r^4 - H (n.r) / r^2] / pi with r = x - x', grad_x' = -grad_r."""
+    x, n, H = disc.x, disc.n, disc.H
+    r = x[:, None, :] - xs[None, :, :]
+    r2 = np.sum(r * r, axis=2)
+    nr = np.einsum("ijk,ik->ij", r, n)
+    nnu = n @ nus.T
+    rnu = np.einsum("ijk,jk->ij", r, nus)
+    return -INV_PI * (2 * nr * nnu / r2 ** 2 - 4 * nr ** 2 * rnu / r2 ** 3
+                      - H[:, None] * nnu / r2 + 2 * H[:, None] * nr * rnu / r2 ** 2)
+
+
+class DirichletBVP(NeumannBVP):
+    """Dense operators of the Dirichlet system of Sec. 5.3 for constant a:
+
+        sigma + R_Gamma[sigma] + T_gamma[mu]             = f        on Gamma
+        +mu / (2a) + K_Gamma[sigma] + N_gamma[mu]        = f_gamma  on gamma
+        u = K_Gamma[sigma] + N_gamma[mu]
+
+    (reading 28: the trace of the double layer from inside is +mu/(2a) plus its value
+    on gamma, and the system's second row has K_Gamma, as the trace theorem states).
+    T_gamma and N_gamma off gamma: oversampled trapezoid rule; N_gamma on gamma:
+    trapezoid rule with the diagonal limit -nu . gamma'' / (4 pi a |gamma'|^2); K_Gamma
+    at an edge node: smooth rule plus corrections, the graded polar rule on the edge
+    patch and the adaptive rule on the other near patches."""
+
+    def __init__(self, osurf, coeff, a_edge, a_over, near=None, processes=None, polar=None):
+        a0 = float(coeff.a[0])
+        if (np.max(np.abs(coeff.a - a0)) > 1e-14 * a0 or np.max(np.abs(coeff.grad_a)) > 0
+                or np.max(np.abs(np.asarray(a_edge) - a0)) > 1e-14 * a0):
+            raise ValueError("the Dirichlet system is built for a constant coefficient")
+        self.a0 = a0
+        super().__init__(osurf, coeff, a_edge, a_over, near=near, processes=processes, polar=polar)
+
+    def _build_edge(self):
+        N, M = self.N, self.M
+        d = self.disc
+        self.Tg = np.zeros((N, M))
+        self.Ng = np.zeros((N, M))
+        off = 0
+        for c in self.curves:
+            I = trig_interp_matrix(c.M, c.F)
+            self.Tg[:, off:off + c.M] = (t_kernel_from_sources(d, c.xo, c.nuo) * c.wo) @ I
+            self.Ng[:, off:off + c.M] = (double_layer_from_sources(d.x, c.xo, c.nuo, self.a0) * c.wo) @ I
+            off += c.M
+        Nd = double_layer_from_sources(self.xe, self.xe, self.nue, self.a0)
+        diag = []
+        for c in self.curves:
+            diag.append(-np.sum(c.nu * c.d2, 1) / (2 * np.sum(c.d1 * c.d1, 1)))
+        Nd[np.diag_indices(M)] = INV_2PI * np.concatenate(diag) / self.a0
+        self.Ngg = Nd * self.we[None, :]
+        KG = parametrix_from_sources(self.xe, d.x, d.a) * d.w[None, :]
+        self.KG = KG + self._k_corrections()
+
+    def _k_corrections(self):
+        d = self.disc
+        pp = d.p * d.p
+        C = np.zeros((self.M, self.N))
+        for e in range(self.M):
+            xe = self.xe[e]
+            P0, u0, v0 = self.edge_patch(e)
+            dist = np.linalg.norm(d.centroid - xe, axis=1)
+            near = sorted(set([P0] + [int(P) for P in np.nonzero(dist < NEAR_FACTOR * d.radius)[0]]))
+            for P in near:
+                if P == P0:
+                    W = k_edge_self_weights(d.patches[P], u0, v0)
+                else:
+                    W = k_edge_near_weights(d.patches[P], xe)
+                k = np.arange(P * pp, (P + 1) * pp)
+                C[e, k] += W / d.a[k] - d.w[k] * parametrix_from_sources(xe[None], d.x[k], d.a[k])[0]
+        return C
+
+    def matrix(self):
+        N, M = self.N, self.M
+        A = np.zeros((N + M, N + M))
+        A[:N, :N] = self.disc.smooth_matrix("R") + self.near.dense("R") + np.eye(N)
+        A[:N, N:] = self.Tg
+        A[N:, :N] = self.KG
+        A[N:, N:] = self.Ngg + np.diag(0.5 / self.a_edge)
+        return A
+
+    def apply(self, sigma, mu):
+        top = sigma + apply_R(self.disc, self.near, sigma) + self.Tg @ mu
+        bot = self.KG @ sigma + self.Ngg @ mu + 0.5 * mu / self.a_edge
+        return top, bot
+
+    def represent(self, sigma, mu):
+        return apply_K(self.disc, self.near, sigma) + self.Ng @ mu

@@ -175,3 +175,25 @@ def edge_patches(osurf: OpenSurface):
         patch.append(a * nphi + b)
         uv.append(np.stack([np.full(c.M, -1.0 if ci == 0 else 1.0), v0], 1))
     return np.concatenate(patch).astype(np.int32), np.concatenate(uv)
+
+
+def constant_band_coefficient(osurf: OpenSurface, value: float = 1.0) -> Coefficient:
+    s = osurf.surface
+    return Coefficient("constant", np.full(s.N, float(value)), np.zeros((s.N, 3)))
+
+
+def newtonian_dirichlet(osurf: OpenSurface, value: float = 1.0, x0=(-3.0, -3.0, 4.0)):
+    """(f [N], f_gamma [M total], v at the nodes [N]) for u = v = -1/|x - x0| and the
+    constant coefficient a = value: f = a Lap_Gamma v, f_gamma = v on gamma."""
+    s = osurf.surface
+    x0 = np.asarray(x0, dtype=np.float64)
+    d = s.nodes - x0
+    rho = np.linalg.norm(d, axis=1)
+    v = -1.0 / rho
+    grad = d / rho[:, None] ** 3
+    n = s.normals
+    dn = np.sum(grad * n, 1)
+    dnn = 1.0 / rho ** 3 - 3.0 * np.sum(d * n, 1) ** 2 / rho ** 5
+    f = value * (-2.0 * s.curvature * dn - dnn)
+    fg = np.concatenate([-1.0 / np.linalg.norm(c.x - x0, axis=1) for c in osurf.curves])
+    return f, fg, v
