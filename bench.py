@@ -845,36 +845,50 @@ def run_paper(args, dev):
 
 
 def run_bvp(args, dev):
-    """Open-surface Neumann problems (Sec. 5.2): torus bands (R = 2, r = 0.7, theta in
-    [0, n_band pi/8]) with a = exp(0.2 x + 0.3 z), the manufactured Newtonian solution
-    u = -1/|x - x0|; edge nodes M per circle, Fourier oversampling F = 16.  Reports the
-    edge quadrature build, the float64 GMRES solve to 1e-12 and u's error against the
-    exact solution (up to the additive constant)."""
+    """Open-surface problems (Sec. 5): torus bands (R = 2, r = 0.7, theta in [0, n_band
+    pi/8]), the manufactured Newtonian solution u = -1/|x - x0|; Neumann with
+    a = exp(0.2 x + 0.3 z) and Fourier oversampling F = 16, Dirichlet with a = 1 and
+    F = 32; edge nodes M per circle.  Reports the edge quadrature build, the float64
+    GMRES solve to 1e-12 and u's error against the exact solution (Neumann: up to the
+    additive constant)."""
     import numpy as np
     import paper_2401_12501_gb300 as pm
-    from workloads.bvp import band_coefficient, edge_a, edge_patches, newtonian_neumann, torus_band
+    from workloads.bvp import (band_coefficient, constant_band_coefficient, edge_a, edge_patches,
+                               newtonian_dirichlet, newtonian_neumann, torus_band)
     ctx = pm.Context(dev.index or 0)
-    out = {"problem": "Neumann, eq. NeuBVPsystem; float64", "cases": {}}
-    for nb, nphi, p, M in ((2, 4, 8, 32), (4, 8, 8, 64), (8, 16, 8, 128)):
-        os_ = torus_band(nb, nphi, p, M, 16)
-        co = band_coefficient(os_)
+    out = {"problem": "Neumann (eq. NeuBVPsystem, a = exp(0.2 x + 0.3 z)) and Dirichlet "
+                      "(eq. DirBVPsystem, a = 1); float64", "cases": {}}
+    for kind, F in (("neumann", 16), ("dirichlet", 32)):
+      for nb, nphi, p, M in ((2, 4, 8, 32), (4, 8, 8, 64), (8, 16, 8, 128)):
+        os_ = torus_band(nb, nphi, p, M, F)
+        co = band_coefficient(os_) if kind == "neumann" else constant_band_coefficient(os_)
         t0 = time.perf_counter()
         s = pm.Surface.from_fixture(ctx, os_.surface)
         s.set_coeff(co.a, co.grad_a)
         t1 = time.perf_counter()
         patch, uv = edge_patches(os_)
-        b = pm.NeumannBVP(s, os_.curves, edge_a(os_), edge_a(os_, True), patch, uv)
+        if kind == "neumann":
+            ae, ao = edge_a(os_), edge_a(os_, True)
+        else:
+            ae, ao = np.ones(os_.M), np.ones(F * os_.M)
+        b = pm.BoundaryValueProblem(s, os_.curves, ae, ao, patch, uv, kind=kind)
         t2 = time.perf_counter()
-        f, fg, v = newtonian_neumann(os_, co)
+        if kind == "neumann":
+            f, fg, v = newtonian_neumann(os_, co)
+        else:
+            f, fg, v = newtonian_dirichlet(os_)
         b.solve(f, fg, tol=1e-12)
         t3 = time.perf_counter()
         u, info, _, _ = b.solve(f, fg, tol=1e-12)
         t4 = time.perf_counter()
         w = os_.surface.weights
-        e = (u - v) - np.dot(w, u - v) / w.sum()
-        vv = v - np.dot(w, v) / w.sum()
-        out["cases"][f"band_{s.N}_edge_{b.Me}"] = {
-            "N": s.N, "edge_nodes": b.Me, "oversampled": 16 * b.Me,
+        if kind == "neumann":
+            e = (u - v) - np.dot(w, u - v) / w.sum()
+            vv = v - np.dot(w, v) / w.sum()
+        else:
+            e, vv = u - v, v
+        out["cases"][f"{kind}_band_{s.N}_edge_{b.Me}"] = {
+            "N": s.N, "edge_nodes": b.Me, "oversampled": F * b.Me,
             "surface_build_s": round(t1 - t0, 3), "edge_build_s": round(t2 - t1, 4),
             "solve_s": round(t4 - t3, 4), "iterations": info.iterations,
             "residual": info.residual,

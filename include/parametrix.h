@@ -338,12 +338,14 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
                    pm_solve_info* info, void* stream);
 
 /*
- * Open-surface Neumann boundary-value problem (Sec. 5.2, eq. NeuBVPsystem):
- * div_Gamma(a grad_Gamma u) = f on an open surface Gamma, nu . grad_Gamma u = f_gamma
- * on its boundary gamma.  s is a surface built by pm_surface_create from Gamma's
- * quadrilateral patches (its nodes interior to the patches) with
- * pm_surface_set_coeff done (c = 0); it must outlive the handle.  gamma is ncurves
- * closed curves; curve c is given at M[c] >= 2 edge nodes, the points at
+ * Open-surface boundary-value problems (Sec. 5): div_Gamma(a grad_Gamma u) = f on an
+ * open surface Gamma with, on its boundary gamma, Neumann data nu . grad_Gamma u =
+ * f_gamma (kind = PM_BVP_NEUMANN, Sec. 5.2, eq. NeuBVPsystem) or Dirichlet data
+ * u = f_gamma (kind = PM_BVP_DIRICHLET, Sec. 5.3, eq. DirBVPsystem; a constant, as the
+ * paper's compactness theorem for T_gamma requires).  s is a surface built by
+ * pm_surface_create from Gamma's quadrilateral patches (its nodes interior to the
+ * patches) with pm_surface_set_coeff done (c = 0); it must outlive the handle.  gamma
+ * is ncurves closed curves; curve c is given at M[c] >= 2 edge nodes, the points at
  * t_k = 2 pi (k + 1/2) / M[c] of a 2 pi-periodic parameter t, and at F[c] M[c]
  * oversampled points t_j = 2 pi j / (F[c] M[c]) (Sec. 6.1.4's Fourier oversampling),
  * curve after curve.  Me = sum M[c] edge nodes (at most 4,096), Fo = sum F[c] M[c]
@@ -353,21 +355,28 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  *   from Gamma), edge_a [Me] = a > 0 at the node, edge_patch [Me] the patch whose
  *   edge holds the node and edge_uv [Me][2] the node's reference coordinates there
  *   (one of them -1 or +1; nodes should avoid patch corners);
- *   over_x [Fo][3], over_speed [Fo] = |dgamma/dt|, over_a [Fo] = a at the points.
- * The system takes sigma at the surface's N nodes and mu at the Me edge nodes:
- *   sigma + R~ sigma + R_gamma mu = f,  -mu/(2a) + K'_Gamma sigma + K'_gamma mu + sum_k w_k mu_k = f_gamma,
- * u = K~ sigma + K_gamma mu, all in float64 (the rank-one term, w_k the trapezoid
- * weights, removes the null space of the Neumann problem: u is unique up to a
- * constant).  Creation computes the K'_Gamma quadrature of every edge node on the
- * device.  PM_ERR_INVALID_ARG for NULL arguments, bad sizes or an edge node not on
- * an edge of its patch; PM_ERR_NO_COEFF without a coefficient.
+ *   over_x [Fo][3], over_nu [Fo][3] (binormal), over_speed [Fo] = |dgamma/dt|,
+ *   over_a [Fo] = a at the oversampled points.
+ * The systems take sigma at the surface's N nodes and mu at the Me edge nodes:
+ *   Neumann:   sigma + R~ sigma + R_gamma mu = f,
+ *              -mu/(2a) + K'_Gamma sigma + K'_gamma mu + sum_k w_k mu_k = f_gamma,
+ *              u = K~ sigma + K_gamma mu  (the rank-one term, w_k the trapezoid
+ *              weights, removes the Neumann null space: u is unique up to a constant);
+ *   Dirichlet: sigma + R~ sigma + T_gamma mu = f,  +mu/(2a) + K~ sigma + N_gamma mu = f_gamma,
+ *              u = K~ sigma + N_gamma mu,
+ * all in float64.  Creation computes the surface quadrature of every edge node on the
+ * device.  PM_ERR_INVALID_ARG for NULL arguments, an unknown kind, bad sizes, an edge
+ * node not on an edge of its patch or a non-constant a for Dirichlet; PM_ERR_NO_COEFF
+ * without a coefficient.
  */
+#define PM_BVP_NEUMANN 0
+#define PM_BVP_DIRICHLET 1
 typedef struct pm_bvp pm_bvp;
-pm_status pm_bvp_create(pm_surface* s, int ncurves, const int* M, const int* F,
+pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const int* M, const int* F,
                         const double* edge_x, const double* edge_d1, const double* edge_d2,
                         const double* edge_nu, const double* edge_a, const int* edge_patch,
-                        const double* edge_uv, const double* over_x, const double* over_speed,
-                        const double* over_a, pm_bvp** out);
+                        const double* edge_uv, const double* over_x, const double* over_nu,
+                        const double* over_speed, const double* over_a, pm_bvp** out);
 void pm_bvp_destroy(pm_bvp* b);
 
 /* The system's operator on host arrays sigma [N], mu [Me] (rank-one term included):

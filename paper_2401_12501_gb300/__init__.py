@@ -341,18 +341,22 @@ class Surface:
         return out + (sig,) if return_sigma else out
 
 
-class NeumannBVP:
-    """pm_bvp_*: the Neumann boundary-value system of an open surface (Sec. 5.2).
+class BoundaryValueProblem:
+    """pm_bvp_*: the Neumann (Sec. 5.2) or, for constant a, Dirichlet (Sec. 5.3)
+    boundary-value system of an open surface; kind "neumann" or "dirichlet".
 
     surface: a Surface built from the open surface's patches, with its coefficient set.
     curves: boundary curves, each with attributes M, F (edge nodes and oversampling
     factor), x, d1, d2, nu [M, 3] (point, dgamma/dt, d2gamma/dt2, binormal at
-    t_k = 2 pi (k + 1/2) / M), xo [F M, 3], speedo [F M] (|dgamma/dt| at
-    t_j = 2 pi j / (F M)); edge_a [Me], over_a [Fo]: a at the edge nodes and the
-    oversampled points; edge_patch [Me], edge_uv [Me, 2]: each edge node's patch and
-    reference coordinates on that patch's edge."""
+    t_k = 2 pi (k + 1/2) / M), xo, nuo [F M, 3], speedo [F M] (point, binormal and
+    |dgamma/dt| at t_j = 2 pi j / (F M)); edge_a [Me], over_a [Fo]: a at the edge nodes
+    and the oversampled points; edge_patch [Me], edge_uv [Me, 2]: each edge node's
+    patch and reference coordinates on that patch's edge."""
 
-    def __init__(self, surface: "Surface", curves, edge_a, over_a, edge_patch, edge_uv):
+    KINDS = {"neumann": 0, "dirichlet": 1}
+
+    def __init__(self, surface: "Surface", curves, edge_a, over_a, edge_patch, edge_uv,
+                 kind: str = "neumann"):
         cat = lambda name: np.ascontiguousarray(                     # noqa: E731
             np.concatenate([np.asarray(getattr(c, name), np.float64).reshape(-1) for c in curves]))
         self.surface = surface
@@ -362,15 +366,18 @@ class NeumannBVP:
             F=np.ascontiguousarray([c.F for c in curves], dtype=np.int32),
             x=cat("x"), d1=cat("d1"), d2=cat("d2"), nu=cat("nu"),
             a=_f64(edge_a, self.Me), patch=np.ascontiguousarray(edge_patch, dtype=np.int32),
-            uv=_f64(edge_uv, 2 * self.Me), xo=cat("xo"), so=cat("speedo"),
+            uv=_f64(edge_uv, 2 * self.Me), xo=cat("xo"), nuo=cat("nuo"), so=cat("speedo"),
             ao=np.ascontiguousarray(over_a, dtype=np.float64))
         k = self._keep
         h = C.c_void_p()
-        check(_lib.lib().pm_bvp_create(surface.handle, len(curves), ptr(k["M"]), ptr(k["F"]),
-                                       ptr(k["x"]), ptr(k["d1"]), ptr(k["d2"]), ptr(k["nu"]),
-                                       ptr(k["a"]), ptr(k["patch"]), ptr(k["uv"]), ptr(k["xo"]),
-                                       ptr(k["so"]), ptr(k["ao"]), C.byref(h)), "pm_bvp_create")
+        self.handle = None
+        check(_lib.lib().pm_bvp_create(surface.handle, self.KINDS[kind], len(curves), ptr(k["M"]),
+                                       ptr(k["F"]), ptr(k["x"]), ptr(k["d1"]), ptr(k["d2"]),
+                                       ptr(k["nu"]), ptr(k["a"]), ptr(k["patch"]), ptr(k["uv"]),
+                                       ptr(k["xo"]), ptr(k["nuo"]), ptr(k["so"]), ptr(k["ao"]),
+                                       C.byref(h)), "pm_bvp_create")
         self.handle = h
+        self.kind = kind
 
     def apply(self, sigma, mu):
         sigma = _f64(sigma, self.surface.N)
@@ -394,6 +401,9 @@ class NeumannBVP:
         if self.handle:
             _lib.lib().pm_bvp_destroy(self.handle)
             self.handle = None
+
+
+NeumannBVP = BoundaryValueProblem      # the default kind
 
 
 def solve_multi(surfaces, rhs, tol=1e-10, maxit=2000, project_rhs=False, stream=None):

@@ -23,6 +23,7 @@ PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF, PM_PREC_FMM = 0, 1, 2, 
 PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
 PM_SOLVE_PROJECT_RHS = 1
 PM_SOLVE_DEVICE_PTRS = 2
+PM_BVP_NEUMANN, PM_BVP_DIRICHLET = 0, 1
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA",
                 4: "PM_ERR_NOT_CONVERGED", 5: "PM_ERR_BREAKDOWN",
@@ -154,7 +155,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.pm_surface_store_ff.argtypes = [P, C.c_int]
     lib.pm_surface_stored_ff.argtypes = [P]
     lib.pm_surface_stored_ff.restype = C.c_int
-    lib.pm_bvp_create.argtypes = [P, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, C.POINTER(P)]
+    lib.pm_bvp_create.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P, P, P, P, P, P, P, P, P,
+                                  C.POINTER(P)]
     lib.pm_bvp_destroy.argtypes = [P]
     lib.pm_bvp_destroy.restype = None
     lib.pm_bvp_apply.argtypes = [P, P, P, P, P]

@@ -1,4 +1,5 @@
-// Neumann boundary-value system on an open surface (Sec. 5.2, eq. NeuBVPsystem).
+// Boundary-value systems on an open surface: Neumann (Sec. 5.2, eq. NeuBVPsystem) and,
+// for a constant coefficient, Dirichlet (Sec. 5.3, eq. DirBVPsystem).
 //
 // Gamma is a surface built from an open surface's patches (pm_surface_create +
 // pm_surface_set_coeff); its boundary gamma is a union of closed curves given at
@@ -13,6 +14,21 @@
 // at edge nodes (nu the binormal).  The rank-one term removes the one-dimensional null
 // space (constants solve the homogeneous Neumann problem); any multiple of it gives the
 // same u up to a constant for consistent data.
+//
+// Dirichlet, a constant (the paper proves T_gamma compact for constant a only):
+//
+//   sigma + R~_Gamma sigma + T_gamma mu                 = f        (surface rows)
+//   +mu / (2a) + K~_Gamma sigma + N_gamma mu            = f_gamma  (edge rows: the trace)
+//   u = K~_Gamma sigma + N_gamma mu
+//
+// N_gamma the double layer nu(x') . grad_x' K, T_gamma = nu(x') . grad_x' R; the trace of
+// the double layer from inside is +mu/(2a) plus its value on gamma (the paper prints
+// -mu/(2a); Gauss's lemma fixes the sign), and the edge row carries K_Gamma[sigma], as
+// the trace theorem states (the printed system writes N_Gamma there).  K~_Gamma at the
+// edge nodes: smooth rule plus corrections (polar rule with dyadic radial panels on the
+// edge patch, quadtree near rule on the others); N_gamma on gamma: trapezoid rule, its
+// diagonal the limit -nu . gamma'' / (4 pi a |gamma'|^2); T_gamma and N_gamma off gamma:
+// the oversampled trapezoid rule.
 //
 // Discretisation (Sec. 6.1.4 with the surface rules of Sec. 6.1):
 // * R~_Gamma, K~_Gamma: the surface's float64 applies (smooth sums + near corrections).
@@ -35,21 +51,22 @@
 
 pm_status pm_bvp_kp_weights(pm_surface* s, int nb, const int* blk_edge, const int* blk_patch,
                             const int* blk_own, const double* xe, const double* nue,
-                            const double* uv, double* W);
+                            const double* uv, int log_kernel, double* W);
 
 struct pm_bvp {
     pm_surface* s = nullptr;
+    int kind = 0;                        // 0 Neumann, 1 Dirichlet
     int N = 0, Me = 0, Fo = 0, ncurves = 0;
     std::vector<int> M, F, off, offo;
     std::vector<double> h_we;
     double *xe = nullptr, *nue = nullptr, *we = nullptr, *ae = nullptr, *uv = nullptr;
-    double *xo = nullptr, *wo = nullptr, *ao = nullptr;
+    double *xo = nullptr, *wo = nullptr, *ao = nullptr, *nuo = nullptr;
     double *interp = nullptr;            // per curve [F M][M], curve blocks concatenated
     int *interp_off = nullptr;           // [ncurves + 1] offsets into interp
     int *curve_of = nullptr;             // [Fo] curve of an oversampled point
-    double *Kpg = nullptr;               // [Me][Me] K'_gamma with weights
+    double *Kpg = nullptr;               // [Me][Me] K'_gamma (Neumann) or N_gamma (Dirichlet), weighted
     int *kp_ptr = nullptr, *kp_patch = nullptr;
-    double *kp_C = nullptr;              // [nblk][pp] K'_Gamma corrections
+    double *kp_C = nullptr;              // [nblk][pp] K'_Gamma (K_Gamma) corrections
     int kp_nblk = 0;
     double *mu_o = nullptr;              // [Fo]
     double *part = nullptr;              // dot partials
@@ -78,21 +95,28 @@ __global__ void k_bvp_interp(const double* __restrict__ I, const int* __restrict
     mu_o[j] = s;
 }
 
-// out[i] += sum_j (wo_j mu_o_j / ao_j) G(x_i, xo_j): WHICH_K = false the remainder
-// (target n, H, a, grad a), true the parametrix log r / (2 pi)
-template <bool WHICH_K>
+// out[i] += sum_j wo_j mu_o_j G(x_i, xo_j) with r = x_i - xo_j: KIND 0 the remainder
+// R / a(x') (target n, H, a, grad a), 1 the parametrix log r / (2 pi a(x')), 2 T =
+// nu' . grad' R for constant a (the a's cancel), 3 the double layer
+// -nu' . r / (2 pi a r^2)
+enum { kEdgeR = 0, kEdgeK = 1, kEdgeT = 2, kEdgeN = 3 };
+template <int KIND>
 __global__ void __launch_bounds__(kT)
 k_bvp_edge_to_surface(int N, const double* __restrict__ x, const double* __restrict__ n,
                       const double* __restrict__ H, const double* __restrict__ a,
                       const double* __restrict__ g, int Fo, const double* __restrict__ xo,
                       const double* __restrict__ wo, const double* __restrict__ ao,
-                      const double* __restrict__ mu_o, double* __restrict__ out) {
+                      const double* __restrict__ nuo, const double* __restrict__ mu_o,
+                      double* __restrict__ out) {
+    constexpr bool WHICH_K = KIND == kEdgeK || KIND == kEdgeN;
     __shared__ double sx[kTile], sy[kTile], sz[kTile], ss[kTile];
+    __shared__ double su[KIND >= kEdgeT ? kTile : 1], sv[KIND >= kEdgeT ? kTile : 1],
+        sw[KIND >= kEdgeT ? kTile : 1];
     const int i = blockIdx.x * kT + threadIdx.x;
     double xi0 = 0, xi1 = 0, xi2 = 0, n0 = 0, n1 = 0, n2 = 0, Hi = 0, ai = 0, g0 = 0, g1 = 0, g2 = 0;
     if (i < N) {
         xi0 = x[3 * i]; xi1 = x[3 * i + 1]; xi2 = x[3 * i + 2];
-        if (!WHICH_K) {
+        if (KIND == kEdgeR || KIND == kEdgeT) {
             n0 = n[3 * i]; n1 = n[3 * i + 1]; n2 = n[3 * i + 2];
             Hi = H[i]; ai = a[i];
             g0 = g[3 * i]; g1 = g[3 * i + 1]; g2 = g[3 * i + 2];
@@ -106,7 +130,12 @@ k_bvp_edge_to_surface(int N, const double* __restrict__ x, const double* __restr
             sx[threadIdx.x] = xo[3 * j];
             sy[threadIdx.x] = xo[3 * j + 1];
             sz[threadIdx.x] = xo[3 * j + 2];
-            ss[threadIdx.x] = wo[j] * mu_o[j] / ao[j];
+            ss[threadIdx.x] = KIND == kEdgeT ? wo[j] * mu_o[j] : wo[j] * mu_o[j] / ao[j];
+            if (KIND >= kEdgeT) {
+                su[threadIdx.x] = nuo[3 * j];
+                sv[threadIdx.x] = nuo[3 * j + 1];
+                sw[threadIdx.x] = nuo[3 * j + 2];
+            }
         }
         __syncthreads();
         const int cnt = min(kTile, Fo - base);
@@ -114,17 +143,31 @@ k_bvp_edge_to_surface(int N, const double* __restrict__ x, const double* __restr
             for (int q = 0; q < cnt; ++q) {
                 const double r0 = xi0 - sx[q], r1 = xi1 - sy[q], r2 = xi2 - sz[q];
                 const double rr = r0 * r0 + r1 * r1 + r2 * r2;
-                if (WHICH_K) {
+                if (KIND == kEdgeK) {
                     acc += ss[q] * log(rr);
-                } else {
+                } else if (KIND == kEdgeR) {
                     const double inv = 1.0 / rr;
                     const double qn = (n0 * r0 + n1 * r1 + n2 * r2) * inv;
                     acc += ss[q] * (ai * (qn * qn - Hi * qn) * (1.0 / M_PI) +
                                     (g0 * r0 + g1 * r1 + g2 * r2) * inv * (0.5 / M_PI));
+                } else if (KIND == kEdgeN) {
+                    acc -= ss[q] * (su[q] * r0 + sv[q] * r1 + sw[q] * r2) / rr;
+                } else {
+                    // -(1/pi) [2 (n.r)(n.nu')/r^4 - 4 (n.r)^2 (r.nu')/r^6 - H (n.nu')/r^2
+                    //          + 2 H (n.r)(r.nu')/r^4]
+                    const double inv = 1.0 / rr;
+                    const double nr = n0 * r0 + n1 * r1 + n2 * r2;
+                    const double nnu = n0 * su[q] + n1 * sv[q] + n2 * sw[q];
+                    const double rnu = r0 * su[q] + r1 * sv[q] + r2 * sw[q];
+                    acc -= ss[q] * inv * (2.0 * nr * nnu * inv - 4.0 * nr * nr * rnu * inv * inv -
+                                          Hi * nnu + 2.0 * Hi * nr * rnu * inv);
                 }
             }
     }
-    if (i < N) out[i] += WHICH_K ? acc * (0.25 / M_PI) : acc;
+    if (i < N)
+        out[i] += KIND == kEdgeK ? acc * (0.25 / M_PI)
+                  : KIND == kEdgeN ? acc * (0.5 / M_PI)
+                  : KIND == kEdgeT ? acc * (1.0 / M_PI) : acc;
 }
 
 __device__ double block_sum(double v, double* red) {
@@ -138,9 +181,11 @@ __device__ double block_sum(double v, double* red) {
     return t;
 }
 
-// edge rows: one block per edge node e
+// edge rows: one block per edge node e; Neumann (dirichlet = 0): K'_Gamma sigma +
+// K'_gamma mu - mu/(2a) + sum w mu; Dirichlet: K_Gamma sigma + N_gamma mu + mu/(2a)
 __global__ void __launch_bounds__(kT)
-k_bvp_edge_row(int N, int Me, int pp, const double* __restrict__ x, const double* __restrict__ wa,
+k_bvp_edge_row(int dirichlet, int N, int Me, int pp, const double* __restrict__ x,
+               const double* __restrict__ wa,
                const double* __restrict__ xe, const double* __restrict__ nue,
                const double* __restrict__ ae, const double* __restrict__ we,
                const int* __restrict__ kp_ptr, const int* __restrict__ kp_patch,
@@ -155,7 +200,7 @@ k_bvp_edge_row(int N, int Me, int pp, const double* __restrict__ x, const double
     for (int j = threadIdx.x; j < N; j += kT) {
         const double r0 = x0 - x[3 * j], r1 = x1 - x[3 * j + 1], r2 = x2 - x[3 * j + 2];
         const double rr = r0 * r0 + r1 * r1 + r2 * r2;
-        acc += wa[j] * sigma[j] * (n0 * r0 + n1 * r1 + n2 * r2) / rr;
+        acc += wa[j] * sigma[j] * (dirichlet ? 0.5 * log(rr) : (n0 * r0 + n1 * r1 + n2 * r2) / rr);
     }
     acc *= 0.5 / M_PI;
     for (int b = kp_ptr[e]; b < kp_ptr[e + 1]; ++b) {
@@ -163,13 +208,15 @@ k_bvp_edge_row(int N, int Me, int pp, const double* __restrict__ x, const double
         const double* sg = sigma + (size_t)kp_patch[b] * pp;
         for (int k = threadIdx.x; k < pp; k += kT) acc += C[k] * sg[k];
     }
-    for (int k = threadIdx.x; k < Me; k += kT) acc += (Kpg[(size_t)e * Me + k] + we[k]) * mu[k];
+    for (int k = threadIdx.x; k < Me; k += kT)
+        acc += (Kpg[(size_t)e * Me + k] + (dirichlet ? 0.0 : we[k])) * mu[k];
     const double t = block_sum(acc, red);
-    if (threadIdx.x == 0) out[e] = t - 0.5 * mu[e] / ae[e];
+    if (threadIdx.x == 0) out[e] = t + (dirichlet ? 0.5 : -0.5) * mu[e] / ae[e];
 }
 
-// C[b][k] = W[b][k] / a_k - w_k nu_e . (x_e - x_k) / (2 pi a_k |x_e - x_k|^2)
-__global__ void k_bvp_combine(int nblk, int pp, const int* __restrict__ blk_edge,
+// C[b][k] = W[b][k] / a_k - w_k G(x_e, x_k) / a_k with G = nu_e . (x_e - x_k) / (2 pi |.|^2)
+// (Neumann) or log|x_e - x_k| / (2 pi) (Dirichlet)
+__global__ void k_bvp_combine(int dirichlet, int nblk, int pp, const int* __restrict__ blk_edge,
                               const int* __restrict__ blk_patch, const double* __restrict__ x,
                               const double* __restrict__ a, const double* __restrict__ w,
                               const double* __restrict__ xe, const double* __restrict__ nue,
@@ -182,8 +229,9 @@ __global__ void k_bvp_combine(int nblk, int pp, const int* __restrict__ blk_edge
     const double r0 = xe[3 * e] - x[3 * j], r1 = xe[3 * e + 1] - x[3 * j + 1],
                  r2 = xe[3 * e + 2] - x[3 * j + 2];
     const double rr = r0 * r0 + r1 * r1 + r2 * r2;
-    const double smooth = w[j] * (nue[3 * e] * r0 + nue[3 * e + 1] * r1 + nue[3 * e + 2] * r2) /
-                          rr * (0.5 / M_PI) / a[j];
+    const double G = dirichlet ? 0.5 * log(rr)
+                               : (nue[3 * e] * r0 + nue[3 * e + 1] * r1 + nue[3 * e + 2] * r2) / rr;
+    const double smooth = w[j] * G * (0.5 / M_PI) / a[j];
     C[q] = C[q] / a[j] - smooth;
 }
 
@@ -244,9 +292,13 @@ pm_status apply_sys(pm_bvp* b, const double* z, double* out) {
             b->interp, b->interp_off, b->curve_of, b->interp_off + b->ncurves + 1,
             b->interp_off + 2 * (b->ncurves + 1), b->interp_off + 3 * (b->ncurves + 1), z + N,
             b->mu_o, b->Fo);
-        k_bvp_edge_to_surface<false><<<pm_ceil_div(N, kT), kT, 0, st>>>(
-            N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->mu_o, out);
-        k_bvp_edge_row<<<b->Me, kT, 0, st>>>(N, b->Me, s->pp, s->x, s->wa, b->xe, b->nue, b->ae,
+        if (b->kind)
+            k_bvp_edge_to_surface<kEdgeT><<<pm_ceil_div(N, kT), kT, 0, st>>>(
+                N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->nuo, b->mu_o, out);
+        else
+            k_bvp_edge_to_surface<kEdgeR><<<pm_ceil_div(N, kT), kT, 0, st>>>(
+                N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->nuo, b->mu_o, out);
+        k_bvp_edge_row<<<b->Me, kT, 0, st>>>(b->kind, N, b->Me, s->pp, s->x, s->wa, b->xe, b->nue, b->ae,
                                              b->we, b->kp_ptr, b->kp_patch, b->kp_C, b->Kpg, z,
                                              z + N, out + N);
     }
@@ -264,8 +316,12 @@ pm_status represent(pm_bvp* b, const double* z, double* u) {
             b->interp, b->interp_off, b->curve_of, b->interp_off + b->ncurves + 1,
             b->interp_off + 2 * (b->ncurves + 1), b->interp_off + 3 * (b->ncurves + 1), z + N,
             b->mu_o, b->Fo);
-        k_bvp_edge_to_surface<true><<<pm_ceil_div(N, kT), kT, 0, st>>>(
-            N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->mu_o, u);
+        if (b->kind)
+            k_bvp_edge_to_surface<kEdgeN><<<pm_ceil_div(N, kT), kT, 0, st>>>(
+                N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->nuo, b->mu_o, u);
+        else
+            k_bvp_edge_to_surface<kEdgeK><<<pm_ceil_div(N, kT), kT, 0, st>>>(
+                N, s->x, s->n, s->H, s->a, s->g, b->Fo, b->xo, b->wo, b->ao, b->nuo, b->mu_o, u);
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -275,7 +331,8 @@ void free_bvp(pm_bvp* b) {
     if (!b) return;
     if (b->s) cudaSetDevice(b->s->ctx->device);
     pm_dfree(b->xe); pm_dfree(b->nue); pm_dfree(b->we); pm_dfree(b->ae); pm_dfree(b->uv);
-    pm_dfree(b->xo); pm_dfree(b->wo); pm_dfree(b->ao); pm_dfree(b->interp); pm_dfree(b->interp_off);
+    pm_dfree(b->xo); pm_dfree(b->wo); pm_dfree(b->ao); pm_dfree(b->nuo); pm_dfree(b->interp);
+    pm_dfree(b->interp_off);
     pm_dfree(b->curve_of); pm_dfree(b->Kpg); pm_dfree(b->kp_ptr); pm_dfree(b->kp_patch);
     pm_dfree(b->kp_C); pm_dfree(b->mu_o); pm_dfree(b->part);
     delete b;
@@ -291,7 +348,7 @@ pm_status upload(T** d, const T* h, size_t n) {
 pm_status create_impl(pm_bvp* b, const double* edge_x, const double* edge_d1,
                       const double* edge_d2, const double* edge_nu, const double* edge_a,
                       const int* edge_patch, const double* edge_uv, const double* over_x,
-                      const double* over_speed, const double* over_a) {
+                      const double* over_nu, const double* over_speed, const double* over_a) {
     pm_surface* s = b->s;
     const int Me = b->Me, Fo = b->Fo, pp = s->pp;
     // trapezoid weights, K'_gamma (host, dense), interpolation matrices
@@ -342,7 +399,10 @@ pm_status create_impl(pm_bvp* b, const double* edge_x, const double* edge_d1,
             } else {
                 const double r0 = xe_[0] - edge_x[3 * k], r1 = xe_[1] - edge_x[3 * k + 1],
                              r2 = xe_[2] - edge_x[3 * k + 2];
-                v = (ne[0] * r0 + ne[1] * r1 + ne[2] * r2) / (r0 * r0 + r1 * r1 + r2 * r2);
+                // Neumann: nu(x_e) . r;  Dirichlet (double layer): -nu(x_k) . r
+                const double* nn = b->kind ? edge_nu + 3 * k : ne;
+                const double sg = b->kind ? -1.0 : 1.0;
+                v = sg * (nn[0] * r0 + nn[1] * r1 + nn[2] * r2) / (r0 * r0 + r1 * r1 + r2 * r2);
             }
             Kpg[(size_t)e * Me + k] = b->h_we[k] * v / (2.0 * M_PI * edge_a[k]);
         }
@@ -380,6 +440,7 @@ pm_status create_impl(pm_bvp* b, const double* edge_x, const double* edge_d1,
     PM_TRY(upload(&b->xo, over_x, 3 * (size_t)Fo));
     PM_TRY(upload(&b->wo, wo.data(), (size_t)Fo));
     PM_TRY(upload(&b->ao, over_a, (size_t)Fo));
+    PM_TRY(upload(&b->nuo, over_nu, 3 * (size_t)Fo));
     PM_TRY(upload(&b->interp, I.data(), I.size()));
     PM_TRY(upload(&b->interp_off, ioff.data(), ioff.size()));
     PM_TRY(upload(&b->curve_of, curve_of.data(), curve_of.size()));
@@ -392,10 +453,11 @@ pm_status create_impl(pm_bvp* b, const double* edge_x, const double* edge_d1,
     pm_status stt = upload(&d_be, blk_edge.data(), blk_edge.size());
     if (stt == PM_OK) stt = upload(&d_own, blk_own.data(), blk_own.size());
     if (stt == PM_OK)
-        stt = pm_bvp_kp_weights(s, b->kp_nblk, d_be, b->kp_patch, d_own, b->xe, b->nue, b->uv, b->kp_C);
+        stt = pm_bvp_kp_weights(s, b->kp_nblk, d_be, b->kp_patch, d_own, b->xe, b->nue, b->uv,
+                                b->kind, b->kp_C);
     if (stt == PM_OK && b->kp_nblk > 0) {
         k_bvp_combine<<<pm_ceil_div((long long)b->kp_nblk * pp, kT), kT>>>(
-            b->kp_nblk, pp, d_be, b->kp_patch, s->x, s->a, s->w, b->xe, b->nue, b->kp_C);
+            b->kind, b->kp_nblk, pp, d_be, b->kp_patch, s->x, s->a, s->w, b->xe, b->nue, b->kp_C);
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
             pm_set_error("pm_bvp_create: correction kernel failed");
             stt = PM_ERR_CUDA;
@@ -408,19 +470,23 @@ pm_status create_impl(pm_bvp* b, const double* edge_x, const double* edge_d1,
 
 }  // namespace
 
-extern "C" pm_status pm_bvp_create(pm_surface* s, int ncurves, const int* M, const int* F,
-                                   const double* edge_x, const double* edge_d1,
+extern "C" pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const int* M,
+                                   const int* F, const double* edge_x, const double* edge_d1,
                                    const double* edge_d2, const double* edge_nu,
                                    const double* edge_a, const int* edge_patch,
                                    const double* edge_uv, const double* over_x,
-                                   const double* over_speed, const double* over_a,
-                                   pm_bvp** out) {
+                                   const double* over_nu, const double* over_speed,
+                                   const double* over_a, pm_bvp** out) {
     if (!out) { pm_set_error("pm_bvp_create: out is NULL"); return PM_ERR_INVALID_ARG; }
     *out = nullptr;
     if (!s || ncurves < 0 || (ncurves > 0 && (!M || !F || !edge_x || !edge_d1 || !edge_d2 ||
                                               !edge_nu || !edge_a || !edge_patch || !edge_uv ||
-                                              !over_x || !over_speed || !over_a))) {
+                                              !over_x || !over_nu || !over_speed || !over_a))) {
         pm_set_error("pm_bvp_create: NULL argument");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (kind != PM_BVP_NEUMANN && kind != PM_BVP_DIRICHLET) {
+        pm_set_error("pm_bvp_create: kind %d is neither PM_BVP_NEUMANN nor PM_BVP_DIRICHLET", kind);
         return PM_ERR_INVALID_ARG;
     }
     if (!s->has_coeff) { pm_set_error("pm_bvp_create: call pm_surface_set_coeff first"); return PM_ERR_NO_COEFF; }
@@ -430,6 +496,7 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int ncurves, const int* M, con
     }
     pm_bvp* b = new pm_bvp();
     b->s = s;
+    b->kind = kind == PM_BVP_DIRICHLET ? 1 : 0;
     b->N = s->N;
     b->ncurves = ncurves;
     for (int c = 0; c < ncurves; ++c) {
@@ -462,8 +529,26 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int ncurves, const int* M, con
         }
     }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    if (b->kind) {
+        // Dirichlet: a constant over the surface, the edge nodes and the oversampled points
+        std::vector<double> ah(s->N), gh(3 * (size_t)s->N);
+        cudaMemcpy(ah.data(), s->a, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
+        cudaMemcpy(gh.data(), s->g, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost);
+        const double a0 = ah[0];
+        bool ok = true;
+        for (double v : ah) ok = ok && std::fabs(v - a0) <= 1e-14 * a0;
+        for (double v : gh) ok = ok && v == 0.0;
+        for (int e = 0; e < b->Me; ++e) ok = ok && std::fabs(edge_a[e] - a0) <= 1e-14 * a0;
+        for (int j = 0; j < b->Fo; ++j) ok = ok && std::fabs(over_a[j] - a0) <= 1e-14 * a0;
+        if (!ok) {
+            pm_set_error("pm_bvp_create: the Dirichlet system needs a constant coefficient "
+                         "(on the surface, the edge nodes and the oversampled points)");
+            delete b;
+            return PM_ERR_INVALID_ARG;
+        }
+    }
     const pm_status st = create_impl(b, edge_x, edge_d1, edge_d2, edge_nu, edge_a, edge_patch,
-                                     edge_uv, over_x, over_speed, over_a);
+                                     edge_uv, over_x, over_nu, over_speed, over_a);
     if (st != PM_OK) {
         free_bvp(b);
         return st;

@@ -945,16 +945,22 @@ __global__ void k_tile_radius(const double* __restrict__ x, int N, int tile,
 
 
 // ------------------------------------------------------------------ boundary-value systems
-// K'_Gamma weights of an edge node x_e of an open surface (Sec. 5.2, Thm. NeumannBCsrep):
-// W_k = int_P nu_e . (x - y) / (2 pi |x - y|^2) l_k J~ du dv over a patch P near x_e
-// (the density sigma / a interpolated, as for the surface operators).  One block per
-// (edge node, patch) pair.  own != 0: x_e lies on an edge of P at reference point
-// (u0, v0); the rule is polar about the patch's own point x = y~(u0, v0) over the
-// directions that enter the square, theta cut at the corner directions and at most
-// pi/16 wide, two radial panels [0, L/4], [L/4, L], 16-point Gauss on each (after the
-// polar Jacobian the integrand is smooth).  own == 0: the quadtree near rule about
-// x = x_e as in k_near_quad.
+// Surface-integral weights at an edge node x_e of an open surface (Sec. 5): for a patch P
+// near x_e, W_k = int_P G(x, y) l_k J~ du dv with G = nu_e . (x - y) / (2 pi |x - y|^2)
+// (K'_Gamma, Sec. 5.2, Thm. NeumannBCsrep; log_kernel = 0) or G = log|x - y| / (2 pi)
+// (K_Gamma on gamma, Sec. 5.3, Thm. Dirhclet_enforce; log_kernel = 1); the density
+// sigma / a is interpolated, as for the surface operators.  One block per (edge node,
+// patch) pair.  own != 0: x_e lies on an edge of P at reference point (u0, v0); the
+// rule is polar about the patch's own point x = y~(u0, v0) over the directions that
+// enter the square, theta cut at the corner directions and at most pi/32 wide (next to
+// a corner direction the ray length L varies fast; pi/16 panels left 1e-10 errors in
+// the weights of an edge node 1/16 of a patch from a corner),
+// 16-point Gauss in theta and on each radial panel: [0, L/4], [L/4, L] for the
+// gradient kernel (after the polar Jacobian its integrand is smooth), dyadic panels
+// [2^-(k+1), 2^-k] L, k < 18, and [0, 2^-18 L] for the log kernel (rho log rho).
+// own == 0: the quadtree near rule about x = x_e as in k_near_quad.
 constexpr int kBvpPts = 128;          // quadrature points per pass of the polar rule
+constexpr int kBvpLogLevels = 18;     // dyadic radial panels of the log-kernel polar rule
 
 __device__ double bvp_ray(double u0, double v0, double ct, double st) {
     double L = 1e300;
@@ -969,8 +975,9 @@ __global__ void __launch_bounds__(kQThreads)
 k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
               const int* __restrict__ blk_edge, const int* __restrict__ blk_patch,
               const int* __restrict__ blk_own, const double* __restrict__ xe,
-              const double* __restrict__ nue, const double* __restrict__ uv, double eta,
-              int max_depth, int max_leaves, double* __restrict__ W, int* __restrict__ err) {
+              const double* __restrict__ nue, const double* __restrict__ uv, int log_kernel,
+              double eta, int max_depth, int max_leaves, double* __restrict__ W,
+              int* __restrict__ err) {
     const int blk = blockIdx.x;
     const int e = blk_edge[blk], P = blk_patch[blk];
     const int pp = p * p, tid = threadIdx.x;
@@ -1039,11 +1046,12 @@ k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
         const int nc = sNcut;
         for (int seg = 0; seg + 1 < nc; ++seg) {
             const double A = sCut[seg], B = sCut[seg + 1];
-            const int nsub = max(1, (int)ceil((B - A) / (M_PI / 16.0) - 1e-9));
+            const int nsub = max(1, (int)ceil((B - A) / (M_PI / 32.0) - 1e-9));
             for (int sub = 0; sub < nsub; ++sub) {
                 const double s0 = A + (B - A) * sub / nsub, s1 = A + (B - A) * (sub + 1) / nsub;
                 const double hs = 0.5 * (s1 - s0);
-                for (int rp = 0; rp < 2; ++rp) {
+                const int nrp = log_kernel ? kBvpLogLevels + 1 : 2;
+                for (int rp = 0; rp < nrp; ++rp) {
                     for (int half = 0; half < 2; ++half) {
                         // point tid: theta node 8 half + tid / 16, radial node tid % 16
                         {
@@ -1051,7 +1059,14 @@ k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
                             const double th = s0 + hs * (cT.g16t[qt] + 1.0);
                             const double ct = cos(th), st = sin(th);
                             const double L = bvp_ray(u0, v0, ct, st);
-                            const double r0 = rp == 0 ? 0.0 : 0.25 * L, r1 = rp == 0 ? 0.25 * L : L;
+                            double r0, r1;
+                            if (log_kernel) {
+                                r0 = rp == 0 ? 0.0 : L * ldexp(1.0, rp - 1 - kBvpLogLevels);
+                                r1 = L * ldexp(1.0, rp - kBvpLogLevels);
+                            } else {
+                                r0 = rp == 0 ? 0.0 : 0.25 * L;
+                                r1 = rp == 0 ? 0.25 * L : L;
+                            }
                             const double hr = 0.5 * (r1 - r0);
                             const double rho = r0 + hr * (cT.g16t[qr] + 1.0);
                             const double u = u0 + rho * ct, v = v0 + rho * st;
@@ -1075,7 +1090,9 @@ k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
                             const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                             const double nr = -(n0 * d0 + n1 * d1 + n2 * d2);
                             const double wgt = hs * cT.g16w[qt] * hr * cT.g16w[qr] * rho * jj;
-                            sF[tid] = r2 > 0.0 ? wgt * nr / r2 * (0.5 / M_PI) : 0.0;
+                            sF[tid] = !(r2 > 0.0) ? 0.0
+                                      : log_kernel ? wgt * log(r2) * (0.25 / M_PI)
+                                                   : wgt * nr / r2 * (0.5 / M_PI);
                         }
                         __syncthreads();
                         if (tid < pp)
@@ -1123,7 +1140,7 @@ k_bvp_kp_quad(int p, const double* __restrict__ x, const double* __restrict__ J,
                 const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 const double nr = -(n0 * d0 + n1 * d1 + n2 * d2);
                 const double wgt = hu * cT.g16w[qn] * hv * cT.g16w[r] * jj;
-                sG[q] = wgt * nr / r2 * (0.5 / M_PI);
+                sG[q] = log_kernel ? wgt * log(r2) * (0.25 / M_PI) : wgt * nr / r2 * (0.5 / M_PI);
             }
             __syncthreads();
             if (tid < pp)
@@ -1346,11 +1363,12 @@ pm_status pm_near_build_c(pm_surface* s) {
     return PM_OK;
 }
 
-// K'_Gamma weights of the edge nodes of a boundary-value system (pm_bvp.cu): one
-// block per (edge node, patch) pair of the device lists; W [nb][p*p].
+// Surface-integral weights at the edge nodes of a boundary-value system (pm_bvp.cu):
+// K'_Gamma (log_kernel = 0) or K_Gamma (log_kernel = 1); one block per (edge node,
+// patch) pair of the device lists; W [nb][p*p].
 pm_status pm_bvp_kp_weights(pm_surface* s, int nb, const int* blk_edge, const int* blk_patch,
                             const int* blk_own, const double* xe, const double* nue,
-                            const double* uv, double* W) {
+                            const double* uv, int log_kernel, double* W) {
     std::lock_guard<std::mutex> build_lock(g_near_build_mu);
     if (nb == 0) return PM_OK;
     QuadTables T;
@@ -1358,7 +1376,7 @@ pm_status pm_bvp_kp_weights(pm_surface* s, int nb, const int* blk_edge, const in
     PM_CUDA_TRY(cudaMemcpyToSymbol(cT, &T, sizeof(QuadTables)));
     PM_CUDA_TRY(cudaMemset(s->dev_err, 0, sizeof(int)));
     k_bvp_kp_quad<<<nb, kQThreads>>>(s->p, s->x, s->J, blk_edge, blk_patch, blk_own, xe, nue, uv,
-                                     s->opts.near_eta, std::min(s->opts.near_max_depth, 12),
+                                     log_kernel, s->opts.near_eta, std::min(s->opts.near_max_depth, 12),
                                      s->opts.near_max_leaves, W, s->dev_err);
     PM_CUDA_TRY(cudaGetLastError());
     PM_CUDA_TRY(cudaDeviceSynchronize());
