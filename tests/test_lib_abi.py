@@ -59,6 +59,16 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.pm_surface_set_coeff_c(None, None, None, None) == 1
     assert lib.pm_apply_c(None, 0, None, None, 0, None) == 1
     assert lib.pm_solve_c(None, None, None, 1e-8, 10, None, None) == 1
+    assert lib.pm_surface_store_ff(None, 3) == 1
+    assert lib.pm_surface_stored_ff(None) == 0
+    h = C.c_void_p()
+    assert lib.pm_bvp_create(None, 0, 1, None, None, None, None, None, None, None, None, None,
+                             None, None, None, None, C.byref(h)) == 1
+    assert lib.pm_bvp_create(None, 0, 0, None, None, None, None, None, None, None, None, None,
+                             None, None, None, None, None) == 1
+    assert lib.pm_bvp_apply(None, None, None, None, None) == 1
+    assert lib.pm_bvp_solve(None, None, None, 1e-10, 10, None, None, None, None) == 1
+    lib.pm_bvp_destroy(None)                          # no-op
 
 
 def _header_struct_fields(name):
