@@ -448,6 +448,30 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_value = job_throughput(world, applies * pairs, e2e_s * 1e3)
 
+    # per-launch kernel times: every operator apply of the step, back to back on the
+    # launching stream, with per-phase events (the host enqueues ahead of the device, so
+    # no launch gap falls inside an event pair, unlike the host-issued profiled pass;
+    # no launch there returns early); the shares stay those of the profiled pass
+    reps = 10
+    sig_k = torch.from_numpy(np.random.default_rng(5).standard_normal(N) + 1.0).to(dev)
+
+    def per_launch(fn, names):
+        fn()
+        torch.cuda.synchronize()
+        surf.profile(True)
+        surf.profile_read(0, reset=True)
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        surf.profile(False)
+        p2 = _phase_totals(surf)
+        return {nm: p2[nm][0] / p2[nm][1] for nm in names if p2[nm][1]}
+
+    klt = {}
+    klt.update(per_launch(lambda: surf.apply_R(sig_k, prec), ["direct_R", "fmm_p2p", "fmm_m2l_gemm"]))
+    klt.update(per_launch(lambda: surf.apply_R(sig_k, "ff"), ["accurate_R"]))
+    klt.update(per_launch(lambda: surf.apply_K(sig_k, "ff"), ["accurate_K"]))
+
     # the same step with the float-float sums evaluated pair by pair (matrices released)
     computed_ff = None
     if stored:
@@ -470,7 +494,7 @@ def run_gpu(args, rank, world, local_rank):
                                "by pair (symmetric tile-pair kernels) instead of read from the "
                                "stored matrices; untimed build excluded either way"}
 
-    # rooflines of the step's kernels, per launch from the profiled pass
+    # rooflines of the step's kernels, per launch from the back-to-back applies
     nt = -(-N // 128)
     sym = N >= 256 and nt * N * 8 <= SYM_PARTIAL_CAP
     ff_name = "k_sym_ff" if sym else "k_direct_ff"
@@ -479,7 +503,7 @@ def run_gpu(args, rank, world, local_rank):
     ld = -(-N // 128) * 128
     if stored and acc_R_n:
         byt = N * ld * 6 + 8 * ld + 8 * N
-        ms = acc_R_ms / acc_R_n
+        ms = klt["accurate_R"]
         ach = byt / (ms * 1e-3) / 1e9
         roofs["accurate_R"] = {
             "bound": "hbm", "kernel": "k_ffmat_gemv (stored float-float remainder matrix, "
@@ -495,7 +519,7 @@ def run_gpu(args, rank, world, local_rank):
         sym_k = N >= 256 and ntk * N * 8 <= SYM_PARTIAL_CAP
         mat = ntk * (ntk + 1) // 2 * 128 * 128 * 6 if sym_k else N * ld * 6
         byt = mat + 8 * ld + 8 * N
-        ms = acc_K_ms / acc_K_n
+        ms = klt["accurate_K"]
         ach = byt / (ms * 1e-3) / 1e9
         roofs["accurate_K"] = {
             "bound": "hbm",
@@ -512,7 +536,7 @@ def run_gpu(args, rank, world, local_rank):
     if acc_R_n and not stored:
         roofs["accurate_R"] = _alu_roofline(
             ff_name + "<R> (float-float remainder sum" + (", each unordered pair once)" if sym else ")"),
-            FLOPS_PER_PAIR_R * pairs, acc_R_ms / acc_R_n, peak_fp32, acc_R_ms * args.steps / prof_total_ms,
+            FLOPS_PER_PAIR_R * pairs, klt["accurate_R"], peak_fp32, acc_R_ms * args.steps / prof_total_ms,
             TRAFFIC_BYTES.get((ff_name + "_R", args.workload)),
             note="algorithmic flops of the float64-class sum (26 per ordered pair); float-float "
                  "arithmetic costs ~10 float32 instructions per algorithmic flop (274 per "
@@ -520,10 +544,10 @@ def run_gpu(args, rank, world, local_rank):
     if acc_K_n and not stored:
         roofs["accurate_K"] = _alu_roofline(
             ff_name + "<K> (float-float parametrix sum)", FLOPS_PER_PAIR_K * pairs,
-            acc_K_ms / acc_K_n, peak_fp32, acc_K_ms * args.steps / prof_total_ms,
+            klt["accurate_K"], peak_fp32, acc_K_ms * args.steps / prof_total_ms,
             TRAFFIC_BYTES.get((ff_name + "_K", args.workload)))
     if fmm and ph["fmm_m2l_gemm"][1]:
-        g_ms = ph["fmm_m2l_gemm"][0] / args.steps / fast_R_eff
+        g_ms = klt["fmm_m2l_gemm"]
         alg = M2L_FLOPS_PER_BOX_PAIR * fmm["m2l_box_pairs"]
         peak_tc = mp_peaks["bf16_tflops_sustained"] or mp_peaks["bf16_tflops"]
         ach = alg / (g_ms * 1e-3) / 1e12
@@ -537,14 +561,14 @@ def run_gpu(args, rank, world, local_rank):
                           + mp_peaks["basis"],
             "step_time_share": round(ph["fmm_m2l_gemm"][0] / prof_total_ms, 4)}
     if fmm and ph["fmm_p2p"][1]:
-        p_ms = ph["fmm_p2p"][0] / args.steps / fast_R_eff
+        p_ms = klt["fmm_p2p"]
         roofs["fmm_p2p"] = _alu_roofline(
             "k_fmm_p2p<R> (FMM adjacent-leaf float32 sums)", FLOPS_PER_PAIR_R * fmm["p2p_pairs"],
             p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms,
             TRAFFIC_BYTES.get(("k_fmm_p2p", args.workload)))
     if not fmm and fast_R_n:
         roofs["direct_R"] = _alu_roofline(
-            "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, fast_R_ms / fast_R_eff,
+            "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, klt["direct_R"],
             peak_fp32, fast_R_ms * args.steps / prof_total_ms,
             TRAFFIC_BYTES.get(("k_direct_R32", args.workload)))
     dom = max(roofs, key=lambda k: roofs[k]["step_time_share"]) if roofs else None
