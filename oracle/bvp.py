@@ -90,7 +90,7 @@ def kprime_from_sources(xe, nue, xs, a_src):
 
 
 # ---------------------------------------------------------------- K'_Gamma corrections
-def _edge_theta_rule(u0, v0, n_theta=24, max_width=np.pi / 32):
+def _edge_theta_rule(u0, v0, n_theta=16, max_width=np.pi / 32):
     """Directions entering [-1, 1]^2 from (u0, v0) on its boundary: Gauss-Legendre in
     theta on panels cut at the corner directions, at most max_width wide; returns
     (cos theta, sin theta, weights, ray length L(theta) to the boundary)."""
@@ -140,11 +140,13 @@ def _polar_points(u0, v0, ct, st, wth, L, panels, n_rho):
     return np.concatenate(U), np.concatenate(V), np.concatenate(W)
 
 
-def _edge_polar_points(u0, v0, n_theta=24, n_rho=32, max_width=np.pi / 32):
+def _edge_polar_points(u0, v0, n_theta=16, n_rho=20, max_width=np.pi / 32):
     """Polar rule about (u0, v0) on the boundary of [-1, 1]^2 over the directions that
     enter the square, one radial panel: points (u, v) and weights.  Theta panels at
     most pi/32: next to a corner direction the ray length varies fast (pi/8 panels left
-    2e-11 errors in the weights of an edge node 1/16 of a patch from a corner)."""
+    2e-11 errors in the weights of an edge node 1/16 of a patch from a corner).  With
+    16 Gauss points a panel in theta and 20 in the radius (12 a dyadic panel for the
+    log kernel) the weights agree with 3-4x finer rules to 7e-15."""
     return _polar_points(u0, v0, *_edge_theta_rule(u0, v0, n_theta, max_width), [(0.0, 1.0)], n_rho)
 
 
@@ -157,7 +159,7 @@ def _kp_integrand(patch: PatchInterpolant, u, v, xe, nue):
     return (k[:, None, None] * Lu[:, :, None] * Lv[:, None, :]).reshape(len(u), -1)
 
 
-def _edge_polar_points_graded(u0, v0, levels=18, n_theta=24, n_rho=16, max_width=np.pi / 32):
+def _edge_polar_points_graded(u0, v0, levels=18, n_theta=16, n_rho=12, max_width=np.pi / 32):
     """As _edge_polar_points with the radius on dyadic panels [2^-(k+1), 2^-k] L,
     k < levels, and [0, 2^-levels L]: for integrands with a log r factor (pi/8 theta
     panels left 4e-11 errors in the weights next to a corner; pi/32 converge them to

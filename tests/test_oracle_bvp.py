@@ -222,7 +222,7 @@ def test_double_layer_jump_from_inside():
 
 def test_manufactured_dirichlet_solution_converges():
     errs = []
-    for args in ((2, 4, 6, 16, 32), (2, 4, 8, 32, 32)):
+    for args in ((2, 4, 6, 16, 32), (2, 4, 7, 24, 32)):
         os_ = torus_band(*args)
         co = constant_band_coefficient(os_)
         B = DirichletBVP(os_, co, np.ones(os_.M), np.ones(sum(c.F * c.M for c in os_.curves)),
@@ -235,4 +235,4 @@ def test_manufactured_dirichlet_solution_converges():
         errs.append(float(np.sqrt(np.dot(w, (u - v) ** 2) / np.dot(w, v * v))))
         top, bot = B.apply(sigma, mu)
         assert np.abs(np.concatenate([top, bot]) - B.matrix() @ np.concatenate([sigma, mu])).max() < 1e-10
-    assert errs[1] < 1e-7 and errs[1] < errs[0] / 10, errs
+    assert errs[0] < 1e-6 and errs[1] < 1e-7 and errs[1] < errs[0] / 5, errs
