@@ -199,5 +199,13 @@ extern "C" pm_status pm_surface_check(pm_surface* s) {
         pm_set_error("pm_surface_check: %s (check %d) at index %d", code_name(h[0]), h[0], h[1]);
         return PM_ERR_INTERNAL;
     }
+    if (s->ffm_err) {
+        int fe = 0;
+        PM_CUDA_TRY(cudaMemcpy(&fe, s->ffm_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (fe != PM_DEV_OK) {
+            pm_set_error("pm_surface_check: a stored-matrix GEMV's bulk copy did not arrive in time");
+            return PM_ERR_TIMEOUT;
+        }
+    }
     return PM_OK;
 }

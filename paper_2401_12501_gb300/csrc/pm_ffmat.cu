@@ -90,6 +90,55 @@ __device__ __forceinline__ float ff_lo(float h, float f) {
 
 __device__ __forceinline__ unsigned code_pack(unsigned lo, unsigned hi) { return lo | (hi << 16); }
 
+// ------------------------------------------------------------- bulk copies (TMA)
+constexpr unsigned long long kBulkWaitNs = 2000000000ull;   // give up on a copy after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait for the phase with the given parity; false (and *err set) after 2 s
+__device__ bool bar_wait(uint32_t bar, uint32_t parity, int* err) {
+    if (bar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (bar_test(bar, parity)) return true;
+        if ((it & 63) == 0 && global_ns() - t0 > kBulkWaitNs) {
+            atomicExch(err, PM_DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 // --------------------------------------------------------------------- build
 // Remainder (KERNEL_K = false): src = src_ff (plain float-float coordinates),
 // tg = tgt_ff (x, n', m pairs of the target).  Parametrix (KERNEL_K = true):
@@ -342,17 +391,45 @@ __device__ __forceinline__ void ff_join(float& S, float& E, float S2, float E2) 
 // a sub-tile lane l holds column l's even chain and column l + 1's odd chain.  The
 // strengths of a sub-tile's 32 columns sit twice in a row in shared memory (and once
 // more shifted by one), so that the pair of a double step is one aligned 8-byte load.
-__global__ void __launch_bounds__(kST, 6)
+// Each warp streams its four 32-column sub-tiles (4 KB of floats and 2 KB of codes each,
+// contiguous in the layout) through a two-stage shared-memory ring filled by bulk copies
+// (TMA), so the loads of the next sub-tile are in flight while one is consumed; lane 0
+// issues them, every wait is bounded (2 s, then *err = PM_DEV_TIMEOUT and the warp stops).
+constexpr int kChunkHi = 8 * 32 * 16;               // floats of one (warp, sub-tile): 4 KB
+constexpr int kChunkQ = 8 * 32 * 8;                 // codes: 2 KB
+constexpr int kStageBytes = kChunkHi + kChunkQ;
+constexpr int kSymDynSmem = 4 * 2 * kStageBytes;    // 4 warps x 2 stages = 48 KB
+
+__global__ void __launch_bounds__(kST, 4)
 k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict__ sv, int N,
-                  int nt, float2* __restrict__ partial, const int* __restrict__ skip) {
+                  int nt, float2* __restrict__ partial, const int* __restrict__ skip,
+                  int* __restrict__ err) {
     if (skip && *skip) return;
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ __align__(8) unsigned long long bars[8];     // [warp][stage]
     // Dh[c][i] = hi of column c 32 + (i mod 32); Ph[c][i] = Dh[c][i + 1] (likewise lo)
     __shared__ __align__(16) float Dh[4][64], Dl[4][64], Ph[4][64], Pl[4][64];
-    __shared__ float2 csh[4][kST];
     int a, b;
     pm_tile_pair(blockIdx.x, nt, a, b);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int i = a * kST + tid, j = b * kST + tid;
+    const unsigned char* tile = T + (size_t)blockIdx.x * kTileBytes;
+    const unsigned char* gh = tile + (size_t)w * 4 * kChunkHi;               // warp's floats
+    const unsigned char* gq = tile + kTileHiBytes + (size_t)w * 4 * kChunkQ; // warp's codes
+    unsigned char* wring = ring + w * 2 * kStageBytes;
+    const uint32_t bar0 = smem_u32(&bars[2 * w]), bar1 = smem_u32(&bars[2 * w + 1]);
+    int issued[2] = {1, 1}, waited[2] = {0, 0};       // copy phases per stage (warp-uniform)
+    if (lane == 0) {
+        bar_init(bar0);
+        bar_init(bar1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t bar = c ? bar1 : bar0;
+            bar_expect(bar, kStageBytes);
+            bulk_load(smem_u32(wring + c * kStageBytes), gh + c * kChunkHi, kChunkHi, bar);
+            bulk_load(smem_u32(wring + c * kStageBytes + kChunkHi), gq + c * kChunkQ, kChunkQ, bar);
+        }
+    }
     {
         const float2 sj = j < N ? sv[j] : make_float2(0.f, 0.f);   // column tid = 32 w + lane
         const int pm = (lane + 31) & 31;
@@ -364,9 +441,7 @@ k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict_
     const float2 si = i < N ? sv[i] : make_float2(0.f, 0.f);
     __syncthreads();
     const bool diag = (a == b);
-    const unsigned char* tile = T + (size_t)blockIdx.x * kTileBytes;
-    const float4* th = reinterpret_cast<const float4*>(tile) + (size_t)w * (4 * 8 * 32) + lane;
-    const uint2* tq = reinterpret_cast<const uint2*>(tile + kTileHiBytes) + (size_t)w * (4 * 8 * 32) + lane;
+    bool ok = true;
     const int nxt2 = (lane + 2) & 31, prv = (lane + 31) & 31;
     const bool odd = lane & 1;
     const float2 SIH = make_float2(si.x, si.x), SIL = make_float2(si.y, si.y);
@@ -378,11 +453,19 @@ k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict_
         const float2* ph = reinterpret_cast<const float2*>(odd ? &Ph[c][lane - 1] : &Dh[c][lane]);
         const float2* pl = reinterpret_cast<const float2*>(odd ? &Pl[c][lane - 1] : &Dl[c][lane]);
         float2 CS = make_float2(0.f, 0.f), CE = make_float2(0.f, 0.f);
+        const int stage = c & 1;
+        if (ok) {
+            ok = bar_wait(stage ? bar1 : bar0, c >> 1, err);
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) ++waited[stage];
+        }
+        const float4* th = reinterpret_cast<const float4*>(wring + stage * kStageBytes) + lane;
+        const uint2* tq = reinterpret_cast<const uint2*>(wring + stage * kStageBytes + kChunkHi) + lane;
 #pragma unroll 4
-        for (int kq = 0; kq < 8; ++kq) {
-            const int o = (c * 8 + kq) * 32;
-            const float4 h4 = __ldcs(th + o);
-            const uint2 w2 = __ldcs(tq + o);
+        for (int kq = 0; kq < 8 && ok; ++kq) {
+            const int o = kq * 32;
+            const float4 h4 = th[o];
+            const uint2 w2 = tq[o];
             const float2 H0 = make_float2(h4.x, h4.y), H1 = make_float2(h4.z, h4.w);
             const float2 F0 = make_float2(code_float<false>(w2.x), code_float<true>(w2.x));
             const float2 F1 = make_float2(code_float<false>(w2.y), code_float<true>(w2.y));
@@ -402,19 +485,44 @@ k_ffmat_symK_gemv(const unsigned char* __restrict__ T, const float2* __restrict_
                 }
             }
         }
+        // the stage is consumed: refill it with sub-tile c + 2
+        __syncwarp();
+        if (ok && c + 2 < 4) {
+            if (lane == 0) {
+                const uint32_t bar = stage ? bar1 : bar0;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect(bar, kStageBytes);
+                bulk_load(smem_u32(wring + stage * kStageBytes), gh + (c + 2) * kChunkHi, kChunkHi,
+                          bar);
+                bulk_load(smem_u32(wring + stage * kStageBytes + kChunkHi), gq + (c + 2) * kChunkQ,
+                          kChunkQ, bar);
+            }
+            ++issued[stage];
+        }
         // column lane: its even chain here, its odd chain on the previous lane
         float s = CS.x, e = CE.x;
         ff_join(s, e, __shfl_sync(0xffffffffu, CS.y, prv), __shfl_sync(0xffffffffu, CE.y, prv));
         cS[c] = s;
         cE[c] = e;
     }
-    if (i < N) {
+    if (!ok) {
+        // a copy did not arrive in time (*err is set; the results are not valid): wait
+        // once more, bounded, for the copies still in flight into this warp's ring
+        // before the ring is reused or the block's shared memory released
+        for (int st2 = 0; st2 < 2; ++st2)
+            for (int ph = waited[st2]; ph < issued[st2]; ++ph)
+                if (!bar_wait(st2 ? bar1 : bar0, ph & 1, err)) break;
+    }
+    if (ok && i < N) {
         float s = RS.x, e = RE.x;
         ff_join(s, e, RS.y, RE.y);
         const ff v = ff_norm(ff{s, e});
         partial[(size_t)b * N + i] = make_float2(v.h, v.l);
     }
-    if (diag) return;
+    if (diag) return;                              // block-uniform
+    // the column sums of the four warps, in the ring once every warp is done with it
+    __syncthreads();
+    float2 (*csh)[kST] = reinterpret_cast<float2 (*)[kST]>(ring);
 #pragma unroll
     for (int c = 0; c < 4; ++c) csh[w][c * 32 + lane] = make_float2(cS[c], cE[c]);
     __syncthreads();
@@ -491,6 +599,7 @@ void pm_ffmat_free(pm_surface* s) {
     pm_dfree(s->ffm_R);
     pm_dfree(s->ffm_K);
     pm_dfree(s->ffm_s);
+    pm_dfree(s->ffm_err);
     s->ffm_ld = 0;
     s->ffm_symK = 0;
 }
@@ -516,8 +625,16 @@ pm_status pm_ffmat_prep(pm_surface* s, const double* sigma, cudaStream_t st) {
 pm_status pm_ffmat_apply(pm_surface* s, int which_K, int* nsplit, cudaStream_t st) {
     if (which_K && s->ffm_symK) {
         const int nt = s->ffm_symK;
-        k_ffmat_symK_gemv<<<nt * (nt + 1) / 2, kST, 0, st>>>(
-            s->ffm_K, s->ffm_s, s->N, nt, reinterpret_cast<float2*>(s->partial), s->skip_flag);
+        static bool attr_set = false;            // per process (one device's attribute suffices
+        if (!attr_set) {                          // for every device: it is a function attribute)
+            PM_CUDA_TRY(cudaFuncSetAttribute(k_ffmat_symK_gemv,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSymDynSmem));
+            attr_set = true;
+        }
+        k_ffmat_symK_gemv<<<nt * (nt + 1) / 2, kST, kSymDynSmem, st>>>(
+            s->ffm_K, s->ffm_s, s->N, nt, reinterpret_cast<float2*>(s->partial), s->skip_flag,
+            s->ffm_err);
         PM_CUDA_TRY(cudaGetLastError());
         *nsplit = nt;
         return PM_OK;
@@ -575,6 +692,11 @@ extern "C" pm_status pm_surface_store_ff(pm_surface* s, int which) {
     if (st == PM_OK && (which & 2)) {
         st = pm_dmalloc(&s->ffm_K, bytesK);
         s->ffm_symK = nt_sym;
+    }
+    if (st == PM_OK) st = pm_dmalloc(&s->ffm_err, 1);
+    if (st == PM_OK && cudaMemset(s->ffm_err, 0, sizeof(int)) != cudaSuccess) {
+        pm_set_error("pm_surface_store_ff: cudaMemset failed");
+        st = PM_ERR_CUDA;
     }
     if (st == PM_OK && cudaMemset(s->ffm_s, 0, sizeof(float2) * s->ffm_ld) != cudaSuccess) {
         pm_set_error("pm_surface_store_ff: cudaMemset failed");

@@ -187,6 +187,7 @@ struct pm_surface {
     unsigned char* ffm_R = nullptr;
     unsigned char* ffm_K = nullptr;
     float2* ffm_s = nullptr;      // [ffm_ld]
+    int* ffm_err = nullptr;       // device error word of the stored-matrix GEMVs (PM_DEV_TIMEOUT)
     long long ffm_ld = 0;
     int ffm_symK = 0;             // tiles of 128 per side when ffm_K holds the symmetric
                                   // tile-pair layout (upper triangle only), else 0

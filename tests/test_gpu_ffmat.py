@@ -7,8 +7,9 @@
   largest entry (the stored format keeps each entry to 2^-40 of its magnitude, against
   ~2^-46 for the float-float evaluation; the errors have random signs, so a row's
   error stays near 2^-40 |y|) and themselves bit for bit.
-* Full size (ellipsoid 9,600, the GEMV in the launch shape of the solve): sampled
-  rows against the oracle at 1e-10 of the row maximum.
+* Full size (ellipsoid 9,600 and the 98,304-node torus the bench times, the GEMVs in
+  the launch shapes of the solve): sampled rows against the oracle at 1e-10 of the row
+  maximum.
 * Storing one kernel leaves the other on the pair-by-pair path; release restores it;
   set_coeff re-evaluates the stored remainder (compared with a fresh surface of the
   new coefficient); clones do not inherit; a c != 0 coefficient releases them.
@@ -112,6 +113,28 @@ def test_stored_full_size_rows(ctx):
     assert np.abs(s.apply_R(sigma, "ff")[rows] - oR).max() < 1e-10 * np.abs(oR).max()
     assert np.abs(s.apply_K(sigma, "ff")[rows] - oK).max() < 1e-10 * np.abs(oK).max()
     s.close()
+
+
+def test_stored_full_size_torus_rows(ctx):
+    """The 98,304-node torus in the layout the bench times (87 GB of stored matrices):
+    sampled rows of both stored applies against the oracle."""
+    from oracle.operator import apply_K, apply_R
+    name = "torus_98304"
+    wl = make_workload(name)
+    rng = np.random.default_rng(35)
+    rows = sorted(set([0, wl.N - 1] + [int(i) for i in rng.integers(0, wl.N, 8)]))
+    _, d, nf = oracle(name, rows)
+    _, s = surface(ctx, name)
+    s.store_ff("RK")
+    assert s.stored_ff() == "RK"
+    sigma = np.cos(3 * wl.surface.nodes[:, 0]) + 0.5 * rng.standard_normal(wl.N)
+    oR = apply_R(d, nf, sigma, rows)
+    oK = apply_K(d, nf, sigma, rows)
+    yR = s.apply_R(sigma, "ff")
+    yK = s.apply_K(sigma, "ff")
+    s.close()
+    assert np.abs(yR[rows] - oR).max() < 1e-10 * np.abs(oR).max()
+    assert np.abs(yK[rows] - oK).max() < 1e-10 * np.abs(oK).max()
 
 
 def test_partial_store_release_coefficient_and_clone(ctx):
