@@ -57,7 +57,7 @@ TRAFFIC_BYTES = {("k_direct_R32", "ellipsoid_9600"): 625408,
                  ("k_ffmat_gemv", "ellipsoid_9600"): 556227840,
                  ("k_ffmat_symK_gemv", "ellipsoid_9600"): 287151616,
                  ("k_ffmat_gemv", "torus_98304"): 58324716356,
-                 ("k_ffmat_symK_gemv", "torus_98304"): 29752530371}
+                 ("k_ffmat_symK_gemv", "torus_98304"): 29752534596}
 SYM_PARTIAL_CAP = 1024 ** 3             # the library's cap on symmetric-sum partial slices
 DEFAULT_PREC = {"torus_98304": "fmm"}   # operator precision of the solve step per workload
 
