@@ -365,7 +365,8 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  *   Dirichlet: sigma + R~ sigma + T_gamma mu = f,  +mu/(2a) + K~ sigma + N_gamma mu = f_gamma,
  *              u = K~ sigma + N_gamma mu,
  * all in float64.  Creation computes the surface quadrature of every edge node on the
- * device.  PM_ERR_INVALID_ARG for NULL arguments, an unknown kind, bad sizes, an edge
+ * device, with s's coefficient built in: after a later pm_surface_set_coeff(_c) on s,
+ * pm_bvp_apply and pm_bvp_solve refuse the handle (PM_ERR_INVALID_ARG); create a new one.  PM_ERR_INVALID_ARG for NULL arguments, an unknown kind, bad sizes, an edge
  * node not on an edge of its patch or a non-constant a for Dirichlet; PM_ERR_NO_COEFF
  * without a coefficient.
  */

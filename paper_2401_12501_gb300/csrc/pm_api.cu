@@ -639,6 +639,7 @@ extern "C" pm_status pm_surface_set_coeff(pm_surface* s, const double* a, const 
     s->has_coeff = true;
     s->has_c = 0;
     s->graph_epoch++;
+    s->coeff_epoch++;
     return PM_OK;
 }
 

@@ -56,6 +56,7 @@ pm_status pm_bvp_kp_weights(pm_surface* s, int nb, const int* blk_edge, const in
 struct pm_bvp {
     pm_surface* s = nullptr;
     int kind = 0;                        // 0 Neumann, 1 Dirichlet
+    long long coeff_epoch = 0;           // the surface's coefficient epoch at creation
     int N = 0, Me = 0, Fo = 0, ncurves = 0;
     std::vector<int> M, F, off, offo;
     std::vector<double> h_we;
@@ -497,6 +498,7 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const i
     pm_bvp* b = new pm_bvp();
     b->s = s;
     b->kind = kind == PM_BVP_DIRICHLET ? 1 : 0;
+    b->coeff_epoch = s->coeff_epoch;
     b->N = s->N;
     b->ncurves = ncurves;
     for (int c = 0; c < ncurves; ++c) {
@@ -565,6 +567,10 @@ extern "C" pm_status pm_bvp_apply(pm_bvp* b, const double* sigma, const double* 
         pm_set_error("pm_bvp_apply: NULL argument");
         return PM_ERR_INVALID_ARG;
     }
+    if (b->coeff_epoch != b->s->coeff_epoch) {
+        pm_set_error("pm_bvp_apply: the surface's coefficient changed after pm_bvp_create");
+        return PM_ERR_INVALID_ARG;
+    }
     PM_CUDA_TRY(cudaSetDevice(b->s->ctx->device));
     const size_t n = (size_t)b->N + b->Me;
     double *z = nullptr, *y = nullptr;
@@ -590,6 +596,10 @@ extern "C" pm_status pm_bvp_solve(pm_bvp* b, const double* f, const double* f_ga
                                   pm_solve_info* info) {
     if (!b || !f || !u || (b->Me > 0 && !f_gamma) || !(tol > 0.0) || maxit < 1) {
         pm_set_error("pm_bvp_solve: NULL argument, tol <= 0 or maxit < 1");
+        return PM_ERR_INVALID_ARG;
+    }
+    if (b->coeff_epoch != b->s->coeff_epoch) {
+        pm_set_error("pm_bvp_solve: the surface's coefficient changed after pm_bvp_create");
         return PM_ERR_INVALID_ARG;
     }
     PM_CUDA_TRY(cudaSetDevice(b->s->ctx->device));

@@ -423,6 +423,7 @@ extern "C" pm_status pm_surface_set_coeff_c(pm_surface* s, const double* a, cons
     PM_TRY(pm_near_build_c(s));
     s->has_c = 1;
     s->graph_epoch++;
+    s->coeff_epoch++;
     return PM_OK;
 }
 

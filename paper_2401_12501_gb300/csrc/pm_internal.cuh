@@ -195,6 +195,7 @@ struct pm_surface {
     // per-phase timing (events recorded around launches while enabled)
     bool profiling = false;
     long long graph_epoch = 0;    // bumped when buffers or launch shapes captured in graphs change
+    long long coeff_epoch = 0;    // bumped by every coefficient change (set_coeff, set_coeff_c)
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_events;
     double prof_ms[PM_PHASE_COUNT] = {};
     int prof_n[PM_PHASE_COUNT] = {};

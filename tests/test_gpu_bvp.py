@@ -127,6 +127,16 @@ def test_invalid_arguments(ctx):
     with pytest.raises(pm.PmError):
         pm.NeumannBVP(s, os_.curves, edge_a(os_), edge_a(os_, True), badp, uv)
     s.close()
+    # a coefficient change on the surface invalidates an existing handle
+    s3 = pm.Surface.from_fixture(ctx, os_.surface)
+    s3.set_coeff(co.a, co.grad_a)
+    b3 = pm.NeumannBVP(s3, os_.curves, edge_a(os_), edge_a(os_, True), patch, uv)
+    b3.apply(np.ones(s3.N), np.ones(b3.Me))
+    s3.set_coeff(2.0 * co.a, 2.0 * co.grad_a)
+    with pytest.raises(pm.PmError):
+        b3.apply(np.ones(s3.N), np.ones(b3.Me))
+    b3.close()
+    s3.close()
     # a variable coefficient is refused for Dirichlet
     import paper_2401_12501_gb300 as pm2
     s2 = pm2.Surface.from_fixture(ctx, os_.surface)
