@@ -863,17 +863,54 @@ k_near_apply32(int N, int ppad, const int* __restrict__ row_ptr,
     if (row_ok && hl == 0) out[i] = (double)hi + (double)lo;
 }
 
+// Float-float partial slices summed per row, one thread a row (the slices of a row are
+// N entries apart, so consecutive threads read consecutive entries of every slice).
+// Runs of 32 slices are added in float-float with the accurate double-word addition
+// (two TwoSums and two renormalisations, relative error below 3 * 2^-48 an addition);
+// the run sums are added in float64, 1/32 of the float64 operations of a float64
+// summation of every slice.  For the many slices of the symmetric sums and of the
+// stored symmetric matrix (one per 128-node tile).
+__global__ void k_sum_slices_ff(int N, int nsplit, const float2* __restrict__ partial,
+                                double* __restrict__ out, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = 0.0;
+    for (int s0 = 0; s0 < nsplit; s0 += 32) {
+        const int s1 = min(s0 + 32, nsplit);
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 8
+        for (int sp = s0; sp < s1; ++sp) {
+            const float2 v = partial[(size_t)sp * N + i];
+            float sh, eh, sl, el;
+            two_sum(hi, v.x, sh, eh);
+            two_sum(lo, v.y, sl, el);
+            eh += sl;
+            hi = sh + eh;                 // fast two-sum: |sh| >= |eh|
+            eh -= hi - sh;
+            eh += el;
+            lo = eh;
+            sh = hi + lo;
+            lo -= sh - hi;
+            hi = sh;
+        }
+        acc += (double)hi + (double)lo;
+    }
+    out[i] = acc;
+}
+
+// add_out != 0: the row starts from out[i] (the slices already summed there)
 __global__ void k_near_apply64(int N, int pp, const int* __restrict__ row_ptr,
                                const int* __restrict__ blk_patch, const double* __restrict__ vals,
                                const double* __restrict__ sigma, const double* __restrict__ partial,
-                               int nsplit, int partial_ff, int use_near, double* __restrict__ out,
-                               const int* __restrict__ skip) {
+                               int nsplit, int partial_ff, int use_near, int add_out,
+                               double* __restrict__ out, const int* __restrict__ skip) {
     if (skip && *skip) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= N) return;
     const int i = warp;
-    double acc = 0.0;
+    double acc = (add_out && lane == 0) ? out[i] : 0.0;
     for (int sp = lane; sp < nsplit; sp += 32) {
         if (partial_ff) {
             const float2 v = reinterpret_cast<const float2*>(partial)[(size_t)sp * N + i];
@@ -1310,11 +1347,19 @@ pm_status pm_near_apply(pm_surface* s, int which_K, const double* sigma, double*
     const int blocks = pm_ceil_div((long long)N * 32, threads);       // float64: warp per row
     // float32: a lane group per row, a warp while the rows fit in one wave of warps
     const bool one_wave = (long long)N * 32 <= (long long)s->ctx->num_sms * 2048;
-    if (prec == PM_PREC_FP64 || prec == PM_PREC_FF)
+    if (prec == PM_PREC_FF && nsplit > 32) {
+        // many float-float slices: summed coalesced first, then the corrections added
+        k_sum_slices_ff<<<pm_ceil_div(N, 256), 256, 0, st>>>(
+            N, nsplit, reinterpret_cast<const float2*>(s->partial), out, s->skip_flag);
+        k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
+                                                   which_K ? s->cK64 : s->cR64, sigma, s->partial,
+                                                   0, 1, use_near, 1, out, s->skip_flag);
+        s->launch_total++;
+    } else if (prec == PM_PREC_FP64 || prec == PM_PREC_FF)
         k_near_apply64<<<blocks, threads, 0, st>>>(N, s->pp, s->row_ptr, s->blk_patch,
                                                    which_K ? s->cK64 : s->cR64, sigma,
                                                    s->partial, nsplit, prec == PM_PREC_FF ? 1 : 0,
-                                                   use_near, out,
+                                                   use_near, 0, out,
                                                    s->skip_flag);
     else
         (one_wave ? k_near_apply32<32, 4> : k_near_apply32<8, 4>)
