@@ -468,7 +468,16 @@ def run_gpu(args, rank, world, local_rank):
         return {nm: p2[nm][0] / p2[nm][1] for nm in names if p2[nm][1]}
 
     klt = {}
+    in_step = {}
+    if fmm:
+        # in the step the far field runs on a second stream beside the P2P; the kernels'
+        # own times come from applies with every launch on one stream (knob fmm_streams)
+        in_step = per_launch(lambda: surf.apply_R(sig_k, prec),
+                             ["direct_R", "fmm_p2p", "fmm_m2l_gemm"])
+        surf.set_knobs(fmm_streams=1)
     klt.update(per_launch(lambda: surf.apply_R(sig_k, prec), ["direct_R", "fmm_p2p", "fmm_m2l_gemm"]))
+    if fmm:
+        surf.set_knobs(fmm_streams=0)
     klt.update(per_launch(lambda: surf.apply_R(sig_k, "ff"), ["accurate_R"]))
     klt.update(per_launch(lambda: surf.apply_K(sig_k, "ff"), ["accurate_K"]))
 
@@ -560,12 +569,21 @@ def run_gpu(args, rank, world, local_rank):
             "peak_basis": "float16 dense rate = bf16 rate (nominal ratio 1); sustained bf16 "
                           + mp_peaks["basis"],
             "step_time_share": round(ph["fmm_m2l_gemm"][0] / prof_total_ms, 4)}
+        if "fmm_m2l_gemm" in in_step:
+            roofs["fmm_m2l_gemm"]["kernel_ms_in_step"] = round(in_step["fmm_m2l_gemm"], 5)
     if fmm and ph["fmm_p2p"][1]:
         p_ms = klt["fmm_p2p"]
         roofs["fmm_p2p"] = _alu_roofline(
             "k_fmm_p2p<R> (FMM adjacent-leaf float32 sums)", FLOPS_PER_PAIR_R * fmm["p2p_pairs"],
             p_ms, peak_fp32, ph["fmm_p2p"][0] / prof_total_ms,
             TRAFFIC_BYTES.get(("k_fmm_p2p", args.workload)))
+        if "fmm_p2p" in in_step:
+            roofs["fmm_p2p"]["kernel_ms_in_step"] = round(in_step["fmm_p2p"], 5)
+            roofs["fmm_p2p"]["timing"] = (
+                "kernel_ms: the P2P alone (every launch of the apply on one stream, back to "
+                "back); kernel_ms_in_step: its event time inside the step's applies, where the "
+                "far field (P2M, M2M, M2L GEMM, L2L) runs beside it on a higher-priority "
+                "stream and shares its SMs; step_time_share from the latter")
     if not fmm and fast_R_n:
         roofs["direct_R"] = _alu_roofline(
             "k_direct_R32 (float32 remainder sum)", FLOPS_PER_PAIR_R * pairs, klt["direct_R"],

@@ -176,6 +176,10 @@ typedef struct {
     int batch_blocks_per_sm;  /* batched float32 sums: blocks aimed at per SM, 1..16 (8)     */
     int fmm_depth;            /* PM_PREC_FMM: octree depth 2..8 (cost model); a change drops
                                  the surface's tree, rebuilt at the next FMM apply          */
+    int fmm_streams;          /* PM_PREC_FMM: 1 = every kernel of an apply on the caller's
+                                 stream, one after another; 2 = the far field (P2M, M2M,
+                                 M2L, L2L) on a second stream of the highest priority, beside
+                                 the adjacent-leaf P2P on the caller's stream (2)           */
 } pm_knobs;
 
 /* Set (all fields, validated first: PM_ERR_INVALID_ARG leaves the surface

@@ -72,7 +72,7 @@ class PmSolveInfo(C.Structure):
 class PmKnobs(C.Structure):
     _fields_ = [("direct_tpt", C.c_int), ("direct_blocks_per_sm", C.c_int),
                 ("batch_rhs_per_block", C.c_int), ("batch_blocks_per_sm", C.c_int),
-                ("fmm_depth", C.c_int)]
+                ("fmm_depth", C.c_int), ("fmm_streams", C.c_int)]
 
 
 class PmTuneResult(C.Structure):

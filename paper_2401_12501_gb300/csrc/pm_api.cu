@@ -554,6 +554,7 @@ extern "C" pm_status pm_surface_clone(const pm_surface* src, pm_surface** out) {
     s->nth_total = src->nth_total;
     s->batch_rb = src->batch_rb;
     s->batch_bps = src->batch_bps;
+    s->fmm_streams = src->fmm_streams;
 #define PM_X(f) s->f = src->f;
     PM_SHARED_FIELDS(PM_X)
 #undef PM_X

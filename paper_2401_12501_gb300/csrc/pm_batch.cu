@@ -1929,7 +1929,10 @@ struct MSolver {
                 return ps;
             }
             cudaGraphExec_t ex = nullptr;
-            cudaError_t ce2 = ce == cudaSuccess ? cudaGraphInstantiate(&ex, g, 0) : ce;
+            cudaError_t ce2 =
+                ce == cudaSuccess
+                    ? cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority)
+                    : ce;
             if (g) cudaGraphDestroy(g);
             if (ce2 != cudaSuccess) {
                 cudaGetLastError();

@@ -743,7 +743,16 @@ struct PmFmmTree {
     float *Cm = nullptr, *msum = nullptr, *colscale = nullptr;
     PmTcGemm gemm[2];              // tensor-core M2L plans: remainder (0), parametrix (1)
     bool gemm_ready[2] = {false, false};
+    // the far field (P2M, M2M, M2L, L2L) runs on `far` (highest stream priority)
+    // beside the adjacent-leaf P2P on the caller's stream: fork after the source
+    // gather, join before L2P
+    cudaStream_t far = nullptr;
+    int far_prio = 0;              // also set on each far-field launch (kept by graph capture)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~PmFmmTree() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (far) cudaStreamDestroy(far);
         pm_tcgemm_free(&gemm[0]);
         pm_tcgemm_free(&gemm[1]);
         pm_dfree(vcol); pm_dfree(vsym); pm_dfree(Bm); pm_dfree(Cm); pm_dfree(msum);
@@ -866,8 +875,7 @@ void build_levels(const std::vector<double>& x, int N, double ox, double oy, dou
 
 }  // namespace
 
-pm_status pm_fmm_build(pm_surface* s) {
-    if (s->fmm) return PM_OK;
+static pm_status fmm_build_tree(pm_surface* s) {
     const int N = s->N;
     const std::vector<double>& x = s->h_x;
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -948,6 +956,14 @@ pm_status pm_fmm_build(pm_surface* s) {
     std::vector<LevelBoxes>& lv = best_lv;
     PmFmmTree* T = new PmFmmTree();
     s->fmm = T;
+    {
+        int lo = 0, hi = 0;
+        PM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        PM_CUDA_TRY(cudaStreamCreateWithPriority(&T->far, cudaStreamNonBlocking, hi));
+        T->far_prio = hi;
+        PM_CUDA_TRY(cudaEventCreateWithFlags(&T->ev_fork, cudaEventDisableTiming));
+        PM_CUDA_TRY(cudaEventCreateWithFlags(&T->ev_join, cudaEventDisableTiming));
+    }
     T->depth = depth;
     T->L0 = (float)L0;
     T->origin = make_float3((float)ox, (float)oy, (float)oz);
@@ -1135,6 +1151,14 @@ pm_status pm_fmm_build(pm_surface* s) {
     return PM_OK;
 }
 
+// A tree whose build failed part way is released, so that no later apply uses it.
+pm_status pm_fmm_build(pm_surface* s) {
+    if (s->fmm) return PM_OK;
+    const pm_status st = fmm_build_tree(s);
+    if (st != PM_OK) pm_fmm_free(s);
+    return st;
+}
+
 namespace {
 
 // Unit-box M2L operators of the context (one set per kernel family), built once.
@@ -1264,45 +1288,69 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
     t.leaf_chunks = T->leaf_chunks;
     const int* skip = s->skip_flag;
     const int depth = T->depth;
-    k_fmm_gather<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->src32, T->perm, s->N, T->sorted, skip);
-    k_fmm_p2m<<<T->nleaf, kThreads, 0, st>>>(t, T->sorted, T->M, skip);
-    for (int l = depth - 1; l >= 2; --l) {
-        const int nb = T->lev_off[l + 1] - T->lev_off[l];
-        k_fmm_m2m<<<nb, kThreads, 0, st>>>(t, l, T->M, skip);
-    }
-    const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
-    if (s->opts.fmm_tensor_m2l) {
+    if (s->opts.fmm_tensor_m2l) {       // operators and GEMM plan (host side, before the fork)
         __half* A = nullptr;
         PM_TRY(ensure_m2l_ops(s, which_K, &A));
         PM_TRY(ensure_m2l_gemm(s, T, which_K, A));
-        if (which_K && nm2l > 0) k_fmm_msum<<<nm2l, kThreads, 0, st>>>(b2, T->M, T->msum, skip);
+    }
+    k_fmm_gather<<<pm_ceil_div(s->N, 256), 256, 0, st>>>(s->src32, T->perm, s->N, T->sorted, skip);
+    PM_CUDA_TRY(cudaGetLastError());
+    // fork: the far field on T->far, the P2P on st (they share only the sorted sources);
+    // with the knob fmm_streams = 1 everything stays on st, in the same order
+    const bool two = s->fmm_streams != 1;
+    cudaStream_t fs = two ? T->far : st;
+    const int pr = two ? T->far_prio : 0;
+    const dim3 bt(kThreads);
+    if (two) {
+        PM_CUDA_TRY(cudaEventRecord(T->ev_fork, st));
+        PM_CUDA_TRY(cudaStreamWaitEvent(fs, T->ev_fork, 0));
+    }
+    PM_CUDA_TRY(pm_launch_prio(k_fmm_p2m, dim3(T->nleaf), bt, 0, fs, pr, t,
+                               (const float4*)T->sorted, T->M, skip));
+    for (int l = depth - 1; l >= 2; --l) {
+        const int nb = T->lev_off[l + 1] - T->lev_off[l];
+        PM_CUDA_TRY(pm_launch_prio(k_fmm_m2m, dim3(nb), bt, 0, fs, pr, t, l, T->M, skip));
+    }
+    const int b2 = T->lev_off[2], nm2l = T->nbox - b2;
+    if (s->opts.fmm_tensor_m2l) {
+        if (which_K && nm2l > 0)
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_msum, dim3(nm2l), bt, 0, fs, pr, b2,
+                                       (const float*)T->M, T->msum, skip));
         if (T->nv > 0)
-            k_fmm_m2l_gather<<<T->nv, kThreads, 0, st>>>(T->v_list, T->vcol, T->vsym, T->M, T->Bm,
-                                                         T->colscale, skip);
-        PM_CUDA_TRY(cudaGetLastError());
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_m2l_gather, dim3(T->nv), bt, 0, fs, pr,
+                                       (const int*)T->v_list, (const int*)T->vcol,
+                                       (const int*)T->vsym, (const float*)T->M, T->Bm,
+                                       T->colscale, skip));
         {
-            PhaseTimer pt(s, PM_PHASE_FMM_M2L, st);
-            PM_TRY(pm_tcgemm_run(&T->gemm[which_K], s->ctx->num_sms, skip, st));
+            PhaseTimer pt(s, PM_PHASE_FMM_M2L, fs);
+            PM_TRY(pm_tcgemm_run(&T->gemm[which_K], s->ctx->num_sms, skip, fs, pr));
         }
         if (which_K)
-            k_fmm_m2l_scatter<true><<<dim3(nm2l, 1), kThreads, 0, st>>>(
-                t, b2, T->Cm, T->vcol, T->vsym, T->colscale, T->msum, T->Lc, skip);
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_m2l_scatter<true>, dim3(nm2l, 1), bt, 0, fs, pr, t,
+                                       b2, (const float*)T->Cm, (const int*)T->vcol,
+                                       (const int*)T->vsym, (const float*)T->colscale,
+                                       (const float*)T->msum, T->Lc, skip));
         else
-            k_fmm_m2l_scatter<false><<<dim3(nm2l, 9), kThreads, 0, st>>>(
-                t, b2, T->Cm, T->vcol, T->vsym, T->colscale, T->msum, T->Lc, skip);
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_m2l_scatter<false>, dim3(nm2l, 9), bt, 0, fs, pr,
+                                       t, b2, (const float*)T->Cm, (const int*)T->vcol,
+                                       (const int*)T->vsym, (const float*)T->colscale,
+                                       (const float*)T->msum, T->Lc, skip));
         s->launch_total += 3 + (which_K ? 1 : 0);
     } else if (which_K) {
-        k_fmm_m2l<true><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
+        PM_CUDA_TRY(pm_launch_prio(k_fmm_m2l<true>, dim3(nm2l), bt, 0, fs, pr, t, b2,
+                                   (const float*)T->M, T->Lc, skip));
     } else {
-        k_fmm_m2l<false><<<nm2l, kThreads, 0, st>>>(t, b2, T->M, T->Lc, skip);
+        PM_CUDA_TRY(pm_launch_prio(k_fmm_m2l<false>, dim3(nm2l), bt, 0, fs, pr, t, b2,
+                                   (const float*)T->M, T->Lc, skip));
     }
     for (int l = 3; l <= depth; ++l) {
         const int nb = T->lev_off[l + 1] - T->lev_off[l];
         if (which_K)
-            k_fmm_l2l<1><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_l2l<1>, dim3(nb), bt, 0, fs, pr, t, l, T->Lc, skip));
         else
-            k_fmm_l2l<9><<<nb, kThreads, 0, st>>>(t, l, T->Lc, skip);
+            PM_CUDA_TRY(pm_launch_prio(k_fmm_l2l<9>, dim3(nb), bt, 0, fs, pr, t, l, T->Lc, skip));
     }
+    if (two) PM_CUDA_TRY(cudaEventRecord(T->ev_join, fs));
     float2* out = reinterpret_cast<float2*>(s->partial);
     const int g2 = T->np2p;
     {
@@ -1312,6 +1360,8 @@ pm_status pm_fmm_apply(pm_surface* s, int which_K, cudaStream_t st) {
         else
             k_fmm_p2p<false><<<g2, kP2PThreads, 0, st>>>(t, T->sorted, s->tgt32, s->eps2, out, skip);
     }
+    // join: L2P reads the far field's local expansions
+    if (two) PM_CUDA_TRY(cudaStreamWaitEvent(st, T->ev_join, 0));
     if (which_K) {
         k_fmm_l2p<true><<<T->nchunks, kL2PThreads, 0, st>>>(t, s->tgt32, T->Lc, out, skip);
     } else {

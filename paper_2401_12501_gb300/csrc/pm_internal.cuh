@@ -9,6 +9,7 @@
 #include <string>
 #include <memory>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/parametrix.h"
@@ -31,6 +32,26 @@ void pm_set_error(const char* fmt, ...);
         pm_status s_ = (expr);                                                     \
         if (s_ != PM_OK) return s_;                                                \
     } while (0)
+
+// Kernel launch with a scheduling priority (cudaLaunchAttributePriority): the
+// attribute travels with the launch into a captured graph, where stream
+// priorities alone are not kept.
+template <typename... KArgs, typename... Args>
+static inline cudaError_t pm_launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                                         size_t smem, cudaStream_t st, int prio,
+                                         Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = prio;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Device-side error word: kernels record a failed check here (no trap).
 enum : int {
@@ -219,6 +240,7 @@ struct pm_surface {
     // launch-shape knobs beyond pm_opts (pm_surface_set_knobs / pm_surface_autotune)
     int batch_rb = 0;             // right-hand sides per block of the batched float32 sums (0 = 16)
     int batch_bps = 0;            // blocks aimed at per SM by the batched float32 sums (0 = 8)
+    int fmm_streams = 0;          // FMM applies: 1 = one stream, 2 (0) = far field beside the P2P
 
     // scratch
     double* partial = nullptr;    // [max_split*N]
@@ -294,7 +316,8 @@ struct PmTcGemm {
 pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const void* B,
                          long long b_rows, int K, int bf16, const std::vector<int>& tiles,
                          float* C, long long ldc, long long c_cols);
-pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st);
+pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st,
+                        int prio = 0);
 pm_status pm_tcgemm_check(const PmTcGemm* g);
 void pm_tcgemm_free(PmTcGemm* g);
 

@@ -641,7 +641,9 @@ struct Solver {
         cudaGraph_t out = nullptr;
         const cudaError_t ce3 = cudaStreamEndCapture(cs, &out);
         if (ce == cudaSuccess) ce = ce3;
-        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&W.exec, out, 0);
+        // per-node priorities: the FMM's far-field kernels keep their stream's priority
+        if (ce == cudaSuccess)
+            ce = cudaGraphInstantiate(&W.exec, out, cudaGraphInstantiateFlagUseNodePriority);
         if (ce != cudaSuccess) {
             if (out) cudaGraphDestroy(out);
             W.exec = nullptr;

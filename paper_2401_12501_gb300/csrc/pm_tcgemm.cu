@@ -417,14 +417,15 @@ pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const voi
     return PM_OK;
 }
 
-pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st) {
+pm_status pm_tcgemm_run(const PmTcGemm* g, int num_sms, const int* skip, cudaStream_t st,
+                        int prio) {
     if (g->ntiles == 0) return PM_OK;
     const int grid = std::max(1, std::min(g->ntiles, num_sms));
-    k_tc_gemm<<<grid, kThreads, kSmemBytes, st>>>(
-        *reinterpret_cast<const CUtensorMap*>(g->mapA),
-        *reinterpret_cast<const CUtensorMap*>(g->mapB), reinterpret_cast<const int4*>(g->tiles),
-        g->ntiles, g->nkb, g->bf16, g->C, g->ldc, g->err, skip);
-    PM_CUDA_TRY(cudaGetLastError());
+    const CUtensorMap mA = *reinterpret_cast<const CUtensorMap*>(g->mapA);
+    const CUtensorMap mB = *reinterpret_cast<const CUtensorMap*>(g->mapB);
+    PM_CUDA_TRY(pm_launch_prio(k_tc_gemm, dim3(grid), dim3(kThreads), kSmemBytes, st, prio, mA,
+                               mB, reinterpret_cast<const int4*>(g->tiles), g->ntiles, g->nkb,
+                               g->bf16, g->C, (long long)g->ldc, g->err, skip));
     return PM_OK;
 }
 

@@ -25,7 +25,8 @@ bool knobs_valid(const pm_knobs& k) {
            (k.batch_rhs_per_block == 0 || k.batch_rhs_per_block == 8 ||
             k.batch_rhs_per_block == 16 || k.batch_rhs_per_block == 32) &&
            k.batch_blocks_per_sm >= 0 && k.batch_blocks_per_sm <= 16 &&
-           (k.fmm_depth == 0 || (k.fmm_depth >= 2 && k.fmm_depth <= 8));
+           (k.fmm_depth == 0 || (k.fmm_depth >= 2 && k.fmm_depth <= 8)) &&
+           k.fmm_streams >= 0 && k.fmm_streams <= 2;
 }
 
 pm_knobs knobs_of(const pm_surface* s) {
@@ -35,6 +36,7 @@ pm_knobs knobs_of(const pm_surface* s) {
     k.batch_rhs_per_block = s->batch_rb;
     k.batch_blocks_per_sm = s->batch_bps;
     k.fmm_depth = s->opts.fmm_depth;
+    k.fmm_streams = s->fmm_streams;
     return k;
 }
 
@@ -45,6 +47,7 @@ void apply_knobs(pm_surface* s, const pm_knobs& k) {
     s->batch_rb = k.batch_rhs_per_block;
     s->batch_bps = k.batch_blocks_per_sm;
     s->opts.fmm_depth = k.fmm_depth;
+    s->fmm_streams = k.fmm_streams;
     s->graph_epoch++;      // captured solve graphs hold launch shapes
 }
 

@@ -13,7 +13,7 @@ import os
 import tempfile
 
 KNOB_FIELDS = ("direct_tpt", "direct_blocks_per_sm", "batch_rhs_per_block",
-               "batch_blocks_per_sm", "fmm_depth")
+               "batch_blocks_per_sm", "fmm_depth", "fmm_streams")
 
 
 def size_bucket(n: int) -> int:

@@ -125,3 +125,23 @@ def test_tensor_core_m2l_matches_direct_m2l(ctx, name):
     for k in (0, 1):
         assert rel(out[1][k], out[0][k]) < 5e-6, (k, rel(out[1][k], out[0][k]))
     assert np.array_equal(out[1][0], out[1][2])            # deterministic
+
+
+@pytest.mark.parametrize("name", ["torus_98304", "ellipsoid_9600"])
+def test_far_field_stream_changes_no_bit(ctx, name):
+    """The far field (P2M, M2M, M2L, L2L) on its own stream beside the P2P (knob
+    fmm_streams = 2, the built-in choice) and every launch on one stream (1) run the
+    same kernels on the same data: applies and a graph-driven solve agree bit for bit."""
+    import paper_2401_12501_gb300 as pm
+    wl, s = surf(ctx, name)
+    sigma = np.random.default_rng(21).standard_normal(wl.N) + 1.0
+    out = {}
+    for k in (1, 2):
+        s.set_knobs(fmm_streams=k)
+        assert s.knobs()["fmm_streams"] == k
+        out[k] = (s.apply_part(pm.PM_PART_SMOOTH_R, sigma, "fmm"),
+                  s.apply_part(pm.PM_PART_SMOOTH_K, sigma, "fmm"),
+                  s.solve(wl.f, tol=1e-8, prec="fmm")[0])
+    s.set_knobs(fmm_streams=0)
+    for a, b in zip(out[1], out[2]):
+        assert np.array_equal(a, b)

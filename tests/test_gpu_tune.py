@@ -102,7 +102,7 @@ def test_invalid_knobs_leave_the_surface_unchanged(ctx):
     _, s = surf(ctx, "ellipsoid_2400")
     before = s.knobs()
     for bad in ({"batch_rhs_per_block": 12}, {"direct_tpt": 3}, {"fmm_depth": 1},
-                {"direct_blocks_per_sm": 17}):
+                {"direct_blocks_per_sm": 17}, {"fmm_streams": 3}):
         with pytest.raises(pm.PmError):
             s.set_knobs(**bad)
         assert s.knobs() == before
