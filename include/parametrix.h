@@ -353,7 +353,8 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  * t_k = 2 pi (k + 1/2) / M[c] of a 2 pi-periodic parameter t, and at F[c] M[c]
  * oversampled points t_j = 2 pi j / (F[c] M[c]) (Sec. 6.1.4's Fourier oversampling),
  * curve after curve.  Me = sum M[c] edge nodes (at most 4,096), Fo = sum F[c] M[c]
- * oversampled points.  Host arrays, copied by the call:
+ * oversampled points, sum F[c] M[c]^2 (the interpolation matrices) at most 2^26.
+ * Host arrays, copied by the call:
  *   edge_x [Me][3], edge_d1 [Me][3] = dgamma/dt, edge_d2 [Me][3] = d2gamma/dt2,
  *   edge_nu [Me][3] the unit binormal (tangent to Gamma, normal to gamma, pointing away
  *   from Gamma), edge_a [Me] = a > 0 at the node, edge_patch [Me] the patch whose
@@ -370,7 +371,8 @@ pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrhs, double t
  *              u = K~ sigma + N_gamma mu,
  * all in float64.  Creation computes the surface quadrature of every edge node on the
  * device, with s's coefficient built in: after a later pm_surface_set_coeff(_c) on s,
- * pm_bvp_apply and pm_bvp_solve refuse the handle (PM_ERR_INVALID_ARG); create a new one.  PM_ERR_INVALID_ARG for NULL arguments, an unknown kind, bad sizes, an edge
+ * pm_bvp_apply and pm_bvp_solve refuse the handle (PM_ERR_INVALID_ARG); create a new
+ * one.  PM_ERR_INVALID_ARG for NULL arguments, an unknown kind, bad sizes, an edge
  * node not on an edge of its patch or a non-constant a for Dirichlet; PM_ERR_NO_COEFF
  * without a coefficient.
  */

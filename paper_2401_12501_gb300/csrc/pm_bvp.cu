@@ -495,6 +495,7 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const i
         pm_set_error("pm_bvp_create: built for quadrilateral patches with c = 0");
         return PM_ERR_INVALID_ARG;
     }
+    PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     pm_bvp* b = new pm_bvp();
     b->s = s;
     b->kind = kind == PM_BVP_DIRICHLET ? 1 : 0;
@@ -514,8 +515,11 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const i
         b->Me += M[c];
         b->Fo += M[c] * F[c];
     }
-    if (b->Me > 4096) {
-        pm_set_error("pm_bvp_create: %d edge nodes (at most 4096)", b->Me);
+    long long interp_entries = 0;        // the interpolation matrices: F M x M per curve
+    for (int c = 0; c < ncurves; ++c) interp_entries += (long long)F[c] * M[c] * M[c];
+    if (b->Me > 4096 || interp_entries > (1LL << 26)) {
+        pm_set_error("pm_bvp_create: %d edge nodes (at most 4096), %lld interpolation entries "
+                     "sum F M^2 (at most 2^26)", b->Me, interp_entries);
         delete b;
         return PM_ERR_INVALID_ARG;
     }
@@ -530,12 +534,17 @@ extern "C" pm_status pm_bvp_create(pm_surface* s, int kind, int ncurves, const i
             return PM_ERR_INVALID_ARG;
         }
     }
-    PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     if (b->kind) {
         // Dirichlet: a constant over the surface, the edge nodes and the oversampled points
         std::vector<double> ah(s->N), gh(3 * (size_t)s->N);
-        cudaMemcpy(ah.data(), s->a, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
-        cudaMemcpy(gh.data(), s->g, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost);
+        cudaError_t ce = cudaMemcpy(ah.data(), s->a, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(gh.data(), s->g, sizeof(double) * gh.size(), cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) {
+            pm_set_error("pm_bvp_create: %s", cudaGetErrorString(ce));
+            delete b;
+            return PM_ERR_CUDA;
+        }
         const double a0 = ah[0];
         bool ok = true;
         for (double v : ah) ok = ok && std::fabs(v - a0) <= 1e-14 * a0;
@@ -577,10 +586,15 @@ extern "C" pm_status pm_bvp_apply(pm_bvp* b, const double* sigma, const double* 
     PM_TRY(pm_dmalloc(&z, n));
     pm_status st = pm_dmalloc(&y, n);
     if (st == PM_OK) {
-        cudaMemcpy(z, sigma, sizeof(double) * b->N, cudaMemcpyHostToDevice);
-        if (b->Me) cudaMemcpy(z + b->N, mu, sizeof(double) * b->Me, cudaMemcpyHostToDevice);
-        st = apply_sys(b, z, y);
+        cudaError_t e = cudaMemcpy(z, sigma, sizeof(double) * b->N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b->Me)
+            e = cudaMemcpy(z + b->N, mu, sizeof(double) * b->Me, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            pm_set_error("pm_bvp_apply: %s", cudaGetErrorString(e));
+            st = PM_ERR_CUDA;
+        }
     }
+    if (st == PM_OK) st = apply_sys(b, z, y);
     if (st == PM_OK) {
         cudaError_t e = cudaMemcpy(out_s, y, sizeof(double) * b->N, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && b->Me) e = cudaMemcpy(out_e, y + b->N, sizeof(double) * b->Me, cudaMemcpyDeviceToHost);
@@ -617,9 +631,17 @@ extern "C" pm_status pm_bvp_solve(pm_bvp* b, const double* f, const double* f_ga
     };
     if (st != PM_OK) { cleanup(); return st; }
     const auto t0 = std::chrono::steady_clock::now();
-    cudaMemcpy(rhs, f, sizeof(double) * b->N, cudaMemcpyHostToDevice);
-    if (b->Me) cudaMemcpy(rhs + b->N, f_gamma, sizeof(double) * b->Me, cudaMemcpyHostToDevice);
-    cudaMemset(x, 0, sizeof(double) * n);
+    {
+        cudaError_t e = cudaMemcpy(rhs, f, sizeof(double) * b->N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && b->Me)
+            e = cudaMemcpy(rhs + b->N, f_gamma, sizeof(double) * b->Me, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(x, 0, sizeof(double) * n);
+        if (e != cudaSuccess) {
+            pm_set_error("pm_bvp_solve: %s", cudaGetErrorString(e));
+            cleanup();
+            return PM_ERR_CUDA;
+        }
+    }
     const int grid = pm_ceil_div(n, kT);
     std::vector<double> d;
     st = dots(b, rhs, 1, rhs, n, d);

@@ -625,13 +625,7 @@ pm_status pm_ffmat_prep(pm_surface* s, const double* sigma, cudaStream_t st) {
 pm_status pm_ffmat_apply(pm_surface* s, int which_K, int* nsplit, cudaStream_t st) {
     if (which_K && s->ffm_symK) {
         const int nt = s->ffm_symK;
-        static bool attr_set = false;            // per process (one device's attribute suffices
-        if (!attr_set) {                          // for every device: it is a function attribute)
-            PM_CUDA_TRY(cudaFuncSetAttribute(k_ffmat_symK_gemv,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSymDynSmem));
-            attr_set = true;
-        }
+        // the dynamic shared-memory limit was raised on this device by pm_surface_store_ff
         k_ffmat_symK_gemv<<<nt * (nt + 1) / 2, kST, kSymDynSmem, st>>>(
             s->ffm_K, s->ffm_s, s->N, nt, reinterpret_cast<float2*>(s->partial), s->skip_flag,
             s->ffm_err);
@@ -692,6 +686,14 @@ extern "C" pm_status pm_surface_store_ff(pm_surface* s, int which) {
     if (st == PM_OK && (which & 2)) {
         st = pm_dmalloc(&s->ffm_K, bytesK);
         s->ffm_symK = nt_sym;
+    }
+    // the symmetric GEMV's shared-memory ring is above the default 48 KB: raise the
+    // function's limit on this device (set here, outside any stream capture)
+    if (st == PM_OK && s->ffm_symK &&
+        cudaFuncSetAttribute(k_ffmat_symK_gemv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSymDynSmem) != cudaSuccess) {
+        pm_set_error("pm_surface_store_ff: cudaFuncSetAttribute failed");
+        st = PM_ERR_CUDA;
     }
     if (st == PM_OK) st = pm_dmalloc(&s->ffm_err, 1);
     if (st == PM_OK && cudaMemset(s->ffm_err, 0, sizeof(int)) != cudaSuccess) {
