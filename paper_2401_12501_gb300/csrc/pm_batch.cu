@@ -1772,14 +1772,10 @@ pm_status multi_setup(pm_ctx* ctx, pm_surface* const* ops, int nops, const int* 
                                cudaMemcpyHostToDevice));
         M->nnear = (int)nitems_v.size();
         M->near_smem = smem;
-        static std::once_flag attr_once;
-        static cudaError_t attr_err = cudaSuccess;
-        std::call_once(attr_once, [] {
-            attr_err = cudaFuncSetAttribute(k_mnear32_patch<kMultiNearRhs>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kMultiNearSmemCap);
-        });
-        PM_CUDA_TRY(attr_err);
+        // on the current device, always the same cap (never lowered under another launch)
+        PM_CUDA_TRY(cudaFuncSetAttribute(k_mnear32_patch<kMultiNearRhs>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMultiNearSmemCap));
     }
     PM_TRY(pm_dmalloc(&M->dI, nops));
     PM_TRY(pm_dmalloc(&M->items, items.size()));

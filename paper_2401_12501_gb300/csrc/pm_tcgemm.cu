@@ -402,13 +402,10 @@ pm_status pm_tcgemm_init(PmTcGemm* g, const void* A, long long a_rows, const voi
     }
     PM_TRY(pm_dmalloc(&g->err, 1));
     PM_CUDA_TRY(cudaMemset(g->err, 0, sizeof(int)));
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kSmemBytes);
-    });
-    PM_CUDA_TRY(attr_err);
+    // the shared-memory limit of the kernel, on the current device (always the same
+    // value, so that setting it again never lowers it under another thread's launch)
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes));
     g->ntiles = nt;
     g->nkb = K / kBK;
     g->bf16 = bf16;
