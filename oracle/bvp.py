@@ -42,7 +42,8 @@ import numpy as np
 from numpy.polynomial.legendre import leggauss
 
 from .kernels import INV_2PI, INV_PI
-from .operator import Discretization, NearField, apply_K, apply_R
+from . import operator as _operator
+from .operator import Discretization, NearField, apply_K, apply_R, spawn_map
 from .patch import PatchInterpolant
 from .quadrature import NEAR_FACTOR
 
@@ -251,6 +252,49 @@ def kp_near_weights(patch: PatchInterpolant, xe, nue, tol=1e-13, max_depth=18):
     return rec((-1.0, 1.0, -1.0, 1.0), root, 1)
 
 
+# ------------------------------------------------- edge-node correction rows
+def edge_correction_row(d, kind, xe, nue, P0, u0, v0, polar):
+    """One edge node's quadrature corrections over the surface nodes: on each patch
+    near x_e, the patch's weights (the polar rule about y~(u0, v0) on the node's own
+    patch P0, the adaptive near rule elsewhere) less the smooth rule's node terms.
+    kind "kp": K'_Gamma (Neumann edge rows); "k": K~ (Dirichlet edge rows)."""
+    pp = d.p * d.p
+    row = np.zeros(d.N)
+    dist = np.linalg.norm(d.centroid - xe, axis=1)
+    near = sorted(set([P0] + [int(P) for P in np.nonzero(dist < NEAR_FACTOR * d.radius)[0]]))
+    for P in near:
+        k = np.arange(P * pp, (P + 1) * pp)
+        if kind == "kp":
+            if P == P0:
+                W = kp_self_weights(d.patches[P], u0, v0, xe, nue, **polar)
+            else:
+                W = kp_near_weights(d.patches[P], xe, nue)
+            smooth = kprime_from_sources(xe[None], nue[None], d.x[k], d.a[k])[0]
+        else:
+            if P == P0:
+                W = k_edge_self_weights(d.patches[P], u0, v0)
+            else:
+                W = k_edge_near_weights(d.patches[P], xe)
+            smooth = parametrix_from_sources(xe[None], d.x[k], d.a[k])[0]
+        row[k] += W / d.a[k] - d.w[k] * smooth
+    return row
+
+
+def _edge_rows_worker(tasks):
+    return [edge_correction_row(_operator._WORKER_DISC, *t) for t in tasks]
+
+
+def edge_correction_rows(disc, tasks, processes=None):
+    """edge_correction_row for every task (kind, xe, nue, P0, u0, v0, polar), over
+    spawned processes when processes > 1 (rows are independent: same values)."""
+    if not processes or processes <= 1 or len(tasks) < 2:
+        return [edge_correction_row(disc, *t) for t in tasks]
+    nch = min(len(tasks), processes * 2)
+    size = (len(tasks) + nch - 1) // nch
+    chunks = [tasks[k:k + size] for k in range(0, len(tasks), size)]
+    return [r for rr in spawn_map(disc, _edge_rows_worker, chunks, processes) for r in rr]
+
+
 # ---------------------------------------------------------------- the system
 class NeumannBVP:
     """Dense operators of eq. NeuBVPsystem for an OpenSurface (workloads.bvp)."""
@@ -262,6 +306,7 @@ class NeumannBVP:
         self.disc = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights,
                                    coeff.a, coeff.grad_a, s.npatch, s.p)
         self.near = near if near is not None else NearField(self.disc, processes=processes)
+        self.processes = processes
         self.N, self.M = self.disc.N, osurf.M
         self.curves = osurf.curves
         self.a_edge = np.asarray(a_edge, dtype=np.float64)
@@ -310,23 +355,13 @@ class NeumannBVP:
         a = 0 if ci == 0 else nb - 1
         return a * nphi + b, (-1.0 if ci == 0 else 1.0), v0
 
+    def _edge_tasks(self, kind, polar):
+        return [(kind, self.xe[e], self.nue[e], *self.edge_patch(e), polar)
+                for e in range(self.M)]
+
     def _kp_corrections(self):
-        d = self.disc
-        pp = d.p * d.p
-        C = np.zeros((self.M, self.N))
-        for e in range(self.M):
-            xe, nue = self.xe[e], self.nue[e]
-            P0, u0, v0 = self.edge_patch(e)
-            dist = np.linalg.norm(d.centroid - xe, axis=1)
-            near = sorted(set([P0] + [int(P) for P in np.nonzero(dist < NEAR_FACTOR * d.radius)[0]]))
-            for P in near:
-                if P == P0:
-                    W = kp_self_weights(d.patches[P], u0, v0, xe, nue, **self.polar)
-                else:
-                    W = kp_near_weights(d.patches[P], xe, nue)
-                k = np.arange(P * pp, (P + 1) * pp)
-                C[e, k] += W / d.a[k] - d.w[k] * kprime_from_sources(xe[None], nue[None], d.x[k], d.a[k])[0]
-        return C
+        rows = edge_correction_rows(self.disc, self._edge_tasks("kp", self.polar), self.processes)
+        return np.array(rows).reshape(self.M, self.N)
 
     # dense system with the rank-one term in the edge row
     def matrix(self):
@@ -421,22 +456,8 @@ class DirichletBVP(NeumannBVP):
         self.KG = KG + self._k_corrections()
 
     def _k_corrections(self):
-        d = self.disc
-        pp = d.p * d.p
-        C = np.zeros((self.M, self.N))
-        for e in range(self.M):
-            xe = self.xe[e]
-            P0, u0, v0 = self.edge_patch(e)
-            dist = np.linalg.norm(d.centroid - xe, axis=1)
-            near = sorted(set([P0] + [int(P) for P in np.nonzero(dist < NEAR_FACTOR * d.radius)[0]]))
-            for P in near:
-                if P == P0:
-                    W = k_edge_self_weights(d.patches[P], u0, v0)
-                else:
-                    W = k_edge_near_weights(d.patches[P], xe)
-                k = np.arange(P * pp, (P + 1) * pp)
-                C[e, k] += W / d.a[k] - d.w[k] * parametrix_from_sources(xe[None], d.x[k], d.a[k])[0]
-        return C
+        rows = edge_correction_rows(self.disc, self._edge_tasks("k", {}), self.processes)
+        return np.array(rows).reshape(self.M, self.N)
 
     def matrix(self):
         N, M = self.N, self.M

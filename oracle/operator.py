@@ -264,19 +264,15 @@ def _worker_rows(rows):
     return [_WORKER_DISC.row_corrections(i) for i in rows]
 
 
-def _pool_map(disc, rows, processes):
+def spawn_map(disc, worker, chunks, processes):
+    """pool.map(worker, chunks) over `processes` spawned processes, each holding a
+    copy of disc (rebuilt from its arrays) as _WORKER_DISC, one BLAS thread each."""
     import multiprocessing as mp
+    import os
     J = np.concatenate([pt.J.ravel() for pt in disc.patches])
     args = (disc.x, disc.n, None, disc.H, disc.w, disc.a, disc.g, disc.npatch, disc.p)
     kw = {"self_opts": disc.self_opts, "near_tol": disc.near_tol, "jac": J, "c": disc.c,
           "b": disc.b}
-    # group rows by local node index so each worker reuses its cached polar rules
-    pp = disc.p * disc.p
-    order = sorted(rows, key=lambda i: (i % pp, i))
-    nch = processes * 4
-    size = (len(order) + nch - 1) // nch
-    chunks = [order[k:k + size] for k in range(0, len(order), size)]
-    import os
     ctx = mp.get_context("spawn")
     # one BLAS thread per worker process (the children read these at import)
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
@@ -285,13 +281,23 @@ def _pool_map(disc, rows, processes):
         os.environ[k] = "1"
     try:
         with ctx.Pool(processes, initializer=_init_worker, initargs=(args, kw)) as pool:
-            res = pool.map(_worker_rows, chunks)
+            return pool.map(worker, chunks)
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
+
+
+def _pool_map(disc, rows, processes):
+    # group rows by local node index so each worker reuses its cached polar rules
+    pp = disc.p * disc.p
+    order = sorted(rows, key=lambda i: (i % pp, i))
+    nch = processes * 4
+    size = (len(order) + nch - 1) // nch
+    chunks = [order[k:k + size] for k in range(0, len(order), size)]
+    res = spawn_map(disc, _worker_rows, chunks, processes)
     out = {}
     for ch, rr in zip(chunks, res):
         for i, r in zip(ch, rr):
