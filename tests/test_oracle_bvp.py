@@ -13,14 +13,15 @@
   (K_Gamma on gamma) matches nested QUADPACK; the double layer N_gamma[mu] from inside
   Gamma tends to +mu/(2a) + N_gamma[mu] on gamma (reading 28); the system has no null
   space and its manufactured solution converges under refinement.
+* The edge-node correction rows do not depend on how many processes compute them.
 """
 
 import numpy as np
 import pytest
 
 from conftest import oracle_processes
-from oracle.bvp import (DirichletBVP, NeumannBVP, k_edge_self_weights, kp_self_weights,
-                        trig_interp_matrix)
+from oracle.bvp import (DirichletBVP, NeumannBVP, edge_correction_rows, k_edge_self_weights,
+                        kp_self_weights, trig_interp_matrix)
 from oracle.kernels import INV_2PI
 from workloads.bvp import (band_coefficient, constant_band_coefficient, edge_a, newtonian_dirichlet,
                            newtonian_neumann, torus_band)
@@ -236,3 +237,25 @@ def test_manufactured_dirichlet_solution_converges():
         top, bot = B.apply(sigma, mu)
         assert np.abs(np.concatenate([top, bot]) - B.matrix() @ np.concatenate([sigma, mu])).max() < 1e-10
     assert errs[0] < 1e-6 and errs[1] < 1e-7 and errs[1] < errs[0] / 5, errs
+
+
+def test_edge_correction_rows_do_not_depend_on_the_worker_count():
+    """The edge-node correction rows (K'_Gamma and K~ kinds) computed over spawned
+    processes equal the serial ones to rounding (the workers rebuild the patches from
+    the surface arrays; each row's terms and their order are the same)."""
+    from oracle.operator import Discretization
+    os_ = torus_band(2, 4, 6, 16, 4)
+    co = band_coefficient(os_)
+    s = os_.surface
+    B = NeumannBVP.__new__(NeumannBVP)          # geometry only: no operators built
+    B.osurf, B.curves = os_, os_.curves
+    disc = Discretization(s.nodes, s.normals, s.tangents, s.curvature, s.weights, co.a,
+                          co.grad_a, s.npatch, s.p)
+    xe = np.concatenate([c.x for c in os_.curves])
+    nue = np.concatenate([c.nu for c in os_.curves])
+    tasks = [(kind, xe[e], nue[e], *B.edge_patch(e), {})
+             for kind, e in (("kp", 0), ("kp", 7), ("kp", 19), ("k", 3), ("k", 24))]
+    serial = np.array(edge_correction_rows(disc, tasks, None))
+    pooled = np.array(edge_correction_rows(disc, tasks, 2))
+    assert np.all(np.isfinite(serial)) and np.abs(serial).max() > 0
+    assert np.abs(pooled - serial).max() <= 1e-14 * np.abs(serial).max()
