@@ -312,6 +312,7 @@ pm_status pm_surface_get_near(const pm_surface* s, int* row_ptr, int* blk_patch,
 /* Flags of pm_solve. */
 #define PM_SOLVE_PROJECT_RHS 1u    /* subtract the mean of f instead of rejecting it */
 #define PM_SOLVE_DEVICE_PTRS 2u    /* f, u, sigma_out are device pointers            */
+#define PM_SOLVE_INITIAL_GUESS 4u  /* sigma_out holds the starting density on entry  */
 
 typedef struct {
     int iterations;          /* total inner GMRES iterations                         */
@@ -334,6 +335,11 @@ typedef struct {
  * With nrhs > 1 (and opts.batch_rhs) all right-hand sides are solved together:
  * batched multi-RHS smooth sums and lockstep GMRES; info[r].iterations then
  * counts the lockstep Arnoldi steps of the whole batch.
+ * PM_SOLVE_INITIAL_GUESS (warm start, e.g. resuming a solve from a saved density):
+ * sigma_out, required, holds a starting sigma per right-hand side on entry; the
+ * solve begins from its true residual f - A sigma (0 iterations when that already
+ * meets tol) and overwrites sigma_out with the final sigma.  Right-hand sides are
+ * then solved one at a time.
  * PM_ERR_RHS_NOT_MEAN_ZERO if f is not mean zero and PM_SOLVE_PROJECT_RHS is not set;
  * PM_ERR_NOT_CONVERGED if tol is not met within maxit inner iterations.
  */

@@ -14,7 +14,8 @@ import numpy as np
 from . import _lib, tunecache
 from ._lib import (PM_PART_NEAR_K, PM_PART_NEAR_R, PM_PART_SMOOTH_K,  # noqa: F401
                    PM_PART_SMOOTH_R, PM_PREC_FF, PM_PREC_FMM, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FP64,
-                   PM_SOLVE_DEVICE_PTRS, PM_SOLVE_PROJECT_RHS, PmError, PmSolveInfo,
+                   PM_SOLVE_DEVICE_PTRS, PM_SOLVE_INITIAL_GUESS, PM_SOLVE_PROJECT_RHS,
+                   PmError, PmSolveInfo,
                    check, default_opts, ptr)
 
 PRECISIONS = {"fp64": PM_PREC_FP64, "fp32": PM_PREC_FP32, "fp32_tc": PM_PREC_FP32_TC,
@@ -316,23 +317,31 @@ class Surface:
         return ms.value, n.value
 
     def solve(self, f, tol=1e-10, maxit=2000, prec="fp32", project_rhs=False,
-              return_sigma=False, stream=None):
-        """u (mean zero) with div(a grad u) = f; returns (u, info[, sigma])."""
+              return_sigma=False, stream=None, sigma0=None):
+        """u (mean zero) with div(a grad u) = f; returns (u, info[, sigma]).  sigma0
+        (same shape and place as f): start from this density (PM_SOLVE_INITIAL_GUESS)."""
         prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         dev = _is_device(f)
-        flags = (PM_SOLVE_PROJECT_RHS if project_rhs else 0) | (PM_SOLVE_DEVICE_PTRS if dev else 0)
+        flags = ((PM_SOLVE_PROJECT_RHS if project_rhs else 0) | (PM_SOLVE_DEVICE_PTRS if dev else 0)
+                 | (PM_SOLVE_INITIAL_GUESS if sigma0 is not None else 0))
+        want_sig = return_sigma or sigma0 is not None
         if dev:
             import torch
             nrhs = f.numel() // self.N
             u = torch.empty_like(f)
-            sig = torch.empty_like(f) if return_sigma else None
+            sig = torch.empty_like(f) if want_sig else None
+            if sigma0 is not None:
+                sig.copy_(sigma0.reshape(f.shape))
+                torch.cuda.current_stream(f.device).synchronize()   # before a caller's stream
             st = C.c_void_p(stream if stream is not None else
                             torch.cuda.current_stream(f.device).cuda_stream)
         else:
             f = np.ascontiguousarray(f, dtype=np.float64)
             nrhs = f.size // self.N
             u = np.empty_like(f)
-            sig = np.empty_like(f) if return_sigma else None
+            sig = np.empty_like(f) if want_sig else None
+            if sigma0 is not None:
+                sig[...] = np.asarray(sigma0, dtype=np.float64).reshape(f.shape)
             st = C.c_void_p(stream)
         infos = (PmSolveInfo * nrhs)()
         check(_lib.lib().pm_solve(self.handle, ptr(f), ptr(u), nrhs, float(tol), int(maxit),

@@ -23,6 +23,7 @@ PM_PREC_FP64, PM_PREC_FP32, PM_PREC_FP32_TC, PM_PREC_FF, PM_PREC_FMM = 0, 1, 2, 
 PM_PART_SMOOTH_R, PM_PART_SMOOTH_K, PM_PART_NEAR_R, PM_PART_NEAR_K = 0, 1, 2, 3
 PM_SOLVE_PROJECT_RHS = 1
 PM_SOLVE_DEVICE_PTRS = 2
+PM_SOLVE_INITIAL_GUESS = 4
 PM_BVP_NEUMANN, PM_BVP_DIRICHLET = 0, 1
 
 STATUS_NAMES = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_OOM", 3: "PM_ERR_CUDA",

@@ -900,9 +900,13 @@ extern "C" pm_status pm_solve(pm_surface* s, const double* f, double* u, int nrh
         pm_set_error("pm_solve: the surface has c != 0 (pm_surface_set_coeff_c): use pm_solve_c");
         return PM_ERR_INVALID_ARG;
     }
+    if ((flags & PM_SOLVE_INITIAL_GUESS) && !sigma_out) {
+        pm_set_error("pm_solve: PM_SOLVE_INITIAL_GUESS needs sigma_out (the starting sigma)");
+        return PM_ERR_INVALID_ARG;
+    }
     PM_CUDA_TRY(cudaSetDevice(s->ctx->device));
     const size_t N = s->N;
-    if (nrhs > 1 && s->opts.batch_rhs)
+    if (nrhs > 1 && s->opts.batch_rhs && !(flags & PM_SOLVE_INITIAL_GUESS))
         return pm_solve_batch(s, f, u, nrhs, tol, maxit, prec, flags, sigma_out, info,
                               (cudaStream_t)stream);
     pm_status worst = PM_OK;

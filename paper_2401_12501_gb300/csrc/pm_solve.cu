@@ -881,15 +881,28 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
         s->launch_total++;
         PM_TRY(S.norm2(W.f, &fnorm));
     }
-    PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * N, st));
+    // starting density: the caller's (warm start) or zero
+    const bool guess = (flags & PM_SOLVE_INITIAL_GUESS) != 0 && sigma_out;
+    if (guess)
+        PM_CUDA_TRY(cudaMemcpyAsync(W.sig, sigma_out, sizeof(double) * N, h2d, st));
+    else
+        PM_CUDA_TRY(cudaMemsetAsync(W.sig, 0, sizeof(double) * N, st));
     int iters = 0, refinements = 0, updated = 0;
     double relres = 0.0;
     bool u_current = false;            // W.u holds the representation of the current sigma
     pm_status result = PM_OK;
     if (fnorm > 0.0) {
         if (prec == PM_PREC_FP64 || prec == PM_PREC_FF) {
-            // one GMRES with accurate applies to the target, confirmed by the true residual
-            PM_TRY(S.gmres(W.f, W.sig, prec, tol * fnorm, maxit, &iters));
+            // one GMRES with accurate applies to the target (on the residual of the
+            // starting density), confirmed by the true residual
+            if (guess) {
+                PM_TRY(S.true_residual(W.f, W.sig, W.res));
+                double r0 = 0.0;
+                PM_TRY(S.norm2(W.res, &r0));
+                if (r0 > tol * fnorm) PM_TRY(S.gmres(W.res, W.sig, prec, tol * fnorm, maxit, &iters));
+            } else {
+                PM_TRY(S.gmres(W.f, W.sig, prec, tol * fnorm, maxit, &iters));
+            }
             PM_TRY(S.true_residual(W.f, W.sig, W.res));
             double rn = 0;
             PM_TRY(S.norm2(W.res, &rn));
@@ -908,8 +921,14 @@ pm_status pm_solve_impl(pm_surface* s, const double* f, double* u, double tol, i
             // ends its refinement; the next one starts from the accurate residual.  When
             // the cycle's target is below the overall tolerance the representation u is
             // enqueued before the synchronisation too.
-            PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
             double rn = fnorm;
+            if (guess) {
+                PM_TRY(S.true_residual(W.f, W.sig, W.res));
+                PM_TRY(S.norm2(W.res, &rn));
+            } else {
+                PM_CUDA_TRY(cudaMemcpyAsync(W.res, W.f, sizeof(double) * N,
+                                            cudaMemcpyDeviceToDevice, st));
+            }
             for (;;) {
                 relres = rn / fnorm;
                 if (relres <= tol || refinements >= s->opts.max_refine || iters >= maxit) break;

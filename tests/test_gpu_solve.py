@@ -9,6 +9,9 @@
   row), and u equals the oracle's K~ sigma at those rows minus the mean.
 * Mean handling (Thm. LBsolvable): a non-mean-zero f is rejected unless the
   projection flag is set; u is mean zero.
+* Warm start (PM_SOLVE_INITIAL_GUESS): a solve resumed from its own final sigma
+  takes no iteration and returns the same u; from a perturbed sigma it reaches the
+  cold solve's u.
 """
 
 import numpy as np
@@ -279,3 +282,24 @@ def test_operator_precision_residuals(ctx, prec):
     finally:
         s.close()
         ref.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fmm"])
+def test_warm_start_from_a_saved_density(ctx, prec):
+    import paper_2401_12501_gb300 as pm
+    wl, s = setup(ctx, "ellipsoid_9600")
+    w = wl.surface.weights
+    rel = lambda a, b: float(np.sqrt(np.dot(w, (a - b) ** 2) / np.dot(w, b * b)))   # noqa: E731
+    u0, i0, sig0 = s.solve(wl.f, tol=1e-10, prec=prec, return_sigma=True)
+    assert i0[0].iterations > 0
+    u1, i1, sig1 = s.solve(wl.f, tol=1e-10, prec=prec, return_sigma=True, sigma0=sig0)
+    assert i1[0].iterations == 0 and i1[0].residual <= 1e-10
+    assert rel(u1, u0) < 1e-12 and np.array_equal(sig1, sig0)
+    pert = sig0 + 1e-3 * np.random.default_rng(3).standard_normal(wl.N) * np.abs(sig0).max()
+    u2, i2, _ = s.solve(wl.f, tol=1e-10, prec=prec, return_sigma=True, sigma0=pert)
+    assert i2[0].residual <= 1e-10 and 0 < i2[0].iterations
+    assert rel(u2, u0) < 1e-8
+    # the flag needs sigma_out (PM_ERR_INVALID_ARG = 1)
+    assert pm._lib.lib().pm_solve(s.handle, pm.ptr(np.ascontiguousarray(wl.f)),
+                                  pm.ptr(np.empty(wl.N)), 1, 1e-10, 100, pm.PM_PREC_FP32,
+                                  pm._lib.PM_SOLVE_INITIAL_GUESS, None, None, None) == 1
